@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark of the Bloch-simulation hot path: spin-steps/s on one B300.
+
+One *step* is one complete simulation of the workload (every spin through
+every discretised sequence step, with the per-ADC-sample signal sum), i.e. one
+``koma_simulate`` call = the Bloch kernel + the fixed-order reduction.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload epi512]
+    python bench.py --impl reference ...     # the FP64 CPU oracle, host cores
+
+Under torchrun (N > 1) every rank simulates its own replica of the workload
+(the path has no data exchange: spins are independent); ``value`` is the
+spin-steps of all ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Bloch spin-steps/s at <=1e-4 rel err vs FP64 oracle"
+UNIT = "spin-steps/s"
+TOL = 1e-4
+
+# Algorithmic FP32 work per unit (FMA = 2 flops; derivation in the design doc):
+# an excitation step rotates M about the step's constant field and relaxes it,
+# an ADC sample advances Mxy by one complex rotation-with-decay and adds it
+# to the signal. Steps without RF and without ADC cost nothing (merged).
+FLOPS_RF_STEP = 50
+FLOPS_ADC_SAMPLE = 8
+# FP32 peak of the part: 148 SMs x 128 lanes x 2 flops x 2032 MHz (max SM clock)
+SM_COUNT = 148
+PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * 2032e6 / 1e12
+
+WORKLOAD_TEXT = {
+    "gre32": "gre32: 32x32 grid phantom (1,024 spins), spoiled GRE 32 TRs x 10 ms on a 10 us grid "
+             "(32,000 steps, 30-deg 1 ms sinc RF, 1,024 ADC samples)",
+    "epi512": "epi512: 512x512 ellipse phantom (262,144 spins, dB0 ~ 20 Hz smooth field), single-shot "
+              "128x128 EPI, 4 us dwell, 90-deg 2 ms sinc at 4 us (17,958 steps, 16,384 ADC samples)",
+    "se128": "se128: 128^3 ellipsoid phantom (1,097,914 spins, dB0 ~ 50 Hz smooth field), 64-shot spin echo, "
+             "90/180-deg 1 ms sinc at 2 us, 256-sample readouts (81,920 steps, 16,384 ADC samples)",
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region (NVML; read only)
+# --------------------------------------------------------------------------
+class ClockSampler:
+    REASONS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
+               "sw_power_cap": 0x4, "hw_power_brake_slowdown": 0x80}
+
+    def __init__(self, device_index: int, interval_s: float = 0.002):
+        self.interval = interval_s
+        self.samples = []
+        self.reasons = set()
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._thread = None
+        self.error = None
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self._nv = pynvml
+            self._h = pynvml.nvmlDeviceGetHandleByIndex(device_index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
+        except Exception as e:  # no NVML: report the absence
+            self._nv = None
+            self.error = repr(e)
+
+    def _run(self):
+        nv = self._nv
+        while not self._stop.is_set():
+            try:
+                self.samples.append(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM))
+                r = nv.nvmlDeviceGetCurrentClocksEventReasons(self._h)
+                for name, bit in self.REASONS.items():
+                    if r & bit:
+                        self.reasons.add(name)
+            except Exception as e:
+                self.error = repr(e)
+                return
+            time.sleep(self.interval)
+
+    def start(self):
+        if self._nv is not None:
+            self._thread = threading.Thread(target=self._run, daemon=True)
+            self._thread.start()
+
+    def stop(self):
+        self._stop.set()
+        if self._thread:
+            self._thread.join()
+        out = {"sm_mhz": float(statistics.median(self.samples)) if self.samples else None,
+               "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons), "samples": len(self.samples),
+               "source": "NVML"}
+        if self.error:
+            out["error"] = self.error
+        return out
+
+
+# --------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in ("paper_2301_02702_b300/csrc/koma_kernels.cu", "paper_2301_02702_b300/csrc/koma_internal.h"):
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str):
+    """DRAM bytes per launch of the Bloch kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "bloch_fp32_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(workload)
+    if not e or e.get("kernel_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def algorithmic_flops(info: dict, n_spins: int) -> float:
+    return float(n_spins) * (info["n_rf"] * FLOPS_RF_STEP + info["n_adc"] * FLOPS_ADC_SAMPLE)
+
+
+def cpu_sample_run(ph, seq, target_s: float, threads: int):
+    """Time the oracle on a random spin sample sized for ~target_s seconds."""
+    import oracle
+    rng = np.random.default_rng(123)
+    n_cal = min(ph.n, max(threads, 8))
+    idx = np.sort(rng.choice(ph.n, n_cal, replace=False))
+    t0 = time.perf_counter()
+    oracle.simulate(ph.subset(idx), seq, threads=threads)
+    t_cal = max(time.perf_counter() - t0, 1e-3)
+    n = int(min(ph.n, max(threads, n_cal * target_s / t_cal)))
+    idx = np.sort(rng.choice(ph.n, n, replace=False))
+    return idx
+
+
+def reduce_max(x: float, world: int):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on the host cores
+# --------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2301_02702_b300.workloads import workload
+    ph, seq = workload(args.workload, "full")
+    threads = os.cpu_count() or 1
+    per_step = max(1.0, min(30.0, args.reference_budget_s / max(1, args.steps + args.warmup)))
+    idx = cpu_sample_run(ph, seq, per_step, threads)
+    sub = ph.subset(idx)
+    for _ in range(args.warmup):
+        oracle.simulate(sub, seq, threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.simulate(sub, seq, threads=threads)
+        times.append(time.perf_counter() - t0)
+    units = len(idx) * seq.n_steps
+    value = units * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "spins": ph.n, "steps_per_sim": seq.n_steps,
+                   "n_adc": seq.n_adc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{len(idx)} of {ph.n} spins (random, seed 123) x all {seq.n_steps} steps "
+                                   f"per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2301_02702_b300 import build, koma
+    from paper_2301_02702_b300.workloads import Phantom, workload
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(koma.LIB_PATH):
+        build.build()
+    barrier(world)
+
+    ph, seq = workload(args.workload, "full")
+    sim = koma.Simulator(local)
+    hp = sim.upload_phantom(ph)
+    hs = sim.upload_sequence(seq)
+    info = koma.koma_sequence_get_info(hs)
+    stream = torch.cuda.Stream(local)
+    out = torch.empty((1, seq.n_adc), dtype=torch.complex128, device=f"cuda:{local}")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > 126 MB L2
+
+    # parity in this launch configuration: PD-masked spin sample vs oracle
+    parity = None
+    if rank == 0 and not args.no_parity:
+        import oracle
+        rng = np.random.default_rng(5)
+        keep = np.sort(rng.choice(ph.n, min(ph.n, 1536), replace=False))
+        pd = np.zeros(ph.n)
+        pd[keep] = ph.pd[keep]
+        hm = sim.upload_phantom(Phantom(ph.x, ph.y, ph.z, pd, ph.t1, ph.t2, ph.dw))
+        with torch.cuda.stream(stream):
+            sim.simulate(hm, hs, "fp32", out=out, stream=stream)
+        sim.sync(stream)
+        got = out.cpu().numpy()
+        koma.koma_phantom_free(hm)
+        ref = oracle.simulate(ph.subset(keep), seq)
+        err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        parity = {"rel_err": err, "tol": TOL, "pass": err <= TOL,
+                  "sample": f"{len(keep)} random spins (others PD=0) in the full-size launch, vs FP64 oracle"}
+
+    koma.koma_set_timing(sim.ctx, True)
+    for _ in range(args.warmup):
+        sim.simulate(hp, hs, "fp32", out=out, stream=stream)
+    sim.sync(stream)
+    launch = sim.launch_info()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    k1_ms = []
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize(local)
+    clocks.start()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()                       # L2 flush between timed steps (not timed)
+            ev[i][0].record(stream)
+            sim.simulate(hp, hs, "fp32", out=out, stream=stream)
+            ev[i][1].record(stream)
+        if args.kernel_timing:
+            k1_ms.append(koma.koma_get_timing(sim.ctx)[0])
+    torch.cuda.synchronize(local)
+    barrier(world)
+    clk = clocks.stop()
+    sim.sync(stream)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    ms_max = reduce_max(ms, world)
+    units = ph.n * seq.n_steps
+    value = units * world / (ms_max / 1e3)
+
+    # end to end through the public host API: host arrays in, host signal out
+    e2e = None
+    if not args.no_e2e:
+        ctx2 = koma.koma_init(local)
+        host_sig = np.empty((1, seq.n_adc), dtype=np.complex128)
+        koma.koma_simulate_host(ctx2, ph, seq, koma.KOMA_FP32_SPLITPHASE, out=host_sig)  # warm
+        n_e2e = max(1, min(args.steps, args.e2e_steps))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            koma.koma_simulate_host(ctx2, ph, seq, koma.KOMA_FP32_SPLITPHASE, out=host_sig)
+        t_e2e = (time.perf_counter() - t0) / n_e2e
+        t_e2e = reduce_max(t_e2e, world)
+        koma.koma_destroy(ctx2)
+        n_pad = max(32, (ph.n + 31) // 32 * 32)
+        h2d = n_pad * (11 * 4 + 7 * 8) + info["n_records"] * (64 + 128)
+        e2e = {"value": units * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(seq.n_adc * 16),
+               "path": "koma_simulate_host: validation + preprocessing + uploads + simulate + signal copy-back"}
+
+    # CPU baseline: the oracle on a bounded spin sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        threads = os.cpu_count() or 1
+        idx = cpu_sample_run(ph, seq, args.cpu_target_s, threads)
+        t0 = time.perf_counter()
+        oracle.simulate(ph.subset(idx), seq, threads=threads)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(idx) * seq.n_steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{len(idx)} of {ph.n} spins (random, seed 123) x all {seq.n_steps} steps, "
+                         f"{dt:.1f} s"}
+
+    if rank == 0:
+        flops = algorithmic_flops(info, ph.n)
+        k1 = (sum(k1_ms) / len(k1_ms)) if k1_ms else None
+        achieved = flops / (k1 / 1e3) / 1e12 if k1 else None
+        roof = {"bound": "alu", "kernel": f"bloch_fp32_kernel<{launch['spins_per_thread']}>",
+                "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                "frac": (achieved / PEAK_FP32_TFLOPS) if achieved else None,
+                "traffic": measured_traffic(args.workload),
+                "kernel_ms": k1, "algorithmic_flops_per_launch": flops,
+                "peak_source": "FP32 peak 148 SMs x 128 lanes x 2 x 2032 MHz (max SM clock)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload], "spins": ph.n, "steps_per_sim": seq.n_steps,
+                       "n_adc": seq.n_adc, "n_rf": info["n_rf"], "records": info["n_records"],
+                       "precision": "KOMA_FP32_SPLITPHASE", "l2": "flushed (256 MB write) between timed steps",
+                       "parallelism": f"replicas x{world}",
+                       "launch": {k: launch[k] for k in ("grid", "block", "spins_per_thread", "spins_per_cta")}},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launch["kernels"] * args.steps,
+            "clocks": clk,
+            "parity": parity,
+        }
+        print(json.dumps(line), flush=True)
+    koma.koma_sequence_free(hs)
+    koma.koma_phantom_free(hp)
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_TEXT), default="epi512")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--cpu-target-s", type=float, default=15.0)
+    ap.add_argument("--reference-budget-s", type=float, default=150.0)
+    ap.add_argument("--no-kernel-timing", dest="kernel_timing", action="store_false")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,247 @@
+/*
+ * koma.h - C ABI of libkoma, a CUDA (sm_103a) Bloch simulator.
+ *
+ * The library computes the complex MR signal of a phantom of independent
+ * spins under a discretised pulse sequence, following the KomaMRI.jl paper
+ * (Castillo-Passi et al., "KomaMRI.jl: An Open-Source Framework for General
+ * MRI Simulations with GPU Acceleration"):
+ *   - each spin obeys the Bloch equation in the rotating frame (Eq. Bloch)
+ *     with effective field B = (B1x, B1y, G.x + dw/gamma) (Eq. "B definition");
+ *   - time is split into steps solved by first-order operator splitting,
+ *     rotation then relaxation (Eqs. rotation_Bloch, relax_Bloch);
+ *   - steps with RF (B1 != 0) rotate by the Cayley-Klein spinor of the
+ *     step's constant field (spinor equations, Eq. Rot_exc); steps without RF
+ *     precess about z by the phase integrated with the trapezoid rule over
+ *     the step's gradient vertices (Eq. Rotation_precession and the integral
+ *     form in Section "Simulation blocks, Regime Switching, and
+ *     Sequence-Aware Time Stepping");
+ *   - relaxation: Mxy e^{-dt/T2}, Mz e^{-dt/T1} + M0 (1 - e^{-dt/T1});
+ *   - the signal at every ADC time point is the sum of Mxy over all spins
+ *     (Section "GPU/CPU Parallelization", the sig[t] matrix).
+ *
+ * Units: SI. Positions m, gradients T/m, B1 T, times s, off-resonance rad/s.
+ * gamma = 2 pi x 42.577478518e6 rad/s/T (koma_gamma()).
+ *
+ * Conventions common to every entry point:
+ *   - Return value: KOMA_OK or an error code; on error the call has no
+ *     effect on its outputs and koma_last_error(ctx) describes the cause.
+ *   - Host pointers ("host") are read synchronously during the call and may
+ *     be freed afterwards. Device pointers ("device") are CUDA global-memory
+ *     pointers of the context's device, owned by the caller.
+ *   - Handles returned through an "out" pointer are owned by the caller and
+ *     released with the matching *_free / koma_destroy.
+ *   - A context is not thread-safe: use one per host thread or lock around it.
+ *   - All entry points are callable without a GPU up to the first CUDA call:
+ *     koma_init then fails with KOMA_E_CUDA.
+ */
+#ifndef KOMA_H
+#define KOMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KOMA_OK = 0,
+    KOMA_E_INVALID = 1, /* bad argument (NULL, size, NaN, T1/T2 <= 0, dt <= 0, ...) */
+    KOMA_E_NOMEM = 2,   /* device allocation failed or the memory budget is exceeded */
+    KOMA_E_CUDA = 3,    /* a CUDA runtime call failed; see koma_last_error */
+    KOMA_E_TIMEOUT = 4, /* a bounded device-side wait gave up (see koma_sync) */
+    KOMA_E_BUSY = 5     /* the object is in use by another request */
+} koma_status;
+
+typedef enum {
+    /* every operation in FP64 on the device */
+    KOMA_FP64 = 0,
+    /* rotation/relaxation in FP32; accumulated phase carried as a hi/lo FP32
+     * pair (FP64-accurate); per-CTA signal sums in FP32, cross-CTA in FP64 */
+    KOMA_FP32_SPLITPHASE = 1
+} koma_precision;
+
+typedef struct koma_ctx koma_ctx;
+typedef struct koma_phantom koma_phantom;
+typedef struct koma_sequence koma_sequence;
+
+/* Launch description of the last koma_simulate call on a context (for
+ * benchmarking and tests). */
+typedef struct {
+    int32_t kernels;          /* kernels launched by the call                */
+    int32_t grid;             /* CTAs of the Bloch kernel                     */
+    int32_t block;            /* threads per CTA                              */
+    int32_t spins_per_thread; /* spins each thread steps                      */
+    int64_t spins_per_cta;
+    int64_t n_records;        /* step records the kernel walked              */
+    int64_t partial_bytes;    /* scratch used for per-CTA signal partials     */
+    void *bloch_stream;       /* stream the kernels were launched on          */
+} koma_launch_info;
+
+/* Counts of the uploaded sequence by step class (hot-path cost model). */
+typedef struct {
+    int64_t n_steps;     /* discretised steps                                 */
+    int64_t n_rf;        /* steps with B1 != 0 (excitation regime)            */
+    int64_t n_adc;       /* ADC time points                                   */
+    int64_t n_precess;   /* steps without RF                                  */
+    int64_t n_records;   /* kernel records: RF steps + precession materialise + ADC runs */
+    int64_t n_adc_runs;  /* ADC records (each <= 64 uniformly spaced samples) */
+    int64_t n_materialize;
+} koma_sequence_info;
+
+/* gamma used by the library, rad/s/T. */
+double koma_gamma(void);
+
+/* Library version string (static storage). */
+const char *koma_version(void);
+
+/*
+ * Create a context on CUDA device `device`.
+ * mem_budget_bytes: upper bound on device memory the context may hold
+ *   (phantoms + sequences + scratch); 0 = unlimited.
+ * out: receives the context. Errors: KOMA_E_INVALID (out NULL, device < 0),
+ *   KOMA_E_CUDA (no such device / no GPU).
+ */
+koma_status koma_init(int device, size_t mem_budget_bytes, koma_ctx **out);
+
+/* Release the context and its scratch. Phantoms and sequences must be freed
+ * first (they hold a reference to the context). NULL is accepted. */
+koma_status koma_destroy(koma_ctx *ctx);
+
+/* Text of the last error on ctx ("" if none). Valid until the next call. */
+const char *koma_last_error(const koma_ctx *ctx);
+
+/* Device memory currently held by the context's objects, bytes. */
+size_t koma_mem_used(const koma_ctx *ctx);
+
+/*
+ * Upload a phantom: n spins with (host, FP64, length n each)
+ *   x, y, z   position, m                     (Phantom, Section "Overview")
+ *   pd        proton density M0, >= 0
+ *   t1, t2    relaxation times, s, > 0; +inf means no relaxation
+ *   dw        off-resonance, rad/s
+ * group_offsets: NULL, or host int64 [n_groups + 1], non-decreasing, from 0
+ *   to n: spins [group_offsets[g], group_offsets[g+1]) form signal group g
+ *   (e.g. the isochromats of one dictionary entry). NULL => one group.
+ * The arrays are copied (and converted to the device layout) synchronously;
+ * the library owns the device copy until koma_phantom_free.
+ * Errors: KOMA_E_INVALID (NULL pointer, n < 0, non-finite value other than
+ *   t1/t2 = +inf, t1 or t2 <= 0, pd < 0, bad group_offsets), KOMA_E_NOMEM,
+ *   KOMA_E_CUDA.
+ */
+koma_status koma_phantom_upload(koma_ctx *ctx, int64_t n,
+                                const double *x, const double *y, const double *z,
+                                const double *pd, const double *t1, const double *t2,
+                                const double *dw, const int64_t *group_offsets,
+                                int64_t n_groups, koma_phantom **out);
+
+/* Number of spins / groups of an uploaded phantom (-1 for NULL). */
+int64_t koma_phantom_n_spins(const koma_phantom *ph);
+int64_t koma_phantom_n_groups(const koma_phantom *ph);
+
+koma_status koma_phantom_free(koma_phantom *ph);
+
+/*
+ * Upload a discretised sequence (the DiscreteSequence of Section
+ * "Simulation blocks, Regime Switching, and Sequence-Aware Time Stepping")
+ * of n_steps steps between time points t_0 .. t_{n_steps}:
+ *   dt        host FP64 [n_steps]      step length t_{n+1} - t_n, s, > 0
+ *   gx,gy,gz  host FP64 [n_steps + 1]  gradient at each time point, T/m
+ *             (piecewise linear between time points)
+ *   b1_re, b1_im host FP64 [n_steps]   RF field, T, constant over the step;
+ *             a step is in the excitation regime iff b1 != 0
+ *   adc       host uint8 [n_steps + 1] 1 = the signal is sampled at t_i
+ *             (state after step i-1; t_0 is the initial equilibrium state)
+ * The host preprocesses it once (regime classification, FP64 cumulative
+ * gradient moments since the last RF step split into hi/lo FP32, uniform
+ * ADC runs) into step records and copies them to the device.
+ * Errors: KOMA_E_INVALID (NULL, n_steps < 0, dt <= 0 or non-finite,
+ *   non-finite G or B1, adc not 0/1), KOMA_E_NOMEM, KOMA_E_CUDA.
+ */
+koma_status koma_sequence_upload(koma_ctx *ctx, int64_t n_steps, const double *dt,
+                                 const double *gx, const double *gy, const double *gz,
+                                 const double *b1_re, const double *b1_im,
+                                 const uint8_t *adc, koma_sequence **out);
+
+/* Number of ADC samples / steps of an uploaded sequence (-1 for NULL). */
+int64_t koma_sequence_n_adc(const koma_sequence *seq);
+int64_t koma_sequence_n_steps(const koma_sequence *seq);
+/* Step-class counts of an uploaded sequence. */
+koma_status koma_sequence_get_info(const koma_sequence *seq, koma_sequence_info *info);
+
+koma_status koma_sequence_free(koma_sequence *seq);
+
+/*
+ * Host-only planning (no device, no context): validate a sequence and run
+ * the preprocessing of koma_sequence_upload, reporting the step-class
+ * counts in `info`. If rec_out is not NULL it receives the FP64 step records,
+ * 16 doubles each ([type, count, first sample, 13 payload values]; payload
+ * as documented for the upload), and rec_capacity (records) must be at
+ * least info->n_records. Record types: 0 = RF step, 1 = move the reference
+ * time (materialise precession), 2 = run of ADC samples. Errors:
+ * KOMA_E_INVALID as for koma_sequence_upload, or capacity too small.
+ */
+koma_status koma_sequence_plan(int64_t n_steps, const double *dt, const double *gx,
+                               const double *gy, const double *gz, const double *b1_re,
+                               const double *b1_im, const uint8_t *adc,
+                               koma_sequence_info *info, double *rec_out, int64_t rec_capacity);
+
+/*
+ * Simulate: enqueue the Bloch kernel and the signal reduction on `stream`
+ * (a cudaStream_t of the context's device; NULL = legacy default stream).
+ * Asynchronous: returns once the work is enqueued.
+ *   sig_dev   device FP64 [n_groups][n_adc][2] (interleaved re, im; i.e. a
+ *             complex128 [n_groups, n_adc] array), written completely.
+ * The context's scratch (per-CTA partial sums, FP32) is grown on demand with
+ * cudaMalloc, so the first call for a larger problem is not capturable.
+ * Grouped phantoms (n_groups > 1) are simulated group by group: the sum runs
+ * within each group.
+ * Errors: KOMA_E_INVALID (NULL handles, objects of another context, bad
+ *   precision), KOMA_E_NOMEM (scratch over budget), KOMA_E_CUDA (launch).
+ * Device-side waits are bounded; a wait that gives up is reported by the
+ * next koma_sync on the context.
+ */
+koma_status koma_simulate(koma_ctx *ctx, const koma_phantom *ph, const koma_sequence *seq,
+                          koma_precision precision, double *sig_dev, void *stream);
+
+/*
+ * Wait for `stream` and report device-side status: KOMA_E_TIMEOUT if a
+ * bounded wait inside a kernel of this context gave up since the last
+ * koma_sync (the flag is then cleared), KOMA_E_CUDA on an asynchronous CUDA
+ * error, else KOMA_OK.
+ */
+koma_status koma_sync(koma_ctx *ctx, void *stream);
+
+/*
+ * Kernel timing. With enable != 0, every later koma_simulate on ctx records
+ * CUDA events on its stream before the Bloch kernel, between it and the
+ * reduction, and after the reduction. koma_get_timing waits for the last
+ * call's final event and returns the two durations in milliseconds.
+ * Errors: KOMA_E_INVALID (NULL, or no timed call yet), KOMA_E_CUDA.
+ */
+koma_status koma_set_timing(koma_ctx *ctx, int enable);
+koma_status koma_get_timing(koma_ctx *ctx, float *bloch_ms, float *reduce_ms);
+
+/* Launch description of the last koma_simulate on ctx. */
+koma_status koma_get_launch_info(const koma_ctx *ctx, koma_launch_info *info);
+
+/*
+ * One call from host arrays to host signal (end-to-end path): uploads the
+ * phantom and the sequence, simulates on the context's internal stream,
+ * copies the signal to `sig_host` (host FP64 [n_groups][n_adc][2]) and
+ * frees the uploads. Synchronous. Arguments as for the three calls above.
+ */
+koma_status koma_simulate_host(koma_ctx *ctx, int64_t n,
+                               const double *x, const double *y, const double *z,
+                               const double *pd, const double *t1, const double *t2,
+                               const double *dw, const int64_t *group_offsets, int64_t n_groups,
+                               int64_t n_steps, const double *dt, const double *gx,
+                               const double *gy, const double *gz, const double *b1_re,
+                               const double *b1_im, const uint8_t *adc,
+                               koma_precision precision, double *sig_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KOMA_H */

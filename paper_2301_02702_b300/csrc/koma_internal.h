@@ -1,0 +1,117 @@
+// Internal definitions shared by the host runtime (koma_runtime.cpp) and the
+// CUDA kernels (koma_kernels.cu). Not part of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace koma {
+
+// ---------------------------------------------------------------------------
+// Step records: the discretised sequence after host preprocessing.
+//
+// The kernel keeps, per spin, the magnetisation at a reference time t_ref
+// (the end of the last RF step, or t_0). Between RF steps the state is never
+// stepped: precession + relaxation over any interval is the closed form of
+// the per-step updates (the product of the per-step e^{i phi} and decay
+// factors; Eq. Rotation_precession with the integral phase of the
+// sequence-aware time stepping section, and the relaxation update):
+//   Mxy(t) = Mxy(t_ref) e^{-tau/T2} e^{-i 2 pi (K(t).x + df tau)}
+//   Mz(t)  = M0 + (Mz(t_ref) - M0) e^{-tau/T1}
+// with tau = t - t_ref, df = dw / 2 pi (Hz) and K(t) = gammabar * integral of
+// G from t_ref to t (turns/m, trapezoid rule over the gradient vertices,
+// exact for piecewise-linear G). K and tau are accumulated on the host in
+// FP64 and stored as hi/lo FP32 pairs.
+// ---------------------------------------------------------------------------
+
+enum RecType : int32_t {
+    REC_RF = 0,     // one excitation step: rotate about the step's field, relax
+    REC_PREC = 1,   // move t_ref: materialise the state at (K, tau), then K = tau = 0
+    REC_ADC = 2,    // `count` samples at (K0 + l dK, tau0 + l dtau), l < count
+};
+
+// largest number of samples in one ADC record (the recurrence between exact
+// evaluations never runs longer than this)
+constexpr int kMaxAdcRun = 64;
+
+// 64-byte record of the FP32 split-phase path.
+//   RF:   a[0..2] gbar * gammabar * dt   (turns/m)   a[3..4] B1 * gammabar * dt (turns)
+//         a[5]    |a[3..4]|^2             a[6] dt (s)
+//   PREC: a[0..5] Kx hi,lo Ky hi,lo Kz hi,lo (turns/m)   a[6..7] tau hi,lo (s)
+//   ADC:  a[0..7] K0, tau0 as in PREC     a[8..10] dK (turns/m)   a[11] dtau (s)
+struct alignas(16) Rec32 {
+    int32_t type;
+    int32_t count;
+    int64_t k0;     // ADC: index of the first sample
+    float a[12];
+};
+static_assert(sizeof(Rec32) == 64, "Rec32 must be 64 bytes");
+
+// 128-byte record of the FP64 path (same meaning, FP64 values, no hi/lo).
+//   RF:   a[0..2] gbar*gammabar*dt  a[3..4] B1*gammabar*dt  a[5] dt
+//   PREC: a[0..2] K  a[3] tau
+//   ADC:  a[0..2] K0 a[3] tau0  a[4..6] dK  a[7] dtau
+struct alignas(16) Rec64 {
+    int32_t type;
+    int32_t count;
+    int64_t k0;
+    double a[14];
+};
+static_assert(sizeof(Rec64) == 128, "Rec64 must be 128 bytes");
+
+// Per-spin device layout: structure of arrays, each array n_pad long.
+enum P32 : int {
+    P32_XH = 0, P32_XL, P32_YH, P32_YL, P32_ZH, P32_ZL,
+    P32_FH, P32_FL,   // df = dw / 2 pi, Hz, hi/lo
+    P32_M0,
+    P32_R1, P32_R2,   // log2(e) / T1, log2(e) / T2 (0 for +inf)
+    P32_N
+};
+enum P64 : int {
+    P64_X = 0, P64_Y, P64_Z,
+    P64_F,            // df, Hz
+    P64_T1, P64_T2,   // s (+inf allowed)
+    P64_M0,
+    P64_N
+};
+
+struct BlochLaunch {
+    int grid = 0;
+    int block = 0;
+    int spins_per_thread = 0;
+    int64_t spins_per_cta = 0;
+};
+
+struct BlochArgs {
+    const float* p32 = nullptr;     // [P32_N][n_pad]
+    const double* p64 = nullptr;    // [P64_N][n_pad]
+    int64_t n_pad = 0;
+    int64_t n = 0;
+    const int64_t* cta_begin = nullptr;  // [grid + 1] first spin of each CTA (grouped), or null
+    int64_t spins_per_cta = 0;           // uniform split when cta_begin is null
+    const void* rec = nullptr;
+    int64_t n_rec = 0;
+    void* partial = nullptr;        // FP32: float2 [grid][n_adc]; FP64: double2 [grid][n_adc]
+    int64_t n_adc = 0;
+    int* status = nullptr;          // device flag word (bit 0: a bounded wait gave up)
+};
+
+struct ReduceArgs {
+    const void* partial = nullptr;
+    int grid = 0;                       // CTAs that wrote partial rows
+    const int32_t* group_cta = nullptr; // [n_groups + 1] CTA range of each group (null: one group)
+    int64_t n_groups = 1;
+    int64_t n_adc = 0;
+    double* sig = nullptr;              // [n_groups][n_adc][2]
+};
+
+// Launch helpers (koma_kernels.cu). Return a cudaError_t as int.
+int launch_bloch_fp32(const BlochArgs& a, const BlochLaunch& L, void* stream);
+int launch_bloch_fp64(const BlochArgs& a, const BlochLaunch& L, void* stream);
+int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream);
+// Largest block size the FP32 / FP64 Bloch kernels accept, and their
+// resident CTAs per SM at that size.
+int bloch_max_block();
+int bloch_ctas_per_sm(bool fp64, int spins_per_thread, int block);
+
+}  // namespace koma

@@ -1,0 +1,639 @@
+// CUDA kernels of libkoma (sm_103a).
+//
+// K1  bloch_fp32_kernel<S>  spins stepped through the record stream in FP32,
+//                           phase in hi/lo FP32, signal partials per CTA.
+// K1d bloch_fp64_kernel     the same walk in FP64 (KOMA_FP64).
+// K2  reduce_partials<P>    fixed-order FP64 sum of the per-CTA partials.
+//
+// Method: KomaMRI.jl paper, Section "Physical and Mathematical Background"
+// (Bloch equation, operator splitting, spinor rotation in the excitation
+// regime, e^{i phi} in the precession regime, relaxation) and Section
+// "Simulation blocks, Regime Switching, and Sequence-Aware Time Stepping"
+// (integral phase over piecewise-linear gradients). The signal at an ADC
+// sample is the sum of Mxy over spins (Section "GPU/CPU Parallelization").
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "koma_internal.h"
+
+namespace koma {
+namespace {
+
+constexpr int kTile = 64;                 // records per TMA tile (4 KB of Rec32)
+constexpr int kMaxBlock = 256;
+constexpr int kMaxWarps = kMaxBlock / 32;
+constexpr int kRed = 128;                 // samples held per reduction buffer
+constexpr int kV = 8;                     // samples per warp reduce-scatter
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bound on any device wait
+
+static_assert(kRed >= kMaxAdcRun, "an ADC record must fit in one reduction buffer");
+static_assert(kMaxAdcRun % kV == 0, "runs are processed in chunks of kV");
+
+// ---------------------------------------------------------------------------
+// sin(pi x), cos(pi x) in FP32.
+// Reduction: x = q/2 + r with q = rint(2x) and |r| <= 1/4; r is exact for
+// |x| < 2^22. Then sin/cos of t = pi r (|t| <= pi/4) by their Taylor series
+// (coefficients 1/n!), truncated where the remainder is below 2e-10, and the
+// quadrant q mod 4 selects/negates. Relative error ~1e-7 also for small
+// arguments (the hardware sine's absolute error would accumulate over the
+// hundreds of small rotations of a soft pulse).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sincospi_f32(float x, float* s, float* c) {
+    const float q = rintf(x + x);
+    const float r = fmaf(q, -0.5f, x);
+    const float t = r * 3.14159265358979323846f;
+    const float t2 = t * t;
+    float ps = fmaf(t2, 2.75573192239858907e-6f, -1.98412698412698413e-4f);  // 1/9!, -1/7!
+    ps = fmaf(ps, t2, 8.33333333333333333e-3f);                              // 1/5!
+    ps = fmaf(ps, t2, -1.66666666666666667e-1f);                             // -1/3!
+    ps = ps * t2;
+    const float sn = fmaf(ps, t, t);
+    float pc = fmaf(t2, -2.75573192239858907e-7f, 2.48015873015873016e-5f); // -1/10!, 1/8!
+    pc = fmaf(pc, t2, -1.38888888888888889e-3f);                             // -1/6!
+    pc = fmaf(pc, t2, 4.16666666666666667e-2f);                              // 1/4!
+    pc = fmaf(pc, t2, -0.5f);
+    const float cs = fmaf(pc, t2, 1.0f);
+    const int iq = static_cast<int>(q);
+    const bool swap = iq & 1;
+    const float s1 = swap ? cs : sn;
+    const float c1 = swap ? sn : cs;
+    *s = __int_as_float(__float_as_int(s1) ^ ((iq & 2) << 30));
+    *c = __int_as_float(__float_as_int(c1) ^ (((iq + 1) & 2) << 30));
+}
+
+// Fractional part (turns) of (ah + al)(bh + bl), to ~1e-7 absolute:
+// ah*bh = p + e exactly (FMA), p - rint(p) is exact, and the cross terms are
+// small. The integer part of the product is dropped (it is a whole turn).
+__device__ __forceinline__ float frac_product(float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    const float e = fmaf(ah, bh, -p);
+    const float r = p - rintf(p);
+    const float c = fmaf(ah, bl, fmaf(al, bh, e));
+    return r + c;
+}
+
+// ---------------------------------------------------------------------------
+// TMA (bulk async copy) + mbarrier helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Bulk copy of `bytes` (multiple of 16, 16-byte aligned ends) global -> this
+// CTA's shared memory, completing on mbarrier `bar`.
+__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void* src, uint32_t bytes,
+                                            uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+// Order this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (TMA) writes to it.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Wait for phase `parity` of `bar`, giving up after kWaitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_timer_ns() - t0 > kWaitNs) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// warp reductions (fixed butterfly order: deterministic)
+// ---------------------------------------------------------------------------
+// Reduce-scatter of kV = 8 per-lane values: returns, on every lane, the warp
+// sum of value index (lane >> 2) & 7.
+__device__ __forceinline__ float reduce_scatter8(float (&a)[kV], int lane) {
+    const bool b4 = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float keep = b4 ? a[i + 4] : a[i];
+        const float send = b4 ? a[i] : a[i + 4];
+        a[i] = keep + __shfl_xor_sync(kFull, send, 16);
+    }
+    const bool b3 = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float keep = b3 ? a[i + 2] : a[i];
+        const float send = b3 ? a[i] : a[i + 2];
+        a[i] = keep + __shfl_xor_sync(kFull, send, 8);
+    }
+    const bool b2 = lane & 4;
+    {
+        const float keep = b2 ? a[1] : a[0];
+        const float send = b2 ? a[0] : a[1];
+        a[0] = keep + __shfl_xor_sync(kFull, send, 4);
+    }
+    a[0] += __shfl_xor_sync(kFull, a[0], 2);
+    a[0] += __shfl_xor_sync(kFull, a[0], 1);
+    return a[0];
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// K1: FP32 split-phase Bloch kernel.
+//
+// Every CTA owns a contiguous spin range; thread `tid` holds spins
+// begin + s * blockDim + tid for s < S in registers for the whole sequence.
+// All threads walk the same record stream (64-record tiles brought into
+// shared memory by TMA bulk copies, double buffered) and read each record as
+// a broadcast. Per spin the kernel keeps M(t_ref) = (mx, my, mz).
+//   RF   rotate by the step's constant field and relax (one step).
+//   PREC replace M(t_ref) by M(t) at the given (K, tau).
+//   ADC  `count` samples: the first from the exact phase, the rest by the
+//        per-sample rotator z = e^{-dtau/T2} e^{-i 2 pi (dK.x + df dtau)}
+//        (exact in exact arithmetic for uniformly spaced samples).
+// Samples are summed over the thread's spins, reduce-scattered across the
+// warp, staged per warp in shared memory and summed over warps in a fixed
+// order into one FP32 partial per (CTA, sample).
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_constant__ BlochArgs A) {
+    __shared__ __align__(128) Rec32 s_rec[2][kTile];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ __align__(16) float2 s_red[2][kMaxWarps][kRed];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int nthr = blockDim.x;
+    const int nwarps = nthr >> 5;
+    const int cta = blockIdx.x;
+
+    int64_t c_begin, c_end;
+    if (A.cta_begin) {
+        c_begin = A.cta_begin[cta];
+        c_end = A.cta_begin[cta + 1];
+    } else {
+        c_begin = static_cast<int64_t>(cta) * A.spins_per_cta;
+        c_end = min(A.n, c_begin + A.spins_per_cta);
+    }
+
+    const float* __restrict__ P = A.p32;
+    const double* __restrict__ P64 = A.p64;
+    const int64_t np = A.n_pad;
+
+    float xh[S], yh[S], zh[S], fh[S], m0[S], r1[S], r2[S];
+    float mx[S], my[S], mz[S], em1[S], em2[S], zr[S], zi[S];
+    bool wact[S];  // warp-uniform: this slot holds at least one spin in the warp
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t j = c_begin + static_cast<int64_t>(s) * nthr + tid;
+        const bool v = j < c_end;
+        wact[s] = __any_sync(kFull, v);
+        xh[s] = v ? P[P32_XH * np + j] : 0.f;
+        yh[s] = v ? P[P32_YH * np + j] : 0.f;
+        zh[s] = v ? P[P32_ZH * np + j] : 0.f;
+        fh[s] = v ? P[P32_FH * np + j] : 0.f;
+        m0[s] = v ? P[P32_M0 * np + j] : 0.f;
+        r1[s] = v ? P[P32_R1 * np + j] : 0.f;
+        r2[s] = v ? P[P32_R2 * np + j] : 0.f;
+        mx[s] = 0.f;
+        my[s] = 0.f;
+        mz[s] = m0[s];
+        em1[s] = 0.f;
+        em2[s] = 0.f;
+        zr[s] = 1.f;
+        zi[s] = 0.f;
+    }
+    // lo parts and FP64 relaxation times are read on demand (rare events)
+    auto spin_index = [&](int s) { return c_begin + static_cast<int64_t>(s) * nthr + tid; };
+
+    float dt_cached = -1.f;                     // uniform: em1/em2 belong to this dt
+    float key0 = __int_as_float(0x7fc00000), key1 = 0.f, key2 = 0.f, key3 = 0.f;  // rotator key (NaN: none)
+
+    int red_buf = 0;
+    int64_t red_base = 0, red_end = 0;          // samples [red_base, red_end) staged
+    float2* __restrict__ partial = static_cast<float2*>(A.partial) + static_cast<int64_t>(cta) * A.n_adc;
+
+    auto flush = [&]() {
+        __syncthreads();
+        const int cnt = static_cast<int>(red_end - red_base);
+        for (int i = tid; i < cnt; i += nthr) {
+            float sr = 0.f, si = 0.f;
+            for (int w = 0; w < nwarps; ++w) {
+                const float2 v = s_red[red_buf][w][i];
+                sr += v.x;
+                si += v.y;
+            }
+            partial[red_base + i] = make_float2(sr, si);
+        }
+        red_buf ^= 1;
+        red_base = red_end;
+    };
+
+    const uint32_t bar[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
+    const Rec32* __restrict__ grec = static_cast<const Rec32*>(A.rec);
+    const int64_t n_tiles = (A.n_rec + kTile - 1) / kTile;
+    if (tid == 0) {
+        mbar_init(bar[0], 1);
+        mbar_init(bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int64_t t = 0; t < 2 && t < n_tiles; ++t) {
+            const int64_t nr = min(static_cast<int64_t>(kTile), A.n_rec - t * kTile);
+            tma_load_1d(smem_u32(&s_rec[t][0]), grec + t * kTile, static_cast<uint32_t>(nr * sizeof(Rec32)),
+                        bar[t]);
+        }
+    }
+
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        const int b = static_cast<int>(t & 1);
+        const bool ok = mbar_wait_bounded(bar[b], static_cast<uint32_t>((t >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            // a tile never arrived: report, wait (bounded) for the copies in
+            // flight into this CTA's shared memory, and leave
+            if (tid == 0) {
+                atomicOr(A.status, 1);
+                mbar_wait_bounded(bar[b], static_cast<uint32_t>((t >> 1) & 1));
+                if (t + 1 < n_tiles) mbar_wait_bounded(bar[b ^ 1], static_cast<uint32_t>(((t + 1) >> 1) & 1));
+            }
+            return;
+        }
+        const int nr = static_cast<int>(min(static_cast<int64_t>(kTile), A.n_rec - t * kTile));
+        for (int r = 0; r < nr; ++r) {
+            const Rec32& R = s_rec[b][r];
+            const int type = R.type;
+            if (type == REC_RF) {
+                const float gx = R.a[0], gy = R.a[1], gz = R.a[2];
+                const float bx = R.a[3], by = R.a[4], b2 = R.a[5], dt = R.a[6];
+                if (dt != dt_cached) {
+                    // relaxation factors minus one, FP64-accurate: repeated
+                    // application over long pulses must not drift
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        const int64_t j = spin_index(s);
+                        if (j < c_end) {
+                            em1[s] = static_cast<float>(expm1(-static_cast<double>(dt) / P64[P64_T1 * np + j]));
+                            em2[s] = static_cast<float>(expm1(-static_cast<double>(dt) / P64[P64_T2 * np + j]));
+                        }
+                    }
+                    dt_cached = dt;
+                }
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    if (!wact[s]) continue;
+                    // rotation vector a = gammabar dt B (turns); the spinor of
+                    // the step is the rotation by -2 pi |a| about a/|a|:
+                    // quaternion w = cos(pi|a|), u = -a sin(pi|a|)/|a|
+                    const float az = fmaf(gx, xh[s], fmaf(gy, yh[s], fmaf(gz, zh[s], fh[s] * dt)));
+                    const float a2 = fmaf(az, az, b2);
+                    const float rs = rsqrtf(a2);
+                    float sh, ch;
+                    sincospi_f32(a2 * rs, &sh, &ch);
+                    const float f = -sh * rs;
+                    const float ux = bx * f, uy = by * f, uz = az * f;
+                    // 2/|q|^2 to first order (keeps |M| from drifting over
+                    // many steps of one constant field)
+                    const float nq = fmaf(ch, ch, fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+                    const float c2 = fmaf(-2.f, nq, 4.f);
+                    // v' = v + 2 w (u x v) + 2 u x (u x v)
+                    const float px = fmaf(uy, mz[s], -uz * my[s]);
+                    const float py = fmaf(uz, mx[s], -ux * mz[s]);
+                    const float pz = fmaf(ux, my[s], -uy * mx[s]);
+                    const float qx = fmaf(uy, pz, -uz * py);
+                    const float qy = fmaf(uz, px, -ux * pz);
+                    const float qz = fmaf(ux, py, -uy * px);
+                    const float nx = fmaf(c2, fmaf(ch, px, qx), mx[s]);
+                    const float ny = fmaf(c2, fmaf(ch, py, qy), my[s]);
+                    const float nz = fmaf(c2, fmaf(ch, pz, qz), mz[s]);
+                    // relaxation over the step
+                    mx[s] = fmaf(em2[s], nx, nx);
+                    my[s] = fmaf(em2[s], ny, ny);
+                    mz[s] = fmaf(em1[s], nz - m0[s], nz);
+                }
+            } else if (type == REC_PREC || type == REC_ADC) {
+                const float kxh = R.a[0], kxl = R.a[1], kyh = R.a[2], kyl = R.a[3];
+                const float kzh = R.a[4], kzl = R.a[5], th = R.a[6], tl = R.a[7];
+                // exact state at (K, tau): phase -(K.x + df tau) turns
+                float er[S], ei[S];
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    er[s] = 0.f;
+                    ei[s] = 0.f;
+                    if (!wact[s]) continue;
+                    const int64_t j = spin_index(s);
+                    const bool v = j < c_end;
+                    const float xl = v ? P[P32_XL * np + j] : 0.f;
+                    const float yl = v ? P[P32_YL * np + j] : 0.f;
+                    const float zl = v ? P[P32_ZL * np + j] : 0.f;
+                    const float fl = v ? P[P32_FL * np + j] : 0.f;
+                    const float F = frac_product(xh[s], xl, kxh, kxl) + frac_product(yh[s], yl, kyh, kyl) +
+                                    frac_product(zh[s], zl, kzh, kzl) + frac_product(fh[s], fl, th, tl);
+                    float sn, cs;
+                    sincospi_f32(-2.f * F, &sn, &cs);
+                    const float e2 = exp2f(-th * r2[s]);
+                    er[s] = e2 * fmaf(mx[s], cs, -my[s] * sn);
+                    ei[s] = e2 * fmaf(mx[s], sn, my[s] * cs);
+                    if (type == REC_PREC) {
+                        const float e1 = exp2f(-th * r1[s]);
+                        mx[s] = er[s];
+                        my[s] = ei[s];
+                        mz[s] = fmaf(mz[s] - m0[s], e1, m0[s]);
+                    }
+                }
+                if (type == REC_ADC) {
+                    const int L = min(max(R.count, 1), kMaxAdcRun);
+                    const int64_t k0 = R.k0;
+                    if (k0 + L > red_base + kRed) flush();
+                    if (L == 1) {
+                        float sr = 0.f, si = 0.f;
+#pragma unroll
+                        for (int s = 0; s < S; ++s) {
+                            sr += er[s];
+                            si += ei[s];
+                        }
+                        sr = warp_sum(sr);
+                        si = warp_sum(si);
+                        if (lane == 0) s_red[red_buf][warp][k0 - red_base] = make_float2(sr, si);
+                    } else {
+                        const float dkx = R.a[8], dky = R.a[9], dkz = R.a[10], dtau = R.a[11];
+                        if (!(dkx == key0 && dky == key1 && dkz == key2 && dtau == key3)) {
+#pragma unroll
+                            for (int s = 0; s < S; ++s) {
+                                const float th1 = -fmaf(dkx, xh[s], fmaf(dky, yh[s], fmaf(dkz, zh[s], fh[s] * dtau)));
+                                float sn, cs;
+                                sincospi_f32(2.f * th1, &sn, &cs);
+                                const float mag = exp2f(-dtau * r2[s]);
+                                zr[s] = mag * cs;
+                                zi[s] = mag * sn;
+                            }
+                            key0 = dkx;
+                            key1 = dky;
+                            key2 = dkz;
+                            key3 = dtau;
+                        }
+                        for (int c = 0; c < L; c += kV) {
+                            float ar[kV], ai[kV];
+#pragma unroll
+                            for (int v = 0; v < kV; ++v) {
+                                ar[v] = 0.f;
+                                ai[v] = 0.f;
+#pragma unroll
+                                for (int s = 0; s < S; ++s) {
+                                    ar[v] += er[s];
+                                    ai[v] += ei[s];
+                                    const float nr_ = fmaf(er[s], zr[s], -ei[s] * zi[s]);
+                                    ei[s] = fmaf(er[s], zi[s], ei[s] * zr[s]);
+                                    er[s] = nr_;
+                                }
+                            }
+                            const float sr = reduce_scatter8(ar, lane);
+                            const float si = reduce_scatter8(ai, lane);
+                            const int vl = (lane >> 2) & 7;
+                            if ((lane & 3) == 0 && c + vl < L)
+                                s_red[red_buf][warp][k0 + c + vl - red_base] = make_float2(sr, si);
+                        }
+                    }
+                    red_end = k0 + L;
+                }
+            }
+        }
+        __syncthreads();  // everyone is done with tile buffer b
+        if (tid == 0 && t + 2 < n_tiles) {
+            fence_proxy_async_smem();
+            const int64_t nr2 = min(static_cast<int64_t>(kTile), A.n_rec - (t + 2) * kTile);
+            tma_load_1d(smem_u32(&s_rec[b][0]), grec + (t + 2) * kTile,
+                        static_cast<uint32_t>(nr2 * sizeof(Rec32)), bar[b]);
+        }
+    }
+    if (red_end > red_base) flush();
+}
+
+// ---------------------------------------------------------------------------
+// K1d: FP64 Bloch kernel (one spin per thread, every sample evaluated exactly).
+// Records are read from global memory (uniform addresses, L1 broadcast).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_constant__ BlochArgs A) {
+    __shared__ __align__(16) double2 s_red[2][kMaxWarps][kRed];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int nthr = blockDim.x;
+    const int nwarps = nthr >> 5;
+    const int cta = blockIdx.x;
+    int64_t c_begin, c_end;
+    if (A.cta_begin) {
+        c_begin = A.cta_begin[cta];
+        c_end = A.cta_begin[cta + 1];
+    } else {
+        c_begin = static_cast<int64_t>(cta) * A.spins_per_cta;
+        c_end = min(A.n, c_begin + A.spins_per_cta);
+    }
+    const int64_t j = c_begin + tid;
+    const bool v = j < c_end;
+    const int64_t np = A.n_pad;
+    const double* __restrict__ P = A.p64;
+    const double x = v ? P[P64_X * np + j] : 0.0;
+    const double y = v ? P[P64_Y * np + j] : 0.0;
+    const double z = v ? P[P64_Z * np + j] : 0.0;
+    const double f = v ? P[P64_F * np + j] : 0.0;
+    const double T1 = v ? P[P64_T1 * np + j] : 1.0;
+    const double T2 = v ? P[P64_T2 * np + j] : 1.0;
+    const double m0 = v ? P[P64_M0 * np + j] : 0.0;
+    double mx = 0.0, my = 0.0, mz = m0, em1 = 0.0, em2 = 0.0, dt_cached = -1.0;
+
+    int red_buf = 0;
+    int64_t red_base = 0, red_end = 0;
+    double2* __restrict__ partial = static_cast<double2*>(A.partial) + static_cast<int64_t>(cta) * A.n_adc;
+    auto flush = [&]() {
+        __syncthreads();
+        const int cnt = static_cast<int>(red_end - red_base);
+        for (int i = tid; i < cnt; i += nthr) {
+            double sr = 0.0, si = 0.0;
+            for (int w = 0; w < nwarps; ++w) {
+                const double2 q = s_red[red_buf][w][i];
+                sr += q.x;
+                si += q.y;
+            }
+            partial[red_base + i] = make_double2(sr, si);
+        }
+        red_buf ^= 1;
+        red_base = red_end;
+    };
+
+    const Rec64* __restrict__ rec = static_cast<const Rec64*>(A.rec);
+    for (int64_t r = 0; r < A.n_rec; ++r) {
+        const Rec64& R = rec[r];
+        const int type = R.type;
+        if (type == REC_RF) {
+            const double gx = R.a[0], gy = R.a[1], gz = R.a[2], bx = R.a[3], by = R.a[4], dt = R.a[5];
+            if (dt != dt_cached) {
+                em1 = expm1(-dt / T1);
+                em2 = expm1(-dt / T2);
+                dt_cached = dt;
+            }
+            const double az = gx * x + gy * y + gz * z + f * dt;
+            const double an = sqrt(bx * bx + by * by + az * az);
+            double sh, ch;
+            sincospi(an, &sh, &ch);
+            const double fct = an > 0.0 ? -sh / an : 0.0;
+            const double ux = bx * fct, uy = by * fct, uz = az * fct;
+            const double px = uy * mz - uz * my, py = uz * mx - ux * mz, pz = ux * my - uy * mx;
+            const double qx = uy * pz - uz * py, qy = uz * px - ux * pz, qz = ux * py - uy * px;
+            const double nx = mx + 2.0 * (ch * px + qx);
+            const double ny = my + 2.0 * (ch * py + qy);
+            const double nz = mz + 2.0 * (ch * pz + qz);
+            mx = nx + em2 * nx;
+            my = ny + em2 * ny;
+            mz = nz + em1 * (nz - m0);
+        } else if (type == REC_PREC) {
+            const double F = R.a[0] * x + R.a[1] * y + R.a[2] * z + f * R.a[3];
+            double sn, cs;
+            sincospi(-2.0 * F, &sn, &cs);
+            const double e2 = exp(-R.a[3] / T2), e1 = exp(-R.a[3] / T1);
+            const double nx = e2 * (mx * cs - my * sn);
+            const double ny = e2 * (mx * sn + my * cs);
+            mx = nx;
+            my = ny;
+            mz = m0 + (mz - m0) * e1;
+        } else if (type == REC_ADC) {
+            const int L = min(max(R.count, 1), kMaxAdcRun);
+            const int64_t k0 = R.k0;
+            if (k0 + L > red_base + kRed) flush();
+            for (int l = 0; l < L; ++l) {
+                const double kx = R.a[0] + l * R.a[4], ky = R.a[1] + l * R.a[5], kz = R.a[2] + l * R.a[6];
+                const double tau = R.a[3] + l * R.a[7];
+                const double F = kx * x + ky * y + kz * z + f * tau;
+                double sn, cs;
+                sincospi(-2.0 * F, &sn, &cs);
+                const double e2 = v ? exp(-tau / T2) : 0.0;
+                double sr = warp_sum(e2 * (mx * cs - my * sn));
+                double si = warp_sum(e2 * (mx * sn + my * cs));
+                if (lane == 0) s_red[red_buf][warp][k0 + l - red_base] = make_double2(sr, si);
+            }
+            red_end = k0 + L;
+        }
+    }
+    if (red_end > red_base) flush();
+}
+
+// ---------------------------------------------------------------------------
+// K2: sig[g][k] = sum over the CTAs c of group g of partial[c][k], in FP64,
+// in a fixed order (deterministic; threadIdx.y strides the CTAs, the eight
+// strided sums are then added in y order).
+// ---------------------------------------------------------------------------
+template <typename P>
+__global__ void __launch_bounds__(256) reduce_partials_kernel(const __grid_constant__ ReduceArgs R) {
+    __shared__ double s_re[8][32];
+    __shared__ double s_im[8][32];
+    const int64_t chunks = (R.n_adc + 31) / 32;
+    const int64_t g = blockIdx.x / chunks;
+    const int64_t k = (blockIdx.x % chunks) * 32 + threadIdx.x;
+    const int c_lo = R.group_cta ? R.group_cta[g] : 0;
+    const int c_hi = R.group_cta ? R.group_cta[g + 1] : R.grid;
+    const P* __restrict__ part = static_cast<const P*>(R.partial);
+    double re = 0.0, im = 0.0;
+    if (k < R.n_adc) {
+        for (int c = c_lo + static_cast<int>(threadIdx.y); c < c_hi; c += 8) {
+            const P p = part[static_cast<int64_t>(c) * R.n_adc + k];
+            re += p.x;
+            im += p.y;
+        }
+    }
+    s_re[threadIdx.y][threadIdx.x] = re;
+    s_im[threadIdx.y][threadIdx.x] = im;
+    __syncthreads();
+    if (threadIdx.y == 0 && k < R.n_adc) {
+        double a = 0.0, b = 0.0;
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+            a += s_re[y][threadIdx.x];
+            b += s_im[y][threadIdx.x];
+        }
+        R.sig[2 * (g * R.n_adc + k)] = a;
+        R.sig[2 * (g * R.n_adc + k) + 1] = b;
+    }
+}
+
+}  // namespace
+
+int bloch_max_block() { return kMaxBlock; }
+
+int bloch_ctas_per_sm(bool fp64, int spins_per_thread, int block) {
+    int n = 0;
+    cudaError_t e;
+    if (fp64) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_fp64_kernel, block, 0);
+    } else if (spins_per_thread == 1) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_fp32_kernel<1>, block, 0);
+    } else if (spins_per_thread == 2) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_fp32_kernel<2>, block, 0);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_fp32_kernel<4>, block, 0);
+    }
+    return e == cudaSuccess ? n : -1;
+}
+
+int launch_bloch_fp32(const BlochArgs& a, const BlochLaunch& L, void* stream) {
+    if (L.block <= 0 || L.block > kMaxBlock || L.block % 32 != 0 || L.grid <= 0) return cudaErrorInvalidValue;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (L.spins_per_thread) {
+        case 1: bloch_fp32_kernel<1><<<L.grid, L.block, 0, st>>>(a); break;
+        case 2: bloch_fp32_kernel<2><<<L.grid, L.block, 0, st>>>(a); break;
+        case 4: bloch_fp32_kernel<4><<<L.grid, L.block, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int launch_bloch_fp64(const BlochArgs& a, const BlochLaunch& L, void* stream) {
+    if (L.block <= 0 || L.block > kMaxBlock || L.block % 32 != 0 || L.grid <= 0 || L.spins_per_thread != 1)
+        return cudaErrorInvalidValue;
+    bloch_fp64_kernel<<<L.grid, L.block, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError();
+}
+
+int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream) {
+    if (r.n_adc <= 0 || r.n_groups <= 0) return cudaSuccess;
+    const int64_t chunks = (r.n_adc + 31) / 32;
+    const int64_t blocks = chunks * r.n_groups;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    dim3 blk(32, 8);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (fp64_partials)
+        reduce_partials_kernel<double2><<<static_cast<unsigned>(blocks), blk, 0, st>>>(r);
+    else
+        reduce_partials_kernel<float2><<<static_cast<unsigned>(blocks), blk, 0, st>>>(r);
+    return cudaGetLastError();
+}
+
+}  // namespace koma

@@ -1,0 +1,778 @@
+// Host runtime of libkoma: the C ABI of include/koma.h.
+//
+// Responsibilities: argument validation, conversion of the phantom to the
+// device layout, sequence preprocessing into step records (regime
+// classification, FP64 cumulative gradient moments since the last RF step,
+// uniform ADC runs), device-memory budget, launch configuration, and the
+// two kernel launches per simulation (Bloch kernel + fixed-order reduction).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "koma.h"
+#include "koma_internal.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kGammaBar = 42.577478518e6;          // Hz/T
+constexpr double kGamma = 2.0 * kPi * kGammaBar;       // rad/s/T
+constexpr double kLog2e = 1.44269504088896340736;
+
+}  // namespace
+
+struct koma_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;  // phantoms + sequences + scratch
+    int sm_count = 0;
+    std::string err;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int* d_status = nullptr;
+    cudaStream_t own_stream = nullptr;
+    koma_launch_info last{};
+    int64_t live_objects = 0;
+    // optional kernel timing: events around the Bloch kernel and the reduction
+    bool timing = false;
+    bool timing_recorded = false;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+struct koma_phantom {
+    koma_ctx* ctx = nullptr;
+    int64_t n = 0, n_pad = 0, n_groups = 1;
+    float* p32 = nullptr;
+    double* p64 = nullptr;
+    std::vector<int64_t> group_offsets;  // host copy ([n_groups + 1]) when grouped
+    size_t bytes = 0;
+    // cached CTA tables of the last grouped launch configuration
+    int64_t cfg_spc = -1;
+    int64_t* d_cta_begin = nullptr;
+    int32_t* d_group_cta = nullptr;
+    int grid = 0;
+    size_t table_bytes = 0;
+};
+
+struct koma_sequence {
+    koma_ctx* ctx = nullptr;
+    koma_sequence_info info{};
+    koma::Rec32* r32 = nullptr;
+    koma::Rec64* r64 = nullptr;
+    size_t bytes = 0;
+};
+
+namespace {
+
+koma_status fail(koma_ctx* ctx, koma_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+koma_status cuda_fail(koma_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? KOMA_E_NOMEM : KOMA_E_CUDA, "%s: %s (%s)", what,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+// Makes ctx->device current for the scope and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = (prev == dev) || cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+koma_status dev_alloc(koma_ctx* ctx, void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) return KOMA_OK;
+    if (ctx->budget && ctx->used + bytes > ctx->budget)
+        return fail(ctx, KOMA_E_NOMEM, "%s: %zu bytes would exceed the memory budget (%zu of %zu used)", what,
+                    bytes, ctx->used, ctx->budget);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return cuda_fail(ctx, e, what);
+    }
+    ctx->used += bytes;
+    return KOMA_OK;
+}
+
+void dev_free(koma_ctx* ctx, void* p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    if (ctx) ctx->used -= std::min(ctx->used, bytes);
+}
+
+inline void split(double v, float* hi, float* lo) {
+    const float h = static_cast<float>(v);
+    *hi = h;
+    *lo = static_cast<float>(v - static_cast<double>(h));
+}
+
+bool finite_or_posinf(double v) { return std::isfinite(v) || (std::isinf(v) && v > 0); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" double koma_gamma(void) { return kGamma; }
+
+extern "C" const char* koma_version(void) { return "koma-b300 0.1 (sm_103a)"; }
+
+extern "C" koma_status koma_init(int device, size_t mem_budget_bytes, koma_ctx** out) {
+    if (!out || device < 0) return KOMA_E_INVALID;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device >= count) {
+        cudaGetLastError();
+        return KOMA_E_CUDA;
+    }
+    koma_ctx* ctx = new (std::nothrow) koma_ctx();
+    if (!ctx) return KOMA_E_NOMEM;
+    ctx->device = device;
+    ctx->budget = mem_budget_bytes;
+    DeviceGuard g(device);
+    if (!g.ok || cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&ctx->d_status), sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        delete ctx;
+        return KOMA_E_CUDA;
+    }
+    *out = ctx;
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_destroy(koma_ctx* ctx) {
+    if (!ctx) return KOMA_OK;
+    if (ctx->live_objects > 0)
+        return fail(ctx, KOMA_E_BUSY, "koma_destroy: %lld phantoms/sequences still allocated",
+                    static_cast<long long>(ctx->live_objects));
+    DeviceGuard g(ctx->device);
+    for (cudaEvent_t& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+    return KOMA_OK;
+}
+
+extern "C" const char* koma_last_error(const koma_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" size_t koma_mem_used(const koma_ctx* ctx) { return ctx ? ctx->used : 0; }
+
+// ---------------------------------------------------------------------------
+// phantom
+// ---------------------------------------------------------------------------
+extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const double* x, const double* y,
+                                           const double* z, const double* pd, const double* t1,
+                                           const double* t2, const double* dw, const int64_t* group_offsets,
+                                           int64_t n_groups, koma_phantom** out) {
+    if (!ctx) return KOMA_E_INVALID;
+    if (!out) return fail(ctx, KOMA_E_INVALID, "phantom_upload: out is NULL");
+    *out = nullptr;
+    if (n < 0) return fail(ctx, KOMA_E_INVALID, "phantom_upload: n = %lld < 0", static_cast<long long>(n));
+    if (n > 0 && (!x || !y || !z || !pd || !t1 || !t2 || !dw))
+        return fail(ctx, KOMA_E_INVALID, "phantom_upload: NULL array");
+    if (group_offsets) {
+        if (n_groups < 1) return fail(ctx, KOMA_E_INVALID, "phantom_upload: n_groups < 1");
+        if (group_offsets[0] != 0 || group_offsets[n_groups] != n)
+            return fail(ctx, KOMA_E_INVALID, "phantom_upload: group_offsets must run from 0 to n");
+        for (int64_t g = 0; g < n_groups; ++g)
+            if (group_offsets[g + 1] < group_offsets[g])
+                return fail(ctx, KOMA_E_INVALID, "phantom_upload: group_offsets decrease at %lld",
+                            static_cast<long long>(g));
+    } else if (n_groups != 1 && n_groups != 0) {
+        return fail(ctx, KOMA_E_INVALID, "phantom_upload: n_groups = %lld without group_offsets",
+                    static_cast<long long>(n_groups));
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        if (!std::isfinite(x[j]) || !std::isfinite(y[j]) || !std::isfinite(z[j]) || !std::isfinite(dw[j]))
+            return fail(ctx, KOMA_E_INVALID, "phantom_upload: non-finite position/off-resonance at spin %lld",
+                        static_cast<long long>(j));
+        if (!std::isfinite(pd[j]) || pd[j] < 0)
+            return fail(ctx, KOMA_E_INVALID, "phantom_upload: pd[%lld] = %g", static_cast<long long>(j), pd[j]);
+        if (!finite_or_posinf(t1[j]) || !(t1[j] > 0) || !finite_or_posinf(t2[j]) || !(t2[j] > 0))
+            return fail(ctx, KOMA_E_INVALID, "phantom_upload: T1/T2 of spin %lld must be > 0 (or +inf)",
+                        static_cast<long long>(j));
+    }
+    koma_phantom* ph = new (std::nothrow) koma_phantom();
+    if (!ph) return fail(ctx, KOMA_E_NOMEM, "phantom_upload: host allocation");
+    ph->ctx = ctx;
+    ph->n = n;
+    ph->n_pad = std::max<int64_t>(32, (n + 31) / 32 * 32);
+    ph->n_groups = group_offsets ? n_groups : 1;
+    if (group_offsets) ph->group_offsets.assign(group_offsets, group_offsets + n_groups + 1);
+
+    std::vector<float> h32(static_cast<size_t>(koma::P32_N * ph->n_pad), 0.f);
+    std::vector<double> h64(static_cast<size_t>(koma::P64_N * ph->n_pad), 0.0);
+    const int64_t np = ph->n_pad;
+    for (int64_t j = 0; j < n; ++j) {
+        const double f = dw[j] / (2.0 * kPi);
+        split(x[j], &h32[koma::P32_XH * np + j], &h32[koma::P32_XL * np + j]);
+        split(y[j], &h32[koma::P32_YH * np + j], &h32[koma::P32_YL * np + j]);
+        split(z[j], &h32[koma::P32_ZH * np + j], &h32[koma::P32_ZL * np + j]);
+        split(f, &h32[koma::P32_FH * np + j], &h32[koma::P32_FL * np + j]);
+        h32[koma::P32_M0 * np + j] = static_cast<float>(pd[j]);
+        h32[koma::P32_R1 * np + j] = static_cast<float>(kLog2e / t1[j]);
+        h32[koma::P32_R2 * np + j] = static_cast<float>(kLog2e / t2[j]);
+        h64[koma::P64_X * np + j] = x[j];
+        h64[koma::P64_Y * np + j] = y[j];
+        h64[koma::P64_Z * np + j] = z[j];
+        h64[koma::P64_F * np + j] = f;
+        h64[koma::P64_T1 * np + j] = t1[j];
+        h64[koma::P64_T2 * np + j] = t2[j];
+        h64[koma::P64_M0 * np + j] = pd[j];
+    }
+    for (int64_t j = n; j < np; ++j) {  // padding: inert spins
+        h64[koma::P64_T1 * np + j] = 1.0;
+        h64[koma::P64_T2 * np + j] = 1.0;
+    }
+    DeviceGuard g(ctx->device);
+    const size_t b32 = h32.size() * sizeof(float), b64 = h64.size() * sizeof(double);
+    koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&ph->p32), b32, "phantom_upload");
+    if (st == KOMA_OK) st = dev_alloc(ctx, reinterpret_cast<void**>(&ph->p64), b64, "phantom_upload");
+    if (st == KOMA_OK) {
+        cudaError_t e = cudaMemcpy(ph->p32, h32.data(), b32, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(ph->p64, h64.data(), b64, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "phantom_upload: copy");
+    }
+    if (st != KOMA_OK) {
+        dev_free(ctx, ph->p32, b32);
+        dev_free(ctx, ph->p64, b64);
+        delete ph;
+        return st;
+    }
+    ph->bytes = b32 + b64;
+    ctx->live_objects++;
+    *out = ph;
+    return KOMA_OK;
+}
+
+extern "C" int64_t koma_phantom_n_spins(const koma_phantom* ph) { return ph ? ph->n : -1; }
+extern "C" int64_t koma_phantom_n_groups(const koma_phantom* ph) { return ph ? ph->n_groups : -1; }
+
+extern "C" koma_status koma_phantom_free(koma_phantom* ph) {
+    if (!ph) return KOMA_OK;
+    koma_ctx* ctx = ph->ctx;
+    DeviceGuard g(ctx->device);
+    dev_free(ctx, ph->p32, static_cast<size_t>(koma::P32_N * ph->n_pad) * sizeof(float));
+    dev_free(ctx, ph->p64, static_cast<size_t>(koma::P64_N * ph->n_pad) * sizeof(double));
+    if (ph->d_cta_begin) dev_free(ctx, ph->d_cta_begin, ph->table_bytes);
+    ctx->live_objects--;
+    delete ph;
+    return KOMA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sequence preprocessing
+// ---------------------------------------------------------------------------
+namespace {
+
+struct RecordBuilder {
+    std::vector<koma::Rec32> r32;
+    std::vector<koma::Rec64> r64;
+    int64_t n_adc = 0;
+    int64_t n_runs = 0;
+    int64_t n_mat = 0;
+    // open ADC run (relative to the current t_ref)
+    bool run_open = false;
+    int64_t run_k0 = 0;
+    int run_count = 0;
+    double run_k[3] = {0, 0, 0}, run_tau = 0;    // first sample
+    double run_dk[3] = {0, 0, 0}, run_dtau = 0;  // spacing (valid once count >= 2)
+    double last_k[3] = {0, 0, 0}, last_tau = 0;
+
+    void close_run() {
+        if (!run_open) return;
+        koma::Rec32 a{};
+        koma::Rec64 b{};
+        a.type = b.type = koma::REC_ADC;
+        a.count = b.count = run_count;
+        a.k0 = b.k0 = run_k0;
+        for (int d = 0; d < 3; ++d) {
+            split(run_k[d], &a.a[2 * d], &a.a[2 * d + 1]);
+            b.a[d] = run_k[d];
+            a.a[8 + d] = static_cast<float>(run_count > 1 ? run_dk[d] : 0.0);
+            b.a[4 + d] = run_count > 1 ? run_dk[d] : 0.0;
+        }
+        split(run_tau, &a.a[6], &a.a[7]);
+        b.a[3] = run_tau;
+        a.a[11] = static_cast<float>(run_count > 1 ? run_dtau : 0.0);
+        b.a[7] = run_count > 1 ? run_dtau : 0.0;
+        r32.push_back(a);
+        r64.push_back(b);
+        ++n_runs;
+        run_open = false;
+    }
+
+    static bool close_to(double a, double b, double tol) { return std::fabs(a - b) <= tol; }
+
+    // A sample at (K, tau) relative to t_ref.
+    void sample(const double k[3], double tau) {
+        bool joined = false;
+        if (run_open && run_count < koma::kMaxAdcRun) {
+            const double dk[3] = {k[0] - last_k[0], k[1] - last_k[1], k[2] - last_k[2]};
+            const double dtau = tau - last_tau;
+            if (run_count == 1) {
+                for (int d = 0; d < 3; ++d) run_dk[d] = dk[d];
+                run_dtau = dtau;
+                joined = true;
+            } else {
+                // uniform spacing: the per-sample rotator reproduces these
+                // samples to well below FP32 resolution
+                const double ktol = 1e-10 + 1e-12 * (std::fabs(run_dk[0]) + std::fabs(run_dk[1]) +
+                                                    std::fabs(run_dk[2]));
+                joined = close_to(dk[0], run_dk[0], ktol) && close_to(dk[1], run_dk[1], ktol) &&
+                         close_to(dk[2], run_dk[2], ktol) &&
+                         close_to(dtau, run_dtau, 1e-15 + 1e-12 * std::fabs(run_dtau));
+            }
+        }
+        if (joined) {
+            ++run_count;
+        } else {
+            close_run();
+            run_open = true;
+            run_k0 = n_adc;
+            run_count = 1;
+            for (int d = 0; d < 3; ++d) run_k[d] = k[d];
+            run_tau = tau;
+        }
+        for (int d = 0; d < 3; ++d) last_k[d] = k[d];
+        last_tau = tau;
+        ++n_adc;
+    }
+};
+
+// Validation + preprocessing shared by koma_sequence_upload and
+// koma_sequence_plan. `err` receives the message on failure.
+koma_status build_records(int64_t n_steps, const double* dt, const double* gx, const double* gy,
+                          const double* gz, const double* b1_re, const double* b1_im, const uint8_t* adc,
+                          RecordBuilder& rb, koma_sequence_info& info, std::string& err) {
+    char buf[256];
+    auto bad = [&](const char* fmt, long long i, double v) {
+        snprintf(buf, sizeof(buf), fmt, i, v);
+        err = buf;
+        return KOMA_E_INVALID;
+    };
+    if (n_steps < 0) return bad("sequence: n_steps = %lld < 0%.0g", n_steps, 0.0);
+    if (!gx || !gy || !gz || !adc || (n_steps > 0 && (!dt || !b1_re || !b1_im)))
+        return bad("sequence: NULL array (n_steps %lld)%.0g", n_steps, 0.0);
+    for (int64_t i = 0; i <= n_steps; ++i) {
+        if (!std::isfinite(gx[i]) || !std::isfinite(gy[i]) || !std::isfinite(gz[i]))
+            return bad("sequence: non-finite gradient at time point %lld%.0g", i, 0.0);
+        if (adc[i] > 1) return bad("sequence: adc[%lld] = %g (must be 0 or 1)", i, adc[i]);
+    }
+    for (int64_t n = 0; n < n_steps; ++n) {
+        if (!std::isfinite(dt[n]) || !(dt[n] > 0))
+            return bad("sequence: dt[%lld] = %g (must be finite and > 0)", n, dt[n]);
+        if (!std::isfinite(b1_re[n]) || !std::isfinite(b1_im[n]))
+            return bad("sequence: non-finite B1 at step %lld%.0g", n, 0.0);
+    }
+    info = koma_sequence_info{};
+    info.n_steps = n_steps;
+    double K[3] = {0, 0, 0}, tau = 0.0;  // moment / time since t_ref (FP64)
+    if (adc[0]) rb.sample(K, tau);
+    for (int64_t n = 0; n < n_steps; ++n) {
+        const double gm[3] = {0.5 * (gx[n] + gx[n + 1]), 0.5 * (gy[n] + gy[n + 1]), 0.5 * (gz[n] + gz[n + 1])};
+        const bool rf = b1_re[n] != 0.0 || b1_im[n] != 0.0;
+        if (rf) {
+            ++info.n_rf;
+            rb.close_run();
+            if (tau > 0.0) {  // bring the state to the start of this RF step
+                koma::Rec32 a{};
+                koma::Rec64 b{};
+                a.type = b.type = koma::REC_PREC;
+                for (int d = 0; d < 3; ++d) {
+                    split(K[d], &a.a[2 * d], &a.a[2 * d + 1]);
+                    b.a[d] = K[d];
+                }
+                split(tau, &a.a[6], &a.a[7]);
+                b.a[3] = tau;
+                rb.r32.push_back(a);
+                rb.r64.push_back(b);
+                ++rb.n_mat;
+            }
+            koma::Rec32 a{};
+            koma::Rec64 b{};
+            a.type = b.type = koma::REC_RF;
+            const double s = kGammaBar * dt[n];  // turns per tesla
+            for (int d = 0; d < 3; ++d) {
+                a.a[d] = static_cast<float>(s * gm[d]);
+                b.a[d] = s * gm[d];
+            }
+            const double bx = s * b1_re[n], by = s * b1_im[n];
+            a.a[3] = static_cast<float>(bx);
+            a.a[4] = static_cast<float>(by);
+            // |a_xy|^2 of the FP32 values; kept above zero so the kernel's
+            // rsqrt stays finite for a vanishing field
+            a.a[5] = std::max(a.a[3] * a.a[3] + a.a[4] * a.a[4], std::numeric_limits<float>::min());
+            a.a[6] = static_cast<float>(dt[n]);
+            b.a[3] = bx;
+            b.a[4] = by;
+            b.a[5] = dt[n];
+            rb.r32.push_back(a);
+            rb.r64.push_back(b);
+            for (int d = 0; d < 3; ++d) K[d] = 0.0;
+            tau = 0.0;
+        } else {
+            ++info.n_precess;
+            for (int d = 0; d < 3; ++d) K[d] += kGammaBar * dt[n] * gm[d];
+            tau += dt[n];
+        }
+        if (adc[n + 1]) rb.sample(K, tau);
+    }
+    rb.close_run();
+    info.n_adc = rb.n_adc;
+    info.n_records = static_cast<int64_t>(rb.r32.size());
+    info.n_adc_runs = rb.n_runs;
+    info.n_materialize = rb.n_mat;
+    return KOMA_OK;
+}
+
+}  // namespace
+
+extern "C" koma_status koma_sequence_plan(int64_t n_steps, const double* dt, const double* gx, const double* gy,
+                                          const double* gz, const double* b1_re, const double* b1_im,
+                                          const uint8_t* adc, koma_sequence_info* info, double* rec_out,
+                                          int64_t rec_capacity) {
+    if (!info) return KOMA_E_INVALID;
+    RecordBuilder rb;
+    std::string err;
+    koma_status st = build_records(n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, rb, *info, err);
+    if (st != KOMA_OK) return st;
+    if (rec_out) {
+        if (rec_capacity < info->n_records) return KOMA_E_INVALID;
+        for (int64_t r = 0; r < info->n_records; ++r) {
+            const koma::Rec64& q = rb.r64[static_cast<size_t>(r)];
+            double* o = rec_out + 16 * r;
+            o[0] = q.type;
+            o[1] = q.count;
+            o[2] = static_cast<double>(q.k0);
+            for (int i = 0; i < 13; ++i) o[3 + i] = q.a[i];
+        }
+    }
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, const double* dt, const double* gx,
+                                            const double* gy, const double* gz, const double* b1_re,
+                                            const double* b1_im, const uint8_t* adc, koma_sequence** out) {
+    if (!ctx) return KOMA_E_INVALID;
+    if (!out) return fail(ctx, KOMA_E_INVALID, "sequence_upload: out is NULL");
+    *out = nullptr;
+    RecordBuilder rb;
+    koma_sequence_info info{};
+    {
+        std::string err;
+        koma_status st = build_records(n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, rb, info, err);
+        if (st != KOMA_OK) return fail(ctx, st, "%s", err.c_str());
+    }
+    koma_sequence* seq = new (std::nothrow) koma_sequence();
+    if (!seq) return fail(ctx, KOMA_E_NOMEM, "sequence_upload: host allocation");
+    seq->ctx = ctx;
+    seq->info = info;
+    DeviceGuard g(ctx->device);
+    const size_t b32 = rb.r32.size() * sizeof(koma::Rec32), b64 = rb.r64.size() * sizeof(koma::Rec64);
+    koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r32), b32, "sequence_upload");
+    if (st == KOMA_OK) st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r64), b64, "sequence_upload");
+    if (st == KOMA_OK && b32) {
+        cudaError_t e = cudaMemcpy(seq->r32, rb.r32.data(), b32, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(seq->r64, rb.r64.data(), b64, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "sequence_upload: copy");
+    }
+    if (st != KOMA_OK) {
+        dev_free(ctx, seq->r32, b32);
+        dev_free(ctx, seq->r64, b64);
+        delete seq;
+        return st;
+    }
+    seq->bytes = b32 + b64;
+    ctx->live_objects++;
+    *out = seq;
+    return KOMA_OK;
+}
+
+extern "C" int64_t koma_sequence_n_adc(const koma_sequence* seq) { return seq ? seq->info.n_adc : -1; }
+extern "C" int64_t koma_sequence_n_steps(const koma_sequence* seq) { return seq ? seq->info.n_steps : -1; }
+
+extern "C" koma_status koma_sequence_get_info(const koma_sequence* seq, koma_sequence_info* info) {
+    if (!seq || !info) return KOMA_E_INVALID;
+    *info = seq->info;
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_sequence_free(koma_sequence* seq) {
+    if (!seq) return KOMA_OK;
+    koma_ctx* ctx = seq->ctx;
+    DeviceGuard g(ctx->device);
+    dev_free(ctx, seq->r32, static_cast<size_t>(seq->info.n_records) * sizeof(koma::Rec32));
+    dev_free(ctx, seq->r64, static_cast<size_t>(seq->info.n_records) * sizeof(koma::Rec64));
+    ctx->live_objects--;
+    delete seq;
+    return KOMA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// simulate
+// ---------------------------------------------------------------------------
+namespace {
+
+// Launch shape: the grid is a whole number of waves of (SMs x resident CTAs)
+// and every CTA gets the same number of spins, so no SM idles on a tail.
+koma::BlochLaunch choose_launch(const koma_ctx* ctx, int64_t n, bool fp64) {
+    koma::BlochLaunch L;
+    const int S = fp64 ? 1 : 4;
+    const int max_block = koma::bloch_max_block();
+    const int per_sm = std::max(1, koma::bloch_ctas_per_sm(fp64, S, max_block));
+    const int64_t slots = static_cast<int64_t>(ctx->sm_count) * per_sm;
+    const int64_t wave_spins = slots * max_block * S;
+    const int64_t waves = std::max<int64_t>(1, (n + wave_spins - 1) / wave_spins);
+    int64_t grid = slots * waves;
+    int64_t spc = std::max<int64_t>(1, (n + grid - 1) / grid);
+    grid = std::max<int64_t>(1, (n + spc - 1) / spc);
+    const int64_t threads = (spc + S - 1) / S;
+    L.block = static_cast<int>(std::min<int64_t>(max_block, std::max<int64_t>(32, (threads + 31) / 32 * 32)));
+    L.grid = static_cast<int>(grid);
+    L.spins_per_thread = S;
+    L.spins_per_cta = spc;
+    return L;
+}
+
+}  // namespace
+
+extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, const koma_sequence* seq,
+                                     koma_precision precision, double* sig_dev, void* stream) {
+    if (!ctx) return KOMA_E_INVALID;
+    koma_phantom* ph = const_cast<koma_phantom*>(ph_c);
+    if (!ph || !seq) return fail(ctx, KOMA_E_INVALID, "simulate: NULL phantom or sequence");
+    if (ph->ctx != ctx || seq->ctx != ctx)
+        return fail(ctx, KOMA_E_INVALID, "simulate: phantom/sequence belong to another context");
+    if (precision != KOMA_FP64 && precision != KOMA_FP32_SPLITPHASE)
+        return fail(ctx, KOMA_E_INVALID, "simulate: unknown precision %d", static_cast<int>(precision));
+    const int64_t n_adc = seq->info.n_adc;
+    if (n_adc > 0 && !sig_dev) return fail(ctx, KOMA_E_INVALID, "simulate: sig_dev is NULL");
+    const bool fp64 = precision == KOMA_FP64;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, KOMA_E_CUDA, "simulate: cannot select device %d", ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ctx->last = koma_launch_info{};
+    ctx->last.bloch_stream = stream;
+    if (n_adc == 0) return KOMA_OK;  // nothing is observed
+    const int64_t out_bytes = n_adc * ph->n_groups * 2 * static_cast<int64_t>(sizeof(double));
+    if (ph->n == 0) {
+        cudaError_t e = cudaMemsetAsync(sig_dev, 0, static_cast<size_t>(out_bytes), st);
+        return e == cudaSuccess ? KOMA_OK : cuda_fail(ctx, e, "simulate: memset");
+    }
+
+    koma::BlochLaunch L = choose_launch(ctx, ph->n, fp64);
+    if (ph->n_groups > 1) {
+        // size CTAs for the largest group (groups never share a CTA)
+        int64_t gmax = 1;
+        for (int64_t gi = 0; gi < ph->n_groups; ++gi)
+            gmax = std::max(gmax, ph->group_offsets[gi + 1] - ph->group_offsets[gi]);
+        if (gmax < L.spins_per_cta) {
+            L.spins_per_cta = gmax;
+            const int64_t threads = (gmax + L.spins_per_thread - 1) / L.spins_per_thread;
+            L.block = static_cast<int>(std::max<int64_t>(32, (threads + 31) / 32 * 32));
+        }
+    }
+    if (fp64) {
+        L.spins_per_thread = 1;
+        L.block = static_cast<int>(std::min<int64_t>(L.block, koma::bloch_max_block()));
+        L.spins_per_cta = std::min<int64_t>(L.spins_per_cta, L.block);
+        L.grid = static_cast<int>((ph->n + L.spins_per_cta - 1) / L.spins_per_cta);
+    }
+    koma::BlochArgs A;
+    A.p32 = ph->p32;
+    A.p64 = ph->p64;
+    A.n_pad = ph->n_pad;
+    A.n = ph->n;
+    A.rec = fp64 ? static_cast<const void*>(seq->r64) : static_cast<const void*>(seq->r32);
+    A.n_rec = seq->info.n_records;
+    A.n_adc = n_adc;
+    A.status = ctx->d_status;
+    A.spins_per_cta = L.spins_per_cta;
+    koma::ReduceArgs R;
+    R.n_adc = n_adc;
+    R.n_groups = ph->n_groups;
+
+    if (ph->n_groups > 1) {
+        // CTAs never straddle a group: each group gets ceil(n_g / spc) CTAs
+        if (ph->cfg_spc != L.spins_per_cta) {
+            // h[c] = first spin of CTA c; CTA c owns [h[c], h[c+1]). The last
+            // CTA of a group ends where the next non-empty group begins, so
+            // the begins alone describe the split (h[grid] = n).
+            std::vector<int64_t> h;
+            std::vector<int32_t> gc(static_cast<size_t>(ph->n_groups + 1), 0);
+            for (int64_t gi = 0; gi < ph->n_groups; ++gi) {
+                gc[gi] = static_cast<int32_t>(h.size());
+                for (int64_t s0 = ph->group_offsets[gi]; s0 < ph->group_offsets[gi + 1]; s0 += L.spins_per_cta)
+                    h.push_back(s0);
+                if (h.size() > static_cast<size_t>(std::numeric_limits<int32_t>::max() - 1))
+                    return fail(ctx, KOMA_E_INVALID, "simulate: grouped launch needs too many CTAs");
+            }
+            gc[ph->n_groups] = static_cast<int32_t>(h.size());
+            const size_t n_cta = h.size();
+            h.push_back(ph->n);
+            if (ph->d_cta_begin) dev_free(ctx, ph->d_cta_begin, ph->table_bytes);
+            ph->d_cta_begin = nullptr;
+            ph->d_group_cta = nullptr;
+            const size_t tbytes = h.size() * sizeof(int64_t) + gc.size() * sizeof(int32_t);
+            koma_status s = dev_alloc(ctx, reinterpret_cast<void**>(&ph->d_cta_begin), tbytes, "simulate: CTA table");
+            if (s != KOMA_OK) return s;
+            ph->table_bytes = tbytes;
+            ph->d_group_cta = reinterpret_cast<int32_t*>(ph->d_cta_begin + h.size());
+            cudaError_t e = cudaMemcpy(ph->d_cta_begin, h.data(), h.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(ph->d_group_cta, gc.data(), gc.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "simulate: CTA table copy");
+            ph->grid = static_cast<int>(n_cta);
+            ph->cfg_spc = L.spins_per_cta;
+        }
+        L.grid = ph->grid;
+        A.cta_begin = ph->d_cta_begin;
+        R.group_cta = ph->d_group_cta;
+    }
+
+    const size_t elem = fp64 ? 2 * sizeof(double) : 2 * sizeof(float);
+    const size_t need = static_cast<size_t>(L.grid) * static_cast<size_t>(n_adc) * elem;
+    if (need > ctx->scratch_bytes) {
+        // the stream may still use the old buffer
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "simulate: sync before scratch growth");
+        if (ctx->scratch) dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
+        ctx->scratch = nullptr;
+        ctx->scratch_bytes = 0;
+        koma_status s = dev_alloc(ctx, &ctx->scratch, need, "simulate: partial-sum scratch");
+        if (s != KOMA_OK) return s;
+        ctx->scratch_bytes = need;
+    }
+    A.partial = ctx->scratch;
+    R.partial = ctx->scratch;
+    R.grid = L.grid;
+    R.sig = sig_dev;
+
+    ctx->timing_recorded = false;
+    if (ctx->timing) cudaEventRecord(ctx->ev[0], st);
+    int e = fp64 ? koma::launch_bloch_fp64(A, L, stream) : koma::launch_bloch_fp32(A, L, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: Bloch kernel launch");
+    if (ctx->timing) cudaEventRecord(ctx->ev[1], st);
+    e = koma::launch_reduce(R, fp64, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: reduction launch");
+    if (ctx->timing) {
+        cudaEventRecord(ctx->ev[2], st);
+        ctx->timing_recorded = true;
+    }
+
+    ctx->last.kernels = 2;
+    ctx->last.grid = L.grid;
+    ctx->last.block = L.block;
+    ctx->last.spins_per_thread = L.spins_per_thread;
+    ctx->last.spins_per_cta = L.spins_per_cta;
+    ctx->last.n_records = seq->info.n_records;
+    ctx->last.partial_bytes = static_cast<int64_t>(need);
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_sync(koma_ctx* ctx, void* stream) {
+    if (!ctx) return KOMA_E_INVALID;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync");
+    int flag = 0;
+    e = cudaMemcpy(&flag, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync: status read");
+    if (flag) {
+        cudaMemset(ctx->d_status, 0, sizeof(int));
+        return fail(ctx, KOMA_E_TIMEOUT, "a bounded device-side wait gave up (status 0x%x)", flag);
+    }
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_set_timing(koma_ctx* ctx, int enable) {
+    if (!ctx) return KOMA_E_INVALID;
+    DeviceGuard g(ctx->device);
+    if (enable && !ctx->ev[0]) {
+        for (cudaEvent_t& e : ctx->ev) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return cuda_fail(ctx, r, "set_timing: event");
+        }
+    }
+    ctx->timing = enable != 0;
+    ctx->timing_recorded = false;
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_get_timing(koma_ctx* ctx, float* bloch_ms, float* reduce_ms) {
+    if (!ctx || !bloch_ms || !reduce_ms) return KOMA_E_INVALID;
+    if (!ctx->timing_recorded) return fail(ctx, KOMA_E_INVALID, "get_timing: no timed simulate call");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaEventSynchronize(ctx->ev[2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(bloch_ms, ctx->ev[0], ctx->ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(reduce_ms, ctx->ev[1], ctx->ev[2]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "get_timing");
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_get_launch_info(const koma_ctx* ctx, koma_launch_info* info) {
+    if (!ctx || !info) return KOMA_E_INVALID;
+    *info = ctx->last;
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_simulate_host(koma_ctx* ctx, int64_t n, const double* x, const double* y,
+                                          const double* z, const double* pd, const double* t1, const double* t2,
+                                          const double* dw, const int64_t* group_offsets, int64_t n_groups,
+                                          int64_t n_steps, const double* dt, const double* gx, const double* gy,
+                                          const double* gz, const double* b1_re, const double* b1_im,
+                                          const uint8_t* adc, koma_precision precision, double* sig_host) {
+    if (!ctx) return KOMA_E_INVALID;
+    koma_phantom* ph = nullptr;
+    koma_sequence* seq = nullptr;
+    double* d_sig = nullptr;
+    koma_status st = koma_phantom_upload(ctx, n, x, y, z, pd, t1, t2, dw, group_offsets, n_groups, &ph);
+    if (st == KOMA_OK) st = koma_sequence_upload(ctx, n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, &seq);
+    size_t out_bytes = 0;
+    DeviceGuard g(ctx->device);
+    if (st == KOMA_OK) {
+        out_bytes = static_cast<size_t>(seq->info.n_adc * ph->n_groups) * 2 * sizeof(double);
+        if (out_bytes && !sig_host) st = fail(ctx, KOMA_E_INVALID, "simulate_host: sig_host is NULL");
+    }
+    if (st == KOMA_OK) st = dev_alloc(ctx, reinterpret_cast<void**>(&d_sig), out_bytes, "simulate_host: signal");
+    if (st == KOMA_OK) st = koma_simulate(ctx, ph, seq, precision, d_sig, ctx->own_stream);
+    if (st == KOMA_OK && out_bytes) {
+        cudaError_t e = cudaMemcpyAsync(sig_host, d_sig, out_bytes, cudaMemcpyDeviceToHost, ctx->own_stream);
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "simulate_host: copy back");
+    }
+    if (st == KOMA_OK) st = koma_sync(ctx, ctx->own_stream);
+    if (d_sig) dev_free(ctx, d_sig, out_bytes);
+    koma_sequence_free(seq);
+    koma_phantom_free(ph);
+    return st;
+}

@@ -1,0 +1,362 @@
+"""Python binding of libkoma (ctypes; argument marshalling only).
+
+Every function named ``koma_*`` here calls the C entry point of the same name
+declared in ``include/koma.h``; all simulation work runs in the library's CUDA
+kernels. PyTorch is used only for device memory and streams (``Simulator``).
+There is no fallback: if ``libkoma.so`` is missing or fails to load, every
+call raises ``KomaError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkoma.so")
+
+KOMA_OK, KOMA_E_INVALID, KOMA_E_NOMEM, KOMA_E_CUDA, KOMA_E_TIMEOUT, KOMA_E_BUSY = range(6)
+STATUS_NAMES = {0: "KOMA_OK", 1: "KOMA_E_INVALID", 2: "KOMA_E_NOMEM", 3: "KOMA_E_CUDA",
+                4: "KOMA_E_TIMEOUT", 5: "KOMA_E_BUSY"}
+KOMA_FP64 = 0
+KOMA_FP32_SPLITPHASE = 1
+PRECISIONS = {"fp64": KOMA_FP64, "fp32": KOMA_FP32_SPLITPHASE}
+
+#: every entry point include/koma.h declares
+EXPORTS = (
+    "koma_gamma", "koma_version", "koma_init", "koma_destroy", "koma_last_error", "koma_mem_used",
+    "koma_phantom_upload", "koma_phantom_n_spins", "koma_phantom_n_groups", "koma_phantom_free",
+    "koma_sequence_upload", "koma_sequence_n_adc", "koma_sequence_n_steps", "koma_sequence_get_info",
+    "koma_sequence_free", "koma_sequence_plan", "koma_simulate", "koma_sync", "koma_set_timing",
+    "koma_get_timing", "koma_get_launch_info", "koma_simulate_host",
+)
+
+
+class KomaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class LaunchInfo(ctypes.Structure):
+    _fields_ = [("kernels", ctypes.c_int32), ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("spins_per_thread", ctypes.c_int32), ("spins_per_cta", ctypes.c_int64),
+                ("n_records", ctypes.c_int64), ("partial_bytes", ctypes.c_int64),
+                ("bloch_stream", ctypes.c_void_p)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SequenceInfo(ctypes.Structure):
+    _fields_ = [("n_steps", ctypes.c_int64), ("n_rf", ctypes.c_int64), ("n_adc", ctypes.c_int64),
+                ("n_precess", ctypes.c_int64), ("n_records", ctypes.c_int64),
+                ("n_adc_runs", ctypes.c_int64), ("n_materialize", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+def load(path: Optional[str] = None):
+    """Load libkoma.so and declare its signatures (raises KomaError if absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise KomaError(KOMA_E_CUDA, f"{p} is not built; run `python -m paper_2301_02702_b300.build`")
+        try:
+            lib = ctypes.CDLL(p)
+        except OSError as e:
+            raise KomaError(KOMA_E_CUDA, f"cannot load {p}: {e}") from e
+        st = ctypes.c_int
+        lib.koma_gamma.restype = ctypes.c_double
+        lib.koma_gamma.argtypes = []
+        lib.koma_version.restype = ctypes.c_char_p
+        lib.koma_version.argtypes = []
+        lib.koma_init.restype = st
+        lib.koma_init.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_vp)]
+        lib.koma_destroy.restype = st
+        lib.koma_destroy.argtypes = [_vp]
+        lib.koma_last_error.restype = ctypes.c_char_p
+        lib.koma_last_error.argtypes = [_vp]
+        lib.koma_mem_used.restype = ctypes.c_size_t
+        lib.koma_mem_used.argtypes = [_vp]
+        lib.koma_phantom_upload.restype = st
+        lib.koma_phantom_upload.argtypes = [_vp, ctypes.c_int64] + [_dp] * 7 + [_i64p, ctypes.c_int64,
+                                                                                 ctypes.POINTER(_vp)]
+        lib.koma_phantom_n_spins.restype = ctypes.c_int64
+        lib.koma_phantom_n_spins.argtypes = [_vp]
+        lib.koma_phantom_n_groups.restype = ctypes.c_int64
+        lib.koma_phantom_n_groups.argtypes = [_vp]
+        lib.koma_phantom_free.restype = st
+        lib.koma_phantom_free.argtypes = [_vp]
+        lib.koma_sequence_upload.restype = st
+        lib.koma_sequence_upload.argtypes = [_vp, ctypes.c_int64] + [_dp] * 6 + [_u8p, ctypes.POINTER(_vp)]
+        lib.koma_sequence_n_adc.restype = ctypes.c_int64
+        lib.koma_sequence_n_adc.argtypes = [_vp]
+        lib.koma_sequence_n_steps.restype = ctypes.c_int64
+        lib.koma_sequence_n_steps.argtypes = [_vp]
+        lib.koma_sequence_get_info.restype = st
+        lib.koma_sequence_get_info.argtypes = [_vp, ctypes.POINTER(SequenceInfo)]
+        lib.koma_sequence_free.restype = st
+        lib.koma_sequence_free.argtypes = [_vp]
+        lib.koma_sequence_plan.restype = st
+        lib.koma_sequence_plan.argtypes = ([ctypes.c_int64] + [_dp] * 6 + [_u8p, ctypes.POINTER(SequenceInfo),
+                                           _dp, ctypes.c_int64])
+        lib.koma_simulate.restype = st
+        lib.koma_simulate.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]
+        lib.koma_sync.restype = st
+        lib.koma_sync.argtypes = [_vp, _vp]
+        lib.koma_set_timing.restype = st
+        lib.koma_set_timing.argtypes = [_vp, ctypes.c_int]
+        lib.koma_get_timing.restype = st
+        lib.koma_get_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+        lib.koma_get_launch_info.restype = st
+        lib.koma_get_launch_info.argtypes = [_vp, ctypes.POINTER(LaunchInfo)]
+        lib.koma_simulate_host.restype = st
+        lib.koma_simulate_host.argtypes = ([_vp, ctypes.c_int64] + [_dp] * 7 + [_i64p, ctypes.c_int64,
+                                           ctypes.c_int64] + [_dp] * 6 + [_u8p, ctypes.c_int, _dp])
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(ctx, rc: int, what: str):
+    if rc != KOMA_OK:
+        msg = load().koma_last_error(ctx).decode() if ctx else ""
+        raise KomaError(rc, f"{what}: {msg}")
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a, t=ctypes.c_double):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+# --------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# --------------------------------------------------------------------------
+
+def koma_gamma() -> float:
+    return load().koma_gamma()
+
+
+def koma_version() -> str:
+    return load().koma_version().decode()
+
+
+def koma_init(device: int = 0, mem_budget_bytes: int = 0):
+    out = _vp()
+    rc = load().koma_init(int(device), int(mem_budget_bytes), ctypes.byref(out))
+    if rc != KOMA_OK:
+        raise KomaError(rc, f"koma_init(device={device}) failed")
+    return out
+
+
+def koma_destroy(ctx):
+    _check(ctx, load().koma_destroy(ctx), "koma_destroy")
+
+
+def koma_last_error(ctx) -> str:
+    return load().koma_last_error(ctx).decode()
+
+
+def koma_mem_used(ctx) -> int:
+    return int(load().koma_mem_used(ctx))
+
+
+def koma_phantom_upload(ctx, phantom):
+    """Upload a phantom (object with x, y, z, pd, t1, t2, dw and optional
+    group_offsets). Returns the phantom handle."""
+    arrs = [_f64(getattr(phantom, f)) for f in ("x", "y", "z", "pd", "t1", "t2", "dw")]
+    n = arrs[0].shape[0]
+    go = getattr(phantom, "group_offsets", None)
+    go_arr = None if go is None else np.ascontiguousarray(go, dtype=np.int64)
+    n_groups = 1 if go_arr is None else go_arr.shape[0] - 1
+    out = _vp()
+    rc = load().koma_phantom_upload(ctx, n, *[_ptr(a) for a in arrs],
+                                    None if go_arr is None else _ptr(go_arr, ctypes.c_int64),
+                                    n_groups, ctypes.byref(out))
+    _check(ctx, rc, "koma_phantom_upload")
+    return out
+
+
+def koma_phantom_n_spins(ph) -> int:
+    return int(load().koma_phantom_n_spins(ph))
+
+
+def koma_phantom_n_groups(ph) -> int:
+    return int(load().koma_phantom_n_groups(ph))
+
+
+def koma_phantom_free(ph):
+    load().koma_phantom_free(ph)
+
+
+def _seq_arrays(seq):
+    b1 = np.asarray(seq.b1, dtype=np.complex128)
+    return (_f64(seq.dt), _f64(seq.gx), _f64(seq.gy), _f64(seq.gz), _f64(b1.real), _f64(b1.imag),
+            np.ascontiguousarray(seq.adc, dtype=np.uint8))
+
+
+def koma_sequence_upload(ctx, seq):
+    """Upload a discretised sequence (object with dt, gx, gy, gz, b1, adc)."""
+    dt, gx, gy, gz, bre, bim, adc = _seq_arrays(seq)
+    out = _vp()
+    rc = load().koma_sequence_upload(ctx, dt.shape[0], _ptr(dt), _ptr(gx), _ptr(gy), _ptr(gz),
+                                     _ptr(bre), _ptr(bim), _ptr(adc, ctypes.c_uint8), ctypes.byref(out))
+    _check(ctx, rc, "koma_sequence_upload")
+    return out
+
+
+def koma_sequence_n_adc(seq) -> int:
+    return int(load().koma_sequence_n_adc(seq))
+
+
+def koma_sequence_n_steps(seq) -> int:
+    return int(load().koma_sequence_n_steps(seq))
+
+
+def koma_sequence_get_info(seq) -> dict:
+    info = SequenceInfo()
+    rc = load().koma_sequence_get_info(seq, ctypes.byref(info))
+    if rc != KOMA_OK:
+        raise KomaError(rc, "koma_sequence_get_info")
+    return info.as_dict()
+
+
+def koma_sequence_free(seq):
+    load().koma_sequence_free(seq)
+
+
+def koma_sequence_plan(seq, with_records: bool = False):
+    """Host-only preprocessing of a sequence (no GPU needed). Returns the
+    step-class counts, and with ``with_records`` also the FP64 records as a
+    [n_records, 16] array ([type, count, first sample, payload...])."""
+    dt, gx, gy, gz, bre, bim, adc = _seq_arrays(seq)
+    info = SequenceInfo()
+    lib = load()
+    rc = lib.koma_sequence_plan(dt.shape[0], _ptr(dt), _ptr(gx), _ptr(gy), _ptr(gz), _ptr(bre), _ptr(bim),
+                                _ptr(adc, ctypes.c_uint8), ctypes.byref(info), None, 0)
+    if rc != KOMA_OK:
+        raise KomaError(rc, "koma_sequence_plan rejected the sequence")
+    if not with_records:
+        return info.as_dict()
+    rec = np.zeros((max(info.n_records, 1), 16), dtype=np.float64)
+    rc = lib.koma_sequence_plan(dt.shape[0], _ptr(dt), _ptr(gx), _ptr(gy), _ptr(gz), _ptr(bre), _ptr(bim),
+                                _ptr(adc, ctypes.c_uint8), ctypes.byref(info), _ptr(rec), rec.shape[0])
+    if rc != KOMA_OK:
+        raise KomaError(rc, "koma_sequence_plan")
+    return info.as_dict(), rec[:info.n_records]
+
+
+def koma_simulate(ctx, ph, seq, precision: int, sig_dev_ptr: int, stream_ptr: int):
+    rc = load().koma_simulate(ctx, ph, seq, int(precision), ctypes.c_void_p(int(sig_dev_ptr)),
+                              ctypes.c_void_p(int(stream_ptr)))
+    _check(ctx, rc, "koma_simulate")
+
+
+def koma_sync(ctx, stream_ptr: int):
+    _check(ctx, load().koma_sync(ctx, ctypes.c_void_p(int(stream_ptr))), "koma_sync")
+
+
+def koma_set_timing(ctx, enable: bool = True):
+    _check(ctx, load().koma_set_timing(ctx, int(bool(enable))), "koma_set_timing")
+
+
+def koma_get_timing(ctx):
+    """(bloch_ms, reduce_ms) of the last timed koma_simulate."""
+    a, b = ctypes.c_float(), ctypes.c_float()
+    _check(ctx, load().koma_get_timing(ctx, ctypes.byref(a), ctypes.byref(b)), "koma_get_timing")
+    return a.value, b.value
+
+
+def koma_get_launch_info(ctx) -> dict:
+    info = LaunchInfo()
+    _check(ctx, load().koma_get_launch_info(ctx, ctypes.byref(info)), "koma_get_launch_info")
+    return info.as_dict()
+
+
+def koma_simulate_host(ctx, phantom, seq, precision: int = KOMA_FP32_SPLITPHASE, out=None):
+    """Host arrays in, host signal out (complex128 [n_groups, n_adc])."""
+    arrs = [_f64(getattr(phantom, f)) for f in ("x", "y", "z", "pd", "t1", "t2", "dw")]
+    go = getattr(phantom, "group_offsets", None)
+    go_arr = None if go is None else np.ascontiguousarray(go, dtype=np.int64)
+    n_groups = 1 if go_arr is None else go_arr.shape[0] - 1
+    dt, gx, gy, gz, bre, bim, adc = _seq_arrays(seq)
+    n_adc = int(np.count_nonzero(adc))
+    if out is None:
+        out = np.empty((n_groups, n_adc), dtype=np.complex128)
+    assert out.dtype == np.complex128 and out.flags.c_contiguous and out.size == n_groups * n_adc
+    rc = load().koma_simulate_host(ctx, arrs[0].shape[0], *[_ptr(a) for a in arrs],
+                                   None if go_arr is None else _ptr(go_arr, ctypes.c_int64), n_groups,
+                                   dt.shape[0], _ptr(dt), _ptr(gx), _ptr(gy), _ptr(gz), _ptr(bre),
+                                   _ptr(bim), _ptr(adc, ctypes.c_uint8), int(precision),
+                                   out.ctypes.data_as(_dp))
+    _check(ctx, rc, "koma_simulate_host")
+    return out
+
+
+# --------------------------------------------------------------------------
+# convenience layer over torch device memory / streams
+# --------------------------------------------------------------------------
+
+class Simulator:
+    """Owns a context on one CUDA device; uploads and simulates.
+
+    >>> sim = Simulator()
+    >>> ph = sim.upload_phantom(phantom); sq = sim.upload_sequence(seq)
+    >>> sig = sim.simulate(ph, sq)          # torch complex128 [n_groups, n_adc] on the device
+    """
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        import torch  # noqa: F401  (device memory and streams)
+        self.device = device
+        self.ctx = koma_init(device, mem_budget_bytes)
+
+    def upload_phantom(self, phantom):
+        return koma_phantom_upload(self.ctx, phantom)
+
+    def upload_sequence(self, seq):
+        return koma_sequence_upload(self.ctx, seq)
+
+    def simulate(self, ph, seq, precision="fp32", out=None, stream=None):
+        import torch
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        n_adc = koma_sequence_n_adc(seq)
+        n_groups = koma_phantom_n_groups(ph)
+        if out is None:
+            out = torch.empty((n_groups, n_adc), dtype=torch.complex128, device=f"cuda:{self.device}")
+        assert out.dtype == torch.complex128 and out.is_contiguous() and out.numel() == n_groups * n_adc
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        koma_simulate(self.ctx, ph, seq, prec, out.data_ptr() if out.numel() else 0, st.cuda_stream)
+        return out
+
+    def sync(self, stream=None):
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        koma_sync(self.ctx, st.cuda_stream)
+
+    def launch_info(self) -> dict:
+        return koma_get_launch_info(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            koma_destroy(self.ctx)
+            self.ctx = None

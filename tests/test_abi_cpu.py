@@ -1,0 +1,133 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+include/koma.h declares, validates its inputs, and its host preprocessing
+(regime classification, cumulative moments, uniform ADC runs) reproduces the
+per-sample gradient moments computed independently here with numpy."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2301_02702_b300 import build, koma
+from paper_2301_02702_b300.workloads import (GAMMA_BAR, Sequence, SequenceBuilder, random_sequence,
+                                             workload)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return koma.load()
+
+
+def declared_entry_points():
+    src = open(os.path.join(ROOT, "include", "koma.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(koma_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_entry_points()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/koma.h but not exported"
+    assert sorted(koma.EXPORTS) == names
+
+
+def test_gamma_and_version(lib):
+    assert koma.koma_gamma() == pytest.approx(oracle.GAMMA, rel=1e-15)
+    assert "sm_103a" in koma.koma_version()
+
+
+def test_init_without_gpu_fails_cleanly(lib, cuda_available):
+    if cuda_available:
+        pytest.skip("a GPU is present")
+    with pytest.raises(koma.KomaError) as e:
+        koma.koma_init(0)
+    assert e.value.status == koma.KOMA_E_CUDA
+    assert lib.koma_destroy(None) == koma.KOMA_OK
+
+
+def test_plan_rejects_bad_sequences(lib):
+    good = random_sequence(20, seed=1)
+    koma.koma_sequence_plan(good)
+    for mutate in (lambda s: s.dt.__setitem__(3, 0.0), lambda s: s.dt.__setitem__(3, -1e-6),
+                   lambda s: s.dt.__setitem__(3, np.nan), lambda s: s.gx.__setitem__(5, np.inf),
+                   lambda s: s.b1.__setitem__(2, complex(np.nan, 0)), lambda s: s.adc.__setitem__(4, 2)):
+        s = random_sequence(20, seed=1)
+        mutate(s)
+        with pytest.raises(koma.KomaError) as e:
+            koma.koma_sequence_plan(s)
+        assert e.value.status == koma.KOMA_E_INVALID
+
+
+def _reference_samples(seq: Sequence):
+    """(K [turns/m], tau [s]) of every ADC sample relative to the end of the
+    last RF step before it, by a plain loop over steps (trapezoid rule)."""
+    K = np.zeros(3)
+    tau = 0.0
+    out = []
+    if seq.adc[0]:
+        out.append((K.copy(), tau))
+    for n in range(seq.n_steps):
+        if seq.b1[n] != 0:
+            K[:] = 0.0
+            tau = 0.0
+        else:
+            gm = 0.5 * np.array([seq.gx[n] + seq.gx[n + 1], seq.gy[n] + seq.gy[n + 1], seq.gz[n] + seq.gz[n + 1]])
+            K += GAMMA_BAR * seq.dt[n] * gm
+            tau += seq.dt[n]
+        if seq.adc[n + 1]:
+            out.append((K.copy(), tau))
+    return out
+
+
+def _decode_samples(rec):
+    out = {}
+    for r in rec:
+        if int(r[0]) != 2:
+            continue
+        count, k0 = int(r[1]), int(r[2])
+        a = r[3:]
+        assert 1 <= count <= 64
+        for l in range(count):
+            out[k0 + l] = (a[0:3] + l * a[4:7], a[3] + l * a[7])
+    return [out[k] for k in range(len(out))]
+
+
+@pytest.mark.parametrize("name", ["gre32", "epi512", "se128", "random"])
+def test_plan_reproduces_sample_moments(lib, name):
+    seq = random_sequence(3000, seed=7) if name == "random" else workload(name, "small")[1]
+    info, rec = koma.koma_sequence_plan(seq, with_records=True)
+    assert info["n_steps"] == seq.n_steps
+    assert info["n_adc"] == seq.n_adc
+    assert info["n_rf"] == seq.n_rf
+    assert info["n_rf"] + info["n_precess"] == seq.n_steps
+    assert info["n_records"] == info["n_rf"] + info["n_adc_runs"] + info["n_materialize"]
+    ref = _reference_samples(seq)
+    got = _decode_samples(rec)
+    assert len(got) == len(ref)
+    for (kr, tr), (kg, tg) in zip(ref, got):
+        assert np.max(np.abs(kr - kg)) <= 1e-9 * (1 + np.max(np.abs(kr)))
+        assert abs(tr - tg) <= 1e-12 * (1 + tr)
+    # the types appear in the order the steps do: every RF step is a record
+    assert int(np.sum(rec[:, 0] == 0)) == seq.n_rf
+
+
+def test_plan_merges_uniform_readouts(lib):
+    """A Cartesian readout of n samples at constant gradient becomes
+    ceil(n / 64) ADC records."""
+    b = SequenceBuilder()
+    b.steps(1, 1e-6, b1=1e-5)
+    b.steps(5, 10e-6, [0.01, 0, 0])
+    b.steps(200, 4e-6, adc=True)
+    info = koma.koma_sequence_plan(b.build())
+    assert info["n_adc"] == 200 and info["n_adc_runs"] == 4
+
+
+def test_plan_empty_and_adc_at_t0(lib):
+    seq = Sequence(np.zeros(0), np.zeros(1), np.zeros(1), np.zeros(1), np.zeros(0, complex), np.ones(1, np.uint8))
+    info = koma.koma_sequence_plan(seq)
+    assert info["n_adc"] == 1 and info["n_records"] == 1

@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Error metric (the paper compares signals normalised by the reference maximum):
+rel_err = max_k |s_gpu[k] - s_ref[k]| / max_k |s_ref[k]|.
+Tolerances: FP32 split-phase path 1e-4; FP64 path 1e-9 (FP64 rounding of a
+different but mathematically equal formulation, over up to ~1e5 steps).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2301_02702_b300 import build, koma
+from paper_2301_02702_b300.workloads import (WORKLOADS, Phantom, Sequence, SequenceBuilder, hard_pulse_b1,
+                                             random_sequence, random_spins, workload)
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-4
+TOL64 = 1e-9
+
+
+@pytest.fixture(scope="module")
+def sim():
+    build.build()
+    s = koma.Simulator(0)
+    yield s
+    s.close()
+
+
+def gpu_signal(sim, ph, seq, precision="fp32"):
+    hp = sim.upload_phantom(ph)
+    hs = sim.upload_sequence(seq)
+    try:
+        out = sim.simulate(hp, hs, precision)
+        sim.sync()
+        return out.cpu().numpy()
+    finally:
+        koma.koma_sequence_free(hs)
+        koma.koma_phantom_free(hp)
+
+
+def rel_err(got, ref):
+    scale = np.max(np.abs(ref))
+    assert scale > 0
+    return float(np.max(np.abs(got - ref)) / scale)
+
+
+@pytest.mark.parametrize("name", WORKLOADS)
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_workloads_small(sim, name, precision):
+    ph, seq = workload(name, "small")
+    ref = oracle.simulate(ph, seq)
+    got = gpu_signal(sim, ph, seq, precision)
+    assert got.shape == ref.shape
+    err = rel_err(got, ref)
+    assert err < (TOL32 if precision == "fp32" else TOL64), err
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_gre32_full_size(sim, precision):
+    """The 1,024-spin, 32,000-step spoiled GRE at its full size."""
+    ph, seq = workload("gre32", "full")
+    ref = oracle.simulate(ph, seq)
+    err = rel_err(gpu_signal(sim, ph, seq, precision), ref)
+    assert err < (TOL32 if precision == "fp32" else TOL64), err
+
+
+@pytest.mark.parametrize("name", ["epi512", "se128"])
+def test_full_size_launch_sampled_spins(sim, name):
+    """Full-size phantom in the benchmark's launch configuration; all spins
+    but a random sample of 1,536 get PD = 0, so the signal is that sample's
+    signal (linearity in PD) and the oracle computes it directly."""
+    ph, seq = workload(name, "full")
+    rng = np.random.default_rng(5)
+    keep = np.sort(rng.choice(ph.n, 1536, replace=False))
+    pd = np.zeros(ph.n)
+    pd[keep] = ph.pd[keep]
+    masked = Phantom(ph.x, ph.y, ph.z, pd, ph.t1, ph.t2, ph.dw)
+    got = gpu_signal(sim, masked, seq)
+    info = sim.launch_info()
+    ref = oracle.simulate(ph.subset(keep), seq)
+    err = rel_err(got, ref)
+    assert err < TOL32, err
+    assert info["grid"] >= 148
+
+
+def test_random_sequences_and_ragged_sizes(sim):
+    for seed, n in ((1, 1), (2, 31), (3, 33), (4, 257), (5, 1000), (6, 4099)):
+        ph = random_spins(n, seed=seed)
+        seq = random_sequence(700, seed=seed + 100)
+        ref = oracle.simulate(ph, seq)
+        for prec, tol in (("fp32", TOL32), ("fp64", TOL64)):
+            err = rel_err(gpu_signal(sim, ph, seq, prec), ref)
+            assert err < tol, (seed, n, prec, err)
+
+
+def test_edge_cases(sim):
+    ph = random_spins(70, seed=9)
+    # ADC at t0 only: equilibrium has no transverse magnetisation
+    seq0 = Sequence(np.zeros(0), np.zeros(1), np.zeros(1), np.zeros(1), np.zeros(0, complex), np.ones(1, np.uint8))
+    assert np.all(gpu_signal(sim, ph, seq0) == 0)
+    # no ADC at all: an empty signal
+    seq1 = random_sequence(50, seed=3, adc_frac=0.0)
+    seq1.adc[:] = 0
+    assert gpu_signal(sim, ph, seq1).shape == (1, 0)
+    # no RF: nothing is ever excited
+    seq2 = random_sequence(80, seed=4, rf_frac=0.0)
+    assert np.all(gpu_signal(sim, ph, seq2) == 0)
+    # infinite T1/T2 and zero PD spins mixed in
+    ph3 = random_spins(100, seed=10)
+    ph3.t1[::3] = np.inf
+    ph3.t2[::4] = np.inf
+    ph3.pd[::5] = 0.0
+    seq3 = random_sequence(400, seed=11)
+    ref = oracle.simulate(ph3, seq3)
+    assert rel_err(gpu_signal(sim, ph3, seq3), ref) < TOL32
+    # RF with every step sampled (samples inside an excitation block)
+    b = SequenceBuilder()
+    b.steps(50, 4e-6, b1=hard_pulse_b1(np.pi / 2, 200e-6, 0.3), adc=True)
+    b.steps(30, 4e-6, [0.01, 0.0, 0.0], adc=True)
+    seq4 = b.build()
+    ref = oracle.simulate(ph3, seq4)
+    assert rel_err(gpu_signal(sim, ph3, seq4), ref) < TOL32
+    # large per-step angles (range reduction of the half angle)
+    b = SequenceBuilder()
+    b.steps(20, 50e-6, [0.0, 0.0, 0.2], b1=hard_pulse_b1(3.0, 1e-3))
+    b.steps(10, 20e-6, adc=True)
+    seq5 = b.build()
+    ref = oracle.simulate(ph3, seq5)
+    assert rel_err(gpu_signal(sim, ph3, seq5), ref) < TOL32
+
+
+def test_grouped_phantom(sim):
+    ph = random_spins(300, seed=21)
+    offs = np.array([0, 7, 7, 100, 101, 240, 300])
+    seq = random_sequence(300, seed=22)
+    phg = random_spins(300, seed=21)
+    phg.group_offsets = offs
+    ref = oracle.simulate(phg, seq)
+    for prec, tol in (("fp32", TOL32), ("fp64", TOL64)):
+        got = gpu_signal(sim, phg, seq, prec)
+        assert got.shape == (6, seq.n_adc)
+        for g in range(6):
+            if offs[g + 1] == offs[g]:
+                assert np.all(got[g] == 0)
+            else:
+                assert np.max(np.abs(got[g] - ref[g])) < tol * np.max(np.abs(ref[g])), (g, prec)
+    del ph
+
+
+def test_deterministic_and_additive(sim):
+    ph, seq = workload("epi512", "small")
+    a = gpu_signal(sim, ph, seq)
+    b = gpu_signal(sim, ph, seq)
+    assert np.array_equal(a, b), "two runs must be bitwise identical"
+    half = ph.n // 2
+    s1 = gpu_signal(sim, ph.subset(np.arange(half)), seq)
+    s2 = gpu_signal(sim, ph.subset(np.arange(half, ph.n)), seq)
+    assert rel_err(s1 + s2, a) < TOL32
+
+
+def test_simulate_host_matches_device_path(sim):
+    ph, seq = workload("se128", "small")
+    dev = gpu_signal(sim, ph, seq)
+    host = koma.koma_simulate_host(sim.ctx, ph, seq, koma.KOMA_FP32_SPLITPHASE)
+    assert np.array_equal(dev, host)
+
+
+def test_abi_errors(sim):
+    bad = random_spins(10, seed=1)
+    bad.t2[3] = 0.0
+    with pytest.raises(koma.KomaError) as e:
+        sim.upload_phantom(bad)
+    assert e.value.status == koma.KOMA_E_INVALID
+    bad = random_spins(10, seed=1)
+    bad.x[2] = np.nan
+    with pytest.raises(koma.KomaError):
+        sim.upload_phantom(bad)
+    small = koma.Simulator(0, mem_budget_bytes=1 << 16)
+    try:
+        with pytest.raises(koma.KomaError) as e:
+            small.upload_phantom(random_spins(100000, seed=2))
+        assert e.value.status == koma.KOMA_E_NOMEM
+    finally:
+        small.close()
+    # objects of one context are rejected by another
+    other = koma.Simulator(0)
+    try:
+        hp = other.upload_phantom(random_spins(10, seed=3))
+        hs = sim.upload_sequence(random_sequence(10, seed=4))
+        with pytest.raises(koma.KomaError) as e:
+            sim.simulate(hp, hs)
+        assert e.value.status == koma.KOMA_E_INVALID
+        koma.koma_phantom_free(hp)
+        koma.koma_sequence_free(hs)
+    finally:
+        other.close()
