@@ -63,7 +63,42 @@ def dist_env():
 # --------------------------------------------------------------------------
 # clocks during the timed region (NVML; read only)
 # --------------------------------------------------------------------------
+class _Nvml:
+    """Read-only NVML queries through ctypes (libnvidia-ml.so.1 ships with
+    the driver; the Python wrapper package may be absent)."""
+
+    def __init__(self, index: int):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("nvmlDeviceGetHandleByIndex failed")
+        try:
+            self._reasons = self.lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            self._reasons = self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sm_clock(self) -> int:
+        v = self.ct.c_uint()
+        self.lib.nvmlDeviceGetClockInfo(self.h, 1, self.ct.byref(v))  # NVML_CLOCK_SM
+        return v.value
+
+    def sm_max_clock(self) -> int:
+        v = self.ct.c_uint()
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, self.ct.byref(v))
+        return v.value
+
+    def reasons(self) -> int:
+        v = self.ct.c_ulonglong()
+        self._reasons(self.h, self.ct.byref(v))
+        return v.value
+
+
 class ClockSampler:
+    """Samples the SM clock and the clock-event reasons while running."""
     REASONS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
                "sw_power_cap": 0x4, "hw_power_brake_slowdown": 0x80}
 
@@ -76,21 +111,17 @@ class ClockSampler:
         self._thread = None
         self.error = None
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            self._nv = pynvml
-            self._h = pynvml.nvmlDeviceGetHandleByIndex(device_index)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
+            self._nv = _Nvml(device_index)
+            self.max_mhz = self._nv.sm_max_clock()
         except Exception as e:  # no NVML: report the absence
             self._nv = None
             self.error = repr(e)
 
     def _run(self):
-        nv = self._nv
         while not self._stop.is_set():
             try:
-                self.samples.append(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM))
-                r = nv.nvmlDeviceGetCurrentClocksEventReasons(self._h)
+                self.samples.append(self._nv.sm_clock())
+                r = self._nv.reasons()
                 for name, bit in self.REASONS.items():
                     if r & bit:
                         self.reasons.add(name)
@@ -110,7 +141,7 @@ class ClockSampler:
             self._thread.join()
         out = {"sm_mhz": float(statistics.median(self.samples)) if self.samples else None,
                "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons), "samples": len(self.samples),
-               "source": "NVML"}
+               "source": "NVML (libnvidia-ml, read only)"}
         if self.error:
             out["error"] = self.error
         return out
@@ -150,7 +181,7 @@ def cpu_sample_run(ph, seq, target_s: float, threads: int):
     """Time the oracle on a random spin sample sized for ~target_s seconds."""
     import oracle
     rng = np.random.default_rng(123)
-    n_cal = min(ph.n, max(threads, 8))
+    n_cal = min(ph.n, max(4 * threads, 64))
     idx = np.sort(rng.choice(ph.n, n_cal, replace=False))
     t0 = time.perf_counter()
     oracle.simulate(ph.subset(idx), seq, threads=threads)

@@ -23,12 +23,13 @@ namespace {
 constexpr int kTile = 64;                 // records per TMA tile (4 KB of Rec32)
 constexpr int kMaxBlock = 256;
 constexpr int kMaxWarps = kMaxBlock / 32;
-constexpr int kRed = 128;                 // samples held per reduction buffer
+constexpr int kRed = 128;                 // samples per reduction buffer (FP64 kernel)
+constexpr int kRed32 = 512;               // samples per reduction buffer (FP32 kernel, dynamic smem)
 constexpr int kV = 8;                     // samples per warp reduce-scatter
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bound on any device wait
 
-static_assert(kRed >= kMaxAdcRun, "an ADC record must fit in one reduction buffer");
+static_assert(kRed >= kMaxAdcRun && kRed32 >= kMaxAdcRun, "an ADC record must fit in one reduction buffer");
 static_assert(kMaxAdcRun % kV == 0, "runs are processed in chunks of kV");
 
 // ---------------------------------------------------------------------------
@@ -167,6 +168,43 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // ---------------------------------------------------------------------------
+// Packed FP32 pairs (two spins per 64-bit register pair). fma/mul/add.f32x2
+// run at the same FP32 pipe rate as two scalar instructions but take one
+// issue slot.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo_of(f32x2 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float hi_of(f32x2 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return b;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
 // K1: FP32 split-phase Bloch kernel.
 //
 // Every CTA owns a contiguous spin range; thread `tid` holds spins
@@ -185,9 +223,12 @@ __device__ __forceinline__ T warp_sum(T v) {
 // ---------------------------------------------------------------------------
 template <int S>
 __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_constant__ BlochArgs A) {
+    static_assert(S % 2 == 0, "spins are processed in packed pairs");
+    constexpr int NP = S / 2;  // packed spin pairs
     __shared__ __align__(128) Rec32 s_rec[2][kTile];
     __shared__ __align__(8) uint64_t s_bar[2];
-    __shared__ __align__(16) float2 s_red[2][kMaxWarps][kRed];
+    // per-warp sample sums, two buffers: [buf][warp][kRed32] (dynamic)
+    extern __shared__ __align__(16) float2 s_red_dyn[];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -241,6 +282,9 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
     int red_buf = 0;
     int64_t red_base = 0, red_end = 0;          // samples [red_base, red_end) staged
     float2* __restrict__ partial = static_cast<float2*>(A.partial) + static_cast<int64_t>(cta) * A.n_adc;
+    auto red_slot = [&](int buf, int w, int i) -> float2& {
+        return s_red_dyn[(buf * nwarps + w) * kRed32 + i];
+    };
 
     auto flush = [&]() {
         __syncthreads();
@@ -248,7 +292,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
         for (int i = tid; i < cnt; i += nthr) {
             float sr = 0.f, si = 0.f;
             for (int w = 0; w < nwarps; ++w) {
-                const float2 v = s_red[red_buf][w][i];
+                const float2 v = red_slot(red_buf, w, i);
                 sr += v.x;
                 si += v.y;
             }
@@ -373,7 +417,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
                 if (type == REC_ADC) {
                     const int L = min(max(R.count, 1), kMaxAdcRun);
                     const int64_t k0 = R.k0;
-                    if (k0 + L > red_base + kRed) flush();
+                    if (k0 + L > red_base + kRed32) flush();
                     if (L == 1) {
                         float sr = 0.f, si = 0.f;
 #pragma unroll
@@ -383,7 +427,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
                         }
                         sr = warp_sum(sr);
                         si = warp_sum(si);
-                        if (lane == 0) s_red[red_buf][warp][k0 - red_base] = make_float2(sr, si);
+                        if (lane == 0) red_slot(red_buf, warp, static_cast<int>(k0 - red_base)) = make_float2(sr, si);
                     } else {
                         const float dkx = R.a[8], dky = R.a[9], dkz = R.a[10], dtau = R.a[11];
                         if (!(dkx == key0 && dky == key1 && dkz == key2 && dtau == key3)) {
@@ -401,26 +445,40 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
                             key2 = dkz;
                             key3 = dtau;
                         }
+                        // spins in packed pairs: m' = m z, acc += m
+                        f32x2 pr[NP], pi_[NP], qr[NP], qi[NP], qn[NP];
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) {
+                            pr[p] = pk(er[2 * p], er[2 * p + 1]);
+                            pi_[p] = pk(ei[2 * p], ei[2 * p + 1]);
+                            qr[p] = pk(zr[2 * p], zr[2 * p + 1]);
+                            qi[p] = pk(zi[2 * p], zi[2 * p + 1]);
+                            qn[p] = pk(-zi[2 * p], -zi[2 * p + 1]);
+                        }
                         for (int c = 0; c < L; c += kV) {
                             float ar[kV], ai[kV];
 #pragma unroll
                             for (int v = 0; v < kV; ++v) {
-                                ar[v] = 0.f;
-                                ai[v] = 0.f;
+                                f32x2 sr2 = pr[0], si2 = pi_[0];
 #pragma unroll
-                                for (int s = 0; s < S; ++s) {
-                                    ar[v] += er[s];
-                                    ai[v] += ei[s];
-                                    const float nr_ = fmaf(er[s], zr[s], -ei[s] * zi[s]);
-                                    ei[s] = fmaf(er[s], zi[s], ei[s] * zr[s]);
-                                    er[s] = nr_;
+                                for (int p = 1; p < NP; ++p) {
+                                    sr2 = add2(sr2, pr[p]);
+                                    si2 = add2(si2, pi_[p]);
+                                }
+                                ar[v] = lo_of(sr2) + hi_of(sr2);
+                                ai[v] = lo_of(si2) + hi_of(si2);
+#pragma unroll
+                                for (int p = 0; p < NP; ++p) {
+                                    const f32x2 nr2 = fma2(pr[p], qr[p], mul2(pi_[p], qn[p]));
+                                    pi_[p] = fma2(pr[p], qi[p], mul2(pi_[p], qr[p]));
+                                    pr[p] = nr2;
                                 }
                             }
                             const float sr = reduce_scatter8(ar, lane);
                             const float si = reduce_scatter8(ai, lane);
                             const int vl = (lane >> 2) & 7;
                             if ((lane & 3) == 0 && c + vl < L)
-                                s_red[red_buf][warp][k0 + c + vl - red_base] = make_float2(sr, si);
+                                red_slot(red_buf, warp, static_cast<int>(k0 + c + vl - red_base)) = make_float2(sr, si);
                         }
                     }
                     red_end = k0 + L;
@@ -584,6 +642,30 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const __grid_const
     }
 }
 
+size_t fp32_dyn_smem(int block) { return static_cast<size_t>(2 * (block / 32) * kRed32) * sizeof(float2); }
+
+template <int S>
+cudaError_t prepare_fp32(size_t dyn) {
+    return cudaFuncSetAttribute(bloch_fp32_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(dyn));
+}
+
+template <int S>
+cudaError_t occupancy_fp32(int* n, int block, size_t dyn) {
+    cudaError_t e = prepare_fp32<S>(dyn);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, bloch_fp32_kernel<S>, block, dyn);
+}
+
+template <int S>
+cudaError_t launch_fp32(const BlochArgs& a, const BlochLaunch& L, cudaStream_t st) {
+    const size_t dyn = fp32_dyn_smem(L.block);
+    cudaError_t e = prepare_fp32<S>(dyn);
+    if (e != cudaSuccess) return e;
+    bloch_fp32_kernel<S><<<L.grid, L.block, dyn, st>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int bloch_max_block() { return kMaxBlock; }
@@ -593,12 +675,14 @@ int bloch_ctas_per_sm(bool fp64, int spins_per_thread, int block) {
     cudaError_t e;
     if (fp64) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_fp64_kernel, block, 0);
-    } else if (spins_per_thread == 1) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_fp32_kernel<1>, block, 0);
-    } else if (spins_per_thread == 2) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_fp32_kernel<2>, block, 0);
     } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_fp32_kernel<4>, block, 0);
+        const size_t dyn = fp32_dyn_smem(block);
+        switch (spins_per_thread) {
+            case 2: e = occupancy_fp32<2>(&n, block, dyn); break;
+            case 4: e = occupancy_fp32<4>(&n, block, dyn); break;
+            case 8: e = occupancy_fp32<8>(&n, block, dyn); break;
+            default: return -1;
+        }
     }
     return e == cudaSuccess ? n : -1;
 }
@@ -607,12 +691,11 @@ int launch_bloch_fp32(const BlochArgs& a, const BlochLaunch& L, void* stream) {
     if (L.block <= 0 || L.block > kMaxBlock || L.block % 32 != 0 || L.grid <= 0) return cudaErrorInvalidValue;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     switch (L.spins_per_thread) {
-        case 1: bloch_fp32_kernel<1><<<L.grid, L.block, 0, st>>>(a); break;
-        case 2: bloch_fp32_kernel<2><<<L.grid, L.block, 0, st>>>(a); break;
-        case 4: bloch_fp32_kernel<4><<<L.grid, L.block, 0, st>>>(a); break;
+        case 2: return launch_fp32<2>(a, L, st);
+        case 4: return launch_fp32<4>(a, L, st);
+        case 8: return launch_fp32<8>(a, L, st);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 int launch_bloch_fp64(const BlochArgs& a, const BlochLaunch& L, void* stream) {
