@@ -205,6 +205,37 @@ koma_status koma_simulate(koma_ctx *ctx, const koma_phantom *ph, const koma_sequ
                           koma_precision precision, double *sig_dev, void *stream);
 
 /*
+ * koma_simulate_static: the KOMA_FP32_SPLITPHASE simulation of koma_simulate
+ * for callers that cannot allocate device memory at simulation time - for
+ * example a host framework whose allocator has reserved the whole device, a
+ * caller that must not trigger cudaMalloc's implicit device synchronisation
+ * in a latency-critical loop, or code that has no allocator of its own. The
+ * paper has no counterpart to this entry point; it is a deployment variant.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine: the per-CTA
+ * partial sums live in a file-scope static device array of 4,194,304 FP32
+ * complex values (32 MiB), which every GPU that loads libkoma holds until
+ * the process exits.
+ *   ph, seq   uploaded objects of one context (ungrouped phantom only)
+ *   sig_dev   device FP64 [n_adc][2] (complex128), written completely
+ *   stream    cudaStream_t of the context's device (NULL = legacy default)
+ * Asynchronous like koma_simulate. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current)
+ * and caches it; make that first call before any stream capture. Every call
+ * on a device shares the one array and leaves its contents behind (each
+ * call overwrites every entry it reads, so nothing needs clearing): calls
+ * whose kernels overlap on the GPU (different streams, no ordering) race
+ * and give wrong results - order them on one stream or by events.
+ * Errors: KOMA_E_INVALID (NULL handles, objects of different contexts, a
+ *   grouped phantom, sig_dev NULL, or a problem needing more partial sums
+ *   than the array holds: CTAs x ADC samples > 4,194,304, e.g. more than
+ *   256 x 16,384 - use koma_simulate then), KOMA_E_CUDA. Messages via
+ *   koma_last_error on the phantom's context.
+ */
+koma_status koma_simulate_static(const koma_phantom *ph, const koma_sequence *seq,
+                                 double *sig_dev, void *stream);
+
+/*
  * Wait for `stream` and report device-side status: KOMA_E_TIMEOUT if a
  * bounded wait inside a kernel of this context gave up since the last
  * koma_sync (the flag is then cleared), KOMA_E_CUDA on an asynchronous CUDA

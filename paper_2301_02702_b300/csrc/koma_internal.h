@@ -109,6 +109,11 @@ struct ReduceArgs {
 int launch_bloch_fp32(const BlochArgs& a, const BlochLaunch& L, void* stream);
 int launch_bloch_fp64(const BlochArgs& a, const BlochLaunch& L, void* stream);
 int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream);
+// Static partial-sum scratch of koma_simulate_static: capacity in float2
+// elements, and its device address on `device` (which must be current; the
+// address is looked up once per device and cached).
+size_t static_partials_capacity();
+int static_partials_ptr(int device, void** out);
 // Largest block size the FP32 / FP64 Bloch kernels accept, and their
 // resident CTAs per SM at that size.
 int bloch_max_block();

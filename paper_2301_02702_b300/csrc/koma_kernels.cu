@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "koma_internal.h"
 
@@ -703,6 +704,42 @@ int launch_bloch_fp64(const BlochArgs& a, const BlochLaunch& L, void* stream) {
         return cudaErrorInvalidValue;
     bloch_fp64_kernel<<<L.grid, L.block, 0, static_cast<cudaStream_t>(stream)>>>(a);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Static scratch for koma_simulate_static (callers that cannot allocate
+// device memory). A file-scope device array of kStaticPartials float2
+// (32 MiB) that every GPU loading this library holds until exit. In host
+// code `g_static_partials` is only a host-side stand-in for the symbol: its
+// device address comes from cudaGetSymbolAddress, taken once per device
+// (with that device current) and cached. All calls share the array.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kStaticPartials = size_t(4) << 20;  // float2 elements = 32 MiB
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) float2 g_static_partials[kStaticPartials];
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+}  // namespace
+
+size_t static_partials_capacity() { return kStaticPartials; }
+
+int static_partials_ptr(int device, void** out) {
+    *out = nullptr;
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[device]) {
+        int cur = -1;
+        cudaError_t e = cudaGetDevice(&cur);
+        if (e != cudaSuccess) return e;
+        if (cur != device) return cudaErrorInvalidDevice;  // caller makes `device` current
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_partials);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[device] = p;
+    }
+    *out = g_static_ptr[device];
+    return cudaSuccess;
 }
 
 int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream) {

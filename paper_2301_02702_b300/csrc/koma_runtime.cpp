@@ -700,6 +700,70 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     return KOMA_OK;
 }
 
+// Allocation-free variant of koma_simulate (FP32 split-phase path): the
+// per-CTA partial sums go to the library's static device array instead of
+// the context's cudaMalloc'ed scratch. Ungrouped phantoms only (a grouped
+// launch needs a device CTA table). Allocates nothing.
+extern "C" koma_status koma_simulate_static(const koma_phantom* ph, const koma_sequence* seq, double* sig_dev,
+                                            void* stream) {
+    if (!ph || !seq) return KOMA_E_INVALID;
+    koma_ctx* ctx = ph->ctx;
+    if (seq->ctx != ctx) return fail(ctx, KOMA_E_INVALID, "simulate_static: phantom and sequence belong to different contexts");
+    if (ph->n_groups > 1)
+        return fail(ctx, KOMA_E_INVALID, "simulate_static: grouped phantoms are not supported (use koma_simulate)");
+    const int64_t n_adc = seq->info.n_adc;
+    if (n_adc == 0) return KOMA_OK;
+    if (!sig_dev) return fail(ctx, KOMA_E_INVALID, "simulate_static: sig_dev is NULL");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(ctx, KOMA_E_CUDA, "simulate_static: cannot select device %d", ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (ph->n == 0) {
+        cudaError_t e = cudaMemsetAsync(sig_dev, 0, static_cast<size_t>(n_adc) * 2 * sizeof(double), st);
+        return e == cudaSuccess ? KOMA_OK : cuda_fail(ctx, e, "simulate_static: memset");
+    }
+    void* scratch = nullptr;
+    int ce = koma::static_partials_ptr(ctx->device, &scratch);
+    if (ce != cudaSuccess)
+        return cuda_fail(ctx, static_cast<cudaError_t>(ce), "simulate_static: static scratch address");
+    const int64_t cap = static_cast<int64_t>(koma::static_partials_capacity());
+    koma::BlochLaunch L = choose_launch(ctx, ph->n, false);
+    if (static_cast<int64_t>(L.grid) * n_adc > cap) {
+        // fewest CTAs: every thread full
+        const int64_t spc = static_cast<int64_t>(koma::bloch_max_block()) * L.spins_per_thread;
+        L.spins_per_cta = spc;
+        L.grid = static_cast<int>((ph->n + spc - 1) / spc);
+        L.block = koma::bloch_max_block();
+    }
+    if (static_cast<int64_t>(L.grid) * n_adc > cap)
+        return fail(ctx, KOMA_E_INVALID,
+                    "simulate_static: %lld spins x %lld ADC samples need %lld partial sums; the static scratch "
+                    "holds %lld (use koma_simulate)",
+                    static_cast<long long>(ph->n), static_cast<long long>(n_adc),
+                    static_cast<long long>(L.grid) * n_adc, static_cast<long long>(cap));
+    koma::BlochArgs A;
+    A.p32 = ph->p32;
+    A.p64 = ph->p64;
+    A.n_pad = ph->n_pad;
+    A.n = ph->n;
+    A.rec = seq->r32;
+    A.n_rec = seq->info.n_records;
+    A.n_adc = n_adc;
+    A.status = ctx->d_status;
+    A.spins_per_cta = L.spins_per_cta;
+    A.partial = scratch;  // every (CTA, sample) entry is written before K2 reads it
+    koma::ReduceArgs R;
+    R.n_adc = n_adc;
+    R.n_groups = 1;
+    R.partial = scratch;
+    R.grid = L.grid;
+    R.sig = sig_dev;
+    int e = koma::launch_bloch_fp32(A, L, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate_static: Bloch kernel launch");
+    e = koma::launch_reduce(R, false, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate_static: reduction launch");
+    return KOMA_OK;
+}
+
 extern "C" koma_status koma_sync(koma_ctx* ctx, void* stream) {
     if (!ctx) return KOMA_E_INVALID;
     DeviceGuard g(ctx->device);

@@ -31,7 +31,7 @@ EXPORTS = (
     "koma_phantom_upload", "koma_phantom_n_spins", "koma_phantom_n_groups", "koma_phantom_free",
     "koma_sequence_upload", "koma_sequence_n_adc", "koma_sequence_n_steps", "koma_sequence_get_info",
     "koma_sequence_free", "koma_sequence_plan", "koma_simulate", "koma_sync", "koma_set_timing",
-    "koma_get_timing", "koma_get_launch_info", "koma_simulate_host",
+    "koma_get_timing", "koma_get_launch_info", "koma_simulate_host", "koma_simulate_static",
 )
 
 
@@ -127,6 +127,8 @@ def load(path: Optional[str] = None):
         lib.koma_get_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
         lib.koma_get_launch_info.restype = st
         lib.koma_get_launch_info.argtypes = [_vp, ctypes.POINTER(LaunchInfo)]
+        lib.koma_simulate_static.restype = st
+        lib.koma_simulate_static.argtypes = [_vp, _vp, _vp, _vp]
         lib.koma_simulate_host.restype = st
         lib.koma_simulate_host.argtypes = ([_vp, ctypes.c_int64] + [_dp] * 7 + [_i64p, ctypes.c_int64,
                                            ctypes.c_int64] + [_dp] * 6 + [_u8p, ctypes.c_int, _dp])
@@ -270,6 +272,13 @@ def koma_simulate(ctx, ph, seq, precision: int, sig_dev_ptr: int, stream_ptr: in
     rc = load().koma_simulate(ctx, ph, seq, int(precision), ctypes.c_void_p(int(sig_dev_ptr)),
                               ctypes.c_void_p(int(stream_ptr)))
     _check(ctx, rc, "koma_simulate")
+
+
+def koma_simulate_static(ctx, ph, seq, sig_dev_ptr: int, stream_ptr: int):
+    """Allocation-free simulation (FP32 path): partial sums in the library's
+    static device array. ``ctx`` is only used to fetch the error message."""
+    rc = load().koma_simulate_static(ph, seq, ctypes.c_void_p(int(sig_dev_ptr)), ctypes.c_void_p(int(stream_ptr)))
+    _check(ctx, rc, "koma_simulate_static")
 
 
 def koma_sync(ctx, stream_ptr: int):
