@@ -85,7 +85,7 @@ typedef struct {
     int64_t n_adc;       /* ADC time points                                   */
     int64_t n_precess;   /* steps without RF                                  */
     int64_t n_records;   /* kernel records: RF steps + precession materialise + ADC runs */
-    int64_t n_adc_runs;  /* ADC records (each <= 64 uniformly spaced samples) */
+    int64_t n_adc_runs;  /* ADC records (each <= 128 uniformly spaced samples) */
     int64_t n_materialize;
 } koma_sequence_info;
 

@@ -32,7 +32,7 @@ enum RecType : int32_t {
 
 // largest number of samples in one ADC record (the recurrence between exact
 // evaluations never runs longer than this)
-constexpr int kMaxAdcRun = 64;
+constexpr int kMaxAdcRun = 128;
 
 // 64-byte record of the FP32 split-phase path.
 //   RF:   a[0..2] gbar * gammabar * dt   (turns/m)   a[3..4] B1 * gammabar * dt (turns)
@@ -94,6 +94,7 @@ struct BlochArgs {
     void* partial = nullptr;        // FP32: float2 [grid][n_adc]; FP64: double2 [grid][n_adc]
     int64_t n_adc = 0;
     int* status = nullptr;          // device flag word (bit 0: a bounded wait gave up)
+    int rf_small = 0;               // every RF step's |a| <= 1/4 turn for every spin
 };
 
 struct ReduceArgs {

@@ -65,6 +65,23 @@ __device__ __forceinline__ void sincospi_f32(float x, float* s, float* c) {
     *c = __int_as_float(__float_as_int(c1) ^ (((iq + 1) & 2) << 30));
 }
 
+// sin(pi x), cos(pi x) for |x| <= 1/4 (no reduction needed): the same
+// series on t = pi x directly.
+__device__ __forceinline__ void sincospi_small_f32(float x, float* s, float* c) {
+    const float t = x * 3.14159265358979323846f;
+    const float t2 = t * t;
+    float ps = fmaf(t2, 2.75573192239858907e-6f, -1.98412698412698413e-4f);
+    ps = fmaf(ps, t2, 8.33333333333333333e-3f);
+    ps = fmaf(ps, t2, -1.66666666666666667e-1f);
+    ps = ps * t2;
+    *s = fmaf(ps, t, t);
+    float pc = fmaf(t2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);
+    pc = fmaf(pc, t2, -1.38888888888888889e-3f);
+    pc = fmaf(pc, t2, 4.16666666666666667e-2f);
+    pc = fmaf(pc, t2, -0.5f);
+    *c = fmaf(pc, t2, 1.0f);
+}
+
 // Fractional part (turns) of (ah + al)(bh + bl), to ~1e-7 absolute:
 // ah*bh = p + e exactly (FMA), p - rint(p) is exact, and the cross terms are
 // small. The integer part of the product is dropped (it is a whole turn).
@@ -203,6 +220,56 @@ __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
     f32x2 r;
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
+}
+
+// One excitation step for the thread's S spins: rotation about the step's
+// constant field, then relaxation over dt. The rotation vector is
+// a = gammabar dt (B1x, B1y, Gbar.x + df/gammabar) in turns; the spinor of the
+// step (Eq. Rot_exc with phi = -2 pi |a|) is the rotation by -2 pi |a| about
+// a/|a|, applied as the quaternion w = cos(pi|a|), u = -a sin(pi|a|)/|a|.
+// SMALL: the host has bounded |a| <= 1/4 turn for every step and spin, so the
+// sine needs no range reduction.
+template <int S, bool SMALL>
+__device__ __forceinline__ void rf_update(float gx, float gy, float gz, float bx, float by, float b2, float dt,
+                              const bool (&wact)[S], const float (&xh)[S], const float (&yh)[S],
+                              const float (&zh)[S], const float (&fh)[S], const float (&m0)[S],
+                              const float (&em1)[S], const float (&em2)[S], float (&mx)[S],
+                              float (&my)[S], float (&mz)[S]) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        if (!wact[s]) continue;
+        // rotation vector a = gammabar dt B (turns); the spinor of
+        // the step is the rotation by -2 pi |a| about a/|a|:
+        // quaternion w = cos(pi|a|), u = -a sin(pi|a|)/|a|
+        const float az = fmaf(gx, xh[s], fmaf(gy, yh[s], fmaf(gz, zh[s], fh[s] * dt)));
+        const float a2 = fmaf(az, az, b2);
+        const float rs = rsqrtf(a2);
+        float sh, ch;
+        if (SMALL)
+            sincospi_small_f32(a2 * rs, &sh, &ch);
+        else
+            sincospi_f32(a2 * rs, &sh, &ch);
+        const float f = -sh * rs;
+        const float ux = bx * f, uy = by * f, uz = az * f;
+        // 2/|q|^2 to first order (keeps |M| from drifting over
+        // many steps of one constant field)
+        const float nq = fmaf(ch, ch, fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+        const float c2 = fmaf(-2.f, nq, 4.f);
+        // v' = v + 2 w (u x v) + 2 u x (u x v)
+        const float px = fmaf(uy, mz[s], -uz * my[s]);
+        const float py = fmaf(uz, mx[s], -ux * mz[s]);
+        const float pz = fmaf(ux, my[s], -uy * mx[s]);
+        const float qx = fmaf(uy, pz, -uz * py);
+        const float qy = fmaf(uz, px, -ux * pz);
+        const float qz = fmaf(ux, py, -uy * px);
+        const float nx = fmaf(c2, fmaf(ch, px, qx), mx[s]);
+        const float ny = fmaf(c2, fmaf(ch, py, qy), my[s]);
+        const float nz = fmaf(c2, fmaf(ch, pz, qz), mz[s]);
+        // relaxation over the step
+        mx[s] = fmaf(em2[s], nx, nx);
+        my[s] = fmaf(em2[s], ny, ny);
+        mz[s] = fmaf(em1[s], nz - m0[s], nz);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -353,38 +420,10 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
                     }
                     dt_cached = dt;
                 }
-#pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    if (!wact[s]) continue;
-                    // rotation vector a = gammabar dt B (turns); the spinor of
-                    // the step is the rotation by -2 pi |a| about a/|a|:
-                    // quaternion w = cos(pi|a|), u = -a sin(pi|a|)/|a|
-                    const float az = fmaf(gx, xh[s], fmaf(gy, yh[s], fmaf(gz, zh[s], fh[s] * dt)));
-                    const float a2 = fmaf(az, az, b2);
-                    const float rs = rsqrtf(a2);
-                    float sh, ch;
-                    sincospi_f32(a2 * rs, &sh, &ch);
-                    const float f = -sh * rs;
-                    const float ux = bx * f, uy = by * f, uz = az * f;
-                    // 2/|q|^2 to first order (keeps |M| from drifting over
-                    // many steps of one constant field)
-                    const float nq = fmaf(ch, ch, fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
-                    const float c2 = fmaf(-2.f, nq, 4.f);
-                    // v' = v + 2 w (u x v) + 2 u x (u x v)
-                    const float px = fmaf(uy, mz[s], -uz * my[s]);
-                    const float py = fmaf(uz, mx[s], -ux * mz[s]);
-                    const float pz = fmaf(ux, my[s], -uy * mx[s]);
-                    const float qx = fmaf(uy, pz, -uz * py);
-                    const float qy = fmaf(uz, px, -ux * pz);
-                    const float qz = fmaf(ux, py, -uy * px);
-                    const float nx = fmaf(c2, fmaf(ch, px, qx), mx[s]);
-                    const float ny = fmaf(c2, fmaf(ch, py, qy), my[s]);
-                    const float nz = fmaf(c2, fmaf(ch, pz, qz), mz[s]);
-                    // relaxation over the step
-                    mx[s] = fmaf(em2[s], nx, nx);
-                    my[s] = fmaf(em2[s], ny, ny);
-                    mz[s] = fmaf(em1[s], nz - m0[s], nz);
-                }
+                if (A.rf_small)
+                    rf_update<S, true>(gx, gy, gz, bx, by, b2, dt, wact, xh, yh, zh, fh, m0, em1, em2, mx, my, mz);
+                else
+                    rf_update<S, false>(gx, gy, gz, bx, by, b2, dt, wact, xh, yh, zh, fh, m0, em1, em2, mx, my, mz);
             } else if (type == REC_PREC || type == REC_ADC) {
                 const float kxh = R.a[0], kxl = R.a[1], kyh = R.a[2], kyl = R.a[3];
                 const float kzh = R.a[4], kzl = R.a[5], th = R.a[6], tl = R.a[7];
@@ -681,7 +720,6 @@ int bloch_ctas_per_sm(bool fp64, int spins_per_thread, int block) {
         switch (spins_per_thread) {
             case 2: e = occupancy_fp32<2>(&n, block, dyn); break;
             case 4: e = occupancy_fp32<4>(&n, block, dyn); break;
-            case 8: e = occupancy_fp32<8>(&n, block, dyn); break;
             default: return -1;
         }
     }
@@ -694,7 +732,6 @@ int launch_bloch_fp32(const BlochArgs& a, const BlochLaunch& L, void* stream) {
     switch (L.spins_per_thread) {
         case 2: return launch_fp32<2>(a, L, st);
         case 4: return launch_fp32<4>(a, L, st);
-        case 8: return launch_fp32<8>(a, L, st);
         default: return cudaErrorInvalidValue;
     }
 }

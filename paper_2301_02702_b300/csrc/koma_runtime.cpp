@@ -60,6 +60,8 @@ struct koma_phantom {
     int32_t* d_group_cta = nullptr;
     int grid = 0;
     size_t table_bytes = 0;
+    // max |x|, |y|, |z| (m) and |df| (Hz) over the spins
+    double max_abs[4] = {0, 0, 0, 0};
 };
 
 struct koma_sequence {
@@ -68,6 +70,9 @@ struct koma_sequence {
     koma::Rec32* r32 = nullptr;
     koma::Rec64* r64 = nullptr;
     size_t bytes = 0;
+    // over RF steps: max |B1| gammabar dt (turns), max |Gbar_d| gammabar dt
+    // (turns/m) per axis, max dt (s); bound the per-step rotation |a|
+    double rf_b1 = 0, rf_g[3] = {0, 0, 0}, rf_dt = 0;
 };
 
 namespace {
@@ -248,6 +253,12 @@ extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const doubl
         h64[koma::P64_T1 * np + j] = t1[j];
         h64[koma::P64_T2 * np + j] = t2[j];
         h64[koma::P64_M0 * np + j] = pd[j];
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        ph->max_abs[0] = std::max(ph->max_abs[0], std::fabs(x[j]));
+        ph->max_abs[1] = std::max(ph->max_abs[1], std::fabs(y[j]));
+        ph->max_abs[2] = std::max(ph->max_abs[2], std::fabs(z[j]));
+        ph->max_abs[3] = std::max(ph->max_abs[3], std::fabs(dw[j]) / (2.0 * kPi));
     }
     for (int64_t j = n; j < np; ++j) {  // padding: inert spins
         h64[koma::P64_T1 * np + j] = 1.0;
@@ -497,6 +508,12 @@ extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, cons
     if (!seq) return fail(ctx, KOMA_E_NOMEM, "sequence_upload: host allocation");
     seq->ctx = ctx;
     seq->info = info;
+    for (const koma::Rec64& q : rb.r64) {
+        if (q.type != koma::REC_RF) continue;
+        seq->rf_b1 = std::max(seq->rf_b1, std::hypot(q.a[3], q.a[4]));
+        for (int d = 0; d < 3; ++d) seq->rf_g[d] = std::max(seq->rf_g[d], std::fabs(q.a[d]));
+        seq->rf_dt = std::max(seq->rf_dt, q.a[5]);
+    }
     DeviceGuard g(ctx->device);
     const size_t b32 = rb.r32.size() * sizeof(koma::Rec32), b64 = rb.r64.size() * sizeof(koma::Rec64);
     koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r32), b32, "sequence_upload");
@@ -542,6 +559,15 @@ extern "C" koma_status koma_sequence_free(koma_sequence* seq) {
 // simulate
 // ---------------------------------------------------------------------------
 namespace {
+
+// True when every RF step rotates every spin of `ph` by at most ~1/4 turn
+// (|a| <= |B1|gammabar dt + sum_d |Gbar_d| gammabar dt |x_d| + |df| dt), so the
+// kernel's sine needs no range reduction. 0.24 leaves room for FP32 rounding.
+bool rf_small_angles(const koma_phantom* ph, const koma_sequence* seq) {
+    double bound = seq->rf_b1 + seq->rf_dt * ph->max_abs[3];
+    for (int d = 0; d < 3; ++d) bound += seq->rf_g[d] * ph->max_abs[d];
+    return bound <= 0.24;
+}
 
 // Launch shape: the grid is a whole number of waves of (SMs x resident CTAs)
 // and every CTA gets the same number of spins, so no SM idles on a tail.
@@ -617,6 +643,7 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     A.n_rec = seq->info.n_records;
     A.n_adc = n_adc;
     A.status = ctx->d_status;
+    A.rf_small = rf_small_angles(ph, seq) ? 1 : 0;
     A.spins_per_cta = L.spins_per_cta;
     koma::ReduceArgs R;
     R.n_adc = n_adc;
@@ -749,6 +776,7 @@ extern "C" koma_status koma_simulate_static(const koma_phantom* ph, const koma_s
     A.n_rec = seq->info.n_records;
     A.n_adc = n_adc;
     A.status = ctx->d_status;
+    A.rf_small = rf_small_angles(ph, seq) ? 1 : 0;
     A.spins_per_cta = L.spins_per_cta;
     A.partial = scratch;  // every (CTA, sample) entry is written before K2 reads it
     koma::ReduceArgs R;

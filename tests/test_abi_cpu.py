@@ -91,7 +91,7 @@ def _decode_samples(rec):
             continue
         count, k0 = int(r[1]), int(r[2])
         a = r[3:]
-        assert 1 <= count <= 64
+        assert 1 <= count <= 128
         for l in range(count):
             out[k0 + l] = (a[0:3] + l * a[4:7], a[3] + l * a[7])
     return [out[k] for k in range(len(out))]
@@ -118,13 +118,13 @@ def test_plan_reproduces_sample_moments(lib, name):
 
 def test_plan_merges_uniform_readouts(lib):
     """A Cartesian readout of n samples at constant gradient becomes
-    ceil(n / 64) ADC records."""
+    ceil(n / 128) ADC records."""
     b = SequenceBuilder()
     b.steps(1, 1e-6, b1=1e-5)
     b.steps(5, 10e-6, [0.01, 0, 0])
     b.steps(200, 4e-6, adc=True)
     info = koma.koma_sequence_plan(b.build())
-    assert info["n_adc"] == 200 and info["n_adc_runs"] == 4
+    assert info["n_adc"] == 200 and info["n_adc_runs"] == 2
 
 
 def test_plan_empty_and_adc_at_t0(lib):
