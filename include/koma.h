@@ -194,8 +194,12 @@ koma_status koma_sequence_plan(int64_t n_steps, const double *dt, const double *
  *             complex128 [n_groups, n_adc] array), written completely.
  * The context's scratch (per-CTA partial sums, FP32) is grown on demand with
  * cudaMalloc, so the first call for a larger problem is not capturable.
- * Grouped phantoms (n_groups > 1) are simulated group by group: the sum runs
- * within each group.
+ * Grouped phantoms (n_groups > 1) sum within each group. Many small groups
+ * (at most 512 spins per group on average, e.g. the isochromats of MRF
+ * dictionary entries) run on the work-item kernel: each group is split into
+ * items of at most 32 x (spins per thread) spins, one warp per item, in one
+ * persistent launch taking items longest first; larger groups are split into
+ * whole CTAs. Both end with a fixed-order per-group sum (deterministic).
  * Errors: KOMA_E_INVALID (NULL handles, objects of another context, bad
  *   precision), KOMA_E_NOMEM (scratch over budget), KOMA_E_CUDA (launch).
  * Device-side waits are bounded; a wait that gives up is reported by the
@@ -234,6 +238,18 @@ koma_status koma_simulate(koma_ctx *ctx, const koma_phantom *ph, const koma_sequ
  */
 koma_status koma_simulate_static(const koma_phantom *ph, const koma_sequence *seq,
                                  double *sig_dev, void *stream);
+
+/*
+ * Autotune the FP32 launch for this (phantom, sequence) pair: times the
+ * candidate configurations on the full problem (grouped phantoms: spins per
+ * thread {2, 4} x block {128, 256} of the work-item kernel; otherwise spins
+ * per thread {2, 4} of the Bloch kernel) and keeps the fastest on the
+ * phantom; later koma_simulate calls with this sequence use it. Synchronous
+ * (waits on `stream`); overwrites sig_dev (device FP64 [n_groups][n_adc][2]).
+ * chosen: NULL or receives the chosen launch. Errors as koma_simulate.
+ */
+koma_status koma_tune(koma_ctx *ctx, const koma_phantom *ph, const koma_sequence *seq,
+                      double *sig_dev, void *stream, koma_launch_info *chosen);
 
 /*
  * Wait for `stream` and report device-side status: KOMA_E_TIMEOUT if a

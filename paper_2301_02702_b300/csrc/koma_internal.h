@@ -33,12 +33,21 @@ enum RecType : int32_t {
 // largest number of samples in one ADC record (the recurrence between exact
 // evaluations never runs longer than this)
 constexpr int kMaxAdcRun = 128;
+constexpr int kCountMask = 0xffff;   // samples field of an ADC record's count
+constexpr int kTermShift = 16;       // nonzero-term bits of PREC/ADC records
 
 // 64-byte record of the FP32 split-phase path.
-//   RF:   a[0..2] gbar * gammabar * dt   (turns/m)   a[3..4] B1 * gammabar * dt (turns)
+//   RF:   a[0..2] pi gbar gammabar dt (rad/m)   a[3..4] pi B1 gammabar dt (rad):
+//         the half-angle rotation vector of the step's field
 //         a[5]    |a[3..4]|^2             a[6] dt (s)
+//         The first record of every run of consecutive RF records carries the
+//         run's length in `count` and the run's maxima in a[7] |a[3..4]|,
+//         a[8..10] |a[d]|, a[11] dt; later ones have count 0.
 //   PREC: a[0..5] Kx hi,lo Ky hi,lo Kz hi,lo (turns/m)   a[6..7] tau hi,lo (s)
 //   ADC:  a[0..7] K0, tau0 as in PREC     a[8..10] dK (turns/m)   a[11] dtau (s)
+//   PREC/ADC: count = samples (ADC; low 16 bits) | nonzero-term bits << 16
+//         (bit 0 Kx, 1 Ky, 2 Kz, 3 tau), so the kernel skips zero phase terms
+//         without testing the payload.
 struct alignas(16) Rec32 {
     int32_t type;
     int32_t count;
@@ -94,7 +103,25 @@ struct BlochArgs {
     void* partial = nullptr;        // FP32: float2 [grid][n_adc]; FP64: double2 [grid][n_adc]
     int64_t n_adc = 0;
     int* status = nullptr;          // device flag word (bit 0: a bounded wait gave up)
-    int rf_small = 0;               // every RF step's |a| <= 1/4 turn for every spin
+    float ext[4] = {0, 0, 0, 0};    // max |x|, |y|, |z| (m), |df| (Hz) over the phantom
+    int used = 0;                   // bit d: coordinate d (x, y, z, df) is nonzero somewhere
+};
+
+struct ItemArgs {
+    const float* p32 = nullptr;
+    const double* p64 = nullptr;
+    int64_t n_pad = 0;
+    const int64_t* item_begin = nullptr;  // [n_items + 1] first spin of each item
+    const int32_t* order = nullptr;       // [n_items] processing order (longest first)
+    int64_t n_items = 0;
+    int* counter = nullptr;               // batch counter, zero at launch
+    const void* rec = nullptr;            // Rec32 records
+    int64_t n_rec = 0;
+    void* partial = nullptr;              // float2 [n_items][n_adc]
+    int64_t n_adc = 0;
+    int* status = nullptr;
+    float ext[4] = {0, 0, 0, 0};
+    int used = 0;
 };
 
 struct ReduceArgs {
@@ -110,6 +137,8 @@ struct ReduceArgs {
 int launch_bloch_fp32(const BlochArgs& a, const BlochLaunch& L, void* stream);
 int launch_bloch_fp64(const BlochArgs& a, const BlochLaunch& L, void* stream);
 int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream);
+int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, void* stream);
+int items_ctas_per_sm(int spins_per_thread, int block);
 // Static partial-sum scratch of koma_simulate_static: capacity in float2
 // elements, and its device address on `device` (which must be current; the
 // address is looked up once per device and cached).

@@ -4,6 +4,8 @@
 //                           phase in hi/lo FP32, signal partials per CTA.
 // K1d bloch_fp64_kernel     the same walk in FP64 (KOMA_FP64).
 // K2  reduce_partials<P>    fixed-order FP64 sum of the per-CTA partials.
+// K3  bloch_items_kernel<S> grouped phantoms: one warp per work item of one
+//                           group, persistent CTAs, per-item partial rows.
 //
 // Method: KomaMRI.jl paper, Section "Physical and Mathematical Background"
 // (Bloch equation, operator splitting, spinor rotation in the excitation
@@ -65,23 +67,6 @@ __device__ __forceinline__ void sincospi_f32(float x, float* s, float* c) {
     *c = __int_as_float(__float_as_int(c1) ^ (((iq + 1) & 2) << 30));
 }
 
-// sin(pi x), cos(pi x) for |x| <= 1/4 (no reduction needed): the same
-// series on t = pi x directly.
-__device__ __forceinline__ void sincospi_small_f32(float x, float* s, float* c) {
-    const float t = x * 3.14159265358979323846f;
-    const float t2 = t * t;
-    float ps = fmaf(t2, 2.75573192239858907e-6f, -1.98412698412698413e-4f);
-    ps = fmaf(ps, t2, 8.33333333333333333e-3f);
-    ps = fmaf(ps, t2, -1.66666666666666667e-1f);
-    ps = ps * t2;
-    *s = fmaf(ps, t, t);
-    float pc = fmaf(t2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);
-    pc = fmaf(pc, t2, -1.38888888888888889e-3f);
-    pc = fmaf(pc, t2, 4.16666666666666667e-2f);
-    pc = fmaf(pc, t2, -0.5f);
-    *c = fmaf(pc, t2, 1.0f);
-}
-
 // Fractional part (turns) of (ah + al)(bh + bl), to ~1e-7 absolute:
 // ah*bh = p + e exactly (FMA), p - rint(p) is exact, and the cross terms are
 // small. The integer part of the product is dropped (it is a whole turn).
@@ -91,6 +76,20 @@ __device__ __forceinline__ float frac_product(float ah, float al, float bh, floa
     const float r = p - rintf(p);
     const float c = fmaf(ah, bl, fmaf(al, bh, e));
     return r + c;
+}
+
+// e^x - 1 in FP32 with relative accuracy also for small |x| (relaxation over
+// one short step, applied many times, must not drift): the Taylor series
+// through x^5 for |x| < 1/32 (remainder below 1e-10 relative), else
+// exp(x) - 1 where the cancellation costs at most 5 bits.
+__device__ __forceinline__ float expm1_f32(float x) {
+    if (fabsf(x) < 0.03125f) {
+        float p = fmaf(x, 1.f / 120.f, 1.f / 24.f);
+        p = fmaf(p, x, 1.f / 6.f);
+        p = fmaf(p, x, 0.5f);
+        return fmaf(p * x, x, x);
+    }
+    return expf(x) - 1.f;
 }
 
 // ---------------------------------------------------------------------------
@@ -196,15 +195,8 @@ __device__ __forceinline__ f32x2 pk(float lo, float hi) {
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
     return r;
 }
-__device__ __forceinline__ float lo_of(f32x2 v) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return a;
-}
-__device__ __forceinline__ float hi_of(f32x2 v) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return b;
+__device__ __forceinline__ void unpk(f32x2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
     f32x2 r;
@@ -222,54 +214,302 @@ __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
     return r;
 }
 
-// One excitation step for the thread's S spins: rotation about the step's
-// constant field, then relaxation over dt. The rotation vector is
-// a = gammabar dt (B1x, B1y, Gbar.x + df/gammabar) in turns; the spinor of the
-// step (Eq. Rot_exc with phi = -2 pi |a|) is the rotation by -2 pi |a| about
-// a/|a|, applied as the quaternion w = cos(pi|a|), u = -a sin(pi|a|)/|a|.
-// SMALL: the host has bounded |a| <= 1/4 turn for every step and spin, so the
-// sine needs no range reduction.
-template <int S, bool SMALL>
-__device__ __forceinline__ void rf_update(float gx, float gy, float gz, float bx, float by, float b2, float dt,
-                              const bool (&wact)[S], const float (&xh)[S], const float (&yh)[S],
-                              const float (&zh)[S], const float (&fh)[S], const float (&m0)[S],
-                              const float (&em1)[S], const float (&em2)[S], float (&mx)[S],
-                              float (&my)[S], float (&mz)[S]) {
+// ---------------------------------------------------------------------------
+// Per-thread spin set: S spins held in registers for a whole walk of the
+// record stream. Slot s is spin base + s * stride when that is < end. Keeps
+// M(t_ref) = (mx, my, mz) per spin; parameters are loaded once.
+// ---------------------------------------------------------------------------
+template <int S>
+struct Spins {
+    static_assert(S % 2 == 0, "spins are processed in packed pairs");
+    static constexpr int NP = S / 2;
+    float xh[S], yh[S], zh[S], fh[S], m0[S], r1[S], r2[S];
+    float mx[S], my[S], mz[S], em1[S], em2[S], zr[S], zi[S];
+    bool wact[S];  // warp-uniform: slot s holds at least one spin of the warp
+    int64_t base, end;
+    int stride;
+    float dt_cached;               // em1/em2 belong to this dt
+    int rf_mode;                   // rotation path of the current RF run (uniform)
+    float key0, key1, key2, key3;  // zr/zi belong to this (dK, dtau)
+
+    __device__ __forceinline__ int64_t index(int s) const { return base + static_cast<int64_t>(s) * stride; }
+
+    __device__ __forceinline__ void load(const float* __restrict__ P, int64_t np, int64_t base_, int stride_,
+                                         int64_t end_) {
+        base = base_;
+        stride = stride_;
+        end = end_;
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        if (!wact[s]) continue;
-        // rotation vector a = gammabar dt B (turns); the spinor of
-        // the step is the rotation by -2 pi |a| about a/|a|:
-        // quaternion w = cos(pi|a|), u = -a sin(pi|a|)/|a|
-        const float az = fmaf(gx, xh[s], fmaf(gy, yh[s], fmaf(gz, zh[s], fh[s] * dt)));
-        const float a2 = fmaf(az, az, b2);
-        const float rs = rsqrtf(a2);
-        float sh, ch;
-        if (SMALL)
-            sincospi_small_f32(a2 * rs, &sh, &ch);
-        else
-            sincospi_f32(a2 * rs, &sh, &ch);
-        const float f = -sh * rs;
-        const float ux = bx * f, uy = by * f, uz = az * f;
-        // 2/|q|^2 to first order (keeps |M| from drifting over
-        // many steps of one constant field)
-        const float nq = fmaf(ch, ch, fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
-        const float c2 = fmaf(-2.f, nq, 4.f);
-        // v' = v + 2 w (u x v) + 2 u x (u x v)
-        const float px = fmaf(uy, mz[s], -uz * my[s]);
-        const float py = fmaf(uz, mx[s], -ux * mz[s]);
-        const float pz = fmaf(ux, my[s], -uy * mx[s]);
-        const float qx = fmaf(uy, pz, -uz * py);
-        const float qy = fmaf(uz, px, -ux * pz);
-        const float qz = fmaf(ux, py, -uy * px);
-        const float nx = fmaf(c2, fmaf(ch, px, qx), mx[s]);
-        const float ny = fmaf(c2, fmaf(ch, py, qy), my[s]);
-        const float nz = fmaf(c2, fmaf(ch, pz, qz), mz[s]);
-        // relaxation over the step
-        mx[s] = fmaf(em2[s], nx, nx);
-        my[s] = fmaf(em2[s], ny, ny);
-        mz[s] = fmaf(em1[s], nz - m0[s], nz);
+        for (int s = 0; s < S; ++s) {
+            const int64_t j = index(s);
+            const bool v = j < end;
+            wact[s] = __any_sync(kFull, v);
+            xh[s] = v ? P[P32_XH * np + j] : 0.f;
+            yh[s] = v ? P[P32_YH * np + j] : 0.f;
+            zh[s] = v ? P[P32_ZH * np + j] : 0.f;
+            fh[s] = v ? P[P32_FH * np + j] : 0.f;
+            m0[s] = v ? P[P32_M0 * np + j] : 0.f;
+            r1[s] = v ? P[P32_R1 * np + j] : 0.f;
+            r2[s] = v ? P[P32_R2 * np + j] : 0.f;
+            mx[s] = 0.f;
+            my[s] = 0.f;
+            mz[s] = m0[s];
+            em1[s] = 0.f;
+            em2[s] = 0.f;
+            zr[s] = 1.f;
+            zi[s] = 0.f;
+        }
+        dt_cached = -1.f;
+        rf_mode = 0;
+        key0 = __int_as_float(0x7fc00000);  // NaN: no rotator yet
+        key1 = key2 = key3 = 0.f;
     }
+
+    // One excitation step: rotation about the step's constant field, then
+    // relaxation over dt. The rotation vector is a = gammabar dt (B1x, B1y,
+    // Gbar.x + df/gammabar) in turns; the spinor of the step (Eq. Rot_exc with
+    // phi = -2 pi |a|) is the rotation by -2 pi |a| about a/|a|, applied as
+    // the quaternion w = cos(pi|a|), u = -a sin(pi|a|)/|a|.
+    // One excitation step for every slot: rotation about the step's constant
+    // field, then relaxation over dt. The record holds theta = pi gammabar dt
+    // (B1x, B1y, Gbar) and the spin adds pi dt df, so theta is the half-angle
+    // vector in radians; the spinor of the step (Eq. Rot_exc, phi = -2|theta|)
+    // is the rotation by -2|theta| about theta/|theta|, applied as the
+    // quaternion w = cos|theta|, u = -theta sin|theta|/|theta|.
+    // SMALL (|theta| <= 0.754 for every step and spin): cos t and sin(t)/t are
+    // even series in t^2 = theta.theta (terms to t^10 and t^8; remainders
+    // below 3e-9), so no square root, division or sine is needed.
+    template <bool SMALL>
+    __device__ __forceinline__ void rf_slots(float gx, float gy, float gz, float bx, float by, float b2, float dt) {
+        const float pdt = dt * 3.14159265358979323846f;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (!wact[s]) continue;
+            const float az = fmaf(gx, xh[s], fmaf(gy, yh[s], fmaf(gz, zh[s], fh[s] * pdt)));
+            const float t2 = fmaf(az, az, b2);
+            float ch, nsinc;  // cos t and -sin(t)/t
+            if (SMALL) {
+                float q = fmaf(t2, -2.75573192239858907e-6f, 1.98412698412698413e-4f);   // -1/9!, 1/7!
+                q = fmaf(q, t2, -8.33333333333333333e-3f);                               // -1/5!
+                q = fmaf(q, t2, 1.66666666666666667e-1f);                                // 1/3!
+                nsinc = fmaf(q, t2, -1.0f);
+                float c = fmaf(t2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);  // -1/10!, 1/8!
+                c = fmaf(c, t2, -1.38888888888888889e-3f);                               // -1/6!
+                c = fmaf(c, t2, 4.16666666666666667e-2f);                                // 1/4!
+                c = fmaf(c, t2, -0.5f);
+                ch = fmaf(c, t2, 1.0f);
+            } else {
+                const float rs = rsqrtf(t2);
+                float sh;
+                sincospi_f32(t2 * rs * 0.318309886183790671538f, &sh, &ch);
+                nsinc = -sh * rs;
+            }
+            const float ux = bx * nsinc, uy = by * nsinc, uz = az * nsinc;
+            // 2/|q|^2 to first order (keeps |M| from drifting over many steps
+            // of one constant field)
+            const float nq = fmaf(ch, ch, fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+            const float c2 = fmaf(-2.f, nq, 4.f);
+            // v' = v + 2 w (u x v) + 2 u x (u x v)
+            const float px = fmaf(uy, mz[s], -uz * my[s]);
+            const float py = fmaf(uz, mx[s], -ux * mz[s]);
+            const float pz = fmaf(ux, my[s], -uy * mx[s]);
+            const float qx = fmaf(uy, pz, -uz * py);
+            const float qy = fmaf(uz, px, -ux * pz);
+            const float qz = fmaf(ux, py, -uy * px);
+            const float nx = fmaf(c2, fmaf(ch, px, qx), mx[s]);
+            const float ny = fmaf(c2, fmaf(ch, py, qy), my[s]);
+            const float nz = fmaf(c2, fmaf(ch, pz, qz), mz[s]);
+            mx[s] = fmaf(em2[s], nx, nx);
+            my[s] = fmaf(em2[s], ny, ny);
+            mz[s] = fmaf(em1[s], nz - m0[s], nz);
+        }
+    }
+
+    // RF record. The first record of a run of RF records carries the run's
+    // maxima; with the phantom's extents `ext` (max |x|, |y|, |z| in m, |df|
+    // in Hz) they choose, once per run, between: one rotation for all spins
+    // (the field's z part vanishes for every spin), the series path
+    // (|theta| <= 0.754 for every step and spin), or the general path.
+    __device__ __forceinline__ void rf(const Rec32& R, const float (&ext)[4]) {
+        const float gx = R.a[0], gy = R.a[1], gz = R.a[2];
+        const float bx = R.a[3], by = R.a[4], b2 = R.a[5], dt = R.a[6];
+        if (R.count > 0) {
+            const float mb = R.a[7], mgx = R.a[8], mgy = R.a[9], mgz = R.a[10], mdt = R.a[11];
+            const bool same = (mgx == 0.f || ext[0] == 0.f) && (mgy == 0.f || ext[1] == 0.f) &&
+                              (mgz == 0.f || ext[2] == 0.f) && ext[3] == 0.f;
+            const float bound = mb + mgx * ext[0] + mgy * ext[1] + mgz * ext[2] +
+                                mdt * 3.14159265358979323846f * ext[3];
+            rf_mode = same ? 2 : (bound <= 0.754f ? 1 : 0);
+        }
+        if (dt != dt_cached) {
+            // relaxation factors minus one over dt, relatively accurate for
+            // short steps (r = log2(e)/T, so -dt/T = -dt r ln 2)
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                em1[s] = expm1_f32(-dt * r1[s] * 0.693147180559945309f);
+                em2[s] = expm1_f32(-dt * r2[s] * 0.693147180559945309f);
+            }
+            dt_cached = dt;
+        }
+        if (rf_mode == 2)
+            rf_uniform(bx, by, b2);
+        else if (rf_mode == 1)
+            rf_slots<true>(gx, gy, gz, bx, by, b2, dt);
+        else
+            rf_slots<false>(gx, gy, gz, bx, by, b2, dt);
+    }
+
+    // RF step whose rotation is the same for every spin (field in the xy
+    // plane): quaternion computed once, applied to every slot, then relaxation.
+    __device__ __forceinline__ void rf_uniform(float bx, float by, float b2) {
+        const float rs = rsqrtf(b2);
+        float sh, ch;
+        sincospi_f32(b2 * rs * 0.318309886183790671538f, &sh, &ch);
+        const float f = -sh * rs;
+        const float ux = bx * f, uy = by * f;
+        const float nq = fmaf(ch, ch, fmaf(ux, ux, uy * uy));
+        const float c2 = fmaf(-2.f, nq, 4.f);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (!wact[s]) continue;
+            // u = (ux, uy, 0): p = u x v, q = u x p
+            const float px = uy * mz[s];
+            const float py = -ux * mz[s];
+            const float pz = fmaf(ux, my[s], -uy * mx[s]);
+            const float qx = uy * pz;
+            const float qy = -ux * pz;
+            const float qz = fmaf(ux, py, -uy * px);
+            const float nx = fmaf(c2, fmaf(ch, px, qx), mx[s]);
+            const float ny = fmaf(c2, fmaf(ch, py, qy), my[s]);
+            const float nz = fmaf(c2, fmaf(ch, pz, qz), mz[s]);
+            mx[s] = fmaf(em2[s], nx, nx);
+            my[s] = fmaf(em2[s], ny, ny);
+            mz[s] = fmaf(em1[s], nz - m0[s], nz);
+        }
+    }
+
+    // Transverse magnetisation at (K, tau) relative to t_ref, per spin:
+    // Mxy(t_ref) e^{-tau/T2} e^{-i 2 pi (K.x + df tau)}, the phase's
+    // fractional turns from hi/lo products. Terms whose coordinate is zero
+    // over the phantom (`used` bits) or whose moment is zero (the record's
+    // term bits) are skipped.
+    // With `prec` the reference moves to (K, tau) (Mz recovers with T1).
+    __device__ __forceinline__ void exact(const Rec32& R, bool prec, const float* __restrict__ P, int64_t np,
+                                          int used, float (&er)[S], float (&ei)[S]) {
+        const float kxh = R.a[0], kxl = R.a[1], kyh = R.a[2], kyl = R.a[3];
+        const float kzh = R.a[4], kzl = R.a[5], th = R.a[6], tl = R.a[7];
+        const int terms = (R.count >> kTermShift) & used;
+        const bool ux = terms & 1, uy = terms & 2, uz = terms & 4, uf = terms & 8;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            er[s] = 0.f;
+            ei[s] = 0.f;
+            if (!wact[s]) continue;
+            const int64_t j = index(s);
+            const bool v = j < end;
+            float F = 0.f;
+            if (ux) F += frac_product(xh[s], v ? P[P32_XL * np + j] : 0.f, kxh, kxl);
+            if (uy) F += frac_product(yh[s], v ? P[P32_YL * np + j] : 0.f, kyh, kyl);
+            if (uz) F += frac_product(zh[s], v ? P[P32_ZL * np + j] : 0.f, kzh, kzl);
+            if (uf) F += frac_product(fh[s], v ? P[P32_FL * np + j] : 0.f, th, tl);
+            float sn = 0.f, cs = 1.f;
+            if (ux || uy || uz || uf) sincospi_f32(-2.f * F, &sn, &cs);
+            const float e2 = exp2f(-th * r2[s]);
+            er[s] = e2 * fmaf(mx[s], cs, -my[s] * sn);
+            ei[s] = e2 * fmaf(mx[s], sn, my[s] * cs);
+            if (prec) {
+                const float e1 = exp2f(-th * r1[s]);
+                mx[s] = er[s];
+                my[s] = ei[s];
+                mz[s] = fmaf(mz[s] - m0[s], e1, m0[s]);
+            }
+        }
+    }
+
+    // ADC record of L samples starting from (er, ei): sums over the warp's
+    // spins of every sample, handed to sink(i, re, im) on one lane per sample
+    // (i = sample index within the run). Samples after the first come from
+    // the per-sample rotator z = e^{-dtau/T2} e^{-i 2 pi (dK.x + df dtau)}
+    // (exact in exact arithmetic for uniformly spaced samples), spins in
+    // packed pairs; warp sums by a fixed butterfly (deterministic).
+    template <class Sink>
+    __device__ __forceinline__ void adc(const Rec32& R, int L, float (&er)[S], float (&ei)[S], int lane,
+                                        Sink&& sink) {
+        if (L == 1) {
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                sr += er[s];
+                si += ei[s];
+            }
+            sr = warp_sum(sr);
+            si = warp_sum(si);
+            if (lane == 0) sink(0, sr, si);
+            return;
+        }
+        const float dkx = R.a[8], dky = R.a[9], dkz = R.a[10], dtau = R.a[11];
+        if (!(dkx == key0 && dky == key1 && dkz == key2 && dtau == key3)) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const float th1 = -fmaf(dkx, xh[s], fmaf(dky, yh[s], fmaf(dkz, zh[s], fh[s] * dtau)));
+                float sn, cs;
+                sincospi_f32(2.f * th1, &sn, &cs);
+                const float mag = exp2f(-dtau * r2[s]);
+                zr[s] = mag * cs;
+                zi[s] = mag * sn;
+            }
+            key0 = dkx;
+            key1 = dky;
+            key2 = dkz;
+            key3 = dtau;
+        }
+        f32x2 pr[NP], pi_[NP], qr[NP], qi[NP], qn[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            pr[p] = pk(er[2 * p], er[2 * p + 1]);
+            pi_[p] = pk(ei[2 * p], ei[2 * p + 1]);
+            qr[p] = pk(zr[2 * p], zr[2 * p + 1]);
+            qi[p] = pk(zi[2 * p], zi[2 * p + 1]);
+            qn[p] = pk(-zi[2 * p], -zi[2 * p + 1]);
+        }
+        for (int c = 0; c < L; c += kV) {
+            float ar[kV], ai[kV];
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                f32x2 sr2 = pr[0], si2 = pi_[0];
+#pragma unroll
+                for (int p = 1; p < NP; ++p) {
+                    sr2 = add2(sr2, pr[p]);
+                    si2 = add2(si2, pi_[p]);
+                }
+                float r0, r1, i0, i1;
+                unpk(sr2, r0, r1);
+                unpk(si2, i0, i1);
+                ar[v] = r0 + r1;
+                ai[v] = i0 + i1;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const f32x2 nr2 = fma2(pr[p], qr[p], mul2(pi_[p], qn[p]));
+                    pi_[p] = fma2(pr[p], qi[p], mul2(pi_[p], qr[p]));
+                    pr[p] = nr2;
+                }
+            }
+            const float sr = reduce_scatter8(ar, lane);
+            const float si = reduce_scatter8(ai, lane);
+            const int vl = (lane >> 2) & 7;
+            if ((lane & 3) == 0 && c + vl < L) sink(c + vl, sr, si);
+        }
+    }
+};
+
+// Tile pipeline of the record stream: 64-record tiles brought into shared
+// memory by TMA bulk copies, double buffered; tile g of the CTA's lifetime
+// sits in buffer g & 1 and completes phase (g >> 1) & 1 of its mbarrier.
+__device__ __forceinline__ void issue_tile(Rec32 (*s_rec)[kTile], const uint32_t (&bar)[2], const Rec32* grec,
+                                           int64_t n_rec, int64_t t, uint64_t g) {
+    const int64_t nr = min(static_cast<int64_t>(kTile), n_rec - t * kTile);
+    tma_load_1d(smem_u32(&s_rec[g & 1][0]), grec + t * kTile, static_cast<uint32_t>(nr * sizeof(Rec32)),
+                bar[g & 1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -277,22 +517,16 @@ __device__ __forceinline__ void rf_update(float gx, float gy, float gz, float bx
 //
 // Every CTA owns a contiguous spin range; thread `tid` holds spins
 // begin + s * blockDim + tid for s < S in registers for the whole sequence.
-// All threads walk the same record stream (64-record tiles brought into
-// shared memory by TMA bulk copies, double buffered) and read each record as
-// a broadcast. Per spin the kernel keeps M(t_ref) = (mx, my, mz).
+// All threads walk the same record stream (tiles in shared memory) and read
+// each record as a broadcast.
 //   RF   rotate by the step's constant field and relax (one step).
 //   PREC replace M(t_ref) by M(t) at the given (K, tau).
-//   ADC  `count` samples: the first from the exact phase, the rest by the
-//        per-sample rotator z = e^{-dtau/T2} e^{-i 2 pi (dK.x + df dtau)}
-//        (exact in exact arithmetic for uniformly spaced samples).
-// Samples are summed over the thread's spins, reduce-scattered across the
-// warp, staged per warp in shared memory and summed over warps in a fixed
-// order into one FP32 partial per (CTA, sample).
+//   ADC  `count` samples (Spins::adc).
+// Warp sample sums are staged per warp in shared memory and summed over
+// warps in a fixed order into one FP32 partial per (CTA, sample).
 // ---------------------------------------------------------------------------
 template <int S>
 __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_constant__ BlochArgs A) {
-    static_assert(S % 2 == 0, "spins are processed in packed pairs");
-    constexpr int NP = S / 2;  // packed spin pairs
     __shared__ __align__(128) Rec32 s_rec[2][kTile];
     __shared__ __align__(8) uint64_t s_bar[2];
     // per-warp sample sums, two buffers: [buf][warp][kRed32] (dynamic)
@@ -313,47 +547,14 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
         c_begin = static_cast<int64_t>(cta) * A.spins_per_cta;
         c_end = min(A.n, c_begin + A.spins_per_cta);
     }
-
-    const float* __restrict__ P = A.p32;
-    const double* __restrict__ P64 = A.p64;
     const int64_t np = A.n_pad;
-
-    float xh[S], yh[S], zh[S], fh[S], m0[S], r1[S], r2[S];
-    float mx[S], my[S], mz[S], em1[S], em2[S], zr[S], zi[S];
-    bool wact[S];  // warp-uniform: this slot holds at least one spin in the warp
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const int64_t j = c_begin + static_cast<int64_t>(s) * nthr + tid;
-        const bool v = j < c_end;
-        wact[s] = __any_sync(kFull, v);
-        xh[s] = v ? P[P32_XH * np + j] : 0.f;
-        yh[s] = v ? P[P32_YH * np + j] : 0.f;
-        zh[s] = v ? P[P32_ZH * np + j] : 0.f;
-        fh[s] = v ? P[P32_FH * np + j] : 0.f;
-        m0[s] = v ? P[P32_M0 * np + j] : 0.f;
-        r1[s] = v ? P[P32_R1 * np + j] : 0.f;
-        r2[s] = v ? P[P32_R2 * np + j] : 0.f;
-        mx[s] = 0.f;
-        my[s] = 0.f;
-        mz[s] = m0[s];
-        em1[s] = 0.f;
-        em2[s] = 0.f;
-        zr[s] = 1.f;
-        zi[s] = 0.f;
-    }
-    // lo parts and FP64 relaxation times are read on demand (rare events)
-    auto spin_index = [&](int s) { return c_begin + static_cast<int64_t>(s) * nthr + tid; };
-
-    float dt_cached = -1.f;                     // uniform: em1/em2 belong to this dt
-    float key0 = __int_as_float(0x7fc00000), key1 = 0.f, key2 = 0.f, key3 = 0.f;  // rotator key (NaN: none)
+    Spins<S> sp;
+    sp.load(A.p32, np, c_begin + tid, nthr, c_end);
 
     int red_buf = 0;
-    int64_t red_base = 0, red_end = 0;          // samples [red_base, red_end) staged
+    int64_t red_base = 0, red_end = 0;  // samples [red_base, red_end) staged
     float2* __restrict__ partial = static_cast<float2*>(A.partial) + static_cast<int64_t>(cta) * A.n_adc;
-    auto red_slot = [&](int buf, int w, int i) -> float2& {
-        return s_red_dyn[(buf * nwarps + w) * kRed32 + i];
-    };
-
+    auto red_slot = [&](int buf, int w, int i) -> float2& { return s_red_dyn[(buf * nwarps + w) * kRed32 + i]; };
     auto flush = [&]() {
         __syncthreads();
         const int cnt = static_cast<int>(red_end - red_base);
@@ -380,11 +581,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
     }
     __syncthreads();
     if (tid == 0) {
-        for (int64_t t = 0; t < 2 && t < n_tiles; ++t) {
-            const int64_t nr = min(static_cast<int64_t>(kTile), A.n_rec - t * kTile);
-            tma_load_1d(smem_u32(&s_rec[t][0]), grec + t * kTile, static_cast<uint32_t>(nr * sizeof(Rec32)),
-                        bar[t]);
-        }
+        for (int64_t t = 0; t < 2 && t < n_tiles; ++t) issue_tile(s_rec, bar, grec, A.n_rec, t, t);
     }
 
     for (int64_t t = 0; t < n_tiles; ++t) {
@@ -405,135 +602,121 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
             const Rec32& R = s_rec[b][r];
             const int type = R.type;
             if (type == REC_RF) {
-                const float gx = R.a[0], gy = R.a[1], gz = R.a[2];
-                const float bx = R.a[3], by = R.a[4], b2 = R.a[5], dt = R.a[6];
-                if (dt != dt_cached) {
-                    // relaxation factors minus one, FP64-accurate: repeated
-                    // application over long pulses must not drift
-#pragma unroll
-                    for (int s = 0; s < S; ++s) {
-                        const int64_t j = spin_index(s);
-                        if (j < c_end) {
-                            em1[s] = static_cast<float>(expm1(-static_cast<double>(dt) / P64[P64_T1 * np + j]));
-                            em2[s] = static_cast<float>(expm1(-static_cast<double>(dt) / P64[P64_T2 * np + j]));
-                        }
-                    }
-                    dt_cached = dt;
-                }
-                if (A.rf_small)
-                    rf_update<S, true>(gx, gy, gz, bx, by, b2, dt, wact, xh, yh, zh, fh, m0, em1, em2, mx, my, mz);
-                else
-                    rf_update<S, false>(gx, gy, gz, bx, by, b2, dt, wact, xh, yh, zh, fh, m0, em1, em2, mx, my, mz);
-            } else if (type == REC_PREC || type == REC_ADC) {
-                const float kxh = R.a[0], kxl = R.a[1], kyh = R.a[2], kyl = R.a[3];
-                const float kzh = R.a[4], kzl = R.a[5], th = R.a[6], tl = R.a[7];
-                // exact state at (K, tau): phase -(K.x + df tau) turns
+                sp.rf(R, A.ext);
+            } else if (type == REC_PREC) {
                 float er[S], ei[S];
-#pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    er[s] = 0.f;
-                    ei[s] = 0.f;
-                    if (!wact[s]) continue;
-                    const int64_t j = spin_index(s);
-                    const bool v = j < c_end;
-                    const float xl = v ? P[P32_XL * np + j] : 0.f;
-                    const float yl = v ? P[P32_YL * np + j] : 0.f;
-                    const float zl = v ? P[P32_ZL * np + j] : 0.f;
-                    const float fl = v ? P[P32_FL * np + j] : 0.f;
-                    const float F = frac_product(xh[s], xl, kxh, kxl) + frac_product(yh[s], yl, kyh, kyl) +
-                                    frac_product(zh[s], zl, kzh, kzl) + frac_product(fh[s], fl, th, tl);
-                    float sn, cs;
-                    sincospi_f32(-2.f * F, &sn, &cs);
-                    const float e2 = exp2f(-th * r2[s]);
-                    er[s] = e2 * fmaf(mx[s], cs, -my[s] * sn);
-                    ei[s] = e2 * fmaf(mx[s], sn, my[s] * cs);
-                    if (type == REC_PREC) {
-                        const float e1 = exp2f(-th * r1[s]);
-                        mx[s] = er[s];
-                        my[s] = ei[s];
-                        mz[s] = fmaf(mz[s] - m0[s], e1, m0[s]);
-                    }
-                }
-                if (type == REC_ADC) {
-                    const int L = min(max(R.count, 1), kMaxAdcRun);
-                    const int64_t k0 = R.k0;
-                    if (k0 + L > red_base + kRed32) flush();
-                    if (L == 1) {
-                        float sr = 0.f, si = 0.f;
-#pragma unroll
-                        for (int s = 0; s < S; ++s) {
-                            sr += er[s];
-                            si += ei[s];
-                        }
-                        sr = warp_sum(sr);
-                        si = warp_sum(si);
-                        if (lane == 0) red_slot(red_buf, warp, static_cast<int>(k0 - red_base)) = make_float2(sr, si);
-                    } else {
-                        const float dkx = R.a[8], dky = R.a[9], dkz = R.a[10], dtau = R.a[11];
-                        if (!(dkx == key0 && dky == key1 && dkz == key2 && dtau == key3)) {
-#pragma unroll
-                            for (int s = 0; s < S; ++s) {
-                                const float th1 = -fmaf(dkx, xh[s], fmaf(dky, yh[s], fmaf(dkz, zh[s], fh[s] * dtau)));
-                                float sn, cs;
-                                sincospi_f32(2.f * th1, &sn, &cs);
-                                const float mag = exp2f(-dtau * r2[s]);
-                                zr[s] = mag * cs;
-                                zi[s] = mag * sn;
-                            }
-                            key0 = dkx;
-                            key1 = dky;
-                            key2 = dkz;
-                            key3 = dtau;
-                        }
-                        // spins in packed pairs: m' = m z, acc += m
-                        f32x2 pr[NP], pi_[NP], qr[NP], qi[NP], qn[NP];
-#pragma unroll
-                        for (int p = 0; p < NP; ++p) {
-                            pr[p] = pk(er[2 * p], er[2 * p + 1]);
-                            pi_[p] = pk(ei[2 * p], ei[2 * p + 1]);
-                            qr[p] = pk(zr[2 * p], zr[2 * p + 1]);
-                            qi[p] = pk(zi[2 * p], zi[2 * p + 1]);
-                            qn[p] = pk(-zi[2 * p], -zi[2 * p + 1]);
-                        }
-                        for (int c = 0; c < L; c += kV) {
-                            float ar[kV], ai[kV];
-#pragma unroll
-                            for (int v = 0; v < kV; ++v) {
-                                f32x2 sr2 = pr[0], si2 = pi_[0];
-#pragma unroll
-                                for (int p = 1; p < NP; ++p) {
-                                    sr2 = add2(sr2, pr[p]);
-                                    si2 = add2(si2, pi_[p]);
-                                }
-                                ar[v] = lo_of(sr2) + hi_of(sr2);
-                                ai[v] = lo_of(si2) + hi_of(si2);
-#pragma unroll
-                                for (int p = 0; p < NP; ++p) {
-                                    const f32x2 nr2 = fma2(pr[p], qr[p], mul2(pi_[p], qn[p]));
-                                    pi_[p] = fma2(pr[p], qi[p], mul2(pi_[p], qr[p]));
-                                    pr[p] = nr2;
-                                }
-                            }
-                            const float sr = reduce_scatter8(ar, lane);
-                            const float si = reduce_scatter8(ai, lane);
-                            const int vl = (lane >> 2) & 7;
-                            if ((lane & 3) == 0 && c + vl < L)
-                                red_slot(red_buf, warp, static_cast<int>(k0 + c + vl - red_base)) = make_float2(sr, si);
-                        }
-                    }
-                    red_end = k0 + L;
-                }
+                sp.exact(R, true, A.p32, np, A.used, er, ei);
+            } else if (type == REC_ADC) {
+                const int L = min(max(R.count & kCountMask, 1), kMaxAdcRun);
+                const int64_t k0 = R.k0;
+                if (k0 + L > red_base + kRed32) flush();
+                float er[S], ei[S];
+                sp.exact(R, false, A.p32, np, A.used, er, ei);
+                const int off = static_cast<int>(k0 - red_base);
+                sp.adc(R, L, er, ei, lane,
+                       [&](int i, float sr, float si) { red_slot(red_buf, warp, off + i) = make_float2(sr, si); });
+                red_end = k0 + L;
             }
         }
         __syncthreads();  // everyone is done with tile buffer b
         if (tid == 0 && t + 2 < n_tiles) {
             fence_proxy_async_smem();
-            const int64_t nr2 = min(static_cast<int64_t>(kTile), A.n_rec - (t + 2) * kTile);
-            tma_load_1d(smem_u32(&s_rec[b][0]), grec + (t + 2) * kTile,
-                        static_cast<uint32_t>(nr2 * sizeof(Rec32)), bar[b]);
+            issue_tile(s_rec, bar, grec, A.n_rec, t + 2, t + 2);
         }
     }
     if (red_end > red_base) flush();
+}
+
+// ---------------------------------------------------------------------------
+// K3: grouped ("dictionary") kernel, persistent.
+//
+// Work item = up to 32 * S spins of one group (a group is split into nearly
+// equal items). One warp steps one item through the whole record stream and
+// writes the item's signal as its own FP32 partial row; K2 then sums each
+// group's item rows in a fixed order. CTAs take batches of (warps per CTA)
+// items from a global counter; the item order is longest first, so the last
+// batches are the shortest and the SMs finish together. All warps of a CTA
+// walk the record stream together (shared TMA tiles).
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_kernel(const __grid_constant__ ItemArgs A) {
+    __shared__ __align__(128) Rec32 s_rec[2][kTile];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ int64_t s_batch;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int64_t np = A.n_pad;
+    const uint32_t bar[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
+    const Rec32* __restrict__ grec = static_cast<const Rec32*>(A.rec);
+    const int64_t n_tiles = (A.n_rec + kTile - 1) / kTile;
+    if (tid == 0) {
+        mbar_init(bar[0], 1);
+        mbar_init(bar[1], 1);
+        fence_mbar_init();
+    }
+    uint64_t g0 = 0;  // tiles this CTA has consumed in earlier batches
+    for (;;) {
+        if (tid == 0) s_batch = atomicAdd(A.counter, 1);
+        __syncthreads();
+        const int64_t batch = s_batch;
+        __syncthreads();
+        if (batch * nwarps >= A.n_items) break;
+        const int64_t oi = batch * nwarps + warp;
+        int64_t item = -1, ib = 0, ie = 0;
+        if (oi < A.n_items) {
+            item = A.order[oi];
+            ib = A.item_begin[item];
+            ie = A.item_begin[item + 1];
+        }
+        Spins<S> sp;
+        sp.load(A.p32, np, ib + lane, 32, ie);
+        float2* __restrict__ row = static_cast<float2*>(A.partial) + (item >= 0 ? item : 0) * A.n_adc;
+        const bool has_row = item >= 0;
+        if (tid == 0) {
+            for (int64_t t = 0; t < 2 && t < n_tiles; ++t) issue_tile(s_rec, bar, grec, A.n_rec, t, g0 + t);
+        }
+        for (int64_t t = 0; t < n_tiles; ++t) {
+            const uint64_t g = g0 + t;
+            const int b = static_cast<int>(g & 1);
+            const bool ok = mbar_wait_bounded(bar[b], static_cast<uint32_t>((g >> 1) & 1));
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicOr(A.status, 1);
+                    mbar_wait_bounded(bar[b], static_cast<uint32_t>((g >> 1) & 1));
+                    if (t + 1 < n_tiles) mbar_wait_bounded(bar[b ^ 1], static_cast<uint32_t>(((g + 1) >> 1) & 1));
+                }
+                return;
+            }
+            const int nr = static_cast<int>(min(static_cast<int64_t>(kTile), A.n_rec - t * kTile));
+            for (int r = 0; r < nr; ++r) {
+                const Rec32& R = s_rec[b][r];
+                const int type = R.type;
+                if (type == REC_RF) {
+                    sp.rf(R, A.ext);
+                } else if (type == REC_PREC) {
+                    float er[S], ei[S];
+                    sp.exact(R, true, A.p32, np, A.used, er, ei);
+                } else if (type == REC_ADC) {
+                    const int L = min(max(R.count & kCountMask, 1), kMaxAdcRun);
+                    const int64_t k0 = R.k0;
+                    float er[S], ei[S];
+                    sp.exact(R, false, A.p32, np, A.used, er, ei);
+                    sp.adc(R, L, er, ei, lane, [&](int i, float sr, float si) {
+                        if (has_row) row[k0 + i] = make_float2(sr, si);
+                    });
+                }
+            }
+            __syncthreads();  // everyone is done with tile buffer b
+            if (tid == 0 && t + 2 < n_tiles) {
+                fence_proxy_async_smem();
+                issue_tile(s_rec, bar, grec, A.n_rec, t + 2, g + 2);
+            }
+        }
+        g0 += static_cast<uint64_t>(n_tiles);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -706,9 +889,31 @@ cudaError_t launch_fp32(const BlochArgs& a, const BlochLaunch& L, cudaStream_t s
     return cudaGetLastError();
 }
 
+template <int S>
+cudaError_t occupancy_items(int* n, int block) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, bloch_items_kernel<S>, block, 0);
+}
+
 }  // namespace
 
 int bloch_max_block() { return kMaxBlock; }
+
+int items_ctas_per_sm(int spins_per_thread, int block) {
+    int n = 0;
+    cudaError_t e = spins_per_thread == 2 ? occupancy_items<2>(&n, block) : occupancy_items<4>(&n, block);
+    return e == cudaSuccess ? n : -1;
+}
+
+int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, void* stream) {
+    if (block <= 0 || block > kMaxBlock || block % 32 != 0 || grid <= 0) return cudaErrorInvalidValue;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (spins_per_thread) {
+        case 2: bloch_items_kernel<2><<<grid, block, 0, st>>>(a); break;
+        case 4: bloch_items_kernel<4><<<grid, block, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 int bloch_ctas_per_sm(bool fp64, int spins_per_thread, int block) {
     int n = 0;

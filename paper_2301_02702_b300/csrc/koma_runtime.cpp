@@ -37,7 +37,7 @@ struct koma_ctx {
     std::string err;
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
-    int* d_status = nullptr;
+    int* d_status = nullptr;  // [0] device status flags, [1] batch counter of the grouped kernel
     cudaStream_t own_stream = nullptr;
     koma_launch_info last{};
     int64_t live_objects = 0;
@@ -62,6 +62,19 @@ struct koma_phantom {
     size_t table_bytes = 0;
     // max |x|, |y|, |z| (m) and |df| (Hz) over the spins
     double max_abs[4] = {0, 0, 0, 0};
+    // work items of the grouped kernel, built for items_s spins per thread:
+    // d_items [n_items + 1] first spin of each item, then (same allocation)
+    // d_order [n_items] longest first, d_group_item [n_groups + 1]
+    int items_s = 0;
+    int64_t n_items = 0;
+    int64_t* d_items = nullptr;
+    int32_t* d_order = nullptr;
+    int32_t* d_group_item = nullptr;
+    size_t items_bytes = 0;
+    // configuration chosen by koma_tune for one sequence
+    const koma_sequence* tuned_seq = nullptr;
+    int64_t tuned_n_rec = -1;
+    int tuned_s = 0, tuned_block = 0;
 };
 
 struct koma_sequence {
@@ -160,8 +173,8 @@ extern "C" koma_status koma_init(int device, size_t mem_budget_bytes, koma_ctx**
     ctx->budget = mem_budget_bytes;
     DeviceGuard g(device);
     if (!g.ok || cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaMalloc(reinterpret_cast<void**>(&ctx->d_status), sizeof(int)) != cudaSuccess ||
-        cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&ctx->d_status), 2 * sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, 2 * sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         if (ctx->d_status) cudaFree(ctx->d_status);
@@ -295,6 +308,7 @@ extern "C" koma_status koma_phantom_free(koma_phantom* ph) {
     dev_free(ctx, ph->p32, static_cast<size_t>(koma::P32_N * ph->n_pad) * sizeof(float));
     dev_free(ctx, ph->p64, static_cast<size_t>(koma::P64_N * ph->n_pad) * sizeof(double));
     if (ph->d_cta_begin) dev_free(ctx, ph->d_cta_begin, ph->table_bytes);
+    if (ph->d_items) dev_free(ctx, ph->d_items, ph->items_bytes);
     ctx->live_objects--;
     delete ph;
     return KOMA_OK;
@@ -324,7 +338,7 @@ struct RecordBuilder {
         koma::Rec32 a{};
         koma::Rec64 b{};
         a.type = b.type = koma::REC_ADC;
-        a.count = b.count = run_count;
+        b.count = run_count;
         a.k0 = b.k0 = run_k0;
         for (int d = 0; d < 3; ++d) {
             split(run_k[d], &a.a[2 * d], &a.a[2 * d + 1]);
@@ -336,6 +350,7 @@ struct RecordBuilder {
         b.a[3] = run_tau;
         a.a[11] = static_cast<float>(run_count > 1 ? run_dtau : 0.0);
         b.a[7] = run_count > 1 ? run_dtau : 0.0;
+        a.count = run_count | (term_bits(a) << koma::kTermShift);
         r32.push_back(a);
         r64.push_back(b);
         ++n_runs;
@@ -343,6 +358,42 @@ struct RecordBuilder {
     }
 
     static bool close_to(double a, double b, double tol) { return std::fabs(a - b) <= tol; }
+
+    // which phase terms of a PREC/ADC record are nonzero (bit 0..2: K x, y,
+    // z; bit 3: tau), from its FP32 hi/lo values
+    static int term_bits(const koma::Rec32& a) {
+        int m = 0;
+        for (int d = 0; d < 4; ++d)
+            if (a.a[2 * d] != 0.f || a.a[2 * d + 1] != 0.f) m |= 1 << d;
+        return m;
+    }
+
+    // Give the first record of every run of consecutive RF records the run's
+    // length and maxima (the kernel chooses its rotation path once per run).
+    void mark_rf_runs() {
+        size_t i = 0;
+        while (i < r32.size()) {
+            if (r32[i].type != koma::REC_RF) {
+                ++i;
+                continue;
+            }
+            size_t j = i;
+            float mb = 0.f, mg[3] = {0.f, 0.f, 0.f}, mdt = 0.f;
+            while (j < r32.size() && r32[j].type == koma::REC_RF) {
+                const koma::Rec32& q = r32[j];
+                mb = std::max(mb, std::sqrt(q.a[3] * q.a[3] + q.a[4] * q.a[4]));
+                for (int d = 0; d < 3; ++d) mg[d] = std::max(mg[d], std::fabs(q.a[d]));
+                mdt = std::max(mdt, q.a[6]);
+                ++j;
+            }
+            koma::Rec32& h = r32[i];
+            h.count = static_cast<int32_t>(std::min<size_t>(j - i, 0x7fffffff));
+            h.a[7] = mb * (1.f + 1e-6f);
+            for (int d = 0; d < 3; ++d) h.a[8 + d] = mg[d];
+            h.a[11] = mdt;
+            i = j;
+        }
+    }
 
     // A sample at (K, tau) relative to t_ref.
     void sample(const double k[3], double tau) {
@@ -425,6 +476,7 @@ koma_status build_records(int64_t n_steps, const double* dt, const double* gx, c
                 }
                 split(tau, &a.a[6], &a.a[7]);
                 b.a[3] = tau;
+                a.count = RecordBuilder::term_bits(a) << koma::kTermShift;
                 rb.r32.push_back(a);
                 rb.r64.push_back(b);
                 ++rb.n_mat;
@@ -433,15 +485,16 @@ koma_status build_records(int64_t n_steps, const double* dt, const double* gx, c
             koma::Rec64 b{};
             a.type = b.type = koma::REC_RF;
             const double s = kGammaBar * dt[n];  // turns per tesla
+            // FP32 record: half-angle vector pi s B (radians); FP64: s B (turns)
             for (int d = 0; d < 3; ++d) {
-                a.a[d] = static_cast<float>(s * gm[d]);
+                a.a[d] = static_cast<float>(kPi * s * gm[d]);
                 b.a[d] = s * gm[d];
             }
             const double bx = s * b1_re[n], by = s * b1_im[n];
-            a.a[3] = static_cast<float>(bx);
-            a.a[4] = static_cast<float>(by);
-            // |a_xy|^2 of the FP32 values; kept above zero so the kernel's
-            // rsqrt stays finite for a vanishing field
+            a.a[3] = static_cast<float>(kPi * bx);
+            a.a[4] = static_cast<float>(kPi * by);
+            // |theta_xy|^2 of the FP32 values; kept above zero so the general
+            // path's rsqrt stays finite for a vanishing field
             a.a[5] = std::max(a.a[3] * a.a[3] + a.a[4] * a.a[4], std::numeric_limits<float>::min());
             a.a[6] = static_cast<float>(dt[n]);
             b.a[3] = bx;
@@ -459,6 +512,7 @@ koma_status build_records(int64_t n_steps, const double* dt, const double* gx, c
         if (adc[n + 1]) rb.sample(K, tau);
     }
     rb.close_run();
+    rb.mark_rf_runs();
     info.n_adc = rb.n_adc;
     info.n_records = static_cast<int64_t>(rb.r32.size());
     info.n_adc_runs = rb.n_runs;
@@ -560,20 +614,139 @@ extern "C" koma_status koma_sequence_free(koma_sequence* seq) {
 // ---------------------------------------------------------------------------
 namespace {
 
-// True when every RF step rotates every spin of `ph` by at most ~1/4 turn
-// (|a| <= |B1|gammabar dt + sum_d |Gbar_d| gammabar dt |x_d| + |df| dt), so the
-// kernel's sine needs no range reduction. 0.24 leaves room for FP32 rounding.
-bool rf_small_angles(const koma_phantom* ph, const koma_sequence* seq) {
-    double bound = seq->rf_b1 + seq->rf_dt * ph->max_abs[3];
-    for (int d = 0; d < 3; ++d) bound += seq->rf_g[d] * ph->max_abs[d];
-    return bound <= 0.24;
+// Phantom extents as FP32 upper bounds (the kernels bound each RF step's
+// rotation with them).
+void phantom_ext(const koma_phantom* ph, float (&ext)[4], int* used) {
+    *used = 0;
+    for (int d = 0; d < 4; ++d) {
+        ext[d] = static_cast<float>(ph->max_abs[d] * (1.0 + 1e-6));
+        if (ph->max_abs[d] > 0) *used |= 1 << d;
+    }
+}
+
+// Split every group into work items of 32 S spins (one warp each, every lane
+// slot full) plus one remainder item, and order them longest first, so a
+// batch of consecutive items has similar sizes. Cached on the phantom per S.
+koma_status ensure_items(koma_ctx* ctx, koma_phantom* ph, int S) {
+    if (ph->items_s == S && ph->d_items) return KOMA_OK;
+    const int64_t cap = 32LL * S;
+    std::vector<int64_t> begin;
+    std::vector<int32_t> gi(static_cast<size_t>(ph->n_groups + 1), 0);
+    for (int64_t g = 0; g < ph->n_groups; ++g) {
+        gi[g] = static_cast<int32_t>(begin.size());
+        const int64_t lo = ph->group_offsets[g], n_g = ph->group_offsets[g + 1] - lo;
+        for (int64_t off = 0; off < n_g; off += cap) begin.push_back(lo + off);
+        if (begin.size() > static_cast<size_t>(std::numeric_limits<int32_t>::max() - 1))
+            return fail(ctx, KOMA_E_INVALID, "simulate: grouped phantom needs too many work items");
+    }
+    gi[ph->n_groups] = static_cast<int32_t>(begin.size());
+    const int64_t n_items = static_cast<int64_t>(begin.size());
+    begin.push_back(ph->n);
+    std::vector<int32_t> order(static_cast<size_t>(n_items));
+    for (int64_t i = 0; i < n_items; ++i) order[i] = static_cast<int32_t>(i);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return begin[a + 1] - begin[a] > begin[b + 1] - begin[b];
+    });
+    if (ph->d_items) dev_free(ctx, ph->d_items, ph->items_bytes);
+    ph->d_items = nullptr;
+    ph->items_s = 0;
+    const size_t b_items = begin.size() * sizeof(int64_t), b_order = order.size() * sizeof(int32_t),
+                 b_gi = gi.size() * sizeof(int32_t);
+    koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&ph->d_items), b_items + b_order + b_gi,
+                               "simulate: work-item table");
+    if (st != KOMA_OK) return st;
+    ph->items_bytes = b_items + b_order + b_gi;
+    ph->d_order = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ph->d_items) + b_items);
+    ph->d_group_item = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ph->d_items) + b_items + b_order);
+    cudaError_t e = cudaMemcpy(ph->d_items, begin.data(), b_items, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && b_order) e = cudaMemcpy(ph->d_order, order.data(), b_order, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ph->d_group_item, gi.data(), b_gi, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "simulate: work-item table copy");
+    ph->n_items = n_items;
+    ph->items_s = S;
+    return KOMA_OK;
+}
+
+// The grouped kernel suits many small groups (dictionaries); a few large
+// groups run faster through the CTA-split path.
+bool use_items_kernel(const koma_phantom* ph) {
+    return ph->n_groups > 1 && ph->n <= 512 * ph->n_groups;
+}
+
+koma_status grow_scratch(koma_ctx* ctx, size_t need, cudaStream_t st) {
+    if (need <= ctx->scratch_bytes) return KOMA_OK;
+    // the stream may still use the old buffer
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "simulate: sync before scratch growth");
+    if (ctx->scratch) dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    koma_status s = dev_alloc(ctx, &ctx->scratch, need, "simulate: partial-sum scratch");
+    if (s != KOMA_OK) return s;
+    ctx->scratch_bytes = need;
+    return KOMA_OK;
+}
+
+// Grouped kernel (K3) + per-group reduction (K2).
+koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence* seq, double* sig_dev,
+                           cudaStream_t st, int S, int block) {
+    koma_status rc = ensure_items(ctx, ph, S);
+    if (rc != KOMA_OK) return rc;
+    const int64_t n_adc = seq->info.n_adc;
+    const int per_sm = std::max(1, koma::items_ctas_per_sm(S, block));
+    const int64_t batches = (ph->n_items + block / 32 - 1) / (block / 32);
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(batches,
+                                                         static_cast<int64_t>(ctx->sm_count) * per_sm)));
+    rc = grow_scratch(ctx, static_cast<size_t>(ph->n_items) * static_cast<size_t>(n_adc) * 2 * sizeof(float), st);
+    if (rc != KOMA_OK) return rc;
+    koma::ItemArgs A;
+    A.p32 = ph->p32;
+    A.p64 = ph->p64;
+    A.n_pad = ph->n_pad;
+    A.item_begin = ph->d_items;
+    A.order = ph->d_order;
+    A.n_items = ph->n_items;
+    A.counter = ctx->d_status + 1;
+    A.rec = seq->r32;
+    A.n_rec = seq->info.n_records;
+    A.partial = ctx->scratch;
+    A.n_adc = n_adc;
+    A.status = ctx->d_status;
+    phantom_ext(ph, A.ext, &A.used);
+    cudaError_t ce = cudaMemsetAsync(A.counter, 0, sizeof(int), st);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "simulate: counter reset");
+    if (ctx->timing) cudaEventRecord(ctx->ev[0], st);
+    int e = koma::launch_items(A, grid, block, S, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: grouped kernel launch");
+    if (ctx->timing) cudaEventRecord(ctx->ev[1], st);
+    koma::ReduceArgs R;
+    R.partial = ctx->scratch;
+    R.grid = static_cast<int>(ph->n_items);
+    R.group_cta = ph->d_group_item;
+    R.n_groups = ph->n_groups;
+    R.n_adc = n_adc;
+    R.sig = sig_dev;
+    e = koma::launch_reduce(R, false, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: reduction launch");
+    if (ctx->timing) {
+        cudaEventRecord(ctx->ev[2], st);
+        ctx->timing_recorded = true;
+    }
+    ctx->last.kernels = 2;
+    ctx->last.grid = grid;
+    ctx->last.block = block;
+    ctx->last.spins_per_thread = S;
+    ctx->last.spins_per_cta = 32LL * S * (block / 32);
+    ctx->last.n_records = seq->info.n_records;
+    ctx->last.partial_bytes = static_cast<int64_t>(ph->n_items * n_adc * 8);
+    return KOMA_OK;
 }
 
 // Launch shape: the grid is a whole number of waves of (SMs x resident CTAs)
 // and every CTA gets the same number of spins, so no SM idles on a tail.
-koma::BlochLaunch choose_launch(const koma_ctx* ctx, int64_t n, bool fp64) {
+koma::BlochLaunch choose_launch(const koma_ctx* ctx, int64_t n, bool fp64, int s_fp32 = 4) {
     koma::BlochLaunch L;
-    const int S = fp64 ? 1 : 4;
+    const int S = fp64 ? 1 : s_fp32;
     const int max_block = koma::bloch_max_block();
     const int per_sm = std::max(1, koma::bloch_ctas_per_sm(fp64, S, max_block));
     const int64_t slots = static_cast<int64_t>(ctx->sm_count) * per_sm;
@@ -616,7 +789,13 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
         return e == cudaSuccess ? KOMA_OK : cuda_fail(ctx, e, "simulate: memset");
     }
 
-    koma::BlochLaunch L = choose_launch(ctx, ph->n, fp64);
+    if (!fp64 && use_items_kernel(ph)) {
+        const bool tuned = ph->tuned_seq == seq && ph->tuned_n_rec == seq->info.n_records;
+        ctx->timing_recorded = false;
+        return simulate_items(ctx, ph, seq, sig_dev, st, tuned ? ph->tuned_s : 4, tuned ? ph->tuned_block : 256);
+    }
+    const bool tuned_k1 = ph->tuned_seq == seq && ph->tuned_n_rec == seq->info.n_records && ph->tuned_s > 0;
+    koma::BlochLaunch L = choose_launch(ctx, ph->n, fp64, tuned_k1 ? ph->tuned_s : 4);
     if (ph->n_groups > 1) {
         // size CTAs for the largest group (groups never share a CTA)
         int64_t gmax = 1;
@@ -643,7 +822,7 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     A.n_rec = seq->info.n_records;
     A.n_adc = n_adc;
     A.status = ctx->d_status;
-    A.rf_small = rf_small_angles(ph, seq) ? 1 : 0;
+    phantom_ext(ph, A.ext, &A.used);
     A.spins_per_cta = L.spins_per_cta;
     koma::ReduceArgs R;
     R.n_adc = n_adc;
@@ -689,16 +868,9 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
 
     const size_t elem = fp64 ? 2 * sizeof(double) : 2 * sizeof(float);
     const size_t need = static_cast<size_t>(L.grid) * static_cast<size_t>(n_adc) * elem;
-    if (need > ctx->scratch_bytes) {
-        // the stream may still use the old buffer
-        cudaError_t e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "simulate: sync before scratch growth");
-        if (ctx->scratch) dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
-        ctx->scratch = nullptr;
-        ctx->scratch_bytes = 0;
-        koma_status s = dev_alloc(ctx, &ctx->scratch, need, "simulate: partial-sum scratch");
+    {
+        koma_status s = grow_scratch(ctx, need, st);
         if (s != KOMA_OK) return s;
-        ctx->scratch_bytes = need;
     }
     A.partial = ctx->scratch;
     R.partial = ctx->scratch;
@@ -776,7 +948,7 @@ extern "C" koma_status koma_simulate_static(const koma_phantom* ph, const koma_s
     A.n_rec = seq->info.n_records;
     A.n_adc = n_adc;
     A.status = ctx->d_status;
-    A.rf_small = rf_small_angles(ph, seq) ? 1 : 0;
+    phantom_ext(ph, A.ext, &A.used);
     A.spins_per_cta = L.spins_per_cta;
     A.partial = scratch;  // every (CTA, sample) entry is written before K2 reads it
     koma::ReduceArgs R;
@@ -790,6 +962,70 @@ extern "C" koma_status koma_simulate_static(const koma_phantom* ph, const koma_s
     e = koma::launch_reduce(R, false, stream);
     if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate_static: reduction launch");
     return KOMA_OK;
+}
+
+extern "C" koma_status koma_tune(koma_ctx* ctx, const koma_phantom* ph_c, const koma_sequence* seq,
+                                 double* sig_dev, void* stream, koma_launch_info* chosen) {
+    if (!ctx) return KOMA_E_INVALID;
+    koma_phantom* ph = const_cast<koma_phantom*>(ph_c);
+    if (!ph || !seq) return fail(ctx, KOMA_E_INVALID, "tune: NULL phantom or sequence");
+    if (ph->ctx != ctx || seq->ctx != ctx) return fail(ctx, KOMA_E_INVALID, "tune: objects of another context");
+    if (seq->info.n_adc > 0 && !sig_dev) return fail(ctx, KOMA_E_INVALID, "tune: sig_dev is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    struct Cand {
+        int s, block;
+    };
+    std::vector<Cand> cands;
+    const bool items = use_items_kernel(ph);
+    if (items)
+        cands = {{2, 128}, {2, 256}, {4, 128}, {4, 256}};
+    else
+        cands = {{2, 0}, {4, 0}};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(ctx, KOMA_E_CUDA, "tune: event creation");
+    float best = -1.f;
+    Cand pick = cands.back();
+    koma_status rc = KOMA_OK;
+    for (size_t i = 0; i < cands.size() && rc == KOMA_OK; ++i) {
+        ph->tuned_seq = seq;
+        ph->tuned_n_rec = seq->info.n_records;
+        ph->tuned_s = cands[i].s;
+        ph->tuned_block = cands[i].block;
+        // one untimed run (tables, scratch), one timed
+        for (int rep = 0; rep < 2 && rc == KOMA_OK; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, st);
+            rc = koma_simulate(ctx, ph, seq, KOMA_FP32_SPLITPHASE, sig_dev, stream);
+            if (rep == 1) cudaEventRecord(e1, st);
+        }
+        if (rc != KOMA_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = fail(ctx, KOMA_E_CUDA, "tune: event wait");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best < 0.f || ms < best) {
+            best = ms;
+            pick = cands[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != KOMA_OK) {
+        ph->tuned_seq = nullptr;
+        return rc;
+    }
+    ph->tuned_seq = seq;
+    ph->tuned_n_rec = seq->info.n_records;
+    ph->tuned_s = pick.s;
+    ph->tuned_block = pick.block;
+    if (chosen) {
+        rc = koma_simulate(ctx, ph, seq, KOMA_FP32_SPLITPHASE, sig_dev, stream);
+        *chosen = ctx->last;
+    }
+    return rc;
 }
 
 extern "C" koma_status koma_sync(koma_ctx* ctx, void* stream) {

@@ -31,7 +31,7 @@ EXPORTS = (
     "koma_phantom_upload", "koma_phantom_n_spins", "koma_phantom_n_groups", "koma_phantom_free",
     "koma_sequence_upload", "koma_sequence_n_adc", "koma_sequence_n_steps", "koma_sequence_get_info",
     "koma_sequence_free", "koma_sequence_plan", "koma_simulate", "koma_sync", "koma_set_timing",
-    "koma_get_timing", "koma_get_launch_info", "koma_simulate_host", "koma_simulate_static",
+    "koma_get_timing", "koma_get_launch_info", "koma_simulate_host", "koma_simulate_static", "koma_tune",
 )
 
 
@@ -127,6 +127,8 @@ def load(path: Optional[str] = None):
         lib.koma_get_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
         lib.koma_get_launch_info.restype = st
         lib.koma_get_launch_info.argtypes = [_vp, ctypes.POINTER(LaunchInfo)]
+        lib.koma_tune.restype = st
+        lib.koma_tune.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(LaunchInfo)]
         lib.koma_simulate_static.restype = st
         lib.koma_simulate_static.argtypes = [_vp, _vp, _vp, _vp]
         lib.koma_simulate_host.restype = st
@@ -274,6 +276,15 @@ def koma_simulate(ctx, ph, seq, precision: int, sig_dev_ptr: int, stream_ptr: in
     _check(ctx, rc, "koma_simulate")
 
 
+def koma_tune(ctx, ph, seq, sig_dev_ptr: int, stream_ptr: int) -> dict:
+    """Autotune the FP32 launch for (ph, seq); returns the chosen launch."""
+    info = LaunchInfo()
+    rc = load().koma_tune(ctx, ph, seq, ctypes.c_void_p(int(sig_dev_ptr)), ctypes.c_void_p(int(stream_ptr)),
+                          ctypes.byref(info))
+    _check(ctx, rc, "koma_tune")
+    return info.as_dict()
+
+
 def koma_simulate_static(ctx, ph, seq, sig_dev_ptr: int, stream_ptr: int):
     """Allocation-free simulation (FP32 path): partial sums in the library's
     static device array. ``ctx`` is only used to fetch the error message."""
@@ -361,6 +372,13 @@ class Simulator:
         import torch
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
         koma_sync(self.ctx, st.cuda_stream)
+
+    def tune(self, ph, seq, stream=None) -> dict:
+        import torch
+        n_adc = koma_sequence_n_adc(seq)
+        out = torch.empty((koma_phantom_n_groups(ph), n_adc), dtype=torch.complex128, device=f"cuda:{self.device}")
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return koma_tune(self.ctx, ph, seq, out.data_ptr() if out.numel() else 0, st.cuda_stream)
 
     def launch_info(self) -> dict:
         return koma_get_launch_info(self.ctx)

@@ -389,6 +389,58 @@ def spin_echo(n_shots: int = 64, n_read: int = 256, fov: float = 0.256, te: floa
 
 
 # --------------------------------------------------------------------------
+# Workload 4: MRF dictionary (grouped isochromats), FISP train
+# --------------------------------------------------------------------------
+
+def mrf_dictionary_phantom(n_t1: int = 250, n_t2: int = 200, n_iso=(50, 400), voxel: float = 1e-3,
+                           t1_range=(0.3, 2.5), t2_range=(0.04, 0.35), seed: int = 1004) -> Phantom:
+    """One group of isochromats per (T1, T2) dictionary entry on a log grid.
+    Group g has n_e ~ U{n_iso} spins at z_k = L (k + 1/2) / n_e - L/2 inside a
+    voxel of length L (PD = 1 / n_e each, so a group's signal is the voxel
+    average scaled to M0 = 1); x = y = 0, no off-resonance."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t1s = np.geomspace(t1_range[0], t1_range[1], n_t1)
+    t2s = np.geomspace(t2_range[0], t2_range[1], n_t2)
+    T1, T2 = np.meshgrid(t1s, t2s, indexing="ij")
+    T1, T2 = T1.ravel(), T2.ravel()
+    counts = rng.integers(n_iso[0], n_iso[1] + 1, size=T1.size)
+    offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    n = int(offs[-1])
+    z = np.empty(n)
+    pd = np.empty(n)
+    for g, c in enumerate(counts):
+        k = np.arange(c)
+        z[offs[g]:offs[g + 1]] = voxel * (k + 0.5) / c - voxel / 2
+        pd[offs[g]:offs[g + 1]] = 1.0 / c
+    return Phantom(x=np.zeros(n), y=np.zeros(n), z=z, pd=pd, t1=np.repeat(T1, counts),
+                   t2=np.repeat(T2, counts), dw=np.zeros(n), group_offsets=offs)
+
+
+def mrf_fisp(n_tr: int = 1000, voxel: float = 1e-3, te: float = 3e-3, rf_dur: float = 100e-6,
+             ti: float = 50e-3, seed: int = 1014) -> Sequence:
+    """FISP fingerprinting train: an inversion (hard 180 deg) and TI, then
+    n_tr TRs of a hard pulse with flip FA_j = 37.5 - 32.5 cos(2 pi j / 250)
+    degrees (5..70), one ADC sample at TE, an unbalanced z gradient lobe whose
+    moment dephases one full turn across the voxel, free precession to the
+    end of the TR (TR_j ~ U[10, 15] ms)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    trs = rng.uniform(10e-3, 15e-3, n_tr)
+    tg = 200e-6
+    amp = (1.0 / voxel) / (GAMMA_BAR * 2 * tg)  # trapezoid of 1 ramp + 1 flat + 1 ramp step
+    b = SequenceBuilder()
+    b.steps(1, rf_dur, b1=hard_pulse_b1(np.pi, rf_dur))
+    b.steps(1, ti - rf_dur)
+    for j in range(n_tr):
+        t0 = b.t
+        fa = np.deg2rad(37.5 - 32.5 * np.cos(2 * np.pi * j / 250.0))
+        b.steps(1, rf_dur, b1=hard_pulse_b1(fa, rf_dur))
+        b.steps(1, te - rf_dur / 2, adc=True)            # TE from the pulse centre
+        b.steps(1, tg, [0, 0, amp]).steps(1, tg).steps(1, tg, [0, 0, 0])
+        b.idle_until(t0 + trs[j])
+    return b.build()
+
+
+# --------------------------------------------------------------------------
 # named workloads (sizes of the benchmark configurations)
 # --------------------------------------------------------------------------
 
@@ -410,10 +462,14 @@ def workload(name: str, scale: str = "full"):
         if full:
             return ellipsoid_phantom(), spin_echo()
         return ellipsoid_phantom(n=12), spin_echo(n_shots=4, n_read=32, rf_steps=100)
+    if name == "mrf":
+        if full:
+            return mrf_dictionary_phantom(), mrf_fisp()
+        return mrf_dictionary_phantom(n_t1=10, n_t2=8), mrf_fisp(n_tr=100)
     raise KeyError(name)
 
 
-WORKLOADS = ("gre32", "epi512", "se128")
+WORKLOADS = ("gre32", "epi512", "se128", "mrf")
 
 
 def random_spins(n: int, seed: int, extent: float = 0.1, dim: int = 3,

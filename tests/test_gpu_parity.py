@@ -195,3 +195,54 @@ def test_abi_errors(sim):
         koma.koma_sequence_free(hs)
     finally:
         other.close()
+
+
+def test_mrf_dictionary_full_size_sampled_groups(sim):
+    """The 50,000-entry dictionary (11.3 M isochromats) in one launch of the
+    work-item kernel; 500 random groups checked against the oracle (groups are
+    independent outputs, so each sampled row is compared exactly)."""
+    from paper_2301_02702_b300.workloads import Phantom as Ph
+    ph, seq = workload("mrf", "full")
+    got = gpu_signal(sim, ph, seq)
+    assert got.shape == (50000, seq.n_adc)
+    rng = np.random.default_rng(11)
+    groups = np.sort(rng.choice(ph.n_groups, 500, replace=False))
+    idx = np.concatenate([np.arange(ph.group_offsets[g], ph.group_offsets[g + 1]) for g in groups])
+    offs = np.concatenate([[0], np.cumsum(np.diff(ph.group_offsets)[groups])])
+    sub = Ph(ph.x[idx], ph.y[idx], ph.z[idx], ph.pd[idx], ph.t1[idx], ph.t2[idx], ph.dw[idx], group_offsets=offs)
+    ref = oracle.simulate(sub, seq)
+    err = np.max(np.abs(got[groups] - ref), axis=1) / np.max(np.abs(ref), axis=1)
+    assert np.max(err) < TOL32, np.max(err)
+
+
+def test_grouped_kernel_deterministic_and_tuned(sim):
+    import torch
+    ph, seq = workload("mrf", "small")
+    hp = sim.upload_phantom(ph)
+    hs = sim.upload_sequence(seq)
+    try:
+        a = sim.simulate(hp, hs).cpu().numpy()
+        b = sim.simulate(hp, hs).cpu().numpy()
+        assert np.array_equal(a, b)
+        choice = sim.tune(hp, hs)
+        assert choice["spins_per_thread"] in (2, 4) and choice["block"] in (128, 256)
+        c = sim.simulate(hp, hs).cpu().numpy()
+        sim.sync()
+        assert sim.launch_info()["spins_per_thread"] == choice["spins_per_thread"]
+        assert rel_err(c, a) < TOL32
+        ref = oracle.simulate(ph, seq)
+        assert rel_err(c, ref) < TOL32
+        # ungrouped phantoms tune the Bloch kernel's spins per thread
+        ph2, seq2 = workload("epi512", "small")
+        hp2 = sim.upload_phantom(ph2)
+        hs2 = sim.upload_sequence(seq2)
+        ch2 = sim.tune(hp2, hs2)
+        assert ch2["spins_per_thread"] in (2, 4)
+        out = sim.simulate(hp2, hs2).cpu().numpy()
+        assert rel_err(out, oracle.simulate(ph2, seq2)) < TOL32
+        koma.koma_sequence_free(hs2)
+        koma.koma_phantom_free(hp2)
+        del torch
+    finally:
+        koma.koma_sequence_free(hs)
+        koma.koma_phantom_free(hp)
