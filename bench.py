@@ -50,6 +50,9 @@ WORKLOAD_TEXT = {
               "128x128 EPI, 4 us dwell, 90-deg 2 ms sinc at 4 us (17,958 steps, 16,384 ADC samples)",
     "se128": "se128: 128^3 ellipsoid phantom (1,097,914 spins, dB0 ~ 50 Hz smooth field), 64-shot spin echo, "
              "90/180-deg 1 ms sinc at 2 us, 256-sample readouts (81,920 steps, 16,384 ADC samples)",
+    "serve": "serve: Poisson stream (200 req/s) of simulations with 1e3-1e6 spins (random subsets of the epi512 "
+             "and se128 phantoms) and 1e3-1e5 steps (the workloads' sequences truncated or repeated), both "
+             "log-uniform, served under a 150 GB device-memory budget",
     "mrf": "mrf: FISP fingerprinting dictionary, 250 T1 x 200 T2 log grid = 50,000 entries of U{50..400} "
            "isochromats over one voxel (11,282,781 spins), inversion + 1,000 TRs of 10-15 ms, flip 5-70 deg "
            "(6,002 steps, 1,000 ADC samples per entry), one persistent autotuned launch",
@@ -246,6 +249,152 @@ def run_reference(args, rank, world):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# serving workload
+# --------------------------------------------------------------------------
+def make_requests(n_req: int, seed: int = 1005):
+    """Request mix of the serving workload (phantom, sequence, spin-steps)."""
+    from paper_2301_02702_b300.workloads import Sequence, workload
+    rng = np.random.default_rng(seed)
+    phs = [workload("epi512", "full")[0], workload("se128", "full")[0]]
+    seqs = [workload(w, "full")[1] for w in ("epi512", "se128", "gre32", "mrf")]
+    seqs[3] = seqs[3]  # the MRF train (ungrouped here: one phantom per request)
+
+    def take(seq, steps):
+        reps = -(-steps // seq.n_steps)
+        s = seq
+        for _ in range(reps - 1):
+            s = s.concat(seq)
+        return Sequence(s.dt[:steps], s.gx[:steps + 1], s.gy[:steps + 1], s.gz[:steps + 1], s.b1[:steps],
+                        s.adc[:steps + 1])
+
+    out = []
+    for _ in range(n_req):
+        n = int(round(np.exp(rng.uniform(np.log(1e3), np.log(1e6)))))
+        steps = int(round(np.exp(rng.uniform(np.log(1e3), np.log(1e5)))))
+        ph = phs[int(rng.integers(len(phs)))]
+        idx = np.sort(rng.choice(ph.n, min(n, ph.n), replace=False))
+        seq = take(seqs[int(rng.integers(len(seqs)))], steps)
+        out.append((ph.subset(idx), seq, len(idx) * steps))
+    return out
+
+
+def run_serve(args, rank, world, local):
+    import torch
+    from paper_2301_02702_b300 import build, koma
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(koma.LIB_PATH):
+        build.build()
+    barrier(world)
+    reqs = make_requests(args.requests)
+    rng = np.random.default_rng(77)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, len(reqs)))
+    total_units = sum(r[2] for r in reqs)
+    srv = koma.Server(local, mem_budget_bytes=int(150e9))
+    for ph, seq, _ in reqs[:3]:  # warm-up
+        srv.wait(srv.submit(ph, seq))
+
+    # open loop: submit at the Poisson arrival times, collect latencies
+    ids = [None] * len(reqs)
+    clocks = ClockSampler(local)
+    barrier(world)
+    clocks.start()
+    t0 = time.perf_counter()
+
+    n_clients = 4  # requests come from several client threads (arrival i -> client i % 4)
+
+    def client(c):
+        for i in range(c, len(reqs), n_clients):
+            d = t0 + arrivals[i] - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            ids[i] = srv.submit(reqs[i][0], reqs[i][1])
+
+    ths = [threading.Thread(target=client, args=(c,)) for c in range(n_clients)]
+    for th in ths:
+        th.start()
+    lat, done = [], []
+    for i in range(len(reqs)):
+        while ids[i] is None:
+            time.sleep(0.0005)
+        _, info = srv.wait(ids[i])
+        lat.append(info["latency_s"])
+        done.append(info["done_s"])
+    for th in ths:
+        th.join()
+    t_open = time.perf_counter() - t0
+    clk = clocks.stop()
+    stats = srv.stats()
+
+    # saturation: everything submitted at once (by the same client threads)
+    sid = [None] * len(reqs)
+
+    def flood(c):
+        for i in range(c, len(reqs), n_clients):
+            sid[i] = srv.submit(reqs[i][0], reqs[i][1])
+
+    t1 = time.perf_counter()
+    ths = [threading.Thread(target=flood, args=(c,)) for c in range(n_clients)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    for rid in sid:
+        srv.wait(rid)
+    t_sat = time.perf_counter() - t1
+    srv.close()
+
+    # plain: one koma_simulate_host per request, in arrival order, one at a time
+    ctx = koma.koma_init(local)
+    service = []
+    for ph, seq, _ in reqs:
+        buf = np.empty((1, seq.n_adc), dtype=np.complex128)
+        ts = time.perf_counter()
+        koma.koma_simulate_host(ctx, ph, seq, koma.KOMA_FP32_SPLITPHASE, out=buf)
+        service.append(time.perf_counter() - ts)
+    koma.koma_destroy(ctx)
+    t_plain = sum(service)
+    free_at, plain_lat = 0.0, []
+    for a, sv in zip(arrivals, service):
+        start = max(a, free_at)
+        free_at = start + sv
+        plain_lat.append(free_at - a)
+
+    value = total_units / t_open
+    value = value * world  # replicas
+    if rank == 0:
+        line = {
+            "metric": "Bloch spin-steps/s served (open-loop Poisson load); p50/p99 latency", "value": value,
+            "unit": UNIT, "n_gpus": world, "steps": len(reqs), "warmup": 3, "ms_per_step": 1e3 * t_open / len(reqs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT["serve"], "requests": len(reqs), "rate_per_s": args.rate,
+                       "mean_spin_steps_per_request": total_units / len(reqs),
+                       "offered_spin_steps_per_s": total_units / arrivals[-1], "parallelism": f"replicas x{world}"},
+            "latency": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                        "mean_s": float(np.mean(lat)), "max_s": float(np.max(lat))},
+            "saturated": {"value": total_units / t_sat, "unit": UNIT, "seconds": t_sat},
+            "vs_plain": {"plain_value": total_units / t_plain, "unit": UNIT,
+                         "ratio_saturated": (total_units / t_sat) / (total_units / t_plain),
+                         "plain_p50_s": float(np.percentile(plain_lat, 50)),
+                         "plain_p99_s": float(np.percentile(plain_lat, 99)),
+                         "plain": "koma_simulate_host per request (upload, simulate, copy back), one at a time in "
+                                  "arrival order; latencies under the same arrivals"},
+            "server": {k: stats[k] for k in ("launches", "batches", "mem_peak", "completed", "failed")},
+            "gpu_launches": int(stats["launches"]),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
     return 0
 
 
@@ -461,12 +610,18 @@ def main(argv=None):
     ap.add_argument("--reference-budget-s", type=float, default=150.0)
     ap.add_argument("--no-kernel-timing", dest="kernel_timing", action="store_false")
     ap.add_argument("--tune", action="store_true", help="autotune the launch first (grouped workloads always do)")
+    ap.add_argument("--requests", type=int, default=200, help="serving workload: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving workload: Poisson arrival rate, 1/s")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     rank, world, local = dist_env()
     if args.impl == "reference":
+        if args.workload == "serve":
+            args.workload = "epi512"
         return run_reference(args, rank, world)
+    if args.workload == "serve":
+        return run_serve(args, rank, world, local)
     return run_ours(args, rank, world, local)
 
 

@@ -287,6 +287,74 @@ koma_status koma_simulate_host(koma_ctx *ctx, int64_t n,
                                const double *b1_im, const uint8_t *adc,
                                koma_precision precision, double *sig_host);
 
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching simulation server.
+ *
+ * Not in the paper: a deployment form of the same simulation. A server owns
+ * a worker thread on one device. Submitted requests (host phantom + host
+ * sequence, same arrays and checks as koma_phantom_upload without groups and
+ * koma_sequence_upload) are admitted in arrival order while the server's
+ * device-memory budget allows; admitted requests share launches of one
+ * persistent kernel that steps 512-spin batches of every request (shortest
+ * remaining work first, two launches in flight), so requests arriving while
+ * others run join within one launch. A request's result (KOMA_FP32_SPLITPHASE
+ * arithmetic) does not depend on the other requests: it is bitwise the same
+ * alone and in any mix.
+ * ---------------------------------------------------------------------- */
+typedef struct koma_server koma_server;
+
+typedef struct {
+    int device;              /* CUDA device                                   */
+    int max_active;          /* admitted requests at once; 0 = 64             */
+    size_t mem_budget_bytes; /* device memory for admitted requests; 0 = none */
+    double launch_work;      /* work per launch, RF spin-step units; 0 = default (~4 ms) */
+} koma_server_config;
+
+typedef struct {
+    uint64_t id;
+    int64_t n_spins, n_steps, n_adc;
+    double submit_s, admit_s, done_s; /* seconds since the server started      */
+    double latency_s;                 /* submit (incl. preprocessing) to result */
+    int32_t launches;                 /* kernel launches the request took part in */
+    koma_status status;
+} koma_request_info;
+
+typedef struct {
+    int64_t submitted, completed, failed, pending, active, launches, batches;
+    size_t mem_used, mem_peak;
+} koma_server_stats;
+
+/* Create a server (cfg NULL: device 0, defaults). Errors: KOMA_E_INVALID,
+ * KOMA_E_CUDA (no device), KOMA_E_NOMEM. */
+koma_status koma_server_create(const koma_server_config *cfg, koma_server **out);
+
+/* Submit one simulation; validates and preprocesses on the calling thread
+ * (host arrays are not kept), then returns its id. Thread-safe. Errors:
+ * KOMA_E_INVALID (as the uploads; message via koma_server_last_error),
+ * KOMA_E_BUSY (server shutting down). */
+koma_status koma_server_submit(koma_server *srv, int64_t n, const double *x, const double *y,
+                               const double *z, const double *pd, const double *t1,
+                               const double *t2, const double *dw, int64_t n_steps,
+                               const double *dt, const double *gx, const double *gy,
+                               const double *gz, const double *b1_re, const double *b1_im,
+                               const uint8_t *adc, uint64_t *id_out);
+
+/* Wait (timeout_s < 0: forever) for request `id`; on success writes its
+ * signal to sig_host (host FP64 [n_adc][2], capacity >= n_adc entries) and
+ * `info` (may be NULL), then forgets the request. Errors: KOMA_E_TIMEOUT
+ * (still running; call again), KOMA_E_INVALID (unknown id or capacity),
+ * KOMA_E_NOMEM (larger than the whole budget), KOMA_E_CUDA, KOMA_E_BUSY
+ * (shut down before admission). Thread-safe. */
+koma_status koma_server_wait(koma_server *srv, uint64_t id, double timeout_s, double *sig_host,
+                             int64_t capacity, koma_request_info *info);
+
+koma_status koma_server_get_stats(koma_server *srv, koma_server_stats *out);
+const char *koma_server_last_error(const koma_server *srv);
+
+/* Finish admitted work, fail requests never admitted, release everything.
+ * No wait may be in progress. */
+koma_status koma_server_destroy(koma_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

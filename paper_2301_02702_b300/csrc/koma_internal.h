@@ -4,6 +4,10 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
+#include <vector>
+
+#include "koma.h"
 
 namespace koma {
 
@@ -133,12 +137,51 @@ struct ReduceArgs {
     double* sig = nullptr;              // [n_groups][n_adc][2]
 };
 
+// One batch of the serving kernel: a spin range of one request's phantom,
+// walked through that request's records; warp w of the batch takes spins
+// [spin_begin + 32 S w, +32 S) and writes row w (rows + w * n_adc).
+struct BatchDesc {
+    const float* p32;
+    int64_t n_pad;
+    const Rec32* rec;
+    int64_t n_rec;
+    float2* rows;
+    int64_t n_adc;
+    int64_t spin_begin, spin_end;
+    float ext[4];
+    int used;
+    int pad_[3];
+};
+static_assert(sizeof(BatchDesc) == 96, "BatchDesc layout");
+
+struct BatchArgs {
+    const BatchDesc* desc = nullptr;
+    const int64_t* n_batches_dev = nullptr;  // device: batches in the table
+    int* counter = nullptr;                  // batch counter, zero at launch
+    int* status = nullptr;
+};
+
+// Host preprocessing (koma_runtime.cpp), shared with the server: validate a
+// phantom and build its FP32 device block [P32_N][n_pad] and extents (max
+// |x|, |y|, |z|, |df|); validate a sequence and build its FP32 records.
+// Return a koma_status; `err` gets the message.
+int host_phantom32(int64_t n, const double* x, const double* y, const double* z, const double* pd,
+                   const double* t1, const double* t2, const double* dw, std::vector<float>& h32, int64_t& n_pad,
+                   double (&max_abs)[4], std::string& err);
+int host_records32(int64_t n_steps, const double* dt, const double* gx, const double* gy, const double* gz,
+                   const double* b1_re, const double* b1_im, const uint8_t* adc, std::vector<Rec32>& r32,
+                   koma_sequence_info& info, std::string& err);
+
 // Launch helpers (koma_kernels.cu). Return a cudaError_t as int.
 int launch_bloch_fp32(const BlochArgs& a, const BlochLaunch& L, void* stream);
 int launch_bloch_fp64(const BlochArgs& a, const BlochLaunch& L, void* stream);
 int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream);
 int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, void* stream);
 int items_ctas_per_sm(int spins_per_thread, int block);
+// Serving kernel (4 spins per thread, `block` threads: a batch is 128 x
+// block/32 spins).
+int launch_batches(const BatchArgs& a, int grid, int block, void* stream);
+int batches_ctas_per_sm(int block);
 // Static partial-sum scratch of koma_simulate_static: capacity in float2
 // elements, and its device address on `device` (which must be current; the
 // address is looked up once per device and cached).

@@ -6,6 +6,8 @@
 // K2  reduce_partials<P>    fixed-order FP64 sum of the per-CTA partials.
 // K3  bloch_items_kernel<S> grouped phantoms: one warp per work item of one
 //                           group, persistent CTAs, per-item partial rows.
+// K4  bloch_batches_kernel  serving: batches of many simulations in one
+//                           persistent launch (spin ranges of each request).
 //
 // Method: KomaMRI.jl paper, Section "Physical and Mathematical Background"
 // (Bloch equation, operator splitting, spinor rotation in the excitation
@@ -627,37 +629,91 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
     if (red_end > red_base) flush();
 }
 
+// One batch of a persistent kernel: every warp of the CTA steps its own spin
+// range [wb, we) of one phantom through the same record stream (TMA tiles
+// shared by the CTA, restarted per batch; `g0` counts the tiles the CTA
+// consumed before) and writes its per-sample sums to `row` (if not null).
+// Returns false if a tile never arrived (status set, copies waited for).
+template <int S>
+__device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const uint32_t (&bar)[2], uint64_t& g0,
+                                           const float* __restrict__ p32, int64_t np, const Rec32* grec,
+                                           int64_t n_rec, const float (&ext)[4], int used, int64_t wb,
+                                           int64_t we, float2* __restrict__ row, int* status) {
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int64_t n_tiles = (n_rec + kTile - 1) / kTile;
+    Spins<S> sp;
+    sp.load(p32, np, wb + lane, 32, we);
+    if (tid == 0) {
+        for (int64_t t = 0; t < 2 && t < n_tiles; ++t) issue_tile(s_rec, bar, grec, n_rec, t, g0 + t);
+    }
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        const uint64_t g = g0 + t;
+        const int b = static_cast<int>(g & 1);
+        const bool ok = mbar_wait_bounded(bar[b], static_cast<uint32_t>((g >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(status, 1);
+                mbar_wait_bounded(bar[b], static_cast<uint32_t>((g >> 1) & 1));
+                if (t + 1 < n_tiles) mbar_wait_bounded(bar[b ^ 1], static_cast<uint32_t>(((g + 1) >> 1) & 1));
+            }
+            return false;
+        }
+        const int nr = static_cast<int>(min(static_cast<int64_t>(kTile), n_rec - t * kTile));
+        for (int r = 0; r < nr; ++r) {
+            const Rec32& R = s_rec[b][r];
+            const int type = R.type;
+            if (type == REC_RF) {
+                sp.rf(R, ext);
+            } else if (type == REC_PREC) {
+                float er[S], ei[S];
+                sp.exact(R, true, p32, np, used, er, ei);
+            } else if (type == REC_ADC) {
+                const int L = min(max(R.count & kCountMask, 1), kMaxAdcRun);
+                const int64_t k0 = R.k0;
+                float er[S], ei[S];
+                sp.exact(R, false, p32, np, used, er, ei);
+                sp.adc(R, L, er, ei, lane, [&](int i, float sr, float si) {
+                    if (row) row[k0 + i] = make_float2(sr, si);
+                });
+            }
+        }
+        __syncthreads();  // everyone is done with tile buffer b
+        if (tid == 0 && t + 2 < n_tiles) {
+            fence_proxy_async_smem();
+            issue_tile(s_rec, bar, grec, n_rec, t + 2, g + 2);
+        }
+    }
+    g0 += static_cast<uint64_t>(n_tiles);
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // K3: grouped ("dictionary") kernel, persistent.
 //
-// Work item = up to 32 * S spins of one group (a group is split into nearly
-// equal items). One warp steps one item through the whole record stream and
-// writes the item's signal as its own FP32 partial row; K2 then sums each
-// group's item rows in a fixed order. CTAs take batches of (warps per CTA)
-// items from a global counter; the item order is longest first, so the last
-// batches are the shortest and the SMs finish together. All warps of a CTA
-// walk the record stream together (shared TMA tiles).
+// Work item = up to 32 * S spins of one group. One warp steps one item
+// through the whole record stream and writes the item's signal as its own
+// FP32 partial row; K2 then sums each group's item rows in a fixed order.
+// CTAs take batches of (warps per CTA) items from a global counter; the item
+// order is longest first, so a batch's items have similar sizes and the last
+// batches are the shortest. All warps of a CTA walk the record stream
+// together (shared TMA tiles).
 // ---------------------------------------------------------------------------
 template <int S>
 __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_kernel(const __grid_constant__ ItemArgs A) {
     __shared__ __align__(128) Rec32 s_rec[2][kTile];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ int64_t s_batch;
-
     const int tid = threadIdx.x;
-    const int lane = tid & 31;
     const int warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int64_t np = A.n_pad;
     const uint32_t bar[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
-    const Rec32* __restrict__ grec = static_cast<const Rec32*>(A.rec);
-    const int64_t n_tiles = (A.n_rec + kTile - 1) / kTile;
     if (tid == 0) {
         mbar_init(bar[0], 1);
         mbar_init(bar[1], 1);
         fence_mbar_init();
     }
-    uint64_t g0 = 0;  // tiles this CTA has consumed in earlier batches
+    uint64_t g0 = 0;
     for (;;) {
         if (tid == 0) s_batch = atomicAdd(A.counter, 1);
         __syncthreads();
@@ -665,57 +721,57 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_kernel(const __grid_
         __syncthreads();
         if (batch * nwarps >= A.n_items) break;
         const int64_t oi = batch * nwarps + warp;
-        int64_t item = -1, ib = 0, ie = 0;
+        int64_t ib = 0, ie = 0;
+        float2* row = nullptr;
         if (oi < A.n_items) {
-            item = A.order[oi];
+            const int64_t item = A.order[oi];
             ib = A.item_begin[item];
             ie = A.item_begin[item + 1];
+            row = static_cast<float2*>(A.partial) + item * A.n_adc;
         }
-        Spins<S> sp;
-        sp.load(A.p32, np, ib + lane, 32, ie);
-        float2* __restrict__ row = static_cast<float2*>(A.partial) + (item >= 0 ? item : 0) * A.n_adc;
-        const bool has_row = item >= 0;
-        if (tid == 0) {
-            for (int64_t t = 0; t < 2 && t < n_tiles; ++t) issue_tile(s_rec, bar, grec, A.n_rec, t, g0 + t);
-        }
-        for (int64_t t = 0; t < n_tiles; ++t) {
-            const uint64_t g = g0 + t;
-            const int b = static_cast<int>(g & 1);
-            const bool ok = mbar_wait_bounded(bar[b], static_cast<uint32_t>((g >> 1) & 1));
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) {
-                    atomicOr(A.status, 1);
-                    mbar_wait_bounded(bar[b], static_cast<uint32_t>((g >> 1) & 1));
-                    if (t + 1 < n_tiles) mbar_wait_bounded(bar[b ^ 1], static_cast<uint32_t>(((g + 1) >> 1) & 1));
-                }
-                return;
-            }
-            const int nr = static_cast<int>(min(static_cast<int64_t>(kTile), A.n_rec - t * kTile));
-            for (int r = 0; r < nr; ++r) {
-                const Rec32& R = s_rec[b][r];
-                const int type = R.type;
-                if (type == REC_RF) {
-                    sp.rf(R, A.ext);
-                } else if (type == REC_PREC) {
-                    float er[S], ei[S];
-                    sp.exact(R, true, A.p32, np, A.used, er, ei);
-                } else if (type == REC_ADC) {
-                    const int L = min(max(R.count & kCountMask, 1), kMaxAdcRun);
-                    const int64_t k0 = R.k0;
-                    float er[S], ei[S];
-                    sp.exact(R, false, A.p32, np, A.used, er, ei);
-                    sp.adc(R, L, er, ei, lane, [&](int i, float sr, float si) {
-                        if (has_row) row[k0 + i] = make_float2(sr, si);
-                    });
-                }
-            }
-            __syncthreads();  // everyone is done with tile buffer b
-            if (tid == 0 && t + 2 < n_tiles) {
-                fence_proxy_async_smem();
-                issue_tile(s_rec, bar, grec, A.n_rec, t + 2, g + 2);
-            }
-        }
-        g0 += static_cast<uint64_t>(n_tiles);
+        if (!walk_batch<S>(s_rec, bar, g0, A.p32, A.n_pad, static_cast<const Rec32*>(A.rec), A.n_rec, A.ext,
+                           A.used, ib, ie, row, A.status))
+            return;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K4: serving kernel, persistent. Batches come from a table that mixes the
+// simulations admitted by the server: batch = a contiguous spin range of one
+// request's phantom, walked through that request's records; warp w of the
+// batch takes the w-th 32 * S spins and writes row w of the batch's rows.
+// Many simulations thereby share one launch; each request's decomposition
+// into batches does not depend on what else is in the launch.
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(kMaxBlock, 2) bloch_batches_kernel(const __grid_constant__ BatchArgs A) {
+    __shared__ __align__(128) Rec32 s_rec[2][kTile];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ int64_t s_batch;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const uint32_t bar[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
+    if (tid == 0) {
+        mbar_init(bar[0], 1);
+        mbar_init(bar[1], 1);
+        fence_mbar_init();
+    }
+    uint64_t g0 = 0;
+    const int64_t n_batches = *A.n_batches_dev;
+    for (;;) {
+        if (tid == 0) s_batch = atomicAdd(A.counter, 1);
+        __syncthreads();
+        const int64_t batch = s_batch;
+        __syncthreads();
+        if (batch >= n_batches) break;
+        const BatchDesc& D = A.desc[batch];
+        const int64_t per_warp = 32LL * S;
+        const int64_t wb = min(D.spin_begin + warp * per_warp, D.spin_end);
+        const int64_t we = min(wb + per_warp, D.spin_end);
+        float2* row = D.rows + static_cast<int64_t>(warp) * D.n_adc;
+        const float ext[4] = {D.ext[0], D.ext[1], D.ext[2], D.ext[3]};
+        if (!walk_batch<S>(s_rec, bar, g0, D.p32, D.n_pad, D.rec, D.n_rec, ext, D.used, wb, we, row, A.status))
+            return;
     }
 }
 
@@ -902,6 +958,18 @@ int items_ctas_per_sm(int spins_per_thread, int block) {
     int n = 0;
     cudaError_t e = spins_per_thread == 2 ? occupancy_items<2>(&n, block) : occupancy_items<4>(&n, block);
     return e == cudaSuccess ? n : -1;
+}
+
+int batches_ctas_per_sm(int block) {
+    int n = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_batches_kernel<4>, block, 0) == cudaSuccess ? n
+                                                                                                            : -1;
+}
+
+int launch_batches(const BatchArgs& a, int grid, int block, void* stream) {
+    if (block <= 0 || block > kMaxBlock || block % 32 != 0 || grid <= 0) return cudaErrorInvalidValue;
+    bloch_batches_kernel<4><<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError();
 }
 
 int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, void* stream) {

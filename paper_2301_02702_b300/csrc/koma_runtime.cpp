@@ -15,6 +15,7 @@
 #include <limits>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "koma.h"
@@ -150,6 +151,47 @@ inline void split(double v, float* hi, float* lo) {
 
 bool finite_or_posinf(double v) { return std::isfinite(v) || (std::isinf(v) && v > 0); }
 
+// fn(lo, hi) over [0, n) split across host threads for large n.
+template <class Fn>
+void parallel_for(int64_t n, Fn&& fn) {
+    const int64_t grain = 1 << 15;
+    unsigned hw = std::thread::hardware_concurrency();
+    int64_t k = std::min<int64_t>(std::max(1u, std::min(hw, 16u)), (n + grain - 1) / grain);
+    if (k <= 1) {
+        fn(int64_t(0), n);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(static_cast<size_t>(k - 1));
+    for (int64_t t = 1; t < k; ++t) th.emplace_back(fn, n * t / k, n * (t + 1) / k);
+    fn(int64_t(0), n / k);
+    for (auto& x : th) x.join();
+}
+
+// Per-spin value checks shared by phantom uploads and server requests.
+bool check_spin_values(int64_t n, const double* x, const double* y, const double* z, const double* pd,
+                       const double* t1, const double* t2, const double* dw, std::string& msg) {
+    char buf[160];
+    for (int64_t j = 0; j < n; ++j) {
+        if (!std::isfinite(x[j]) || !std::isfinite(y[j]) || !std::isfinite(z[j]) || !std::isfinite(dw[j])) {
+            snprintf(buf, sizeof(buf), "phantom: non-finite position/off-resonance at spin %lld", static_cast<long long>(j));
+            msg = buf;
+            return false;
+        }
+        if (!std::isfinite(pd[j]) || pd[j] < 0) {
+            snprintf(buf, sizeof(buf), "phantom: pd[%lld] = %g", static_cast<long long>(j), pd[j]);
+            msg = buf;
+            return false;
+        }
+        if (!finite_or_posinf(t1[j]) || !(t1[j] > 0) || !finite_or_posinf(t2[j]) || !(t2[j] > 0)) {
+            snprintf(buf, sizeof(buf), "phantom: T1/T2 of spin %lld must be > 0 (or +inf)", static_cast<long long>(j));
+            msg = buf;
+            return false;
+        }
+    }
+    return true;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -229,15 +271,9 @@ extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const doubl
         return fail(ctx, KOMA_E_INVALID, "phantom_upload: n_groups = %lld without group_offsets",
                     static_cast<long long>(n_groups));
     }
-    for (int64_t j = 0; j < n; ++j) {
-        if (!std::isfinite(x[j]) || !std::isfinite(y[j]) || !std::isfinite(z[j]) || !std::isfinite(dw[j]))
-            return fail(ctx, KOMA_E_INVALID, "phantom_upload: non-finite position/off-resonance at spin %lld",
-                        static_cast<long long>(j));
-        if (!std::isfinite(pd[j]) || pd[j] < 0)
-            return fail(ctx, KOMA_E_INVALID, "phantom_upload: pd[%lld] = %g", static_cast<long long>(j), pd[j]);
-        if (!finite_or_posinf(t1[j]) || !(t1[j] > 0) || !finite_or_posinf(t2[j]) || !(t2[j] > 0))
-            return fail(ctx, KOMA_E_INVALID, "phantom_upload: T1/T2 of spin %lld must be > 0 (or +inf)",
-                        static_cast<long long>(j));
+    {
+        std::string msg;
+        if (!check_spin_values(n, x, y, z, pd, t1, t2, dw, msg)) return fail(ctx, KOMA_E_INVALID, "%s", msg.c_str());
     }
     koma_phantom* ph = new (std::nothrow) koma_phantom();
     if (!ph) return fail(ctx, KOMA_E_NOMEM, "phantom_upload: host allocation");
@@ -250,23 +286,25 @@ extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const doubl
     std::vector<float> h32(static_cast<size_t>(koma::P32_N * ph->n_pad), 0.f);
     std::vector<double> h64(static_cast<size_t>(koma::P64_N * ph->n_pad), 0.0);
     const int64_t np = ph->n_pad;
-    for (int64_t j = 0; j < n; ++j) {
-        const double f = dw[j] / (2.0 * kPi);
-        split(x[j], &h32[koma::P32_XH * np + j], &h32[koma::P32_XL * np + j]);
-        split(y[j], &h32[koma::P32_YH * np + j], &h32[koma::P32_YL * np + j]);
-        split(z[j], &h32[koma::P32_ZH * np + j], &h32[koma::P32_ZL * np + j]);
-        split(f, &h32[koma::P32_FH * np + j], &h32[koma::P32_FL * np + j]);
-        h32[koma::P32_M0 * np + j] = static_cast<float>(pd[j]);
-        h32[koma::P32_R1 * np + j] = static_cast<float>(kLog2e / t1[j]);
-        h32[koma::P32_R2 * np + j] = static_cast<float>(kLog2e / t2[j]);
-        h64[koma::P64_X * np + j] = x[j];
-        h64[koma::P64_Y * np + j] = y[j];
-        h64[koma::P64_Z * np + j] = z[j];
-        h64[koma::P64_F * np + j] = f;
-        h64[koma::P64_T1 * np + j] = t1[j];
-        h64[koma::P64_T2 * np + j] = t2[j];
-        h64[koma::P64_M0 * np + j] = pd[j];
-    }
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+        for (int64_t j = lo; j < hi; ++j) {
+            const double f = dw[j] / (2.0 * kPi);
+            split(x[j], &h32[koma::P32_XH * np + j], &h32[koma::P32_XL * np + j]);
+            split(y[j], &h32[koma::P32_YH * np + j], &h32[koma::P32_YL * np + j]);
+            split(z[j], &h32[koma::P32_ZH * np + j], &h32[koma::P32_ZL * np + j]);
+            split(f, &h32[koma::P32_FH * np + j], &h32[koma::P32_FL * np + j]);
+            h32[koma::P32_M0 * np + j] = static_cast<float>(pd[j]);
+            h32[koma::P32_R1 * np + j] = static_cast<float>(kLog2e / t1[j]);
+            h32[koma::P32_R2 * np + j] = static_cast<float>(kLog2e / t2[j]);
+            h64[koma::P64_X * np + j] = x[j];
+            h64[koma::P64_Y * np + j] = y[j];
+            h64[koma::P64_Z * np + j] = z[j];
+            h64[koma::P64_F * np + j] = f;
+            h64[koma::P64_T1 * np + j] = t1[j];
+            h64[koma::P64_T2 * np + j] = t2[j];
+            h64[koma::P64_M0 * np + j] = pd[j];
+        }
+    });
     for (int64_t j = 0; j < n; ++j) {
         ph->max_abs[0] = std::max(ph->max_abs[0], std::fabs(x[j]));
         ph->max_abs[1] = std::max(ph->max_abs[1], std::fabs(y[j]));
@@ -1104,3 +1142,57 @@ extern "C" koma_status koma_simulate_host(koma_ctx* ctx, int64_t n, const double
     koma_phantom_free(ph);
     return st;
 }
+
+// ---------------------------------------------------------------------------
+// host preprocessing shared with the server (koma_server.cpp)
+// ---------------------------------------------------------------------------
+namespace koma {
+
+int host_phantom32(int64_t n, const double* x, const double* y, const double* z, const double* pd,
+                   const double* t1, const double* t2, const double* dw, std::vector<float>& h32, int64_t& n_pad,
+                   double (&max_abs)[4], std::string& err) {
+    if (n < 0) {
+        err = "phantom: n < 0";
+        return KOMA_E_INVALID;
+    }
+    if (n > 0 && (!x || !y || !z || !pd || !t1 || !t2 || !dw)) {
+        err = "phantom: NULL array";
+        return KOMA_E_INVALID;
+    }
+    if (!check_spin_values(n, x, y, z, pd, t1, t2, dw, err)) return KOMA_E_INVALID;
+    n_pad = std::max<int64_t>(32, (n + 31) / 32 * 32);
+    h32.assign(static_cast<size_t>(P32_N * n_pad), 0.f);
+    for (int d = 0; d < 4; ++d) max_abs[d] = 0.0;
+    const int64_t np = n_pad;
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+        for (int64_t j = lo; j < hi; ++j) {
+            const double f = dw[j] / (2.0 * kPi);
+            split(x[j], &h32[P32_XH * np + j], &h32[P32_XL * np + j]);
+            split(y[j], &h32[P32_YH * np + j], &h32[P32_YL * np + j]);
+            split(z[j], &h32[P32_ZH * np + j], &h32[P32_ZL * np + j]);
+            split(f, &h32[P32_FH * np + j], &h32[P32_FL * np + j]);
+            h32[P32_M0 * np + j] = static_cast<float>(pd[j]);
+            h32[P32_R1 * np + j] = static_cast<float>(kLog2e / t1[j]);
+            h32[P32_R2 * np + j] = static_cast<float>(kLog2e / t2[j]);
+        }
+    });
+    for (int64_t j = 0; j < n; ++j) {
+        max_abs[0] = std::max(max_abs[0], std::fabs(x[j]));
+        max_abs[1] = std::max(max_abs[1], std::fabs(y[j]));
+        max_abs[2] = std::max(max_abs[2], std::fabs(z[j]));
+        max_abs[3] = std::max(max_abs[3], std::fabs(dw[j]) / (2.0 * kPi));
+    }
+    return KOMA_OK;
+}
+
+int host_records32(int64_t n_steps, const double* dt, const double* gx, const double* gy, const double* gz,
+                   const double* b1_re, const double* b1_im, const uint8_t* adc, std::vector<Rec32>& r32,
+                   koma_sequence_info& info, std::string& err) {
+    RecordBuilder rb;
+    koma_status st = build_records(n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, rb, info, err);
+    if (st != KOMA_OK) return st;
+    r32.swap(rb.r32);
+    return KOMA_OK;
+}
+
+}  // namespace koma

@@ -1,0 +1,614 @@
+// Continuous-batching simulation server (native runtime of libkoma).
+//
+// Requests (a phantom and a sequence, host arrays) are validated and
+// preprocessed on the submitting thread, then one worker thread:
+//   * admits them in arrival order while the device-memory budget allows
+//     (stream-ordered allocations from a server-owned pool, so a finishing
+//     request frees its memory without a device-wide synchronisation);
+//   * keeps two launches of the serving kernel (K4) in flight on two streams;
+//     each launch takes CTA-batches (512 spins of one request) from every
+//     admitted request, shortest remaining work first, enough to fill the GPU
+//     and up to a work cap, so a request arriving while others run joins the
+//     next launch and shares it with them;
+//   * when all batches of a request are done, reduces its partial rows in a
+//     fixed order (K2), copies the signal to pinned host memory and frees
+//     the request's device memory.
+// A request's decomposition into batches does not depend on the other
+// requests, so its result is bitwise the same alone and in any mix.
+// Each slot's launch is a CUDA graph (copy of the batch table, including the
+// zeroed batch counter, then K4); only the copy's length changes per launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "koma.h"
+#include "koma_internal.h"
+
+namespace {
+
+constexpr int kBlock = 128;                        // K4 CTA: 4 warps
+constexpr int kWarps = kBlock / 32;
+constexpr int64_t kBatchSpins = kWarps * 32 * 4;   // 4 spins per thread
+constexpr int kSlots = 2;
+constexpr size_t kHeader = 16;                     // int64 n_batches, int32 counter, pad
+
+enum ReqState { PENDING, ADMITTED, REDUCING, DONE, FAILED };
+
+struct Req {
+    uint64_t id = 0;
+    double t_submit = 0, t_admit = -1, t_done = -1;
+    int64_t n = 0, n_pad = 0, n_steps = 0, n_adc = 0, n_rec = 0;
+    std::vector<float> h32;
+    std::vector<koma::Rec32> recs;
+    double max_abs[4] = {0, 0, 0, 0};
+    float ext[4] = {0, 0, 0, 0};
+    int used = 0;
+    double work_per_spin = 0;  // relative cost units per spin (RF step = 1)
+    int64_t n_batches = 0, next_batch = 0, batches_done = 0;
+    int launches = 0;
+    size_t dev_bytes = 0;
+    float* d32 = nullptr;
+    koma::Rec32* drec = nullptr;
+    float2* drows = nullptr;
+    double* dsig = nullptr;
+    double* hsig = nullptr;  // pinned
+    cudaEvent_t ev_up = nullptr, ev_done = nullptr;
+    ReqState state = PENDING;
+    koma_status err = KOMA_OK;
+    std::string msg;
+
+    double remaining_work() const {
+        return static_cast<double>(n_batches - next_batch) * kBatchSpins * work_per_spin;
+    }
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    char* h_buf = nullptr;  // pinned: header + BatchDesc[cap]
+    char* d_buf = nullptr;
+    int64_t cap = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t copy = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    std::vector<std::pair<Req*, int64_t>> members;
+};
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct koma_server {
+    int device = 0;
+    size_t budget = 0, used = 0, peak = 0;
+    int max_active = 64;
+    double launch_work = 0;  // work units per launch (cap)
+    int sm_count = 0, grid = 0;
+    double t0 = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    std::thread worker;
+    std::deque<Req*> pending;
+    std::vector<Req*> active;
+    std::map<uint64_t, Req*> all;
+    uint64_t next_id = 1;
+    cudaStream_t s_up = nullptr, s_red = nullptr;
+    cudaMemPool_t pool = nullptr;
+    Slot slots[kSlots];
+    int* d_status = nullptr;
+    // statistics
+    int64_t submitted = 0, completed = 0, failed = 0, launches = 0, batches = 0;
+    std::string fatal;
+};
+
+namespace {
+
+koma_status cuda_err(koma_server* S, cudaError_t e, const char* what) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    S->fatal = buf;
+    return e == cudaErrorMemoryAllocation ? KOMA_E_NOMEM : KOMA_E_CUDA;
+}
+
+size_t req_bytes(const Req* r) {
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    return al(r->h32.size() * sizeof(float)) + al(r->recs.size() * sizeof(koma::Rec32)) +
+           al(static_cast<size_t>(r->n_batches) * kWarps * r->n_adc * sizeof(float2)) +
+           al(static_cast<size_t>(r->n_adc) * 2 * sizeof(double));
+}
+
+void fail_req(Req* r, koma_status st, const std::string& m) {
+    r->state = FAILED;
+    r->err = st;
+    r->msg = m;
+}
+
+// Worker side: allocate and upload an admitted request (stream s_up).
+koma_status admit(koma_server* S, Req* r) {
+    const size_t b32 = r->h32.size() * sizeof(float), brec = r->recs.size() * sizeof(koma::Rec32);
+    const size_t brows = static_cast<size_t>(r->n_batches) * kWarps * r->n_adc * sizeof(float2);
+    const size_t bsig = static_cast<size_t>(r->n_adc) * 2 * sizeof(double);
+    cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->d32), b32, S->pool, S->s_up);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->drec), brec, S->pool, S->s_up);
+    if (e == cudaSuccess && brows)
+        e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->drows), brows, S->pool, S->s_up);
+    if (e == cudaSuccess && bsig) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dsig), bsig, S->pool, S->s_up);
+    if (e == cudaSuccess && bsig) e = cudaMallocHost(reinterpret_cast<void**>(&r->hsig), bsig);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r->d32, r->h32.data(), b32, cudaMemcpyHostToDevice, S->s_up);
+    if (e == cudaSuccess && brec)
+        e = cudaMemcpyAsync(r->drec, r->recs.data(), brec, cudaMemcpyHostToDevice, S->s_up);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_up, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(r->ev_up, S->s_up);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? KOMA_E_NOMEM : KOMA_E_CUDA;
+    r->dev_bytes = req_bytes(r);
+    r->t_admit = now_s();
+    r->state = ADMITTED;
+    return KOMA_OK;
+}
+
+void release_device(koma_server* S, Req* r) {
+    if (r->d32) cudaFreeAsync(r->d32, S->s_red);
+    if (r->drec) cudaFreeAsync(r->drec, S->s_red);
+    if (r->drows) cudaFreeAsync(r->drows, S->s_red);
+    if (r->dsig) cudaFreeAsync(r->dsig, S->s_red);
+    r->d32 = nullptr;
+    r->drec = nullptr;
+    r->drows = nullptr;
+    r->dsig = nullptr;
+    S->used -= std::min(S->used, r->dev_bytes);
+    r->dev_bytes = 0;
+    r->h32.clear();
+    r->h32.shrink_to_fit();
+    r->recs.clear();
+    r->recs.shrink_to_fit();
+}
+
+koma_status make_slot(koma_server* S, Slot& sl, int64_t cap) {
+    sl.cap = cap;
+    const size_t bytes = kHeader + static_cast<size_t>(cap) * sizeof(koma::BatchDesc);
+    cudaError_t e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&sl.h_buf), bytes);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sl.d_buf), bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_err(S, e, "server: slot set-up");
+    std::memset(sl.h_buf, 0, bytes);
+    // graph: copy (header with zero counter + table) -> serving kernel
+    koma::BatchArgs A;
+    A.desc = reinterpret_cast<const koma::BatchDesc*>(sl.d_buf + kHeader);
+    A.n_batches_dev = reinterpret_cast<const int64_t*>(sl.d_buf);
+    A.counter = reinterpret_cast<int*>(sl.d_buf + 8);
+    A.status = S->d_status;
+    e = cudaStreamBeginCapture(sl.st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemcpyAsync(sl.d_buf, sl.h_buf, kHeader + sizeof(koma::BatchDesc), cudaMemcpyHostToDevice, sl.st);
+        koma::launch_batches(A, S->grid, kBlock, sl.st);
+        e = cudaStreamEndCapture(sl.st, &sl.graph);
+    }
+    if (e != cudaSuccess) return cuda_err(S, e, "server: graph capture");
+    size_t n_nodes = 0;
+    cudaGraphGetNodes(sl.graph, nullptr, &n_nodes);
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    cudaGraphGetNodes(sl.graph, nodes.data(), &n_nodes);
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        cudaGraphNodeGetType(nd, &t);
+        if (t == cudaGraphNodeTypeMemcpy) sl.copy = nd;
+    }
+    if (!sl.copy) return cuda_err(S, cudaErrorUnknown, "server: graph has no copy node");
+    e = cudaGraphInstantiate(&sl.exec, sl.graph, 0);
+    if (e != cudaSuccess) return cuda_err(S, e, "server: graph instantiate");
+    return KOMA_OK;
+}
+
+// Fill a free slot with batches and launch it. Returns true if launched.
+bool launch_slot(koma_server* S, Slot& sl) {
+    std::vector<Req*> cand;
+    for (Req* r : S->active)
+        if (r->state == ADMITTED && r->next_batch < r->n_batches) cand.push_back(r);
+    if (cand.empty()) return false;
+    std::sort(cand.begin(), cand.end(), [](const Req* a, const Req* b) {
+        return a->remaining_work() < b->remaining_work() ||
+               (a->remaining_work() == b->remaining_work() && a->id < b->id);
+    });
+    koma::BatchDesc* tab = reinterpret_cast<koma::BatchDesc*>(sl.h_buf + kHeader);
+    int64_t nb = 0;
+    double work = 0;
+    sl.members.clear();
+    for (Req* r : cand) {
+        int64_t take = 0;
+        while (r->next_batch < r->n_batches && nb < sl.cap) {
+            const double w = kBatchSpins * r->work_per_spin;
+            if (nb >= S->grid && work + w > S->launch_work) break;
+            koma::BatchDesc& D = tab[nb++];
+            std::memset(&D, 0, sizeof(D));
+            D.p32 = r->d32;
+            D.n_pad = r->n_pad;
+            D.rec = r->drec;
+            D.n_rec = r->n_rec;
+            D.rows = r->drows + static_cast<size_t>(r->next_batch) * kWarps * r->n_adc;
+            D.n_adc = r->n_adc;
+            D.spin_begin = r->next_batch * kBatchSpins;
+            D.spin_end = std::min(r->n, D.spin_begin + kBatchSpins);
+            for (int d = 0; d < 4; ++d) D.ext[d] = r->ext[d];
+            D.used = r->used;
+            ++r->next_batch;
+            ++take;
+            work += w;
+        }
+        if (take) {
+            sl.members.emplace_back(r, take);
+            ++r->launches;
+            cudaStreamWaitEvent(sl.st, r->ev_up, 0);  // no-op once the upload is done
+        }
+        if (nb >= sl.cap || (nb >= S->grid && work >= S->launch_work)) break;
+    }
+    if (nb == 0) return false;
+    *reinterpret_cast<int64_t*>(sl.h_buf) = nb;
+    *reinterpret_cast<int32_t*>(sl.h_buf + 8) = 0;
+    cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(sl.exec, sl.copy, sl.d_buf, sl.h_buf,
+                                                       kHeader + static_cast<size_t>(nb) * sizeof(koma::BatchDesc),
+                                                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaGraphLaunch(sl.exec, sl.st);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.st);
+    if (e != cudaSuccess) {
+        for (auto& m : sl.members) fail_req(m.first, KOMA_E_CUDA, cudaGetErrorString(e));
+        sl.members.clear();
+        return false;
+    }
+    sl.busy = true;
+    ++S->launches;
+    S->batches += nb;
+    return true;
+}
+
+void finalize(koma_server* S, Req* r) {
+    koma::ReduceArgs R;
+    R.partial = r->drows;
+    R.grid = static_cast<int>(r->n_batches * kWarps);
+    R.n_groups = 1;
+    R.n_adc = r->n_adc;
+    R.sig = r->dsig;
+    int e = r->n_adc > 0 ? koma::launch_reduce(R, false, S->s_red) : cudaSuccess;
+    cudaError_t ce = static_cast<cudaError_t>(e);
+    if (ce == cudaSuccess && r->n_adc > 0)
+        ce = cudaMemcpyAsync(r->hsig, r->dsig, static_cast<size_t>(r->n_adc) * 2 * sizeof(double),
+                             cudaMemcpyDeviceToHost, S->s_red);
+    if (ce == cudaSuccess) ce = cudaEventRecord(r->ev_done, S->s_red);
+    if (ce != cudaSuccess) {
+        fail_req(r, KOMA_E_CUDA, cudaGetErrorString(ce));
+        return;
+    }
+    r->state = REDUCING;
+}
+
+void worker_loop(koma_server* S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        bool progress = false;
+        // admission (arrival order, device-memory budget)
+        while (!S->pending.empty() && static_cast<int>(S->active.size()) < S->max_active) {
+            Req* r = S->pending.front();
+            const size_t need = req_bytes(r);
+            if (S->budget && S->used + need > S->budget) {
+                if (S->active.empty()) {
+                    S->pending.pop_front();
+                    fail_req(r, KOMA_E_NOMEM, "request needs more device memory than the server's budget");
+                    r->t_done = now_s();
+                    S->failed++;
+                    S->cv_done.notify_all();
+                    progress = true;
+                    continue;
+                }
+                break;
+            }
+            S->pending.pop_front();
+            const koma_status st = admit(S, r);
+            if (st != KOMA_OK) {
+                release_device(S, r);
+                fail_req(r, st, "admission failed (device allocation or upload)");
+                r->t_done = now_s();
+                S->failed++;
+                S->cv_done.notify_all();
+            } else {
+                S->used += r->dev_bytes;
+                S->peak = std::max(S->peak, S->used);
+                S->active.push_back(r);
+                if (r->n_batches == 0) finalize(S, r);  // nothing to step
+            }
+            progress = true;
+        }
+        // completed launches
+        for (Slot& sl : S->slots) {
+            if (!sl.busy) continue;
+            const cudaError_t q = cudaEventQuery(sl.done);
+            if (q == cudaErrorNotReady) continue;
+            sl.busy = false;
+            progress = true;
+            for (auto& m : sl.members) {
+                Req* r = m.first;
+                if (q != cudaSuccess) {
+                    fail_req(r, KOMA_E_CUDA, cudaGetErrorString(q));
+                    continue;
+                }
+                r->batches_done += m.second;
+                if (r->state == ADMITTED && r->batches_done == r->n_batches) finalize(S, r);
+            }
+            sl.members.clear();
+        }
+        // new launches
+        for (Slot& sl : S->slots)
+            if (!sl.busy && launch_slot(S, sl)) progress = true;
+        // finished requests
+        for (size_t i = 0; i < S->active.size();) {
+            Req* r = S->active[i];
+            bool out = false;
+            if (r->state == REDUCING) {
+                const cudaError_t q = cudaEventQuery(r->ev_done);
+                if (q != cudaErrorNotReady) {
+                    if (q == cudaSuccess) {
+                        r->state = DONE;
+                        S->completed++;
+                    } else {
+                        fail_req(r, KOMA_E_CUDA, cudaGetErrorString(q));
+                        S->failed++;
+                    }
+                    r->t_done = now_s();
+                    out = true;
+                }
+            } else if (r->state == FAILED) {
+                // wait until no launch still uses its memory
+                bool in_use = false;
+                for (Slot& sl : S->slots)
+                    for (auto& m : sl.members) in_use |= m.first == r;
+                if (!in_use) {
+                    if (r->t_done < 0) r->t_done = now_s();
+                    S->failed++;
+                    out = true;
+                }
+            }
+            if (out) {
+                release_device(S, r);
+                S->active.erase(S->active.begin() + static_cast<long>(i));
+                S->cv_done.notify_all();
+                progress = true;
+            } else {
+                ++i;
+            }
+        }
+        const bool idle = S->pending.empty() && S->active.empty();
+        if (S->stop && idle) break;
+        if (idle) {
+            S->cv_work.wait(lk);
+        } else if (!progress) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lk.lock();
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" koma_status koma_server_create(const koma_server_config* cfg, koma_server** out) {
+    if (!out) return KOMA_E_INVALID;
+    *out = nullptr;
+    koma_server_config c{};
+    if (cfg) c = *cfg;
+    if (c.device < 0 || c.max_active < 0 || c.launch_work < 0) return KOMA_E_INVALID;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || c.device >= count) {
+        cudaGetLastError();
+        return KOMA_E_CUDA;
+    }
+    koma_server* S = new (std::nothrow) koma_server();
+    if (!S) return KOMA_E_NOMEM;
+    S->device = c.device;
+    S->budget = c.mem_budget_bytes;
+    S->max_active = c.max_active > 0 ? c.max_active : 64;
+    // default cap: ~4 ms of the serving kernel at ~4.5e11 RF spin-steps/s
+    S->launch_work = c.launch_work > 0 ? c.launch_work : 1.8e9;
+    S->t0 = now_s();
+    int prev = -1;
+    cudaGetDevice(&prev);
+    koma_status st = KOMA_OK;
+    cudaError_t e = cudaSetDevice(S->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&S->sm_count, cudaDevAttrMultiProcessorCount, S->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->s_up, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->s_red, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&S->d_status), sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(S->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = S->device;
+        e = cudaMemPoolCreate(&S->pool, &props);
+        if (e == cudaSuccess) {
+            uint64_t keep = ~0ull;  // keep freed memory in the pool for reuse
+            cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
+    if (e != cudaSuccess) st = cuda_err(S, e, "server: set-up");
+    if (st == KOMA_OK) {
+        const int per_sm = std::max(1, koma::batches_ctas_per_sm(kBlock));
+        S->grid = S->sm_count * per_sm;
+        for (Slot& sl : S->slots) {
+            st = make_slot(S, sl, std::max<int64_t>(4096, 4 * S->grid));
+            if (st != KOMA_OK) break;
+        }
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    if (st != KOMA_OK) {
+        koma_server_destroy(S);
+        return st;
+    }
+    S->worker = std::thread(worker_loop, S);
+    *out = S;
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const double* x, const double* y,
+                                          const double* z, const double* pd, const double* t1, const double* t2,
+                                          const double* dw, int64_t n_steps, const double* dt, const double* gx,
+                                          const double* gy, const double* gz, const double* b1_re,
+                                          const double* b1_im, const uint8_t* adc, uint64_t* id_out) {
+    if (!S || !id_out) return KOMA_E_INVALID;
+    Req* r = new (std::nothrow) Req();
+    if (!r) return KOMA_E_NOMEM;
+    r->t_submit = now_s();
+    std::string err;
+    int st = koma::host_phantom32(n, x, y, z, pd, t1, t2, dw, r->h32, r->n_pad, r->max_abs, err);
+    koma_sequence_info info{};
+    if (st == KOMA_OK) st = koma::host_records32(n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, r->recs, info, err);
+    if (st != KOMA_OK) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->fatal = err;
+        delete r;
+        return static_cast<koma_status>(st);
+    }
+    r->n = n;
+    r->n_steps = n_steps;
+    r->n_adc = info.n_adc;
+    r->n_rec = info.n_records;
+    for (int d = 0; d < 4; ++d) {
+        r->ext[d] = static_cast<float>(r->max_abs[d] * (1.0 + 1e-6));
+        if (r->max_abs[d] > 0) r->used |= 1 << d;
+    }
+    double w = 0;
+    for (const koma::Rec32& q : r->recs)
+        w += q.type == koma::REC_ADC ? 1.0 + (q.count & koma::kCountMask) / 8.0 : 1.0;
+    r->work_per_spin = std::max(1.0, w);
+    r->n_batches = (r->n_adc > 0 && n > 0) ? (n + kBatchSpins - 1) / kBatchSpins : 0;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) {
+        delete r;
+        return KOMA_E_BUSY;
+    }
+    r->id = S->next_id++;
+    S->all[r->id] = r;
+    S->pending.push_back(r);
+    S->submitted++;
+    *id_out = r->id;
+    S->cv_work.notify_all();
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_server_wait(koma_server* S, uint64_t id, double timeout_s, double* sig_host,
+                                        int64_t capacity, koma_request_info* info) {
+    if (!S) return KOMA_E_INVALID;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return KOMA_E_INVALID;
+    Req* r = it->second;
+    auto finished = [&] { return (r->state == DONE || r->state == FAILED) && r->t_done >= 0 && !r->d32; };
+    if (timeout_s < 0) {
+        S->cv_done.wait(lk, finished);
+    } else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), finished)) {
+        return KOMA_E_TIMEOUT;
+    }
+    if (info) {
+        info->id = r->id;
+        info->n_spins = r->n;
+        info->n_steps = r->n_steps;
+        info->n_adc = r->n_adc;
+        info->submit_s = r->t_submit - S->t0;
+        info->admit_s = r->t_admit >= 0 ? r->t_admit - S->t0 : -1;
+        info->done_s = r->t_done - S->t0;
+        info->latency_s = r->t_done - r->t_submit;
+        info->launches = r->launches;
+        info->status = r->state == DONE ? KOMA_OK : r->err;
+    }
+    koma_status st = r->state == DONE ? KOMA_OK : r->err;
+    if (st == KOMA_OK && r->n_adc > 0) {
+        if (!sig_host || capacity < r->n_adc) return KOMA_E_INVALID;  // keep the result for a retry
+        std::memcpy(sig_host, r->hsig, static_cast<size_t>(r->n_adc) * 2 * sizeof(double));
+    } else if (st == KOMA_OK && sig_host && capacity > 0) {
+        // nothing observed
+    }
+    if (st != KOMA_OK) S->fatal = r->msg;
+    S->all.erase(it);
+    lk.unlock();
+    if (r->hsig) cudaFreeHost(r->hsig);
+    if (r->ev_up) cudaEventDestroy(r->ev_up);
+    if (r->ev_done) cudaEventDestroy(r->ev_done);
+    delete r;
+    return st;
+}
+
+extern "C" koma_status koma_server_get_stats(koma_server* S, koma_server_stats* out) {
+    if (!S || !out) return KOMA_E_INVALID;
+    std::lock_guard<std::mutex> lk(S->mu);
+    out->submitted = S->submitted;
+    out->completed = S->completed;
+    out->failed = S->failed;
+    out->pending = static_cast<int64_t>(S->pending.size());
+    out->active = static_cast<int64_t>(S->active.size());
+    out->launches = S->launches;
+    out->batches = S->batches;
+    out->mem_used = S->used;
+    out->mem_peak = S->peak;
+    return KOMA_OK;
+}
+
+extern "C" const char* koma_server_last_error(const koma_server* S) { return S ? S->fatal.c_str() : "null server"; }
+
+extern "C" koma_status koma_server_destroy(koma_server* S) {
+    if (!S) return KOMA_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        for (Req* r : S->pending) fail_req(r, KOMA_E_BUSY, "server shut down before admission");
+        for (Req* r : S->pending) {
+            r->t_done = now_s();
+            S->failed++;
+        }
+        S->pending.clear();
+        S->cv_work.notify_all();
+        S->cv_done.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(S->device);
+    if (S->s_red) cudaStreamSynchronize(S->s_red);
+    for (Slot& sl : S->slots) {
+        if (sl.st) cudaStreamSynchronize(sl.st);
+        if (sl.exec) cudaGraphExecDestroy(sl.exec);
+        if (sl.graph) cudaGraphDestroy(sl.graph);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.h_buf) cudaFreeHost(sl.h_buf);
+        if (sl.d_buf) cudaFree(sl.d_buf);
+        if (sl.st) cudaStreamDestroy(sl.st);
+    }
+    for (auto& kv : S->all) {
+        Req* r = kv.second;
+        if (r->hsig) cudaFreeHost(r->hsig);
+        if (r->ev_up) cudaEventDestroy(r->ev_up);
+        if (r->ev_done) cudaEventDestroy(r->ev_done);
+        delete r;
+    }
+    if (S->pool) cudaMemPoolDestroy(S->pool);
+    if (S->d_status) cudaFree(S->d_status);
+    if (S->s_up) cudaStreamDestroy(S->s_up);
+    if (S->s_red) cudaStreamDestroy(S->s_red);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete S;
+    return KOMA_OK;
+}

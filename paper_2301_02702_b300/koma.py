@@ -32,6 +32,8 @@ EXPORTS = (
     "koma_sequence_upload", "koma_sequence_n_adc", "koma_sequence_n_steps", "koma_sequence_get_info",
     "koma_sequence_free", "koma_sequence_plan", "koma_simulate", "koma_sync", "koma_set_timing",
     "koma_get_timing", "koma_get_launch_info", "koma_simulate_host", "koma_simulate_static", "koma_tune",
+    "koma_server_create", "koma_server_submit", "koma_server_wait", "koma_server_get_stats",
+    "koma_server_last_error", "koma_server_destroy",
 )
 
 
@@ -55,6 +57,30 @@ class SequenceInfo(ctypes.Structure):
     _fields_ = [("n_steps", ctypes.c_int64), ("n_rf", ctypes.c_int64), ("n_adc", ctypes.c_int64),
                 ("n_precess", ctypes.c_int64), ("n_records", ctypes.c_int64),
                 ("n_adc_runs", ctypes.c_int64), ("n_materialize", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("max_active", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
+                ("launch_work", ctypes.c_double)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("n_spins", ctypes.c_int64), ("n_steps", ctypes.c_int64),
+                ("n_adc", ctypes.c_int64), ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("latency_s", ctypes.c_double), ("launches", ctypes.c_int32),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("active", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("mem_used", ctypes.c_size_t), ("mem_peak", ctypes.c_size_t)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -127,6 +153,20 @@ def load(path: Optional[str] = None):
         lib.koma_get_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
         lib.koma_get_launch_info.restype = st
         lib.koma_get_launch_info.argtypes = [_vp, ctypes.POINTER(LaunchInfo)]
+        lib.koma_server_create.restype = st
+        lib.koma_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]
+        lib.koma_server_submit.restype = st
+        lib.koma_server_submit.argtypes = ([_vp, ctypes.c_int64] + [_dp] * 7 + [ctypes.c_int64] + [_dp] * 6
+                                           + [_u8p, ctypes.POINTER(ctypes.c_uint64)])
+        lib.koma_server_wait.restype = st
+        lib.koma_server_wait.argtypes = [_vp, ctypes.c_uint64, ctypes.c_double, _dp, ctypes.c_int64,
+                                         ctypes.POINTER(RequestInfo)]
+        lib.koma_server_get_stats.restype = st
+        lib.koma_server_get_stats.argtypes = [_vp, ctypes.POINTER(ServerStats)]
+        lib.koma_server_last_error.restype = ctypes.c_char_p
+        lib.koma_server_last_error.argtypes = [_vp]
+        lib.koma_server_destroy.restype = st
+        lib.koma_server_destroy.argtypes = [_vp]
         lib.koma_tune.restype = st
         lib.koma_tune.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(LaunchInfo)]
         lib.koma_simulate_static.restype = st
@@ -387,3 +427,80 @@ class Simulator:
         if self.ctx is not None:
             koma_destroy(self.ctx)
             self.ctx = None
+
+
+# --------------------------------------------------------------------------
+# continuous-batching server
+# --------------------------------------------------------------------------
+
+def koma_server_create(device: int = 0, mem_budget_bytes: int = 0, max_active: int = 0, launch_work: float = 0.0):
+    cfg = ServerConfig(int(device), int(max_active), int(mem_budget_bytes), float(launch_work))
+    out = _vp()
+    rc = load().koma_server_create(ctypes.byref(cfg), ctypes.byref(out))
+    if rc != KOMA_OK:
+        raise KomaError(rc, "koma_server_create failed")
+    return out
+
+
+def koma_server_last_error(srv) -> str:
+    return load().koma_server_last_error(srv).decode()
+
+
+def koma_server_submit(srv, phantom, seq) -> int:
+    arrs = [_f64(getattr(phantom, f)) for f in ("x", "y", "z", "pd", "t1", "t2", "dw")]
+    dt, gx, gy, gz, bre, bim, adc = _seq_arrays(seq)
+    rid = ctypes.c_uint64()
+    rc = load().koma_server_submit(srv, arrs[0].shape[0], *[_ptr(a) for a in arrs], dt.shape[0], _ptr(dt),
+                                   _ptr(gx), _ptr(gy), _ptr(gz), _ptr(bre), _ptr(bim), _ptr(adc, ctypes.c_uint8),
+                                   ctypes.byref(rid))
+    if rc != KOMA_OK:
+        raise KomaError(rc, "koma_server_submit: " + koma_server_last_error(srv))
+    return int(rid.value)
+
+
+def koma_server_wait(srv, rid: int, n_adc: int, timeout_s: float = -1.0):
+    """(signal complex128 [n_adc], info dict) of request `rid`."""
+    out = np.empty(max(n_adc, 1), dtype=np.complex128)
+    info = RequestInfo()
+    rc = load().koma_server_wait(srv, int(rid), float(timeout_s), out.ctypes.data_as(_dp), n_adc, ctypes.byref(info))
+    if rc != KOMA_OK:
+        raise KomaError(rc, "koma_server_wait: " + koma_server_last_error(srv))
+    return out[:n_adc], info.as_dict()
+
+
+def koma_server_get_stats(srv) -> dict:
+    st = ServerStats()
+    rc = load().koma_server_get_stats(srv, ctypes.byref(st))
+    if rc != KOMA_OK:
+        raise KomaError(rc, "koma_server_get_stats")
+    return st.as_dict()
+
+
+def koma_server_destroy(srv):
+    load().koma_server_destroy(srv)
+
+
+class Server:
+    """Continuous-batching simulation server on one device (native worker)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_active: int = 0, launch_work: float = 0.0):
+        self.srv = koma_server_create(device, mem_budget_bytes, max_active, launch_work)
+        self._n_adc = {}
+
+    def submit(self, phantom, seq) -> int:
+        rid = koma_server_submit(self.srv, phantom, seq)
+        self._n_adc[rid] = int(np.count_nonzero(seq.adc))
+        return rid
+
+    def wait(self, rid: int, timeout_s: float = -1.0):
+        sig, info = koma_server_wait(self.srv, rid, self._n_adc[rid], timeout_s)
+        del self._n_adc[rid]
+        return sig, info
+
+    def stats(self) -> dict:
+        return koma_server_get_stats(self.srv)
+
+    def close(self):
+        if self.srv is not None:
+            koma_server_destroy(self.srv)
+            self.srv = None

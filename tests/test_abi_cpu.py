@@ -131,3 +131,11 @@ def test_plan_empty_and_adc_at_t0(lib):
     seq = Sequence(np.zeros(0), np.zeros(1), np.zeros(1), np.zeros(1), np.zeros(0, complex), np.ones(1, np.uint8))
     info = koma.koma_sequence_plan(seq)
     assert info["n_adc"] == 1 and info["n_records"] == 1
+
+
+def test_server_create_without_gpu_fails_cleanly(lib, cuda_available):
+    if cuda_available:
+        pytest.skip("a GPU is present")
+    with pytest.raises(koma.KomaError) as e:
+        koma.koma_server_create(0)
+    assert e.value.status == koma.KOMA_E_CUDA

@@ -1,0 +1,113 @@
+"""The continuous-batching server: results against the oracle and against the
+single-simulation path, the same result alone and in a mix (bitwise), and
+admission under a device-memory budget."""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2301_02702_b300 import build, koma
+from paper_2301_02702_b300.workloads import random_sequence, random_spins, workload
+
+pytestmark = pytest.mark.gpu
+TOL32 = 1e-4
+
+
+def rel_err(got, ref):
+    return float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+
+
+@pytest.fixture(scope="module")
+def server():
+    build.build()
+    srv = koma.Server(0)
+    yield srv
+    srv.close()
+
+
+def _mix(seed, k):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(k):
+        n = int(rng.integers(1, 3000))
+        out.append((random_spins(n, seed=1000 * seed + i), random_sequence(int(rng.integers(20, 600)), seed=77 * seed + i)))
+    return out
+
+
+def test_server_matches_oracle(server):
+    reqs = [workload("epi512", "small"), workload("se128", "small"), workload("gre32", "small")] + _mix(3, 5)
+    ids = [server.submit(ph, seq) for ph, seq in reqs]
+    for (ph, seq), rid in zip(reqs, ids):
+        sig, info = server.wait(rid)
+        assert info["status"] == 0 and info["latency_s"] > 0 and info["launches"] >= 1
+        ref = oracle.simulate(ph, seq)[0]
+        assert rel_err(sig, ref) < TOL32
+
+
+def test_same_result_alone_and_in_a_mix(server):
+    ph, seq = workload("epi512", "small")
+    alone, _ = server.wait(server.submit(ph, seq))
+    mix = _mix(7, 12)
+    ids = []
+    for i, (p, s) in enumerate(mix):
+        ids.append(server.submit(p, s))
+        if i == 5:
+            target = server.submit(ph, seq)
+    with_mix, info = server.wait(target)
+    for rid in ids:
+        server.wait(rid)
+    assert np.array_equal(alone, with_mix), "a request's result must not depend on the mix"
+    # and both agree with the single-simulation path within tolerance
+    sim = koma.Simulator(0)
+    try:
+        hp, hs = sim.upload_phantom(ph), sim.upload_sequence(seq)
+        direct = sim.simulate(hp, hs).cpu().numpy()[0]
+        koma.koma_phantom_free(hp)
+        koma.koma_sequence_free(hs)
+    finally:
+        sim.close()
+    assert rel_err(alone, direct) < TOL32
+
+
+def test_concurrent_submitters(server):
+    mix = _mix(11, 16)
+    results = {}
+
+    def worker(lo, hi):
+        for i in range(lo, hi):
+            rid = server.submit(*mix[i])
+            results[i] = server.wait(rid)[0]
+
+    th = [threading.Thread(target=worker, args=(4 * t, 4 * t + 4)) for t in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for i, (ph, seq) in enumerate(mix):
+        ref = oracle.simulate(ph, seq)[0]
+        if np.max(np.abs(ref)) > 0:
+            assert rel_err(results[i], ref) < TOL32
+
+
+def test_admission_by_memory_budget():
+    """A small budget admits requests one or two at a time; all complete, the
+    peak stays under the budget; a request larger than the whole budget fails."""
+    reqs = _mix(21, 6)
+    srv = koma.Server(0, mem_budget_bytes=400 << 10)
+    try:
+        ids = [srv.submit(p, s) for p, s in reqs]
+        for (ph, seq), rid in zip(reqs, ids):
+            sig, _ = srv.wait(rid)
+            ref = oracle.simulate(ph, seq)[0]
+            if np.max(np.abs(ref)) > 0:
+                assert rel_err(sig, ref) < TOL32
+        st = srv.stats()
+        assert st["completed"] == len(reqs) and st["mem_peak"] <= 400 << 10
+        big_ph, big_seq = workload("epi512", "full")
+        rid = srv.submit(big_ph, big_seq)
+        with pytest.raises(koma.KomaError) as e:
+            srv.wait(rid)
+        assert e.value.status == koma.KOMA_E_NOMEM
+    finally:
+        srv.close()
