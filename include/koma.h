@@ -297,7 +297,9 @@ koma_status koma_simulate_host(koma_ctx *ctx, int64_t n,
  * device-memory budget allows; admitted requests share launches of one
  * persistent kernel that steps 512-spin batches of every request (shortest
  * remaining work first, two launches in flight), so requests arriving while
- * others run join within one launch. A request's result (KOMA_FP32_SPLITPHASE
+ * others run join within one launch. A batch walks its sequence in chunks of
+ * step records, its spin state checkpointed in device memory between
+ * launches, so a long simulation never holds the GPU for long. A request's result (KOMA_FP32_SPLITPHASE
  * arithmetic) does not depend on the other requests: it is bitwise the same
  * alone and in any mix.
  * ---------------------------------------------------------------------- */
@@ -308,6 +310,9 @@ typedef struct {
     int max_active;          /* admitted requests at once; 0 = 64             */
     size_t mem_budget_bytes; /* device memory for admitted requests; 0 = none */
     double launch_work;      /* work per launch, RF spin-step units; 0 = default (~4 ms) */
+    int64_t chunk_records;   /* a batch walks at most this many step records per launch and is
+                                checkpointed between launches (long sequences do not hold the GPU);
+                                0 = 4096 */
 } koma_server_config;
 
 typedef struct {

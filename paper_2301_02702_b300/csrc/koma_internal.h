@@ -148,11 +148,15 @@ struct BatchDesc {
     float2* rows;
     int64_t n_adc;
     int64_t spin_begin, spin_end;
+    int64_t rec_begin, rec_end;  // records walked by this launch
+    float* state;                // [3][n_pad] checkpoint between chunks (null: one chunk)
     float ext[4];
     int used;
-    int pad_[3];
+    int pad0_;
+    int64_t rf_hdr;              // header of the RF run rec_begin lies inside (-1: none)
+    int64_t pad1_;
 };
-static_assert(sizeof(BatchDesc) == 96, "BatchDesc layout");
+static_assert(sizeof(BatchDesc) == 128, "BatchDesc layout");
 
 struct BatchArgs {
     const BatchDesc* desc = nullptr;

@@ -272,6 +272,30 @@ struct Spins {
     // Gbar.x + df/gammabar) in turns; the spinor of the step (Eq. Rot_exc with
     // phi = -2 pi |a|) is the rotation by -2 pi |a| about a/|a|, applied as
     // the quaternion w = cos(pi|a|), u = -a sin(pi|a|)/|a|.
+    // Checkpointed state [3][np] (Mx, My, Mz at t_ref) of a walk that was cut.
+    __device__ __forceinline__ void load_state(const float* __restrict__ st, int64_t np) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int64_t j = index(s);
+            if (j < end) {
+                mx[s] = st[j];
+                my[s] = st[np + j];
+                mz[s] = st[2 * np + j];
+            }
+        }
+    }
+    __device__ __forceinline__ void save_state(float* __restrict__ st, int64_t np) const {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int64_t j = index(s);
+            if (j < end) {
+                st[j] = mx[s];
+                st[np + j] = my[s];
+                st[2 * np + j] = mz[s];
+            }
+        }
+    }
+
     // One excitation step for every slot: rotation about the step's constant
     // field, then relaxation over dt. The record holds theta = pi gammabar dt
     // (B1x, B1y, Gbar) and the spin adds pi dt df, so theta is the half-angle
@@ -327,6 +351,15 @@ struct Spins {
         }
     }
 
+    // Rotation path of an RF run from its header record (see rf()).
+    __device__ __forceinline__ void set_mode(const Rec32& H, const float (&ext)[4]) {
+        const float mb = H.a[7], mgx = H.a[8], mgy = H.a[9], mgz = H.a[10], mdt = H.a[11];
+        const bool same = (mgx == 0.f || ext[0] == 0.f) && (mgy == 0.f || ext[1] == 0.f) &&
+                          (mgz == 0.f || ext[2] == 0.f) && ext[3] == 0.f;
+        const float bound = mb + mgx * ext[0] + mgy * ext[1] + mgz * ext[2] + mdt * 3.14159265358979323846f * ext[3];
+        rf_mode = same ? 2 : (bound <= 0.754f ? 1 : 0);
+    }
+
     // RF record. The first record of a run of RF records carries the run's
     // maxima; with the phantom's extents `ext` (max |x|, |y|, |z| in m, |df|
     // in Hz) they choose, once per run, between: one rotation for all spins
@@ -335,14 +368,7 @@ struct Spins {
     __device__ __forceinline__ void rf(const Rec32& R, const float (&ext)[4]) {
         const float gx = R.a[0], gy = R.a[1], gz = R.a[2];
         const float bx = R.a[3], by = R.a[4], b2 = R.a[5], dt = R.a[6];
-        if (R.count > 0) {
-            const float mb = R.a[7], mgx = R.a[8], mgy = R.a[9], mgz = R.a[10], mdt = R.a[11];
-            const bool same = (mgx == 0.f || ext[0] == 0.f) && (mgy == 0.f || ext[1] == 0.f) &&
-                              (mgz == 0.f || ext[2] == 0.f) && ext[3] == 0.f;
-            const float bound = mb + mgx * ext[0] + mgy * ext[1] + mgz * ext[2] +
-                                mdt * 3.14159265358979323846f * ext[3];
-            rf_mode = same ? 2 : (bound <= 0.754f ? 1 : 0);
-        }
+        if (R.count > 0) set_mode(R, ext);
         if (dt != dt_cached) {
             // relaxation factors minus one over dt, relatively accurate for
             // short steps (r = log2(e)/T, so -dt/T = -dt r ln 2)
@@ -630,22 +656,33 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
 }
 
 // One batch of a persistent kernel: every warp of the CTA steps its own spin
-// range [wb, we) of one phantom through the same record stream (TMA tiles
-// shared by the CTA, restarted per batch; `g0` counts the tiles the CTA
-// consumed before) and writes its per-sample sums to `row` (if not null).
-// Returns false if a tile never arrived (status set, copies waited for).
+// range [wb, we) of one phantom through records [rb, re) of one record
+// stream (TMA tiles shared by the CTA, restarted per batch; `g0` counts the
+// tiles the CTA consumed before) and writes its per-sample sums to `row` (if
+// not null). A walk that does not start at record 0 resumes from the
+// checkpoint `state` (inside an RF run, the run's header `rf_hdr` sets the
+// RF path exactly as an unsplit walk had it);
+// one that stops before the end saves it there. Returns false if a tile never
+// arrived (status set, copies waited for).
 template <int S>
 __device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const uint32_t (&bar)[2], uint64_t& g0,
                                            const float* __restrict__ p32, int64_t np, const Rec32* grec,
-                                           int64_t n_rec, const float (&ext)[4], int used, int64_t wb,
-                                           int64_t we, float2* __restrict__ row, int* status) {
+                                           int64_t n_rec, int64_t rb, int64_t re, float* state, int64_t rf_hdr,
+                                           const float (&ext)[4], int used, int64_t wb, int64_t we,
+                                           float2* __restrict__ row, int* status) {
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int64_t n_tiles = (n_rec + kTile - 1) / kTile;
+    const Rec32* base = grec + rb;
+    const int64_t n_walk = re - rb;
+    const int64_t n_tiles = (n_walk + kTile - 1) / kTile;
     Spins<S> sp;
     sp.load(p32, np, wb + lane, 32, we);
+    if (state && rb > 0) {
+        sp.load_state(state, np);
+        if (rf_hdr >= 0) sp.set_mode(grec[rf_hdr], ext);
+    }
     if (tid == 0) {
-        for (int64_t t = 0; t < 2 && t < n_tiles; ++t) issue_tile(s_rec, bar, grec, n_rec, t, g0 + t);
+        for (int64_t t = 0; t < 2 && t < n_tiles; ++t) issue_tile(s_rec, bar, base, n_walk, t, g0 + t);
     }
     for (int64_t t = 0; t < n_tiles; ++t) {
         const uint64_t g = g0 + t;
@@ -659,7 +696,7 @@ __device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const uint32_t
             }
             return false;
         }
-        const int nr = static_cast<int>(min(static_cast<int64_t>(kTile), n_rec - t * kTile));
+        const int nr = static_cast<int>(min(static_cast<int64_t>(kTile), n_walk - t * kTile));
         for (int r = 0; r < nr; ++r) {
             const Rec32& R = s_rec[b][r];
             const int type = R.type;
@@ -681,9 +718,10 @@ __device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const uint32_t
         __syncthreads();  // everyone is done with tile buffer b
         if (tid == 0 && t + 2 < n_tiles) {
             fence_proxy_async_smem();
-            issue_tile(s_rec, bar, grec, n_rec, t + 2, g + 2);
+            issue_tile(s_rec, bar, base, n_walk, t + 2, g + 2);
         }
     }
+    if (state && re < n_rec) sp.save_state(state, np);
     g0 += static_cast<uint64_t>(n_tiles);
     return true;
 }
@@ -729,8 +767,8 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_kernel(const __grid_
             ie = A.item_begin[item + 1];
             row = static_cast<float2*>(A.partial) + item * A.n_adc;
         }
-        if (!walk_batch<S>(s_rec, bar, g0, A.p32, A.n_pad, static_cast<const Rec32*>(A.rec), A.n_rec, A.ext,
-                           A.used, ib, ie, row, A.status))
+        if (!walk_batch<S>(s_rec, bar, g0, A.p32, A.n_pad, static_cast<const Rec32*>(A.rec), A.n_rec, 0, A.n_rec,
+                           nullptr, -1, A.ext, A.used, ib, ie, row, A.status))
             return;
     }
 }
@@ -738,8 +776,9 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_kernel(const __grid_
 // ---------------------------------------------------------------------------
 // K4: serving kernel, persistent. Batches come from a table that mixes the
 // simulations admitted by the server: batch = a contiguous spin range of one
-// request's phantom, walked through that request's records; warp w of the
-// batch takes the w-th 32 * S spins and writes row w of the batch's rows.
+// request's phantom, walked through a chunk of that request's records
+// (checkpointed between chunks); warp w of the batch takes the w-th 32 * S
+// spins and writes row w of the batch's rows.
 // Many simulations thereby share one launch; each request's decomposition
 // into batches does not depend on what else is in the launch.
 // ---------------------------------------------------------------------------
@@ -770,7 +809,8 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_batches_kernel(const __gri
         const int64_t we = min(wb + per_warp, D.spin_end);
         float2* row = D.rows + static_cast<int64_t>(warp) * D.n_adc;
         const float ext[4] = {D.ext[0], D.ext[1], D.ext[2], D.ext[3]};
-        if (!walk_batch<S>(s_rec, bar, g0, D.p32, D.n_pad, D.rec, D.n_rec, ext, D.used, wb, we, row, A.status))
+        if (!walk_batch<S>(s_rec, bar, g0, D.p32, D.n_pad, D.rec, D.n_rec, D.rec_begin, D.rec_end, D.state,
+                           D.rf_hdr, ext, D.used, wb, we, row, A.status))
             return;
     }
 }

@@ -54,7 +54,16 @@ struct Req {
     float ext[4] = {0, 0, 0, 0};
     int used = 0;
     double work_per_spin = 0;  // relative cost units per spin (RF step = 1)
-    int64_t n_batches = 0, next_batch = 0, batches_done = 0;
+    int64_t n_batches = 0;
+    // the record stream is walked in chunks of `chunk` records (checkpointed
+    // between launches); a unit of work = one batch x one chunk
+    int64_t chunk = 0, n_chunks = 1, units_total = 0, units_done = 0;
+    std::vector<double> chunk_work;   // work units per spin of each chunk
+    std::vector<int64_t> chunk_hdr;   // RF run header a chunk starts inside, or -1
+    std::vector<int32_t> batch_next;  // next chunk of each batch
+    std::vector<char> batch_busy;     // batch is in a launch in flight
+    double rem_work = 0;
+    float* dstate = nullptr;
     int launches = 0;
     size_t dev_bytes = 0;
     float* d32 = nullptr;
@@ -67,9 +76,7 @@ struct Req {
     koma_status err = KOMA_OK;
     std::string msg;
 
-    double remaining_work() const {
-        return static_cast<double>(n_batches - next_batch) * kBatchSpins * work_per_spin;
-    }
+    double remaining_work() const { return rem_work; }
 };
 
 struct Slot {
@@ -82,7 +89,7 @@ struct Slot {
     cudaGraphNode_t copy = nullptr;
     cudaEvent_t done = nullptr;
     bool busy = false;
-    std::vector<std::pair<Req*, int64_t>> members;
+    std::vector<std::pair<Req*, int32_t>> members;  // (request, batch) per table entry
 };
 
 double now_s() {
@@ -94,6 +101,7 @@ double now_s() {
 
 struct koma_server {
     int device = 0;
+    int64_t chunk = 4096;  // records per chunk of a batch's walk
     size_t budget = 0, used = 0, peak = 0;
     int max_active = 64;
     double launch_work = 0;  // work units per launch (cap)
@@ -129,7 +137,8 @@ size_t req_bytes(const Req* r) {
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     return al(r->h32.size() * sizeof(float)) + al(r->recs.size() * sizeof(koma::Rec32)) +
            al(static_cast<size_t>(r->n_batches) * kWarps * r->n_adc * sizeof(float2)) +
-           al(static_cast<size_t>(r->n_adc) * 2 * sizeof(double));
+           al(static_cast<size_t>(r->n_adc) * 2 * sizeof(double)) +
+           (r->n_chunks > 1 ? al(static_cast<size_t>(3 * r->n_pad) * sizeof(float)) : 0);
 }
 
 void fail_req(Req* r, koma_status st, const std::string& m) {
@@ -149,6 +158,9 @@ koma_status admit(koma_server* S, Req* r) {
         e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->drows), brows, S->pool, S->s_up);
     if (e == cudaSuccess && bsig) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dsig), bsig, S->pool, S->s_up);
     if (e == cudaSuccess && bsig) e = cudaMallocHost(reinterpret_cast<void**>(&r->hsig), bsig);
+    if (e == cudaSuccess && r->n_chunks > 1)
+        e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dstate), static_cast<size_t>(3 * r->n_pad) * sizeof(float),
+                                    S->pool, S->s_up);
     if (e == cudaSuccess) e = cudaMemcpyAsync(r->d32, r->h32.data(), b32, cudaMemcpyHostToDevice, S->s_up);
     if (e == cudaSuccess && brec)
         e = cudaMemcpyAsync(r->drec, r->recs.data(), brec, cudaMemcpyHostToDevice, S->s_up);
@@ -167,6 +179,8 @@ void release_device(koma_server* S, Req* r) {
     if (r->drec) cudaFreeAsync(r->drec, S->s_red);
     if (r->drows) cudaFreeAsync(r->drows, S->s_red);
     if (r->dsig) cudaFreeAsync(r->dsig, S->s_red);
+    if (r->dstate) cudaFreeAsync(r->dstate, S->s_red);
+    r->dstate = nullptr;
     r->d32 = nullptr;
     r->drec = nullptr;
     r->drows = nullptr;
@@ -216,11 +230,13 @@ koma_status make_slot(koma_server* S, Slot& sl, int64_t cap) {
     return KOMA_OK;
 }
 
-// Fill a free slot with batches and launch it. Returns true if launched.
+// Fill a free slot with units (batch x chunk) and launch it. Requests are
+// taken shortest remaining work first; the launch holds at least enough units
+// to fill the GPU (when there are that many) and stops at the work cap.
 bool launch_slot(koma_server* S, Slot& sl) {
     std::vector<Req*> cand;
     for (Req* r : S->active)
-        if (r->state == ADMITTED && r->next_batch < r->n_batches) cand.push_back(r);
+        if (r->state == ADMITTED && r->units_done + 0 < r->units_total) cand.push_back(r);
     if (cand.empty()) return false;
     std::sort(cand.begin(), cand.end(), [](const Req* a, const Req* b) {
         return a->remaining_work() < b->remaining_work() ||
@@ -231,9 +247,11 @@ bool launch_slot(koma_server* S, Slot& sl) {
     double work = 0;
     sl.members.clear();
     for (Req* r : cand) {
-        int64_t take = 0;
-        while (r->next_batch < r->n_batches && nb < sl.cap) {
-            const double w = kBatchSpins * r->work_per_spin;
+        bool took = false;
+        for (int64_t b = 0; b < r->n_batches && nb < sl.cap; ++b) {
+            if (r->batch_busy[b] || r->batch_next[b] >= r->n_chunks) continue;
+            const int32_t c = r->batch_next[b];
+            const double w = kBatchSpins * r->chunk_work[c];
             if (nb >= S->grid && work + w > S->launch_work) break;
             koma::BatchDesc& D = tab[nb++];
             std::memset(&D, 0, sizeof(D));
@@ -241,18 +259,23 @@ bool launch_slot(koma_server* S, Slot& sl) {
             D.n_pad = r->n_pad;
             D.rec = r->drec;
             D.n_rec = r->n_rec;
-            D.rows = r->drows + static_cast<size_t>(r->next_batch) * kWarps * r->n_adc;
+            D.rows = r->drows + static_cast<size_t>(b) * kWarps * r->n_adc;
             D.n_adc = r->n_adc;
-            D.spin_begin = r->next_batch * kBatchSpins;
+            D.spin_begin = b * kBatchSpins;
             D.spin_end = std::min(r->n, D.spin_begin + kBatchSpins);
+            D.rec_begin = static_cast<int64_t>(c) * r->chunk;
+            D.rec_end = std::min(r->n_rec, D.rec_begin + r->chunk);
+            D.state = r->dstate;
+            D.rf_hdr = r->chunk_hdr[c];
             for (int d = 0; d < 4; ++d) D.ext[d] = r->ext[d];
             D.used = r->used;
-            ++r->next_batch;
-            ++take;
+            r->batch_busy[b] = 1;
+            r->rem_work -= w;
+            sl.members.emplace_back(r, static_cast<int32_t>(b));
             work += w;
+            took = true;
         }
-        if (take) {
-            sl.members.emplace_back(r, take);
+        if (took) {
             ++r->launches;
             cudaStreamWaitEvent(sl.st, r->ev_up, 0);  // no-op once the upload is done
         }
@@ -330,7 +353,7 @@ void worker_loop(koma_server* S) {
                 S->used += r->dev_bytes;
                 S->peak = std::max(S->peak, S->used);
                 S->active.push_back(r);
-                if (r->n_batches == 0) finalize(S, r);  // nothing to step
+                if (r->units_total == 0) finalize(S, r);  // nothing to step
             }
             progress = true;
         }
@@ -347,8 +370,10 @@ void worker_loop(koma_server* S) {
                     fail_req(r, KOMA_E_CUDA, cudaGetErrorString(q));
                     continue;
                 }
-                r->batches_done += m.second;
-                if (r->state == ADMITTED && r->batches_done == r->n_batches) finalize(S, r);
+                r->batch_busy[m.second] = 0;
+                ++r->batch_next[m.second];
+                ++r->units_done;
+                if (r->state == ADMITTED && r->units_done == r->units_total) finalize(S, r);
             }
             sl.members.clear();
         }
@@ -424,6 +449,7 @@ extern "C" koma_status koma_server_create(const koma_server_config* cfg, koma_se
     S->max_active = c.max_active > 0 ? c.max_active : 64;
     // default cap: ~4 ms of the serving kernel at ~4.5e11 RF spin-steps/s
     S->launch_work = c.launch_work > 0 ? c.launch_work : 1.8e9;
+    if (c.chunk_records > 0) S->chunk = c.chunk_records;
     S->t0 = now_s();
     int prev = -1;
     cudaGetDevice(&prev);
@@ -491,11 +517,26 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
         r->ext[d] = static_cast<float>(r->max_abs[d] * (1.0 + 1e-6));
         if (r->max_abs[d] > 0) r->used |= 1 << d;
     }
-    double w = 0;
-    for (const koma::Rec32& q : r->recs)
-        w += q.type == koma::REC_ADC ? 1.0 + (q.count & koma::kCountMask) / 8.0 : 1.0;
-    r->work_per_spin = std::max(1.0, w);
     r->n_batches = (r->n_adc > 0 && n > 0) ? (n + kBatchSpins - 1) / kBatchSpins : 0;
+    r->chunk = S->chunk;
+    r->n_chunks = std::max<int64_t>(1, (r->n_rec + r->chunk - 1) / r->chunk);
+    r->chunk_work.assign(static_cast<size_t>(r->n_chunks), 0.0);
+    r->chunk_hdr.assign(static_cast<size_t>(r->n_chunks), -1);
+    int64_t hdr = -1;
+    for (int64_t i = 0; i < r->n_rec; ++i) {
+        const koma::Rec32& q = r->recs[static_cast<size_t>(i)];
+        const int64_t c = i / r->chunk;
+        if (i == c * r->chunk && q.type == koma::REC_RF && q.count == 0) r->chunk_hdr[c] = hdr;
+        if (q.type == koma::REC_RF && q.count > 0) hdr = i;
+        r->chunk_work[c] += q.type == koma::REC_ADC ? 1.0 + (q.count & koma::kCountMask) / 8.0 : 1.0;
+    }
+    double w = 0;
+    for (double cw : r->chunk_work) w += cw;
+    r->work_per_spin = std::max(1.0, w);
+    r->units_total = r->n_batches * r->n_chunks;
+    r->batch_next.assign(static_cast<size_t>(r->n_batches), 0);
+    r->batch_busy.assign(static_cast<size_t>(r->n_batches), 0);
+    r->rem_work = static_cast<double>(r->n_batches) * kBatchSpins * w;
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->stop) {
         delete r;

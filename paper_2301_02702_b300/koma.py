@@ -64,7 +64,7 @@ class SequenceInfo(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_active", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
-                ("launch_work", ctypes.c_double)]
+                ("launch_work", ctypes.c_double), ("chunk_records", ctypes.c_int64)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -433,8 +433,9 @@ class Simulator:
 # continuous-batching server
 # --------------------------------------------------------------------------
 
-def koma_server_create(device: int = 0, mem_budget_bytes: int = 0, max_active: int = 0, launch_work: float = 0.0):
-    cfg = ServerConfig(int(device), int(max_active), int(mem_budget_bytes), float(launch_work))
+def koma_server_create(device: int = 0, mem_budget_bytes: int = 0, max_active: int = 0, launch_work: float = 0.0,
+                       chunk_records: int = 0):
+    cfg = ServerConfig(int(device), int(max_active), int(mem_budget_bytes), float(launch_work), int(chunk_records))
     out = _vp()
     rc = load().koma_server_create(ctypes.byref(cfg), ctypes.byref(out))
     if rc != KOMA_OK:
@@ -483,8 +484,9 @@ def koma_server_destroy(srv):
 class Server:
     """Continuous-batching simulation server on one device (native worker)."""
 
-    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_active: int = 0, launch_work: float = 0.0):
-        self.srv = koma_server_create(device, mem_budget_bytes, max_active, launch_work)
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_active: int = 0, launch_work: float = 0.0,
+                 chunk_records: int = 0):
+        self.srv = koma_server_create(device, mem_budget_bytes, max_active, launch_work, chunk_records)
         self._n_adc = {}
 
     def submit(self, phantom, seq) -> int:

@@ -111,3 +111,21 @@ def test_admission_by_memory_budget():
         assert e.value.status == koma.KOMA_E_NOMEM
     finally:
         srv.close()
+
+
+def test_checkpointed_chunks_equal_unsplit_walk(server):
+    """Walking a sequence in chunks of 37 step records, with the spin state
+    checkpointed in device memory between launches (cuts fall inside RF runs
+    and between samples), gives bitwise the result of the unsplit walk."""
+    reqs = [workload("se128", "small"), workload("epi512", "small"), (random_spins(700, seed=4),
+                                                                       random_sequence(900, seed=5))]
+    whole = [server.wait(server.submit(ph, seq))[0] for ph, seq in reqs]
+    small = koma.Server(0, chunk_records=37)
+    try:
+        parts = [small.wait(small.submit(ph, seq)) for ph, seq in reqs]
+    finally:
+        small.close()
+    for (ph, seq), a, (b, info) in zip(reqs, whole, parts):
+        assert info["launches"] > 1
+        assert np.array_equal(a, b)
+        assert rel_err(b, oracle.simulate(ph, seq)[0]) < TOL32
