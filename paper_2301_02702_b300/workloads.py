@@ -466,6 +466,15 @@ def workload(name: str, scale: str = "full"):
         if full:
             return mrf_dictionary_phantom(), mrf_fisp()
         return mrf_dictionary_phantom(n_t1=10, n_t2=8), mrf_fisp(n_tr=100)
+    if name in ("paper_a", "paper_b"):
+        # the paper's experiments (a)/(b): fully specified phantoms, single-shot
+        # EPI (FOV 230 mm, 100 x 100, TE 100 ms, hard pulse) built from events
+        from .discretize import discretize, epi_blocks, paper_phantom_a, paper_phantom_b
+        ph = paper_phantom_a() if name == "paper_a" else paper_phantom_b()
+        seq = discretize(epi_blocks() if full else epi_blocks(n=20, te=20e-3))
+        if not full:
+            ph = ph.subset(np.arange(0, ph.n, 4))
+        return ph, seq
     raise KeyError(name)
 
 

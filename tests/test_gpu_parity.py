@@ -246,3 +246,15 @@ def test_grouped_kernel_deterministic_and_tuned(sim):
     finally:
         koma.koma_sequence_free(hs)
         koma.koma_phantom_free(hp)
+
+
+@pytest.mark.parametrize("name", ["paper_a", "paper_b"])
+def test_paper_experiments_full_size(sim, name):
+    """The paper's fully specified phantoms (experiments (a) column of four
+    segments, (b) concentric circles with a 200 rad/s offset), single-shot
+    EPI (FOV 230 mm, 100 x 100, TE 100 ms, hard pulse) built by the
+    discretiser, at full size against the oracle."""
+    ph, seq = workload(name, "full")
+    ref = oracle.simulate(ph, seq)
+    for prec, tol in (("fp32", TOL32), ("fp64", TOL64)):
+        assert rel_err(gpu_signal(sim, ph, seq, prec), ref) < tol
