@@ -226,13 +226,14 @@ struct Spins {
     static_assert(S % 2 == 0, "spins are processed in packed pairs");
     static constexpr int NP = S / 2;
     float xh[S], yh[S], zh[S], fh[S], m0[S], r1[S], r2[S];
-    float mx[S], my[S], mz[S], em1[S], em2[S], zr[S], zi[S];
+    float mx[S], my[S], mz[S], em1[S], em2[S], zr[S], zi[S], zr2[S], zi2[S];
     bool wact[S];  // warp-uniform: slot s holds at least one spin of the warp
     int64_t base, end;
     int stride;
     float dt_cached;               // em1/em2 belong to this dt
     int rf_mode;                   // rotation path of the current RF run (uniform)
     float key0, key1, key2, key3;  // zr/zi belong to this (dK, dtau)
+    float kb0, kb1, kb2, kb3;      // zr2/zi2 belong to this one (the previous run's)
 
     __device__ __forceinline__ int64_t index(int s) const { return base + static_cast<int64_t>(s) * stride; }
 
@@ -260,11 +261,15 @@ struct Spins {
             em2[s] = 0.f;
             zr[s] = 1.f;
             zi[s] = 0.f;
+            zr2[s] = 1.f;
+            zi2[s] = 0.f;
         }
         dt_cached = -1.f;
         rf_mode = 0;
         key0 = __int_as_float(0x7fc00000);  // NaN: no rotator yet
         key1 = key2 = key3 = 0.f;
+        kb0 = key0;
+        kb1 = kb2 = kb3 = 0.f;
     }
 
     // One excitation step: rotation about the step's constant field, then
@@ -440,8 +445,14 @@ struct Spins {
             if (uy) F += frac_product(yh[s], v ? P[P32_YL * np + j] : 0.f, kyh, kyl);
             if (uz) F += frac_product(zh[s], v ? P[P32_ZL * np + j] : 0.f, kzh, kzl);
             if (uf) F += frac_product(fh[s], v ? P[P32_FL * np + j] : 0.f, th, tl);
+            // one-shot phase: reduce to [-1/2, 1/2] turn and use the hardware
+            // sine (absolute error ~4e-7, not accumulated: every run and every
+            // materialisation starts from an exact evaluation)
             float sn = 0.f, cs = 1.f;
-            if (ux || uy || uz || uf) sincospi_f32(-2.f * F, &sn, &cs);
+            if (ux || uy || uz || uf) {
+                const float r = F - rintf(F);
+                __sincosf(-6.28318530717958647692f * r, &sn, &cs);
+            }
             const float e2 = exp2f(-th * r2[s]);
             er[s] = e2 * fmaf(mx[s], cs, -my[s] * sn);
             ei[s] = e2 * fmaf(mx[s], sn, my[s] * cs);
@@ -476,16 +487,35 @@ struct Spins {
             return;
         }
         const float dkx = R.a[8], dky = R.a[9], dkz = R.a[10], dtau = R.a[11];
+        // two cached rotators: alternating runs (an EPI's two readout
+        // directions) reuse both
         if (!(dkx == key0 && dky == key1 && dkz == key2 && dtau == key3)) {
+            if (dkx == kb0 && dky == kb1 && dkz == kb2 && dtau == kb3) {
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const float th1 = -fmaf(dkx, xh[s], fmaf(dky, yh[s], fmaf(dkz, zh[s], fh[s] * dtau)));
-                float sn, cs;
-                sincospi_f32(2.f * th1, &sn, &cs);
-                const float mag = exp2f(-dtau * r2[s]);
-                zr[s] = mag * cs;
-                zi[s] = mag * sn;
+                for (int s = 0; s < S; ++s) {
+                    const float a = zr[s], b = zi[s];
+                    zr[s] = zr2[s];
+                    zi[s] = zi2[s];
+                    zr2[s] = a;
+                    zi2[s] = b;
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    zr2[s] = zr[s];
+                    zi2[s] = zi[s];
+                    const float th1 = -fmaf(dkx, xh[s], fmaf(dky, yh[s], fmaf(dkz, zh[s], fh[s] * dtau)));
+                    float sn, cs;
+                    sincospi_f32(2.f * th1, &sn, &cs);
+                    const float mag = exp2f(-dtau * r2[s]);
+                    zr[s] = mag * cs;
+                    zi[s] = mag * sn;
+                }
             }
+            kb0 = key0;
+            kb1 = key1;
+            kb2 = key2;
+            kb3 = key3;
             key0 = dkx;
             key1 = dky;
             key2 = dkz;
