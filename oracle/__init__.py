@@ -59,6 +59,12 @@ def _load():
             lib.oracle_simulate.restype = ctypes.c_int
             lib.oracle_simulate.argtypes = ([ctypes.c_int64] + [dp] * 7 + [i64p, ctypes.c_int64,
                                             ctypes.c_int64] + [dp] * 6 + [u8p, ctypes.c_int, dp, dp])
+            lib.oracle_simulate_moving.restype = ctypes.c_int
+            lib.oracle_simulate_moving.argtypes = ([ctypes.c_int64] + [dp] * 10 + [i64p, ctypes.c_int64,
+                                                   ctypes.c_int64] + [dp] * 6 + [u8p, ctypes.c_int, dp, dp])
+            lib.oracle_rk4_moving.restype = ctypes.c_int
+            lib.oracle_rk4_moving.argtypes = ([ctypes.c_double] * 10 + [ctypes.c_int64] + [dp] * 6
+                                              + [u8p, ctypes.c_int64, dp, dp])
             lib.oracle_rk4.restype = ctypes.c_int
             lib.oracle_rk4.argtypes = ([ctypes.c_double] * 7 + [ctypes.c_int64] + [dp] * 6
                                        + [u8p, ctypes.c_int64, dp, dp])
@@ -82,8 +88,9 @@ def _seq_arrays(seq):
 
 def simulate(phantom, seq, threads: int = 0, return_state: bool = False):
     """Signal of ``phantom`` under ``seq``: complex128 array [n_groups, n_adc]
-    (grouped phantoms sum within each group). With ``return_state`` also the
-    final magnetisation [n, 3] = (Mx, My, Mz)."""
+    (grouped phantoms sum within each group). A phantom attribute
+    ``velocity = (vx, vy, vz)`` (m/s per spin) moves the spins, x(t) = x + v t.
+    With ``return_state`` also the final magnetisation [n, 3] = (Mx, My, Mz)."""
     lib = _load()
     ph = [_d(getattr(phantom, f)) for f in ("x", "y", "z", "pd", "t1", "t2", "dw")]
     n = ph[0].shape[0]
@@ -95,8 +102,11 @@ def simulate(phantom, seq, threads: int = 0, return_state: bool = False):
     n_adc = int(np.count_nonzero(adc))
     sig = np.zeros((n_groups, max(n_adc, 0), 2), dtype=np.float64)
     mf = np.zeros((n, 3), dtype=np.float64) if return_state else None
-    rc = lib.oracle_simulate(
-        n, *[_ptr(a) for a in ph],
+    vel = getattr(phantom, "velocity", None)
+    vel = None if vel is None else [_d(v) for v in vel]  # kept alive through the call
+    vptr = [None, None, None] if vel is None else [_ptr(v) for v in vel]
+    rc = lib.oracle_simulate_moving(
+        n, *[_ptr(a) for a in ph], *vptr,
         None if go_arr is None else _ptr(go_arr, ctypes.c_int64), n_groups,
         n_steps, _ptr(dt), _ptr(gx), _ptr(gy), _ptr(gz), _ptr(b1re), _ptr(b1im),
         _ptr(adc, ctypes.c_uint8), int(threads),
@@ -110,17 +120,20 @@ def simulate(phantom, seq, threads: int = 0, return_state: bool = False):
 
 def rk4(spin, seq, substeps: int):
     """Brute-force RK4 of the Bloch equation for ONE spin (a mapping or object
-    with scalar x, y, z, pd, t1, t2, dw). Returns (signal [n_adc] complex128,
-    final magnetisation [3])."""
+    with scalar x, y, z, pd, t1, t2, dw and optionally vx, vy, vz for a
+    constant velocity). Returns (signal [n_adc] complex128, final
+    magnetisation [3])."""
     lib = _load()
     get = (lambda k: float(spin[k])) if isinstance(spin, dict) else (lambda k: float(getattr(spin, k)))
     dt, gx, gy, gz, b1re, b1im, adc = _seq_arrays(seq)
     n_adc = int(np.count_nonzero(adc))
     sig = np.zeros((max(n_adc, 1), 2))
     mf = np.zeros(3)
-    rc = lib.oracle_rk4(get("x"), get("y"), get("z"), get("pd"), get("t1"), get("t2"), get("dw"),
-                        dt.shape[0], _ptr(dt), _ptr(gx), _ptr(gy), _ptr(gz), _ptr(b1re),
-                        _ptr(b1im), _ptr(adc, ctypes.c_uint8), int(substeps), _ptr(sig), _ptr(mf))
+    v = [float(spin.get(k, 0.0)) if isinstance(spin, dict) else float(getattr(spin, k, 0.0))
+         for k in ("vx", "vy", "vz")]
+    rc = lib.oracle_rk4_moving(get("x"), get("y"), get("z"), get("pd"), get("t1"), get("t2"), get("dw"),
+                               *v, dt.shape[0], _ptr(dt), _ptr(gx), _ptr(gy), _ptr(gz), _ptr(b1re),
+                               _ptr(b1im), _ptr(adc, ctypes.c_uint8), int(substeps), _ptr(sig), _ptr(mf))
     if rc != 0:
         raise ValueError("oracle_rk4 rejected its arguments")
     return (sig[:n_adc, 0] + 1j * sig[:n_adc, 1]), mf

@@ -28,14 +28,17 @@ def shard_phantom(phantom, rank: int, world: int):
     from .workloads import Phantom
     go = getattr(phantom, "group_offsets", None)
     fields = ("x", "y", "z", "pd", "t1", "t2", "dw")
+    vel = getattr(phantom, "velocity", None)
     if go is None:
         lo, hi = shard_range(phantom.n, rank, world)
-        part = Phantom(*(getattr(phantom, f)[lo:hi] for f in fields))
+        part = Phantom(*(getattr(phantom, f)[lo:hi] for f in fields),
+                       velocity=None if vel is None else vel[:, lo:hi])
         return part, (0, 1)
     g_lo, g_hi = shard_range(len(go) - 1, rank, world)
     s_lo, s_hi = int(go[g_lo]), int(go[g_hi])
     part = Phantom(*(getattr(phantom, f)[s_lo:s_hi] for f in fields),
-                   group_offsets=np.asarray(go[g_lo:g_hi + 1]) - s_lo)
+                   group_offsets=np.asarray(go[g_lo:g_hi + 1]) - s_lo,
+                   velocity=None if vel is None else vel[:, s_lo:s_hi])
     return part, (g_lo, g_hi)
 
 

@@ -41,12 +41,17 @@ class Phantom:
     t2: np.ndarray
     dw: np.ndarray  # off-resonance Δω, rad/s
     group_offsets: Optional[np.ndarray] = None  # int64 [n_groups + 1]
+    # motion u(x, t) = v t: per-spin constant velocity [3, n] (m/s), or None
+    velocity: Optional[np.ndarray] = None
 
     def __post_init__(self):
         for f in ("x", "y", "z", "pd", "t1", "t2", "dw"):
             setattr(self, f, np.ascontiguousarray(getattr(self, f), dtype=np.float64))
         if self.group_offsets is not None:
             self.group_offsets = np.ascontiguousarray(self.group_offsets, dtype=np.int64)
+        if self.velocity is not None:
+            self.velocity = np.ascontiguousarray(np.broadcast_to(self.velocity, (3, self.x.shape[0])),
+                                                 dtype=np.float64)
 
     @property
     def n(self) -> int:
@@ -58,7 +63,8 @@ class Phantom:
 
     def subset(self, idx) -> "Phantom":
         idx = np.asarray(idx)
-        return Phantom(*(getattr(self, f)[idx] for f in ("x", "y", "z", "pd", "t1", "t2", "dw")))
+        return Phantom(*(getattr(self, f)[idx] for f in ("x", "y", "z", "pd", "t1", "t2", "dw")),
+                       velocity=None if self.velocity is None else self.velocity[:, idx])
 
     def arrays(self):
         return self.x, self.y, self.z, self.pd, self.t1, self.t2, self.dw

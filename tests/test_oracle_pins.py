@@ -350,3 +350,130 @@ def test_degenerate_inputs():
     none = Phantom(*(np.zeros(0) for _ in range(7)))
     seq = random_sequence(10, seed=62)
     assert np.all(oracle.simulate(none, seq) == 0)
+
+
+# --------------------------------------------------------------------------
+# motion: x(t) = x + v t (the phantom's motion field u(x, t), Section
+# "Overview"; Eq. "B definition" with G(t).x(t); the constant-velocity
+# displacement of the paper's experiment (d))
+# --------------------------------------------------------------------------
+
+def moving_spin(v, **kw):
+    ph = one_spin(**kw)
+    ph.velocity = np.reshape(np.asarray(v, dtype=np.float64), (3, 1))
+    return ph
+
+
+def test_motion_zero_velocity_is_static():
+    """A phantom that moves with v = 0 gives the static result."""
+    seq = random_sequence(400, seed=71)
+    ph = random_spins(40, seed=72)
+    still = oracle.simulate(ph, seq)
+    ph.velocity = np.zeros((3, ph.n))
+    assert np.max(np.abs(oracle.simulate(ph, seq) - still)) < 1e-12 * np.max(np.abs(still))
+
+
+@pytest.mark.parametrize("v", [0.1, -0.37, 1.5])
+def test_motion_bipolar_flow_phase(v):
+    """Phase-contrast flow encoding: a bipolar pair of trapezoid lobes with
+    areas +A and -A, centroids T apart, has zero net area and first moment
+    -A T (each lobe's moment is its area times its centroid time). A static
+    spin ends with no phase; one moving at v along the gradient gets the
+    phase +gamma v A T, wherever it starts."""
+    g, ramp, flat = 0.02, 0.2e-3, 1.0e-3
+    area = g * (flat + ramp)
+    T = 2 * ramp + flat  # centroid of lobe 2 minus that of lobe 1
+    b = SequenceBuilder()
+    hard(b, np.pi / 2, 1e-12, 0.0)
+    b.steps(1, 0.3e-3)
+    for amp in (g, -g):
+        b.steps(4, ramp / 4, [amp, 0, 0])
+        b.steps(5, flat / 5)
+        b.steps(4, ramp / 4, [0, 0, 0])
+    b.steps(1, 0.1e-3, adc=True)
+    seq = b.build()
+    for x0 in (0.0, 0.031):
+        still = oracle.simulate(one_spin(x=x0), seq)[0, 0]
+        moving = oracle.simulate(moving_spin([v, 0, 0], x=x0), seq)[0, 0]
+        assert abs(np.angle(still / 1j)) < 1e-8
+        assert abs(moving / still - np.exp(1j * GAMMA * v * area * T)) < 1e-9
+        assert abs(abs(moving) - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("v", [0.1, -0.8])
+def test_motion_constant_gradient_quadratic_phase(v):
+    """Under a constant gradient G a spin at x0 + v t precesses at
+    -gamma G (x0 + v t): its FID phase after the pulse (ending at t_p) is
+    -gamma G [x0 (t - t_p) + v (t^2 - t_p^2) / 2]. Long 1 ms steps make any
+    quadrature that is not exact for the quadratic integrand fail."""
+    G = 0.004
+    tp = 1e-12
+    n = 40
+    dt = np.concatenate([[tp], np.full(n, 1e-3)])
+    b1 = np.zeros(n + 1, complex)
+    b1[0] = hard_pulse_b1(np.pi / 2, tp)
+    adc = np.concatenate([[0, 0], np.ones(n, np.uint8)])
+    seq = Sequence(dt, np.full(n + 2, G), np.zeros(n + 2), np.zeros(n + 2), b1, adc)
+    x0 = 0.012
+    sig = oracle.simulate(moving_spin([v, 0, 0], x=x0), seq)[0]
+    t = tp + 1e-3 * np.arange(1, 41)
+    phase = -GAMMA * G * (x0 * (t - tp) + v * (t * t - tp * tp) / 2)
+    assert np.max(np.abs(sig - 1j * np.exp(1j * phase))) < 1e-8
+
+
+def test_motion_time_origin():
+    """Starting the clock earlier by an idle interval T (no RF, no gradient,
+    equilibrium magnetisation) with the spin T v further back is the same
+    experiment."""
+    seq = random_sequence(300, seed=73)
+    idle = Sequence(np.full(3, 0.7e-3), np.zeros(4), np.zeros(4), np.zeros(4), np.zeros(3, complex),
+                    np.zeros(4, np.uint8))
+    ph = random_spins(30, seed=74)
+    rng = np.random.default_rng(75)
+    ph.velocity = rng.uniform(-0.5, 0.5, (3, ph.n))
+    shifted = ph.subset(np.arange(ph.n))
+    T = idle.duration
+    shifted.x = ph.x - ph.velocity[0] * T
+    shifted.y = ph.y - ph.velocity[1] * T
+    shifted.z = ph.z - ph.velocity[2] * T
+    seq0 = Sequence(seq.dt, seq.gx * 0 + seq.gx, seq.gy, seq.gz, seq.b1, seq.adc)
+    seq0.gx[0] = seq0.gy[0] = seq0.gz[0] = 0.0  # the idle interval joins at zero gradient
+    seq0 = Sequence(seq0.dt, seq0.gx, seq0.gy, seq0.gz, seq0.b1, seq0.adc)
+    a = oracle.simulate(ph, seq0)
+    b = oracle.simulate(shifted, idle.concat(seq0))
+    assert np.max(np.abs(a - b)) < 1e-10 * np.max(np.abs(a))
+
+
+def test_motion_matches_rk4():
+    """Moving spins through RF (a soft pulse with a gradient) and precession
+    with piecewise-linear gradients, against RK4 of Eq. 1 with x(t) = x + v t
+    inside the field. Short RF steps keep the midpoint position's error below
+    the bound; the precession phase is exact."""
+    rng = np.random.default_rng(76)
+    b = SequenceBuilder()
+    b.steps(1, 1e-12, [0.0, 0.0, 0.003])
+    b.steps(20, 2e-6, b1=hard_pulse_b1(0.8, 40e-6, 0.2))
+    for _ in range(8):
+        b.steps(int(rng.integers(1, 5)), float(rng.uniform(20e-6, 100e-6)),
+                rng.uniform(-0.005, 0.005, 3), adc=True)
+    b.steps(2, 40e-6, [0, 0, 0])
+    b.steps(1, 1e-12, b1=hard_pulse_b1(2.0, 1e-12, 1.0))
+    b.steps(6, 100e-6, [0.004, -0.005, 0.002], adc=True)
+    seq = b.build()
+    ph = random_spins(6, seed=77)
+    # no relaxation: the soft pulse's steps are then exact rotations but for
+    # the spin's motion within a step
+    ph.t1[:] = INF
+    ph.t2[:] = INF
+    ph.velocity = rng.uniform(-1.0, 1.0, (3, ph.n))
+    for j in range(ph.n):
+        spin = _spin_dict(ph, j)
+        spin.update(vx=ph.velocity[0, j], vy=ph.velocity[1, j], vz=ph.velocity[2, j])
+        sig, m = oracle.simulate(ph.subset([j]), seq, return_state=True)
+        r_sig, r_m = oracle.rk4(spin, seq, substeps=1000)
+        assert np.max(np.abs(sig[0] - r_sig)) < 1e-6, j
+        assert np.max(np.abs(m[0] - r_m)) < 1e-6, j
+        # and the motion matters at this size
+        still = oracle.simulate(Phantom(*(np.atleast_1d(spin[k]) for k in ("x", "y", "z", "pd", "t1", "t2", "dw"))),
+                                seq)[0]
+        assert np.max(np.abs(still - r_sig)) > 1e-2
