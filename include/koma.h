@@ -142,6 +142,25 @@ int64_t koma_phantom_n_groups(const koma_phantom *ph);
 koma_status koma_phantom_free(koma_phantom *ph);
 
 /*
+ * Motion (the phantom's motion field u(x, t), Section "Overview", entering
+ * the field as G(t).x(t) in Eq. "B definition"; experiment (d) moves the
+ * object at a constant 0.1 m/s): give every spin a constant velocity, so
+ * that x_j(t) = x_j + v_j t with t measured from t_0 of the sequence.
+ *   vx, vy, vz  host FP64 [n] (m/s), finite; all three NULL makes the
+ *               phantom static again.
+ * Copied synchronously; the library owns the device copy until
+ * koma_phantom_free. A moving phantom runs on the motion kernels of
+ * koma_simulate (FP32: the phase from t_ref to t is 2 pi (K.x + K1.v + df tau)
+ * with the first gradient moment K1 = gammabar * integral of G(s) s ds; an RF
+ * step takes the spin's position at the step midpoint; FP64 likewise).
+ * koma_simulate_static and the server take static phantoms only.
+ * Errors: KOMA_E_INVALID (NULL phantom, one or two NULL arrays, non-finite
+ *   velocity), KOMA_E_NOMEM, KOMA_E_CUDA.
+ */
+koma_status koma_phantom_set_motion(koma_phantom *ph, const double *vx, const double *vy,
+                                    const double *vz);
+
+/*
  * Upload a discretised sequence (the DiscreteSequence of Section
  * "Simulation blocks, Regime Switching, and Sequence-Aware Time Stepping")
  * of n_steps steps between time points t_0 .. t_{n_steps}:
@@ -175,11 +194,20 @@ koma_status koma_sequence_free(koma_sequence *seq);
  * Host-only planning (no device, no context): validate a sequence and run
  * the preprocessing of koma_sequence_upload, reporting the step-class
  * counts in `info`. If rec_out is not NULL it receives the FP64 step records,
- * 16 doubles each ([type, count, first sample, 13 payload values]; payload
- * as documented for the upload), and rec_capacity (records) must be at
- * least info->n_records. Record types: 0 = RF step, 1 = move the reference
- * time (materialise precession), 2 = run of ADC samples. Errors:
- * KOMA_E_INVALID as for koma_sequence_upload, or capacity too small.
+ * 17 doubles each ([type, count, first sample, 14 payload values]), and
+ * rec_capacity (records) must be at least info->n_records. Payload, times
+ * relative to the reference time t_ref (end of the last RF step, or t_0):
+ *   RF (0):   gammabar dt Gbar (3, turns/m), gammabar dt B1 (2, turns),
+ *             dt, t_mid (the step's midpoint time, s)
+ *   PREC (1): K (3, turns/m), tau (s), K1 (3, turns s/m)
+ *   ADC (2):  K, tau of the first sample, dK (3), dtau, K1 of the first
+ *             sample (3), dK1_0 (3): sample l sits at K + l dK,
+ *             tau + l dtau, K1 + l dK1_0 + l (l - 1)/2 dtau dK
+ * with K = gammabar * integral of G since t_ref and K1 = gammabar *
+ * integral of G(s) s ds since t_ref (s absolute time from t_0). Record
+ * types: 0 = RF step, 1 = move the reference time (materialise
+ * precession), 2 = run of ADC samples. Errors: KOMA_E_INVALID as for
+ * koma_sequence_upload, or capacity too small.
  */
 koma_status koma_sequence_plan(int64_t n_steps, const double *dt, const double *gx,
                                const double *gy, const double *gz, const double *b1_re,

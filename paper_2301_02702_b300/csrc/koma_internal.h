@@ -60,10 +60,22 @@ struct alignas(16) Rec32 {
 };
 static_assert(sizeof(Rec32) == 64, "Rec32 must be 64 bytes");
 
+// Motion (the phantom's u(x, t) as a constant velocity, x(t) = x + v t, t
+// from t_0): the phase from t_ref to t becomes
+//   2 pi (K.x + K1.v + df tau),  K1 = gammabar * integral from t_ref to t of G(s) s ds
+// (turns s/m; s is absolute time, trapezoid-exact per step for linear G).
+// Within an ADC run of uniformly spaced samples under a gradient that
+// repeats from one sample interval to the next (a constant readout
+// gradient), the K1 increment of interval l is dK1_0 + l dtau dK, so the
+// per-sample phase increment grows linearly in l. The host only joins
+// samples into a run when their K1 increments follow that rule.
+
 // 128-byte record of the FP64 path (same meaning, FP64 values, no hi/lo).
 //   RF:   a[0..2] gbar*gammabar*dt  a[3..4] B1*gammabar*dt  a[5] dt
-//   PREC: a[0..2] K  a[3] tau
-//   ADC:  a[0..2] K0 a[3] tau0  a[4..6] dK  a[7] dtau
+//         a[6] t_mid (s): the step's midpoint, where a moving spin sits
+//   PREC: a[0..2] K  a[3] tau  a[4..6] K1
+//   ADC:  a[0..2] K0 a[3] tau0  a[4..6] dK  a[7] dtau  a[8..10] K1 of the
+//         first sample  a[11..13] dK1_0 (K1 increment to the second sample)
 struct alignas(16) Rec64 {
     int32_t type;
     int32_t count;
@@ -71,6 +83,20 @@ struct alignas(16) Rec64 {
     double a[14];
 };
 static_assert(sizeof(Rec64) == 128, "Rec64 must be 128 bytes");
+
+// 128-byte record of the FP32 motion kernel: Rec32's fields in a[0..11]
+// (same meaning, run headers included) plus
+//   RF:   a[12] max t_mid over the RF run (header only)   a[13] t_mid (s)
+//   PREC: a[8..13] K1 x, y, z hi/lo
+//   ADC:  a[12..17] K1 hi/lo of the first sample   a[18..23] dK1_0 hi/lo
+//   PREC/ADC term bits: bits 0..3 as Rec32, bits 4..6 K1 x, y, z nonzero.
+struct alignas(16) RecM {
+    int32_t type;
+    int32_t count;
+    int64_t k0;
+    float a[28];
+};
+static_assert(sizeof(RecM) == 128, "RecM must be 128 bytes");
 
 // Per-spin device layout: structure of arrays, each array n_pad long.
 enum P32 : int {
@@ -87,6 +113,9 @@ enum P64 : int {
     P64_M0,
     P64_N
 };
+// Velocities of a moving phantom: FP32 hi/lo block [PV32_N][n_pad] and FP64
+// block [3][n_pad] (m/s).
+enum PV32 : int { PV32_XH = 0, PV32_XL, PV32_YH, PV32_YL, PV32_ZH, PV32_ZL, PV32_N };
 
 struct BlochLaunch {
     int grid = 0;
@@ -108,7 +137,12 @@ struct BlochArgs {
     int64_t n_adc = 0;
     int* status = nullptr;          // device flag word (bit 0: a bounded wait gave up)
     float ext[4] = {0, 0, 0, 0};    // max |x|, |y|, |z| (m), |df| (Hz) over the phantom
-    int used = 0;                   // bit d: coordinate d (x, y, z, df) is nonzero somewhere
+    int used = 0;                   // bit d: coordinate d (x, y, z, df) is nonzero somewhere;
+                                    // bit 4 + d: velocity component d is nonzero somewhere
+    // moving phantoms (motion kernels only)
+    const float* pv32 = nullptr;    // [PV32_N][n_pad]
+    const double* pv64 = nullptr;   // [3][n_pad]
+    float vext[3] = {0, 0, 0};      // max |v_x|, |v_y|, |v_z| (m/s)
 };
 
 struct ItemArgs {
@@ -179,6 +213,12 @@ int host_records32(int64_t n_steps, const double* dt, const double* gx, const do
 // Launch helpers (koma_kernels.cu). Return a cudaError_t as int.
 int launch_bloch_fp32(const BlochArgs& a, const BlochLaunch& L, void* stream);
 int launch_bloch_fp64(const BlochArgs& a, const BlochLaunch& L, void* stream);
+// Moving phantoms: FP32 motion kernel (RecM records, 2 spins per thread) and
+// the FP64 kernel's motion variant (Rec64 records with K1).
+int launch_bloch_motion(const BlochArgs& a, const BlochLaunch& L, void* stream);
+int launch_bloch_fp64_motion(const BlochArgs& a, const BlochLaunch& L, void* stream);
+int motion_ctas_per_sm(int block);
+constexpr int kMotionSpinsPerThread = 2;
 int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream);
 int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, void* stream);
 int items_ctas_per_sm(int spins_per_thread, int block);

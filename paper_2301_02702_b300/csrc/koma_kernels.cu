@@ -846,9 +846,418 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_batches_kernel(const __gri
 }
 
 // ---------------------------------------------------------------------------
+// K5: FP32 kernel for moving phantoms, x(t) = x + v t.
+//
+// The walk of K1 over RecM records. What motion changes:
+//   RF    the step's field uses the spin's position at the step midpoint
+//         t_mid: az = theta_G.(x + v t_mid) + pi dt df.
+//   phase from t_ref to t: 2 pi (K.x + K1.v + df tau), every product in
+//         hi/lo (K1 grows with absolute time, so K1.v can be many turns).
+//   ADC   the phase increment from sample l to l + 1 is phi1 + l phi2 with
+//         phi1 = dK.x + dK1_0.v + df dtau and phi2 = dtau dK.v, so the
+//         per-sample rotator itself turns by e^{-i 2 pi phi2} every sample.
+//         The rotator is evaluated exactly at every kV-th sample and
+//         advanced by that factor in between (at most kV - 1 products).
+// Two spins per thread (one packed pair).
+// ---------------------------------------------------------------------------
+template <int S>
+struct MSpins {
+    static_assert(S % 2 == 0, "spins are processed in packed pairs");
+    static constexpr int NP = S / 2;
+    float xh[S], yh[S], zh[S], fh[S], vxh[S], vyh[S], vzh[S], m0[S], r1[S], r2[S];
+    float mx[S], my[S], mz[S], em1[S], em2[S];
+    bool wact[S];
+    int64_t base, end;
+    int stride;
+    float dt_cached;
+    int rf_mode;
+
+    __device__ __forceinline__ int64_t index(int s) const { return base + static_cast<int64_t>(s) * stride; }
+
+    __device__ __forceinline__ void load(const float* __restrict__ P, const float* __restrict__ V, int64_t np,
+                                         int64_t base_, int stride_, int64_t end_) {
+        base = base_;
+        stride = stride_;
+        end = end_;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int64_t j = index(s);
+            const bool v = j < end;
+            wact[s] = __any_sync(kFull, v);
+            xh[s] = v ? P[P32_XH * np + j] : 0.f;
+            yh[s] = v ? P[P32_YH * np + j] : 0.f;
+            zh[s] = v ? P[P32_ZH * np + j] : 0.f;
+            fh[s] = v ? P[P32_FH * np + j] : 0.f;
+            m0[s] = v ? P[P32_M0 * np + j] : 0.f;
+            r1[s] = v ? P[P32_R1 * np + j] : 0.f;
+            r2[s] = v ? P[P32_R2 * np + j] : 0.f;
+            vxh[s] = v ? V[PV32_XH * np + j] : 0.f;
+            vyh[s] = v ? V[PV32_YH * np + j] : 0.f;
+            vzh[s] = v ? V[PV32_ZH * np + j] : 0.f;
+            mx[s] = 0.f;
+            my[s] = 0.f;
+            mz[s] = m0[s];
+            em1[s] = 0.f;
+            em2[s] = 0.f;
+        }
+        dt_cached = -1.f;
+        rf_mode = 0;
+    }
+
+    // Rotation path of an RF run (header record): the field's z part
+    // vanishes for every spin at every time (uniform rotation), or the
+    // half angle stays <= 0.754 for every spin wherever it has moved by the
+    // run's last midpoint (series path), else the general path.
+    __device__ __forceinline__ void set_mode(const RecM& H, const float (&ext)[4], const float (&vext)[3]) {
+        const float mb = H.a[7], mgx = H.a[8], mgy = H.a[9], mgz = H.a[10], mdt = H.a[11], tmax = H.a[12];
+        const float ex = fmaf(vext[0], tmax, ext[0]), ey = fmaf(vext[1], tmax, ext[1]),
+                    ez = fmaf(vext[2], tmax, ext[2]);
+        const bool same = (mgx == 0.f || ex == 0.f) && (mgy == 0.f || ey == 0.f) && (mgz == 0.f || ez == 0.f) &&
+                          ext[3] == 0.f;
+        const float bound = mb + mgx * ex + mgy * ey + mgz * ez + mdt * 3.14159265358979323846f * ext[3];
+        rf_mode = same ? 2 : (bound <= 0.754f ? 1 : 0);
+    }
+
+    // Rotate slot s by the quaternion (ch, u) (c2 = 2/|q|^2 to first order),
+    // then relax over the step.
+    __device__ __forceinline__ void rotate_relax(int s, float ch, float ux, float uy, float uz, float c2) {
+        const float px = fmaf(uy, mz[s], -uz * my[s]);
+        const float py = fmaf(uz, mx[s], -ux * mz[s]);
+        const float pz = fmaf(ux, my[s], -uy * mx[s]);
+        const float qx = fmaf(uy, pz, -uz * py);
+        const float qy = fmaf(uz, px, -ux * pz);
+        const float qz = fmaf(ux, py, -uy * px);
+        const float nx = fmaf(c2, fmaf(ch, px, qx), mx[s]);
+        const float ny = fmaf(c2, fmaf(ch, py, qy), my[s]);
+        const float nz = fmaf(c2, fmaf(ch, pz, qz), mz[s]);
+        mx[s] = fmaf(em2[s], nx, nx);
+        my[s] = fmaf(em2[s], ny, ny);
+        mz[s] = fmaf(em1[s], nz - m0[s], nz);
+    }
+
+    // One excitation step (quaternion w = cos|theta|, u = -theta sin|theta|/|theta|
+    // of the half-angle vector theta, as in K1; cos and sinc as even series
+    // in |theta|^2 on the SMALL path).
+    template <bool SMALL>
+    __device__ __forceinline__ void rf_slots(float gx, float gy, float gz, float bx, float by, float b2, float dt,
+                                             float tm) {
+        const float pdt = dt * 3.14159265358979323846f;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (!wact[s]) continue;
+            const float px = fmaf(vxh[s], tm, xh[s]), py = fmaf(vyh[s], tm, yh[s]), pz = fmaf(vzh[s], tm, zh[s]);
+            const float az = fmaf(gx, px, fmaf(gy, py, fmaf(gz, pz, fh[s] * pdt)));
+            const float t2 = fmaf(az, az, b2);
+            float ch, nsinc;
+            if (SMALL) {
+                float q = fmaf(t2, -2.75573192239858907e-6f, 1.98412698412698413e-4f);   // -1/9!, 1/7!
+                q = fmaf(q, t2, -8.33333333333333333e-3f);                               // -1/5!
+                q = fmaf(q, t2, 1.66666666666666667e-1f);                                // 1/3!
+                nsinc = fmaf(q, t2, -1.0f);
+                float c = fmaf(t2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);  // -1/10!, 1/8!
+                c = fmaf(c, t2, -1.38888888888888889e-3f);                               // -1/6!
+                c = fmaf(c, t2, 4.16666666666666667e-2f);                                // 1/4!
+                c = fmaf(c, t2, -0.5f);
+                ch = fmaf(c, t2, 1.0f);
+            } else {
+                const float rs = rsqrtf(t2);
+                float sh;
+                sincospi_f32(t2 * rs * 0.318309886183790671538f, &sh, &ch);
+                nsinc = -sh * rs;
+            }
+            const float ux = bx * nsinc, uy = by * nsinc, uz = az * nsinc;
+            const float nq = fmaf(ch, ch, fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+            rotate_relax(s, ch, ux, uy, uz, fmaf(-2.f, nq, 4.f));
+        }
+    }
+
+    __device__ __forceinline__ void rf(const RecM& R, const float (&ext)[4], const float (&vext)[3]) {
+        const float gx = R.a[0], gy = R.a[1], gz = R.a[2];
+        const float bx = R.a[3], by = R.a[4], b2 = R.a[5], dt = R.a[6], tm = R.a[13];
+        if (R.count > 0) set_mode(R, ext, vext);
+        if (dt != dt_cached) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                em1[s] = expm1_f32(-dt * r1[s] * 0.693147180559945309f);
+                em2[s] = expm1_f32(-dt * r2[s] * 0.693147180559945309f);
+            }
+            dt_cached = dt;
+        }
+        if (rf_mode == 2) {
+            const float rs = rsqrtf(b2);
+            float sh, ch;
+            sincospi_f32(b2 * rs * 0.318309886183790671538f, &sh, &ch);
+            const float f = -sh * rs;
+            const float ux = bx * f, uy = by * f;
+            const float c2 = fmaf(-2.f, fmaf(ch, ch, fmaf(ux, ux, uy * uy)), 4.f);
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+                if (wact[s]) rotate_relax(s, ch, ux, uy, 0.f, c2);
+        } else if (rf_mode == 1) {
+            rf_slots<true>(gx, gy, gz, bx, by, b2, dt, tm);
+        } else {
+            rf_slots<false>(gx, gy, gz, bx, by, b2, dt, tm);
+        }
+    }
+
+    // Transverse magnetisation at (K, K1, tau) relative to t_ref:
+    // Mxy(t_ref) e^{-tau/T2} e^{-i 2 pi (K.x + K1.v + df tau)}; hi/lo
+    // products for every term (`koff`: where the record keeps K1).
+    __device__ __forceinline__ void exact(const RecM& R, bool prec, int koff, const float* __restrict__ P,
+                                          const float* __restrict__ V, int64_t np, int used, float (&er)[S],
+                                          float (&ei)[S]) {
+        const int terms = (R.count >> kTermShift) & used;
+        const float th = R.a[6], tl = R.a[7];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            er[s] = 0.f;
+            ei[s] = 0.f;
+            if (!wact[s]) continue;
+            const int64_t j = index(s);
+            const bool v = j < end;
+            float F = 0.f;
+            if (terms & 1) F += frac_product(xh[s], v ? P[P32_XL * np + j] : 0.f, R.a[0], R.a[1]);
+            if (terms & 2) F += frac_product(yh[s], v ? P[P32_YL * np + j] : 0.f, R.a[2], R.a[3]);
+            if (terms & 4) F += frac_product(zh[s], v ? P[P32_ZL * np + j] : 0.f, R.a[4], R.a[5]);
+            if (terms & 8) F += frac_product(fh[s], v ? P[P32_FL * np + j] : 0.f, th, tl);
+            if (terms & 16) F += frac_product(vxh[s], v ? V[PV32_XL * np + j] : 0.f, R.a[koff], R.a[koff + 1]);
+            if (terms & 32) F += frac_product(vyh[s], v ? V[PV32_YL * np + j] : 0.f, R.a[koff + 2], R.a[koff + 3]);
+            if (terms & 64) F += frac_product(vzh[s], v ? V[PV32_ZL * np + j] : 0.f, R.a[koff + 4], R.a[koff + 5]);
+            float sn = 0.f, cs = 1.f;
+            if (terms) {
+                const float r = F - rintf(F);
+                __sincosf(-6.28318530717958647692f * r, &sn, &cs);
+            }
+            const float e2 = exp2f(-th * r2[s]);
+            er[s] = e2 * fmaf(mx[s], cs, -my[s] * sn);
+            ei[s] = e2 * fmaf(mx[s], sn, my[s] * cs);
+            if (prec) {
+                const float e1 = exp2f(-th * r1[s]);
+                mx[s] = er[s];
+                my[s] = ei[s];
+                mz[s] = fmaf(mz[s] - m0[s], e1, m0[s]);
+            }
+        }
+    }
+
+    // ADC record of L samples from (er, ei); sink(i, re, im) gets the warp
+    // sums of sample i on one lane.
+    template <class Sink>
+    __device__ __forceinline__ void adc(const RecM& R, int L, const float* __restrict__ V, int64_t np, int used,
+                                        float (&er)[S], float (&ei)[S], int lane, Sink&& sink) {
+        if (L == 1) {
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                sr += er[s];
+                si += ei[s];
+            }
+            sr = warp_sum(sr);
+            si = warp_sum(si);
+            if (lane == 0) sink(0, sr, si);
+            return;
+        }
+        const float dkx = R.a[8], dky = R.a[9], dkz = R.a[10], dtau = R.a[11];
+        // the increment's linear term exists iff the gradient moves a moving spin
+        const bool quad = (dkx != 0.f && (used & 16)) || (dky != 0.f && (used & 32)) || (dkz != 0.f && (used & 64));
+        float phi1[S], phi2[S], mag[S];
+        f32x2 wr[NP], wi[NP], wn[NP];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int64_t j = index(s);
+            const bool v = j < end;
+            float p = fmaf(dkx, xh[s], fmaf(dky, yh[s], fmaf(dkz, zh[s], fh[s] * dtau)));
+            if (used & 16) p += frac_product(vxh[s], v ? V[PV32_XL * np + j] : 0.f, R.a[18], R.a[19]);
+            if (used & 32) p += frac_product(vyh[s], v ? V[PV32_YL * np + j] : 0.f, R.a[20], R.a[21]);
+            if (used & 64) p += frac_product(vzh[s], v ? V[PV32_ZL * np + j] : 0.f, R.a[22], R.a[23]);
+            phi1[s] = p - rintf(p);
+            phi2[s] = dtau * fmaf(dkx, vxh[s], fmaf(dky, vyh[s], dkz * vzh[s]));
+            mag[s] = exp2f(-dtau * r2[s]);
+        }
+        if (quad) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                float s0, c0, s1, c1;
+                sincospi_f32(-2.f * phi2[2 * p], &s0, &c0);
+                sincospi_f32(-2.f * phi2[2 * p + 1], &s1, &c1);
+                wr[p] = pk(c0, c1);
+                wi[p] = pk(s0, s1);
+                wn[p] = pk(-s0, -s1);
+            }
+        }
+        f32x2 pr[NP], pi_[NP], qr[NP], qi[NP], qn[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            pr[p] = pk(er[2 * p], er[2 * p + 1]);
+            pi_[p] = pk(ei[2 * p], ei[2 * p + 1]);
+        }
+        for (int c = 0; c < L; c += kV) {
+            if (c == 0 || quad) {
+                // rotator of sample c exactly: mag e^{-i 2 pi (phi1 + c phi2)}
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    float zs[2], zc[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int s = 2 * p + h;
+                        float q = fmaf(static_cast<float>(c), phi2[s], phi1[s]);
+                        q -= rintf(q);
+                        sincospi_f32(-2.f * q, &zs[h], &zc[h]);
+                        zs[h] *= mag[s];
+                        zc[h] *= mag[s];
+                    }
+                    qr[p] = pk(zc[0], zc[1]);
+                    qi[p] = pk(zs[0], zs[1]);
+                    qn[p] = pk(-zs[0], -zs[1]);
+                }
+            }
+            float ar[kV], ai[kV];
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                f32x2 sr2 = pr[0], si2 = pi_[0];
+#pragma unroll
+                for (int p = 1; p < NP; ++p) {
+                    sr2 = add2(sr2, pr[p]);
+                    si2 = add2(si2, pi_[p]);
+                }
+                float r0, r1_, i0, i1;
+                unpk(sr2, r0, r1_);
+                unpk(si2, i0, i1);
+                ar[v] = r0 + r1_;
+                ai[v] = i0 + i1;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const f32x2 nr2 = fma2(pr[p], qr[p], mul2(pi_[p], qn[p]));
+                    pi_[p] = fma2(pr[p], qi[p], mul2(pi_[p], qr[p]));
+                    pr[p] = nr2;
+                    if (quad) {
+                        const f32x2 zr2 = fma2(qr[p], wr[p], mul2(qi[p], wn[p]));
+                        qi[p] = fma2(qr[p], wi[p], mul2(qi[p], wr[p]));
+                        qr[p] = zr2;
+                        qn[p] = mul2(qi[p], pk(-1.f, -1.f));
+                    }
+                }
+            }
+            const float sr = reduce_scatter8(ar, lane);
+            const float si = reduce_scatter8(ai, lane);
+            const int vl = (lane >> 2) & 7;
+            if ((lane & 3) == 0 && c + vl < L) sink(c + vl, sr, si);
+        }
+    }
+};
+
+template <int S>
+__global__ void __launch_bounds__(kMaxBlock, 2) bloch_motion_kernel(const __grid_constant__ BlochArgs A) {
+    __shared__ __align__(128) RecM s_rec[2][kTile];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    extern __shared__ __align__(16) float2 s_red_dyn[];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int nthr = blockDim.x;
+    const int nwarps = nthr >> 5;
+    const int cta = blockIdx.x;
+
+    int64_t c_begin, c_end;
+    if (A.cta_begin) {
+        c_begin = A.cta_begin[cta];
+        c_end = A.cta_begin[cta + 1];
+    } else {
+        c_begin = static_cast<int64_t>(cta) * A.spins_per_cta;
+        c_end = min(A.n, c_begin + A.spins_per_cta);
+    }
+    const int64_t np = A.n_pad;
+    MSpins<S> sp;
+    sp.load(A.p32, A.pv32, np, c_begin + tid, nthr, c_end);
+
+    int red_buf = 0;
+    int64_t red_base = 0, red_end = 0;
+    float2* __restrict__ partial = static_cast<float2*>(A.partial) + static_cast<int64_t>(cta) * A.n_adc;
+    auto red_slot = [&](int buf, int w, int i) -> float2& { return s_red_dyn[(buf * nwarps + w) * kRed32 + i]; };
+    auto flush = [&]() {
+        __syncthreads();
+        const int cnt = static_cast<int>(red_end - red_base);
+        for (int i = tid; i < cnt; i += nthr) {
+            float sr = 0.f, si = 0.f;
+            for (int w = 0; w < nwarps; ++w) {
+                const float2 v = red_slot(red_buf, w, i);
+                sr += v.x;
+                si += v.y;
+            }
+            partial[red_base + i] = make_float2(sr, si);
+        }
+        red_buf ^= 1;
+        red_base = red_end;
+    };
+
+    const uint32_t bar[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
+    const RecM* __restrict__ grec = static_cast<const RecM*>(A.rec);
+    const int64_t n_tiles = (A.n_rec + kTile - 1) / kTile;
+    auto issue = [&](int64_t t) {
+        const int64_t nr = min(static_cast<int64_t>(kTile), A.n_rec - t * kTile);
+        tma_load_1d(smem_u32(&s_rec[t & 1][0]), grec + t * kTile, static_cast<uint32_t>(nr * sizeof(RecM)),
+                    bar[t & 1]);
+    };
+    if (tid == 0) {
+        mbar_init(bar[0], 1);
+        mbar_init(bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int64_t t = 0; t < 2 && t < n_tiles; ++t) issue(t);
+    }
+
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        const int b = static_cast<int>(t & 1);
+        const bool ok = mbar_wait_bounded(bar[b], static_cast<uint32_t>((t >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(A.status, 1);
+                mbar_wait_bounded(bar[b], static_cast<uint32_t>((t >> 1) & 1));
+                if (t + 1 < n_tiles) mbar_wait_bounded(bar[b ^ 1], static_cast<uint32_t>(((t + 1) >> 1) & 1));
+            }
+            return;
+        }
+        const int nr = static_cast<int>(min(static_cast<int64_t>(kTile), A.n_rec - t * kTile));
+        for (int r = 0; r < nr; ++r) {
+            const RecM& R = s_rec[b][r];
+            const int type = R.type;
+            if (type == REC_RF) {
+                sp.rf(R, A.ext, A.vext);
+            } else if (type == REC_PREC) {
+                float er[S], ei[S];
+                sp.exact(R, true, 8, A.p32, A.pv32, np, A.used, er, ei);
+            } else if (type == REC_ADC) {
+                const int L = min(max(R.count & kCountMask, 1), kMaxAdcRun);
+                const int64_t k0 = R.k0;
+                if (k0 + L > red_base + kRed32) flush();
+                float er[S], ei[S];
+                sp.exact(R, false, 12, A.p32, A.pv32, np, A.used, er, ei);
+                const int off = static_cast<int>(k0 - red_base);
+                sp.adc(R, L, A.pv32, np, A.used, er, ei, lane,
+                       [&](int i, float sr, float si) { red_slot(red_buf, warp, off + i) = make_float2(sr, si); });
+                red_end = k0 + L;
+            }
+        }
+        __syncthreads();  // everyone is done with tile buffer b
+        if (tid == 0 && t + 2 < n_tiles) {
+            fence_proxy_async_smem();
+            issue(t + 2);
+        }
+    }
+    if (red_end > red_base) flush();
+}
+
+// ---------------------------------------------------------------------------
 // K1d: FP64 Bloch kernel (one spin per thread, every sample evaluated exactly).
 // Records are read from global memory (uniform addresses, L1 broadcast).
+// MOV: the spin moves, x(t) = x + v t: an RF step sees the position at its
+// midpoint t_mid, and a phase from t_ref to t is 2 pi (K.x + K1.v + df tau)
+// with K1 of sample l of a run equal to K1 + l dK1_0 + l (l - 1) / 2 dtau dK.
 // ---------------------------------------------------------------------------
+template <bool MOV>
 __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_constant__ BlochArgs A) {
     __shared__ __align__(16) double2 s_red[2][kMaxWarps][kRed];
     const int tid = threadIdx.x;
@@ -876,6 +1285,12 @@ __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_cons
     const double T1 = v ? P[P64_T1 * np + j] : 1.0;
     const double T2 = v ? P[P64_T2 * np + j] : 1.0;
     const double m0 = v ? P[P64_M0 * np + j] : 0.0;
+    double vx = 0.0, vy = 0.0, vz = 0.0;
+    if (MOV && v) {
+        vx = A.pv64[j];
+        vy = A.pv64[np + j];
+        vz = A.pv64[2 * np + j];
+    }
     double mx = 0.0, my = 0.0, mz = m0, em1 = 0.0, em2 = 0.0, dt_cached = -1.0;
 
     int red_buf = 0;
@@ -908,7 +1323,14 @@ __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_cons
                 em2 = expm1(-dt / T2);
                 dt_cached = dt;
             }
-            const double az = gx * x + gy * y + gz * z + f * dt;
+            double px0 = x, py0 = y, pz0 = z;
+            if (MOV) {
+                const double tm = R.a[6];
+                px0 = fma(vx, tm, x);
+                py0 = fma(vy, tm, y);
+                pz0 = fma(vz, tm, z);
+            }
+            const double az = gx * px0 + gy * py0 + gz * pz0 + f * dt;
             const double an = sqrt(bx * bx + by * by + az * az);
             double sh, ch;
             sincospi(an, &sh, &ch);
@@ -923,7 +1345,8 @@ __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_cons
             my = ny + em2 * ny;
             mz = nz + em1 * (nz - m0);
         } else if (type == REC_PREC) {
-            const double F = R.a[0] * x + R.a[1] * y + R.a[2] * z + f * R.a[3];
+            double F = R.a[0] * x + R.a[1] * y + R.a[2] * z + f * R.a[3];
+            if (MOV) F += R.a[4] * vx + R.a[5] * vy + R.a[6] * vz;
             double sn, cs;
             sincospi(-2.0 * F, &sn, &cs);
             const double e2 = exp(-R.a[3] / T2), e1 = exp(-R.a[3] / T1);
@@ -939,7 +1362,14 @@ __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_cons
             for (int l = 0; l < L; ++l) {
                 const double kx = R.a[0] + l * R.a[4], ky = R.a[1] + l * R.a[5], kz = R.a[2] + l * R.a[6];
                 const double tau = R.a[3] + l * R.a[7];
-                const double F = kx * x + ky * y + kz * z + f * tau;
+                double F = kx * x + ky * y + kz * z + f * tau;
+                if (MOV) {
+                    const double c2 = 0.5 * l * (l - 1) * R.a[7];
+                    const double k1x = R.a[8] + l * R.a[11] + c2 * R.a[4];
+                    const double k1y = R.a[9] + l * R.a[12] + c2 * R.a[5];
+                    const double k1z = R.a[10] + l * R.a[13] + c2 * R.a[6];
+                    F += k1x * vx + k1y * vy + k1z * vz;
+                }
                 double sn, cs;
                 sincospi(-2.0 * F, &sn, &cs);
                 const double e2 = v ? exp(-tau / T2) : 0.0;
@@ -1015,6 +1445,11 @@ cudaError_t launch_fp32(const BlochArgs& a, const BlochLaunch& L, cudaStream_t s
     return cudaGetLastError();
 }
 
+cudaError_t prepare_motion(size_t dyn) {
+    return cudaFuncSetAttribute(bloch_motion_kernel<kMotionSpinsPerThread>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+}
+
 template <int S>
 cudaError_t occupancy_items(int* n, int block) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, bloch_items_kernel<S>, block, 0);
@@ -1057,7 +1492,7 @@ int bloch_ctas_per_sm(bool fp64, int spins_per_thread, int block) {
     int n = 0;
     cudaError_t e;
     if (fp64) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_fp64_kernel, block, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_fp64_kernel<false>, block, 0);
     } else {
         const size_t dyn = fp32_dyn_smem(block);
         switch (spins_per_thread) {
@@ -1079,10 +1514,37 @@ int launch_bloch_fp32(const BlochArgs& a, const BlochLaunch& L, void* stream) {
     }
 }
 
+int motion_ctas_per_sm(int block) {
+    const size_t dyn = fp32_dyn_smem(block);
+    if (prepare_motion(dyn) != cudaSuccess) return -1;
+    int n = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_motion_kernel<kMotionSpinsPerThread>, block,
+                                                         dyn) == cudaSuccess ? n : -1;
+}
+
+int launch_bloch_motion(const BlochArgs& a, const BlochLaunch& L, void* stream) {
+    if (L.block <= 0 || L.block > kMaxBlock || L.block % 32 != 0 || L.grid <= 0 ||
+        L.spins_per_thread != kMotionSpinsPerThread || !a.pv32)
+        return cudaErrorInvalidValue;
+    const size_t dyn = fp32_dyn_smem(L.block);
+    cudaError_t e = prepare_motion(dyn);
+    if (e != cudaSuccess) return e;
+    bloch_motion_kernel<kMotionSpinsPerThread><<<L.grid, L.block, dyn, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError();
+}
+
 int launch_bloch_fp64(const BlochArgs& a, const BlochLaunch& L, void* stream) {
     if (L.block <= 0 || L.block > kMaxBlock || L.block % 32 != 0 || L.grid <= 0 || L.spins_per_thread != 1)
         return cudaErrorInvalidValue;
-    bloch_fp64_kernel<<<L.grid, L.block, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    bloch_fp64_kernel<false><<<L.grid, L.block, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError();
+}
+
+int launch_bloch_fp64_motion(const BlochArgs& a, const BlochLaunch& L, void* stream) {
+    if (L.block <= 0 || L.block > kMaxBlock || L.block % 32 != 0 || L.grid <= 0 || L.spins_per_thread != 1 ||
+        !a.pv64)
+        return cudaErrorInvalidValue;
+    bloch_fp64_kernel<true><<<L.grid, L.block, 0, static_cast<cudaStream_t>(stream)>>>(a);
     return cudaGetLastError();
 }
 

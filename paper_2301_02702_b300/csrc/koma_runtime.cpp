@@ -72,6 +72,11 @@ struct koma_phantom {
     int32_t* d_order = nullptr;
     int32_t* d_group_item = nullptr;
     size_t items_bytes = 0;
+    // motion: per-spin constant velocity (koma_phantom_set_motion)
+    float* pv32 = nullptr;   // [PV32_N][n_pad] hi/lo
+    double* pv64 = nullptr;  // [3][n_pad]
+    double max_v[3] = {0, 0, 0};
+    bool moving() const { return pv32 != nullptr; }
     // configuration chosen by koma_tune for one sequence
     const koma_sequence* tuned_seq = nullptr;
     int64_t tuned_n_rec = -1;
@@ -83,6 +88,7 @@ struct koma_sequence {
     koma_sequence_info info{};
     koma::Rec32* r32 = nullptr;
     koma::Rec64* r64 = nullptr;
+    koma::RecM* rm = nullptr;
     size_t bytes = 0;
     // over RF steps: max |B1| gammabar dt (turns), max |Gbar_d| gammabar dt
     // (turns/m) per axis, max dt (s); bound the per-step rotation |a|
@@ -347,8 +353,62 @@ extern "C" koma_status koma_phantom_free(koma_phantom* ph) {
     dev_free(ctx, ph->p64, static_cast<size_t>(koma::P64_N * ph->n_pad) * sizeof(double));
     if (ph->d_cta_begin) dev_free(ctx, ph->d_cta_begin, ph->table_bytes);
     if (ph->d_items) dev_free(ctx, ph->d_items, ph->items_bytes);
+    dev_free(ctx, ph->pv32, static_cast<size_t>(koma::PV32_N * ph->n_pad) * sizeof(float));
+    dev_free(ctx, ph->pv64, static_cast<size_t>(3 * ph->n_pad) * sizeof(double));
     ctx->live_objects--;
     delete ph;
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_phantom_set_motion(koma_phantom* ph, const double* vx, const double* vy,
+                                               const double* vz) {
+    if (!ph) return KOMA_E_INVALID;
+    koma_ctx* ctx = ph->ctx;
+    const int64_t n = ph->n, np = ph->n_pad;
+    const size_t bv32 = static_cast<size_t>(koma::PV32_N * np) * sizeof(float),
+                 bv64 = static_cast<size_t>(3 * np) * sizeof(double);
+    DeviceGuard g(ctx->device);
+    if (!vx && !vy && !vz) {  // back to a static phantom
+        dev_free(ctx, ph->pv32, bv32);
+        dev_free(ctx, ph->pv64, bv64);
+        ph->pv32 = nullptr;
+        ph->pv64 = nullptr;
+        ph->bytes = static_cast<size_t>(koma::P32_N * np) * sizeof(float) +
+                    static_cast<size_t>(koma::P64_N * np) * sizeof(double);
+        for (double& m : ph->max_v) m = 0.0;
+        return KOMA_OK;
+    }
+    if (n > 0 && (!vx || !vy || !vz))
+        return fail(ctx, KOMA_E_INVALID, "phantom_set_motion: give all three velocity arrays or none");
+    for (int64_t j = 0; j < n; ++j)
+        if (!std::isfinite(vx[j]) || !std::isfinite(vy[j]) || !std::isfinite(vz[j]))
+            return fail(ctx, KOMA_E_INVALID, "phantom_set_motion: non-finite velocity at spin %lld",
+                        static_cast<long long>(j));
+    std::vector<float> h32(static_cast<size_t>(koma::PV32_N * np), 0.f);
+    std::vector<double> h64(static_cast<size_t>(3 * np), 0.0);
+    double mv[3] = {0, 0, 0};
+    const double* v[3] = {vx, vy, vz};
+    for (int d = 0; d < 3; ++d)
+        for (int64_t j = 0; j < n; ++j) {
+            split(v[d][j], &h32[(2 * d) * np + j], &h32[(2 * d + 1) * np + j]);
+            h64[d * np + j] = v[d][j];
+            mv[d] = std::max(mv[d], std::fabs(v[d][j]));
+        }
+    if (!ph->pv32) {
+        koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&ph->pv32), bv32, "phantom_set_motion");
+        if (st == KOMA_OK) st = dev_alloc(ctx, reinterpret_cast<void**>(&ph->pv64), bv64, "phantom_set_motion");
+        if (st != KOMA_OK) {
+            dev_free(ctx, ph->pv32, bv32);
+            ph->pv32 = nullptr;
+            ph->pv64 = nullptr;
+            return st;
+        }
+        ph->bytes += bv32 + bv64;
+    }
+    cudaError_t e = cudaMemcpy(ph->pv32, h32.data(), bv32, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ph->pv64, h64.data(), bv64, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "phantom_set_motion: copy");
+    for (int d = 0; d < 3; ++d) ph->max_v[d] = mv[d];
     return KOMA_OK;
 }
 
@@ -360,6 +420,7 @@ namespace {
 struct RecordBuilder {
     std::vector<koma::Rec32> r32;
     std::vector<koma::Rec64> r64;
+    std::vector<koma::RecM> rm;  // motion records (Rec32 fields + first moments)
     int64_t n_adc = 0;
     int64_t n_runs = 0;
     int64_t n_mat = 0;
@@ -367,9 +428,27 @@ struct RecordBuilder {
     bool run_open = false;
     int64_t run_k0 = 0;
     int run_count = 0;
-    double run_k[3] = {0, 0, 0}, run_tau = 0;    // first sample
-    double run_dk[3] = {0, 0, 0}, run_dtau = 0;  // spacing (valid once count >= 2)
-    double last_k[3] = {0, 0, 0}, last_tau = 0;
+    double run_k[3] = {0, 0, 0}, run_k1[3] = {0, 0, 0}, run_tau = 0;  // first sample
+    double run_dk[3] = {0, 0, 0}, run_dk1[3] = {0, 0, 0}, run_dtau = 0;  // first spacing (count >= 2)
+    double last_k[3] = {0, 0, 0}, last_k1[3] = {0, 0, 0}, last_tau = 0;
+
+    // Motion record carrying `a`'s fields.
+    static koma::RecM extend(const koma::Rec32& a) {
+        koma::RecM m{};
+        m.type = a.type;
+        m.count = a.count;
+        m.k0 = a.k0;
+        for (int i = 0; i < 12; ++i) m.a[i] = a.a[i];
+        return m;
+    }
+
+    // K1 term bits (4..6) of a motion record whose K1 hi/lo starts at a[off]
+    static int k1_bits(const koma::RecM& m, int off) {
+        int b = 0;
+        for (int d = 0; d < 3; ++d)
+            if (m.a[off + 2 * d] != 0.f || m.a[off + 2 * d + 1] != 0.f) b |= 1 << (4 + d);
+        return b;
+    }
 
     void close_run() {
         if (!run_open) return;
@@ -383,14 +462,23 @@ struct RecordBuilder {
             b.a[d] = run_k[d];
             a.a[8 + d] = static_cast<float>(run_count > 1 ? run_dk[d] : 0.0);
             b.a[4 + d] = run_count > 1 ? run_dk[d] : 0.0;
+            b.a[8 + d] = run_k1[d];
+            b.a[11 + d] = run_count > 1 ? run_dk1[d] : 0.0;
         }
         split(run_tau, &a.a[6], &a.a[7]);
         b.a[3] = run_tau;
         a.a[11] = static_cast<float>(run_count > 1 ? run_dtau : 0.0);
         b.a[7] = run_count > 1 ? run_dtau : 0.0;
         a.count = run_count | (term_bits(a) << koma::kTermShift);
+        koma::RecM m = extend(a);
+        for (int d = 0; d < 3; ++d) {
+            split(run_k1[d], &m.a[12 + 2 * d], &m.a[13 + 2 * d]);
+            split(run_count > 1 ? run_dk1[d] : 0.0, &m.a[18 + 2 * d], &m.a[19 + 2 * d]);
+        }
+        m.count = a.count | (k1_bits(m, 12) << koma::kTermShift);
         r32.push_back(a);
         r64.push_back(b);
+        rm.push_back(m);
         ++n_runs;
         run_open = false;
     }
@@ -407,7 +495,8 @@ struct RecordBuilder {
     }
 
     // Give the first record of every run of consecutive RF records the run's
-    // length and maxima (the kernel chooses its rotation path once per run).
+    // length and maxima (the kernel chooses its rotation path once per run);
+    // motion records also get the run's latest midpoint time.
     void mark_rf_runs() {
         size_t i = 0;
         while (i < r32.size()) {
@@ -416,12 +505,13 @@ struct RecordBuilder {
                 continue;
             }
             size_t j = i;
-            float mb = 0.f, mg[3] = {0.f, 0.f, 0.f}, mdt = 0.f;
+            float mb = 0.f, mg[3] = {0.f, 0.f, 0.f}, mdt = 0.f, mt = 0.f;
             while (j < r32.size() && r32[j].type == koma::REC_RF) {
                 const koma::Rec32& q = r32[j];
                 mb = std::max(mb, std::sqrt(q.a[3] * q.a[3] + q.a[4] * q.a[4]));
                 for (int d = 0; d < 3; ++d) mg[d] = std::max(mg[d], std::fabs(q.a[d]));
                 mdt = std::max(mdt, q.a[6]);
+                mt = std::max(mt, rm[j].a[13]);
                 ++j;
             }
             koma::Rec32& h = r32[i];
@@ -429,18 +519,26 @@ struct RecordBuilder {
             h.a[7] = mb * (1.f + 1e-6f);
             for (int d = 0; d < 3; ++d) h.a[8 + d] = mg[d];
             h.a[11] = mdt;
+            koma::RecM& hm = rm[i];
+            hm.count = h.count;
+            for (int k = 7; k < 12; ++k) hm.a[k] = h.a[k];
+            hm.a[12] = mt * (1.f + 1e-6f);
             i = j;
         }
     }
 
-    // A sample at (K, tau) relative to t_ref.
-    void sample(const double k[3], double tau) {
+    // A sample at (K, K1, tau) relative to t_ref.
+    void sample(const double k[3], const double k1[3], double tau) {
         bool joined = false;
         if (run_open && run_count < koma::kMaxAdcRun) {
             const double dk[3] = {k[0] - last_k[0], k[1] - last_k[1], k[2] - last_k[2]};
+            const double dk1[3] = {k1[0] - last_k1[0], k1[1] - last_k1[1], k1[2] - last_k1[2]};
             const double dtau = tau - last_tau;
             if (run_count == 1) {
-                for (int d = 0; d < 3; ++d) run_dk[d] = dk[d];
+                for (int d = 0; d < 3; ++d) {
+                    run_dk[d] = dk[d];
+                    run_dk1[d] = dk1[d];
+                }
                 run_dtau = dtau;
                 joined = true;
             } else {
@@ -451,6 +549,11 @@ struct RecordBuilder {
                 joined = close_to(dk[0], run_dk[0], ktol) && close_to(dk[1], run_dk[1], ktol) &&
                          close_to(dk[2], run_dk[2], ktol) &&
                          close_to(dtau, run_dtau, 1e-15 + 1e-12 * std::fabs(run_dtau));
+                // first moments: interval l = run_count - 1 adds dK1_0 + l dtau dK
+                const double k1tol = 1e-10 + 1e-12 * (std::fabs(k1[0]) + std::fabs(k1[1]) + std::fabs(k1[2]));
+                const double l = static_cast<double>(run_count - 1);
+                for (int d = 0; d < 3 && joined; ++d)
+                    joined = close_to(dk1[d], run_dk1[d] + l * run_dtau * run_dk[d], k1tol);
             }
         }
         if (joined) {
@@ -460,10 +563,16 @@ struct RecordBuilder {
             run_open = true;
             run_k0 = n_adc;
             run_count = 1;
-            for (int d = 0; d < 3; ++d) run_k[d] = k[d];
+            for (int d = 0; d < 3; ++d) {
+                run_k[d] = k[d];
+                run_k1[d] = k1[d];
+            }
             run_tau = tau;
         }
-        for (int d = 0; d < 3; ++d) last_k[d] = k[d];
+        for (int d = 0; d < 3; ++d) {
+            last_k[d] = k[d];
+            last_k1[d] = k1[d];
+        }
         last_tau = tau;
         ++n_adc;
     }
@@ -496,11 +605,14 @@ koma_status build_records(int64_t n_steps, const double* dt, const double* gx, c
     }
     info = koma_sequence_info{};
     info.n_steps = n_steps;
-    double K[3] = {0, 0, 0}, tau = 0.0;  // moment / time since t_ref (FP64)
-    if (adc[0]) rb.sample(K, tau);
+    // moments since t_ref (FP64): K = gammabar int G, K1 = gammabar int G s ds
+    // with s absolute time (t_0 = 0), tau = t - t_ref
+    double K[3] = {0, 0, 0}, K1[3] = {0, 0, 0}, tau = 0.0, t = 0.0;
+    if (adc[0]) rb.sample(K, K1, tau);
     for (int64_t n = 0; n < n_steps; ++n) {
         const double gm[3] = {0.5 * (gx[n] + gx[n + 1]), 0.5 * (gy[n] + gy[n + 1]), 0.5 * (gz[n] + gz[n + 1])};
         const bool rf = b1_re[n] != 0.0 || b1_im[n] != 0.0;
+        const double t_next = t + dt[n];
         if (rf) {
             ++info.n_rf;
             rb.close_run();
@@ -511,12 +623,17 @@ koma_status build_records(int64_t n_steps, const double* dt, const double* gx, c
                 for (int d = 0; d < 3; ++d) {
                     split(K[d], &a.a[2 * d], &a.a[2 * d + 1]);
                     b.a[d] = K[d];
+                    b.a[4 + d] = K1[d];
                 }
                 split(tau, &a.a[6], &a.a[7]);
                 b.a[3] = tau;
                 a.count = RecordBuilder::term_bits(a) << koma::kTermShift;
+                koma::RecM m = RecordBuilder::extend(a);
+                for (int d = 0; d < 3; ++d) split(K1[d], &m.a[8 + 2 * d], &m.a[9 + 2 * d]);
+                m.count = a.count | (RecordBuilder::k1_bits(m, 8) << koma::kTermShift);
                 rb.r32.push_back(a);
                 rb.r64.push_back(b);
+                rb.rm.push_back(m);
                 ++rb.n_mat;
             }
             koma::Rec32 a{};
@@ -538,16 +655,27 @@ koma_status build_records(int64_t n_steps, const double* dt, const double* gx, c
             b.a[3] = bx;
             b.a[4] = by;
             b.a[5] = dt[n];
+            const double t_mid = t + 0.5 * dt[n];
+            b.a[6] = t_mid;
+            koma::RecM m = RecordBuilder::extend(a);
+            m.a[13] = static_cast<float>(t_mid);
             rb.r32.push_back(a);
             rb.r64.push_back(b);
-            for (int d = 0; d < 3; ++d) K[d] = 0.0;
+            rb.rm.push_back(m);
+            for (int d = 0; d < 3; ++d) K[d] = K1[d] = 0.0;
             tau = 0.0;
         } else {
             ++info.n_precess;
-            for (int d = 0; d < 3; ++d) K[d] += kGammaBar * dt[n] * gm[d];
+            const double g0[3] = {gx[n], gy[n], gz[n]}, g1[3] = {gx[n + 1], gy[n + 1], gz[n + 1]};
+            for (int d = 0; d < 3; ++d) {
+                K[d] += kGammaBar * dt[n] * gm[d];
+                // integral of a linear G times s over [t, t_next]
+                K1[d] += kGammaBar * dt[n] / 6.0 * (g0[d] * (2.0 * t + t_next) + g1[d] * (t + 2.0 * t_next));
+            }
             tau += dt[n];
         }
-        if (adc[n + 1]) rb.sample(K, tau);
+        t = t_next;
+        if (adc[n + 1]) rb.sample(K, K1, tau);
     }
     rb.close_run();
     rb.mark_rf_runs();
@@ -573,11 +701,11 @@ extern "C" koma_status koma_sequence_plan(int64_t n_steps, const double* dt, con
         if (rec_capacity < info->n_records) return KOMA_E_INVALID;
         for (int64_t r = 0; r < info->n_records; ++r) {
             const koma::Rec64& q = rb.r64[static_cast<size_t>(r)];
-            double* o = rec_out + 16 * r;
+            double* o = rec_out + 17 * r;
             o[0] = q.type;
             o[1] = q.count;
             o[2] = static_cast<double>(q.k0);
-            for (int i = 0; i < 13; ++i) o[3 + i] = q.a[i];
+            for (int i = 0; i < 14; ++i) o[3 + i] = q.a[i];
         }
     }
     return KOMA_OK;
@@ -607,21 +735,25 @@ extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, cons
         seq->rf_dt = std::max(seq->rf_dt, q.a[5]);
     }
     DeviceGuard g(ctx->device);
-    const size_t b32 = rb.r32.size() * sizeof(koma::Rec32), b64 = rb.r64.size() * sizeof(koma::Rec64);
+    const size_t b32 = rb.r32.size() * sizeof(koma::Rec32), b64 = rb.r64.size() * sizeof(koma::Rec64),
+                 bm = rb.rm.size() * sizeof(koma::RecM);
     koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r32), b32, "sequence_upload");
     if (st == KOMA_OK) st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r64), b64, "sequence_upload");
+    if (st == KOMA_OK) st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->rm), bm, "sequence_upload");
     if (st == KOMA_OK && b32) {
         cudaError_t e = cudaMemcpy(seq->r32, rb.r32.data(), b32, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(seq->r64, rb.r64.data(), b64, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(seq->rm, rb.rm.data(), bm, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) st = cuda_fail(ctx, e, "sequence_upload: copy");
     }
     if (st != KOMA_OK) {
         dev_free(ctx, seq->r32, b32);
         dev_free(ctx, seq->r64, b64);
+        dev_free(ctx, seq->rm, bm);
         delete seq;
         return st;
     }
-    seq->bytes = b32 + b64;
+    seq->bytes = b32 + b64 + bm;
     ctx->live_objects++;
     *out = seq;
     return KOMA_OK;
@@ -642,6 +774,7 @@ extern "C" koma_status koma_sequence_free(koma_sequence* seq) {
     DeviceGuard g(ctx->device);
     dev_free(ctx, seq->r32, static_cast<size_t>(seq->info.n_records) * sizeof(koma::Rec32));
     dev_free(ctx, seq->r64, static_cast<size_t>(seq->info.n_records) * sizeof(koma::Rec64));
+    dev_free(ctx, seq->rm, static_cast<size_t>(seq->info.n_records) * sizeof(koma::RecM));
     ctx->live_objects--;
     delete seq;
     return KOMA_OK;
@@ -659,6 +792,16 @@ void phantom_ext(const koma_phantom* ph, float (&ext)[4], int* used) {
     for (int d = 0; d < 4; ++d) {
         ext[d] = static_cast<float>(ph->max_abs[d] * (1.0 + 1e-6));
         if (ph->max_abs[d] > 0) *used |= 1 << d;
+    }
+}
+
+// Velocity block, extents and used bits of a moving phantom.
+void motion_args(const koma_phantom* ph, koma::BlochArgs& A) {
+    A.pv32 = ph->pv32;
+    A.pv64 = ph->pv64;
+    for (int d = 0; d < 3; ++d) {
+        A.vext[d] = static_cast<float>(ph->max_v[d] * (1.0 + 1e-6));
+        if (ph->max_v[d] > 0) A.used |= 1 << (4 + d);
     }
 }
 
@@ -782,11 +925,12 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
 
 // Launch shape: the grid is a whole number of waves of (SMs x resident CTAs)
 // and every CTA gets the same number of spins, so no SM idles on a tail.
-koma::BlochLaunch choose_launch(const koma_ctx* ctx, int64_t n, bool fp64, int s_fp32 = 4) {
+koma::BlochLaunch choose_launch(const koma_ctx* ctx, int64_t n, bool fp64, int s_fp32 = 4, bool moving = false) {
     koma::BlochLaunch L;
-    const int S = fp64 ? 1 : s_fp32;
+    const int S = fp64 ? 1 : (moving ? koma::kMotionSpinsPerThread : s_fp32);
     const int max_block = koma::bloch_max_block();
-    const int per_sm = std::max(1, koma::bloch_ctas_per_sm(fp64, S, max_block));
+    const int per_sm = std::max(1, moving && !fp64 ? koma::motion_ctas_per_sm(max_block)
+                                                   : koma::bloch_ctas_per_sm(fp64, S, max_block));
     const int64_t slots = static_cast<int64_t>(ctx->sm_count) * per_sm;
     const int64_t wave_spins = slots * max_block * S;
     const int64_t waves = std::max<int64_t>(1, (n + wave_spins - 1) / wave_spins);
@@ -827,13 +971,14 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
         return e == cudaSuccess ? KOMA_OK : cuda_fail(ctx, e, "simulate: memset");
     }
 
-    if (!fp64 && use_items_kernel(ph)) {
+    const bool moving = ph->moving();
+    if (!fp64 && !moving && use_items_kernel(ph)) {
         const bool tuned = ph->tuned_seq == seq && ph->tuned_n_rec == seq->info.n_records;
         ctx->timing_recorded = false;
         return simulate_items(ctx, ph, seq, sig_dev, st, tuned ? ph->tuned_s : 4, tuned ? ph->tuned_block : 256);
     }
     const bool tuned_k1 = ph->tuned_seq == seq && ph->tuned_n_rec == seq->info.n_records && ph->tuned_s > 0;
-    koma::BlochLaunch L = choose_launch(ctx, ph->n, fp64, tuned_k1 ? ph->tuned_s : 4);
+    koma::BlochLaunch L = choose_launch(ctx, ph->n, fp64, tuned_k1 ? ph->tuned_s : 4, moving);
     if (ph->n_groups > 1) {
         // size CTAs for the largest group (groups never share a CTA)
         int64_t gmax = 1;
@@ -856,11 +1001,13 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     A.p64 = ph->p64;
     A.n_pad = ph->n_pad;
     A.n = ph->n;
-    A.rec = fp64 ? static_cast<const void*>(seq->r64) : static_cast<const void*>(seq->r32);
+    A.rec = fp64 ? static_cast<const void*>(seq->r64)
+                 : (moving ? static_cast<const void*>(seq->rm) : static_cast<const void*>(seq->r32));
     A.n_rec = seq->info.n_records;
     A.n_adc = n_adc;
     A.status = ctx->d_status;
     phantom_ext(ph, A.ext, &A.used);
+    if (moving) motion_args(ph, A);
     A.spins_per_cta = L.spins_per_cta;
     koma::ReduceArgs R;
     R.n_adc = n_adc;
@@ -917,7 +1064,11 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
 
     ctx->timing_recorded = false;
     if (ctx->timing) cudaEventRecord(ctx->ev[0], st);
-    int e = fp64 ? koma::launch_bloch_fp64(A, L, stream) : koma::launch_bloch_fp32(A, L, stream);
+    int e;
+    if (moving)
+        e = fp64 ? koma::launch_bloch_fp64_motion(A, L, stream) : koma::launch_bloch_motion(A, L, stream);
+    else
+        e = fp64 ? koma::launch_bloch_fp64(A, L, stream) : koma::launch_bloch_fp32(A, L, stream);
     if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: Bloch kernel launch");
     if (ctx->timing) cudaEventRecord(ctx->ev[1], st);
     e = koma::launch_reduce(R, fp64, stream);
@@ -948,6 +1099,8 @@ extern "C" koma_status koma_simulate_static(const koma_phantom* ph, const koma_s
     if (seq->ctx != ctx) return fail(ctx, KOMA_E_INVALID, "simulate_static: phantom and sequence belong to different contexts");
     if (ph->n_groups > 1)
         return fail(ctx, KOMA_E_INVALID, "simulate_static: grouped phantoms are not supported (use koma_simulate)");
+    if (ph->moving())
+        return fail(ctx, KOMA_E_INVALID, "simulate_static: moving phantoms are not supported (use koma_simulate)");
     const int64_t n_adc = seq->info.n_adc;
     if (n_adc == 0) return KOMA_OK;
     if (!sig_dev) return fail(ctx, KOMA_E_INVALID, "simulate_static: sig_dev is NULL");
@@ -1015,8 +1168,10 @@ extern "C" koma_status koma_tune(koma_ctx* ctx, const koma_phantom* ph_c, const 
         int s, block;
     };
     std::vector<Cand> cands;
-    const bool items = use_items_kernel(ph);
-    if (items)
+    const bool items = !ph->moving() && use_items_kernel(ph);
+    if (ph->moving())
+        cands = {{koma::kMotionSpinsPerThread, 0}};  // one motion kernel shape
+    else if (items)
         cands = {{2, 128}, {2, 256}, {4, 128}, {4, 256}};
     else
         cands = {{2, 0}, {4, 0}};

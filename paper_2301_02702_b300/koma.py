@@ -29,6 +29,7 @@ PRECISIONS = {"fp64": KOMA_FP64, "fp32": KOMA_FP32_SPLITPHASE}
 EXPORTS = (
     "koma_gamma", "koma_version", "koma_init", "koma_destroy", "koma_last_error", "koma_mem_used",
     "koma_phantom_upload", "koma_phantom_n_spins", "koma_phantom_n_groups", "koma_phantom_free",
+    "koma_phantom_set_motion",
     "koma_sequence_upload", "koma_sequence_n_adc", "koma_sequence_n_steps", "koma_sequence_get_info",
     "koma_sequence_free", "koma_sequence_plan", "koma_simulate", "koma_sync", "koma_set_timing",
     "koma_get_timing", "koma_get_launch_info", "koma_simulate_host", "koma_simulate_static", "koma_tune",
@@ -130,6 +131,8 @@ def load(path: Optional[str] = None):
         lib.koma_phantom_n_groups.argtypes = [_vp]
         lib.koma_phantom_free.restype = st
         lib.koma_phantom_free.argtypes = [_vp]
+        lib.koma_phantom_set_motion.restype = st
+        lib.koma_phantom_set_motion.argtypes = [_vp, _dp, _dp, _dp]
         lib.koma_sequence_upload.restype = st
         lib.koma_sequence_upload.argtypes = [_vp, ctypes.c_int64] + [_dp] * 6 + [_u8p, ctypes.POINTER(_vp)]
         lib.koma_sequence_n_adc.restype = ctypes.c_int64
@@ -227,7 +230,7 @@ def koma_mem_used(ctx) -> int:
 
 def koma_phantom_upload(ctx, phantom):
     """Upload a phantom (object with x, y, z, pd, t1, t2, dw and optional
-    group_offsets). Returns the phantom handle."""
+    group_offsets and velocity [3, n]). Returns the phantom handle."""
     arrs = [_f64(getattr(phantom, f)) for f in ("x", "y", "z", "pd", "t1", "t2", "dw")]
     n = arrs[0].shape[0]
     go = getattr(phantom, "group_offsets", None)
@@ -238,7 +241,27 @@ def koma_phantom_upload(ctx, phantom):
                                     None if go_arr is None else _ptr(go_arr, ctypes.c_int64),
                                     n_groups, ctypes.byref(out))
     _check(ctx, rc, "koma_phantom_upload")
+    vel = getattr(phantom, "velocity", None)
+    if vel is not None:
+        try:
+            koma_phantom_set_motion(ctx, out, vel)
+        except KomaError:
+            load().koma_phantom_free(out)
+            raise
     return out
+
+
+def koma_phantom_set_motion(ctx, ph, velocity):
+    """Give an uploaded phantom constant per-spin velocities ``velocity``
+    [3, n] (m/s; x(t) = x + v t), or make it static again with None."""
+    lib = load()
+    if velocity is None:
+        _check(ctx, lib.koma_phantom_set_motion(ph, None, None, None), "koma_phantom_set_motion")
+        return
+    v = [_f64(a) for a in velocity]
+    if len(v) != 3 or any(a.shape != (koma_phantom_n_spins(ph),) for a in v):
+        raise KomaError(KOMA_E_INVALID, "koma_phantom_set_motion: velocity must be [3, n_spins]")
+    _check(ctx, lib.koma_phantom_set_motion(ph, *[_ptr(a) for a in v]), "koma_phantom_set_motion")
 
 
 def koma_phantom_n_spins(ph) -> int:
@@ -292,7 +315,7 @@ def koma_sequence_free(seq):
 def koma_sequence_plan(seq, with_records: bool = False):
     """Host-only preprocessing of a sequence (no GPU needed). Returns the
     step-class counts, and with ``with_records`` also the FP64 records as a
-    [n_records, 16] array ([type, count, first sample, payload...])."""
+    [n_records, 17] array ([type, count, first sample, 14 payload values])."""
     dt, gx, gy, gz, bre, bim, adc = _seq_arrays(seq)
     info = SequenceInfo()
     lib = load()
@@ -302,7 +325,7 @@ def koma_sequence_plan(seq, with_records: bool = False):
         raise KomaError(rc, "koma_sequence_plan rejected the sequence")
     if not with_records:
         return info.as_dict()
-    rec = np.zeros((max(info.n_records, 1), 16), dtype=np.float64)
+    rec = np.zeros((max(info.n_records, 1), 17), dtype=np.float64)
     rc = lib.koma_sequence_plan(dt.shape[0], _ptr(dt), _ptr(gx), _ptr(gy), _ptr(gz), _ptr(bre), _ptr(bim),
                                 _ptr(adc, ctypes.c_uint8), ctypes.byref(info), _ptr(rec), rec.shape[0])
     if rc != KOMA_OK:

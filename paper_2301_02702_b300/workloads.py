@@ -481,6 +481,19 @@ def workload(name: str, scale: str = "full"):
         if not full:
             ph = ph.subset(np.arange(0, ph.n, 4))
         return ph, seq
+    if name == "paper_d":
+        # the paper's experiment (d): a head at the phantoms' 1 mm resolution
+        # (the ellipse head stands in for the BrainWeb brain), no
+        # off-resonance, displaced along y by u_y = v_y t with v_y = 0.1 m/s,
+        # single-shot EPI as in (a)/(b)
+        from .discretize import discretize, epi_blocks
+        ph = ellipse_phantom(n=230 if full else 58, fov=0.23)
+        ph = ph.subset(np.flatnonzero(ph.pd > 0))
+        ph.dw[:] = 0.0
+        v = np.zeros((3, ph.n))
+        v[1] = 0.1
+        ph.velocity = v
+        return ph, discretize(epi_blocks() if full else epi_blocks(n=20, te=20e-3))
     raise KeyError(name)
 
 

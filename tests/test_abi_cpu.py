@@ -64,23 +64,37 @@ def test_plan_rejects_bad_sequences(lib):
 
 
 def _reference_samples(seq: Sequence):
-    """(K [turns/m], tau [s]) of every ADC sample relative to the end of the
-    last RF step before it, by a plain loop over steps (trapezoid rule)."""
+    """(K [turns/m], tau [s], K1 [turns s/m]) of every ADC sample relative
+    to the end of the last RF step before it, by a plain loop over steps:
+    the trapezoid rule for K, and for K1 = gammabar * integral of G(s) s ds
+    Gauss-Legendre quadrature with two nodes per step (exact for the
+    quadratic integrand)."""
     K = np.zeros(3)
+    K1 = np.zeros(3)
     tau = 0.0
+    t = 0.0
     out = []
+    nodes = np.array([-1.0, 1.0]) / np.sqrt(3.0)
     if seq.adc[0]:
-        out.append((K.copy(), tau))
+        out.append((K.copy(), tau, K1.copy()))
     for n in range(seq.n_steps):
+        g0 = np.array([seq.gx[n], seq.gy[n], seq.gz[n]])
+        g1 = np.array([seq.gx[n + 1], seq.gy[n + 1], seq.gz[n + 1]])
+        dt = seq.dt[n]
         if seq.b1[n] != 0:
             K[:] = 0.0
+            K1[:] = 0.0
             tau = 0.0
         else:
-            gm = 0.5 * np.array([seq.gx[n] + seq.gx[n + 1], seq.gy[n] + seq.gy[n + 1], seq.gz[n] + seq.gz[n + 1]])
-            K += GAMMA_BAR * seq.dt[n] * gm
-            tau += seq.dt[n]
+            K += GAMMA_BAR * dt * 0.5 * (g0 + g1)
+            for u in nodes:
+                f = 0.5 * (1.0 + u)
+                s = t + f * dt
+                K1 += GAMMA_BAR * 0.5 * dt * ((1.0 - f) * g0 + f * g1) * s
+            tau += dt
+        t += dt
         if seq.adc[n + 1]:
-            out.append((K.copy(), tau))
+            out.append((K.copy(), tau, K1.copy()))
     return out
 
 
@@ -93,7 +107,8 @@ def _decode_samples(rec):
         a = r[3:]
         assert 1 <= count <= 128
         for l in range(count):
-            out[k0 + l] = (a[0:3] + l * a[4:7], a[3] + l * a[7])
+            out[k0 + l] = (a[0:3] + l * a[4:7], a[3] + l * a[7],
+                           a[8:11] + l * a[11:14] + 0.5 * l * (l - 1) * a[7] * a[4:7])
     return [out[k] for k in range(len(out))]
 
 
@@ -109,9 +124,10 @@ def test_plan_reproduces_sample_moments(lib, name):
     ref = _reference_samples(seq)
     got = _decode_samples(rec)
     assert len(got) == len(ref)
-    for (kr, tr), (kg, tg) in zip(ref, got):
+    for (kr, tr, k1r), (kg, tg, k1g) in zip(ref, got):
         assert np.max(np.abs(kr - kg)) <= 1e-9 * (1 + np.max(np.abs(kr)))
         assert abs(tr - tg) <= 1e-12 * (1 + tr)
+        assert np.max(np.abs(k1r - k1g)) <= 1e-9 * (1 + np.max(np.abs(k1r)))
     # the types appear in the order the steps do: every RF step is a record
     assert int(np.sum(rec[:, 0] == 0)) == seq.n_rf
 
