@@ -39,6 +39,11 @@ TOL = 1e-4
 # to the signal. Steps without RF and without ADC cost nothing (merged).
 FLOPS_RF_STEP = 50
 FLOPS_ADC_SAMPLE = 8
+# moving spins: the RF step's field also moves the position (3 FMA), and an
+# ADC sample also turns the per-sample rotator by its own increment (one
+# more complex product)
+FLOPS_RF_STEP_MOVING = 56
+FLOPS_ADC_SAMPLE_MOVING = 16
 # FP32 peak of the part: 148 SMs x 128 lanes x 2 flops x 2032 MHz (max SM clock)
 SM_COUNT = 148
 PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * 2032e6 / 1e12
@@ -53,6 +58,9 @@ WORKLOAD_TEXT = {
     "serve": "serve: Poisson stream (200 req/s) of simulations with 1e3-1e6 spins (random subsets of the epi512 "
              "and se128 phantoms) and 1e3-1e5 steps (the workloads' sequences truncated or repeated), both "
              "log-uniform, served under a 150 GB device-memory budget",
+    "paper_d": "paper_d: the paper's experiment (d): 230x230 mm head phantom at 1 mm (26,874 spins, no "
+               "off-resonance) moving along y at v_y = 0.1 m/s, single-shot EPI FOV 230 mm 100x100 TE 100 ms with "
+               "a hard 90-deg pulse (10,479 steps, 10,000 ADC samples), motion kernel",
     "mrf": "mrf: FISP fingerprinting dictionary, 250 T1 x 200 T2 log grid = 50,000 entries of U{50..400} "
            "isochromats over one voxel (11,282,781 spins), inversion + 1,000 TRs of 10-15 ms, flip 5-70 deg "
            "(6,002 steps, 1,000 ADC samples per entry), one persistent autotuned launch",
@@ -179,7 +187,9 @@ def measured_traffic(workload: str):
     return e.get("dram_bytes_per_launch")
 
 
-def algorithmic_flops(info: dict, n_spins: int) -> float:
+def algorithmic_flops(info: dict, n_spins: int, moving: bool = False) -> float:
+    if moving:
+        return float(n_spins) * (info["n_rf"] * FLOPS_RF_STEP_MOVING + info["n_adc"] * FLOPS_ADC_SAMPLE_MOVING)
     return float(n_spins) * (info["n_rf"] * FLOPS_RF_STEP + info["n_adc"] * FLOPS_ADC_SAMPLE)
 
 
@@ -452,7 +462,7 @@ def run_ours(args, rank, world, local):
         keep = np.sort(rng.choice(ph.n, min(ph.n, 1536), replace=False))
         pd = np.zeros(ph.n)
         pd[keep] = ph.pd[keep]
-        hm = sim.upload_phantom(Phantom(ph.x, ph.y, ph.z, pd, ph.t1, ph.t2, ph.dw))
+        hm = sim.upload_phantom(Phantom(ph.x, ph.y, ph.z, pd, ph.t1, ph.t2, ph.dw, velocity=ph.velocity))
         with torch.cuda.stream(stream):
             sim.simulate(hm, hs, "fp32", out=out, stream=stream)
         sim.sync(stream)
@@ -523,7 +533,35 @@ def run_ours(args, rank, world, local):
 
     # end to end through the public host API: host arrays in, host signal out
     e2e = None
-    if not args.no_e2e:
+    moving = ph.velocity is not None
+    if not args.no_e2e and moving:
+        # moving phantoms: upload (with the velocities), simulate, copy the
+        # signal back and free, every step, through the Simulator API
+        host_sig = np.empty((ph.n_groups, seq.n_adc), dtype=np.complex128)
+
+        def e2e_step():
+            p_ = sim.upload_phantom(ph)
+            s_ = sim.upload_sequence(seq)
+            sig = sim.simulate(p_, s_, "fp32", stream=stream)
+            sim.sync(stream)
+            host_sig[...] = sig.cpu().numpy()
+            koma.koma_sequence_free(s_)
+            koma.koma_phantom_free(p_)
+
+        e2e_step()
+        n_e2e = max(1, min(args.steps, args.e2e_steps))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        t_e2e = reduce_max((time.perf_counter() - t0) / n_e2e, world)
+        n_pad = max(32, (ph.n + 31) // 32 * 32)
+        h2d = n_pad * (11 * 4 + 7 * 8 + 6 * 4 + 3 * 8) + info["n_records"] * (64 + 128 + 128)
+        e2e = {"value": units * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(ph.n_groups * seq.n_adc * 16),
+               "path": "Simulator: phantom + velocity upload, sequence preprocessing + upload, simulate, "
+                       "signal copy-back, free"}
+    elif not args.no_e2e:
         ctx2 = koma.koma_init(local)
         host_sig = np.empty((ph.n_groups, seq.n_adc), dtype=np.complex128)
         koma.koma_simulate_host(ctx2, ph, seq, koma.KOMA_FP32_SPLITPHASE, out=host_sig)  # warm
@@ -536,7 +574,7 @@ def run_ours(args, rank, world, local):
         t_e2e = reduce_max(t_e2e, world)
         koma.koma_destroy(ctx2)
         n_pad = max(32, (ph.n + 31) // 32 * 32)
-        h2d = n_pad * (11 * 4 + 7 * 8) + info["n_records"] * (64 + 128)
+        h2d = n_pad * (11 * 4 + 7 * 8) + info["n_records"] * (64 + 128 + 128)
         e2e = {"value": units * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(ph.n_groups * seq.n_adc * 16),
                "path": "koma_simulate_host: validation + preprocessing + uploads + simulate + signal copy-back"}
@@ -555,10 +593,10 @@ def run_ours(args, rank, world, local):
                          f"{dt:.1f} s"}
 
     if rank == 0:
-        flops = algorithmic_flops(info, ph.n)
+        flops = algorithmic_flops(info, ph.n, moving)
         k1 = (sum(k1_ms) / len(k1_ms)) if k1_ms else None
         achieved = flops / (k1 / 1e3) / 1e12 if k1 else None
-        kname = "bloch_items_kernel" if grouped else "bloch_fp32_kernel"
+        kname = "bloch_motion_kernel" if moving else ("bloch_items_kernel" if grouped else "bloch_fp32_kernel")
         roof = {"bound": "alu", "kernel": f"{kname}<{launch['spins_per_thread']}>",
                 "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
                 "frac": (achieved / PEAK_FP32_TFLOPS) if achieved else None,
