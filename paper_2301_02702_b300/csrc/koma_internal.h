@@ -211,6 +211,19 @@ int host_records32(int64_t n_steps, const double* dt, const double* gx, const do
                    koma_sequence_info& info, std::string& err);
 
 // Launch helpers (koma_kernels.cu). Return a cudaError_t as int.
+// Phantom conversion: p64 [P64_N][n_pad] holds the raw rows x, y, z, dw
+// (rad/s), T1, T2, pd for spins j < n; writes the FP32 block p32
+// [P32_N][n_pad], replaces row P64_F by df = dw / 2 pi and fills the padding
+// (inert spins: zero state, T1 = T2 = 1 in the FP64 block). It also checks
+// every spin (the upload's input rules) and takes the extents: `cs` must hold
+// first_bad = ~0 and max_bits = 0 before the launch; afterwards first_bad
+// is the lowest invalid spin (~0: none) and max_bits the bit patterns of
+// max |x|, |y|, |z| (m) and |df| (Hz) over the spins.
+struct ConvertStatus {
+    unsigned long long first_bad;
+    unsigned long long max_bits[4];
+};
+int launch_phantom_convert(double* p64, float* p32, int64_t n, int64_t n_pad, ConvertStatus* cs, void* stream);
 int launch_bloch_fp32(const BlochArgs& a, const BlochLaunch& L, void* stream);
 int launch_bloch_fp64(const BlochArgs& a, const BlochLaunch& L, void* stream);
 // Moving phantoms: FP32 motion kernel (RecM records, 2 spins per thread) and

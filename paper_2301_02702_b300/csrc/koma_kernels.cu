@@ -17,6 +17,7 @@
 // sample is the sum of Mxy over spins (Section "GPU/CPU Parallelization").
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -219,7 +220,10 @@ __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
 // ---------------------------------------------------------------------------
 // Per-thread spin set: S spins held in registers for a whole walk of the
 // record stream. Slot s is spin base + s * stride when that is < end. Keeps
-// M(t_ref) = (mx, my, mz) per spin; parameters are loaded once.
+// M(t_ref) = (mx, my, mz) per spin; parameters are loaded once. A slot past
+// the end holds M0 = 0 and zero state and is stepped like the others (its
+// values stay 0): no per-slot branch, so the S spins' dependency chains
+// interleave.
 // ---------------------------------------------------------------------------
 template <int S>
 struct Spins {
@@ -227,7 +231,6 @@ struct Spins {
     static constexpr int NP = S / 2;
     float xh[S], yh[S], zh[S], fh[S], m0[S], r1[S], r2[S];
     float mx[S], my[S], mz[S], em1[S], em2[S], zr[S], zi[S], zr2[S], zi2[S];
-    bool wact[S];  // warp-uniform: slot s holds at least one spin of the warp
     int64_t base, end;
     int stride;
     float dt_cached;               // em1/em2 belong to this dt
@@ -246,7 +249,6 @@ struct Spins {
         for (int s = 0; s < S; ++s) {
             const int64_t j = index(s);
             const bool v = j < end;
-            wact[s] = __any_sync(kFull, v);
             xh[s] = v ? P[P32_XH * np + j] : 0.f;
             yh[s] = v ? P[P32_YH * np + j] : 0.f;
             zh[s] = v ? P[P32_ZH * np + j] : 0.f;
@@ -315,7 +317,6 @@ struct Spins {
         const float pdt = dt * 3.14159265358979323846f;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            if (!wact[s]) continue;
             const float az = fmaf(gx, xh[s], fmaf(gy, yh[s], fmaf(gz, zh[s], fh[s] * pdt)));
             const float t2 = fmaf(az, az, b2);
             float ch, nsinc;  // cos t and -sin(t)/t
@@ -404,7 +405,6 @@ struct Spins {
         const float c2 = fmaf(-2.f, nq, 4.f);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            if (!wact[s]) continue;
             // u = (ux, uy, 0): p = u x v, q = u x p
             const float px = uy * mz[s];
             const float py = -ux * mz[s];
@@ -437,7 +437,6 @@ struct Spins {
         for (int s = 0; s < S; ++s) {
             er[s] = 0.f;
             ei[s] = 0.f;
-            if (!wact[s]) continue;
             const int64_t j = index(s);
             const bool v = j < end;
             float F = 0.f;
@@ -866,7 +865,6 @@ struct MSpins {
     static constexpr int NP = S / 2;
     float xh[S], yh[S], zh[S], fh[S], vxh[S], vyh[S], vzh[S], m0[S], r1[S], r2[S];
     float mx[S], my[S], mz[S], em1[S], em2[S];
-    bool wact[S];
     int64_t base, end;
     int stride;
     float dt_cached;
@@ -883,7 +881,6 @@ struct MSpins {
         for (int s = 0; s < S; ++s) {
             const int64_t j = index(s);
             const bool v = j < end;
-            wact[s] = __any_sync(kFull, v);
             xh[s] = v ? P[P32_XH * np + j] : 0.f;
             yh[s] = v ? P[P32_YH * np + j] : 0.f;
             zh[s] = v ? P[P32_ZH * np + j] : 0.f;
@@ -944,7 +941,6 @@ struct MSpins {
         const float pdt = dt * 3.14159265358979323846f;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            if (!wact[s]) continue;
             const float px = fmaf(vxh[s], tm, xh[s]), py = fmaf(vyh[s], tm, yh[s]), pz = fmaf(vzh[s], tm, zh[s]);
             const float az = fmaf(gx, px, fmaf(gy, py, fmaf(gz, pz, fh[s] * pdt)));
             const float t2 = fmaf(az, az, b2);
@@ -992,7 +988,7 @@ struct MSpins {
             const float c2 = fmaf(-2.f, fmaf(ch, ch, fmaf(ux, ux, uy * uy)), 4.f);
 #pragma unroll
             for (int s = 0; s < S; ++s)
-                if (wact[s]) rotate_relax(s, ch, ux, uy, 0.f, c2);
+                rotate_relax(s, ch, ux, uy, 0.f, c2);
         } else if (rf_mode == 1) {
             rf_slots<true>(gx, gy, gz, bx, by, b2, dt, tm);
         } else {
@@ -1012,7 +1008,6 @@ struct MSpins {
         for (int s = 0; s < S; ++s) {
             er[s] = 0.f;
             ei[s] = 0.f;
-            if (!wact[s]) continue;
             const int64_t j = index(s);
             const bool v = j < end;
             float F = 0.f;
@@ -1384,6 +1379,63 @@ __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_cons
 }
 
 // ---------------------------------------------------------------------------
+// Phantom conversion (upload): the FP32 block from the FP64 rows, element by
+// element. hi = float(v), lo = float(v - hi), log2(e)/T in FP64 then rounded
+// (T = +inf gives 0).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_f64(double v, float* hi, float* lo) {
+    const float h = __double2float_rn(v);
+    *hi = h;
+    *lo = __double2float_rn(v - static_cast<double>(h));
+}
+
+__global__ void __launch_bounds__(256) phantom_convert_kernel(double* __restrict__ p64, float* __restrict__ p32,
+                                                              int64_t n, int64_t np, ConvertStatus* __restrict__ cs) {
+    const double kLog2e = 1.44269504088896340736;
+    double ext[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < np;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (j < n) {
+            const double x = p64[P64_X * np + j], y = p64[P64_Y * np + j], z = p64[P64_Z * np + j];
+            const double dw = p64[P64_F * np + j], t1 = p64[P64_T1 * np + j], t2 = p64[P64_T2 * np + j];
+            const double pd = p64[P64_M0 * np + j];
+            // the upload's input checks: finite x, y, z, dw and pd >= 0; T1, T2 > 0 (+inf allowed)
+            const bool ok = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(dw) && isfinite(pd) && pd >= 0.0 &&
+                            t1 > 0.0 && !isnan(t1) && t2 > 0.0 && !isnan(t2);
+            if (!ok) atomicMin(&cs->first_bad, static_cast<unsigned long long>(j));
+            const double f = dw / (2.0 * 3.14159265358979323846);
+            split_f64(x, &p32[P32_XH * np + j], &p32[P32_XL * np + j]);
+            split_f64(y, &p32[P32_YH * np + j], &p32[P32_YL * np + j]);
+            split_f64(z, &p32[P32_ZH * np + j], &p32[P32_ZL * np + j]);
+            split_f64(f, &p32[P32_FH * np + j], &p32[P32_FL * np + j]);
+            p32[P32_M0 * np + j] = __double2float_rn(pd);
+            p32[P32_R1 * np + j] = __double2float_rn(kLog2e / t1);
+            p32[P32_R2 * np + j] = __double2float_rn(kLog2e / t2);
+            p64[P64_F * np + j] = f;
+            if (ok) {
+                ext[0] = fmax(ext[0], fabs(x));
+                ext[1] = fmax(ext[1], fabs(y));
+                ext[2] = fmax(ext[2], fabs(z));
+                ext[3] = fmax(ext[3], fabs(dw) / (2.0 * 3.14159265358979323846));
+            }
+        } else {
+            for (int r = 0; r < P32_N; ++r) p32[r * np + j] = 0.f;
+            for (int r = 0; r < P64_N; ++r) p64[r * np + j] = (r == P64_T1 || r == P64_T2) ? 1.0 : 0.0;
+        }
+    }
+    // extents: warp maxima, then one atomic per warp on the bit patterns
+    // (non-negative doubles order like their bits as unsigned integers)
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        double v = ext[d];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+        if ((threadIdx.x & 31) == 0 && v > 0.0)
+            atomicMax(&cs->max_bits[d], static_cast<unsigned long long>(__double_as_longlong(v)));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // K2: sig[g][k] = sum over the CTAs c of group g of partial[c][k], in FP64,
 // in a fixed order (deterministic; threadIdx.y strides the CTAs, the eight
 // strided sums are then added in y order).
@@ -1582,6 +1634,14 @@ int static_partials_ptr(int device, void** out) {
     }
     *out = g_static_ptr[device];
     return cudaSuccess;
+}
+
+int launch_phantom_convert(double* p64, float* p32, int64_t n, int64_t n_pad, ConvertStatus* cs, void* stream) {
+    if (n_pad <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n_pad + 255) / 256, 148 * 16);
+    phantom_convert_kernel<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(p64, p32, n,
+                                                                                                         n_pad, cs);
+    return cudaGetLastError();
 }
 
 int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream) {

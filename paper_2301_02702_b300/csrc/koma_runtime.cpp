@@ -12,6 +12,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <condition_variable>
+#include <functional>
+#include <initializer_list>
+#include <mutex>
 #include <limits>
 #include <new>
 #include <string>
@@ -46,6 +50,10 @@ struct koma_ctx {
     bool timing = false;
     bool timing_recorded = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    // pinned double buffer for host-to-device staging of phantom uploads
+    double* stage = nullptr;       // [2][kStageRows][kStageSpins]
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+    koma::ConvertStatus* d_conv = nullptr;  // checks and extents of the last upload
 };
 
 struct koma_phantom {
@@ -157,6 +165,85 @@ inline void split(double v, float* hi, float* lo) {
 
 bool finite_or_posinf(double v) { return std::isfinite(v) || (std::isinf(v) && v > 0); }
 
+// Persistent host worker threads for parallel_for: spawning threads costs
+// tens of microseconds each, a noticeable share of an upload. One job runs
+// at a time; a caller that finds the pool busy spawns its own threads.
+class HostPool {
+  public:
+    static HostPool& get() {
+        static HostPool pool;
+        return pool;
+    }
+    int workers() const { return static_cast<int>(threads_.size()); }
+    // Runs task(t) for t in [0, k) on the workers and the caller; returns
+    // false (nothing run) if another job holds the pool.
+    bool try_run(int k, const std::function<void(int)>& task) {
+        std::unique_lock<std::mutex> job(job_mu_, std::try_to_lock);
+        if (!job.owns_lock()) return false;
+        {
+            std::lock_guard<std::mutex> lock(mu_);
+            task_ = &task;
+            n_tasks_ = k;
+            next_ = 1;  // task 0 runs on the caller
+            done_ = 0;
+            ++epoch_;
+        }
+        cv_.notify_all();
+        task(0);
+        work_loop_caller();
+        std::unique_lock<std::mutex> lock(mu_);
+        done_cv_.wait(lock, [&] { return done_ == n_tasks_ - 1; });
+        task_ = nullptr;
+        return true;
+    }
+
+  private:
+    HostPool() {
+        const unsigned hw = std::max(1u, std::min(std::thread::hardware_concurrency(), 16u));
+        for (unsigned i = 1; i < hw; ++i) threads_.emplace_back([this] { worker(); });
+    }
+    ~HostPool() {
+        {
+            std::lock_guard<std::mutex> lock(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto& t : threads_) t.join();
+    }
+    // claim and run tasks of the current job; returns when none are left
+    void drain(std::unique_lock<std::mutex>& lock) {
+        while (task_ && next_ < n_tasks_) {
+            const int t = next_++;
+            const std::function<void(int)>* fn = task_;
+            lock.unlock();
+            (*fn)(t);
+            lock.lock();
+            if (++done_ == n_tasks_ - 1) done_cv_.notify_all();
+        }
+    }
+    void work_loop_caller() {
+        std::unique_lock<std::mutex> lock(mu_);
+        drain(lock);
+    }
+    void worker() {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lock(mu_);
+        for (;;) {
+            cv_.wait(lock, [&] { return stop_ || epoch_ != seen; });
+            if (stop_) return;
+            seen = epoch_;
+            drain(lock);
+        }
+    }
+    std::vector<std::thread> threads_;
+    std::mutex job_mu_, mu_;
+    std::condition_variable cv_, done_cv_;
+    const std::function<void(int)>* task_ = nullptr;
+    int n_tasks_ = 0, next_ = 0, done_ = 0;
+    uint64_t epoch_ = 0;
+    bool stop_ = false;
+};
+
 // fn(lo, hi) over [0, n) split across host threads for large n.
 template <class Fn>
 void parallel_for(int64_t n, Fn&& fn) {
@@ -167,6 +254,8 @@ void parallel_for(int64_t n, Fn&& fn) {
         fn(int64_t(0), n);
         return;
     }
+    const std::function<void(int)> task = [&](int t) { fn(n * t / k, n * (t + 1) / k); };
+    if (HostPool::get().try_run(static_cast<int>(k), task)) return;
     std::vector<std::thread> th;
     th.reserve(static_cast<size_t>(k - 1));
     for (int64_t t = 1; t < k; ++t) th.emplace_back(fn, n * t / k, n * (t + 1) / k);
@@ -196,6 +285,64 @@ bool check_spin_values(int64_t n, const double* x, const double* y, const double
         }
     }
     return true;
+}
+
+constexpr int kStageRows = 7;
+constexpr int64_t kStageSpins = int64_t(1) << 17;  // spins per half of the pinned buffer (7 MB)
+
+// Copy `rows` host arrays of n doubles into consecutive rows (pitch np) of
+// the device block `dst`, through the context's pinned double buffer:
+// chunks of kStageSpins spins are packed by host threads into one half while
+// the DMA of the previous chunk reads the other. Copies run on own_stream;
+// the caller synchronises it.
+koma_status stage_rows(koma_ctx* ctx, double* dst, int64_t np, int64_t n,
+                       std::initializer_list<const double*> rows) {
+    const int nr = static_cast<int>(rows.size());
+    if (nr > kStageRows) return fail(ctx, KOMA_E_INVALID, "internal: too many staged rows");
+    if (!ctx->stage) {
+        void* p = nullptr;
+        cudaError_t e = cudaHostAlloc(&p, sizeof(double) * 2 * kStageRows * kStageSpins, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->stage_ev[0], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->stage_ev[1], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&ctx->d_conv), sizeof(koma::ConvertStatus));
+        if (e != cudaSuccess) {
+            if (p) cudaFreeHost(p);
+            for (cudaEvent_t& ev : ctx->stage_ev) {
+                if (ev) cudaEventDestroy(ev);
+                ev = nullptr;
+            }
+            if (ctx->d_conv) cudaFree(ctx->d_conv);
+            ctx->d_conv = nullptr;
+            return cuda_fail(ctx, e, "phantom_upload: pinned staging buffer");
+        }
+        ctx->stage = static_cast<double*>(p);
+    }
+    std::vector<const double*> src(rows);
+    for (int64_t c0 = 0, k = 0; c0 < n; c0 += kStageSpins, ++k) {
+        const int64_t len = std::min(kStageSpins, n - c0);
+        const int b = static_cast<int>(k & 1);
+        double* half = ctx->stage + static_cast<size_t>(b) * kStageRows * kStageSpins;
+        if (k >= 2) {  // the DMA of chunk k - 2 read this half
+            cudaError_t e = cudaEventSynchronize(ctx->stage_ev[b]);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "phantom_upload: staging wait");
+        }
+        parallel_for(static_cast<int64_t>(nr) * len, [&](int64_t lo, int64_t hi) {
+            // flat index i = r * len + j
+            while (lo < hi) {
+                const int64_t r = lo / len, j = lo % len, m = std::min(hi - lo, len - j);
+                std::memcpy(half + r * kStageSpins + j, src[static_cast<size_t>(r)] + c0 + j,
+                            static_cast<size_t>(m) * sizeof(double));
+                lo += m;
+            }
+        });
+        cudaError_t e = cudaMemcpy2DAsync(dst + c0, static_cast<size_t>(np) * sizeof(double), half,
+                                          static_cast<size_t>(kStageSpins) * sizeof(double),
+                                          static_cast<size_t>(len) * sizeof(double), static_cast<size_t>(nr),
+                                          cudaMemcpyHostToDevice, ctx->own_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->stage_ev[b], ctx->own_stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "phantom_upload: staging copy");
+    }
+    return KOMA_OK;
 }
 
 }  // namespace
@@ -243,6 +390,10 @@ extern "C" koma_status koma_destroy(koma_ctx* ctx) {
         if (e) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->stage) cudaFreeHost(ctx->stage);
+    if (ctx->d_conv) cudaFree(ctx->d_conv);
+    for (cudaEvent_t& e : ctx->stage_ev)
+        if (e) cudaEventDestroy(e);
     if (ctx->d_status) cudaFree(ctx->d_status);
     delete ctx;
     return KOMA_OK;
@@ -277,10 +428,6 @@ extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const doubl
         return fail(ctx, KOMA_E_INVALID, "phantom_upload: n_groups = %lld without group_offsets",
                     static_cast<long long>(n_groups));
     }
-    {
-        std::string msg;
-        if (!check_spin_values(n, x, y, z, pd, t1, t2, dw, msg)) return fail(ctx, KOMA_E_INVALID, "%s", msg.c_str());
-    }
     koma_phantom* ph = new (std::nothrow) koma_phantom();
     if (!ph) return fail(ctx, KOMA_E_NOMEM, "phantom_upload: host allocation");
     ph->ctx = ctx;
@@ -288,48 +435,42 @@ extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const doubl
     ph->n_pad = std::max<int64_t>(32, (n + 31) / 32 * 32);
     ph->n_groups = group_offsets ? n_groups : 1;
     if (group_offsets) ph->group_offsets.assign(group_offsets, group_offsets + n_groups + 1);
-
-    std::vector<float> h32(static_cast<size_t>(koma::P32_N * ph->n_pad), 0.f);
-    std::vector<double> h64(static_cast<size_t>(koma::P64_N * ph->n_pad), 0.0);
     const int64_t np = ph->n_pad;
-    parallel_for(n, [&](int64_t lo, int64_t hi) {
-        for (int64_t j = lo; j < hi; ++j) {
-            const double f = dw[j] / (2.0 * kPi);
-            split(x[j], &h32[koma::P32_XH * np + j], &h32[koma::P32_XL * np + j]);
-            split(y[j], &h32[koma::P32_YH * np + j], &h32[koma::P32_YL * np + j]);
-            split(z[j], &h32[koma::P32_ZH * np + j], &h32[koma::P32_ZL * np + j]);
-            split(f, &h32[koma::P32_FH * np + j], &h32[koma::P32_FL * np + j]);
-            h32[koma::P32_M0 * np + j] = static_cast<float>(pd[j]);
-            h32[koma::P32_R1 * np + j] = static_cast<float>(kLog2e / t1[j]);
-            h32[koma::P32_R2 * np + j] = static_cast<float>(kLog2e / t2[j]);
-            h64[koma::P64_X * np + j] = x[j];
-            h64[koma::P64_Y * np + j] = y[j];
-            h64[koma::P64_Z * np + j] = z[j];
-            h64[koma::P64_F * np + j] = f;
-            h64[koma::P64_T1 * np + j] = t1[j];
-            h64[koma::P64_T2 * np + j] = t2[j];
-            h64[koma::P64_M0 * np + j] = pd[j];
-        }
-    });
-    for (int64_t j = 0; j < n; ++j) {
-        ph->max_abs[0] = std::max(ph->max_abs[0], std::fabs(x[j]));
-        ph->max_abs[1] = std::max(ph->max_abs[1], std::fabs(y[j]));
-        ph->max_abs[2] = std::max(ph->max_abs[2], std::fabs(z[j]));
-        ph->max_abs[3] = std::max(ph->max_abs[3], std::fabs(dw[j]) / (2.0 * kPi));
-    }
-    for (int64_t j = n; j < np; ++j) {  // padding: inert spins
-        h64[koma::P64_T1 * np + j] = 1.0;
-        h64[koma::P64_T2 * np + j] = 1.0;
-    }
+
+    // The FP64 block receives the raw rows [x, y, z, dw, T1, T2, pd] through a
+    // pinned double buffer (the host fills one half while the other is in
+    // flight); a device kernel then checks every spin, takes the extents,
+    // builds the FP32 block, turns dw into df and fills the padding.
     DeviceGuard g(ctx->device);
-    const size_t b32 = h32.size() * sizeof(float), b64 = h64.size() * sizeof(double);
+    const size_t b32 = static_cast<size_t>(koma::P32_N * np) * sizeof(float),
+                 b64 = static_cast<size_t>(koma::P64_N * np) * sizeof(double);
     koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&ph->p32), b32, "phantom_upload");
     if (st == KOMA_OK) st = dev_alloc(ctx, reinterpret_cast<void**>(&ph->p64), b64, "phantom_upload");
+    if (st == KOMA_OK) st = stage_rows(ctx, ph->p64, np, n, {x, y, z, dw, t1, t2, pd});
+    koma::ConvertStatus cs{};
     if (st == KOMA_OK) {
-        cudaError_t e = cudaMemcpy(ph->p32, h32.data(), b32, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(ph->p64, h64.data(), b64, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) st = cuda_fail(ctx, e, "phantom_upload: copy");
+        cudaError_t ce = cudaMemsetAsync(ctx->d_conv, 0, sizeof(koma::ConvertStatus), ctx->own_stream);
+        if (ce == cudaSuccess)
+            ce = cudaMemsetAsync(&ctx->d_conv->first_bad, 0xff, sizeof(unsigned long long), ctx->own_stream);
+        if (ce == cudaSuccess)
+            ce = static_cast<cudaError_t>(koma::launch_phantom_convert(ph->p64, ph->p32, n, np, ctx->d_conv,
+                                                                       ctx->own_stream));
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(&cs, ctx->d_conv, sizeof(cs), cudaMemcpyDeviceToHost, ctx->own_stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->own_stream);
+        if (ce != cudaSuccess) st = cuda_fail(ctx, ce, "phantom_upload: conversion");
     }
+    if (st == KOMA_OK && cs.first_bad != ~0ull) {  // report the first offending spin
+        std::string msg;
+        check_spin_values(n, x, y, z, pd, t1, t2, dw, msg);
+        st = fail(ctx, KOMA_E_INVALID, "%s", msg.c_str());
+    }
+    if (st == KOMA_OK)
+        for (int d = 0; d < 4; ++d) {
+            double v;
+            std::memcpy(&v, &cs.max_bits[d], sizeof(v));
+            ph->max_abs[d] = v;
+        }
     if (st != KOMA_OK) {
         dev_free(ctx, ph->p32, b32);
         dev_free(ctx, ph->p64, b64);
