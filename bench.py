@@ -556,7 +556,8 @@ def run_ours(args, rank, world, local):
             e2e_step()
         t_e2e = reduce_max((time.perf_counter() - t0) / n_e2e, world)
         n_pad = max(32, (ph.n + 31) // 32 * 32)
-        h2d = n_pad * (11 * 4 + 7 * 8 + 6 * 4 + 3 * 8) + info["n_records"] * (64 + 128 + 128)
+        # raw FP64 phantom rows, velocity blocks (FP32 hi/lo + FP64), three record streams
+        h2d = ph.n * 7 * 8 + n_pad * (6 * 4 + 3 * 8) + info["n_records"] * (64 + 128 + 128)
         e2e = {"value": units * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(ph.n_groups * seq.n_adc * 16),
                "path": "Simulator: phantom + velocity upload, sequence preprocessing + upload, simulate, "
@@ -573,8 +574,8 @@ def run_ours(args, rank, world, local):
         t_e2e = (time.perf_counter() - t0) / n_e2e
         t_e2e = reduce_max(t_e2e, world)
         koma.koma_destroy(ctx2)
-        n_pad = max(32, (ph.n + 31) // 32 * 32)
-        h2d = n_pad * (11 * 4 + 7 * 8) + info["n_records"] * (64 + 128 + 128)
+        # raw FP64 phantom rows (the FP32 block is built on the device), three record streams
+        h2d = ph.n * 7 * 8 + info["n_records"] * (64 + 128 + 128)
         e2e = {"value": units * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(ph.n_groups * seq.n_adc * 16),
                "path": "koma_simulate_host: validation + preprocessing + uploads + simulate + signal copy-back"}

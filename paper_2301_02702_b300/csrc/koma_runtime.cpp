@@ -14,7 +14,6 @@
 #include <cstring>
 #include <condition_variable>
 #include <functional>
-#include <initializer_list>
 #include <mutex>
 #include <limits>
 #include <new>
@@ -50,10 +49,7 @@ struct koma_ctx {
     bool timing = false;
     bool timing_recorded = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    // pinned double buffer for host-to-device staging of phantom uploads
-    double* stage = nullptr;       // [2][kStageRows][kStageSpins]
-    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
-    koma::ConvertStatus* d_conv = nullptr;  // checks and extents of the last upload
+    koma::ConvertStatus* d_conv = nullptr;  // checks and extents of the last phantom upload
 };
 
 struct koma_phantom {
@@ -287,64 +283,6 @@ bool check_spin_values(int64_t n, const double* x, const double* y, const double
     return true;
 }
 
-constexpr int kStageRows = 7;
-constexpr int64_t kStageSpins = int64_t(1) << 17;  // spins per half of the pinned buffer (7 MB)
-
-// Copy `rows` host arrays of n doubles into consecutive rows (pitch np) of
-// the device block `dst`, through the context's pinned double buffer:
-// chunks of kStageSpins spins are packed by host threads into one half while
-// the DMA of the previous chunk reads the other. Copies run on own_stream;
-// the caller synchronises it.
-koma_status stage_rows(koma_ctx* ctx, double* dst, int64_t np, int64_t n,
-                       std::initializer_list<const double*> rows) {
-    const int nr = static_cast<int>(rows.size());
-    if (nr > kStageRows) return fail(ctx, KOMA_E_INVALID, "internal: too many staged rows");
-    if (!ctx->stage) {
-        void* p = nullptr;
-        cudaError_t e = cudaHostAlloc(&p, sizeof(double) * 2 * kStageRows * kStageSpins, cudaHostAllocDefault);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->stage_ev[0], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->stage_ev[1], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&ctx->d_conv), sizeof(koma::ConvertStatus));
-        if (e != cudaSuccess) {
-            if (p) cudaFreeHost(p);
-            for (cudaEvent_t& ev : ctx->stage_ev) {
-                if (ev) cudaEventDestroy(ev);
-                ev = nullptr;
-            }
-            if (ctx->d_conv) cudaFree(ctx->d_conv);
-            ctx->d_conv = nullptr;
-            return cuda_fail(ctx, e, "phantom_upload: pinned staging buffer");
-        }
-        ctx->stage = static_cast<double*>(p);
-    }
-    std::vector<const double*> src(rows);
-    for (int64_t c0 = 0, k = 0; c0 < n; c0 += kStageSpins, ++k) {
-        const int64_t len = std::min(kStageSpins, n - c0);
-        const int b = static_cast<int>(k & 1);
-        double* half = ctx->stage + static_cast<size_t>(b) * kStageRows * kStageSpins;
-        if (k >= 2) {  // the DMA of chunk k - 2 read this half
-            cudaError_t e = cudaEventSynchronize(ctx->stage_ev[b]);
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "phantom_upload: staging wait");
-        }
-        parallel_for(static_cast<int64_t>(nr) * len, [&](int64_t lo, int64_t hi) {
-            // flat index i = r * len + j
-            while (lo < hi) {
-                const int64_t r = lo / len, j = lo % len, m = std::min(hi - lo, len - j);
-                std::memcpy(half + r * kStageSpins + j, src[static_cast<size_t>(r)] + c0 + j,
-                            static_cast<size_t>(m) * sizeof(double));
-                lo += m;
-            }
-        });
-        cudaError_t e = cudaMemcpy2DAsync(dst + c0, static_cast<size_t>(np) * sizeof(double), half,
-                                          static_cast<size_t>(kStageSpins) * sizeof(double),
-                                          static_cast<size_t>(len) * sizeof(double), static_cast<size_t>(nr),
-                                          cudaMemcpyHostToDevice, ctx->own_stream);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->stage_ev[b], ctx->own_stream);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "phantom_upload: staging copy");
-    }
-    return KOMA_OK;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -390,10 +328,7 @@ extern "C" koma_status koma_destroy(koma_ctx* ctx) {
         if (e) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     if (ctx->scratch) cudaFree(ctx->scratch);
-    if (ctx->stage) cudaFreeHost(ctx->stage);
     if (ctx->d_conv) cudaFree(ctx->d_conv);
-    for (cudaEvent_t& e : ctx->stage_ev)
-        if (e) cudaEventDestroy(e);
     if (ctx->d_status) cudaFree(ctx->d_status);
     delete ctx;
     return KOMA_OK;
@@ -437,16 +372,31 @@ extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const doubl
     if (group_offsets) ph->group_offsets.assign(group_offsets, group_offsets + n_groups + 1);
     const int64_t np = ph->n_pad;
 
-    // The FP64 block receives the raw rows [x, y, z, dw, T1, T2, pd] through a
-    // pinned double buffer (the host fills one half while the other is in
-    // flight); a device kernel then checks every spin, takes the extents,
-    // builds the FP32 block, turns dw into df and fills the padding.
+    // The FP64 block receives the caller's rows [x, y, z, dw, T1, T2, pd] as
+    // they are (the driver's pipelined copy from pageable memory measured
+    // faster than packing into pinned memory on the host first); a device
+    // kernel then checks every spin, takes the extents, builds the FP32
+    // block, turns dw into df and fills the padding.
     DeviceGuard g(ctx->device);
     const size_t b32 = static_cast<size_t>(koma::P32_N * np) * sizeof(float),
                  b64 = static_cast<size_t>(koma::P64_N * np) * sizeof(double);
     koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&ph->p32), b32, "phantom_upload");
     if (st == KOMA_OK) st = dev_alloc(ctx, reinterpret_cast<void**>(&ph->p64), b64, "phantom_upload");
-    if (st == KOMA_OK) st = stage_rows(ctx, ph->p64, np, n, {x, y, z, dw, t1, t2, pd});
+    if (st == KOMA_OK && !ctx->d_conv) {
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ctx->d_conv), sizeof(koma::ConvertStatus));
+        if (e != cudaSuccess) {
+            ctx->d_conv = nullptr;
+            st = cuda_fail(ctx, e, "phantom_upload: status word");
+        }
+    }
+    {
+        const double* rows[koma::P64_N] = {x, y, z, dw, t1, t2, pd};  // the order of enum P64
+        for (int r = 0; r < koma::P64_N && st == KOMA_OK && n > 0; ++r) {
+            cudaError_t e = cudaMemcpyAsync(ph->p64 + r * np, rows[r], static_cast<size_t>(n) * sizeof(double),
+                                            cudaMemcpyHostToDevice, ctx->own_stream);
+            if (e != cudaSuccess) st = cuda_fail(ctx, e, "phantom_upload: copy");
+        }
+    }
     koma::ConvertStatus cs{};
     if (st == KOMA_OK) {
         cudaError_t ce = cudaMemsetAsync(ctx->d_conv, 0, sizeof(koma::ConvertStatus), ctx->own_stream);
