@@ -47,6 +47,17 @@ FLOPS_ADC_SAMPLE_MOVING = 16
 # FP32 peak of the part: 148 SMs x 128 lanes x 2 flops x 2032 MHz (max SM clock)
 SM_COUNT = 148
 PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * 2032e6 / 1e12
+# The step-class cost model of the method evaluated per sample (every ADC
+# sample an exact phase evaluation, every RF step a spinor rotation): FP32
+# operations and MUFU operations per spin and step class, with the issue rates
+# measured on B300 by paper_2301_02702_b300/csrc/probe_rates.cu (FFMA 117,
+# MUFU ex2 21 per SM per clock). t_min = max(sum FP32 / R_FP32, sum MUFU /
+# R_MUFU); the kernels do less work than this model (merged precession,
+# per-sample rotator), so t_min / t_kernel can exceed 1.
+MODEL_RF = (50, 3)
+MODEL_ADC = (25, 3)
+PROBE_FFMA_PER_SM_CLK = 117
+PROBE_MUFU_PER_SM_CLK = 21
 
 WORKLOAD_TEXT = {
     "gre32": "gre32: 32x32 grid phantom (1,024 spins), spoiled GRE 32 TRs x 10 ms on a 10 us grid "
@@ -604,6 +615,17 @@ def run_ours(args, rank, world, local):
                 "traffic": measured_traffic(args.workload),
                 "kernel_ms": k1, "algorithmic_flops_per_launch": flops,
                 "peak_source": "FP32 peak 148 SMs x 128 lanes x 2 x 2032 MHz (max SM clock)"}
+        if k1:
+            mhz = (clk or {}).get("sm_mhz") or 2032.0
+            fp32_ops = ph.n * (info["n_rf"] * MODEL_RF[0] + info["n_adc"] * MODEL_ADC[0])
+            mufu_ops = ph.n * (info["n_rf"] * MODEL_RF[1] + info["n_adc"] * MODEL_ADC[1])
+            t_fp32 = fp32_ops / (SM_COUNT * PROBE_FFMA_PER_SM_CLK * mhz * 1e6) * 1e3
+            t_mufu = mufu_ops / (SM_COUNT * PROBE_MUFU_PER_SM_CLK * mhz * 1e6) * 1e3
+            roof["step_model"] = {"fp32_ops": fp32_ops, "mufu_ops": mufu_ops, "t_fp32_ms": t_fp32,
+                                  "t_mufu_ms": t_mufu, "t_min_ms": max(t_fp32, t_mufu),
+                                  "frac": max(t_fp32, t_mufu) / k1,
+                                  "model": "per spin: RF step 50 FP32 + 3 MUFU, ADC sample 25 FP32 + 3 MUFU, "
+                                           "at the probed FFMA/MUFU issue rates and the sampled SM clock"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
