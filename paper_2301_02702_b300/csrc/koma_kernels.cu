@@ -363,14 +363,15 @@ struct Spins {
         const bool same = (mgx == 0.f || ext[0] == 0.f) && (mgy == 0.f || ext[1] == 0.f) &&
                           (mgz == 0.f || ext[2] == 0.f) && ext[3] == 0.f;
         const float bound = mb + mgx * ext[0] + mgy * ext[1] + mgz * ext[2] + mdt * 3.14159265358979323846f * ext[3];
-        rf_mode = same ? 2 : (bound <= 0.754f ? 1 : 0);
+        rf_mode = same ? (mb <= 0.754f ? 3 : 2) : (bound <= 0.754f ? 1 : 0);
     }
 
     // RF record. The first record of a run of RF records carries the run's
     // maxima; with the phantom's extents `ext` (max |x|, |y|, |z| in m, |df|
     // in Hz) they choose, once per run, between: one rotation for all spins
-    // (the field's z part vanishes for every spin), the series path
-    // (|theta| <= 0.754 for every step and spin), or the general path.
+    // (the field's z part vanishes for every spin; by the series when the
+    // run's largest half angle is <= 0.754), the series path (|theta| <= 0.754
+    // for every step and spin), or the general path.
     __device__ __forceinline__ void rf(const Rec32& R, const float (&ext)[4]) {
         const float gx = R.a[0], gy = R.a[1], gz = R.a[2];
         const float bx = R.a[3], by = R.a[4], b2 = R.a[5], dt = R.a[6];
@@ -385,8 +386,8 @@ struct Spins {
             }
             dt_cached = dt;
         }
-        if (rf_mode == 2)
-            rf_uniform(bx, by, b2);
+        if (rf_mode >= 2)
+            rf_uniform(bx, by, b2, rf_mode == 3);
         else if (rf_mode == 1)
             rf_slots<true>(gx, gy, gz, bx, by, b2, dt);
         else
@@ -395,11 +396,26 @@ struct Spins {
 
     // RF step whose rotation is the same for every spin (field in the xy
     // plane): quaternion computed once, applied to every slot, then relaxation.
-    __device__ __forceinline__ void rf_uniform(float bx, float by, float b2) {
-        const float rs = rsqrtf(b2);
-        float sh, ch;
-        sincospi_f32(b2 * rs * 0.318309886183790671538f, &sh, &ch);
-        const float f = -sh * rs;
+    // SMALL (the run's largest |theta| <= 0.754): cos and sin(t)/t by their
+    // even series in t^2 = |theta|^2, as on the per-spin series path.
+    __device__ __forceinline__ void rf_uniform(float bx, float by, float b2, bool small) {
+        float ch, f;
+        if (small) {
+            float q = fmaf(b2, -2.75573192239858907e-6f, 1.98412698412698413e-4f);   // -1/9!, 1/7!
+            q = fmaf(q, b2, -8.33333333333333333e-3f);                               // -1/5!
+            q = fmaf(q, b2, 1.66666666666666667e-1f);                                // 1/3!
+            f = fmaf(q, b2, -1.0f);
+            float c = fmaf(b2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);  // -1/10!, 1/8!
+            c = fmaf(c, b2, -1.38888888888888889e-3f);                               // -1/6!
+            c = fmaf(c, b2, 4.16666666666666667e-2f);                                // 1/4!
+            c = fmaf(c, b2, -0.5f);
+            ch = fmaf(c, b2, 1.0f);
+        } else {
+            const float rs = rsqrtf(b2);
+            float sh;
+            sincospi_f32(b2 * rs * 0.318309886183790671538f, &sh, &ch);
+            f = -sh * rs;
+        }
         const float ux = bx * f, uy = by * f;
         const float nq = fmaf(ch, ch, fmaf(ux, ux, uy * uy));
         const float c2 = fmaf(-2.f, nq, 4.f);
@@ -912,7 +928,7 @@ struct MSpins {
         const bool same = (mgx == 0.f || ex == 0.f) && (mgy == 0.f || ey == 0.f) && (mgz == 0.f || ez == 0.f) &&
                           ext[3] == 0.f;
         const float bound = mb + mgx * ex + mgy * ey + mgz * ez + mdt * 3.14159265358979323846f * ext[3];
-        rf_mode = same ? 2 : (bound <= 0.754f ? 1 : 0);
+        rf_mode = same ? (mb <= 0.754f ? 3 : 2) : (bound <= 0.754f ? 1 : 0);
     }
 
     // Rotate slot s by the quaternion (ch, u) (c2 = 2/|q|^2 to first order),
@@ -979,11 +995,24 @@ struct MSpins {
             }
             dt_cached = dt;
         }
-        if (rf_mode == 2) {
-            const float rs = rsqrtf(b2);
-            float sh, ch;
-            sincospi_f32(b2 * rs * 0.318309886183790671538f, &sh, &ch);
-            const float f = -sh * rs;
+        if (rf_mode >= 2) {
+            float ch, f;
+            if (rf_mode == 3) {
+                float q = fmaf(b2, -2.75573192239858907e-6f, 1.98412698412698413e-4f);   // -1/9!, 1/7!
+                q = fmaf(q, b2, -8.33333333333333333e-3f);                                       // -1/5!
+                q = fmaf(q, b2, 1.66666666666666667e-1f);                                        // 1/3!
+                f = fmaf(q, b2, -1.0f);
+                float c = fmaf(b2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);  // -1/10!, 1/8!
+                c = fmaf(c, b2, -1.38888888888888889e-3f);                                       // -1/6!
+                c = fmaf(c, b2, 4.16666666666666667e-2f);                                        // 1/4!
+                c = fmaf(c, b2, -0.5f);
+                ch = fmaf(c, b2, 1.0f);
+            } else {
+                const float rs = rsqrtf(b2);
+                float sh;
+                sincospi_f32(b2 * rs * 0.318309886183790671538f, &sh, &ch);
+                f = -sh * rs;
+            }
             const float ux = bx * f, uy = by * f;
             const float c2 = fmaf(-2.f, fmaf(ch, ch, fmaf(ux, ux, uy * uy)), 4.f);
 #pragma unroll

@@ -43,6 +43,8 @@ struct koma_ctx {
     size_t scratch_bytes = 0;
     int* d_status = nullptr;  // [0] device status flags, [1] batch counter of the grouped kernel
     cudaStream_t own_stream = nullptr;
+    cudaMemPool_t pool = nullptr;  // device memory of phantoms, sequences and scratch
+    cudaStream_t alloc_stream = nullptr;  // orders the pool's allocations and frees only
     koma_launch_info last{};
     int64_t live_objects = 0;
     // optional kernel timing: events around the Bloch kernel and the reduction
@@ -50,6 +52,7 @@ struct koma_ctx {
     bool timing_recorded = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     koma::ConvertStatus* d_conv = nullptr;  // checks and extents of the last phantom upload
+    koma::ConvertStatus* h_conv = nullptr;  // pinned host copy of *d_conv
 };
 
 struct koma_phantom {
@@ -90,7 +93,7 @@ struct koma_phantom {
 struct koma_sequence {
     koma_ctx* ctx = nullptr;
     koma_sequence_info info{};
-    koma::Rec32* r32 = nullptr;
+    koma::Rec32* r32 = nullptr;  // one allocation: r32, then r64, then rm
     koma::Rec64* r64 = nullptr;
     koma::RecM* rm = nullptr;
     size_t bytes = 0;
@@ -131,13 +134,21 @@ struct DeviceGuard {
     }
 };
 
+// Device memory of phantoms, sequences and scratch comes from the context's
+// memory pool (allocations stay mapped, so an upload-simulate-free cycle
+// does not pay cudaMalloc/cudaFree). Allocations and frees are ordered on a
+// stream of their own that carries no other work, and each completes before
+// the call returns, so a block can be used from any stream at once. A free
+// first waits for the whole device, as cudaFree does (the memory may still
+// be read by a kernel on any stream).
 koma_status dev_alloc(koma_ctx* ctx, void** p, size_t bytes, const char* what) {
     *p = nullptr;
     if (bytes == 0) return KOMA_OK;
     if (ctx->budget && ctx->used + bytes > ctx->budget)
         return fail(ctx, KOMA_E_NOMEM, "%s: %zu bytes would exceed the memory budget (%zu of %zu used)", what,
                     bytes, ctx->used, ctx->budget);
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->alloc_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->alloc_stream);
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
@@ -149,8 +160,10 @@ koma_status dev_alloc(koma_ctx* ctx, void** p, size_t bytes, const char* what) {
 
 void dev_free(koma_ctx* ctx, void* p, size_t bytes) {
     if (!p) return;
-    cudaFree(p);
-    if (ctx) ctx->used -= std::min(ctx->used, bytes);
+    cudaDeviceSynchronize();
+    cudaFreeAsync(p, ctx->alloc_stream);
+    cudaStreamSynchronize(ctx->alloc_stream);
+    ctx->used -= std::min(ctx->used, bytes);
 }
 
 inline void split(double v, float* hi, float* lo) {
@@ -314,6 +327,28 @@ extern "C" koma_status koma_init(int device, size_t mem_budget_bytes, koma_ctx**
         delete ctx;
         return KOMA_E_CUDA;
     }
+    {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaError_t e = cudaMemPoolCreate(&ctx->pool, &props);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->alloc_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) {
+            uint64_t keep = ~0ull;  // keep freed blocks mapped for reuse
+            e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (ctx->alloc_stream) cudaStreamDestroy(ctx->alloc_stream);
+            if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+            cudaStreamDestroy(ctx->own_stream);
+            cudaFree(ctx->d_status);
+            delete ctx;
+            return KOMA_E_CUDA;
+        }
+    }
     *out = ctx;
     return KOMA_OK;
 }
@@ -326,9 +361,12 @@ extern "C" koma_status koma_destroy(koma_ctx* ctx) {
     DeviceGuard g(ctx->device);
     for (cudaEvent_t& e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->scratch) dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
-    if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->alloc_stream) cudaStreamDestroy(ctx->alloc_stream);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->d_conv) cudaFree(ctx->d_conv);
+    if (ctx->h_conv) cudaFreeHost(ctx->h_conv);
     if (ctx->d_status) cudaFree(ctx->d_status);
     delete ctx;
     return KOMA_OK;
@@ -341,11 +379,20 @@ extern "C" size_t koma_mem_used(const koma_ctx* ctx) { return ctx ? ctx->used : 
 // ---------------------------------------------------------------------------
 // phantom
 // ---------------------------------------------------------------------------
-extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const double* x, const double* y,
-                                           const double* z, const double* pd, const double* t1,
-                                           const double* t2, const double* dw, const int64_t* group_offsets,
-                                           int64_t n_groups, koma_phantom** out) {
-    if (!ctx) return KOMA_E_INVALID;
+namespace {
+
+// First half of a phantom upload: argument checks, device blocks, the copies
+// of the caller's rows and the conversion kernel, all enqueued on own_stream;
+// the conversion's status is copied back into ctx->h_conv (pinned). The
+// caller may do other host work before phantom_upload_finish. The FP64 block
+// receives the caller's rows [x, y, z, dw, T1, T2, pd] as they are (pinned
+// rows are copied by DMA directly; for pageable ones the driver's pipelined
+// copy measured faster than packing into pinned memory on the host first);
+// the kernel checks every spin, takes the extents, builds the FP32 block,
+// turns dw into df and fills the padding.
+koma_status phantom_upload_start(koma_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
+                                 const double* pd, const double* t1, const double* t2, const double* dw,
+                                 const int64_t* group_offsets, int64_t n_groups, koma_phantom** out) {
     if (!out) return fail(ctx, KOMA_E_INVALID, "phantom_upload: out is NULL");
     *out = nullptr;
     if (n < 0) return fail(ctx, KOMA_E_INVALID, "phantom_upload: n = %lld < 0", static_cast<long long>(n));
@@ -372,11 +419,6 @@ extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const doubl
     if (group_offsets) ph->group_offsets.assign(group_offsets, group_offsets + n_groups + 1);
     const int64_t np = ph->n_pad;
 
-    // The FP64 block receives the caller's rows [x, y, z, dw, T1, T2, pd] as
-    // they are (the driver's pipelined copy from pageable memory measured
-    // faster than packing into pinned memory on the host first); a device
-    // kernel then checks every spin, takes the extents, builds the FP32
-    // block, turns dw into df and fills the padding.
     DeviceGuard g(ctx->device);
     const size_t b32 = static_cast<size_t>(koma::P32_N * np) * sizeof(float),
                  b64 = static_cast<size_t>(koma::P64_N * np) * sizeof(double);
@@ -384,8 +426,13 @@ extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const doubl
     if (st == KOMA_OK) st = dev_alloc(ctx, reinterpret_cast<void**>(&ph->p64), b64, "phantom_upload");
     if (st == KOMA_OK && !ctx->d_conv) {
         cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ctx->d_conv), sizeof(koma::ConvertStatus));
+        if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&ctx->h_conv), sizeof(koma::ConvertStatus),
+                                                cudaHostAllocDefault);
         if (e != cudaSuccess) {
+            if (ctx->d_conv) cudaFree(ctx->d_conv);
+    if (ctx->h_conv) cudaFreeHost(ctx->h_conv);
             ctx->d_conv = nullptr;
+            ctx->h_conv = nullptr;
             st = cuda_fail(ctx, e, "phantom_upload: status word");
         }
     }
@@ -397,7 +444,6 @@ extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const doubl
             if (e != cudaSuccess) st = cuda_fail(ctx, e, "phantom_upload: copy");
         }
     }
-    koma::ConvertStatus cs{};
     if (st == KOMA_OK) {
         cudaError_t ce = cudaMemsetAsync(ctx->d_conv, 0, sizeof(koma::ConvertStatus), ctx->own_stream);
         if (ce == cudaSuccess)
@@ -406,22 +452,12 @@ extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const doubl
             ce = static_cast<cudaError_t>(koma::launch_phantom_convert(ph->p64, ph->p32, n, np, ctx->d_conv,
                                                                        ctx->own_stream));
         if (ce == cudaSuccess)
-            ce = cudaMemcpyAsync(&cs, ctx->d_conv, sizeof(cs), cudaMemcpyDeviceToHost, ctx->own_stream);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->own_stream);
+            ce = cudaMemcpyAsync(ctx->h_conv, ctx->d_conv, sizeof(koma::ConvertStatus), cudaMemcpyDeviceToHost,
+                                 ctx->own_stream);
         if (ce != cudaSuccess) st = cuda_fail(ctx, ce, "phantom_upload: conversion");
     }
-    if (st == KOMA_OK && cs.first_bad != ~0ull) {  // report the first offending spin
-        std::string msg;
-        check_spin_values(n, x, y, z, pd, t1, t2, dw, msg);
-        st = fail(ctx, KOMA_E_INVALID, "%s", msg.c_str());
-    }
-    if (st == KOMA_OK)
-        for (int d = 0; d < 4; ++d) {
-            double v;
-            std::memcpy(&v, &cs.max_bits[d], sizeof(v));
-            ph->max_abs[d] = v;
-        }
     if (st != KOMA_OK) {
+        cudaStreamSynchronize(ctx->own_stream);  // no copy may still read or write the blocks
         dev_free(ctx, ph->p32, b32);
         dev_free(ctx, ph->p64, b64);
         delete ph;
@@ -431,6 +467,46 @@ extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const doubl
     ctx->live_objects++;
     *out = ph;
     return KOMA_OK;
+}
+
+// Second half: wait for the conversion and check its result. On invalid
+// input the phantom is freed, *out reset, and the caller's rows are scanned
+// on the host for the message.
+koma_status phantom_upload_finish(koma_ctx* ctx, koma_phantom** out, const double* x, const double* y,
+                                  const double* z, const double* pd, const double* t1, const double* t2,
+                                  const double* dw) {
+    koma_phantom* ph = *out;
+    DeviceGuard g(ctx->device);
+    cudaError_t ce = cudaStreamSynchronize(ctx->own_stream);
+    koma_status st = ce == cudaSuccess ? KOMA_OK : cuda_fail(ctx, ce, "phantom_upload: conversion");
+    if (st == KOMA_OK && ctx->h_conv->first_bad != ~0ull) {  // report the first offending spin
+        std::string msg;
+        check_spin_values(ph->n, x, y, z, pd, t1, t2, dw, msg);
+        st = fail(ctx, KOMA_E_INVALID, "%s", msg.c_str());
+    }
+    if (st != KOMA_OK) {
+        koma_phantom_free(ph);
+        *out = nullptr;
+        return st;
+    }
+    for (int d = 0; d < 4; ++d) {
+        double v;
+        std::memcpy(&v, &ctx->h_conv->max_bits[d], sizeof(v));
+        ph->max_abs[d] = v;
+    }
+    return KOMA_OK;
+}
+
+}  // namespace
+
+extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const double* x, const double* y,
+                                           const double* z, const double* pd, const double* t1,
+                                           const double* t2, const double* dw, const int64_t* group_offsets,
+                                           int64_t n_groups, koma_phantom** out) {
+    if (!ctx) return KOMA_E_INVALID;
+    koma_status st = phantom_upload_start(ctx, n, x, y, z, pd, t1, t2, dw, group_offsets, n_groups, out);
+    if (st != KOMA_OK) return st;
+    return phantom_upload_finish(ctx, out, x, y, z, pd, t1, t2, dw);
 }
 
 extern "C" int64_t koma_phantom_n_spins(const koma_phantom* ph) { return ph ? ph->n : -1; }
@@ -828,19 +904,21 @@ extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, cons
     DeviceGuard g(ctx->device);
     const size_t b32 = rb.r32.size() * sizeof(koma::Rec32), b64 = rb.r64.size() * sizeof(koma::Rec64),
                  bm = rb.rm.size() * sizeof(koma::RecM);
-    koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r32), b32, "sequence_upload");
-    if (st == KOMA_OK) st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r64), b64, "sequence_upload");
-    if (st == KOMA_OK) st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->rm), bm, "sequence_upload");
+    // one device block [Rec32 | Rec64 | RecM] (each part 16-byte aligned:
+    // 64- and 128-byte records) filled by one copy
+    koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r32), b32 + b64 + bm, "sequence_upload");
     if (st == KOMA_OK && b32) {
-        cudaError_t e = cudaMemcpy(seq->r32, rb.r32.data(), b32, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(seq->r64, rb.r64.data(), b64, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(seq->rm, rb.rm.data(), bm, cudaMemcpyHostToDevice);
+        seq->r64 = reinterpret_cast<koma::Rec64*>(reinterpret_cast<char*>(seq->r32) + b32);
+        seq->rm = reinterpret_cast<koma::RecM*>(reinterpret_cast<char*>(seq->r32) + b32 + b64);
+        std::vector<char> host(b32 + b64 + bm);
+        std::memcpy(host.data(), rb.r32.data(), b32);
+        std::memcpy(host.data() + b32, rb.r64.data(), b64);
+        std::memcpy(host.data() + b32 + b64, rb.rm.data(), bm);
+        cudaError_t e = cudaMemcpy(seq->r32, host.data(), host.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) st = cuda_fail(ctx, e, "sequence_upload: copy");
     }
     if (st != KOMA_OK) {
-        dev_free(ctx, seq->r32, b32);
-        dev_free(ctx, seq->r64, b64);
-        dev_free(ctx, seq->rm, bm);
+        dev_free(ctx, seq->r32, b32 + b64 + bm);
         delete seq;
         return st;
     }
@@ -863,9 +941,8 @@ extern "C" koma_status koma_sequence_free(koma_sequence* seq) {
     if (!seq) return KOMA_OK;
     koma_ctx* ctx = seq->ctx;
     DeviceGuard g(ctx->device);
-    dev_free(ctx, seq->r32, static_cast<size_t>(seq->info.n_records) * sizeof(koma::Rec32));
-    dev_free(ctx, seq->r64, static_cast<size_t>(seq->info.n_records) * sizeof(koma::Rec64));
-    dev_free(ctx, seq->rm, static_cast<size_t>(seq->info.n_records) * sizeof(koma::RecM));
+    dev_free(ctx, seq->r32, static_cast<size_t>(seq->info.n_records) *
+                                (sizeof(koma::Rec32) + sizeof(koma::Rec64) + sizeof(koma::RecM)));
     ctx->live_objects--;
     delete seq;
     return KOMA_OK;
@@ -1368,8 +1445,14 @@ extern "C" koma_status koma_simulate_host(koma_ctx* ctx, int64_t n, const double
     koma_phantom* ph = nullptr;
     koma_sequence* seq = nullptr;
     double* d_sig = nullptr;
-    koma_status st = koma_phantom_upload(ctx, n, x, y, z, pd, t1, t2, dw, group_offsets, n_groups, &ph);
+    // the phantom's copies and conversion run on the device while the host
+    // preprocesses and uploads the sequence
+    koma_status st = phantom_upload_start(ctx, n, x, y, z, pd, t1, t2, dw, group_offsets, n_groups, &ph);
     if (st == KOMA_OK) st = koma_sequence_upload(ctx, n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, &seq);
+    if (ph) {
+        const koma_status sp = phantom_upload_finish(ctx, &ph, x, y, z, pd, t1, t2, dw);
+        if (st == KOMA_OK) st = sp;
+    }
     size_t out_bytes = 0;
     DeviceGuard g(ctx->device);
     if (st == KOMA_OK) {
