@@ -274,11 +274,6 @@ struct Spins {
         kb1 = kb2 = kb3 = 0.f;
     }
 
-    // One excitation step: rotation about the step's constant field, then
-    // relaxation over dt. The rotation vector is a = gammabar dt (B1x, B1y,
-    // Gbar.x + df/gammabar) in turns; the spinor of the step (Eq. Rot_exc with
-    // phi = -2 pi |a|) is the rotation by -2 pi |a| about a/|a|, applied as
-    // the quaternion w = cos(pi|a|), u = -a sin(pi|a|)/|a|.
     // Checkpointed state [3][np] (Mx, My, Mz at t_ref) of a walk that was cut.
     __device__ __forceinline__ void load_state(const float* __restrict__ st, int64_t np) {
 #pragma unroll
@@ -308,34 +303,18 @@ struct Spins {
     // (B1x, B1y, Gbar) and the spin adds pi dt df, so theta is the half-angle
     // vector in radians; the spinor of the step (Eq. Rot_exc, phi = -2|theta|)
     // is the rotation by -2|theta| about theta/|theta|, applied as the
-    // quaternion w = cos|theta|, u = -theta sin|theta|/|theta|.
-    // SMALL (|theta| <= 0.754 for every step and spin): cos t and sin(t)/t are
-    // even series in t^2 = theta.theta (terms to t^10 and t^8; remainders
-    // below 3e-9), so no square root, division or sine is needed.
-    template <bool SMALL>
+    // quaternion w = cos|theta|, u = -theta sin|theta|/|theta|. General path:
+    // |theta| by rsqrt, sin and cos of pi x after exact reduction.
     __device__ __forceinline__ void rf_slots(float gx, float gy, float gz, float bx, float by, float b2, float dt) {
         const float pdt = dt * 3.14159265358979323846f;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const float az = fmaf(gx, xh[s], fmaf(gy, yh[s], fmaf(gz, zh[s], fh[s] * pdt)));
             const float t2 = fmaf(az, az, b2);
-            float ch, nsinc;  // cos t and -sin(t)/t
-            if (SMALL) {
-                float q = fmaf(t2, -2.75573192239858907e-6f, 1.98412698412698413e-4f);   // -1/9!, 1/7!
-                q = fmaf(q, t2, -8.33333333333333333e-3f);                               // -1/5!
-                q = fmaf(q, t2, 1.66666666666666667e-1f);                                // 1/3!
-                nsinc = fmaf(q, t2, -1.0f);
-                float c = fmaf(t2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);  // -1/10!, 1/8!
-                c = fmaf(c, t2, -1.38888888888888889e-3f);                               // -1/6!
-                c = fmaf(c, t2, 4.16666666666666667e-2f);                                // 1/4!
-                c = fmaf(c, t2, -0.5f);
-                ch = fmaf(c, t2, 1.0f);
-            } else {
-                const float rs = rsqrtf(t2);
-                float sh;
-                sincospi_f32(t2 * rs * 0.318309886183790671538f, &sh, &ch);
-                nsinc = -sh * rs;
-            }
+            const float rs = rsqrtf(t2);
+            float ch, sh;
+            sincospi_f32(t2 * rs * 0.318309886183790671538f, &sh, &ch);
+            const float nsinc = -sh * rs;  // -sin(t)/t
             const float ux = bx * nsinc, uy = by * nsinc, uz = az * nsinc;
             // 2/|q|^2 to first order (keeps |M| from drifting over many steps
             // of one constant field)
@@ -354,6 +333,56 @@ struct Spins {
             mx[s] = fmaf(em2[s], nx, nx);
             my[s] = fmaf(em2[s], ny, ny);
             mz[s] = fmaf(em1[s], nz - m0[s], nz);
+        }
+    }
+
+    // Series path (|theta| <= 0.754 for every step and spin): cos t and
+    // sin(t)/t as even series in t^2 = theta.theta (terms to t^10 and t^8;
+    // remainders below 3e-9), so no square root, division or sine is needed;
+    // the same rotation and relaxation as rf_slots, on spin pairs in packed
+    // f32x2 arithmetic (half the issued instructions).
+    __device__ __forceinline__ void rf_pairs_small(float gx, float gy, float gz, float bx, float by, float b2,
+                                                   float dt) {
+        const float pdt = dt * 3.14159265358979323846f;
+        const f32x2 GX = pk(gx, gx), GY = pk(gy, gy), GZ = pk(gz, gz), PDT = pk(pdt, pdt), B2 = pk(b2, b2);
+        const f32x2 BX = pk(bx, bx), BY = pk(by, by), NBX = pk(-bx, -bx), NBY = pk(-by, -by);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const int s0 = 2 * p, s1 = 2 * p + 1;
+            const f32x2 X = pk(xh[s0], xh[s1]), Y = pk(yh[s0], yh[s1]), Z = pk(zh[s0], zh[s1]), F = pk(fh[s0], fh[s1]);
+            const f32x2 az = fma2(GX, X, fma2(GY, Y, fma2(GZ, Z, mul2(F, PDT))));
+            const f32x2 t2 = fma2(az, az, B2);
+            f32x2 q = fma2(t2, pk(-2.75573192239858907e-6f, -2.75573192239858907e-6f),
+                           pk(1.98412698412698413e-4f, 1.98412698412698413e-4f));
+            q = fma2(q, t2, pk(-8.33333333333333333e-3f, -8.33333333333333333e-3f));
+            q = fma2(q, t2, pk(1.66666666666666667e-1f, 1.66666666666666667e-1f));
+            const f32x2 nsinc = fma2(q, t2, pk(-1.0f, -1.0f));
+            f32x2 c = fma2(t2, pk(-2.75573192239858907e-7f, -2.75573192239858907e-7f),
+                           pk(2.48015873015873016e-5f, 2.48015873015873016e-5f));
+            c = fma2(c, t2, pk(-1.38888888888888889e-3f, -1.38888888888888889e-3f));
+            c = fma2(c, t2, pk(4.16666666666666667e-2f, 4.16666666666666667e-2f));
+            c = fma2(c, t2, pk(-0.5f, -0.5f));
+            const f32x2 ch = fma2(c, t2, pk(1.0f, 1.0f));
+            const f32x2 ux = mul2(BX, nsinc), uy = mul2(BY, nsinc), uz = mul2(az, nsinc);
+            const f32x2 nux = mul2(NBX, nsinc), nuy = mul2(NBY, nsinc), nuz = mul2(az, mul2(nsinc, pk(-1.f, -1.f)));
+            const f32x2 nq = fma2(ch, ch, fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))));
+            const f32x2 c2 = fma2(pk(-2.f, -2.f), nq, pk(4.f, 4.f));
+            const f32x2 MX = pk(mx[s0], mx[s1]), MY = pk(my[s0], my[s1]), MZ = pk(mz[s0], mz[s1]);
+            const f32x2 px = fma2(uy, MZ, mul2(nuz, MY));
+            const f32x2 py = fma2(uz, MX, mul2(nux, MZ));
+            const f32x2 pz = fma2(ux, MY, mul2(nuy, MX));
+            const f32x2 qx = fma2(uy, pz, mul2(nuz, py));
+            const f32x2 qy = fma2(uz, px, mul2(nux, pz));
+            const f32x2 qz = fma2(ux, py, mul2(nuy, px));
+            const f32x2 nx = fma2(c2, fma2(ch, px, qx), MX);
+            const f32x2 ny = fma2(c2, fma2(ch, py, qy), MY);
+            const f32x2 nz = fma2(c2, fma2(ch, pz, qz), MZ);
+            const f32x2 E2 = pk(em2[s0], em2[s1]), E1 = pk(em1[s0], em1[s1]);
+            const f32x2 rx = fma2(E2, nx, nx), ry = fma2(E2, ny, ny);
+            const f32x2 rz = fma2(E1, add2(nz, pk(-m0[s0], -m0[s1])), nz);
+            unpk(rx, mx[s0], mx[s1]);
+            unpk(ry, my[s0], my[s1]);
+            unpk(rz, mz[s0], mz[s1]);
         }
     }
 
@@ -389,9 +418,9 @@ struct Spins {
         if (rf_mode >= 2)
             rf_uniform(bx, by, b2, rf_mode == 3);
         else if (rf_mode == 1)
-            rf_slots<true>(gx, gy, gz, bx, by, b2, dt);
+            rf_pairs_small(gx, gy, gz, bx, by, b2, dt);
         else
-            rf_slots<false>(gx, gy, gz, bx, by, b2, dt);
+            rf_slots(gx, gy, gz, bx, by, b2, dt);
     }
 
     // RF step whose rotation is the same for every spin (field in the xy
