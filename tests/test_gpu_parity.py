@@ -258,3 +258,46 @@ def test_paper_experiments_full_size(sim, name):
     ref = oracle.simulate(ph, seq)
     for prec, tol in (("fp32", TOL32), ("fp64", TOL64)):
         assert rel_err(gpu_signal(sim, ph, seq, prec), ref) < tol
+
+
+def test_invalid_spin_reported_by_index(sim):
+    """The device-side input check names the first offending spin."""
+    bad = random_spins(5000, seed=7)
+    bad.t1[4321] = -1.0
+    bad.pd[4400] = -0.5
+    with pytest.raises(koma.KomaError) as e:
+        sim.upload_phantom(bad)
+    assert e.value.status == koma.KOMA_E_INVALID
+    assert "4321" in str(e.value)
+    bad = random_spins(300, seed=8)
+    bad.dw[299] = np.inf
+    with pytest.raises(koma.KomaError) as e:
+        sim.upload_phantom(bad)
+    assert "299" in str(e.value)
+
+
+def test_upload_cycles_reuse_memory(sim):
+    """Upload / simulate / free cycles return the context's accounted memory
+    to where it was and do not grow the device footprint (pooled blocks are
+    reused)."""
+    import torch
+    ph, seq = workload("epi512", "small")
+    first = None
+    used = None
+    for i in range(4):
+        hp = sim.upload_phantom(ph)
+        hs = sim.upload_sequence(seq)
+        sim.simulate(hp, hs)
+        sim.sync()
+        koma.koma_sequence_free(hs)
+        koma.koma_phantom_free(hp)
+        # what stays accounted is the context's partial-sum scratch
+        if used is None:
+            used = koma.koma_mem_used(sim.ctx)
+        assert koma.koma_mem_used(sim.ctx) == used
+        torch.cuda.synchronize()
+        free = torch.cuda.mem_get_info()[0]
+        if i == 1:
+            first = free
+        elif i > 1:
+            assert free == first, "device footprint grew across identical cycles"
