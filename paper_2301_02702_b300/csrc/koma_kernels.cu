@@ -231,6 +231,11 @@ struct Spins {
     static constexpr int NP = S / 2;
     float xh[S], yh[S], zh[S], fh[S], m0[S], r1[S], r2[S];
     float mx[S], my[S], mz[S], em1[S], em2[S], zr[S], zi[S], zr2[S], zi2[S];
+    // lo halves of x, y, z, df: in registers for 2 spins per thread (the
+    // grouped kernel's usual shape), read from L1 at each exact evaluation
+    // for 4 (no registers to spare there)
+    static constexpr bool kLoRegs = S <= 2;
+    float xl[kLoRegs ? S : 1], yl[kLoRegs ? S : 1], zl[kLoRegs ? S : 1], fl[kLoRegs ? S : 1];
     int64_t base, end;
     int stride;
     float dt_cached;               // em1/em2 belong to this dt
@@ -239,6 +244,16 @@ struct Spins {
     float kb0, kb1, kb2, kb3;      // zr2/zi2 belong to this one (the previous run's)
 
     __device__ __forceinline__ int64_t index(int s) const { return base + static_cast<int64_t>(s) * stride; }
+
+    // lo half of a coordinate of slot s (spin j; v: j < end)
+    template <int N>
+    __device__ __forceinline__ float lo(const float (&regs)[N], int row, int s, const float* __restrict__ P,
+                                        int64_t np, int64_t j, bool v) const {
+        if constexpr (kLoRegs)
+            return regs[s];
+        else
+            return v ? P[row * np + j] : 0.f;
+    }
 
     __device__ __forceinline__ void load(const float* __restrict__ P, int64_t np, int64_t base_, int stride_,
                                          int64_t end_) {
@@ -256,6 +271,12 @@ struct Spins {
             m0[s] = v ? P[P32_M0 * np + j] : 0.f;
             r1[s] = v ? P[P32_R1 * np + j] : 0.f;
             r2[s] = v ? P[P32_R2 * np + j] : 0.f;
+            if constexpr (kLoRegs) {
+                xl[s] = v ? P[P32_XL * np + j] : 0.f;
+                yl[s] = v ? P[P32_YL * np + j] : 0.f;
+                zl[s] = v ? P[P32_ZL * np + j] : 0.f;
+                fl[s] = v ? P[P32_FL * np + j] : 0.f;
+            }
             mx[s] = 0.f;
             my[s] = 0.f;
             mz[s] = m0[s];
@@ -485,10 +506,10 @@ struct Spins {
             const int64_t j = index(s);
             const bool v = j < end;
             float F = 0.f;
-            if (ux) F += frac_product(xh[s], v ? P[P32_XL * np + j] : 0.f, kxh, kxl);
-            if (uy) F += frac_product(yh[s], v ? P[P32_YL * np + j] : 0.f, kyh, kyl);
-            if (uz) F += frac_product(zh[s], v ? P[P32_ZL * np + j] : 0.f, kzh, kzl);
-            if (uf) F += frac_product(fh[s], v ? P[P32_FL * np + j] : 0.f, th, tl);
+            if (ux) F += frac_product(xh[s], lo(xl, P32_XL, s, P, np, j, v), kxh, kxl);
+            if (uy) F += frac_product(yh[s], lo(yl, P32_YL, s, P, np, j, v), kyh, kyl);
+            if (uz) F += frac_product(zh[s], lo(zl, P32_ZL, s, P, np, j, v), kzh, kzl);
+            if (uf) F += frac_product(fh[s], lo(fl, P32_FL, s, P, np, j, v), th, tl);
             // one-shot phase: reduce to [-1/2, 1/2] turn and use the hardware
             // sine (absolute error ~4e-7, not accumulated: every run and every
             // materialisation starts from an exact evaluation)
