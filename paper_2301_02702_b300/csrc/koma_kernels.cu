@@ -469,21 +469,28 @@ struct Spins {
         const float ux = bx * f, uy = by * f;
         const float nq = fmaf(ch, ch, fmaf(ux, ux, uy * uy));
         const float c2 = fmaf(-2.f, nq, 4.f);
+        // u = (ux, uy, 0): p = u x v, q = u x p, on spin pairs in packed f32x2
+        const f32x2 UX = pk(ux, ux), UY = pk(uy, uy), NUX = pk(-ux, -ux), NUY = pk(-uy, -uy);
+        const f32x2 CH = pk(ch, ch), C2 = pk(c2, c2);
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            // u = (ux, uy, 0): p = u x v, q = u x p
-            const float px = uy * mz[s];
-            const float py = -ux * mz[s];
-            const float pz = fmaf(ux, my[s], -uy * mx[s]);
-            const float qx = uy * pz;
-            const float qy = -ux * pz;
-            const float qz = fmaf(ux, py, -uy * px);
-            const float nx = fmaf(c2, fmaf(ch, px, qx), mx[s]);
-            const float ny = fmaf(c2, fmaf(ch, py, qy), my[s]);
-            const float nz = fmaf(c2, fmaf(ch, pz, qz), mz[s]);
-            mx[s] = fmaf(em2[s], nx, nx);
-            my[s] = fmaf(em2[s], ny, ny);
-            mz[s] = fmaf(em1[s], nz - m0[s], nz);
+        for (int p = 0; p < NP; ++p) {
+            const int s0 = 2 * p, s1 = 2 * p + 1;
+            const f32x2 MX = pk(mx[s0], mx[s1]), MY = pk(my[s0], my[s1]), MZ = pk(mz[s0], mz[s1]);
+            const f32x2 px = mul2(UY, MZ);
+            const f32x2 py = mul2(NUX, MZ);
+            const f32x2 pz = fma2(UX, MY, mul2(NUY, MX));
+            const f32x2 qx = mul2(UY, pz);
+            const f32x2 qy = mul2(NUX, pz);
+            const f32x2 qz = fma2(UX, py, mul2(NUY, px));
+            const f32x2 nx = fma2(C2, fma2(CH, px, qx), MX);
+            const f32x2 ny = fma2(C2, fma2(CH, py, qy), MY);
+            const f32x2 nz = fma2(C2, fma2(CH, pz, qz), MZ);
+            const f32x2 E2 = pk(em2[s0], em2[s1]), E1 = pk(em1[s0], em1[s1]);
+            const f32x2 rx = fma2(E2, nx, nx), ry = fma2(E2, ny, ny);
+            const f32x2 rz = fma2(E1, add2(nz, pk(-m0[s0], -m0[s1])), nz);
+            unpk(rx, mx[s0], mx[s1]);
+            unpk(ry, my[s0], my[s1]);
+            unpk(rz, mz[s0], mz[s1]);
         }
     }
 
