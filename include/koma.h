@@ -280,6 +280,18 @@ koma_status koma_tune(koma_ctx *ctx, const koma_phantom *ph, const koma_sequence
                       double *sig_dev, void *stream, koma_launch_info *chosen);
 
 /*
+ * Self-check of the device-side timeout path (no counterpart in the paper).
+ * Enqueues on `stream` a one-thread kernel that waits, with the bounded wait
+ * the Bloch kernels use for their record tiles, on a barrier that nothing
+ * completes; after limit_us microseconds (1 .. 2,000,000) it gives up and
+ * sets the context's status word. The next koma_sync on the stream then
+ * returns KOMA_E_TIMEOUT (clearing the word), and the context stays usable.
+ * It faults and hangs nothing: the wait is bounded by the device's global
+ * timer. Errors: KOMA_E_INVALID (limit out of range), KOMA_E_CUDA (launch).
+ */
+koma_status koma_check_bounded_wait(koma_ctx *ctx, int64_t limit_us, void *stream);
+
+/*
  * Wait for `stream` and report device-side status: KOMA_E_TIMEOUT if a
  * bounded wait inside a kernel of this context gave up since the last
  * koma_sync (the flag is then cleared), KOMA_E_CUDA on an asynchronous CUDA

@@ -233,6 +233,9 @@ int launch_bloch_fp64_motion(const BlochArgs& a, const BlochLaunch& L, void* str
 int motion_ctas_per_sm(int block);
 constexpr int kMotionSpinsPerThread = 2;
 int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream);
+// One thread waits, bounded by limit_ns, on an mbarrier nothing completes,
+// then sets bit 1 of *status (the timeout path of the record-tile waits).
+int launch_bounded_wait_check(int* status, unsigned long long limit_ns, void* stream);
 int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, void* stream);
 int items_ctas_per_sm(int spins_per_thread, int block);
 // Serving kernel (4 spins per thread, `block` threads: a batch is 128 x

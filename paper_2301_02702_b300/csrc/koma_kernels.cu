@@ -139,12 +139,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-// Wait for phase `parity` of `bar`, giving up after kWaitNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// Wait for phase `parity` of `bar`, giving up after `limit_ns` (default kWaitNs).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     while (!mbar_try_wait(bar, parity)) {
-        if (global_timer_ns() - t0 > kWaitNs) return false;
+        if (global_timer_ns() - t0 > limit_ns) return false;
     }
     return true;
 }
@@ -1522,6 +1523,21 @@ __global__ void __launch_bounds__(256) phantom_convert_kernel(double* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// Self-check of the device-side timeout path: one thread waits, with the
+// bounded wait the Bloch kernels use on their record tiles, on an mbarrier
+// that nothing completes (no copy is ever issued to it). After `limit_ns` it
+// gives up, sets bit 1 of the status word and returns; the next koma_sync
+// reports KOMA_E_TIMEOUT and the context stays usable.
+// ---------------------------------------------------------------------------
+__global__ void bounded_wait_check_kernel(int* status, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t s_bar;
+    const uint32_t bar = smem_u32(&s_bar);
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    if (!mbar_wait_bounded(bar, 0, limit_ns)) atomicOr(status, 2);
+}
+
+// ---------------------------------------------------------------------------
 // K2: sig[g][k] = sum over the CTAs c of group g of partial[c][k], in FP64,
 // in a fixed order (deterministic; threadIdx.y strides the CTAs, the eight
 // strided sums are then added in y order).
@@ -1727,6 +1743,11 @@ int launch_phantom_convert(double* p64, float* p32, int64_t n, int64_t n_pad, Co
     const int64_t blocks = std::min<int64_t>((n_pad + 255) / 256, 148 * 16);
     phantom_convert_kernel<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(p64, p32, n,
                                                                                                          n_pad, cs);
+    return cudaGetLastError();
+}
+
+int launch_bounded_wait_check(int* status, unsigned long long limit_ns, void* stream) {
+    bounded_wait_check_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(status, limit_ns);
     return cudaGetLastError();
 }
 

@@ -1389,6 +1389,17 @@ extern "C" koma_status koma_tune(koma_ctx* ctx, const koma_phantom* ph_c, const 
     return rc;
 }
 
+extern "C" koma_status koma_check_bounded_wait(koma_ctx* ctx, int64_t limit_us, void* stream) {
+    if (!ctx) return KOMA_E_INVALID;
+    if (limit_us < 1 || limit_us > 2000000)
+        return fail(ctx, KOMA_E_INVALID, "check_bounded_wait: limit_us = %lld (1 .. 2,000,000)",
+                    static_cast<long long>(limit_us));
+    DeviceGuard g(ctx->device);
+    int e = koma::launch_bounded_wait_check(ctx->d_status, static_cast<unsigned long long>(limit_us) * 1000ull,
+                                            stream);
+    return e == cudaSuccess ? KOMA_OK : cuda_fail(ctx, static_cast<cudaError_t>(e), "check_bounded_wait: launch");
+}
+
 extern "C" koma_status koma_sync(koma_ctx* ctx, void* stream) {
     if (!ctx) return KOMA_E_INVALID;
     DeviceGuard g(ctx->device);

@@ -34,7 +34,7 @@ EXPORTS = (
     "koma_sequence_free", "koma_sequence_plan", "koma_simulate", "koma_sync", "koma_set_timing",
     "koma_get_timing", "koma_get_launch_info", "koma_simulate_host", "koma_simulate_static", "koma_tune",
     "koma_server_create", "koma_server_submit", "koma_server_wait", "koma_server_get_stats",
-    "koma_server_last_error", "koma_server_destroy",
+    "koma_server_last_error", "koma_server_destroy", "koma_check_bounded_wait",
 )
 
 
@@ -172,6 +172,8 @@ def load(path: Optional[str] = None):
         lib.koma_server_destroy.argtypes = [_vp]
         lib.koma_tune.restype = st
         lib.koma_tune.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(LaunchInfo)]
+        lib.koma_check_bounded_wait.restype = st
+        lib.koma_check_bounded_wait.argtypes = [_vp, ctypes.c_int64, _vp]
         lib.koma_simulate_static.restype = st
         lib.koma_simulate_static.argtypes = [_vp, _vp, _vp, _vp]
         lib.koma_simulate_host.restype = st
@@ -490,6 +492,13 @@ def koma_server_wait(srv, rid: int, n_adc: int, timeout_s: float = -1.0):
     if rc != KOMA_OK:
         raise KomaError(rc, "koma_server_wait: " + koma_server_last_error(srv))
     return out[:n_adc], info.as_dict()
+
+
+def koma_check_bounded_wait(ctx, limit_us: int, stream_handle: int = 0):
+    """Enqueue the self-check of the device-side timeout path (see koma.h);
+    the next koma_sync on the stream raises KomaError(KOMA_E_TIMEOUT)."""
+    _check(ctx, load().koma_check_bounded_wait(ctx, int(limit_us), stream_handle or None),
+           "koma_check_bounded_wait")
 
 
 def koma_server_get_stats(srv) -> dict:
