@@ -97,3 +97,50 @@ def test_reference_arm_under_torchrun_two_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def _failing_worker(rank, world, port, out_q):
+    """Rank 1's shard computation fails (a host-side injected fault) and that
+    rank exits; rank 0 must learn of it from the collective's error within the
+    process group's timeout instead of waiting for ever."""
+    import datetime
+    import time
+    import torch.distributed as dist
+    from paper_2301_02702_b300.shard import simulate_sharded
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    ph = random_spins(20, seed=5)
+    seq = random_sequence(60, seed=6)
+
+    def shard(p, s):
+        if rank == 1:
+            raise RuntimeError("injected shard failure")
+        return oracle.simulate(p, s, threads=1)
+
+    t0 = time.monotonic()
+    try:
+        simulate_sharded(ph, seq, shard, rank, world)
+        out_q.put((rank, "completed", time.monotonic() - t0))
+    except Exception as e:  # noqa: BLE001 - the failure is the point
+        out_q.put((rank, f"failed: {type(e).__name__}", time.monotonic() - t0))
+        if rank == 1:
+            out_q.close()
+            out_q.join_thread()  # deliver the report before leaving
+            os._exit(3)  # the failed rank leaves without joining the collective
+    dist.destroy_process_group()
+
+
+def test_shard_failure_is_detected_by_the_other_rank():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict((r, (status, dt)) for r, status, dt in (q.get(timeout=120) for _ in procs))
+    for p in procs:
+        p.join(timeout=60)
+    assert res[1][0].startswith("failed")
+    assert res[0][0].startswith("failed"), res  # rank 0's all-reduce reported the lost peer
+    assert res[0][1] < 60.0
+    assert procs[1].exitcode == 3
