@@ -21,6 +21,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "koma.h"
 #include "koma_internal.h"
 
@@ -103,6 +105,15 @@ struct koma_sequence {
 };
 
 namespace {
+
+// NVTX range for the scope (a no-op unless a profiler is attached): marks
+// uploads, simulations and their host phases on a profiler's timeline.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 koma_status fail(koma_ctx* ctx, koma_status st, const char* fmt, ...) {
     if (ctx) {
@@ -503,6 +514,7 @@ extern "C" koma_status koma_phantom_upload(koma_ctx* ctx, int64_t n, const doubl
                                            const double* z, const double* pd, const double* t1,
                                            const double* t2, const double* dw, const int64_t* group_offsets,
                                            int64_t n_groups, koma_phantom** out) {
+    NvtxRange nvtx_("koma_phantom_upload");
     if (!ctx) return KOMA_E_INVALID;
     koma_status st = phantom_upload_start(ctx, n, x, y, z, pd, t1, t2, dw, group_offsets, n_groups, out);
     if (st != KOMA_OK) return st;
@@ -529,6 +541,7 @@ extern "C" koma_status koma_phantom_free(koma_phantom* ph) {
 
 extern "C" koma_status koma_phantom_set_motion(koma_phantom* ph, const double* vx, const double* vy,
                                                const double* vz) {
+    NvtxRange nvtx_("koma_phantom_set_motion");
     if (!ph) return KOMA_E_INVALID;
     koma_ctx* ctx = ph->ctx;
     const int64_t n = ph->n, np = ph->n_pad;
@@ -881,6 +894,7 @@ extern "C" koma_status koma_sequence_plan(int64_t n_steps, const double* dt, con
 extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, const double* dt, const double* gx,
                                             const double* gy, const double* gz, const double* b1_re,
                                             const double* b1_im, const uint8_t* adc, koma_sequence** out) {
+    NvtxRange nvtx_("koma_sequence_upload");
     if (!ctx) return KOMA_E_INVALID;
     if (!out) return fail(ctx, KOMA_E_INVALID, "sequence_upload: out is NULL");
     *out = nullptr;
@@ -1117,6 +1131,7 @@ koma::BlochLaunch choose_launch(const koma_ctx* ctx, int64_t n, bool fp64, int s
 
 extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, const koma_sequence* seq,
                                      koma_precision precision, double* sig_dev, void* stream) {
+    NvtxRange nvtx_("koma_simulate");
     if (!ctx) return KOMA_E_INVALID;
     koma_phantom* ph = const_cast<koma_phantom*>(ph_c);
     if (!ph || !seq) return fail(ctx, KOMA_E_INVALID, "simulate: NULL phantom or sequence");
@@ -1262,6 +1277,7 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
 // launch needs a device CTA table). Allocates nothing.
 extern "C" koma_status koma_simulate_static(const koma_phantom* ph, const koma_sequence* seq, double* sig_dev,
                                             void* stream) {
+    NvtxRange nvtx_("koma_simulate_static");
     if (!ph || !seq) return KOMA_E_INVALID;
     koma_ctx* ctx = ph->ctx;
     if (seq->ctx != ctx) return fail(ctx, KOMA_E_INVALID, "simulate_static: phantom and sequence belong to different contexts");
@@ -1325,6 +1341,7 @@ extern "C" koma_status koma_simulate_static(const koma_phantom* ph, const koma_s
 
 extern "C" koma_status koma_tune(koma_ctx* ctx, const koma_phantom* ph_c, const koma_sequence* seq,
                                  double* sig_dev, void* stream, koma_launch_info* chosen) {
+    NvtxRange nvtx_("koma_tune");
     if (!ctx) return KOMA_E_INVALID;
     koma_phantom* ph = const_cast<koma_phantom*>(ph_c);
     if (!ph || !seq) return fail(ctx, KOMA_E_INVALID, "tune: NULL phantom or sequence");
@@ -1452,6 +1469,7 @@ extern "C" koma_status koma_simulate_host(koma_ctx* ctx, int64_t n, const double
                                           int64_t n_steps, const double* dt, const double* gx, const double* gy,
                                           const double* gz, const double* b1_re, const double* b1_im,
                                           const uint8_t* adc, koma_precision precision, double* sig_host) {
+    NvtxRange nvtx_("koma_simulate_host");
     if (!ctx) return KOMA_E_INVALID;
     koma_phantom* ph = nullptr;
     koma_sequence* seq = nullptr;

@@ -31,6 +31,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "koma.h"
 #include "koma_internal.h"
 
@@ -126,6 +128,14 @@ struct koma_server {
 
 namespace {
 
+// NVTX range for the scope (a no-op unless a profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 koma_status cuda_err(koma_server* S, cudaError_t e, const char* what) {
     char buf[256];
     snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
@@ -149,6 +159,7 @@ void fail_req(Req* r, koma_status st, const std::string& m) {
 
 // Worker side: allocate and upload an admitted request (stream s_up).
 koma_status admit(koma_server* S, Req* r) {
+    NvtxRange nvtx_("server admit");
     const size_t b32 = r->h32.size() * sizeof(float), brec = r->recs.size() * sizeof(koma::Rec32);
     const size_t brows = static_cast<size_t>(r->n_batches) * kWarps * r->n_adc * sizeof(float2);
     const size_t bsig = static_cast<size_t>(r->n_adc) * 2 * sizeof(double);
@@ -234,6 +245,7 @@ koma_status make_slot(koma_server* S, Slot& sl, int64_t cap) {
 // taken shortest remaining work first; the launch holds at least enough units
 // to fill the GPU (when there are that many) and stops at the work cap.
 bool launch_slot(koma_server* S, Slot& sl) {
+    NvtxRange nvtx_("server launch");
     std::vector<Req*> cand;
     for (Req* r : S->active)
         if (r->state == ADMITTED && r->units_done + 0 < r->units_total) cand.push_back(r);
@@ -301,6 +313,7 @@ bool launch_slot(koma_server* S, Slot& sl) {
 }
 
 void finalize(koma_server* S, Req* r) {
+    NvtxRange nvtx_("server finalize");
     koma::ReduceArgs R;
     R.partial = r->drows;
     R.grid = static_cast<int>(r->n_batches * kWarps);
@@ -495,6 +508,7 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
                                           const double* dw, int64_t n_steps, const double* dt, const double* gx,
                                           const double* gy, const double* gz, const double* b1_re,
                                           const double* b1_im, const uint8_t* adc, uint64_t* id_out) {
+    NvtxRange nvtx_("koma_server_submit");
     if (!S || !id_out) return KOMA_E_INVALID;
     Req* r = new (std::nothrow) Req();
     if (!r) return KOMA_E_NOMEM;
