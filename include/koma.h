@@ -272,8 +272,11 @@ koma_status koma_simulate_static(const koma_phantom *ph, const koma_sequence *se
  * candidate configurations on the full problem (grouped phantoms: spins per
  * thread {2, 4} x block {128, 256} of the work-item kernel; otherwise spins
  * per thread {2, 4} of the Bloch kernel) and keeps the fastest on the
- * phantom; later koma_simulate calls with this sequence use it. Synchronous
- * (waits on `stream`); overwrites sig_dev (device FP64 [n_groups][n_adc][2]).
+ * phantom; later koma_simulate calls with this sequence use it. The choice
+ * is also cached on the context by problem shape (kernel family and the
+ * powers of two of spins, groups, records, ADC samples and RF steps), and
+ * untuned launches of a cached shape use it. Synchronous (waits on
+ * `stream`); overwrites sig_dev (device FP64 [n_groups][n_adc][2]).
  * chosen: NULL or receives the chosen launch. Errors as koma_simulate.
  */
 koma_status koma_tune(koma_ctx *ctx, const koma_phantom *ph, const koma_sequence *seq,

@@ -16,6 +16,7 @@
 #include <functional>
 #include <mutex>
 #include <limits>
+#include <map>
 #include <new>
 #include <string>
 #include <thread>
@@ -53,6 +54,9 @@ struct koma_ctx {
     bool timing = false;
     bool timing_recorded = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    // autotuner results by problem shape (see tune_key): launches of a shape
+    // tuned once reuse the choice for other phantoms and sequences of that shape
+    std::map<uint64_t, std::pair<int, int>> tune_cache;  // key -> (spins per thread, block)
     koma::ConvertStatus* d_conv = nullptr;  // checks and extents of the last phantom upload
     koma::ConvertStatus* h_conv = nullptr;  // pinned host copy of *d_conv
 };
@@ -1105,6 +1109,16 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     return KOMA_OK;
 }
 
+// Shape bucket of a launch for the autotuner cache: the kernel family
+// (grouped items, FP32 Bloch, motion), and the powers of two of the spins,
+// groups, records and ADC samples.
+uint64_t tune_key(const koma_phantom* ph, const koma_sequence* seq, bool items) {
+    auto lg = [](int64_t v) { return static_cast<uint64_t>(v > 0 ? 64 - __builtin_clzll(static_cast<uint64_t>(v)) : 0); };
+    const uint64_t family = items ? 1 : (ph->moving() ? 2 : 0);
+    return family | lg(ph->n) << 2 | lg(ph->n_groups) << 10 | lg(seq->info.n_records) << 18 |
+           lg(seq->info.n_adc) << 26 | lg(seq->info.n_rf) << 34;
+}
+
 // Launch shape: the grid is a whole number of waves of (SMs x resident CTAs)
 // and every CTA gets the same number of spins, so no SM idles on a tail.
 koma::BlochLaunch choose_launch(const koma_ctx* ctx, int64_t n, bool fp64, int s_fp32 = 4, bool moving = false) {
@@ -1157,11 +1171,24 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     const bool moving = ph->moving();
     if (!fp64 && !moving && use_items_kernel(ph)) {
         const bool tuned = ph->tuned_seq == seq && ph->tuned_n_rec == seq->info.n_records;
+        int S = tuned ? ph->tuned_s : 4, block = tuned ? ph->tuned_block : 256;
+        if (!tuned) {
+            auto it = ctx->tune_cache.find(tune_key(ph, seq, true));
+            if (it != ctx->tune_cache.end()) {
+                S = it->second.first;
+                block = it->second.second;
+            }
+        }
         ctx->timing_recorded = false;
-        return simulate_items(ctx, ph, seq, sig_dev, st, tuned ? ph->tuned_s : 4, tuned ? ph->tuned_block : 256);
+        return simulate_items(ctx, ph, seq, sig_dev, st, S, block);
     }
     const bool tuned_k1 = ph->tuned_seq == seq && ph->tuned_n_rec == seq->info.n_records && ph->tuned_s > 0;
-    koma::BlochLaunch L = choose_launch(ctx, ph->n, fp64, tuned_k1 ? ph->tuned_s : 4, moving);
+    int s_k1 = tuned_k1 ? ph->tuned_s : 4;
+    if (!tuned_k1 && !fp64) {
+        auto it = ctx->tune_cache.find(tune_key(ph, seq, false));
+        if (it != ctx->tune_cache.end()) s_k1 = it->second.first;
+    }
+    koma::BlochLaunch L = choose_launch(ctx, ph->n, fp64, s_k1, moving);
     if (ph->n_groups > 1) {
         // size CTAs for the largest group (groups never share a CTA)
         int64_t gmax = 1;
@@ -1399,6 +1426,7 @@ extern "C" koma_status koma_tune(koma_ctx* ctx, const koma_phantom* ph_c, const 
     ph->tuned_n_rec = seq->info.n_records;
     ph->tuned_s = pick.s;
     ph->tuned_block = pick.block;
+    ctx->tune_cache[tune_key(ph, seq, items)] = {pick.s, pick.block};
     if (chosen) {
         rc = koma_simulate(ctx, ph, seq, KOMA_FP32_SPLITPHASE, sig_dev, stream);
         *chosen = ctx->last;

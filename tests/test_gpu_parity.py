@@ -301,3 +301,59 @@ def test_upload_cycles_reuse_memory(sim):
             first = free
         elif i > 1:
             assert free == first, "device footprint grew across identical cycles"
+
+
+def test_tuned_shape_is_reused_by_other_phantoms(sim):
+    """A shape tuned once is reused, without tuning, by another phantom of
+    the same size bucket (the autotuner's cache on the context)."""
+    ph, seq = workload("mrf", "small")
+    hp = sim.upload_phantom(ph)
+    hs = sim.upload_sequence(seq)
+    try:
+        choice = sim.tune(hp, hs)
+        # a second dictionary of the same shape: same sizes, other relaxation values
+        ph2, _ = workload("mrf", "small")
+        ph2.t2 = ph2.t2 * 1.1
+        hp2 = sim.upload_phantom(ph2)
+        try:
+            got = sim.simulate(hp2, hs).cpu().numpy()
+            info = sim.launch_info()
+            assert (info["spins_per_thread"], info["block"]) == (choice["spins_per_thread"], choice["block"])
+            ref = oracle.simulate(ph2, seq)
+            assert rel_err(got, ref) < TOL32
+        finally:
+            koma.koma_phantom_free(hp2)
+    finally:
+        koma.koma_sequence_free(hs)
+        koma.koma_phantom_free(hp)
+
+
+@pytest.mark.parametrize("name", ["epi512", "mrf", "paper_d"])
+def test_simulate_captures_into_a_cuda_graph(sim, name):
+    """After one warm call (scratch and launch tables in place) a simulation
+    is capturable: the Bloch, grouped and motion launches replay from a CUDA
+    graph bitwise identical to the direct call."""
+    import torch
+    ph, seq = workload(name, "small")
+    hp = sim.upload_phantom(ph)
+    hs = sim.upload_sequence(seq)
+    try:
+        s = torch.cuda.Stream()
+        out = torch.empty((ph.n_groups, seq.n_adc), dtype=torch.complex128, device="cuda")
+        with torch.cuda.stream(s):
+            sim.simulate(hp, hs, out=out, stream=s)
+        sim.sync(s)
+        ref = out.clone()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            sim.simulate(hp, hs, out=out, stream=s)
+        out.zero_()
+        torch.cuda.synchronize()
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+        del g
+    finally:
+        koma.koma_sequence_free(hs)
+        koma.koma_phantom_free(hp)
