@@ -76,6 +76,10 @@ typedef struct {
     int64_t n_records;        /* step records the kernel walked              */
     int64_t partial_bytes;    /* scratch used for per-CTA signal partials     */
     void *bloch_stream;       /* stream the kernels were launched on          */
+    int32_t split;            /* CTAs sharing a spin range, dividing its ADC
+                                 runs (1: none; used when the spins fill few
+                                 warps and sampling dominates the work)     */
+    int32_t reserved_;
 } koma_launch_info;
 
 /* Counts of the uploaded sequence by step class (hot-path cost model). */

@@ -129,13 +129,20 @@ struct BlochArgs {
     const double* p64 = nullptr;    // [P64_N][n_pad]
     int64_t n_pad = 0;
     int64_t n = 0;
-    const int64_t* cta_begin = nullptr;  // [grid + 1] first spin of each CTA (grouped), or null
+    const int64_t* cta_begin = nullptr;  // [spin CTAs + 1] first spin of each (grouped), or null
     int64_t spins_per_cta = 0;           // uniform split when cta_begin is null
+    // ADC-run split (FP32 Bloch and motion kernels): `split` CTAs walk each
+    // spin range; CTA spin_cta * split + p takes the ADC records whose index
+    // is p mod split and writes those samples of the range's partial row
+    // (one row per spin range, every sample written by exactly one part; all
+    // parts step every RF and PREC record). For launches whose spins fill
+    // few warps. 1 = off.
     const void* rec = nullptr;
     int64_t n_rec = 0;
     void* partial = nullptr;        // FP32: float2 [grid][n_adc]; FP64: double2 [grid][n_adc]
     int64_t n_adc = 0;
     int* status = nullptr;          // device flag word (bit 0: a bounded wait gave up)
+    int split = 1;
     float ext[4] = {0, 0, 0, 0};    // max |x|, |y|, |z| (m), |df| (Hz) over the phantom
     int used = 0;                   // bit d: coordinate d (x, y, z, df) is nonzero somewhere;
                                     // bit 4 + d: velocity component d is nonzero somewhere

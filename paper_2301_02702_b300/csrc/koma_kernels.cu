@@ -1,13 +1,16 @@
 // CUDA kernels of libkoma (sm_103a).
 //
-// K1  bloch_fp32_kernel<S>  spins stepped through the record stream in FP32,
-//                           phase in hi/lo FP32, signal partials per CTA.
+// K1  bloch_fp32_kernel<S, SPLIT>  spins stepped through the record stream
+//                           in FP32, phase in hi/lo FP32, signal partials per
+//                           spin range (SPLIT: several CTAs per range divide
+//                           its ADC runs).
 // K1d bloch_fp64_kernel     the same walk in FP64 (KOMA_FP64).
 // K2  reduce_partials<P>    fixed-order FP64 sum of the per-CTA partials.
 // K3  bloch_items_kernel<S> grouped phantoms: one warp per work item of one
 //                           group, persistent CTAs, per-item partial rows.
 // K4  bloch_batches_kernel  serving: batches of many simulations in one
 //                           persistent launch (spin ranges of each request).
+// K5  bloch_motion_kernel<S, SPLIT>  moving spins, x(t) = x + v t.
 //
 // Method: KomaMRI.jl paper, Section "Physical and Mathematical Background"
 // (Bloch equation, operator splitting, spinor rotation in the excitation
@@ -656,7 +659,7 @@ __device__ __forceinline__ void issue_tile(Rec32 (*s_rec)[kTile], const uint32_t
 // Warp sample sums are staged per warp in shared memory and summed over
 // warps in a fixed order into one FP32 partial per (CTA, sample).
 // ---------------------------------------------------------------------------
-template <int S>
+template <int S, bool SPLIT>
 __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_constant__ BlochArgs A) {
     __shared__ __align__(128) Rec32 s_rec[2][kTile];
     __shared__ __align__(8) uint64_t s_bar[2];
@@ -669,13 +672,17 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
     const int nthr = blockDim.x;
     const int nwarps = nthr >> 5;
     const int cta = blockIdx.x;
+    // ADC-run split: CTAs cta = spin_cta * split + part share one spin range;
+    // part p handles the ADC records whose index is p mod split
+    const int split = SPLIT ? A.split : 1;
+    const int part = SPLIT ? cta % split : 0, scta = SPLIT ? cta / split : cta;
 
     int64_t c_begin, c_end;
     if (A.cta_begin) {
-        c_begin = A.cta_begin[cta];
-        c_end = A.cta_begin[cta + 1];
+        c_begin = A.cta_begin[scta];
+        c_end = A.cta_begin[scta + 1];
     } else {
-        c_begin = static_cast<int64_t>(cta) * A.spins_per_cta;
+        c_begin = static_cast<int64_t>(scta) * A.spins_per_cta;
         c_end = min(A.n, c_begin + A.spins_per_cta);
     }
     const int64_t np = A.n_pad;
@@ -684,12 +691,16 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
 
     int red_buf = 0;
     int64_t red_base = 0, red_end = 0;  // samples [red_base, red_end) staged
-    float2* __restrict__ partial = static_cast<float2*>(A.partial) + static_cast<int64_t>(cta) * A.n_adc;
+    // one partial row per spin range; with a split each part writes the
+    // samples of its own runs (s_own marks them in the staged window)
+    __shared__ unsigned char s_own[SPLIT ? 2 : 1][SPLIT ? kRed32 : 1];
+    float2* __restrict__ partial = static_cast<float2*>(A.partial) + static_cast<int64_t>(scta) * A.n_adc;
     auto red_slot = [&](int buf, int w, int i) -> float2& { return s_red_dyn[(buf * nwarps + w) * kRed32 + i]; };
     auto flush = [&]() {
         __syncthreads();
         const int cnt = static_cast<int>(red_end - red_base);
         for (int i = tid; i < cnt; i += nthr) {
+            if (SPLIT && !s_own[red_buf][i]) continue;
             float sr = 0.f, si = 0.f;
             for (int w = 0; w < nwarps; ++w) {
                 const float2 v = red_slot(red_buf, w, i);
@@ -741,11 +752,16 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
                 const int L = min(max(R.count & kCountMask, 1), kMaxAdcRun);
                 const int64_t k0 = R.k0;
                 if (k0 + L > red_base + kRed32) flush();
-                float er[S], ei[S];
-                sp.exact(R, false, A.p32, np, A.used, er, ei);
                 const int off = static_cast<int>(k0 - red_base);
-                sp.adc(R, L, er, ei, lane,
-                       [&](int i, float sr, float si) { red_slot(red_buf, warp, off + i) = make_float2(sr, si); });
+                const bool own = !SPLIT || (t * kTile + r) % split == part;
+                if (SPLIT && warp == 0)
+                    for (int i = lane; i < L; i += 32) s_own[red_buf][off + i] = own;
+                if (own) {
+                    float er[S], ei[S];
+                    sp.exact(R, false, A.p32, np, A.used, er, ei);
+                    sp.adc(R, L, er, ei, lane,
+                           [&](int i, float sr, float si) { red_slot(red_buf, warp, off + i) = make_float2(sr, si); });
+                }
                 red_end = k0 + L;
             }
         }
@@ -1228,7 +1244,7 @@ struct MSpins {
     }
 };
 
-template <int S>
+template <int S, bool SPLIT>
 __global__ void __launch_bounds__(kMaxBlock, 2) bloch_motion_kernel(const __grid_constant__ BlochArgs A) {
     __shared__ __align__(128) RecM s_rec[2][kTile];
     __shared__ __align__(8) uint64_t s_bar[2];
@@ -1240,13 +1256,17 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_motion_kernel(const __grid
     const int nthr = blockDim.x;
     const int nwarps = nthr >> 5;
     const int cta = blockIdx.x;
+    // ADC-run split: CTAs cta = spin_cta * split + part share one spin range;
+    // part p handles the ADC records whose index is p mod split
+    const int split = SPLIT ? A.split : 1;
+    const int part = SPLIT ? cta % split : 0, scta = SPLIT ? cta / split : cta;
 
     int64_t c_begin, c_end;
     if (A.cta_begin) {
-        c_begin = A.cta_begin[cta];
-        c_end = A.cta_begin[cta + 1];
+        c_begin = A.cta_begin[scta];
+        c_end = A.cta_begin[scta + 1];
     } else {
-        c_begin = static_cast<int64_t>(cta) * A.spins_per_cta;
+        c_begin = static_cast<int64_t>(scta) * A.spins_per_cta;
         c_end = min(A.n, c_begin + A.spins_per_cta);
     }
     const int64_t np = A.n_pad;
@@ -1254,13 +1274,17 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_motion_kernel(const __grid
     sp.load(A.p32, A.pv32, np, c_begin + tid, nthr, c_end);
 
     int red_buf = 0;
-    int64_t red_base = 0, red_end = 0;
-    float2* __restrict__ partial = static_cast<float2*>(A.partial) + static_cast<int64_t>(cta) * A.n_adc;
+    int64_t red_base = 0, red_end = 0;  // samples [red_base, red_end) staged
+    // one partial row per spin range; with a split each part writes the
+    // samples of its own runs (s_own marks them in the staged window)
+    __shared__ unsigned char s_own[SPLIT ? 2 : 1][SPLIT ? kRed32 : 1];
+    float2* __restrict__ partial = static_cast<float2*>(A.partial) + static_cast<int64_t>(scta) * A.n_adc;
     auto red_slot = [&](int buf, int w, int i) -> float2& { return s_red_dyn[(buf * nwarps + w) * kRed32 + i]; };
     auto flush = [&]() {
         __syncthreads();
         const int cnt = static_cast<int>(red_end - red_base);
         for (int i = tid; i < cnt; i += nthr) {
+            if (SPLIT && !s_own[red_buf][i]) continue;
             float sr = 0.f, si = 0.f;
             for (int w = 0; w < nwarps; ++w) {
                 const float2 v = red_slot(red_buf, w, i);
@@ -1315,11 +1339,16 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_motion_kernel(const __grid
                 const int L = min(max(R.count & kCountMask, 1), kMaxAdcRun);
                 const int64_t k0 = R.k0;
                 if (k0 + L > red_base + kRed32) flush();
-                float er[S], ei[S];
-                sp.exact(R, false, 12, A.p32, A.pv32, np, A.used, er, ei);
                 const int off = static_cast<int>(k0 - red_base);
-                sp.adc(R, L, A.pv32, np, A.used, er, ei, lane,
-                       [&](int i, float sr, float si) { red_slot(red_buf, warp, off + i) = make_float2(sr, si); });
+                const bool own = !SPLIT || (t * kTile + r) % split == part;
+                if (SPLIT && warp == 0)
+                    for (int i = lane; i < L; i += 32) s_own[red_buf][off + i] = own;
+                if (own) {
+                    float er[S], ei[S];
+                    sp.exact(R, false, 12, A.p32, A.pv32, np, A.used, er, ei);
+                    sp.adc(R, L, A.pv32, np, A.used, er, ei, lane,
+                           [&](int i, float sr, float si) { red_slot(red_buf, warp, off + i) = make_float2(sr, si); });
+                }
                 red_end = k0 + L;
             }
         }
@@ -1579,7 +1608,10 @@ size_t fp32_dyn_smem(int block) { return static_cast<size_t>(2 * (block / 32) * 
 
 template <int S>
 cudaError_t prepare_fp32(size_t dyn) {
-    return cudaFuncSetAttribute(bloch_fp32_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(bloch_fp32_kernel<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(dyn));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(bloch_fp32_kernel<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(dyn));
 }
 
@@ -1587,7 +1619,7 @@ template <int S>
 cudaError_t occupancy_fp32(int* n, int block, size_t dyn) {
     cudaError_t e = prepare_fp32<S>(dyn);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, bloch_fp32_kernel<S>, block, dyn);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, bloch_fp32_kernel<S, false>, block, dyn);
 }
 
 template <int S>
@@ -1595,12 +1627,18 @@ cudaError_t launch_fp32(const BlochArgs& a, const BlochLaunch& L, cudaStream_t s
     const size_t dyn = fp32_dyn_smem(L.block);
     cudaError_t e = prepare_fp32<S>(dyn);
     if (e != cudaSuccess) return e;
-    bloch_fp32_kernel<S><<<L.grid, L.block, dyn, st>>>(a);
+    if (a.split > 1)
+        bloch_fp32_kernel<S, true><<<L.grid, L.block, dyn, st>>>(a);
+    else
+        bloch_fp32_kernel<S, false><<<L.grid, L.block, dyn, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t prepare_motion(size_t dyn) {
-    return cudaFuncSetAttribute(bloch_motion_kernel<kMotionSpinsPerThread>,
+    cudaError_t e = cudaFuncSetAttribute(bloch_motion_kernel<kMotionSpinsPerThread, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(bloch_motion_kernel<kMotionSpinsPerThread, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
 }
 
@@ -1672,8 +1710,8 @@ int motion_ctas_per_sm(int block) {
     const size_t dyn = fp32_dyn_smem(block);
     if (prepare_motion(dyn) != cudaSuccess) return -1;
     int n = 0;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_motion_kernel<kMotionSpinsPerThread>, block,
-                                                         dyn) == cudaSuccess ? n : -1;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_motion_kernel<kMotionSpinsPerThread, false>,
+                                                         block, dyn) == cudaSuccess ? n : -1;
 }
 
 int launch_bloch_motion(const BlochArgs& a, const BlochLaunch& L, void* stream) {
@@ -1683,7 +1721,10 @@ int launch_bloch_motion(const BlochArgs& a, const BlochLaunch& L, void* stream) 
     const size_t dyn = fp32_dyn_smem(L.block);
     cudaError_t e = prepare_motion(dyn);
     if (e != cudaSuccess) return e;
-    bloch_motion_kernel<kMotionSpinsPerThread><<<L.grid, L.block, dyn, static_cast<cudaStream_t>(stream)>>>(a);
+    if (a.split > 1)
+        bloch_motion_kernel<kMotionSpinsPerThread, true><<<L.grid, L.block, dyn, static_cast<cudaStream_t>(stream)>>>(a);
+    else
+        bloch_motion_kernel<kMotionSpinsPerThread, false><<<L.grid, L.block, dyn, static_cast<cudaStream_t>(stream)>>>(a);
     return cudaGetLastError();
 }
 

@@ -1106,6 +1106,7 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     ctx->last.spins_per_cta = 32LL * S * (block / 32);
     ctx->last.n_records = seq->info.n_records;
     ctx->last.partial_bytes = static_cast<int64_t>(ph->n_items * n_adc * 8);
+    ctx->last.split = 1;
     return KOMA_OK;
 }
 
@@ -1117,6 +1118,20 @@ uint64_t tune_key(const koma_phantom* ph, const koma_sequence* seq, bool items) 
     const uint64_t family = items ? 1 : (ph->moving() ? 2 : 0);
     return family | lg(ph->n) << 2 | lg(ph->n_groups) << 10 | lg(seq->info.n_records) << 18 |
            lg(seq->info.n_adc) << 26 | lg(seq->info.n_rf) << 34;
+}
+
+// ADC-run split for a launch whose spins fill few warps: CTAs sharing a
+// spin range each take every split-th ADC record (all of them step the RF
+// and PREC records), up to about 16 resident warps per SM. Only when
+// sampling dominates the work (the RF steps are repeated by every part) and
+// there are enough runs to share.
+int choose_split(const koma_ctx* ctx, const koma::BlochLaunch& L, const koma_sequence* seq) {
+    const int64_t warps = static_cast<int64_t>(L.grid) * ((L.block + 31) / 32);
+    const int64_t target = static_cast<int64_t>(ctx->sm_count) * 16;
+    if (50 * seq->info.n_rf > 8 * seq->info.n_adc) return 1;
+    int split = 1;
+    while (split < 8 && warps * split * 2 <= target && seq->info.n_adc_runs >= 8 * split) split *= 2;
+    return split;
 }
 
 // Launch shape: the grid is a whole number of waves of (SMs x resident CTAs)
@@ -1206,7 +1221,10 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
         L.spins_per_cta = std::min<int64_t>(L.spins_per_cta, L.block);
         L.grid = static_cast<int>((ph->n + L.spins_per_cta - 1) / L.spins_per_cta);
     }
+    const int split = (!fp64 && ph->n_groups == 1) ? choose_split(ctx, L, seq) : 1;
+    L.grid *= split;
     koma::BlochArgs A;
+    A.split = split;
     A.p32 = ph->p32;
     A.p64 = ph->p64;
     A.n_pad = ph->n_pad;
@@ -1262,14 +1280,15 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     }
 
     const size_t elem = fp64 ? 2 * sizeof(double) : 2 * sizeof(float);
-    const size_t need = static_cast<size_t>(L.grid) * static_cast<size_t>(n_adc) * elem;
+    const int rows = L.grid / split;  // one partial row per spin range
+    const size_t need = static_cast<size_t>(rows) * static_cast<size_t>(n_adc) * elem;
     {
         koma_status s = grow_scratch(ctx, need, st);
         if (s != KOMA_OK) return s;
     }
     A.partial = ctx->scratch;
     R.partial = ctx->scratch;
-    R.grid = L.grid;
+    R.grid = rows;
     R.sig = sig_dev;
 
     ctx->timing_recorded = false;
@@ -1295,6 +1314,7 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     ctx->last.spins_per_cta = L.spins_per_cta;
     ctx->last.n_records = seq->info.n_records;
     ctx->last.partial_bytes = static_cast<int64_t>(need);
+    ctx->last.split = split;
     return KOMA_OK;
 }
 

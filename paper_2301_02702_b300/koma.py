@@ -48,7 +48,7 @@ class LaunchInfo(ctypes.Structure):
     _fields_ = [("kernels", ctypes.c_int32), ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("spins_per_thread", ctypes.c_int32), ("spins_per_cta", ctypes.c_int64),
                 ("n_records", ctypes.c_int64), ("partial_bytes", ctypes.c_int64),
-                ("bloch_stream", ctypes.c_void_p)]
+                ("bloch_stream", ctypes.c_void_p), ("split", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -357,3 +357,21 @@ def test_simulate_captures_into_a_cuda_graph(sim, name):
     finally:
         koma.koma_sequence_free(hs)
         koma.koma_phantom_free(hp)
+
+
+def test_adc_run_split_for_small_single_shot_problems(sim):
+    """A phantom that fills few warps under a single-shot readout gets CTAs
+    that share its spin ranges and divide the ADC runs (the launch reports
+    the split); the signal matches the oracle and is deterministic. A launch
+    that fills the GPU, or an RF-dominated sequence, does not split."""
+    ph, seq = workload("paper_b", "full")
+    a = gpu_signal(sim, ph, seq)
+    info = sim.launch_info()
+    assert info["split"] > 1
+    b = gpu_signal(sim, ph, seq)
+    assert np.array_equal(a, b)
+    assert rel_err(a, oracle.simulate(ph, seq)) < TOL32
+    gpu_signal(sim, *workload("epi512", "full"))
+    assert sim.launch_info()["split"] == 1
+    gpu_signal(sim, *workload("gre32", "full"))
+    assert sim.launch_info()["split"] == 1
