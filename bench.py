@@ -591,7 +591,14 @@ def run_ours(args, rank, world, local):
                "path": "Simulator from pinned host arrays: phantom + velocity upload, sequence preprocessing + "
                        "upload, simulate, signal copy-back into pinned memory, free"}
     elif not args.no_e2e:
-        ctx2 = koma.koma_init(local)
+        sim2 = koma.Simulator(local)  # a context of its own
+        ctx2 = sim2.ctx
+        if tuned is not None:
+            # a user tunes a shape once; later host calls of that shape reuse the choice
+            hp2, hs2 = sim2.upload_phantom(ph), sim2.upload_sequence(seq)
+            sim2.tune(hp2, hs2, stream)
+            koma.koma_sequence_free(hs2)
+            koma.koma_phantom_free(hp2)
         host_sig = pinned(np.empty((ph.n_groups, seq.n_adc), dtype=np.complex128))
         koma.koma_simulate_host(ctx2, ph_host, seq_host, koma.KOMA_FP32_SPLITPHASE, out=host_sig)  # warm
         n_e2e = max(1, min(args.steps, args.e2e_steps))
@@ -601,7 +608,7 @@ def run_ours(args, rank, world, local):
             koma.koma_simulate_host(ctx2, ph_host, seq_host, koma.KOMA_FP32_SPLITPHASE, out=host_sig)
         t_e2e = (time.perf_counter() - t0) / n_e2e
         t_e2e = reduce_max(t_e2e, world)
-        koma.koma_destroy(ctx2)
+        sim2.close()
         # raw FP64 phantom rows (the FP32 block is built on the device), three record streams
         h2d = ph.n * 7 * 8 + info["n_records"] * (64 + 128 + 128)
         e2e = {"value": units * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

@@ -1186,7 +1186,8 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     const bool moving = ph->moving();
     if (!fp64 && !moving && use_items_kernel(ph)) {
         const bool tuned = ph->tuned_seq == seq && ph->tuned_n_rec == seq->info.n_records;
-        int S = tuned ? ph->tuned_s : 4, block = tuned ? ph->tuned_block : 256;
+        // untuned default: the tuner's usual pick for dictionaries of small groups
+        int S = tuned ? ph->tuned_s : 2, block = tuned ? ph->tuned_block : 128;
         if (!tuned) {
             auto it = ctx->tune_cache.find(tune_key(ph, seq, true));
             if (it != ctx->tune_cache.end()) {
