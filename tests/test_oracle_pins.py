@@ -477,3 +477,21 @@ def test_motion_matches_rk4():
         still = oracle.simulate(Phantom(*(np.atleast_1d(spin[k]) for k in ("x", "y", "z", "pd", "t1", "t2", "dw"))),
                                 seq)[0]
         assert np.max(np.abs(still - r_sig)) > 1e-2
+
+
+def test_gamma_matches_the_value_the_paper_prints():
+    """The oracle's gamma, read off a hard pulse's flip angle (angle = gamma
+    B1 dt), agrees with the paper's printed 0.267538 rad/us/mT to its
+    precision (tests/golden/gyromagnetic_ratio.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "gyromagnetic_ratio.txt")
+    vals = dict(line.split() for line in open(path) if line.strip() and not line.startswith("#"))
+    g_paper = float(vals["gamma_rad_per_us_per_mT"]) * 1e6 * 1e3  # rad/s/T
+    tol = float(vals["relative_precision"])
+    b1, tp = 1e-6, 1e-6  # T, s: a small angle, so sin(angle) ~ angle is resolved
+    seq = hard(SequenceBuilder(), 0.0, tp, adc=True).build()
+    seq.b1[:] = b1
+    sig = oracle.simulate(one_spin(), seq)
+    angle = float(np.arcsin(abs(sig[0, 0])))
+    g_oracle = angle / (b1 * tp)
+    assert abs(g_oracle / g_paper - 1.0) < tol
