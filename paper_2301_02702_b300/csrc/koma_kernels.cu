@@ -236,10 +236,13 @@ struct Spins {
     float xh[S], yh[S], zh[S], fh[S], m0[S], r1[S], r2[S];
     float mx[S], my[S], mz[S], em1[S], em2[S], zr[S], zi[S], zr2[S], zi2[S];
     // lo halves of x, y, z, df: in registers for 2 spins per thread (the
-    // grouped kernel's usual shape), read from L1 at each exact evaluation
-    // for 4 (no registers to spare there)
+    // grouped kernel's usual shape); for 4 (no registers to spare) from a
+    // shared-memory copy the kernel made of its slots (`slo`, K1), else from
+    // L1 at each exact evaluation
     static constexpr bool kLoRegs = S <= 2;
     float xl[kLoRegs ? S : 1], yl[kLoRegs ? S : 1], zl[kLoRegs ? S : 1], fl[kLoRegs ? S : 1];
+    const float* slo = nullptr;  // shared [4][S * stride]: x, y, z, df lo of slot s of thread t at t + s * stride
+    int sidx = 0;                // this thread's t
     int64_t base, end;
     int stride;
     float dt_cached;               // em1/em2 belong to this dt
@@ -253,10 +256,12 @@ struct Spins {
     template <int N>
     __device__ __forceinline__ float lo(const float (&regs)[N], int row, int s, const float* __restrict__ P,
                                         int64_t np, int64_t j, bool v) const {
-        if constexpr (kLoRegs)
+        if constexpr (kLoRegs) {
             return regs[s];
-        else
+        } else {
+            if (slo) return slo[((row - P32_XL) >> 1) * (S * stride) + sidx + s * stride];
             return v ? P[row * np + j] : 0.f;
+        }
     }
 
     __device__ __forceinline__ void load(const float* __restrict__ P, int64_t np, int64_t base_, int stride_,
@@ -688,6 +693,20 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
     const int64_t np = A.n_pad;
     Spins<S> sp;
     sp.load(A.p32, np, c_begin + tid, nthr, c_end);
+    // the lo halves of the CTA's spins, read at every exact evaluation
+    __shared__ float s_lo[Spins<S>::kLoRegs ? 1 : 4 * S * kMaxBlock];
+    if constexpr (!Spins<S>::kLoRegs) {
+        for (int i = tid; i < S * nthr; i += nthr) {
+            const int64_t j = c_begin + i;
+            const bool v = j < c_end;
+            s_lo[0 * S * nthr + i] = v ? A.p32[P32_XL * np + j] : 0.f;
+            s_lo[1 * S * nthr + i] = v ? A.p32[P32_YL * np + j] : 0.f;
+            s_lo[2 * S * nthr + i] = v ? A.p32[P32_ZL * np + j] : 0.f;
+            s_lo[3 * S * nthr + i] = v ? A.p32[P32_FL * np + j] : 0.f;
+        }
+        sp.slo = s_lo;
+        sp.sidx = tid;
+    }
 
     int red_buf = 0;
     int64_t red_base = 0, red_end = 0;  // samples [red_base, red_end) staged
