@@ -978,6 +978,12 @@ struct MSpins {
     int stride;
     float dt_cached;
     int rf_mode;
+    // shared [7][S * stride]: lo halves of x, y, z, df, v_x, v_y, v_z of slot
+    // s of thread t at t + s * stride (the kernel copies them once)
+    const float* slo = nullptr;
+    int sidx = 0;
+
+    __device__ __forceinline__ float lo(int q, int s) const { return slo[q * (S * stride) + sidx + s * stride]; }
 
     __device__ __forceinline__ int64_t index(int s) const { return base + static_cast<int64_t>(s) * stride; }
 
@@ -1133,13 +1139,13 @@ struct MSpins {
             const int64_t j = index(s);
             const bool v = j < end;
             float F = 0.f;
-            if (terms & 1) F += frac_product(xh[s], v ? P[P32_XL * np + j] : 0.f, R.a[0], R.a[1]);
-            if (terms & 2) F += frac_product(yh[s], v ? P[P32_YL * np + j] : 0.f, R.a[2], R.a[3]);
-            if (terms & 4) F += frac_product(zh[s], v ? P[P32_ZL * np + j] : 0.f, R.a[4], R.a[5]);
-            if (terms & 8) F += frac_product(fh[s], v ? P[P32_FL * np + j] : 0.f, th, tl);
-            if (terms & 16) F += frac_product(vxh[s], v ? V[PV32_XL * np + j] : 0.f, R.a[koff], R.a[koff + 1]);
-            if (terms & 32) F += frac_product(vyh[s], v ? V[PV32_YL * np + j] : 0.f, R.a[koff + 2], R.a[koff + 3]);
-            if (terms & 64) F += frac_product(vzh[s], v ? V[PV32_ZL * np + j] : 0.f, R.a[koff + 4], R.a[koff + 5]);
+            if (terms & 1) F += frac_product(xh[s], lo(0, s), R.a[0], R.a[1]);
+            if (terms & 2) F += frac_product(yh[s], lo(1, s), R.a[2], R.a[3]);
+            if (terms & 4) F += frac_product(zh[s], lo(2, s), R.a[4], R.a[5]);
+            if (terms & 8) F += frac_product(fh[s], lo(3, s), th, tl);
+            if (terms & 16) F += frac_product(vxh[s], lo(4, s), R.a[koff], R.a[koff + 1]);
+            if (terms & 32) F += frac_product(vyh[s], lo(5, s), R.a[koff + 2], R.a[koff + 3]);
+            if (terms & 64) F += frac_product(vzh[s], lo(6, s), R.a[koff + 4], R.a[koff + 5]);
             float sn = 0.f, cs = 1.f;
             if (terms) {
                 const float r = F - rintf(F);
@@ -1184,9 +1190,9 @@ struct MSpins {
             const int64_t j = index(s);
             const bool v = j < end;
             float p = fmaf(dkx, xh[s], fmaf(dky, yh[s], fmaf(dkz, zh[s], fh[s] * dtau)));
-            if (used & 16) p += frac_product(vxh[s], v ? V[PV32_XL * np + j] : 0.f, R.a[18], R.a[19]);
-            if (used & 32) p += frac_product(vyh[s], v ? V[PV32_YL * np + j] : 0.f, R.a[20], R.a[21]);
-            if (used & 64) p += frac_product(vzh[s], v ? V[PV32_ZL * np + j] : 0.f, R.a[22], R.a[23]);
+            if (used & 16) p += frac_product(vxh[s], lo(4, s), R.a[18], R.a[19]);
+            if (used & 32) p += frac_product(vyh[s], lo(5, s), R.a[20], R.a[21]);
+            if (used & 64) p += frac_product(vzh[s], lo(6, s), R.a[22], R.a[23]);
             phi1[s] = p - rintf(p);
             phi2[s] = dtau * fmaf(dkx, vxh[s], fmaf(dky, vyh[s], dkz * vzh[s]));
             mag[s] = exp2f(-dtau * r2[s]);
@@ -1291,6 +1297,22 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_motion_kernel(const __grid
     const int64_t np = A.n_pad;
     MSpins<S> sp;
     sp.load(A.p32, A.pv32, np, c_begin + tid, nthr, c_end);
+    // the lo halves of the CTA's positions, off-resonances and velocities,
+    // in dynamic shared memory after the reduction stage
+    float* s_lo = reinterpret_cast<float*>(s_red_dyn + 2 * nwarps * kRed32);
+    for (int i = tid; i < S * nthr; i += nthr) {
+        const int64_t j = c_begin + i;
+        const bool v = j < c_end;
+        s_lo[0 * S * nthr + i] = v ? A.p32[P32_XL * np + j] : 0.f;
+        s_lo[1 * S * nthr + i] = v ? A.p32[P32_YL * np + j] : 0.f;
+        s_lo[2 * S * nthr + i] = v ? A.p32[P32_ZL * np + j] : 0.f;
+        s_lo[3 * S * nthr + i] = v ? A.p32[P32_FL * np + j] : 0.f;
+        s_lo[4 * S * nthr + i] = v ? A.pv32[PV32_XL * np + j] : 0.f;
+        s_lo[5 * S * nthr + i] = v ? A.pv32[PV32_YL * np + j] : 0.f;
+        s_lo[6 * S * nthr + i] = v ? A.pv32[PV32_ZL * np + j] : 0.f;
+    }
+    sp.slo = s_lo;
+    sp.sidx = tid;
 
     int red_buf = 0;
     int64_t red_base = 0, red_end = 0;  // samples [red_base, red_end) staged
@@ -1725,8 +1747,12 @@ int launch_bloch_fp32(const BlochArgs& a, const BlochLaunch& L, void* stream) {
     }
 }
 
+size_t motion_dyn_smem(int block) {
+    return fp32_dyn_smem(block) + static_cast<size_t>(7 * kMotionSpinsPerThread * block) * sizeof(float);
+}
+
 int motion_ctas_per_sm(int block) {
-    const size_t dyn = fp32_dyn_smem(block);
+    const size_t dyn = motion_dyn_smem(block);
     if (prepare_motion(dyn) != cudaSuccess) return -1;
     int n = 0;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_motion_kernel<kMotionSpinsPerThread, false>,
@@ -1737,7 +1763,7 @@ int launch_bloch_motion(const BlochArgs& a, const BlochLaunch& L, void* stream) 
     if (L.block <= 0 || L.block > kMaxBlock || L.block % 32 != 0 || L.grid <= 0 ||
         L.spins_per_thread != kMotionSpinsPerThread || !a.pv32)
         return cudaErrorInvalidValue;
-    const size_t dyn = fp32_dyn_smem(L.block);
+    const size_t dyn = motion_dyn_smem(L.block);
     cudaError_t e = prepare_motion(dyn);
     if (e != cudaSuccess) return e;
     if (a.split > 1)
