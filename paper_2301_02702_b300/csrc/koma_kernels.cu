@@ -807,7 +807,7 @@ __device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const uint32_t
                                            const float* __restrict__ p32, int64_t np, const Rec32* grec,
                                            int64_t n_rec, int64_t rb, int64_t re, float* state, int64_t rf_hdr,
                                            const float (&ext)[4], int used, int64_t wb, int64_t we,
-                                           float2* __restrict__ row, int* status) {
+                                           float2* __restrict__ row, int* status, float* warp_lo) {
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const Rec32* base = grec + rb;
@@ -815,6 +815,22 @@ __device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const uint32_t
     const int64_t n_tiles = (n_walk + kTile - 1) / kTile;
     Spins<S> sp;
     sp.load(p32, np, wb + lane, 32, we);
+    if constexpr (!Spins<S>::kLoRegs) {
+        // the lo halves of the warp's spins, read at every exact evaluation
+        __syncwarp();  // the previous batch's reads of warp_lo are done
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int64_t j = wb + lane + 32 * s;
+            const bool v = j < we;
+            warp_lo[0 * S * 32 + lane + 32 * s] = v ? p32[P32_XL * np + j] : 0.f;
+            warp_lo[1 * S * 32 + lane + 32 * s] = v ? p32[P32_YL * np + j] : 0.f;
+            warp_lo[2 * S * 32 + lane + 32 * s] = v ? p32[P32_ZL * np + j] : 0.f;
+            warp_lo[3 * S * 32 + lane + 32 * s] = v ? p32[P32_FL * np + j] : 0.f;
+        }
+        __syncwarp();
+        sp.slo = warp_lo;
+        sp.sidx = lane;
+    }
     if (state && rb > 0) {
         sp.load_state(state, np);
         if (rf_hdr >= 0) sp.set_mode(grec[rf_hdr], ext);
@@ -879,6 +895,7 @@ template <int S>
 __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_kernel(const __grid_constant__ ItemArgs A) {
     __shared__ __align__(128) Rec32 s_rec[2][kTile];
     __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ float s_lo_w[Spins<S>::kLoRegs ? 1 : kMaxWarps * 4 * S * 32];  // per-warp lo halves
     __shared__ int64_t s_batch;
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -906,7 +923,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_kernel(const __grid_
             row = static_cast<float2*>(A.partial) + item * A.n_adc;
         }
         if (!walk_batch<S>(s_rec, bar, g0, A.p32, A.n_pad, static_cast<const Rec32*>(A.rec), A.n_rec, 0, A.n_rec,
-                           nullptr, -1, A.ext, A.used, ib, ie, row, A.status))
+                           nullptr, -1, A.ext, A.used, ib, ie, row, A.status, s_lo_w + warp * (4 * S * 32)))
             return;
     }
 }
@@ -924,6 +941,7 @@ template <int S>
 __global__ void __launch_bounds__(kMaxBlock, 2) bloch_batches_kernel(const __grid_constant__ BatchArgs A) {
     __shared__ __align__(128) Rec32 s_rec[2][kTile];
     __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ float s_lo_w[Spins<S>::kLoRegs ? 1 : kMaxWarps * 4 * S * 32];  // per-warp lo halves
     __shared__ int64_t s_batch;
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -948,7 +966,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_batches_kernel(const __gri
         float2* row = D.rows + static_cast<int64_t>(warp) * D.n_adc;
         const float ext[4] = {D.ext[0], D.ext[1], D.ext[2], D.ext[3]};
         if (!walk_batch<S>(s_rec, bar, g0, D.p32, D.n_pad, D.rec, D.n_rec, D.rec_begin, D.rec_end, D.state,
-                           D.rf_hdr, ext, D.used, wb, we, row, A.status))
+                           D.rf_hdr, ext, D.used, wb, we, row, A.status, s_lo_w + warp * (4 * S * 32)))
             return;
     }
 }
