@@ -79,7 +79,8 @@ typedef struct {
     int32_t split;            /* CTAs sharing a spin range, dividing its ADC
                                  runs (1: none; used when the spins fill few
                                  warps and sampling dominates the work)     */
-    int32_t reserved_;
+    int32_t mma_grid;         /* CTAs of the tensor-core readout (0: not
+                                 used by this call)                        */
 } koma_launch_info;
 
 /* Counts of the uploaded sequence by step class (hot-path cost model). */
@@ -91,6 +92,10 @@ typedef struct {
     int64_t n_records;   /* kernel records: RF steps + precession materialise + ADC runs */
     int64_t n_adc_runs;  /* ADC records (each <= 128 uniformly spaced samples) */
     int64_t n_materialize;
+    int64_t n_mma_groups; /* groups of ADC runs sharing their per-sample
+                             rotator (same dK, dtau), summed as matrix
+                             products on the tensor cores (FP32 path)      */
+    int64_t n_mma_runs;   /* ADC runs in those groups                       */
 } koma_sequence_info;
 
 /* gamma used by the library, rad/s/T. */
@@ -232,6 +237,16 @@ koma_status koma_sequence_plan(int64_t n_steps, const double *dt, const double *
  * items of at most 32 x (spins per thread) spins, one warp per item, in one
  * persistent launch taking items longest first; larger groups are split into
  * whole CTAs. Both end with a fixed-order per-group sum (deterministic).
+ * FP32 path, static ungrouped phantom: the ADC runs of the sequence's
+ * matrix-form groups (koma_sequence_info.n_mma_groups > 0: runs sharing
+ * their per-sample rotator, e.g. the readout lines of an EPI or a Cartesian
+ * scan) are summed by a tensor-core kernel: sample l of run r is
+ * sum_s E_s(r) z_s^l (E_s(r) the spin's Mxy at the run's first sample, z_s
+ * its per-sample rotator), a complex matrix product over the spins taken in
+ * FP16 hi/lo pairs (three products, ~22-bit operands) with FP32
+ * accumulation. The Bloch kernel then stores E (8 bytes per spin and run, in
+ * the scratch) instead of stepping those samples. koma_set_mma switches this
+ * off and on.
  * Errors: KOMA_E_INVALID (NULL handles, objects of another context, bad
  *   precision), KOMA_E_NOMEM (scratch over budget), KOMA_E_CUDA (launch).
  * Device-side waits are bounded; a wait that gives up is reported by the
@@ -308,13 +323,22 @@ koma_status koma_sync(koma_ctx *ctx, void *stream);
 
 /*
  * Kernel timing. With enable != 0, every later koma_simulate on ctx records
- * CUDA events on its stream before the Bloch kernel, between it and the
- * reduction, and after the reduction. koma_get_timing waits for the last
+ * CUDA events on its stream before the Bloch kernel, after it, after the
+ * tensor-core readout, and after the reduction. koma_get_timing waits for the last
  * call's final event and returns the two durations in milliseconds.
  * Errors: KOMA_E_INVALID (NULL, or no timed call yet), KOMA_E_CUDA.
  */
 koma_status koma_set_timing(koma_ctx *ctx, int enable);
 koma_status koma_get_timing(koma_ctx *ctx, float *bloch_ms, float *reduce_ms);
+/* The same call split into its three stages: the Bloch kernel, the
+ * tensor-core readout (0 when the call did not launch it) and the
+ * reduction; bloch_ms + mma_ms is koma_get_timing's bloch_ms. */
+koma_status koma_get_stage_timing(koma_ctx *ctx, float *bloch_ms, float *mma_ms, float *reduce_ms);
+
+/* Matrix-form (tensor-core) readout on (enable != 0, the default) or off:
+ * off, every ADC sample is stepped by the Bloch kernel. Errors:
+ * KOMA_E_INVALID (NULL). */
+koma_status koma_set_mma(koma_ctx *ctx, int enable);
 
 /* Launch description of the last koma_simulate on ctx. */
 koma_status koma_get_launch_info(const koma_ctx *ctx, koma_launch_info *info);

@@ -40,6 +40,36 @@ constexpr int kMaxAdcRun = 128;
 constexpr int kCountMask = 0xffff;   // samples field of an ADC record's count
 constexpr int kTermShift = 16;       // nonzero-term bits of PREC/ADC records
 
+// Matrix form of the readout. ADC runs whose samples share the per-sample
+// rotator (the same dK and dtau, as FP32 values) are grouped, up to kMmaRuns
+// runs a group. Sample l of run r sums E_s(r) z_s^l over the spins s, with
+// E_s(r) the spin's transverse magnetisation at the run's first sample (the
+// exact evaluation the Bloch kernel makes at every run start) and z_s the
+// rotator e^{-dtau/T2} e^{-i 2 pi (dK.x + df dtau)}: a complex matrix product
+// C[r][l] = sum_s E_s(r) z_s^l over spins, taken on the tensor cores. The
+// Bloch kernel stores E for the flagged ADC records (row `slot` of an
+// [n_slots][n_pad] buffer, slots in record order) instead of sampling them.
+constexpr int kMmaRuns = 64;          // runs per group: 128 matrix rows (Re, Im of each)
+constexpr int kMmaFlag = 1 << 28;     // ADC record count bit: sampled by the matrix form
+constexpr int kMmaMinRuns = 8;        // smallest group worth a tensor-core pass
+constexpr int64_t kMmaMinSamples = 1024;
+
+struct MmaGroup {
+    float dk[3];      // rotator: dK (turns/m) ...
+    float dtau;       // ... and dtau (s), as in the group's records
+    int32_t run0;     // first entry of the group in the run table
+    int32_t n_runs;   // 1..kMmaRuns
+    int32_t max_len;  // longest run (samples)
+    int32_t pad_;
+};
+static_assert(sizeof(MmaGroup) == 32, "MmaGroup layout");
+struct MmaRun {
+    int64_t k0;    // first sample
+    int32_t len;   // samples
+    int32_t slot;  // row of the E buffer
+};
+static_assert(sizeof(MmaRun) == 16, "MmaRun layout");
+
 // 64-byte record of the FP32 split-phase path.
 //   RF:   a[0..2] pi gbar gammabar dt (rad/m)   a[3..4] pi B1 gammabar dt (rad):
 //         the half-angle rotation vector of the step's field
@@ -150,6 +180,29 @@ struct BlochArgs {
     const float* pv32 = nullptr;    // [PV32_N][n_pad]
     const double* pv64 = nullptr;   // [3][n_pad]
     float vext[3] = {0, 0, 0};      // max |v_x|, |v_y|, |v_z| (m/s)
+    // matrix-form readout (FP32 static kernel only): if set, ADC records
+    // carrying kMmaFlag store E = Mxy at their first sample into row `slot`
+    // of this [n_slots][n_pad] buffer (slot = the record's rank among the
+    // flagged records) and are not sampled here
+    float2* mma_e = nullptr;
+};
+
+// Tensor-core readout (K6): CTA c takes spins [c spins_per_cta, +spins_per_cta)
+// in blocks of 32 and, for every group, writes the group's samples of row c
+// of `partial` (float2 [grid][n_adc]).
+struct MmaArgs {
+    const float* p32 = nullptr;
+    int64_t n_pad = 0;
+    int64_t n = 0;
+    const float2* e = nullptr;       // [n_slots][n_pad]
+    const MmaGroup* groups = nullptr;
+    int32_t n_groups = 0;
+    const MmaRun* runs = nullptr;
+    float2* partial = nullptr;
+    int64_t n_adc = 0;
+    int64_t spins_per_cta = 0;       // multiple of 32
+    float escale = 1.f, einv = 1.f;  // power-of-two scale keeping E in FP16 range
+    int* status = nullptr;
 };
 
 struct ItemArgs {
@@ -176,6 +229,11 @@ struct ReduceArgs {
     int64_t n_groups = 1;
     int64_t n_adc = 0;
     double* sig = nullptr;              // [n_groups][n_adc][2]
+    // samples k with from_mma[k] != 0 come from the tensor-core readout's
+    // rows instead (one group only)
+    const void* partial_mma = nullptr;
+    int grid_mma = 0;
+    const uint8_t* from_mma = nullptr;
 };
 
 // One batch of the serving kernel: a spin range of one request's phantom,
@@ -225,10 +283,10 @@ int host_records32(int64_t n_steps, const double* dt, const double* gx, const do
 // every spin (the upload's input rules) and takes the extents: `cs` must hold
 // first_bad = ~0 and max_bits = 0 before the launch; afterwards first_bad
 // is the lowest invalid spin (~0: none) and max_bits the bit patterns of
-// max |x|, |y|, |z| (m) and |df| (Hz) over the spins.
+// max |x|, |y|, |z| (m), |df| (Hz) and pd over the spins.
 struct ConvertStatus {
     unsigned long long first_bad;
-    unsigned long long max_bits[4];
+    unsigned long long max_bits[5];  // and max pd
 };
 int launch_phantom_convert(double* p64, float* p32, int64_t n, int64_t n_pad, ConvertStatus* cs, void* stream);
 int launch_bloch_fp32(const BlochArgs& a, const BlochLaunch& L, void* stream);
@@ -238,6 +296,8 @@ int launch_bloch_fp64(const BlochArgs& a, const BlochLaunch& L, void* stream);
 int launch_bloch_motion(const BlochArgs& a, const BlochLaunch& L, void* stream);
 int launch_bloch_fp64_motion(const BlochArgs& a, const BlochLaunch& L, void* stream);
 int motion_ctas_per_sm(int block);
+// Tensor-core readout: `grid` CTAs of the kernel's fixed shape (one per SM).
+int launch_readout_mma(const MmaArgs& a, int grid, void* stream);
 constexpr int kMotionSpinsPerThread = 2;
 int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream);
 // One thread waits, bounded by limit_ns, on an mbarrier nothing completes,

@@ -18,6 +18,7 @@
 // "Simulation blocks, Regime Switching, and Sequence-Aware Time Stepping"
 // (integral phase over piecewise-linear gradients). The signal at an ADC
 // sample is the sum of Mxy over spins (Section "GPU/CPU Parallelization").
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -710,6 +711,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
 
     int red_buf = 0;
     int64_t red_base = 0, red_end = 0;  // samples [red_base, red_end) staged
+    int mma_slot = 0;                   // flagged ADC records seen so far
     // one partial row per spin range; with a split each part writes the
     // samples of its own runs (s_own marks them in the staged window)
     __shared__ unsigned char s_own[SPLIT ? 2 : 1][SPLIT ? kRed32 : 1];
@@ -773,14 +775,28 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
                 if (k0 + L > red_base + kRed32) flush();
                 const int off = static_cast<int>(k0 - red_base);
                 const bool own = !SPLIT || (t * kTile + r) % split == part;
+                // a run of the matrix-form readout: only its first sample's
+                // Mxy is stored (its samples of this CTA's row are never read)
+                const bool mma = A.mma_e != nullptr && (R.count & kMmaFlag);
                 if (SPLIT && warp == 0)
-                    for (int i = lane; i < L; i += 32) s_own[red_buf][off + i] = own;
+                    for (int i = lane; i < L; i += 32) s_own[red_buf][off + i] = own && !mma;
                 if (own) {
                     float er[S], ei[S];
                     sp.exact(R, false, A.p32, np, A.used, er, ei);
-                    sp.adc(R, L, er, ei, lane,
-                           [&](int i, float sr, float si) { red_slot(red_buf, warp, off + i) = make_float2(sr, si); });
+                    if (mma) {
+                        float2* __restrict__ erow = A.mma_e + static_cast<int64_t>(mma_slot) * np;
+#pragma unroll
+                        for (int s = 0; s < S; ++s) {
+                            const int64_t j = sp.index(s);
+                            if (j < sp.end) erow[j] = make_float2(er[s], ei[s]);
+                        }
+                    } else {
+                        sp.adc(R, L, er, ei, lane, [&](int i, float sr, float si) {
+                            red_slot(red_buf, warp, off + i) = make_float2(sr, si);
+                        });
+                    }
                 }
+                mma_slot += mma ? 1 : 0;
                 red_end = k0 + L;
             }
         }
@@ -1554,6 +1570,280 @@ __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_cons
 }
 
 // ---------------------------------------------------------------------------
+// K6: tensor-core readout (the matrix form of a group of ADC runs).
+//
+// For a group of R <= 64 runs sharing the rotator z_s and a block of 32
+// spins, the signal contribution is the complex product
+//   C[r][l] = sum_s E_s(r) z_s^l
+// written as one real product of a 128-row matrix (rows 2r, 2r+1 = Re, Im of
+// run r) by the 128 samples: with k = (spin s, part p) the contraction index,
+//   A[2r][s,0] = Re E   A[2r][s,1] = -Im E   A[2r+1][s,0] = Im E   A[2r+1][s,1] = Re E
+//   B[l][s,0]  = Re z^l B[l][s,1]  = Im z^l
+// so D = A B^T holds Re C in row 2r and Im C in row 2r+1. Operands are FP16
+// pairs hi + lo (hi = fp16(v), lo = fp16(v - hi)): the three products
+// hi hi + hi lo + lo hi carry ~22 bits, accumulated in FP32 in tensor memory
+// across every spin block of the CTA. One tcgen05.mma (kind::f16, M = N =
+// 128, K = 16) takes 8 spins; a 32-spin block is 4 x 3 of them.
+//
+// Shared memory: two stages of [A hi | A lo | B hi | B lo] x 4 K slices of
+// 128 rows x 16 FP16 (4 KB), K-major without swizzle: 8-row x 16-byte core
+// matrices, K-adjacent ones 128 B apart, row-adjacent ones 256 B apart. The
+// 256 threads fill stage i & 1 for block i while the tensor core works on
+// block i - 1; one thread issues the MMAs and commits them to the stage's
+// mbarrier. z_s^l comes from z^(j + 32 g) and z^8 (direct, exact phase
+// reduction) and three complex products: l = 8 q + j.
+// ---------------------------------------------------------------------------
+constexpr int kMmaThreads = 256;
+constexpr int kMmaChunk = 32;                     // spins per block
+constexpr int kMmaTileBytes = 128 * 16 * 2;       // one K = 16 slice of a 128-row FP16 operand
+constexpr int kMmaStageBytes = 16 * kMmaTileBytes;  // A hi, A lo, B hi, B lo x 4 slices (64 KB)
+constexpr uint32_t kMmaTmemCols = 128;            // FP32 accumulator: 128 lanes x 128 columns
+constexpr size_t kMmaDynSmem = 2 * kMmaStageBytes + 256;  // + barriers, TMEM address (one CTA per SM)
+
+// byte offset of the 16-byte row word (row, K group kg of 8 elements) in a slice
+__device__ __forceinline__ uint32_t mma_word_off(int row, int kg) {
+    return static_cast<uint32_t>((row >> 3) * 256 + kg * 128 + (row & 7) * 16);
+}
+// shared-memory matrix descriptor: start address, leading (K) byte offset
+// 128, stride (row) byte offset 256, in 16-byte units; bits 46..48 = 0b001
+// (the tcgen05 descriptor version); no swizzle
+__device__ __forceinline__ uint64_t mma_smem_desc(uint32_t addr) {
+    return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(128 >> 4) << 16) |
+           (static_cast<uint64_t>(256 >> 4) << 32) | (1ull << 46);
+}
+// instruction descriptor, kind::f16: D FP32, A and B FP16, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t kMmaIdesc = (1u << 4) | (static_cast<uint32_t>(128 >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(kMmaIdesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+// 16 FP32 columns of this warp's 32 TMEM lanes (lane quarter warp % 4)
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// v = hi + lo as FP16 pairs (a in the low half)
+__device__ __forceinline__ void split_half2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 f = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - f.x, b - f.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// A slices (E part) of one stage for spins [s0, s0 + 32) of a group: 4 tasks
+// a thread, each one 16-byte row word (4 spins of one row) in hi and lo; the
+// 32 lanes of a warp write 512 contiguous bytes of one slice.
+__device__ __forceinline__ void mma_fill_e(unsigned char* stage, const MmaArgs& A, const MmaGroup& G, int64_t s0,
+                                           int64_t c_end, int warp, int lane) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int wt = warp + 8 * i;
+        const int kap = wt >> 3;
+        const int row = 16 * (wt & 7) + 8 * (lane >> 4) + (lane & 7);
+        const int kg = (lane >> 3) & 1;
+        const int r = row >> 1;
+        const bool im_row = row & 1;
+        const int64_t sp = s0 + 8 * kap + 4 * kg;
+        float2 e[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if (r < G.n_runs) {
+            const MmaRun run = A.runs[G.run0 + r];
+            const float2* __restrict__ erow = A.e + static_cast<int64_t>(run.slot) * A.n_pad;
+            if (sp + 3 < c_end) {
+                const float4 a = *reinterpret_cast<const float4*>(erow + sp);
+                const float4 b = *reinterpret_cast<const float4*>(erow + sp + 2);
+                e[0] = make_float2(a.x, a.y);
+                e[1] = make_float2(a.z, a.w);
+                e[2] = make_float2(b.x, b.y);
+                e[3] = make_float2(b.z, b.w);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (sp + q < c_end) e[q] = erow[sp + q];
+            }
+        }
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float re = e[q].x * A.escale, im = e[q].y * A.escale;
+            split_half2(im_row ? im : re, im_row ? re : -im, hi[q], lo[q]);
+        }
+        const uint32_t off = static_cast<uint32_t>(kap * kMmaTileBytes) + mma_word_off(row, kg);
+        *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(stage + 4 * kMmaTileBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+}
+
+// B slices (rotator powers) of one stage: thread = (spin quad, j = l mod 8,
+// g = l div 32): 4 spins x samples l = 32 g + 8 q + j, q < 4.
+__device__ __forceinline__ void mma_fill_z(unsigned char* stage, const MmaArgs& A, const MmaGroup& G, int64_t s0,
+                                           int64_t c_end, int warp, int lane) {
+    const int kap = 2 * (warp & 1) + (lane >> 4);
+    const int kg = (lane >> 3) & 1, j = lane & 7, g = warp >> 1;
+    const int64_t sp = s0 + 8 * kap + 4 * kg;
+    const int64_t np = A.n_pad;
+    const float m0 = static_cast<float>(j + 32 * g);
+    float zr[4], zi[4], wr[4], wi[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        zr[q] = zi[q] = wr[q] = wi[q] = 0.f;
+        const int64_t s = sp + q;
+        if (s < c_end) {
+            const float xh = A.p32[P32_XH * np + s], yh = A.p32[P32_YH * np + s];
+            const float zh = A.p32[P32_ZH * np + s], fh = A.p32[P32_FH * np + s];
+            const float r2 = A.p32[P32_R2 * np + s];
+            // turns per sample, as the Bloch kernel's rotator
+            const float th1 = -fmaf(G.dk[0], xh, fmaf(G.dk[1], yh, fmaf(G.dk[2], zh, fh * G.dtau)));
+            const float rate = G.dtau * r2;
+            float sn, cs;
+            sincospi_f32(2.f * frac_product(m0, 0.f, th1, 0.f), &sn, &cs);
+            const float mag = exp2f(-m0 * rate);
+            zr[q] = mag * cs;
+            zi[q] = mag * sn;
+            sincospi_f32(2.f * frac_product(8.f, 0.f, th1, 0.f), &sn, &cs);
+            const float mag8 = exp2f(-8.f * rate);
+            wr[q] = mag8 * cs;
+            wi[q] = mag8 * sn;
+        }
+    }
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+        const int l = 32 * g + 8 * qq + j;
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) split_half2(zr[q], zi[q], hi[q], lo[q]);
+        const uint32_t off = static_cast<uint32_t>((8 + kap) * kMmaTileBytes) + mma_word_off(l, kg);
+        *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(stage + 4 * kMmaTileBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        if (qq < 3) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float nr = fmaf(zr[q], wr[q], -zi[q] * wi[q]);
+                zi[q] = fmaf(zr[q], wi[q], zi[q] * wr[q]);
+                zr[q] = nr;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kMmaThreads, 1) readout_mma_kernel(const __grid_constant__ MmaArgs A) {
+    extern __shared__ __align__(1024) unsigned char s_mma[];
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_mma + 2 * kMmaStageBytes);
+    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(s_mma + 2 * kMmaStageBytes + 64);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t c_begin = static_cast<int64_t>(blockIdx.x) * A.spins_per_cta;
+    const int64_t c_end = min(A.n, c_begin + A.spins_per_cta);
+    const int n_chunks = c_end > c_begin ? static_cast<int>((c_end - c_begin + kMmaChunk - 1) / kMmaChunk) : 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_taddr)),
+                     "r"(kMmaTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&s_bar[0]), 1);
+        mbar_init(smem_u32(&s_bar[1]), 1);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_taddr;
+    const uint32_t bar[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
+    float* __restrict__ out = reinterpret_cast<float*>(A.partial + static_cast<int64_t>(blockIdx.x) * A.n_adc);
+
+    bool ok = true;
+    uint32_t it = 0;  // blocks issued: block i uses stage i & 1, phase (i >> 1) & 1 of bar[i & 1]
+    for (int gi = 0; gi < A.n_groups && ok && n_chunks > 0; ++gi) {
+        const MmaGroup G = A.groups[gi];
+        for (int ch = 0; ch < n_chunks; ++ch, ++it) {
+            const int st = static_cast<int>(it & 1);
+            if (it >= 2) {
+                // the MMAs of block it - 2 (same stage) are done reading it
+                const bool w = mbar_wait_bounded(bar[st], ((it - 2) >> 1) & 1);
+                if (__syncthreads_or(!w)) {
+                    ok = false;
+                    break;
+                }
+            }
+            unsigned char* stage = s_mma + st * kMmaStageBytes;
+            const int64_t s0 = c_begin + static_cast<int64_t>(ch) * kMmaChunk;
+            mma_fill_e(stage, A, G, s0, c_end, warp, lane);
+            mma_fill_z(stage, A, G, s0, c_end, warp, lane);
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t base = smem_u32(stage);
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint64_t ah = mma_smem_desc(base + ks * kMmaTileBytes);
+                    const uint64_t al = mma_smem_desc(base + (4 + ks) * kMmaTileBytes);
+                    const uint64_t bh = mma_smem_desc(base + (8 + ks) * kMmaTileBytes);
+                    const uint64_t bl = mma_smem_desc(base + (12 + ks) * kMmaTileBytes);
+                    tc_mma_f16(tmem, ah, bh, (ch > 0 || ks > 0) ? 1u : 0u);
+                    tc_mma_f16(tmem, ah, bl, 1u);
+                    tc_mma_f16(tmem, al, bh, 1u);
+                }
+                tc_commit(bar[st]);
+            }
+        }
+        if (!ok) break;
+        // epilogue: wait for the group's last block, then TMEM -> this CTA's row
+        const uint32_t last = it - 1;
+        const bool w = mbar_wait_bounded(bar[last & 1], (last >> 1) & 1);
+        if (__syncthreads_or(!w)) {
+            ok = false;
+            break;
+        }
+        tc_fence_after();
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = 32 * quarter + lane, r = row >> 1, part = row & 1;
+        MmaRun run{0, 0, 0};
+        if (r < G.n_runs) run = A.runs[G.run0 + r];
+#pragma unroll
+        for (int cc = 0; cc < 64; cc += 16) {
+            const int col0 = 64 * half + cc;
+            uint32_t v[16];
+            tc_ld16(tmem + (static_cast<uint32_t>(32 * quarter) << 16) + static_cast<uint32_t>(col0), v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (col0 + q < run.len) out[2 * (run.k0 + col0 + q) + part] = __uint_as_float(v[q]) * A.einv;
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (!ok) {
+        if (tid == 0) atomicOr(A.status, 1);
+        // no MMA may still write tensor memory when it is released
+        if (it > 0) mbar_wait_bounded(bar[(it - 1) & 1], ((it - 1) >> 1) & 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMmaTmemCols)
+                     : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Phantom conversion (upload): the FP32 block from the FP64 rows, element by
 // element. hi = float(v), lo = float(v - hi), log2(e)/T in FP64 then rounded
 // (T = +inf gives 0).
@@ -1567,7 +1857,7 @@ __device__ __forceinline__ void split_f64(double v, float* hi, float* lo) {
 __global__ void __launch_bounds__(256) phantom_convert_kernel(double* __restrict__ p64, float* __restrict__ p32,
                                                               int64_t n, int64_t np, ConvertStatus* __restrict__ cs) {
     const double kLog2e = 1.44269504088896340736;
-    double ext[4] = {0.0, 0.0, 0.0, 0.0};
+    double ext[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < np;
          j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         if (j < n) {
@@ -1592,6 +1882,7 @@ __global__ void __launch_bounds__(256) phantom_convert_kernel(double* __restrict
                 ext[1] = fmax(ext[1], fabs(y));
                 ext[2] = fmax(ext[2], fabs(z));
                 ext[3] = fmax(ext[3], fabs(dw) / (2.0 * 3.14159265358979323846));
+                ext[4] = fmax(ext[4], pd);
             }
         } else {
             for (int r = 0; r < P32_N; ++r) p32[r * np + j] = 0.f;
@@ -1601,7 +1892,7 @@ __global__ void __launch_bounds__(256) phantom_convert_kernel(double* __restrict
     // extents: warp maxima, then one atomic per warp on the bit patterns
     // (non-negative doubles order like their bits as unsigned integers)
 #pragma unroll
-    for (int d = 0; d < 4; ++d) {
+    for (int d = 0; d < 5; ++d) {
         double v = ext[d];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
@@ -1637,9 +1928,11 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const __grid_const
     const int64_t chunks = (R.n_adc + 31) / 32;
     const int64_t g = blockIdx.x / chunks;
     const int64_t k = (blockIdx.x % chunks) * 32 + threadIdx.x;
-    const int c_lo = R.group_cta ? R.group_cta[g] : 0;
-    const int c_hi = R.group_cta ? R.group_cta[g + 1] : R.grid;
-    const P* __restrict__ part = static_cast<const P*>(R.partial);
+    // samples of the matrix-form readout sum its rows instead (one group)
+    const bool mm = R.from_mma != nullptr && k < R.n_adc && R.from_mma[k] != 0;
+    const int c_lo = mm ? 0 : (R.group_cta ? R.group_cta[g] : 0);
+    const int c_hi = mm ? R.grid_mma : (R.group_cta ? R.group_cta[g + 1] : R.grid);
+    const P* __restrict__ part = static_cast<const P*>(mm ? R.partial_mma : R.partial);
     double re = 0.0, im = 0.0;
     if (k < R.n_adc) {
         for (int c = c_lo + static_cast<int>(threadIdx.y); c < c_hi; c += 8) {
@@ -1852,6 +2145,16 @@ int launch_phantom_convert(double* p64, float* p32, int64_t n, int64_t n_pad, Co
 
 int launch_bounded_wait_check(int* status, unsigned long long limit_ns, void* stream) {
     bounded_wait_check_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(status, limit_ns);
+    return cudaGetLastError();
+}
+
+int launch_readout_mma(const MmaArgs& a, int grid, void* stream) {
+    const cudaError_t attr = cudaFuncSetAttribute(readout_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  static_cast<int>(kMmaDynSmem));
+    if (attr != cudaSuccess) return attr;
+    if (grid <= 0 || a.spins_per_cta % kMmaChunk != 0 || a.n_pad % 2 != 0) return cudaErrorInvalidValue;
+    readout_mma_kernel<<<static_cast<unsigned>(grid), kMmaThreads, kMmaDynSmem, static_cast<cudaStream_t>(stream)>>>(
+        a);
     return cudaGetLastError();
 }
 

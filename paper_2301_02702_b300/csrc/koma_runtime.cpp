@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -50,10 +51,13 @@ struct koma_ctx {
     cudaStream_t alloc_stream = nullptr;  // orders the pool's allocations and frees only
     koma_launch_info last{};
     int64_t live_objects = 0;
-    // optional kernel timing: events around the Bloch kernel and the reduction
+    // optional kernel timing: events before the Bloch kernel, after it, after
+    // the tensor-core readout (right after the Bloch kernel when there is
+    // none) and after the reduction
     bool timing = false;
     bool timing_recorded = false;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool mma_enabled = true;  // koma_set_mma
     // autotuner results by problem shape (see tune_key): launches of a shape
     // tuned once reuse the choice for other phantoms and sequences of that shape
     std::map<uint64_t, std::pair<int, int>> tune_cache;  // key -> (spins per thread, block)
@@ -76,6 +80,7 @@ struct koma_phantom {
     size_t table_bytes = 0;
     // max |x|, |y|, |z| (m) and |df| (Hz) over the spins
     double max_abs[4] = {0, 0, 0, 0};
+    double max_pd = 0;
     // work items of the grouped kernel, built for items_s spins per thread:
     // d_items [n_items + 1] first spin of each item, then (same allocation)
     // d_order [n_items] longest first, d_group_item [n_groups + 1]
@@ -106,6 +111,14 @@ struct koma_sequence {
     // over RF steps: max |B1| gammabar dt (turns), max |Gbar_d| gammabar dt
     // (turns/m) per axis, max dt (s); bound the per-step rotation |a|
     double rf_b1 = 0, rf_g[3] = {0, 0, 0}, rf_dt = 0;
+    // matrix-form readout tables, in the same device block after the
+    // records: groups, runs (n_mma_runs = rows of the E buffer) and the
+    // per-sample source map of the reduction
+    koma::MmaGroup* d_mma_groups = nullptr;
+    koma::MmaRun* d_mma_runs = nullptr;
+    uint8_t* d_from_mma = nullptr;
+    int32_t n_mma_groups = 0;
+    int64_t n_mma_runs = 0;
 };
 
 namespace {
@@ -509,6 +522,7 @@ koma_status phantom_upload_finish(koma_ctx* ctx, koma_phantom** out, const doubl
         std::memcpy(&v, &ctx->h_conv->max_bits[d], sizeof(v));
         ph->max_abs[d] = v;
     }
+    std::memcpy(&ph->max_pd, &ctx->h_conv->max_bits[4], sizeof(ph->max_pd));
     return KOMA_OK;
 }
 
@@ -872,6 +886,72 @@ koma_status build_records(int64_t n_steps, const double* dt, const double* gx, c
 
 }  // namespace
 
+// Matrix-form readout plan. ADC records of at least two samples are bucketed
+// by their rotator (dK, dtau as FP32 bit patterns); a bucket of at least
+// kMmaMinRuns runs and kMmaMinSamples samples is taken by the tensor-core
+// readout: its records get kMmaFlag, E-buffer rows (slots) are numbered in
+// record order (the order the Bloch kernel meets the flagged records), and
+// its runs form groups of up to kMmaRuns in record order.
+struct MmaPlan {
+    std::vector<koma::MmaGroup> groups;
+    std::vector<koma::MmaRun> runs;
+    std::vector<uint8_t> from;  // [n_adc]: 1 = sample taken by the matrix form
+};
+
+void plan_mma(std::vector<koma::Rec32>& r32, int64_t n_adc, MmaPlan& P) {
+    std::map<std::array<uint32_t, 4>, std::vector<size_t>> buckets;
+    for (size_t i = 0; i < r32.size(); ++i) {
+        const koma::Rec32& R = r32[i];
+        if (R.type != koma::REC_ADC || (R.count & koma::kCountMask) < 2) continue;
+        std::array<uint32_t, 4> key;
+        std::memcpy(key.data(), &R.a[8], sizeof(key));
+        buckets[key].push_back(i);
+    }
+    std::vector<char> taken(r32.size(), 0);
+    std::vector<const std::vector<size_t>*> chosen;
+    for (const auto& kv : buckets) {
+        int64_t samples = 0;
+        for (size_t i : kv.second) samples += r32[i].count & koma::kCountMask;
+        if (static_cast<int64_t>(kv.second.size()) >= koma::kMmaMinRuns && samples >= koma::kMmaMinSamples) {
+            chosen.push_back(&kv.second);
+            for (size_t i : kv.second) taken[i] = 1;
+        }
+    }
+    if (chosen.empty()) return;
+    std::vector<int32_t> slot(r32.size(), -1);
+    int32_t next = 0;
+    for (size_t i = 0; i < r32.size(); ++i)
+        if (taken[i]) {
+            slot[i] = next++;
+            r32[i].count |= koma::kMmaFlag;
+        }
+    P.from.assign(static_cast<size_t>(n_adc), 0);
+    for (const std::vector<size_t>* v : chosen) {
+        for (size_t g0 = 0; g0 < v->size(); g0 += koma::kMmaRuns) {
+            const size_t g1 = std::min(v->size(), g0 + static_cast<size_t>(koma::kMmaRuns));
+            koma::MmaGroup G{};
+            const koma::Rec32& H = r32[(*v)[g0]];
+            G.dk[0] = H.a[8];
+            G.dk[1] = H.a[9];
+            G.dk[2] = H.a[10];
+            G.dtau = H.a[11];
+            G.run0 = static_cast<int32_t>(P.runs.size());
+            G.n_runs = static_cast<int32_t>(g1 - g0);
+            for (size_t q = g0; q < g1; ++q) {
+                const koma::Rec32& R = r32[(*v)[q]];
+                koma::MmaRun run{};
+                run.k0 = R.k0;
+                run.len = R.count & koma::kCountMask;
+                run.slot = slot[(*v)[q]];
+                G.max_len = std::max(G.max_len, run.len);
+                P.runs.push_back(run);
+                std::fill(P.from.begin() + run.k0, P.from.begin() + run.k0 + run.len, 1);
+            }
+            P.groups.push_back(G);
+        }
+    }
+}
+
 extern "C" koma_status koma_sequence_plan(int64_t n_steps, const double* dt, const double* gx, const double* gy,
                                           const double* gz, const double* b1_re, const double* b1_im,
                                           const uint8_t* adc, koma_sequence_info* info, double* rec_out,
@@ -881,6 +961,10 @@ extern "C" koma_status koma_sequence_plan(int64_t n_steps, const double* dt, con
     std::string err;
     koma_status st = build_records(n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, rb, *info, err);
     if (st != KOMA_OK) return st;
+    MmaPlan mp;
+    plan_mma(rb.r32, info->n_adc, mp);
+    info->n_mma_groups = static_cast<int64_t>(mp.groups.size());
+    info->n_mma_runs = static_cast<int64_t>(mp.runs.size());
     if (rec_out) {
         if (rec_capacity < info->n_records) return KOMA_E_INVALID;
         for (int64_t r = 0; r < info->n_records; ++r) {
@@ -919,28 +1003,46 @@ extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, cons
         for (int d = 0; d < 3; ++d) seq->rf_g[d] = std::max(seq->rf_g[d], std::fabs(q.a[d]));
         seq->rf_dt = std::max(seq->rf_dt, q.a[5]);
     }
+    MmaPlan mp;
+    plan_mma(rb.r32, info.n_adc, mp);
+    seq->info.n_mma_groups = static_cast<int64_t>(mp.groups.size());
+    seq->info.n_mma_runs = static_cast<int64_t>(mp.runs.size());
     DeviceGuard g(ctx->device);
+    auto up16 = [](size_t b) { return (b + 15) / 16 * 16; };
     const size_t b32 = rb.r32.size() * sizeof(koma::Rec32), b64 = rb.r64.size() * sizeof(koma::Rec64),
-                 bm = rb.rm.size() * sizeof(koma::RecM);
-    // one device block [Rec32 | Rec64 | RecM] (each part 16-byte aligned:
-    // 64- and 128-byte records) filled by one copy
-    koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r32), b32 + b64 + bm, "sequence_upload");
+                 bm = rb.rm.size() * sizeof(koma::RecM), bg = mp.groups.size() * sizeof(koma::MmaGroup),
+                 br = mp.runs.size() * sizeof(koma::MmaRun), bf = up16(mp.from.size());
+    const size_t total = b32 + b64 + bm + bg + br + bf;
+    // one device block [Rec32 | Rec64 | RecM | MmaGroup | MmaRun | sample map]
+    // (each part 16-byte aligned) filled by one copy
+    koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r32), total, "sequence_upload");
     if (st == KOMA_OK && b32) {
-        seq->r64 = reinterpret_cast<koma::Rec64*>(reinterpret_cast<char*>(seq->r32) + b32);
-        seq->rm = reinterpret_cast<koma::RecM*>(reinterpret_cast<char*>(seq->r32) + b32 + b64);
-        std::vector<char> host(b32 + b64 + bm);
+        char* base = reinterpret_cast<char*>(seq->r32);
+        seq->r64 = reinterpret_cast<koma::Rec64*>(base + b32);
+        seq->rm = reinterpret_cast<koma::RecM*>(base + b32 + b64);
+        if (!mp.groups.empty()) {
+            seq->d_mma_groups = reinterpret_cast<koma::MmaGroup*>(base + b32 + b64 + bm);
+            seq->d_mma_runs = reinterpret_cast<koma::MmaRun*>(base + b32 + b64 + bm + bg);
+            seq->d_from_mma = reinterpret_cast<uint8_t*>(base + b32 + b64 + bm + bg + br);
+            seq->n_mma_groups = static_cast<int32_t>(mp.groups.size());
+            seq->n_mma_runs = static_cast<int64_t>(mp.runs.size());
+        }
+        std::vector<char> host(total, 0);
         std::memcpy(host.data(), rb.r32.data(), b32);
         std::memcpy(host.data() + b32, rb.r64.data(), b64);
         std::memcpy(host.data() + b32 + b64, rb.rm.data(), bm);
+        if (bg) std::memcpy(host.data() + b32 + b64 + bm, mp.groups.data(), bg);
+        if (br) std::memcpy(host.data() + b32 + b64 + bm + bg, mp.runs.data(), br);
+        if (!mp.from.empty()) std::memcpy(host.data() + b32 + b64 + bm + bg + br, mp.from.data(), mp.from.size());
         cudaError_t e = cudaMemcpy(seq->r32, host.data(), host.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) st = cuda_fail(ctx, e, "sequence_upload: copy");
     }
     if (st != KOMA_OK) {
-        dev_free(ctx, seq->r32, b32 + b64 + bm);
+        dev_free(ctx, seq->r32, total);
         delete seq;
         return st;
     }
-    seq->bytes = b32 + b64 + bm;
+    seq->bytes = total;
     ctx->live_objects++;
     *out = seq;
     return KOMA_OK;
@@ -959,8 +1061,7 @@ extern "C" koma_status koma_sequence_free(koma_sequence* seq) {
     if (!seq) return KOMA_OK;
     koma_ctx* ctx = seq->ctx;
     DeviceGuard g(ctx->device);
-    dev_free(ctx, seq->r32, static_cast<size_t>(seq->info.n_records) *
-                                (sizeof(koma::Rec32) + sizeof(koma::Rec64) + sizeof(koma::RecM)));
+    dev_free(ctx, seq->r32, seq->bytes);
     ctx->live_objects--;
     delete seq;
     return KOMA_OK;
@@ -1085,7 +1186,10 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     if (ctx->timing) cudaEventRecord(ctx->ev[0], st);
     int e = koma::launch_items(A, grid, block, S, st);
     if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: grouped kernel launch");
-    if (ctx->timing) cudaEventRecord(ctx->ev[1], st);
+    if (ctx->timing) {
+        cudaEventRecord(ctx->ev[1], st);
+        cudaEventRecord(ctx->ev[2], st);
+    }
     koma::ReduceArgs R;
     R.partial = ctx->scratch;
     R.grid = static_cast<int>(ph->n_items);
@@ -1096,7 +1200,7 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     e = koma::launch_reduce(R, false, st);
     if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: reduction launch");
     if (ctx->timing) {
-        cudaEventRecord(ctx->ev[2], st);
+        cudaEventRecord(ctx->ev[3], st);
         ctx->timing_recorded = true;
     }
     ctx->last.kernels = 2;
@@ -1119,6 +1223,10 @@ uint64_t tune_key(const koma_phantom* ph, const koma_sequence* seq, bool items) 
     return family | lg(ph->n) << 2 | lg(ph->n_groups) << 10 | lg(seq->info.n_records) << 18 |
            lg(seq->info.n_adc) << 26 | lg(seq->info.n_rf) << 34;
 }
+
+// Largest E buffer (8 bytes per spin and matrix-form run) the tensor-core
+// readout takes; beyond it the Bloch kernel samples every run itself.
+constexpr size_t kMmaMaxEBytes = size_t{16} << 30;
 
 // ADC-run split for a launch whose spins fill few warps: CTAs sharing a
 // spin range each take every split-th ADC record (all of them step the RF
@@ -1282,7 +1390,28 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
 
     const size_t elem = fp64 ? 2 * sizeof(double) : 2 * sizeof(float);
     const int rows = L.grid / split;  // one partial row per spin range
-    const size_t need = static_cast<size_t>(rows) * static_cast<size_t>(n_adc) * elem;
+    size_t need = static_cast<size_t>(rows) * static_cast<size_t>(n_adc) * elem;
+    // tensor-core readout of the sequence's matrix-form groups: scratch
+    // [Bloch rows | readout rows (grid_mma x n_adc float2) | E (n_mma_runs x n_pad float2)]
+    const size_t e_bytes = static_cast<size_t>(seq->n_mma_runs) * static_cast<size_t>(ph->n_pad) * sizeof(float2);
+    const bool use_mma = !fp64 && !moving && ph->n_groups == 1 && seq->n_mma_groups > 0 && ctx->mma_enabled &&
+                         e_bytes <= kMmaMaxEBytes;
+    int grid_mma = 0;
+    int64_t spc_mma = 0;
+    size_t off_rows = 0, off_e = 0;
+    if (use_mma) {
+        // every CTA gets at least one block of 32 spins (each writes its whole row)
+        const int64_t blocks = (ph->n + 31) / 32;
+        int64_t g6 = std::min<int64_t>(ctx->sm_count, blocks);
+        const int64_t per_cta = (blocks + g6 - 1) / g6;
+        g6 = (blocks + per_cta - 1) / per_cta;
+        grid_mma = static_cast<int>(g6);
+        spc_mma = per_cta * 32;
+        auto up256 = [](size_t b) { return (b + 255) / 256 * 256; };
+        off_rows = up256(need);
+        off_e = up256(off_rows + static_cast<size_t>(grid_mma) * static_cast<size_t>(n_adc) * sizeof(float2));
+        need = off_e + e_bytes;
+    }
     {
         koma_status s = grow_scratch(ctx, need, st);
         if (s != KOMA_OK) return s;
@@ -1291,6 +1420,32 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     R.partial = ctx->scratch;
     R.grid = rows;
     R.sig = sig_dev;
+    koma::MmaArgs M;
+    if (use_mma) {
+        char* base = static_cast<char*>(ctx->scratch);
+        A.mma_e = reinterpret_cast<float2*>(base + off_e);
+        M.p32 = ph->p32;
+        M.n_pad = ph->n_pad;
+        M.n = ph->n;
+        M.e = A.mma_e;
+        M.groups = seq->d_mma_groups;
+        M.n_groups = seq->n_mma_groups;
+        M.runs = seq->d_mma_runs;
+        M.partial = reinterpret_cast<float2*>(base + off_rows);
+        M.n_adc = n_adc;
+        M.spins_per_cta = spc_mma;
+        // |Mxy| <= about max pd: scale E by a power of two below 1/max pd
+        // (exact) so its FP16 parts stay in range; undone on the result
+        int ex = 0;
+        if (ph->max_pd > 0) std::frexp(ph->max_pd, &ex);
+        ex = std::max(-100, std::min(100, ex));
+        M.escale = std::ldexp(1.0f, -ex);
+        M.einv = std::ldexp(1.0f, ex);
+        M.status = ctx->d_status;
+        R.partial_mma = M.partial;
+        R.grid_mma = grid_mma;
+        R.from_mma = seq->d_from_mma;
+    }
 
     ctx->timing_recorded = false;
     if (ctx->timing) cudaEventRecord(ctx->ev[0], st);
@@ -1301,14 +1456,20 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
         e = fp64 ? koma::launch_bloch_fp64(A, L, stream) : koma::launch_bloch_fp32(A, L, stream);
     if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: Bloch kernel launch");
     if (ctx->timing) cudaEventRecord(ctx->ev[1], st);
+    if (use_mma) {
+        e = koma::launch_readout_mma(M, grid_mma, stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: readout launch");
+    }
+    if (ctx->timing) cudaEventRecord(ctx->ev[2], st);
     e = koma::launch_reduce(R, fp64, stream);
     if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: reduction launch");
     if (ctx->timing) {
-        cudaEventRecord(ctx->ev[2], st);
+        cudaEventRecord(ctx->ev[3], st);
         ctx->timing_recorded = true;
     }
 
-    ctx->last.kernels = 2;
+    ctx->last.kernels = use_mma ? 3 : 2;
+    ctx->last.mma_grid = grid_mma;
     ctx->last.grid = L.grid;
     ctx->last.block = L.block;
     ctx->last.spins_per_thread = L.spins_per_thread;
@@ -1499,10 +1660,28 @@ extern "C" koma_status koma_get_timing(koma_ctx* ctx, float* bloch_ms, float* re
     if (!ctx || !bloch_ms || !reduce_ms) return KOMA_E_INVALID;
     if (!ctx->timing_recorded) return fail(ctx, KOMA_E_INVALID, "get_timing: no timed simulate call");
     DeviceGuard g(ctx->device);
-    cudaError_t e = cudaEventSynchronize(ctx->ev[2]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(bloch_ms, ctx->ev[0], ctx->ev[1]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(reduce_ms, ctx->ev[1], ctx->ev[2]);
+    cudaError_t e = cudaEventSynchronize(ctx->ev[3]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(bloch_ms, ctx->ev[0], ctx->ev[2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(reduce_ms, ctx->ev[2], ctx->ev[3]);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "get_timing");
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_get_stage_timing(koma_ctx* ctx, float* bloch_ms, float* mma_ms, float* reduce_ms) {
+    if (!ctx || !bloch_ms || !mma_ms || !reduce_ms) return KOMA_E_INVALID;
+    if (!ctx->timing_recorded) return fail(ctx, KOMA_E_INVALID, "get_stage_timing: no timed simulate call");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaEventSynchronize(ctx->ev[3]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(bloch_ms, ctx->ev[0], ctx->ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(mma_ms, ctx->ev[1], ctx->ev[2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(reduce_ms, ctx->ev[2], ctx->ev[3]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "get_stage_timing");
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_set_mma(koma_ctx* ctx, int enable) {
+    if (!ctx) return KOMA_E_INVALID;
+    ctx->mma_enabled = enable != 0;
     return KOMA_OK;
 }
 

@@ -34,7 +34,8 @@ EXPORTS = (
     "koma_sequence_free", "koma_sequence_plan", "koma_simulate", "koma_sync", "koma_set_timing",
     "koma_get_timing", "koma_get_launch_info", "koma_simulate_host", "koma_simulate_static", "koma_tune",
     "koma_server_create", "koma_server_submit", "koma_server_wait", "koma_server_get_stats",
-    "koma_server_last_error", "koma_server_destroy", "koma_check_bounded_wait",
+    "koma_server_last_error", "koma_server_destroy", "koma_check_bounded_wait", "koma_get_stage_timing",
+    "koma_set_mma",
 )
 
 
@@ -48,7 +49,7 @@ class LaunchInfo(ctypes.Structure):
     _fields_ = [("kernels", ctypes.c_int32), ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("spins_per_thread", ctypes.c_int32), ("spins_per_cta", ctypes.c_int64),
                 ("n_records", ctypes.c_int64), ("partial_bytes", ctypes.c_int64),
-                ("bloch_stream", ctypes.c_void_p), ("split", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+                ("bloch_stream", ctypes.c_void_p), ("split", ctypes.c_int32), ("mma_grid", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -57,7 +58,8 @@ class LaunchInfo(ctypes.Structure):
 class SequenceInfo(ctypes.Structure):
     _fields_ = [("n_steps", ctypes.c_int64), ("n_rf", ctypes.c_int64), ("n_adc", ctypes.c_int64),
                 ("n_precess", ctypes.c_int64), ("n_records", ctypes.c_int64),
-                ("n_adc_runs", ctypes.c_int64), ("n_materialize", ctypes.c_int64)]
+                ("n_adc_runs", ctypes.c_int64), ("n_materialize", ctypes.c_int64),
+                ("n_mma_groups", ctypes.c_int64), ("n_mma_runs", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -154,6 +156,10 @@ def load(path: Optional[str] = None):
         lib.koma_set_timing.argtypes = [_vp, ctypes.c_int]
         lib.koma_get_timing.restype = st
         lib.koma_get_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+        lib.koma_get_stage_timing.restype = st
+        lib.koma_get_stage_timing.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_float)] * 3
+        lib.koma_set_mma.restype = st
+        lib.koma_set_mma.argtypes = [_vp, ctypes.c_int]
         lib.koma_get_launch_info.restype = st
         lib.koma_get_launch_info.argtypes = [_vp, ctypes.POINTER(LaunchInfo)]
         lib.koma_server_create.restype = st
@@ -370,6 +376,19 @@ def koma_get_timing(ctx):
     a, b = ctypes.c_float(), ctypes.c_float()
     _check(ctx, load().koma_get_timing(ctx, ctypes.byref(a), ctypes.byref(b)), "koma_get_timing")
     return a.value, b.value
+
+
+def koma_get_stage_timing(ctx):
+    """(bloch_ms, mma_ms, reduce_ms) of the last timed koma_simulate; mma_ms
+    is the tensor-core readout (0 when it did not run)."""
+    a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+    _check(ctx, load().koma_get_stage_timing(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "koma_get_stage_timing")
+    return a.value, b.value, c.value
+
+
+def koma_set_mma(ctx, enable: bool = True):
+    _check(ctx, load().koma_set_mma(ctx, int(bool(enable))), "koma_set_mma")
 
 
 def koma_get_launch_info(ctx) -> dict:
