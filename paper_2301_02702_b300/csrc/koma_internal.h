@@ -185,6 +185,7 @@ struct BlochArgs {
     // of this [n_slots][n_pad] buffer (slot = the record's rank among the
     // flagged records) and are not sampled here
     float2* mma_e = nullptr;
+    float mma_escale = 1.f;         // E is stored times this power of two (FP16 range)
 };
 
 // Tensor-core readout (K6): CTA c takes spins [c spins_per_cta, +spins_per_cta)
@@ -194,14 +195,14 @@ struct MmaArgs {
     const float* p32 = nullptr;
     int64_t n_pad = 0;
     int64_t n = 0;
-    const float2* e = nullptr;       // [n_slots][n_pad]
+    const float2* e = nullptr;       // [n_slots][n_pad], scaled by 1 / einv
     const MmaGroup* groups = nullptr;
     int32_t n_groups = 0;
     const MmaRun* runs = nullptr;
     float2* partial = nullptr;
     int64_t n_adc = 0;
     int64_t spins_per_cta = 0;       // multiple of 32
-    float escale = 1.f, einv = 1.f;  // power-of-two scale keeping E in FP16 range
+    float einv = 1.f;                // 1 / the power-of-two scale E was stored with
     int* status = nullptr;
 };
 

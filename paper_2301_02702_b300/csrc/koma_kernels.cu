@@ -143,6 +143,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
+// Two adjacent mbarriers in shared memory, addressed by index without a
+// local-memory array.
+struct BarPair {
+    uint32_t b0;
+    __device__ __forceinline__ uint32_t operator[](int i) const { return b0 + 8u * static_cast<uint32_t>(i); }
+};
+
 // Wait for phase `parity` of `bar`, giving up after `limit_ns` (default kWaitNs).
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
                                                   unsigned long long limit_ns = kWaitNs) {
@@ -645,7 +652,8 @@ struct Spins {
 // Tile pipeline of the record stream: 64-record tiles brought into shared
 // memory by TMA bulk copies, double buffered; tile g of the CTA's lifetime
 // sits in buffer g & 1 and completes phase (g >> 1) & 1 of its mbarrier.
-__device__ __forceinline__ void issue_tile(Rec32 (*s_rec)[kTile], const uint32_t (&bar)[2], const Rec32* grec,
+template <class Bars>
+__device__ __forceinline__ void issue_tile(Rec32 (*s_rec)[kTile], const Bars& bar, const Rec32* grec,
                                            int64_t n_rec, int64_t t, uint64_t g) {
     const int64_t nr = min(static_cast<int64_t>(kTile), n_rec - t * kTile);
     tma_load_1d(smem_u32(&s_rec[g & 1][0]), grec + t * kTile, static_cast<uint32_t>(nr * sizeof(Rec32)),
@@ -788,7 +796,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
 #pragma unroll
                         for (int s = 0; s < S; ++s) {
                             const int64_t j = sp.index(s);
-                            if (j < sp.end) erow[j] = make_float2(er[s], ei[s]);
+                            if (j < sp.end) erow[j] = make_float2(er[s] * A.mma_escale, ei[s] * A.mma_escale);
                         }
                     } else {
                         sp.adc(R, L, er, ei, lane, [&](int i, float sr, float si) {
@@ -819,7 +827,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
 // one that stops before the end saves it there. Returns false if a tile never
 // arrived (status set, copies waited for).
 template <int S>
-__device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const uint32_t (&bar)[2], uint64_t& g0,
+__device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const BarPair bar, uint64_t& g0,
                                            const float* __restrict__ p32, int64_t np, const Rec32* grec,
                                            int64_t n_rec, int64_t rb, int64_t re, float* state, int64_t rf_hdr,
                                            const float (&ext)[4], int used, int64_t wb, int64_t we,
@@ -916,7 +924,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_kernel(const __grid_
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
-    const uint32_t bar[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
+    const BarPair bar{smem_u32(&s_bar[0])};
     if (tid == 0) {
         mbar_init(bar[0], 1);
         mbar_init(bar[1], 1);
@@ -961,7 +969,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_batches_kernel(const __gri
     __shared__ int64_t s_batch;
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
-    const uint32_t bar[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
+    const BarPair bar{smem_u32(&s_bar[0])};
     if (tid == 0) {
         mbar_init(bar[0], 1);
         mbar_init(bar[1], 1);
@@ -1372,7 +1380,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_motion_kernel(const __grid
         red_base = red_end;
     };
 
-    const uint32_t bar[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
+    const BarPair bar{smem_u32(&s_bar[0])};
     const RecM* __restrict__ grec = static_cast<const RecM*>(A.rec);
     const int64_t n_tiles = (A.n_rec + kTile - 1) / kTile;
     auto issue = [&](int64_t t) {
@@ -1585,20 +1593,30 @@ __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_cons
 // across every spin block of the CTA. One tcgen05.mma (kind::f16, M = N =
 // 128, K = 16) takes 8 spins; a 32-spin block is 4 x 3 of them.
 //
-// Shared memory: two stages of [A hi | A lo | B hi | B lo] x 4 K slices of
-// 128 rows x 16 FP16 (4 KB), K-major without swizzle: 8-row x 16-byte core
-// matrices, K-adjacent ones 128 B apart, row-adjacent ones 256 B apart. The
-// 256 threads fill stage i & 1 for block i while the tensor core works on
-// block i - 1; one thread issues the MMAs and commits them to the stage's
-// mbarrier. z_s^l comes from z^(j + 32 g) and z^8 (direct, exact phase
-// reduction) and three complex products: l = 8 q + j.
+// Pipeline per CTA (one per SM), block i of the flattened (group, block)
+// sequence:
+//   cp.async brings block i + 1's E rows and spin parameters into staging
+//   buffer (i + 1) & 1 (zero-filled past the last spin), while
+//   the 512 threads turn block i's staging into the FP16 operand slices of
+//   stage i & 1 (after the MMAs of block i - 2 have released it), and
+//   one thread issues block i's 12 MMAs and commits them to the stage's
+//   mbarrier; after a group's last block the accumulator goes from tensor
+//   memory to the CTA's partial row.
+// Operand slices: 128 rows x 16 FP16 (4 KB), K-major without swizzle: 8-row
+// x 16-byte core matrices, K-adjacent ones 128 B apart, row-adjacent ones
+// 256 B apart. z_s^l comes from z^(j + 32 g) and z^8 (direct, with an exact
+// phase reduction) and three complex products: l = 32 g + 8 q + j.
 // ---------------------------------------------------------------------------
-constexpr int kMmaThreads = 256;
-constexpr int kMmaChunk = 32;                     // spins per block
-constexpr int kMmaTileBytes = 128 * 16 * 2;       // one K = 16 slice of a 128-row FP16 operand
+constexpr int kMmaThreads = 512;
+constexpr int kMmaChunk = 32;                       // spins per block
+constexpr int kMmaTileBytes = 128 * 16 * 2;         // one K = 16 slice of a 128-row FP16 operand
 constexpr int kMmaStageBytes = 16 * kMmaTileBytes;  // A hi, A lo, B hi, B lo x 4 slices (64 KB)
-constexpr uint32_t kMmaTmemCols = 128;            // FP32 accumulator: 128 lanes x 128 columns
-constexpr size_t kMmaDynSmem = 2 * kMmaStageBytes + 256;  // + barriers, TMEM address (one CTA per SM)
+constexpr int kMmaERowBytes = kMmaChunk * 8 + 32;   // staged E row: 32 spins + 32 B (bank spread)
+constexpr int kMmaStageE = kMmaRuns * kMmaERowBytes;           // 18 KB
+constexpr int kMmaStageIn = kMmaStageE + 5 * kMmaChunk * 4;    // + xh, yh, zh, fh, r2 of the block
+constexpr int kMmaStageInPad = (kMmaStageIn + 127) / 128 * 128;
+constexpr uint32_t kMmaTmemCols = 128;              // FP32 accumulator: 128 lanes x 128 columns
+constexpr size_t kMmaDynSmem = 2 * kMmaStageBytes + 2 * kMmaStageInPad + 256;  // one CTA per SM
 
 // byte offset of the 16-byte row word (row, K group kg of 8 elements) in a slice
 __device__ __forceinline__ uint32_t mma_word_off(int row, int kg) {
@@ -1639,6 +1657,14 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// 16-byte global -> shared copy, bytes past `src_bytes` (0..16) zero-filled
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // v = hi + lo as FP16 pairs (a in the low half)
 __device__ __forceinline__ void split_half2(float a, float b, uint32_t& hi, uint32_t& lo) {
     const __half2 h = __floats2half2_rn(a, b);
@@ -1648,93 +1674,107 @@ __device__ __forceinline__ void split_half2(float a, float b, uint32_t& hi, uint
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// A slices (E part) of one stage for spins [s0, s0 + 32) of a group: 4 tasks
-// a thread, each one 16-byte row word (4 spins of one row) in hi and lo; the
-// 32 lanes of a warp write 512 contiguous bytes of one slice.
-__device__ __forceinline__ void mma_fill_e(unsigned char* stage, const MmaArgs& A, const MmaGroup& G, int64_t s0,
-                                           int64_t c_end, int warp, int lane) {
+// Staging of block [s0, s0 + 32) of group G: E rows (zero past c_end and for
+// rows >= n_runs) and the block's xh, yh, zh, fh, r2 (the FP32 block is
+// zero-padded to a multiple of 32 spins).
+__device__ __forceinline__ void mma_prefetch(unsigned char* in, const MmaArgs& A, const MmaGroup& G, int64_t s0,
+                                             int64_t c_end, int tid) {
+    const uint32_t base = smem_u32(in);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int wt = warp + 8 * i;
+    for (int i = 0; i < kMmaRuns * 16 / kMmaThreads; ++i) {
+        const int p = tid + kMmaThreads * i;
+        const int r = p >> 4, q = p & 15;
+        const int64_t sp = s0 + 2 * q;
+        const float2* src = A.e;
+        uint32_t bytes = 0;
+        if (r < G.n_runs) {
+            const int64_t left = c_end - sp;
+            bytes = left >= 2 ? 16u : (left == 1 ? 8u : 0u);
+            src = A.e + static_cast<int64_t>(__ldg(&A.runs[G.run0 + r].slot)) * A.n_pad + (bytes ? sp : 0);
+        }
+        cp_async16(base + static_cast<uint32_t>(r * kMmaERowBytes + q * 16), src, bytes);
+    }
+    if (tid < 40) {
+        const int a = tid >> 3, q = tid & 7;
+        const int row = a == 0 ? P32_XH : a == 1 ? P32_YH : a == 2 ? P32_ZH : a == 3 ? P32_FH : P32_R2;
+        cp_async16(base + static_cast<uint32_t>(kMmaStageE + a * kMmaChunk * 4 + q * 16),
+                   A.p32 + static_cast<int64_t>(row) * A.n_pad + s0 + 4 * q, 16u);
+    }
+}
+
+// A slices (E part) of a stage from the staging: 2 row words a thread (4
+// spins of one row, hi and lo); the 32 lanes of a warp write 512 contiguous
+// bytes of one slice.
+__device__ __forceinline__ void mma_fill_e(unsigned char* stage, const unsigned char* in, int warp, int lane) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int wt = warp + 16 * i;
         const int kap = wt >> 3;
         const int row = 16 * (wt & 7) + 8 * (lane >> 4) + (lane & 7);
         const int kg = (lane >> 3) & 1;
-        const int r = row >> 1;
         const bool im_row = row & 1;
-        const int64_t sp = s0 + 8 * kap + 4 * kg;
-        float2 e[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        if (r < G.n_runs) {
-            const MmaRun run = A.runs[G.run0 + r];
-            const float2* __restrict__ erow = A.e + static_cast<int64_t>(run.slot) * A.n_pad;
-            if (sp + 3 < c_end) {
-                const float4 a = *reinterpret_cast<const float4*>(erow + sp);
-                const float4 b = *reinterpret_cast<const float4*>(erow + sp + 2);
-                e[0] = make_float2(a.x, a.y);
-                e[1] = make_float2(a.z, a.w);
-                e[2] = make_float2(b.x, b.y);
-                e[3] = make_float2(b.z, b.w);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (sp + q < c_end) e[q] = erow[sp + q];
-            }
-        }
+        const float4* e4 = reinterpret_cast<const float4*>(in + (row >> 1) * kMmaERowBytes + (8 * kap + 4 * kg) * 8);
+        const float4 a = e4[0], b = e4[1];
+        const float re[4] = {a.x, a.z, b.x, b.z};
+        const float im[4] = {a.y, a.w, b.y, b.w};
         uint32_t hi[4], lo[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float re = e[q].x * A.escale, im = e[q].y * A.escale;
-            split_half2(im_row ? im : re, im_row ? re : -im, hi[q], lo[q]);
-        }
+        for (int q = 0; q < 4; ++q) split_half2(im_row ? im[q] : re[q], im_row ? re[q] : -im[q], hi[q], lo[q]);
         const uint32_t off = static_cast<uint32_t>(kap * kMmaTileBytes) + mma_word_off(row, kg);
         *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
         *reinterpret_cast<uint4*>(stage + 4 * kMmaTileBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
 }
 
-// B slices (rotator powers) of one stage: thread = (spin quad, j = l mod 8,
-// g = l div 32): 4 spins x samples l = 32 g + 8 q + j, q < 4.
-__device__ __forceinline__ void mma_fill_z(unsigned char* stage, const MmaArgs& A, const MmaGroup& G, int64_t s0,
-                                           int64_t c_end, int warp, int lane) {
-    const int kap = 2 * (warp & 1) + (lane >> 4);
-    const int kg = (lane >> 3) & 1, j = lane & 7, g = warp >> 1;
-    const int64_t sp = s0 + 8 * kap + 4 * kg;
-    const int64_t np = A.n_pad;
+// B slices (rotator powers) of a stage: thread = (spin pair, j = l mod 8,
+// g = l div 32), warp w: K slice w & 3, g = w >> 2; lane: pair half, j, K
+// group. 2 spins x samples l = 32 g + 8 q + j, q < 4; a warp's 8-byte
+// stores of one q fill 256 contiguous bytes. Spins past the last one have
+// zero parameters (z = 1) and zero E.
+__device__ __forceinline__ void mma_fill_z(unsigned char* stage, const unsigned char* in, const MmaGroup& G, int warp,
+                                           int lane) {
+    const int kap = warp & 3, g = warp >> 2;
+    const int half = lane & 1, j = (lane >> 1) & 7, kg = lane >> 4;
+    const int s2 = 8 * kap + 4 * kg + 2 * half;
+    const float* prm = reinterpret_cast<const float*>(in + kMmaStageE);
+    const float2 X = *reinterpret_cast<const float2*>(prm + 0 * kMmaChunk + s2);
+    const float2 Y = *reinterpret_cast<const float2*>(prm + 1 * kMmaChunk + s2);
+    const float2 Z = *reinterpret_cast<const float2*>(prm + 2 * kMmaChunk + s2);
+    const float2 F = *reinterpret_cast<const float2*>(prm + 3 * kMmaChunk + s2);
+    const float2 R2 = *reinterpret_cast<const float2*>(prm + 4 * kMmaChunk + s2);
+    const float xs[2] = {X.x, X.y}, ys[2] = {Y.x, Y.y}, zs[2] = {Z.x, Z.y};
+    const float fs[2] = {F.x, F.y}, rs[2] = {R2.x, R2.y};
     const float m0 = static_cast<float>(j + 32 * g);
-    float zr[4], zi[4], wr[4], wi[4];
+    float zr[2], zi[2], wr[2], wi[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        zr[q] = zi[q] = wr[q] = wi[q] = 0.f;
-        const int64_t s = sp + q;
-        if (s < c_end) {
-            const float xh = A.p32[P32_XH * np + s], yh = A.p32[P32_YH * np + s];
-            const float zh = A.p32[P32_ZH * np + s], fh = A.p32[P32_FH * np + s];
-            const float r2 = A.p32[P32_R2 * np + s];
-            // turns per sample, as the Bloch kernel's rotator
-            const float th1 = -fmaf(G.dk[0], xh, fmaf(G.dk[1], yh, fmaf(G.dk[2], zh, fh * G.dtau)));
-            const float rate = G.dtau * r2;
-            float sn, cs;
-            sincospi_f32(2.f * frac_product(m0, 0.f, th1, 0.f), &sn, &cs);
-            const float mag = exp2f(-m0 * rate);
-            zr[q] = mag * cs;
-            zi[q] = mag * sn;
-            sincospi_f32(2.f * frac_product(8.f, 0.f, th1, 0.f), &sn, &cs);
-            const float mag8 = exp2f(-8.f * rate);
-            wr[q] = mag8 * cs;
-            wi[q] = mag8 * sn;
-        }
+    for (int q = 0; q < 2; ++q) {
+        // turns per sample, as the Bloch kernel's rotator
+        const float th1 = -fmaf(G.dk[0], xs[q], fmaf(G.dk[1], ys[q], fmaf(G.dk[2], zs[q], fs[q] * G.dtau)));
+        const float rate = G.dtau * rs[q];
+        // one-shot phases (not accumulated beyond three products): the
+        // fractional turn exactly reduced, then the hardware sine
+        float sn, cs;
+        __sincosf(6.28318530717958647692f * frac_product(m0, 0.f, th1, 0.f), &sn, &cs);
+        const float mag = exp2f(-m0 * rate);
+        zr[q] = mag * cs;
+        zi[q] = mag * sn;
+        __sincosf(6.28318530717958647692f * frac_product(8.f, 0.f, th1, 0.f), &sn, &cs);
+        const float mag8 = exp2f(-8.f * rate);
+        wr[q] = mag8 * cs;
+        wi[q] = mag8 * sn;
     }
 #pragma unroll
     for (int qq = 0; qq < 4; ++qq) {
         const int l = 32 * g + 8 * qq + j;
-        uint32_t hi[4], lo[4];
+        uint32_t hi[2], lo[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) split_half2(zr[q], zi[q], hi[q], lo[q]);
-        const uint32_t off = static_cast<uint32_t>((8 + kap) * kMmaTileBytes) + mma_word_off(l, kg);
-        *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(stage + 4 * kMmaTileBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        for (int q = 0; q < 2; ++q) split_half2(zr[q], zi[q], hi[q], lo[q]);
+        const uint32_t off = static_cast<uint32_t>((8 + kap) * kMmaTileBytes) + mma_word_off(l, kg) + 8u * half;
+        *reinterpret_cast<uint2*>(stage + off) = make_uint2(hi[0], hi[1]);
+        *reinterpret_cast<uint2*>(stage + 4 * kMmaTileBytes + off) = make_uint2(lo[0], lo[1]);
         if (qq < 3) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 2; ++q) {
                 const float nr = fmaf(zr[q], wr[q], -zi[q] * wi[q]);
                 zi[q] = fmaf(zr[q], wi[q], zi[q] * wr[q]);
                 zr[q] = nr;
@@ -1745,12 +1785,14 @@ __device__ __forceinline__ void mma_fill_z(unsigned char* stage, const MmaArgs& 
 
 __global__ void __launch_bounds__(kMmaThreads, 1) readout_mma_kernel(const __grid_constant__ MmaArgs A) {
     extern __shared__ __align__(1024) unsigned char s_mma[];
-    uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_mma + 2 * kMmaStageBytes);
-    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(s_mma + 2 * kMmaStageBytes + 64);
+    unsigned char* s_in = s_mma + 2 * kMmaStageBytes;  // two staging buffers
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_in + 2 * kMmaStageInPad);
+    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(s_in + 2 * kMmaStageInPad + 64);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t c_begin = static_cast<int64_t>(blockIdx.x) * A.spins_per_cta;
     const int64_t c_end = min(A.n, c_begin + A.spins_per_cta);
     const int n_chunks = c_end > c_begin ? static_cast<int>((c_end - c_begin + kMmaChunk - 1) / kMmaChunk) : 0;
+    const int n_it = n_chunks * A.n_groups;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_taddr)),
@@ -1763,65 +1805,71 @@ __global__ void __launch_bounds__(kMmaThreads, 1) readout_mma_kernel(const __gri
         mbar_init(smem_u32(&s_bar[1]), 1);
         fence_mbar_init();
     }
+    if (n_it > 0) mma_prefetch(s_in, A, A.groups[0], c_begin, c_end, tid);
+    cp_async_commit();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *s_taddr;
-    const uint32_t bar[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
+    const BarPair bar{smem_u32(&s_bar[0])};
     float* __restrict__ out = reinterpret_cast<float*>(A.partial + static_cast<int64_t>(blockIdx.x) * A.n_adc);
 
     bool ok = true;
-    uint32_t it = 0;  // blocks issued: block i uses stage i & 1, phase (i >> 1) & 1 of bar[i & 1]
-    for (int gi = 0; gi < A.n_groups && ok && n_chunks > 0; ++gi) {
+    int it = 0;  // block it: stage and staging it & 1, phase (it >> 1) & 1 of bar[it & 1]
+    for (; it < n_it; ++it) {
+        const int gi = it / n_chunks, ch = it - gi * n_chunks;
         const MmaGroup G = A.groups[gi];
-        for (int ch = 0; ch < n_chunks; ++ch, ++it) {
-            const int st = static_cast<int>(it & 1);
-            if (it >= 2) {
-                // the MMAs of block it - 2 (same stage) are done reading it
-                const bool w = mbar_wait_bounded(bar[st], ((it - 2) >> 1) & 1);
-                if (__syncthreads_or(!w)) {
-                    ok = false;
-                    break;
-                }
-            }
-            unsigned char* stage = s_mma + st * kMmaStageBytes;
-            const int64_t s0 = c_begin + static_cast<int64_t>(ch) * kMmaChunk;
-            mma_fill_e(stage, A, G, s0, c_end, warp, lane);
-            mma_fill_z(stage, A, G, s0, c_end, warp, lane);
-            fence_proxy_async_smem();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t base = smem_u32(stage);
-#pragma unroll
-                for (int ks = 0; ks < 4; ++ks) {
-                    const uint64_t ah = mma_smem_desc(base + ks * kMmaTileBytes);
-                    const uint64_t al = mma_smem_desc(base + (4 + ks) * kMmaTileBytes);
-                    const uint64_t bh = mma_smem_desc(base + (8 + ks) * kMmaTileBytes);
-                    const uint64_t bl = mma_smem_desc(base + (12 + ks) * kMmaTileBytes);
-                    tc_mma_f16(tmem, ah, bh, (ch > 0 || ks > 0) ? 1u : 0u);
-                    tc_mma_f16(tmem, ah, bl, 1u);
-                    tc_mma_f16(tmem, al, bh, 1u);
-                }
-                tc_commit(bar[st]);
-            }
+        const int st = it & 1;
+        if (it + 1 < n_it) {
+            const int gn = (it + 1) / n_chunks, cn = it + 1 - gn * n_chunks;
+            mma_prefetch(s_in + (st ^ 1) * kMmaStageInPad, A, A.groups[gn],
+                         c_begin + static_cast<int64_t>(cn) * kMmaChunk, c_end, tid);
         }
-        if (!ok) break;
-        // epilogue: wait for the group's last block, then TMEM -> this CTA's row
-        const uint32_t last = it - 1;
-        const bool w = mbar_wait_bounded(bar[last & 1], (last >> 1) & 1);
+        cp_async_commit();
+        cp_async_wait<1>();  // this block's staging has landed (this thread's copies)
+        bool w = true;
+        if (it >= 2) w = mbar_wait_bounded(bar[st], ((it - 2) >> 1) & 1);  // MMAs of block it - 2 done
         if (__syncthreads_or(!w)) {
             ok = false;
             break;
         }
+        unsigned char* stage = s_mma + st * kMmaStageBytes;
+        const unsigned char* in = s_in + st * kMmaStageInPad;
+        mma_fill_e(stage, in, warp, lane);
+        mma_fill_z(stage, in, G, warp, lane);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t base = smem_u32(stage);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t ah = mma_smem_desc(base + ks * kMmaTileBytes);
+                const uint64_t al = mma_smem_desc(base + (4 + ks) * kMmaTileBytes);
+                const uint64_t bh = mma_smem_desc(base + (8 + ks) * kMmaTileBytes);
+                const uint64_t bl = mma_smem_desc(base + (12 + ks) * kMmaTileBytes);
+                tc_mma_f16(tmem, ah, bh, (ch > 0 || ks > 0) ? 1u : 0u);
+                tc_mma_f16(tmem, ah, bl, 1u);
+                tc_mma_f16(tmem, al, bh, 1u);
+            }
+            tc_commit(bar[st]);
+        }
+        if (ch + 1 < n_chunks) continue;
+        // epilogue of group gi: wait for its last block, then TMEM -> this CTA's row
+        w = mbar_wait_bounded(bar[st], (it >> 1) & 1);
+        if (__syncthreads_or(!w)) {
+            ok = false;
+            ++it;  // block it was issued
+            break;
+        }
         tc_fence_after();
-        const int quarter = warp & 3, half = warp >> 2;
+        const int quarter = warp & 3, cgrp = warp >> 2;
         const int row = 32 * quarter + lane, r = row >> 1, part = row & 1;
         MmaRun run{0, 0, 0};
         if (r < G.n_runs) run = A.runs[G.run0 + r];
 #pragma unroll
-        for (int cc = 0; cc < 64; cc += 16) {
-            const int col0 = 64 * half + cc;
+        for (int cc = 0; cc < 32; cc += 16) {
+            const int col0 = 32 * cgrp + cc;
             uint32_t v[16];
             tc_ld16(tmem + (static_cast<uint32_t>(32 * quarter) << 16) + static_cast<uint32_t>(col0), v);
 #pragma unroll
@@ -1831,6 +1879,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) readout_mma_kernel(const __gri
         tc_fence_before();
         __syncthreads();
     }
+    cp_async_wait<0>();
     if (!ok) {
         if (tid == 0) atomicOr(A.status, 1);
         // no MMA may still write tensor memory when it is released

@@ -1439,7 +1439,7 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
         int ex = 0;
         if (ph->max_pd > 0) std::frexp(ph->max_pd, &ex);
         ex = std::max(-100, std::min(100, ex));
-        M.escale = std::ldexp(1.0f, -ex);
+        A.mma_escale = std::ldexp(1.0f, -ex);
         M.einv = std::ldexp(1.0f, ex);
         M.status = ctx->d_status;
         R.partial_mma = M.partial;
