@@ -58,6 +58,11 @@ MODEL_RF = (50, 3)
 MODEL_ADC = (25, 3)
 PROBE_FFMA_PER_SM_CLK = 117
 PROBE_MUFU_PER_SM_CLK = 21
+# tensor-core readout: per 32-spin block and matrix-form group, 4 K slices x
+# 3 FP16 products (hi hi, hi lo, lo hi) of one M = N = 128, K = 16 MMA
+MMA_FLOPS_PER_BLOCK_GROUP = 12 * 2 * 128 * 128 * 16
+# dense FP16/BF16 tensor peak when MEASURED_PEAKS.json is absent (fallback)
+PEAK_TENSOR_FALLBACK = 1800.0
 
 WORKLOAD_TEXT = {
     "gre32": "gre32: 32x32 grid phantom (1,024 spins), spoiled GRE 32 TRs x 10 ms on a 10 us grid "
@@ -196,6 +201,17 @@ def measured_traffic(workload: str):
     if not e or e.get("kernel_hash") != kernel_source_hash():
         return None
     return e.get("dram_bytes_per_launch")
+
+
+def tensor_peak():
+    """(TFLOP/s, source) of the dense 16-bit tensor peak: the measured cuBLAS
+    BF16 burst rate of this pool's parts (FP16 has the same nominal rate)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["bf16_tflops"])
+        return v, "measured dense BF16 GEMM burst (MEASURED_PEAKS.json; FP16 same nominal rate)"
+    except (OSError, KeyError, ValueError, TypeError):
+        return PEAK_TENSOR_FALLBACK, "fallback 1.8 PFLOP/s dense BF16 (no measured peaks file)"
 
 
 def algorithmic_flops(info: dict, n_spins: int, moving: bool = False) -> float:
@@ -508,7 +524,7 @@ def run_ours(args, rank, world, local):
             sim.simulate(hp, hs, "fp32", out=out, stream=stream)
             ev[i][1].record(stream)
         if args.kernel_timing:
-            k1_ms.append(koma.koma_get_timing(sim.ctx)[0])
+            k1_ms.append(koma.koma_get_stage_timing(sim.ctx))
     torch.cuda.synchronize(local)
     barrier(world)
     clk = clocks.stop()
@@ -635,8 +651,17 @@ def run_ours(args, rank, world, local):
                          f"{dt:.1f} s"}
 
     if rank == 0:
-        flops = algorithmic_flops(info, ph.n, moving)
-        k1 = (sum(k1_ms) / len(k1_ms)) if k1_ms else None
+        # stages of one simulate: Bloch kernel, tensor-core readout (0 when the
+        # call has none), reduction
+        k1 = k6 = None
+        if k1_ms:
+            k1 = sum(t[0] for t in k1_ms) / len(k1_ms)
+            k6 = sum(t[1] for t in k1_ms) / len(k1_ms)
+        mma = launch.get("mma_grid", 0) > 0
+        mma_samples = info.get("n_mma_samples", 0) if mma else 0
+        flops_all = algorithmic_flops(info, ph.n, moving)
+        # the Bloch kernel's share: every RF step and the samples it steps
+        flops = flops_all - float(ph.n) * mma_samples * FLOPS_ADC_SAMPLE
         achieved = flops / (k1 / 1e3) / 1e12 if k1 else None
         kname = "bloch_motion_kernel" if moving else ("bloch_items_kernel" if grouped else "bloch_fp32_kernel")
         roof = {"bound": "alu", "kernel": f"{kname}<{launch['spins_per_thread']}>",
@@ -645,7 +670,23 @@ def run_ours(args, rank, world, local):
                 "traffic": measured_traffic(args.workload),
                 "kernel_ms": k1, "algorithmic_flops_per_launch": flops,
                 "peak_source": "FP32 peak 148 SMs x 128 lanes x 2 x 2032 MHz (max SM clock)"}
+        roof_mma = None
+        if mma and k6:
+            peak_t, peak_src = tensor_peak()
+            blocks = (ph.n + 31) // 32
+            tflops = float(blocks) * info["n_mma_groups"] * MMA_FLOPS_PER_BLOCK_GROUP
+            direct = float(ph.n) * mma_samples * FLOPS_ADC_SAMPLE
+            roof_mma = {"bound": "tensor", "kernel": "readout_mma_kernel", "achieved": tflops / (k6 / 1e3) / 1e12,
+                        "peak": peak_t, "unit": "TFLOP/s", "frac": tflops / (k6 / 1e3) / 1e12 / peak_t,
+                        "traffic": measured_traffic(args.workload + ":readout"), "kernel_ms": k6,
+                        "tensor_flops_per_launch": tflops, "peak_source": peak_src,
+                        "samples": mma_samples,
+                        "direct_sum_flops_per_launch": direct,
+                        "direct_sum_tflops": direct / (k6 / 1e3) / 1e12}
+            if k6 > k1:  # the readout dominates the step: it is the line's roofline
+                roof, roof_mma = roof_mma, roof
         if k1:
+            k1_total = k1 + (k6 or 0.0)
             mhz = (clk or {}).get("sm_mhz") or 2032.0
             fp32_ops = ph.n * (info["n_rf"] * MODEL_RF[0] + info["n_adc"] * MODEL_ADC[0])
             mufu_ops = ph.n * (info["n_rf"] * MODEL_RF[1] + info["n_adc"] * MODEL_ADC[1])
@@ -653,7 +694,8 @@ def run_ours(args, rank, world, local):
             t_mufu = mufu_ops / (SM_COUNT * PROBE_MUFU_PER_SM_CLK * mhz * 1e6) * 1e3
             roof["step_model"] = {"fp32_ops": fp32_ops, "mufu_ops": mufu_ops, "t_fp32_ms": t_fp32,
                                   "t_mufu_ms": t_mufu, "t_min_ms": max(t_fp32, t_mufu),
-                                  "frac": max(t_fp32, t_mufu) / k1,
+                                  "kernels_ms": k1_total,
+                                  "frac": max(t_fp32, t_mufu) / k1_total,
                                   "model": "per spin: RF step 50 FP32 + 3 MUFU, ADC sample 25 FP32 + 3 MUFU, "
                                            "at the probed FFMA/MUFU issue rates and the sampled SM clock"}
         line = {
@@ -666,6 +708,7 @@ def run_ours(args, rank, world, local):
                        "parallelism": f"replicas x{world}",
                        "launch": {k: launch[k] for k in ("grid", "block", "spins_per_thread", "spins_per_cta")}},
             "roofline": roof,
+            "roofline_other": roof_mma,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launch["kernels"] * args.steps,

@@ -96,6 +96,7 @@ typedef struct {
                              rotator (same dK, dtau), summed as matrix
                              products on the tensor cores (FP32 path)      */
     int64_t n_mma_runs;   /* ADC runs in those groups                       */
+    int64_t n_mma_samples; /* ADC samples in those runs                     */
 } koma_sequence_info;
 
 /* gamma used by the library, rad/s/T. */

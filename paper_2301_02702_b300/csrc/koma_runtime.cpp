@@ -896,6 +896,7 @@ struct MmaPlan {
     std::vector<koma::MmaGroup> groups;
     std::vector<koma::MmaRun> runs;
     std::vector<uint8_t> from;  // [n_adc]: 1 = sample taken by the matrix form
+    int64_t n_samples = 0;
 };
 
 void plan_mma(std::vector<koma::Rec32>& r32, int64_t n_adc, MmaPlan& P) {
@@ -944,6 +945,7 @@ void plan_mma(std::vector<koma::Rec32>& r32, int64_t n_adc, MmaPlan& P) {
                 run.len = R.count & koma::kCountMask;
                 run.slot = slot[(*v)[q]];
                 G.max_len = std::max(G.max_len, run.len);
+                P.n_samples += run.len;
                 P.runs.push_back(run);
                 std::fill(P.from.begin() + run.k0, P.from.begin() + run.k0 + run.len, 1);
             }
@@ -965,6 +967,7 @@ extern "C" koma_status koma_sequence_plan(int64_t n_steps, const double* dt, con
     plan_mma(rb.r32, info->n_adc, mp);
     info->n_mma_groups = static_cast<int64_t>(mp.groups.size());
     info->n_mma_runs = static_cast<int64_t>(mp.runs.size());
+    info->n_mma_samples = mp.n_samples;
     if (rec_out) {
         if (rec_capacity < info->n_records) return KOMA_E_INVALID;
         for (int64_t r = 0; r < info->n_records; ++r) {
@@ -1007,6 +1010,7 @@ extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, cons
     plan_mma(rb.r32, info.n_adc, mp);
     seq->info.n_mma_groups = static_cast<int64_t>(mp.groups.size());
     seq->info.n_mma_runs = static_cast<int64_t>(mp.runs.size());
+    seq->info.n_mma_samples = mp.n_samples;
     DeviceGuard g(ctx->device);
     auto up16 = [](size_t b) { return (b + 15) / 16 * 16; };
     const size_t b32 = rb.r32.size() * sizeof(koma::Rec32), b64 = rb.r64.size() * sizeof(koma::Rec64),

@@ -59,7 +59,8 @@ class SequenceInfo(ctypes.Structure):
     _fields_ = [("n_steps", ctypes.c_int64), ("n_rf", ctypes.c_int64), ("n_adc", ctypes.c_int64),
                 ("n_precess", ctypes.c_int64), ("n_records", ctypes.c_int64),
                 ("n_adc_runs", ctypes.c_int64), ("n_materialize", ctypes.c_int64),
-                ("n_mma_groups", ctypes.c_int64), ("n_mma_runs", ctypes.c_int64)]
+                ("n_mma_groups", ctypes.c_int64), ("n_mma_runs", ctypes.c_int64),
+                ("n_mma_samples", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

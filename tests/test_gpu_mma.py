@@ -222,3 +222,27 @@ def test_random_sequences_unaffected(sim):
     got, li = run(sim, ph, seq)
     assert li["mma_grid"] == 0
     assert rel_err(got, ref) < TOL32
+
+
+def test_stage_timing_splits_the_bloch_time(sim):
+    """koma_get_stage_timing splits koma_get_timing's Bloch time into the
+    Bloch kernel and the readout; the readout is 0 when it does not run."""
+    seq = epi(n_read=128, n_lines=32, fov=0.23, rf_steps=100)
+    ph = head_like(3000, 71)
+    hp = sim.upload_phantom(ph)
+    hs = sim.upload_sequence(seq)
+    try:
+        koma.koma_set_timing(sim.ctx, True)
+        for mma in (True, False):
+            koma.koma_set_mma(sim.ctx, mma)
+            sim.simulate(hp, hs)
+            sim.sync()
+            b, m, r = koma.koma_get_stage_timing(sim.ctx)
+            tb, tr = koma.koma_get_timing(sim.ctx)
+            assert b > 0 and r > 0 and (m > 0.003 if mma else m < 0.003)
+            assert abs((b + m) - tb) <= 0.005 and abs(r - tr) <= 0.005
+    finally:
+        koma.koma_set_timing(sim.ctx, False)
+        koma.koma_set_mma(sim.ctx, True)
+        koma.koma_sequence_free(hs)
+        koma.koma_phantom_free(hp)
