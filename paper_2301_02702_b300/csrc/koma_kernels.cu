@@ -1593,15 +1593,19 @@ __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_cons
 // across every spin block of the CTA. One tcgen05.mma (kind::f16, M = N =
 // 128, K = 16) takes 8 spins; a 32-spin block is 4 x 3 of them.
 //
-// Pipeline per CTA (one per SM), block i of the flattened (group, block)
-// sequence:
-//   cp.async brings block i + 1's E rows and spin parameters into staging
-//   buffer (i + 1) & 1 (zero-filled past the last spin), while
-//   the 512 threads turn block i's staging into the FP16 operand slices of
-//   stage i & 1 (after the MMAs of block i - 2 have released it), and
-//   one thread issues block i's 12 MMAs and commits them to the stage's
-//   mbarrier; after a group's last block the accumulator goes from tensor
-//   memory to the CTA's partial row.
+// Pipeline per CTA (one per SM), warp-specialised, block i of the flattened
+// (group, block) sequence:
+//   16 producer warps: cp.async brings block i + 2's E rows and spin
+//   parameters into one of four staging buffers (zero-filled past the last
+//   spin); block i's staging becomes the FP16 operand slices of stage i & 1
+//   once the MMAs of block i - 2 have released it (mbarrier "empty", the
+//   tensor core's commit), then each producer arrives on "full";
+//   one MMA warp waits for "full", issues block i's 12 MMAs into accumulator
+//   buffer (group & 1) and commits them to "empty";
+//   after a group's last block the producers read the accumulator from
+//   tensor memory into the CTA's partial row and release the buffer.
+// Every wait is bounded; a wait that gives up stops both roles (a uniform
+// decision among producers via a reducing named barrier).
 // Operand slices: 128 rows x 16 FP16 (4 KB), K-major without swizzle: 8-row
 // x 16-byte core matrices, K-adjacent ones 128 B apart, row-adjacent ones
 // 256 B apart. z_s^l comes from z^(j + 32 g) and z^8 (direct, with an exact
@@ -1615,8 +1619,9 @@ constexpr int kMmaERowBytes = kMmaChunk * 8 + 32;   // staged E row: 32 spins + 
 constexpr int kMmaStageE = kMmaRuns * kMmaERowBytes;           // 18 KB
 constexpr int kMmaStageIn = kMmaStageE + 5 * kMmaChunk * 4;    // + xh, yh, zh, fh, r2 of the block
 constexpr int kMmaStageInPad = (kMmaStageIn + 127) / 128 * 128;
-constexpr uint32_t kMmaTmemCols = 128;              // FP32 accumulator: 128 lanes x 128 columns
-constexpr size_t kMmaDynSmem = 2 * kMmaStageBytes + 2 * kMmaStageInPad + 256;  // one CTA per SM
+constexpr int kMmaStaging = 4;                      // staging buffers (prefetch distance 2)
+constexpr uint32_t kMmaTmemCols = 256;              // two FP32 accumulators of 128 lanes x 128 columns
+constexpr size_t kMmaDynSmem = 2 * kMmaStageBytes + kMmaStaging * kMmaStageInPad + 256;  // one CTA per SM
 
 // byte offset of the 16-byte row word (row, K group kg of 8 elements) in a slice
 __device__ __forceinline__ uint32_t mma_word_off(int row, int kg) {
@@ -1672,34 +1677,6 @@ __device__ __forceinline__ void split_half2(float a, float b, uint32_t& hi, uint
     const __half2 l = __floats2half2_rn(a - f.x, b - f.y);
     hi = *reinterpret_cast<const uint32_t*>(&h);
     lo = *reinterpret_cast<const uint32_t*>(&l);
-}
-
-// Staging of block [s0, s0 + 32) of group G: E rows (zero past c_end and for
-// rows >= n_runs) and the block's xh, yh, zh, fh, r2 (the FP32 block is
-// zero-padded to a multiple of 32 spins).
-__device__ __forceinline__ void mma_prefetch(unsigned char* in, const MmaArgs& A, const MmaGroup& G, int64_t s0,
-                                             int64_t c_end, int tid) {
-    const uint32_t base = smem_u32(in);
-#pragma unroll
-    for (int i = 0; i < kMmaRuns * 16 / kMmaThreads; ++i) {
-        const int p = tid + kMmaThreads * i;
-        const int r = p >> 4, q = p & 15;
-        const int64_t sp = s0 + 2 * q;
-        const float2* src = A.e;
-        uint32_t bytes = 0;
-        if (r < G.n_runs) {
-            const int64_t left = c_end - sp;
-            bytes = left >= 2 ? 16u : (left == 1 ? 8u : 0u);
-            src = A.e + static_cast<int64_t>(__ldg(&A.runs[G.run0 + r].slot)) * A.n_pad + (bytes ? sp : 0);
-        }
-        cp_async16(base + static_cast<uint32_t>(r * kMmaERowBytes + q * 16), src, bytes);
-    }
-    if (tid < 40) {
-        const int a = tid >> 3, q = tid & 7;
-        const int row = a == 0 ? P32_XH : a == 1 ? P32_YH : a == 2 ? P32_ZH : a == 3 ? P32_FH : P32_R2;
-        cp_async16(base + static_cast<uint32_t>(kMmaStageE + a * kMmaChunk * 4 + q * 16),
-                   A.p32 + static_cast<int64_t>(row) * A.n_pad + s0 + 4 * q, 16u);
-    }
 }
 
 // A slices (E part) of a stage from the staging: 2 row words a thread (4
@@ -1783,111 +1760,211 @@ __device__ __forceinline__ void mma_fill_z(unsigned char* stage, const unsigned 
     }
 }
 
-__global__ void __launch_bounds__(kMmaThreads, 1) readout_mma_kernel(const __grid_constant__ MmaArgs A) {
+// One 16-byte-piece prefetch of a block into a staging buffer: E rows of the
+// block's group (zero past c_end and for rows >= n_runs) and the block's xh,
+// yh, zh, fh, r2 (the FP32 block is zero-padded to a multiple of 32 spins).
+// Thread t copies pieces t and t + 512 of the E rows (rows t / 16 and
+// t / 16 + 32, 2 spins each); the group's row offsets are cached per thread.
+struct MmaPrefetch {
+    int group = -1;
+    int64_t off[2] = {-1, -1};  // element offset of the thread's two E rows (slot x n_pad), -1: no run
+
+    __device__ __forceinline__ void prefetch(unsigned char* in, const MmaArgs& A, int g, int64_t s0, int64_t c_end,
+                                             int tid) {
+        if (g != group) {
+            const MmaGroup G = A.groups[g];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = (tid >> 4) + 32 * i;
+                off[i] = r < G.n_runs ? static_cast<int64_t>(A.runs[G.run0 + r].slot) * A.n_pad : -1;
+            }
+            group = g;
+        }
+        const uint32_t base = smem_u32(in);
+        const int q = tid & 15;
+        const int64_t sp = s0 + 2 * q;
+        const int64_t left = c_end - sp;
+        const uint32_t nb = left >= 2 ? 16u : (left == 1 ? 8u : 0u);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int r = (tid >> 4) + 32 * i;
+            const bool live = off[i] >= 0 && nb > 0;
+            cp_async16(base + static_cast<uint32_t>(r * kMmaERowBytes + q * 16), live ? A.e + off[i] + sp : A.e,
+                       live ? nb : 0u);
+        }
+        if (tid < 40) {
+            const int a = tid >> 3, qq = tid & 7;
+            const int row = a == 0 ? P32_XH : a == 1 ? P32_YH : a == 2 ? P32_ZH : a == 3 ? P32_FH : P32_R2;
+            cp_async16(base + static_cast<uint32_t>(kMmaStageE + a * kMmaChunk * 4 + qq * 16),
+                       A.p32 + static_cast<int64_t>(row) * A.n_pad + s0 + 4 * qq, 16u);
+        }
+    }
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Barrier 1 over the producer threads only, returning the OR of `v` over them
+// (every producer gets the same answer).
+__device__ __forceinline__ bool producer_sync_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(v)), "n"(kMmaThreads)
+        : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const __grid_constant__ MmaArgs A) {
     extern __shared__ __align__(1024) unsigned char s_mma[];
-    unsigned char* s_in = s_mma + 2 * kMmaStageBytes;  // two staging buffers
-    uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_in + 2 * kMmaStageInPad);
-    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(s_in + 2 * kMmaStageInPad + 64);
+    unsigned char* s_in = s_mma + 2 * kMmaStageBytes;  // kMmaStaging staging buffers
+    // s_bar [0, 1] stage full (one arrival per producer thread), [2, 3] stage
+    // empty (the MMA commit), [4, 5] accumulator buffer read (one arrival per
+    // producer thread); then the TMEM address, the abort flag, the commit count
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_in + kMmaStaging * kMmaStageInPad);
+    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(s_bar + 6);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(s_bar + 7);
+    volatile int* s_issued = reinterpret_cast<volatile int*>(s_bar + 8);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t c_begin = static_cast<int64_t>(blockIdx.x) * A.spins_per_cta;
     const int64_t c_end = min(A.n, c_begin + A.spins_per_cta);
     const int n_chunks = c_end > c_begin ? static_cast<int>((c_end - c_begin + kMmaChunk - 1) / kMmaChunk) : 0;
     const int n_it = n_chunks * A.n_groups;
+    const BarPair full{smem_u32(&s_bar[0])}, empty{smem_u32(&s_bar[2])}, acc_free{smem_u32(&s_bar[4])};
+    constexpr int kProducerWarps = kMmaThreads / 32;
 
-    if (warp == 0) {
+    if (warp == kProducerWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_taddr)),
                      "r"(kMmaTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(smem_u32(&s_bar[0]), 1);
-        mbar_init(smem_u32(&s_bar[1]), 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(full[i], kMmaThreads);
+            mbar_init(empty[i], 1);
+            mbar_init(acc_free[i], kMmaThreads);
+        }
+        *s_abort = 0;
+        *s_issued = 0;
         fence_mbar_init();
     }
-    if (n_it > 0) mma_prefetch(s_in, A, A.groups[0], c_begin, c_end, tid);
-    cp_async_commit();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *s_taddr;
-    const BarPair bar{smem_u32(&s_bar[0])};
-    float* __restrict__ out = reinterpret_cast<float*>(A.partial + static_cast<int64_t>(blockIdx.x) * A.n_adc);
 
-    bool ok = true;
-    int it = 0;  // block it: stage and staging it & 1, phase (it >> 1) & 1 of bar[it & 1]
-    for (; it < n_it; ++it) {
-        const int gi = it / n_chunks, ch = it - gi * n_chunks;
-        const MmaGroup G = A.groups[gi];
-        const int st = it & 1;
-        if (it + 1 < n_it) {
-            const int gn = (it + 1) / n_chunks, cn = it + 1 - gn * n_chunks;
-            mma_prefetch(s_in + (st ^ 1) * kMmaStageInPad, A, A.groups[gn],
-                         c_begin + static_cast<int64_t>(cn) * kMmaChunk, c_end, tid);
-        }
-        cp_async_commit();
-        cp_async_wait<1>();  // this block's staging has landed (this thread's copies)
-        bool w = true;
-        if (it >= 2) w = mbar_wait_bounded(bar[st], ((it - 2) >> 1) & 1);  // MMAs of block it - 2 done
-        if (__syncthreads_or(!w)) {
-            ok = false;
-            break;
-        }
-        unsigned char* stage = s_mma + st * kMmaStageBytes;
-        const unsigned char* in = s_in + st * kMmaStageInPad;
-        mma_fill_e(stage, in, warp, lane);
-        mma_fill_z(stage, in, G, warp, lane);
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t base = smem_u32(stage);
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-                const uint64_t ah = mma_smem_desc(base + ks * kMmaTileBytes);
-                const uint64_t al = mma_smem_desc(base + (4 + ks) * kMmaTileBytes);
-                const uint64_t bh = mma_smem_desc(base + (8 + ks) * kMmaTileBytes);
-                const uint64_t bl = mma_smem_desc(base + (12 + ks) * kMmaTileBytes);
-                tc_mma_f16(tmem, ah, bh, (ch > 0 || ks > 0) ? 1u : 0u);
-                tc_mma_f16(tmem, ah, bl, 1u);
-                tc_mma_f16(tmem, al, bh, 1u);
+    if (warp == kProducerWarps) {
+        // ---- MMA issuer: block it into accumulator buffer (its group) & 1
+        for (int it = 0; it < n_it; ++it) {
+            const int gi = it / n_chunks, ch = it - gi * n_chunks, st = it & 1;
+            bool w = true;
+            if (ch == 0 && gi >= 2) w = mbar_wait_bounded(acc_free[gi & 1], ((gi - 2) >> 1) & 1);
+            if (w) w = mbar_wait_bounded(full[st], (it >> 1) & 1);
+            if (!__all_sync(kFull, w && !*s_abort)) {
+                if (lane == 0) *s_abort = 1;
+                break;
             }
-            tc_commit(bar[st]);
-        }
-        if (ch + 1 < n_chunks) continue;
-        // epilogue of group gi: wait for its last block, then TMEM -> this CTA's row
-        w = mbar_wait_bounded(bar[st], (it >> 1) & 1);
-        if (__syncthreads_or(!w)) {
-            ok = false;
-            ++it;  // block it was issued
-            break;
-        }
-        tc_fence_after();
-        const int quarter = warp & 3, cgrp = warp >> 2;
-        const int row = 32 * quarter + lane, r = row >> 1, part = row & 1;
-        MmaRun run{0, 0, 0};
-        if (r < G.n_runs) run = A.runs[G.run0 + r];
+            tc_fence_after();
+            if (lane == 0) {
+                const uint32_t base = smem_u32(s_mma + st * kMmaStageBytes);
+                const uint32_t d = tmem + static_cast<uint32_t>((gi & 1) * 128);
 #pragma unroll
-        for (int cc = 0; cc < 32; cc += 16) {
-            const int col0 = 32 * cgrp + cc;
-            uint32_t v[16];
-            tc_ld16(tmem + (static_cast<uint32_t>(32 * quarter) << 16) + static_cast<uint32_t>(col0), v);
-#pragma unroll
-            for (int q = 0; q < 16; ++q)
-                if (col0 + q < run.len) out[2 * (run.k0 + col0 + q) + part] = __uint_as_float(v[q]) * A.einv;
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint64_t ah = mma_smem_desc(base + ks * kMmaTileBytes);
+                    const uint64_t al = mma_smem_desc(base + (4 + ks) * kMmaTileBytes);
+                    const uint64_t bh = mma_smem_desc(base + (8 + ks) * kMmaTileBytes);
+                    const uint64_t bl = mma_smem_desc(base + (12 + ks) * kMmaTileBytes);
+                    tc_mma_f16(d, ah, bh, (ch > 0 || ks > 0) ? 1u : 0u);
+                    tc_mma_f16(d, ah, bl, 1u);
+                    tc_mma_f16(d, al, bh, 1u);
+                }
+                tc_commit(empty[st]);
+                *s_issued = it + 1;
+            }
+            __syncwarp();
         }
-        tc_fence_before();
-        __syncthreads();
+    } else {
+        // ---- producers: staging two blocks ahead (cp.async), operand slices,
+        // each group's epilogue
+        float* __restrict__ out = reinterpret_cast<float*>(A.partial + static_cast<int64_t>(blockIdx.x) * A.n_adc);
+        MmaPrefetch pf;
+#pragma unroll 1
+        for (int k = 0; k < 2; ++k) {
+            if (k < n_it) {
+                const int gk = k / n_chunks;
+                pf.prefetch(s_in + k * kMmaStageInPad, A, gk,
+                            c_begin + static_cast<int64_t>(k - gk * n_chunks) * kMmaChunk, c_end, tid);
+            }
+            cp_async_commit();
+        }
+        for (int it = 0; it < n_it; ++it) {
+            const int gi = it / n_chunks, ch = it - gi * n_chunks, st = it & 1;
+            if (it + 2 < n_it) {
+                const int gk = (it + 2) / n_chunks;
+                pf.prefetch(s_in + ((it + 2) % kMmaStaging) * kMmaStageInPad, A, gk,
+                            c_begin + static_cast<int64_t>(it + 2 - gk * n_chunks) * kMmaChunk, c_end, tid);
+            }
+            cp_async_commit();
+            cp_async_wait<2>();  // this thread's copies of block it have landed
+            bool w = true;
+            if (it >= 2) w = mbar_wait_bounded(empty[st], ((it - 2) >> 1) & 1);  // MMAs of block it - 2 done
+            // staging of block it visible to every producer; a uniform stop
+            if (producer_sync_or(!w || *s_abort)) {
+                *s_abort = 1;
+                break;
+            }
+            const MmaGroup G = A.groups[gi];
+            unsigned char* stage = s_mma + st * kMmaStageBytes;
+            const unsigned char* in = s_in + (it % kMmaStaging) * kMmaStageInPad;
+            mma_fill_e(stage, in, warp, lane);
+            mma_fill_z(stage, in, G, warp, lane);
+            fence_proxy_async_smem();
+            mbar_arrive(full[st]);
+            if (ch + 1 < n_chunks) continue;
+            // epilogue of group gi: its last commit covers all its MMAs
+            w = mbar_wait_bounded(empty[st], (it >> 1) & 1);
+            if (producer_sync_or(!w || *s_abort)) {
+                *s_abort = 1;
+                break;
+            }
+            tc_fence_after();
+            const int quarter = warp & 3, cgrp = warp >> 2;
+            const int row = 32 * quarter + lane, r = row >> 1, part = row & 1;
+            MmaRun run{0, 0, 0};
+            if (r < G.n_runs) run = A.runs[G.run0 + r];
+#pragma unroll
+            for (int cc = 0; cc < 32; cc += 16) {
+                const int col0 = 32 * cgrp + cc;
+                uint32_t v[16];
+                tc_ld16(tmem + (static_cast<uint32_t>(32 * quarter) << 16) +
+                            static_cast<uint32_t>((gi & 1) * 128 + col0),
+                        v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (col0 + q < run.len) out[2 * (run.k0 + col0 + q) + part] = __uint_as_float(v[q]) * A.einv;
+            }
+            tc_fence_before();
+            mbar_arrive(acc_free[gi & 1]);
+        }
+        cp_async_wait<0>();
     }
-    cp_async_wait<0>();
-    if (!ok) {
-        if (tid == 0) atomicOr(A.status, 1);
-        // no MMA may still write tensor memory when it is released
-        if (it > 0) mbar_wait_bounded(bar[(it - 1) & 1], ((it - 1) >> 1) & 1);
+    __syncthreads();
+    if (*s_abort && tid == 0) {
+        atomicOr(A.status, 1);
+        // tensor memory is released only after every issued MMA completed
+        // (commits complete in order: wait for the latest)
+        const int n = *s_issued;
+        if (n > 0) mbar_wait_bounded(empty[(n - 1) & 1], ((n - 1) >> 1) & 1);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0)
+    tc_fence_after();
+    if (warp == kProducerWarps)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMmaTmemCols)
                      : "memory");
 }
@@ -2202,8 +2279,8 @@ int launch_readout_mma(const MmaArgs& a, int grid, void* stream) {
                                                   static_cast<int>(kMmaDynSmem));
     if (attr != cudaSuccess) return attr;
     if (grid <= 0 || a.spins_per_cta % kMmaChunk != 0 || a.n_pad % 2 != 0) return cudaErrorInvalidValue;
-    readout_mma_kernel<<<static_cast<unsigned>(grid), kMmaThreads, kMmaDynSmem, static_cast<cudaStream_t>(stream)>>>(
-        a);
+    readout_mma_kernel<<<static_cast<unsigned>(grid), kMmaThreads + 32, kMmaDynSmem,
+                         static_cast<cudaStream_t>(stream)>>>(a);
     return cudaGetLastError();
 }
 
