@@ -1595,17 +1595,19 @@ __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_cons
 //
 // Pipeline per CTA (one per SM), warp-specialised, block i of the flattened
 // (group, block) sequence:
-//   16 producer warps: cp.async brings block i + 2's E rows and spin
-//   parameters into one of four staging buffers (zero-filled past the last
-//   spin); block i's staging becomes the FP16 operand slices of stage i & 1
-//   once the MMAs of block i - 2 have released it (mbarrier "empty", the
-//   tensor core's commit), then each producer arrives on "full";
+//   16 producer warps copy block i + 2's E rows (256 bytes per run) and
+//   spin parameters into staging buffer (i + 2) % 4 with cp.async once
+//   every producer has read the block that used it before ("staging
+//   read"); each thread arrives on "staged" when its copies have landed;
+//   they turn block i's staging into the FP16 operand slices
+//   of stage i & 1 once the MMAs of block i - 2 have released it ("empty",
+//   the tensor core's commit), then arrive on "full" and "staging read";
 //   one MMA warp waits for "full", issues block i's 12 MMAs into accumulator
 //   buffer (group & 1) and commits them to "empty";
 //   after a group's last block the producers read the accumulator from
-//   tensor memory into the CTA's partial row and release the buffer.
-// Every wait is bounded; a wait that gives up stops both roles (a uniform
-// decision among producers via a reducing named barrier).
+//   tensor memory into the CTA's partial row and release the buffer
+//   ("accumulator read").
+// Every wait is bounded; a wait that gives up stops every role.
 // Operand slices: 128 rows x 16 FP16 (4 KB), K-major without swizzle: 8-row
 // x 16-byte core matrices, K-adjacent ones 128 B apart, row-adjacent ones
 // 256 B apart. z_s^l comes from z^(j + 32 g) and z^8 (direct, with an exact
@@ -1619,7 +1621,7 @@ constexpr int kMmaERowBytes = kMmaChunk * 8 + 32;   // staged E row: 32 spins + 
 constexpr int kMmaStageE = kMmaRuns * kMmaERowBytes;           // 18 KB
 constexpr int kMmaStageIn = kMmaStageE + 5 * kMmaChunk * 4;    // + xh, yh, zh, fh, r2 of the block
 constexpr int kMmaStageInPad = (kMmaStageIn + 127) / 128 * 128;
-constexpr int kMmaStaging = 4;                      // staging buffers (prefetch distance 2)
+constexpr int kMmaStaging = 4;                      // staging buffers (the loader runs up to 4 blocks ahead)
 constexpr uint32_t kMmaTmemCols = 256;              // two FP32 accumulators of 128 lanes x 128 columns
 constexpr size_t kMmaDynSmem = 2 * kMmaStageBytes + kMmaStaging * kMmaStageInPad + 256;  // one CTA per SM
 
@@ -1662,14 +1664,6 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-// 16-byte global -> shared copy, bytes past `src_bytes` (0..16) zero-filled
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 // v = hi + lo as FP16 pairs (a in the low half)
 __device__ __forceinline__ void split_half2(float a, float b, uint32_t& hi, uint32_t& lo) {
     const __half2 h = __floats2half2_rn(a, b);
@@ -1681,8 +1675,10 @@ __device__ __forceinline__ void split_half2(float a, float b, uint32_t& hi, uint
 
 // A slices (E part) of a stage from the staging: 2 row words a thread (4
 // spins of one row, hi and lo); the 32 lanes of a warp write 512 contiguous
-// bytes of one slice.
-__device__ __forceinline__ void mma_fill_e(unsigned char* stage, const unsigned char* in, int warp, int lane) {
+// bytes of one slice. Rows of runs past the group's n_runs and spins past
+// the block's `live` ones are zero (their staging is stale or unwritten).
+__device__ __forceinline__ void mma_fill_e(unsigned char* stage, const unsigned char* in, int n_runs, int live,
+                                           int warp, int lane) {
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         const int wt = warp + 16 * i;
@@ -1690,10 +1686,17 @@ __device__ __forceinline__ void mma_fill_e(unsigned char* stage, const unsigned 
         const int row = 16 * (wt & 7) + 8 * (lane >> 4) + (lane & 7);
         const int kg = (lane >> 3) & 1;
         const bool im_row = row & 1;
-        const float4* e4 = reinterpret_cast<const float4*>(in + (row >> 1) * kMmaERowBytes + (8 * kap + 4 * kg) * 8);
-        const float4 a = e4[0], b = e4[1];
-        const float re[4] = {a.x, a.z, b.x, b.z};
-        const float im[4] = {a.y, a.w, b.y, b.w};
+        const int sb = 8 * kap + 4 * kg;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        if ((row >> 1) < n_runs) {
+            const float4* e4 = reinterpret_cast<const float4*>(in + (row >> 1) * kMmaERowBytes + sb * 8);
+            a = e4[0];
+            b = e4[1];
+        }
+        const float re[4] = {sb < live ? a.x : 0.f, sb + 1 < live ? a.z : 0.f, sb + 2 < live ? b.x : 0.f,
+                             sb + 3 < live ? b.z : 0.f};
+        const float im[4] = {sb < live ? a.y : 0.f, sb + 1 < live ? a.w : 0.f, sb + 2 < live ? b.y : 0.f,
+                             sb + 3 < live ? b.w : 0.f};
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) split_half2(im_row ? im[q] : re[q], im_row ? re[q] : -im[q], hi[q], lo[q]);
@@ -1760,84 +1763,83 @@ __device__ __forceinline__ void mma_fill_z(unsigned char* stage, const unsigned 
     }
 }
 
-// One 16-byte-piece prefetch of a block into a staging buffer: E rows of the
-// block's group (zero past c_end and for rows >= n_runs) and the block's xh,
-// yh, zh, fh, r2 (the FP32 block is zero-padded to a multiple of 32 spins).
-// Thread t copies pieces t and t + 512 of the E rows (rows t / 16 and
-// t / 16 + 32, 2 spins each); the group's row offsets are cached per thread.
-struct MmaPrefetch {
-    int group = -1;
-    int64_t off[2] = {-1, -1};  // element offset of the thread's two E rows (slot x n_pad), -1: no run
-
-    __device__ __forceinline__ void prefetch(unsigned char* in, const MmaArgs& A, int g, int64_t s0, int64_t c_end,
-                                             int tid) {
-        if (g != group) {
-            const MmaGroup G = A.groups[g];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = (tid >> 4) + 32 * i;
-                off[i] = r < G.n_runs ? static_cast<int64_t>(A.runs[G.run0 + r].slot) * A.n_pad : -1;
-            }
-            group = g;
-        }
-        const uint32_t base = smem_u32(in);
-        const int q = tid & 15;
-        const int64_t sp = s0 + 2 * q;
-        const int64_t left = c_end - sp;
-        const uint32_t nb = left >= 2 ? 16u : (left == 1 ? 8u : 0u);
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int r = (tid >> 4) + 32 * i;
-            const bool live = off[i] >= 0 && nb > 0;
-            cp_async16(base + static_cast<uint32_t>(r * kMmaERowBytes + q * 16), live ? A.e + off[i] + sp : A.e,
-                       live ? nb : 0u);
-        }
-        if (tid < 40) {
-            const int a = tid >> 3, qq = tid & 7;
-            const int row = a == 0 ? P32_XH : a == 1 ? P32_YH : a == 2 ? P32_ZH : a == 3 ? P32_FH : P32_R2;
-            cp_async16(base + static_cast<uint32_t>(kMmaStageE + a * kMmaChunk * 4 + qq * 16),
-                       A.p32 + static_cast<int64_t>(row) * A.n_pad + s0 + 4 * qq, 16u);
-        }
-    }
-};
-
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
-// Barrier 1 over the producer threads only, returning the OR of `v` over them
-// (every producer gets the same answer).
-__device__ __forceinline__ bool producer_sync_or(bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.or.pred p, 1, %2, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(r)
-        : "r"(static_cast<uint32_t>(v)), "n"(kMmaThreads)
-        : "memory");
-    return r != 0;
+// Staging of one block by the 512 producer threads: the E rows of the
+// block's group (thread t copies 16 bytes of rows t / 16 and t / 16 + 32;
+// rows of runs past n_runs are skipped and read as zero) and the block's
+// xh, yh, zh, fh, r2 (threads 0..39). Spins past the last one are copied as
+// they are (inside the padded rows) and read as zero. The group's row
+// offsets are cached per thread.
+struct MmaStager {
+    int group = -1;
+    int64_t off[2] = {-1, -1};  // element offset of the thread's two E rows (slot x n_pad), -1: no run
+
+    __device__ __forceinline__ void stage(unsigned char* in, const MmaArgs& A, int g, int64_t s0, int tid);
+};
+
+// 16-byte global -> shared copy (cp.async, L2 only), and the arrival on
+// `bar` of this thread once all its earlier copies have landed
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void MmaStager::stage(unsigned char* in, const MmaArgs& A, int g, int64_t s0, int tid) {
+    if (g != group) {
+        const MmaGroup G = A.groups[g];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int r = (tid >> 4) + 32 * i;
+            off[i] = r < G.n_runs ? static_cast<int64_t>(A.runs[G.run0 + r].slot) * A.n_pad : -1;
+        }
+        group = g;
+    }
+    const uint32_t base = smem_u32(in);
+    const int q = tid & 15;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        if (off[i] >= 0)
+            cp_async16(base + static_cast<uint32_t>(((tid >> 4) + 32 * i) * kMmaERowBytes + q * 16),
+                       A.e + off[i] + s0 + 2 * q);
+    if (tid < 40) {
+        const int a = tid >> 3, qq = tid & 7;
+        const int row = a == 0 ? P32_XH : a == 1 ? P32_YH : a == 2 ? P32_ZH : a == 3 ? P32_FH : P32_R2;
+        cp_async16(base + static_cast<uint32_t>(kMmaStageE + a * kMmaChunk * 4 + qq * 16),
+                   A.p32 + static_cast<int64_t>(row) * A.n_pad + s0 + 4 * qq);
+    }
 }
 
 __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const __grid_constant__ MmaArgs A) {
     extern __shared__ __align__(1024) unsigned char s_mma[];
     unsigned char* s_in = s_mma + 2 * kMmaStageBytes;  // kMmaStaging staging buffers
-    // s_bar [0, 1] stage full (one arrival per producer thread), [2, 3] stage
-    // empty (the MMA commit), [4, 5] accumulator buffer read (one arrival per
-    // producer thread); then the TMEM address, the abort flag, the commit count
+    // mbarriers: [0, 1] stage full (producer threads arrive), [2, 3] stage
+    // empty (MMA commit), [4, 5] accumulator buffer read (producer threads),
+    // [6 .. 9] staging loaded (producer threads, on their copies' completion),
+    // [10 .. 13] staging read
+    // (producer threads); then the TMEM address, the abort flag, the commit count
     uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_in + kMmaStaging * kMmaStageInPad);
-    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(s_bar + 6);
-    volatile int* s_abort = reinterpret_cast<volatile int*>(s_bar + 7);
-    volatile int* s_issued = reinterpret_cast<volatile int*>(s_bar + 8);
+    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(s_bar + 14);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(s_bar + 15);
+    volatile int* s_issued = reinterpret_cast<volatile int*>(s_bar + 16);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t c_begin = static_cast<int64_t>(blockIdx.x) * A.spins_per_cta;
     const int64_t c_end = min(A.n, c_begin + A.spins_per_cta);
     const int n_chunks = c_end > c_begin ? static_cast<int>((c_end - c_begin + kMmaChunk - 1) / kMmaChunk) : 0;
     const int n_it = n_chunks * A.n_groups;
-    const BarPair full{smem_u32(&s_bar[0])}, empty{smem_u32(&s_bar[2])}, acc_free{smem_u32(&s_bar[4])};
+    const uint32_t bar0 = smem_u32(s_bar);
+    auto full = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(i); };
+    auto empty = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(2 + i); };
+    auto acc_free = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(4 + i); };
+    auto staged = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(6 + i); };
+    auto staging_free = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(10 + i); };
     constexpr int kProducerWarps = kMmaThreads / 32;
+    constexpr int kMmaWarp = kProducerWarps;
 
-    if (warp == kProducerWarps) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_taddr)),
                      "r"(kMmaTmemCols)
                      : "memory");
@@ -1845,9 +1847,13 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
     }
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
-            mbar_init(full[i], kMmaThreads);
-            mbar_init(empty[i], 1);
-            mbar_init(acc_free[i], kMmaThreads);
+            mbar_init(full(i), kMmaThreads);
+            mbar_init(empty(i), 1);
+            mbar_init(acc_free(i), kMmaThreads);
+        }
+        for (int i = 0; i < kMmaStaging; ++i) {
+            mbar_init(staged(i), kMmaThreads);
+            mbar_init(staging_free(i), kMmaThreads);
         }
         *s_abort = 0;
         *s_issued = 0;
@@ -1858,13 +1864,14 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
     tc_fence_after();
     const uint32_t tmem = *s_taddr;
 
-    if (warp == kProducerWarps) {
+    if (warp == kMmaWarp) {
         // ---- MMA issuer: block it into accumulator buffer (its group) & 1
+        int gi = 0, ch = 0;
         for (int it = 0; it < n_it; ++it) {
-            const int gi = it / n_chunks, ch = it - gi * n_chunks, st = it & 1;
+            const int st = it & 1;
             bool w = true;
-            if (ch == 0 && gi >= 2) w = mbar_wait_bounded(acc_free[gi & 1], ((gi - 2) >> 1) & 1);
-            if (w) w = mbar_wait_bounded(full[st], (it >> 1) & 1);
+            if (ch == 0 && gi >= 2) w = mbar_wait_bounded(acc_free(gi & 1), ((gi - 2) >> 1) & 1);
+            if (w) w = mbar_wait_bounded(full(st), (it >> 1) & 1);
             if (!__all_sync(kFull, w && !*s_abort)) {
                 if (lane == 0) *s_abort = 1;
                 break;
@@ -1883,52 +1890,60 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
                     tc_mma_f16(d, ah, bl, 1u);
                     tc_mma_f16(d, al, bh, 1u);
                 }
-                tc_commit(empty[st]);
+                tc_commit(empty(st));
                 *s_issued = it + 1;
             }
             __syncwarp();
+            if (++ch == n_chunks) {
+                ch = 0;
+                ++gi;
+            }
         }
     } else {
-        // ---- producers: staging two blocks ahead (cp.async), operand slices,
-        // each group's epilogue
+        // ---- producers: staging two blocks ahead, operand slices from the
+        // staging, each group's epilogue
         float* __restrict__ out = reinterpret_cast<float*>(A.partial + static_cast<int64_t>(blockIdx.x) * A.n_adc);
-        MmaPrefetch pf;
-#pragma unroll 1
-        for (int k = 0; k < 2; ++k) {
-            if (k < n_it) {
-                const int gk = k / n_chunks;
-                pf.prefetch(s_in + k * kMmaStageInPad, A, gk,
-                            c_begin + static_cast<int64_t>(k - gk * n_chunks) * kMmaChunk, c_end, tid);
+        MmaStager pf;
+        int pg = 0, pc = 0;  // (group, block) of the next block to stage
+        auto stage_next = [&](int k) {
+            pf.stage(s_in + (k % kMmaStaging) * kMmaStageInPad, A, pg, c_begin + static_cast<int64_t>(pc) * kMmaChunk,
+                     tid);
+            cp_async_arrive(staged(k % kMmaStaging));
+            if (++pc == n_chunks) {
+                pc = 0;
+                ++pg;
             }
-            cp_async_commit();
-        }
+        };
+        for (int k = 0; k < 2 && k < n_it; ++k) stage_next(k);
+        int gi = 0, ch = 0;
+        MmaGroup G = n_it > 0 ? A.groups[0] : MmaGroup{};
         for (int it = 0; it < n_it; ++it) {
-            const int gi = it / n_chunks, ch = it - gi * n_chunks, st = it & 1;
-            if (it + 2 < n_it) {
-                const int gk = (it + 2) / n_chunks;
-                pf.prefetch(s_in + ((it + 2) % kMmaStaging) * kMmaStageInPad, A, gk,
-                            c_begin + static_cast<int64_t>(it + 2 - gk * n_chunks) * kMmaChunk, c_end, tid);
-            }
-            cp_async_commit();
-            cp_async_wait<2>();  // this thread's copies of block it have landed
+            const int st = it & 1, buf = it % kMmaStaging;
             bool w = true;
-            if (it >= 2) w = mbar_wait_bounded(empty[st], ((it - 2) >> 1) & 1);  // MMAs of block it - 2 done
-            // staging of block it visible to every producer; a uniform stop
-            if (producer_sync_or(!w || *s_abort)) {
+            if (it + 2 < n_it) {
+                // buffer (it + 2) % 4 last held block it - 2: every producer has read it
+                if (it + 2 >= kMmaStaging)
+                    w = mbar_wait_bounded(staging_free((it + 2) % kMmaStaging), ((it + 2 - kMmaStaging) / kMmaStaging) & 1);
+                if (w) stage_next(it + 2);
+            }
+            if (w) w = mbar_wait_bounded(staged(buf), (it / kMmaStaging) & 1);
+            if (w && it >= 2) w = mbar_wait_bounded(empty(st), ((it - 2) >> 1) & 1);  // MMAs of block it - 2 done
+            if (!w || *s_abort) {
                 *s_abort = 1;
                 break;
             }
-            const MmaGroup G = A.groups[gi];
+            const int64_t s0 = c_begin + static_cast<int64_t>(ch) * kMmaChunk;
+            const int live = static_cast<int>(min(static_cast<int64_t>(kMmaChunk), c_end - s0));
             unsigned char* stage = s_mma + st * kMmaStageBytes;
-            const unsigned char* in = s_in + (it % kMmaStaging) * kMmaStageInPad;
-            mma_fill_e(stage, in, warp, lane);
+            const unsigned char* in = s_in + buf * kMmaStageInPad;
+            mma_fill_e(stage, in, G.n_runs, live, warp, lane);
             mma_fill_z(stage, in, G, warp, lane);
             fence_proxy_async_smem();
-            mbar_arrive(full[st]);
-            if (ch + 1 < n_chunks) continue;
-            // epilogue of group gi: its last commit covers all its MMAs
-            w = mbar_wait_bounded(empty[st], (it >> 1) & 1);
-            if (producer_sync_or(!w || *s_abort)) {
+            mbar_arrive(full(st));
+            mbar_arrive(staging_free(buf));
+            if (++ch < n_chunks) continue;
+            // epilogue of the group: its last commit covers all its MMAs
+            if (!mbar_wait_bounded(empty(st), (it >> 1) & 1) || *s_abort) {
                 *s_abort = 1;
                 break;
             }
@@ -1949,9 +1964,11 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
                     if (col0 + q < run.len) out[2 * (run.k0 + col0 + q) + part] = __uint_as_float(v[q]) * A.einv;
             }
             tc_fence_before();
-            mbar_arrive(acc_free[gi & 1]);
+            mbar_arrive(acc_free(gi & 1));
+            ch = 0;
+            if (++gi < A.n_groups) G = A.groups[gi];
         }
-        cp_async_wait<0>();
+        asm volatile("cp.async.wait_all;" ::: "memory");
     }
     __syncthreads();
     if (*s_abort && tid == 0) {
@@ -1959,12 +1976,12 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
         // tensor memory is released only after every issued MMA completed
         // (commits complete in order: wait for the latest)
         const int n = *s_issued;
-        if (n > 0) mbar_wait_bounded(empty[(n - 1) & 1], ((n - 1) >> 1) & 1);
+        if (n > 0) mbar_wait_bounded(empty((n - 1) & 1), ((n - 1) >> 1) & 1);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kProducerWarps)
+    if (warp == kMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMmaTmemCols)
                      : "memory");
 }
