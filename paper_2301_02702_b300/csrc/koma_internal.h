@@ -43,14 +43,19 @@ constexpr int kTermShift = 16;       // nonzero-term bits of PREC/ADC records
 // Matrix form of the readout. ADC runs whose samples share the per-sample
 // rotator (the same dK and dtau, as FP32 values) are grouped, up to kMmaRuns
 // runs a group. Sample l of run r sums E_s(r) z_s^l over the spins s, with
-// E_s(r) the spin's transverse magnetisation at the run's first sample (the
-// exact evaluation the Bloch kernel makes at every run start) and z_s the
-// rotator e^{-dtau/T2} e^{-i 2 pi (dK.x + df dtau)}: a complex matrix product
-// C[r][l] = sum_s E_s(r) z_s^l over spins, taken on the tensor cores. The
-// Bloch kernel stores E for the flagged ADC records (row `slot` of an
-// [n_slots][n_pad] buffer, slots in record order) instead of sampling them.
+// E_s(r) the spin's transverse magnetisation at the run's first sample and
+// z_s the rotator e^{-dtau/T2} e^{-i 2 pi (dK.x + df dtau)}: a complex matrix
+// product C[r][l] = sum_s E_s(r) z_s^l over spins, taken on the tensor cores.
+// E_s(r) = Mxy_s(t_ref) e^{-tau0/T2} e^{-i 2 pi (K0.x + df tau0)} is
+// evaluated there too, from the run's (K0, tau0) and a snapshot of
+// Mxy(t_ref): the state is constant between RF and PREC records, so the
+// Bloch kernel stores one snapshot per such stretch ("block") that holds
+// matrix-form runs, at the block's first flagged record (kMmaSnapFlag), into
+// row `snap` of an [n_snaps][n_pad] buffer (rows in record order), and
+// steps no flagged sample itself.
 constexpr int kMmaRuns = 64;          // runs per group: 128 matrix rows (Re, Im of each)
 constexpr int kMmaFlag = 1 << 28;     // ADC record count bit: sampled by the matrix form
+constexpr int kMmaSnapFlag = 1 << 29; // ... and the first of its block: store the snapshot
 constexpr int kMmaMinRuns = 8;        // smallest group worth a tensor-core pass
 constexpr int64_t kMmaMinSamples = 1024;
 
@@ -60,15 +65,19 @@ struct MmaGroup {
     int32_t run0;     // first entry of the group in the run table
     int32_t n_runs;   // 1..kMmaRuns
     int32_t max_len;  // longest run (samples)
-    int32_t pad_;
+    int32_t one_snap; // 1: every run of the group uses the same snapshot row
 };
 static_assert(sizeof(MmaGroup) == 32, "MmaGroup layout");
 struct MmaRun {
-    int64_t k0;    // first sample
-    int32_t len;   // samples
-    int32_t slot;  // row of the E buffer
+    int64_t k0;       // first sample
+    int32_t len;      // samples
+    int32_t snap;     // snapshot row of the run's block
+    float kh[3], kl[3];  // K0 (turns/m) hi/lo, relative to the block's t_ref
+    float th, tl;     // tau0 (s) hi/lo
+    int32_t terms;    // nonzero terms of K0, tau0 (bits 0..3: x, y, z, tau), as the record's
+    int32_t pad_[3];
 };
-static_assert(sizeof(MmaRun) == 16, "MmaRun layout");
+static_assert(sizeof(MmaRun) == 64, "MmaRun layout");
 
 // 64-byte record of the FP32 split-phase path.
 //   RF:   a[0..2] pi gbar gammabar dt (rad/m)   a[3..4] pi B1 gammabar dt (rad):
@@ -181,11 +190,11 @@ struct BlochArgs {
     const double* pv64 = nullptr;   // [3][n_pad]
     float vext[3] = {0, 0, 0};      // max |v_x|, |v_y|, |v_z| (m/s)
     // matrix-form readout (FP32 static kernel only): if set, ADC records
-    // carrying kMmaFlag store E = Mxy at their first sample into row `slot`
-    // of this [n_slots][n_pad] buffer (slot = the record's rank among the
-    // flagged records) and are not sampled here
-    float2* mma_e = nullptr;
-    float mma_escale = 1.f;         // E is stored times this power of two (FP16 range)
+    // carrying kMmaFlag are not sampled here; those also carrying
+    // kMmaSnapFlag store Mxy(t_ref) x mma_escale into the next row of this
+    // [n_snaps][n_pad] buffer (rows in record order)
+    float2* mma_snap = nullptr;
+    float mma_escale = 1.f;         // power of two keeping E in FP16 range
 };
 
 // Tensor-core readout (K6): CTA c takes spins [c spins_per_cta, +spins_per_cta)
@@ -195,7 +204,8 @@ struct MmaArgs {
     const float* p32 = nullptr;
     int64_t n_pad = 0;
     int64_t n = 0;
-    const float2* e = nullptr;       // [n_slots][n_pad], scaled by 1 / einv
+    const float2* snap = nullptr;    // [n_snaps][n_pad] Mxy(t_ref) of each block, scaled by 1 / einv
+    int used = 0;                    // bit d: coordinate d (x, y, z, df) nonzero somewhere
     const MmaGroup* groups = nullptr;
     int32_t n_groups = 0;
     const MmaRun* runs = nullptr;

@@ -719,7 +719,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
 
     int red_buf = 0;
     int64_t red_base = 0, red_end = 0;  // samples [red_base, red_end) staged
-    int mma_slot = 0;                   // flagged ADC records seen so far
+    int mma_snap_row = 0;               // snapshot rows stored so far
     // one partial row per spin range; with a split each part writes the
     // samples of its own runs (s_own marks them in the staged window)
     __shared__ unsigned char s_own[SPLIT ? 2 : 1][SPLIT ? kRed32 : 1];
@@ -783,28 +783,28 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
                 if (k0 + L > red_base + kRed32) flush();
                 const int off = static_cast<int>(k0 - red_base);
                 const bool own = !SPLIT || (t * kTile + r) % split == part;
-                // a run of the matrix-form readout: only its first sample's
-                // Mxy is stored (its samples of this CTA's row are never read)
-                const bool mma = A.mma_e != nullptr && (R.count & kMmaFlag);
+                // a run of the matrix-form readout is not sampled here (its
+                // samples of this CTA's row are never read); the first of its
+                // block stores the block's Mxy(t_ref)
+                const bool mma = A.mma_snap != nullptr && (R.count & kMmaFlag);
+                const bool snap = mma && (R.count & kMmaSnapFlag);
                 if (SPLIT && warp == 0)
                     for (int i = lane; i < L; i += 32) s_own[red_buf][off + i] = own && !mma;
-                if (own) {
+                if (own && snap) {
+                    float2* __restrict__ row = A.mma_snap + static_cast<int64_t>(mma_snap_row) * np;
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        const int64_t j = sp.index(s);
+                        if (j < sp.end) row[j] = make_float2(sp.mx[s] * A.mma_escale, sp.my[s] * A.mma_escale);
+                    }
+                } else if (own && !mma) {
                     float er[S], ei[S];
                     sp.exact(R, false, A.p32, np, A.used, er, ei);
-                    if (mma) {
-                        float2* __restrict__ erow = A.mma_e + static_cast<int64_t>(mma_slot) * np;
-#pragma unroll
-                        for (int s = 0; s < S; ++s) {
-                            const int64_t j = sp.index(s);
-                            if (j < sp.end) erow[j] = make_float2(er[s] * A.mma_escale, ei[s] * A.mma_escale);
-                        }
-                    } else {
-                        sp.adc(R, L, er, ei, lane, [&](int i, float sr, float si) {
-                            red_slot(red_buf, warp, off + i) = make_float2(sr, si);
-                        });
-                    }
+                    sp.adc(R, L, er, ei, lane, [&](int i, float sr, float si) {
+                        red_slot(red_buf, warp, off + i) = make_float2(sr, si);
+                    });
                 }
-                mma_slot += mma ? 1 : 0;
+                mma_snap_row += snap ? 1 : 0;
                 red_end = k0 + L;
             }
         }
@@ -1617,9 +1617,11 @@ constexpr int kMmaThreads = 512;
 constexpr int kMmaChunk = 32;                       // spins per block
 constexpr int kMmaTileBytes = 128 * 16 * 2;         // one K = 16 slice of a 128-row FP16 operand
 constexpr int kMmaStageBytes = 16 * kMmaTileBytes;  // A hi, A lo, B hi, B lo x 4 slices (64 KB)
-constexpr int kMmaERowBytes = kMmaChunk * 8 + 32;   // staged E row: 32 spins + 32 B (bank spread)
+constexpr int kMmaERowBytes = kMmaChunk * 8 + 32;   // staged snapshot row: 32 spins + 32 B (bank spread)
 constexpr int kMmaStageE = kMmaRuns * kMmaERowBytes;           // 18 KB
-constexpr int kMmaStageIn = kMmaStageE + 5 * kMmaChunk * 4;    // + xh, yh, zh, fh, r2 of the block
+// + the block's xh, xl, yh, yl, zh, zl, fh, fl, r2 (staged in this order)
+constexpr int kMmaParams = 9;
+constexpr int kMmaStageIn = kMmaStageE + kMmaParams * kMmaChunk * 4;
 constexpr int kMmaStageInPad = (kMmaStageIn + 127) / 128 * 128;
 constexpr int kMmaStaging = 4;                      // staging buffers (the loader runs up to 4 blocks ahead)
 constexpr uint32_t kMmaTmemCols = 256;              // two FP32 accumulators of 128 lanes x 128 columns
@@ -1673,37 +1675,65 @@ __device__ __forceinline__ void split_half2(float a, float b, uint32_t& hi, uint
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// A slices (E part) of a stage from the staging: 2 row words a thread (4
-// spins of one row, hi and lo); the 32 lanes of a warp write 512 contiguous
-// bytes of one slice. Rows of runs past the group's n_runs and spins past
-// the block's `live` ones are zero (their staging is stale or unwritten).
-__device__ __forceinline__ void mma_fill_e(unsigned char* stage, const unsigned char* in, int n_runs, int live,
-                                           int warp, int lane) {
+// A slices (E part) of a stage: thread = (run r, spin quad); it evaluates
+// E_s(r) = Mxy_s(t_ref) e^{-tau0/T2} e^{-i 2 pi (K0.x + df tau0)} for its 4
+// spins (the Bloch kernel's exact evaluation: hi/lo phase products, exact
+// reduction to a fractional turn, hardware sine) and writes rows 2r
+// (Re E, -Im E) and 2r + 1 (Im E, Re E), hi and lo. Runs past n_runs and
+// spins past the block's `live` ones give zero rows.
+__device__ __forceinline__ void mma_fill_e(unsigned char* stage, const unsigned char* in, const MmaRun& run,
+                                           bool run_live, bool one_snap, int used, int live, int warp, int lane) {
+    const int r = 4 * warp + (lane & 3), q8 = lane >> 2;
+    const int kap = q8 >> 1, kg = q8 & 1, sb = 8 * kap + 4 * kg;
+    float er[4] = {0.f, 0.f, 0.f, 0.f}, ei[4] = {0.f, 0.f, 0.f, 0.f};
+    if (run_live) {
+        const float* prm = reinterpret_cast<const float*>(in + kMmaStageE);
+        const float4 XH = *reinterpret_cast<const float4*>(prm + 0 * kMmaChunk + sb);
+        const float4 XL = *reinterpret_cast<const float4*>(prm + 1 * kMmaChunk + sb);
+        const float4 YH = *reinterpret_cast<const float4*>(prm + 2 * kMmaChunk + sb);
+        const float4 YL = *reinterpret_cast<const float4*>(prm + 3 * kMmaChunk + sb);
+        const float4 ZH = *reinterpret_cast<const float4*>(prm + 4 * kMmaChunk + sb);
+        const float4 ZL = *reinterpret_cast<const float4*>(prm + 5 * kMmaChunk + sb);
+        const float4 FH = *reinterpret_cast<const float4*>(prm + 6 * kMmaChunk + sb);
+        const float4 FL = *reinterpret_cast<const float4*>(prm + 7 * kMmaChunk + sb);
+        const float4 R2 = *reinterpret_cast<const float4*>(prm + 8 * kMmaChunk + sb);
+        const float4* m4 = reinterpret_cast<const float4*>(in + (one_snap ? 0 : r) * kMmaERowBytes + sb * 8);
+        const float4 ma = m4[0], mb = m4[1];
+        const float xh[4] = {XH.x, XH.y, XH.z, XH.w}, xl[4] = {XL.x, XL.y, XL.z, XL.w};
+        const float yh[4] = {YH.x, YH.y, YH.z, YH.w}, yl[4] = {YL.x, YL.y, YL.z, YL.w};
+        const float zh[4] = {ZH.x, ZH.y, ZH.z, ZH.w}, zl[4] = {ZL.x, ZL.y, ZL.z, ZL.w};
+        const float fh[4] = {FH.x, FH.y, FH.z, FH.w}, fl[4] = {FL.x, FL.y, FL.z, FL.w};
+        const float r2[4] = {R2.x, R2.y, R2.z, R2.w};
+        const float mx[4] = {ma.x, ma.z, mb.x, mb.z}, my[4] = {ma.y, ma.w, mb.y, mb.w};
+        const int terms = run.terms & used;
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int wt = warp + 16 * i;
-        const int kap = wt >> 3;
-        const int row = 16 * (wt & 7) + 8 * (lane >> 4) + (lane & 7);
-        const int kg = (lane >> 3) & 1;
-        const bool im_row = row & 1;
-        const int sb = 8 * kap + 4 * kg;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-        if ((row >> 1) < n_runs) {
-            const float4* e4 = reinterpret_cast<const float4*>(in + (row >> 1) * kMmaERowBytes + sb * 8);
-            a = e4[0];
-            b = e4[1];
+        for (int q = 0; q < 4; ++q) {
+            float F = 0.f;
+            if (terms & 1) F += frac_product(xh[q], xl[q], run.kh[0], run.kl[0]);
+            if (terms & 2) F += frac_product(yh[q], yl[q], run.kh[1], run.kl[1]);
+            if (terms & 4) F += frac_product(zh[q], zl[q], run.kh[2], run.kl[2]);
+            if (terms & 8) F += frac_product(fh[q], fl[q], run.th, run.tl);
+            float sn = 0.f, cs = 1.f;
+            if (terms) __sincosf(-6.28318530717958647692f * (F - rintf(F)), &sn, &cs);
+            const float e2 = exp2f(-run.th * r2[q]);
+            const bool v = sb + q < live;
+            er[q] = v ? e2 * fmaf(mx[q], cs, -my[q] * sn) : 0.f;
+            ei[q] = v ? e2 * fmaf(mx[q], sn, my[q] * cs) : 0.f;
         }
-        const float re[4] = {sb < live ? a.x : 0.f, sb + 1 < live ? a.z : 0.f, sb + 2 < live ? b.x : 0.f,
-                             sb + 3 < live ? b.z : 0.f};
-        const float im[4] = {sb < live ? a.y : 0.f, sb + 1 < live ? a.w : 0.f, sb + 2 < live ? b.y : 0.f,
-                             sb + 3 < live ? b.w : 0.f};
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) split_half2(im_row ? im[q] : re[q], im_row ? re[q] : -im[q], hi[q], lo[q]);
-        const uint32_t off = static_cast<uint32_t>(kap * kMmaTileBytes) + mma_word_off(row, kg);
-        *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(stage + 4 * kMmaTileBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
+    uint32_t hi[4], lo[4], hi2[4], lo2[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        split_half2(er[q], -ei[q], hi[q], lo[q]);
+        // (Im E, Re E): the halves swapped, the new low half negated (exact)
+        hi2[q] = __byte_perm(hi[q], 0u, 0x1032) ^ 0x8000u;
+        lo2[q] = __byte_perm(lo[q], 0u, 0x1032) ^ 0x8000u;
+    }
+    const uint32_t off = static_cast<uint32_t>(kap * kMmaTileBytes) + mma_word_off(2 * r, kg);
+    *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(stage + 4 * kMmaTileBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    *reinterpret_cast<uint4*>(stage + off + 16) = make_uint4(hi2[0], hi2[1], hi2[2], hi2[3]);
+    *reinterpret_cast<uint4*>(stage + 4 * kMmaTileBytes + off + 16) = make_uint4(lo2[0], lo2[1], lo2[2], lo2[3]);
 }
 
 // B slices (rotator powers) of a stage: thread = (spin pair, j = l mod 8,
@@ -1718,10 +1748,10 @@ __device__ __forceinline__ void mma_fill_z(unsigned char* stage, const unsigned 
     const int s2 = 8 * kap + 4 * kg + 2 * half;
     const float* prm = reinterpret_cast<const float*>(in + kMmaStageE);
     const float2 X = *reinterpret_cast<const float2*>(prm + 0 * kMmaChunk + s2);
-    const float2 Y = *reinterpret_cast<const float2*>(prm + 1 * kMmaChunk + s2);
-    const float2 Z = *reinterpret_cast<const float2*>(prm + 2 * kMmaChunk + s2);
-    const float2 F = *reinterpret_cast<const float2*>(prm + 3 * kMmaChunk + s2);
-    const float2 R2 = *reinterpret_cast<const float2*>(prm + 4 * kMmaChunk + s2);
+    const float2 Y = *reinterpret_cast<const float2*>(prm + 2 * kMmaChunk + s2);
+    const float2 Z = *reinterpret_cast<const float2*>(prm + 4 * kMmaChunk + s2);
+    const float2 F = *reinterpret_cast<const float2*>(prm + 6 * kMmaChunk + s2);
+    const float2 R2 = *reinterpret_cast<const float2*>(prm + 8 * kMmaChunk + s2);
     const float xs[2] = {X.x, X.y}, ys[2] = {Y.x, Y.y}, zs[2] = {Z.x, Z.y};
     const float fs[2] = {F.x, F.y}, rs[2] = {R2.x, R2.y};
     const float m0 = static_cast<float>(j + 32 * g);
@@ -1766,15 +1796,15 @@ __device__ __forceinline__ void mma_fill_z(unsigned char* stage, const unsigned 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
-// Staging of one block by the 512 producer threads: the E rows of the
-// block's group (thread t copies 16 bytes of rows t / 16 and t / 16 + 32;
-// rows of runs past n_runs are skipped and read as zero) and the block's
-// xh, yh, zh, fh, r2 (threads 0..39). Spins past the last one are copied as
-// they are (inside the padded rows) and read as zero. The group's row
+// Staging of one block by the 512 producer threads: the snapshot rows of
+// the block's group (thread t copies 16 bytes of rows t / 16 and t / 16 + 32:
+// the rows of the group's runs, or row 0 alone when they share one) and the
+// block's spin parameters (threads 0..71). Spins past the last one are copied
+// as they are (inside the padded rows) and read as zero. The group's row
 // offsets are cached per thread.
 struct MmaStager {
     int group = -1;
-    int64_t off[2] = {-1, -1};  // element offset of the thread's two E rows (slot x n_pad), -1: no run
+    int64_t off[2] = {-1, -1};  // element offset of the thread's two snapshot rows (snap x n_pad), -1: none
 
     __device__ __forceinline__ void stage(unsigned char* in, const MmaArgs& A, int g, int64_t s0, int tid);
 };
@@ -1791,10 +1821,11 @@ __device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
 __device__ __forceinline__ void MmaStager::stage(unsigned char* in, const MmaArgs& A, int g, int64_t s0, int tid) {
     if (g != group) {
         const MmaGroup G = A.groups[g];
+        const int rows = G.one_snap ? 1 : G.n_runs;
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int r = (tid >> 4) + 32 * i;
-            off[i] = r < G.n_runs ? static_cast<int64_t>(A.runs[G.run0 + r].slot) * A.n_pad : -1;
+            off[i] = r < rows ? static_cast<int64_t>(A.runs[G.run0 + r].snap) * A.n_pad : -1;
         }
         group = g;
     }
@@ -1804,10 +1835,11 @@ __device__ __forceinline__ void MmaStager::stage(unsigned char* in, const MmaArg
     for (int i = 0; i < 2; ++i)
         if (off[i] >= 0)
             cp_async16(base + static_cast<uint32_t>(((tid >> 4) + 32 * i) * kMmaERowBytes + q * 16),
-                       A.e + off[i] + s0 + 2 * q);
-    if (tid < 40) {
+                       A.snap + off[i] + s0 + 2 * q);
+    if (tid < kMmaParams * 8) {
         const int a = tid >> 3, qq = tid & 7;
-        const int row = a == 0 ? P32_XH : a == 1 ? P32_YH : a == 2 ? P32_ZH : a == 3 ? P32_FH : P32_R2;
+        const int row = a == 0 ? P32_XH : a == 1 ? P32_XL : a == 2 ? P32_YH : a == 3 ? P32_YL : a == 4 ? P32_ZH
+                      : a == 5 ? P32_ZL : a == 6 ? P32_FH : a == 7 ? P32_FL : P32_R2;
         cp_async16(base + static_cast<uint32_t>(kMmaStageE + a * kMmaChunk * 4 + qq * 16),
                    A.p32 + static_cast<int64_t>(row) * A.n_pad + s0 + 4 * qq);
     }
@@ -1917,6 +1949,10 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
         for (int k = 0; k < 2 && k < n_it; ++k) stage_next(k);
         int gi = 0, ch = 0;
         MmaGroup G = n_it > 0 ? A.groups[0] : MmaGroup{};
+        // this thread's run of the E slices (run 4 warp + lane % 4 of the group)
+        const int my_r = 4 * warp + (lane & 3);
+        MmaRun my_run{};
+        if (n_it > 0 && my_r < G.n_runs) my_run = A.runs[G.run0 + my_r];
         for (int it = 0; it < n_it; ++it) {
             const int st = it & 1, buf = it % kMmaStaging;
             bool w = true;
@@ -1936,7 +1972,7 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
             const int live = static_cast<int>(min(static_cast<int64_t>(kMmaChunk), c_end - s0));
             unsigned char* stage = s_mma + st * kMmaStageBytes;
             const unsigned char* in = s_in + buf * kMmaStageInPad;
-            mma_fill_e(stage, in, G.n_runs, live, warp, lane);
+            mma_fill_e(stage, in, my_run, my_r < G.n_runs, G.one_snap != 0, A.used, live, warp, lane);
             mma_fill_z(stage, in, G, warp, lane);
             fence_proxy_async_smem();
             mbar_arrive(full(st));
@@ -1966,7 +2002,10 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
             tc_fence_before();
             mbar_arrive(acc_free(gi & 1));
             ch = 0;
-            if (++gi < A.n_groups) G = A.groups[gi];
+            if (++gi < A.n_groups) {
+                G = A.groups[gi];
+                if (my_r < G.n_runs) my_run = A.runs[G.run0 + my_r];
+            }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     }

@@ -119,6 +119,7 @@ struct koma_sequence {
     uint8_t* d_from_mma = nullptr;
     int32_t n_mma_groups = 0;
     int64_t n_mma_runs = 0;
+    int64_t n_mma_snaps = 0;  // rows of the snapshot buffer
 };
 
 namespace {
@@ -889,14 +890,17 @@ koma_status build_records(int64_t n_steps, const double* dt, const double* gx, c
 // Matrix-form readout plan. ADC records of at least two samples are bucketed
 // by their rotator (dK, dtau as FP32 bit patterns); a bucket of at least
 // kMmaMinRuns runs and kMmaMinSamples samples is taken by the tensor-core
-// readout: its records get kMmaFlag, E-buffer rows (slots) are numbered in
-// record order (the order the Bloch kernel meets the flagged records), and
-// its runs form groups of up to kMmaRuns in record order.
+// readout: its records get kMmaFlag and its runs form groups of up to
+// kMmaRuns in record order. Blocks (stretches between RF and PREC records,
+// where the state is constant) holding taken runs get one snapshot row each,
+// in record order; the first taken record of such a block also gets
+// kMmaSnapFlag (the Bloch kernel stores the snapshot there).
 struct MmaPlan {
     std::vector<koma::MmaGroup> groups;
     std::vector<koma::MmaRun> runs;
     std::vector<uint8_t> from;  // [n_adc]: 1 = sample taken by the matrix form
     int64_t n_samples = 0;
+    int64_t n_snaps = 0;
 };
 
 void plan_mma(std::vector<koma::Rec32>& r32, int64_t n_adc, MmaPlan& P) {
@@ -919,13 +923,26 @@ void plan_mma(std::vector<koma::Rec32>& r32, int64_t n_adc, MmaPlan& P) {
         }
     }
     if (chosen.empty()) return;
-    std::vector<int32_t> slot(r32.size(), -1);
+    // snapshot rows: one per block holding taken runs
+    std::vector<int32_t> snap(r32.size(), -1);
     int32_t next = 0;
-    for (size_t i = 0; i < r32.size(); ++i)
-        if (taken[i]) {
-            slot[i] = next++;
-            r32[i].count |= koma::kMmaFlag;
+    bool block_has = false;
+    for (size_t i = 0; i < r32.size(); ++i) {
+        koma::Rec32& R = r32[i];
+        if (R.type != koma::REC_ADC) {
+            block_has = false;  // RF or PREC: the state changes, a new block begins
+            continue;
         }
+        if (!taken[i]) continue;
+        R.count |= koma::kMmaFlag;
+        if (!block_has) {
+            R.count |= koma::kMmaSnapFlag;
+            ++next;
+            block_has = true;
+        }
+        snap[i] = next - 1;
+    }
+    P.n_snaps = next;
     P.from.assign(static_cast<size_t>(n_adc), 0);
     for (const std::vector<size_t>* v : chosen) {
         for (size_t g0 = 0; g0 < v->size(); g0 += koma::kMmaRuns) {
@@ -938,13 +955,22 @@ void plan_mma(std::vector<koma::Rec32>& r32, int64_t n_adc, MmaPlan& P) {
             G.dtau = H.a[11];
             G.run0 = static_cast<int32_t>(P.runs.size());
             G.n_runs = static_cast<int32_t>(g1 - g0);
+            G.one_snap = 1;
             for (size_t q = g0; q < g1; ++q) {
                 const koma::Rec32& R = r32[(*v)[q]];
                 koma::MmaRun run{};
                 run.k0 = R.k0;
                 run.len = R.count & koma::kCountMask;
-                run.slot = slot[(*v)[q]];
+                run.snap = snap[(*v)[q]];
+                for (int d = 0; d < 3; ++d) {
+                    run.kh[d] = R.a[2 * d];
+                    run.kl[d] = R.a[2 * d + 1];
+                }
+                run.th = R.a[6];
+                run.tl = R.a[7];
+                run.terms = (R.count >> koma::kTermShift) & 0xF;
                 G.max_len = std::max(G.max_len, run.len);
+                if (run.snap != snap[(*v)[g0]]) G.one_snap = 0;
                 P.n_samples += run.len;
                 P.runs.push_back(run);
                 std::fill(P.from.begin() + run.k0, P.from.begin() + run.k0 + run.len, 1);
@@ -1030,6 +1056,7 @@ extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, cons
             seq->d_from_mma = reinterpret_cast<uint8_t*>(base + b32 + b64 + bm + bg + br);
             seq->n_mma_groups = static_cast<int32_t>(mp.groups.size());
             seq->n_mma_runs = static_cast<int64_t>(mp.runs.size());
+            seq->n_mma_snaps = mp.n_snaps;
         }
         std::vector<char> host(total, 0);
         std::memcpy(host.data(), rb.r32.data(), b32);
@@ -1228,8 +1255,9 @@ uint64_t tune_key(const koma_phantom* ph, const koma_sequence* seq, bool items) 
            lg(seq->info.n_adc) << 26 | lg(seq->info.n_rf) << 34;
 }
 
-// Largest E buffer (8 bytes per spin and matrix-form run) the tensor-core
-// readout takes; beyond it the Bloch kernel samples every run itself.
+// Largest snapshot buffer (8 bytes per spin and block of matrix-form runs)
+// the tensor-core readout takes; beyond it the Bloch kernel samples every
+// run itself.
 constexpr size_t kMmaMaxEBytes = size_t{16} << 30;
 
 // ADC-run split for a launch whose spins fill few warps: CTAs sharing a
@@ -1396,8 +1424,8 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     const int rows = L.grid / split;  // one partial row per spin range
     size_t need = static_cast<size_t>(rows) * static_cast<size_t>(n_adc) * elem;
     // tensor-core readout of the sequence's matrix-form groups: scratch
-    // [Bloch rows | readout rows (grid_mma x n_adc float2) | E (n_mma_runs x n_pad float2)]
-    const size_t e_bytes = static_cast<size_t>(seq->n_mma_runs) * static_cast<size_t>(ph->n_pad) * sizeof(float2);
+    // [Bloch rows | readout rows (grid_mma x n_adc float2) | snapshots (n_mma_snaps x n_pad float2)]
+    const size_t e_bytes = static_cast<size_t>(seq->n_mma_snaps) * static_cast<size_t>(ph->n_pad) * sizeof(float2);
     const bool use_mma = !fp64 && !moving && ph->n_groups == 1 && seq->n_mma_groups > 0 && ctx->mma_enabled &&
                          e_bytes <= kMmaMaxEBytes;
     int grid_mma = 0;
@@ -1427,11 +1455,12 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     koma::MmaArgs M;
     if (use_mma) {
         char* base = static_cast<char*>(ctx->scratch);
-        A.mma_e = reinterpret_cast<float2*>(base + off_e);
+        A.mma_snap = reinterpret_cast<float2*>(base + off_e);
         M.p32 = ph->p32;
         M.n_pad = ph->n_pad;
         M.n = ph->n;
-        M.e = A.mma_e;
+        M.snap = A.mma_snap;
+        M.used = A.used;
         M.groups = seq->d_mma_groups;
         M.n_groups = seq->n_mma_groups;
         M.runs = seq->d_mma_runs;
