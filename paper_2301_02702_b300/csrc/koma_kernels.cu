@@ -255,6 +255,7 @@ struct Spins {
     int stride;
     float dt_cached;               // em1/em2 belong to this dt
     int rf_mode;                   // rotation path of the current RF run (uniform)
+    bool rf_grad;                  // the run's gradient reaches some spin (else theta_z = pi dt df)
     float key0, key1, key2, key3;  // zr/zi belong to this (dK, dtau)
     float kb0, kb1, kb2, kb3;      // zr2/zi2 belong to this one (the previous run's)
 
@@ -306,6 +307,7 @@ struct Spins {
         }
         dt_cached = -1.f;
         rf_mode = 0;
+        rf_grad = true;
         key0 = __int_as_float(0x7fc00000);  // NaN: no rotator yet
         key1 = key2 = key3 = 0.f;
         kb0 = key0;
@@ -379,6 +381,7 @@ struct Spins {
     // remainders below 3e-9), so no square root, division or sine is needed;
     // the same rotation and relaxation as rf_slots, on spin pairs in packed
     // f32x2 arithmetic (half the issued instructions).
+    template <bool GRAD>
     __device__ __forceinline__ void rf_pairs_small(float gx, float gy, float gz, float bx, float by, float b2,
                                                    float dt) {
         const float pdt = dt * 3.14159265358979323846f;
@@ -387,8 +390,12 @@ struct Spins {
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             const int s0 = 2 * p, s1 = 2 * p + 1;
-            const f32x2 X = pk(xh[s0], xh[s1]), Y = pk(yh[s0], yh[s1]), Z = pk(zh[s0], zh[s1]), F = pk(fh[s0], fh[s1]);
-            const f32x2 az = fma2(GX, X, fma2(GY, Y, fma2(GZ, Z, mul2(F, PDT))));
+            const f32x2 F = pk(fh[s0], fh[s1]);
+            f32x2 az = mul2(F, PDT);
+            if constexpr (GRAD) {
+                const f32x2 X = pk(xh[s0], xh[s1]), Y = pk(yh[s0], yh[s1]), Z = pk(zh[s0], zh[s1]);
+                az = fma2(GX, X, fma2(GY, Y, fma2(GZ, Z, az)));
+            }
             const f32x2 t2 = fma2(az, az, B2);
             f32x2 q = fma2(t2, pk(-2.75573192239858907e-6f, -2.75573192239858907e-6f),
                            pk(1.98412698412698413e-4f, 1.98412698412698413e-4f));
@@ -431,6 +438,7 @@ struct Spins {
                           (mgz == 0.f || ext[2] == 0.f) && ext[3] == 0.f;
         const float bound = mb + mgx * ext[0] + mgy * ext[1] + mgz * ext[2] + mdt * 3.14159265358979323846f * ext[3];
         rf_mode = same ? (mb <= 0.754f ? 3 : 2) : (bound <= 0.754f ? 1 : 0);
+        rf_grad = (mgx != 0.f && ext[0] != 0.f) || (mgy != 0.f && ext[1] != 0.f) || (mgz != 0.f && ext[2] != 0.f);
     }
 
     // RF record. The first record of a run of RF records carries the run's
@@ -456,7 +464,7 @@ struct Spins {
         if (rf_mode >= 2)
             rf_uniform(bx, by, b2, rf_mode == 3);
         else if (rf_mode == 1)
-            rf_pairs_small(gx, gy, gz, bx, by, b2, dt);
+            rf_grad ? rf_pairs_small<true>(gx, gy, gz, bx, by, b2, dt) : rf_pairs_small<false>(gx, gy, gz, bx, by, b2, dt);
         else
             rf_slots(gx, gy, gz, bx, by, b2, dt);
     }
