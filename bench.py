@@ -597,7 +597,8 @@ def run_ours(args, rank, world, local):
             koma.koma_sequence_free(s_)
             koma.koma_phantom_free(p_)
 
-        e2e_step()
+        for _ in range(max(3, args.warmup)):
+            e2e_step()
         n_e2e = max(1, min(args.steps, args.e2e_steps))
         barrier(world)
         t0 = time.perf_counter()
@@ -621,7 +622,8 @@ def run_ours(args, rank, world, local):
             koma.koma_sequence_free(hs2)
             koma.koma_phantom_free(hp2)
         host_sig = pinned(np.empty((ph.n_groups, seq.n_adc), dtype=np.complex128))
-        koma.koma_simulate_host(ctx2, ph_host, seq_host, koma.KOMA_FP32_SPLITPHASE, out=host_sig)  # warm
+        for _ in range(max(3, args.warmup)):  # warm-up calls, as for the device-timed steps
+            koma.koma_simulate_host(ctx2, ph_host, seq_host, koma.KOMA_FP32_SPLITPHASE, out=host_sig)
         n_e2e = max(1, min(args.steps, args.e2e_steps))
         barrier(world)
         t0 = time.perf_counter()
@@ -737,7 +739,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOAD_TEXT), default="epi512")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--cpu-target-s", type=float, default=15.0)
