@@ -155,3 +155,22 @@ def test_server_create_without_gpu_fails_cleanly(lib, cuda_available):
     with pytest.raises(koma.KomaError) as e:
         koma.koma_server_create(0)
     assert e.value.status == koma.KOMA_E_CUDA
+
+
+def test_plan_groups_readout_lines(lib):
+    """Matrix-form readout plan: runs sharing (dK, dtau) form groups of at
+    most 64 runs when a bucket has >= 8 runs and >= 1,024 samples; the two
+    readout directions of an EPI are two buckets."""
+    from paper_2301_02702_b300.workloads import epi
+    info = koma.koma_sequence_plan(epi(n_read=128, n_lines=128, fov=0.23, rf_steps=100))
+    assert (info["n_mma_groups"], info["n_mma_runs"], info["n_mma_samples"]) == (2, 128, 16384)
+    # lines longer than a run: 128 + 72 samples, 150 runs a direction -> 64 + 64 + 22
+    info = koma.koma_sequence_plan(epi(n_read=200, n_lines=150, fov=0.23, rf_steps=100))
+    assert (info["n_mma_groups"], info["n_mma_runs"], info["n_mma_samples"]) == (6, 300, 30000)
+    # thresholds: 8 runs of 128 samples a direction qualify, of 127 (1,016 samples) not;
+    # 7 runs a direction not
+    assert koma.koma_sequence_plan(epi(n_read=128, n_lines=16, fov=0.23, rf_steps=100))["n_mma_groups"] == 2
+    assert koma.koma_sequence_plan(epi(n_read=127, n_lines=16, fov=0.23, rf_steps=100))["n_mma_groups"] == 0
+    assert koma.koma_sequence_plan(epi(n_read=128, n_lines=14, fov=0.23, rf_steps=100))["n_mma_groups"] == 0
+    # unstructured sequences: none
+    assert koma.koma_sequence_plan(random_sequence(3000, seed=7))["n_mma_groups"] == 0
