@@ -223,6 +223,9 @@ __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
+// -a for both halves: the sign bits flipped by an integer operation (ALU
+// pipe, exact), so the FP32 pipe keeps its cycles for arithmetic
+__device__ __forceinline__ f32x2 neg2(f32x2 a) { return a ^ 0x8000000080000000ull; }
 __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
     f32x2 r;
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
@@ -386,7 +389,7 @@ struct Spins {
                                                    float dt) {
         const float pdt = dt * 3.14159265358979323846f;
         const f32x2 GX = pk(gx, gx), GY = pk(gy, gy), GZ = pk(gz, gz), PDT = pk(pdt, pdt), B2 = pk(b2, b2);
-        const f32x2 BX = pk(bx, bx), BY = pk(by, by), NBX = pk(-bx, -bx), NBY = pk(-by, -by);
+        const f32x2 BX = pk(bx, bx), BY = pk(by, by);
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             const int s0 = 2 * p, s1 = 2 * p + 1;
@@ -409,7 +412,7 @@ struct Spins {
             c = fma2(c, t2, pk(-0.5f, -0.5f));
             const f32x2 ch = fma2(c, t2, pk(1.0f, 1.0f));
             const f32x2 ux = mul2(BX, nsinc), uy = mul2(BY, nsinc), uz = mul2(az, nsinc);
-            const f32x2 nux = mul2(NBX, nsinc), nuy = mul2(NBY, nsinc), nuz = mul2(az, mul2(nsinc, pk(-1.f, -1.f)));
+            const f32x2 nux = neg2(ux), nuy = neg2(uy), nuz = neg2(uz);
             const f32x2 nq = fma2(ch, ch, fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))));
             const f32x2 c2 = fma2(pk(-2.f, -2.f), nq, pk(4.f, 4.f));
             const f32x2 MX = pk(mx[s0], mx[s1]), MY = pk(my[s0], my[s1]), MZ = pk(mz[s0], mz[s1]);
@@ -1307,7 +1310,7 @@ struct MSpins {
                         const f32x2 zr2 = fma2(qr[p], wr[p], mul2(qi[p], wn[p]));
                         qi[p] = fma2(qr[p], wi[p], mul2(qi[p], wr[p]));
                         qr[p] = zr2;
-                        qn[p] = mul2(qi[p], pk(-1.f, -1.f));
+                        qn[p] = neg2(qi[p]);
                     }
                 }
             }
