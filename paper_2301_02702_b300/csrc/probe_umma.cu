@@ -147,6 +147,69 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// The readout kernel's issue pattern: per 32-spin block, 4 K slices x 3
+// products (A hi B hi, A hi B lo, A lo B hi) from one of two 64 KB stages of
+// 16 distinct 4 KB slices, optionally with a commit to an mbarrier and a
+// tcgen05 fence after every block. Operand contents are whatever shared
+// memory holds (the rate does not depend on them).
+__global__ void __launch_bounds__(128, 1) umma_pattern_kernel(int blocks, int commit_each, int* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * 16 * kTileBytes);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 2 * 16 * kTileBytes + 64);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // bar[0]: the per-block commits (never waited on); bar[1]: the final commit
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar[0])), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar[1])), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    if (tid == 0) {
+        const uint32_t idesc = idesc_f16(kM, kN);
+        for (int b = 0; b < blocks; ++b) {
+            const uint32_t base = smem_u32(smem + (b & 1) * 16 * kTileBytes);
+            if (commit_each) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t ah = smem_desc(base + ks * kTileBytes), al = smem_desc(base + (4 + ks) * kTileBytes);
+                const uint64_t bh = smem_desc(base + (8 + ks) * kTileBytes), bl = smem_desc(base + (12 + ks) * kTileBytes);
+                const uint64_t ops[3][2] = {{ah, bh}, {ah, bl}, {al, bh}};
+                for (int q = 0; q < 3; ++q) {
+                    const uint32_t acc = (b > 0 || ks > 0 || q > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ops[q][0]), "l"(ops[q][1]), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+            }
+            if (commit_each && b + 1 < blocks)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&bar[0]))
+                             : "memory");
+        }
+        // completes when every MMA issued above has
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&bar[1]))
+                     : "memory");
+    }
+    const bool ok = __syncthreads_and(mbar_wait_bounded(smem_u32(&bar[1]), 0));
+    if (!ok && tid == 0) atomicOr(status, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
 }  // namespace
 
 #define CK(x)                                                                          \
@@ -220,5 +283,24 @@ int main() {
     const double flops = 148.0 * iters * 4 * 2.0 * kM * kN * 16;
     std::printf("rate: status %d, %d MMAs per CTA in %.3f ms: %.1f TFLOP/s\n", st, iters * 4, ms,
                 flops / (ms * 1e-3) / 1e12);
+    if (st != 0) return 3;
+
+    // the readout kernel's pattern: 1,344 blocks of 12 MMAs per CTA
+    CK(cudaFuncSetAttribute(umma_pattern_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            static_cast<int>(2 * 16 * kTileBytes + 256)));
+    for (int commit_each = 0; commit_each < 2; ++commit_each) {
+        const int blocks = 1344;
+        umma_pattern_kernel<<<148, 128, 2 * 16 * kTileBytes + 256>>>(64, commit_each, dst);
+        CK(cudaDeviceSynchronize());
+        CK(cudaEventRecord(e0));
+        umma_pattern_kernel<<<148, 128, 2 * 16 * kTileBytes + 256>>>(blocks, commit_each, dst);
+        CK(cudaEventRecord(e1));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        CK(cudaMemcpy(&st, dst, sizeof(int), cudaMemcpyDeviceToHost));
+        const double f = 148.0 * blocks * 12 * 2.0 * kM * kN * 16;
+        std::printf("pattern (2 stages x 16 slices, 3 products, commit %s): status %d, %.3f ms: %.1f TFLOP/s\n",
+                    commit_each ? "every block" : "at the end", st, ms, f / (ms * 1e-3) / 1e12);
+    }
     return st != 0 ? 3 : 0;
 }
