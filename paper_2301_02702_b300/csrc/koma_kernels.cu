@@ -789,33 +789,42 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
                 float er[S], ei[S];
                 sp.exact(R, true, A.p32, np, A.used, er, ei);
             } else if (type == REC_ADC) {
+                const bool own = !SPLIT || (t * kTile + r) % split == part;
+                if (A.mma_snap != nullptr && (R.count & kMmaFlag)) {
+                    // a run of the matrix-form readout: not sampled here and not
+                    // staged (its samples of this CTA's row are never read); the
+                    // first of its block stores the block's Mxy(t_ref)
+                    if (R.count & kMmaSnapFlag) {
+                        if (own) {
+                            float2* __restrict__ row = A.mma_snap + static_cast<int64_t>(mma_snap_row) * np;
+#pragma unroll
+                            for (int s = 0; s < S; ++s) {
+                                const int64_t j = sp.index(s);
+                                if (j < sp.end)
+                                    row[j] = make_float2(sp.mx[s] * A.mma_escale, sp.my[s] * A.mma_escale);
+                            }
+                        }
+                        ++mma_snap_row;
+                    }
+                    continue;
+                }
                 const int L = min(max(R.count & kCountMask, 1), kMaxAdcRun);
                 const int64_t k0 = R.k0;
-                if (k0 + L > red_base + kRed32) flush();
+                if (k0 + L > red_base + kRed32) {
+                    flush();
+                    // samples skipped since (matrix-form runs) are not this row's
+                    red_base = k0;
+                }
                 const int off = static_cast<int>(k0 - red_base);
-                const bool own = !SPLIT || (t * kTile + r) % split == part;
-                // a run of the matrix-form readout is not sampled here (its
-                // samples of this CTA's row are never read); the first of its
-                // block stores the block's Mxy(t_ref)
-                const bool mma = A.mma_snap != nullptr && (R.count & kMmaFlag);
-                const bool snap = mma && (R.count & kMmaSnapFlag);
                 if (SPLIT && warp == 0)
-                    for (int i = lane; i < L; i += 32) s_own[red_buf][off + i] = own && !mma;
-                if (own && snap) {
-                    float2* __restrict__ row = A.mma_snap + static_cast<int64_t>(mma_snap_row) * np;
-#pragma unroll
-                    for (int s = 0; s < S; ++s) {
-                        const int64_t j = sp.index(s);
-                        if (j < sp.end) row[j] = make_float2(sp.mx[s] * A.mma_escale, sp.my[s] * A.mma_escale);
-                    }
-                } else if (own && !mma) {
+                    for (int i = lane; i < L; i += 32) s_own[red_buf][off + i] = own;
+                if (own) {
                     float er[S], ei[S];
                     sp.exact(R, false, A.p32, np, A.used, er, ei);
                     sp.adc(R, L, er, ei, lane, [&](int i, float sr, float si) {
                         red_slot(red_buf, warp, off + i) = make_float2(sr, si);
                     });
                 }
-                mma_snap_row += snap ? 1 : 0;
                 red_end = k0 + L;
             }
         }
