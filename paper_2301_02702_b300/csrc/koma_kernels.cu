@@ -1930,17 +1930,14 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
             }
             tc_fence_after();
             if (lane == 0) {
-                // descriptors of the stage's 16 slices differ only in the
-                // start address field (16-byte units, slices 4 KB apart)
-                const uint64_t d0 = mma_smem_desc(smem_u32(s_mma + st * kMmaStageBytes));
+                const uint32_t base = smem_u32(s_mma + st * kMmaStageBytes);
                 const uint32_t d = tmem + static_cast<uint32_t>((gi & 1) * 128);
-                constexpr uint64_t kSlice = kMmaTileBytes >> 4;
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks) {
-                    const uint64_t ah = d0 + ks * kSlice;
-                    const uint64_t al = d0 + (4 + ks) * kSlice;
-                    const uint64_t bh = d0 + (8 + ks) * kSlice;
-                    const uint64_t bl = d0 + (12 + ks) * kSlice;
+                    const uint64_t ah = mma_smem_desc(base + ks * kMmaTileBytes);
+                    const uint64_t al = mma_smem_desc(base + (4 + ks) * kMmaTileBytes);
+                    const uint64_t bh = mma_smem_desc(base + (8 + ks) * kMmaTileBytes);
+                    const uint64_t bl = mma_smem_desc(base + (12 + ks) * kMmaTileBytes);
                     tc_mma_f16(d, ah, bh, (ch > 0 || ks > 0) ? 1u : 0u);
                     tc_mma_f16(d, ah, bl, 1u);
                     tc_mma_f16(d, al, bh, 1u);
