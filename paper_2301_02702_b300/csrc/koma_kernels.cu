@@ -30,7 +30,8 @@
 namespace koma {
 namespace {
 
-constexpr int kTile = 64;                 // records per TMA tile (4 KB of Rec32)
+constexpr int kTile = 64;                 // records per TMA tile (4 KB of Rec32; persistent and motion kernels)
+constexpr int kTile1 = 256;               // records per tile of the FP32 Bloch kernel (16 KB: fewer tile barriers)
 constexpr int kMaxBlock = 256;
 constexpr int kMaxWarps = kMaxBlock / 32;
 constexpr int kRed = 128;                 // samples per reduction buffer (FP64 kernel)
@@ -663,11 +664,11 @@ struct Spins {
 // Tile pipeline of the record stream: 64-record tiles brought into shared
 // memory by TMA bulk copies, double buffered; tile g of the CTA's lifetime
 // sits in buffer g & 1 and completes phase (g >> 1) & 1 of its mbarrier.
-template <class Bars>
-__device__ __forceinline__ void issue_tile(Rec32 (*s_rec)[kTile], const Bars& bar, const Rec32* grec,
+template <int T, class Bars>
+__device__ __forceinline__ void issue_tile(Rec32 (*s_rec)[T], const Bars& bar, const Rec32* grec,
                                            int64_t n_rec, int64_t t, uint64_t g) {
-    const int64_t nr = min(static_cast<int64_t>(kTile), n_rec - t * kTile);
-    tma_load_1d(smem_u32(&s_rec[g & 1][0]), grec + t * kTile, static_cast<uint32_t>(nr * sizeof(Rec32)),
+    const int64_t nr = min(static_cast<int64_t>(T), n_rec - t * T);
+    tma_load_1d(smem_u32(&s_rec[g & 1][0]), grec + t * T, static_cast<uint32_t>(nr * sizeof(Rec32)),
                 bar[g & 1]);
 }
 
@@ -686,7 +687,7 @@ __device__ __forceinline__ void issue_tile(Rec32 (*s_rec)[kTile], const Bars& ba
 // ---------------------------------------------------------------------------
 template <int S, bool SPLIT>
 __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_constant__ BlochArgs A) {
-    __shared__ __align__(128) Rec32 s_rec[2][kTile];
+    __shared__ __align__(128) Rec32 s_rec[2][kTile1];
     __shared__ __align__(8) uint64_t s_bar[2];
     // per-warp sample sums, two buffers: [buf][warp][kRed32] (dynamic)
     extern __shared__ __align__(16) float2 s_red_dyn[];
@@ -755,7 +756,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
 
     const uint32_t bar[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
     const Rec32* __restrict__ grec = static_cast<const Rec32*>(A.rec);
-    const int64_t n_tiles = (A.n_rec + kTile - 1) / kTile;
+    const int64_t n_tiles = (A.n_rec + kTile1 - 1) / kTile1;
     if (tid == 0) {
         mbar_init(bar[0], 1);
         mbar_init(bar[1], 1);
@@ -779,7 +780,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
             }
             return;
         }
-        const int nr = static_cast<int>(min(static_cast<int64_t>(kTile), A.n_rec - t * kTile));
+        const int nr = static_cast<int>(min(static_cast<int64_t>(kTile1), A.n_rec - t * kTile1));
         for (int r = 0; r < nr; ++r) {
             const Rec32& R = s_rec[b][r];
             const int type = R.type;
@@ -789,7 +790,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
                 float er[S], ei[S];
                 sp.exact(R, true, A.p32, np, A.used, er, ei);
             } else if (type == REC_ADC) {
-                const bool own = !SPLIT || (t * kTile + r) % split == part;
+                const bool own = !SPLIT || (t * kTile1 + r) % split == part;
                 if (A.mma_snap != nullptr && (R.count & kMmaFlag)) {
                     // a run of the matrix-form readout: not sampled here and not
                     // staged (its samples of this CTA's row are never read); the
