@@ -246,3 +246,21 @@ def test_stage_timing_splits_the_bloch_time(sim):
         koma.koma_set_mma(sim.ctx, True)
         koma.koma_sequence_free(hs)
         koma.koma_phantom_free(hp)
+
+
+def test_multi_shot_epi_groups_span_blocks(sim):
+    """Four EPI shots of 30-degree excitations: each readout direction's group
+    holds runs of four RF-separated blocks (four snapshot rows, magnetisation
+    carried from shot to shot)."""
+    one = epi(n_read=64, n_lines=16, fov=0.2, rf_steps=40, flip_deg=30.0)
+    seq = one.concat(one).concat(one).concat(one)
+    info = koma.koma_sequence_plan(seq)
+    assert info["n_mma_groups"] == 2 and info["n_mma_runs"] == 64
+    ph = head_like(777, 81, fov=0.2)
+    ph.t1 = np.full(ph.n, 0.3)
+    ref = oracle.simulate(ph, seq)
+    got, li = run(sim, ph, seq)
+    assert li["mma_grid"] >= 1
+    assert rel_err(got, ref) < TOL32
+    off, _ = run(sim, ph, seq, mma=False)
+    assert rel_err(got, off) < 2e-5
