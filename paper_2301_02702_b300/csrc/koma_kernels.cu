@@ -11,6 +11,9 @@
 // K4  bloch_batches_kernel  serving: batches of many simulations in one
 //                           persistent launch (spin ranges of each request).
 // K5  bloch_motion_kernel<S, SPLIT>  moving spins, x(t) = x + v t.
+// K6  readout_mma_kernel    ADC runs sharing their per-sample rotator, summed
+//                           as complex matrix products on the tensor cores
+//                           (tcgen05.mma, FP16 hi/lo operands, FP32 in TMEM).
 //
 // Method: KomaMRI.jl paper, Section "Physical and Mathematical Background"
 // (Bloch equation, operator splitting, spinor rotation in the excitation

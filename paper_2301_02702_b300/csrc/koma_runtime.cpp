@@ -3,8 +3,10 @@
 // Responsibilities: argument validation, conversion of the phantom to the
 // device layout, sequence preprocessing into step records (regime
 // classification, FP64 cumulative gradient moments since the last RF step,
-// uniform ADC runs), device-memory budget, launch configuration, and the
-// two kernel launches per simulation (Bloch kernel + fixed-order reduction).
+// uniform ADC runs, the matrix-form readout plan), device-memory budget,
+// launch configuration, and the kernel launches per simulation (Bloch kernel,
+// the tensor-core readout when the sequence has matrix-form groups, the
+// fixed-order reduction).
 #include <cuda_runtime.h>
 
 #include <algorithm>
