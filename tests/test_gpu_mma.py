@@ -59,6 +59,7 @@ def head_like(n, seed, fov=0.23):
     (200, 150, 517, 3),    # lines split into 128 + 72 samples; 64 + 64 + ... runs, a short last group
     (64, 40, 1, 4),        # one spin
     (40, 60, 33, 5),       # spins not a multiple of 32
+    (96, 130, 333, 6),     # 65 runs a direction: a last group of a single run
 ])
 def test_epi_readouts_match_oracle(sim, n_read, n_lines, n_spins, seed):
     seq = epi(n_read=n_read, n_lines=n_lines, fov=0.23, rf_steps=100)
@@ -264,3 +265,22 @@ def test_multi_shot_epi_groups_span_blocks(sim):
     assert rel_err(got, ref) < TOL32
     off, _ = run(sim, ph, seq, mma=False)
     assert rel_err(got, off) < 2e-5
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_readout_shapes(sim, seed):
+    """Random EPI shapes: line lengths from 8 to 300 samples (runs of up to
+    128, a short last run), 8 to 140 lines (groups of 64 runs and a short
+    last group, down to a single run), random spin counts."""
+    rng = np.random.default_rng(900 + seed)
+    n_read = int(rng.integers(8, 301))
+    n_lines = int(rng.integers(8, 141))
+    n_read = max(n_read, -(-2048 // n_lines))  # enough samples for a group
+    seq = epi(n_read=n_read, n_lines=n_lines, fov=0.2, rf_steps=int(rng.integers(1, 60)),
+              flip_deg=float(rng.uniform(10, 90)))
+    info = koma.koma_sequence_plan(seq)
+    ph = head_like(int(rng.integers(1, 700)), 1000 + seed, fov=0.2)
+    ref = oracle.simulate(ph, seq)
+    got, li = run(sim, ph, seq)
+    assert (li["mma_grid"] > 0) == (info["n_mma_groups"] > 0)
+    assert rel_err(got, ref) < TOL32, (n_read, n_lines, info)
