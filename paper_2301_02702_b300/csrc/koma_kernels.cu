@@ -2162,6 +2162,31 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const __grid_const
     }
 }
 
+// The same sum for launches whose groups hold few rows each (the grouped
+// work-item kernel: a few items per dictionary entry): one thread per
+// (group, sample) adds the group's rows in order (deterministic), so a block
+// covers 256 samples of one group instead of 32 samples with mostly idle
+// row lanes.
+template <typename P>
+__global__ void __launch_bounds__(256) reduce_rows_kernel(const __grid_constant__ ReduceArgs R) {
+    const int64_t chunks = (R.n_adc + 255) / 256;
+    const int64_t g = blockIdx.x / chunks;
+    const int64_t k = (blockIdx.x % chunks) * 256 + threadIdx.x;
+    if (k >= R.n_adc) return;
+    const int c_lo = R.group_cta ? R.group_cta[g] : 0;
+    const int c_hi = R.group_cta ? R.group_cta[g + 1] : R.grid;
+    const P* __restrict__ part = static_cast<const P*>(R.partial);
+    double re = 0.0, im = 0.0;
+#pragma unroll 4
+    for (int c = c_lo; c < c_hi; ++c) {
+        const P p = part[static_cast<int64_t>(c) * R.n_adc + k];
+        re += p.x;
+        im += p.y;
+    }
+    R.sig[2 * (g * R.n_adc + k)] = re;
+    R.sig[2 * (g * R.n_adc + k) + 1] = im;
+}
+
 size_t fp32_dyn_smem(int block) { return static_cast<size_t>(2 * (block / 32) * kRed32) * sizeof(float2); }
 
 template <int S>
@@ -2366,6 +2391,17 @@ int launch_readout_mma(const MmaArgs& a, int grid, void* stream) {
 
 int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream) {
     if (r.n_adc <= 0 || r.n_groups <= 0) return cudaSuccess;
+    if (r.from_mma == nullptr && r.grid <= 8 * r.n_groups) {
+        // few rows a group (<= 8 on average)
+        const int64_t blocks = (r.n_adc + 255) / 256 * r.n_groups;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (fp64_partials)
+            reduce_rows_kernel<double2><<<static_cast<unsigned>(blocks), 256, 0, st>>>(r);
+        else
+            reduce_rows_kernel<float2><<<static_cast<unsigned>(blocks), 256, 0, st>>>(r);
+        return cudaGetLastError();
+    }
     const int64_t chunks = (r.n_adc + 31) / 32;
     const int64_t blocks = chunks * r.n_groups;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
