@@ -74,8 +74,7 @@ struct MmaRun {
     int32_t snap;     // snapshot row of the run's block
     float kh[3], kl[3];  // K0 (turns/m) hi/lo, relative to the block's t_ref
     float th, tl;     // tau0 (s) hi/lo
-    int32_t terms;    // nonzero terms of K0, tau0 (bits 0..3: x, y, z, tau), as the record's
-    int32_t pad_[3];
+    int32_t pad_[4];
 };
 static_assert(sizeof(MmaRun) == 64, "MmaRun layout");
 

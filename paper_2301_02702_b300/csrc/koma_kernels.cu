@@ -1699,56 +1699,130 @@ __device__ __forceinline__ void split_half2(float a, float b, uint32_t& hi, uint
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
+// Packed helpers of the operand generation (two spins per f32x2)
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 bcast2(float v) { return pk(v, v); }
+// v - rint(v) for both halves (exact)
+__device__ __forceinline__ f32x2 frac2(f32x2 v) {
+    float a, b;
+    unpk(v, a, b);
+    return sub2(v, pk(rintf(a), rintf(b)));
+}
+// frac_product for two spins (a) and one factor (b, both halves equal):
+// the same operations as the scalar form, lane by lane
+__device__ __forceinline__ f32x2 frac_product2(f32x2 ah, f32x2 al, f32x2 bh, f32x2 bl) {
+    const f32x2 p = mul2(ah, bh);
+    const f32x2 e = fma2(ah, bh, neg2(p));
+    return add2(frac2(p), fma2(ah, bl, fma2(al, bh, e)));
+}
+// 2^x (PTX ex2.approx, subnormal results flushed to zero: the decays here
+// are factors in (0, 1] next to unit-scale values)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// two complex values (re, im: one spin per half) split into FP16 hi + lo
+// words, one word per spin: (re, im) with re in the low half
+__device__ __forceinline__ void split_cplx2(f32x2 re, f32x2 im, uint32_t (&hi)[2], uint32_t (&lo)[2]) {
+    float r0, r1, i0, i1;
+    unpk(re, r0, r1);
+    unpk(im, i0, i1);
+    const __half2 h0 = __floats2half2_rn(r0, i0), h1 = __floats2half2_rn(r1, i1);
+    const f32x2 lr = sub2(re, pk(__low2float(h0), __low2float(h1)));
+    const f32x2 li = sub2(im, pk(__high2float(h0), __high2float(h1)));
+    float a0, a1, b0, b1;
+    unpk(lr, a0, a1);
+    unpk(li, b0, b1);
+    const __half2 l0 = __floats2half2_rn(a0, b0), l1 = __floats2half2_rn(a1, b1);
+    hi[0] = *reinterpret_cast<const uint32_t*>(&h0);
+    hi[1] = *reinterpret_cast<const uint32_t*>(&h1);
+    lo[0] = *reinterpret_cast<const uint32_t*>(&l0);
+    lo[1] = *reinterpret_cast<const uint32_t*>(&l1);
+}
+
+// Constants of one run of the E slices, both halves equal (built once per
+// group): K0 hi/lo per axis, tau0 hi/lo, -tau0
+struct MmaRunPk {
+    f32x2 kh[3], kl[3], th, tl, nth;
+    __device__ __forceinline__ void set(const MmaRun& r) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            kh[d] = bcast2(r.kh[d]);
+            kl[d] = bcast2(r.kl[d]);
+        }
+        th = bcast2(r.th);
+        tl = bcast2(r.tl);
+        nth = bcast2(-r.th);
+    }
+};
+// Constants of one group's rotator, both halves equal: -dK, -dtau, dtau
+struct MmaGroupPk {
+    f32x2 ndk[3], ndtau, dtau;
+    __device__ __forceinline__ void set(const MmaGroup& g) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ndk[d] = bcast2(-g.dk[d]);
+        ndtau = bcast2(-g.dtau);
+        dtau = bcast2(g.dtau);
+    }
+};
+
 // A slices (E part) of a stage: thread = (run r, spin quad); it evaluates
 // E_s(r) = Mxy_s(t_ref) e^{-tau0/T2} e^{-i 2 pi (K0.x + df tau0)} for its 4
-// spins (the Bloch kernel's exact evaluation: hi/lo phase products, exact
-// reduction to a fractional turn, hardware sine) and writes rows 2r
-// (Re E, -Im E) and 2r + 1 (Im E, Re E), hi and lo. Runs past n_runs and
-// spins past the block's `live` ones give zero rows.
-__device__ __forceinline__ void mma_fill_e(unsigned char* stage, const unsigned char* in, const MmaRun& run,
-                                           bool run_live, bool one_snap, int used, int live, int warp, int lane) {
+// spins, two at a time (the Bloch kernel's exact evaluation: hi/lo phase
+// products, exact reduction to a fractional turn, hardware sine) and writes
+// rows 2r (Re E, -Im E) and 2r + 1 (Im E, Re E), hi and lo. Runs past n_runs
+// and spins past the block's `live` ones give zero rows. The x and y terms
+// are always formed (a zero factor gives a zero term), the z and
+// off-resonance terms only when some spin has them (kZ, kDF): no branches in
+// the phase chain.
+template <bool kZ, bool kDF>
+__device__ __forceinline__ void mma_fill_e(unsigned char* stage, const unsigned char* in, const MmaRunPk& run,
+                                           bool run_live, bool one_snap, int live, int warp, int lane) {
     const int r = 4 * warp + (lane & 3), q8 = lane >> 2;
     const int kap = q8 >> 1, kg = q8 & 1, sb = 8 * kap + 4 * kg;
-    float er[4] = {0.f, 0.f, 0.f, 0.f}, ei[4] = {0.f, 0.f, 0.f, 0.f};
+    constexpr int R = kMmaChunk / 2;  // pairs per staged parameter row
+    f32x2 er[2] = {0ull, 0ull}, nei[2] = {0ull, 0ull};
     if (run_live) {
-        const float* prm = reinterpret_cast<const float*>(in + kMmaStageE);
-        const float4 XH = *reinterpret_cast<const float4*>(prm + 0 * kMmaChunk + sb);
-        const float4 XL = *reinterpret_cast<const float4*>(prm + 1 * kMmaChunk + sb);
-        const float4 YH = *reinterpret_cast<const float4*>(prm + 2 * kMmaChunk + sb);
-        const float4 YL = *reinterpret_cast<const float4*>(prm + 3 * kMmaChunk + sb);
-        const float4 ZH = *reinterpret_cast<const float4*>(prm + 4 * kMmaChunk + sb);
-        const float4 ZL = *reinterpret_cast<const float4*>(prm + 5 * kMmaChunk + sb);
-        const float4 FH = *reinterpret_cast<const float4*>(prm + 6 * kMmaChunk + sb);
-        const float4 FL = *reinterpret_cast<const float4*>(prm + 7 * kMmaChunk + sb);
-        const float4 R2 = *reinterpret_cast<const float4*>(prm + 8 * kMmaChunk + sb);
+        const f32x2* prm = reinterpret_cast<const f32x2*>(in + kMmaStageE) + (sb >> 1);
         const float4* m4 = reinterpret_cast<const float4*>(in + (one_snap ? 0 : r) * kMmaERowBytes + sb * 8);
         const float4 ma = m4[0], mb = m4[1];
-        const float xh[4] = {XH.x, XH.y, XH.z, XH.w}, xl[4] = {XL.x, XL.y, XL.z, XL.w};
-        const float yh[4] = {YH.x, YH.y, YH.z, YH.w}, yl[4] = {YL.x, YL.y, YL.z, YL.w};
-        const float zh[4] = {ZH.x, ZH.y, ZH.z, ZH.w}, zl[4] = {ZL.x, ZL.y, ZL.z, ZL.w};
-        const float fh[4] = {FH.x, FH.y, FH.z, FH.w}, fl[4] = {FL.x, FL.y, FL.z, FL.w};
-        const float r2[4] = {R2.x, R2.y, R2.z, R2.w};
         const float mx[4] = {ma.x, ma.z, mb.x, mb.z}, my[4] = {ma.y, ma.w, mb.y, mb.w};
-        const int terms = run.terms & used;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float F = 0.f;
-            if (terms & 1) F += frac_product(xh[q], xl[q], run.kh[0], run.kl[0]);
-            if (terms & 2) F += frac_product(yh[q], yl[q], run.kh[1], run.kl[1]);
-            if (terms & 4) F += frac_product(zh[q], zl[q], run.kh[2], run.kl[2]);
-            if (terms & 8) F += frac_product(fh[q], fl[q], run.th, run.tl);
-            float sn = 0.f, cs = 1.f;
-            if (terms) __sincosf(-6.28318530717958647692f * (F - rintf(F)), &sn, &cs);
-            const float e2 = exp2f(-run.th * r2[q]);
-            const bool v = sb + q < live;
-            er[q] = v ? e2 * fmaf(mx[q], cs, -my[q] * sn) : 0.f;
-            ei[q] = v ? e2 * fmaf(mx[q], sn, my[q] * cs) : 0.f;
+        for (int h = 0; h < 2; ++h) {
+            const f32x2* q = prm + h;
+            f32x2 F = add2(frac_product2(q[0 * R], q[1 * R], run.kh[0], run.kl[0]),
+                           frac_product2(q[2 * R], q[3 * R], run.kh[1], run.kl[1]));
+            if (kZ) F = add2(F, frac_product2(q[4 * R], q[5 * R], run.kh[2], run.kl[2]));
+            if (kDF) F = add2(F, frac_product2(q[6 * R], q[7 * R], run.th, run.tl));
+            float a0, a1, d0, d1, s0, c0, s1, c1;
+            unpk(mul2(frac2(F), bcast2(-6.28318530717958647692f)), a0, a1);
+            __sincosf(a0, &s0, &c0);
+            __sincosf(a1, &s1, &c1);
+            unpk(mul2(run.nth, q[8 * R]), d0, d1);
+            const float e0 = ex2_approx(d0), e1 = ex2_approx(d1);
+            const int i0 = 2 * h, i1 = 2 * h + 1;
+            const bool v0 = sb + i0 < live, v1 = sb + i1 < live;
+            er[h] = pk(v0 ? e0 * fmaf(mx[i0], c0, -my[i0] * s0) : 0.f, v1 ? e1 * fmaf(mx[i1], c1, -my[i1] * s1) : 0.f);
+            nei[h] = pk(v0 ? -e0 * fmaf(mx[i0], s0, my[i0] * c0) : 0.f, v1 ? -e1 * fmaf(mx[i1], s1, my[i1] * c1) : 0.f);
         }
     }
     uint32_t hi[4], lo[4], hi2[4], lo2[4];
 #pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t a[2], b[2];
+        split_cplx2(er[h], nei[h], a, b);
+        hi[2 * h] = a[0];
+        hi[2 * h + 1] = a[1];
+        lo[2 * h] = b[0];
+        lo[2 * h + 1] = b[1];
+    }
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
-        split_half2(er[q], -ei[q], hi[q], lo[q]);
         // (Im E, Re E): the halves swapped, the new low half negated (exact)
         hi2[q] = __byte_perm(hi[q], 0u, 0x1032) ^ 0x8000u;
         lo2[q] = __byte_perm(lo[q], 0u, 0x1032) ^ 0x8000u;
@@ -1762,57 +1836,54 @@ __device__ __forceinline__ void mma_fill_e(unsigned char* stage, const unsigned 
 
 // B slices (rotator powers) of a stage: thread = (spin pair, j = l mod 8,
 // g = l div 32), warp w: K slice w & 3, g = w >> 2; lane: pair half, j, K
-// group. 2 spins x samples l = 32 g + 8 q + j, q < 4; a warp's 8-byte
-// stores of one q fill 256 contiguous bytes. Spins past the last one have
-// zero parameters (z = 1) and zero E.
-__device__ __forceinline__ void mma_fill_z(unsigned char* stage, const unsigned char* in, const MmaGroup& G, int warp,
-                                           int lane) {
+// group. 2 spins (one per f32x2 half) x samples l = 32 g + 8 q + j, q < 4;
+// a warp's 8-byte stores of one q fill 256 contiguous bytes. Spins past the
+// last one have zero parameters (z = 1) and zero E.
+__device__ __forceinline__ void mma_fill_z(unsigned char* stage, const unsigned char* in, const MmaGroupPk& G,
+                                           int warp, int lane) {
     const int kap = warp & 3, g = warp >> 2;
     const int half = lane & 1, j = (lane >> 1) & 7, kg = lane >> 4;
     const int s2 = 8 * kap + 4 * kg + 2 * half;
-    const float* prm = reinterpret_cast<const float*>(in + kMmaStageE);
-    const float2 X = *reinterpret_cast<const float2*>(prm + 0 * kMmaChunk + s2);
-    const float2 Y = *reinterpret_cast<const float2*>(prm + 2 * kMmaChunk + s2);
-    const float2 Z = *reinterpret_cast<const float2*>(prm + 4 * kMmaChunk + s2);
-    const float2 F = *reinterpret_cast<const float2*>(prm + 6 * kMmaChunk + s2);
-    const float2 R2 = *reinterpret_cast<const float2*>(prm + 8 * kMmaChunk + s2);
-    const float xs[2] = {X.x, X.y}, ys[2] = {Y.x, Y.y}, zs[2] = {Z.x, Z.y};
-    const float fs[2] = {F.x, F.y}, rs[2] = {R2.x, R2.y};
+    constexpr int R = kMmaChunk / 2;
+    const f32x2* prm = reinterpret_cast<const f32x2*>(in + kMmaStageE) + (s2 >> 1);
+    const f32x2 X = prm[0 * R], Y = prm[2 * R], Z = prm[4 * R], F = prm[6 * R], R2 = prm[8 * R];
+    // turns per sample, as the Bloch kernel's rotator (the negated constants
+    // give the same roundings as negating the sum)
+    const f32x2 th1 = fma2(G.ndk[0], X, fma2(G.ndk[1], Y, fma2(G.ndk[2], Z, mul2(F, G.ndtau))));
+    const f32x2 rate = mul2(G.dtau, R2);
     const float m0 = static_cast<float>(j + 32 * g);
-    float zr[2], zi[2], wr[2], wi[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        // turns per sample, as the Bloch kernel's rotator
-        const float th1 = -fmaf(G.dk[0], xs[q], fmaf(G.dk[1], ys[q], fmaf(G.dk[2], zs[q], fs[q] * G.dtau)));
-        const float rate = G.dtau * rs[q];
-        // one-shot phases (not accumulated beyond three products): the
-        // fractional turn exactly reduced, then the hardware sine
-        float sn, cs;
-        __sincosf(6.28318530717958647692f * frac_product(m0, 0.f, th1, 0.f), &sn, &cs);
-        const float mag = exp2f(-m0 * rate);
-        zr[q] = mag * cs;
-        zi[q] = mag * sn;
-        __sincosf(6.28318530717958647692f * frac_product(8.f, 0.f, th1, 0.f), &sn, &cs);
-        const float mag8 = exp2f(-8.f * rate);
-        wr[q] = mag8 * cs;
-        wi[q] = mag8 * sn;
-    }
+    // one-shot phases (not accumulated beyond three products): the
+    // fractional turn exactly reduced, then the hardware sine; 8 th1 is exact
+    const f32x2 M0 = bcast2(m0);
+    const f32x2 p = mul2(M0, th1);
+    const f32x2 ph0 = add2(frac2(p), fma2(M0, th1, neg2(p)));
+    const f32x2 ph8 = frac2(mul2(bcast2(8.f), th1));
+    const f32x2 two_pi = bcast2(6.28318530717958647692f);
+    float a0, a1, b0, b1, c0, s0, c1, s1, c8, s8, c9, s9;
+    unpk(mul2(two_pi, ph0), a0, a1);
+    unpk(mul2(two_pi, ph8), b0, b1);
+    __sincosf(a0, &s0, &c0);
+    __sincosf(a1, &s1, &c1);
+    __sincosf(b0, &s8, &c8);
+    __sincosf(b1, &s9, &c9);
+    float d0, d1, e0, e1;
+    unpk(mul2(bcast2(-m0), rate), d0, d1);
+    unpk(mul2(bcast2(-8.f), rate), e0, e1);
+    const f32x2 mag = pk(ex2_approx(d0), ex2_approx(d1)), mag8 = pk(ex2_approx(e0), ex2_approx(e1));
+    f32x2 zr = mul2(mag, pk(c0, c1)), zi = mul2(mag, pk(s0, s1));
+    const f32x2 wr = mul2(mag8, pk(c8, c9)), wi = mul2(mag8, pk(s8, s9)), nwi = neg2(wi);
 #pragma unroll
     for (int qq = 0; qq < 4; ++qq) {
         const int l = 32 * g + 8 * qq + j;
         uint32_t hi[2], lo[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) split_half2(zr[q], zi[q], hi[q], lo[q]);
+        split_cplx2(zr, zi, hi, lo);
         const uint32_t off = static_cast<uint32_t>((8 + kap) * kMmaTileBytes) + mma_word_off(l, kg) + 8u * half;
         *reinterpret_cast<uint2*>(stage + off) = make_uint2(hi[0], hi[1]);
         *reinterpret_cast<uint2*>(stage + 4 * kMmaTileBytes + off) = make_uint2(lo[0], lo[1]);
         if (qq < 3) {
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const float nr = fmaf(zr[q], wr[q], -zi[q] * wi[q]);
-                zi[q] = fmaf(zr[q], wi[q], zi[q] * wr[q]);
-                zr[q] = nr;
-            }
+            const f32x2 nr = fma2(zr, wr, mul2(zi, nwi));
+            zi = fma2(zr, wi, mul2(zi, wr));
+            zr = nr;
         }
     }
 }
@@ -1869,6 +1940,7 @@ __device__ __forceinline__ void MmaStager::stage(unsigned char* in, const MmaArg
     }
 }
 
+template <bool kZ, bool kDF>
 __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const __grid_constant__ MmaArgs A) {
     extern __shared__ __align__(1024) unsigned char s_mma[];
     unsigned char* s_in = s_mma + 2 * kMmaStageBytes;  // kMmaStaging staging buffers
@@ -1973,10 +2045,12 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
         for (int k = 0; k < 2 && k < n_it; ++k) stage_next(k);
         int gi = 0, ch = 0;
         MmaGroup G = n_it > 0 ? A.groups[0] : MmaGroup{};
+        MmaGroupPk gpk;
+        gpk.set(G);
         // this thread's run of the E slices (run 4 warp + lane % 4 of the group)
         const int my_r = 4 * warp + (lane & 3);
-        MmaRun my_run{};
-        if (n_it > 0 && my_r < G.n_runs) my_run = A.runs[G.run0 + my_r];
+        MmaRunPk my_run;
+        if (n_it > 0 && my_r < G.n_runs) my_run.set(A.runs[G.run0 + my_r]);
         for (int it = 0; it < n_it; ++it) {
             const int st = it & 1, buf = it % kMmaStaging;
             bool w = true;
@@ -1996,8 +2070,8 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
             const int live = static_cast<int>(min(static_cast<int64_t>(kMmaChunk), c_end - s0));
             unsigned char* stage = s_mma + st * kMmaStageBytes;
             const unsigned char* in = s_in + buf * kMmaStageInPad;
-            mma_fill_e(stage, in, my_run, my_r < G.n_runs, G.one_snap != 0, A.used, live, warp, lane);
-            mma_fill_z(stage, in, G, warp, lane);
+            mma_fill_e<kZ, kDF>(stage, in, my_run, my_r < G.n_runs, G.one_snap != 0, live, warp, lane);
+            mma_fill_z(stage, in, gpk, warp, lane);
             fence_proxy_async_smem();
             mbar_arrive(full(st));
             mbar_arrive(staging_free(buf));
@@ -2028,7 +2102,8 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
             ch = 0;
             if (++gi < A.n_groups) {
                 G = A.groups[gi];
-                if (my_r < G.n_runs) my_run = A.runs[G.run0 + my_r];
+                gpk.set(G);
+                if (my_r < G.n_runs) my_run.set(A.runs[G.run0 + my_r]);
             }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
@@ -2379,14 +2454,22 @@ int launch_bounded_wait_check(int* status, unsigned long long limit_ns, void* st
     return cudaGetLastError();
 }
 
-int launch_readout_mma(const MmaArgs& a, int grid, void* stream) {
-    const cudaError_t attr = cudaFuncSetAttribute(readout_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <bool kZ, bool kDF>
+static int launch_readout_mma_t(const MmaArgs& a, int grid, cudaStream_t st) {
+    const cudaError_t attr = cudaFuncSetAttribute(readout_mma_kernel<kZ, kDF>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   static_cast<int>(kMmaDynSmem));
     if (attr != cudaSuccess) return attr;
-    if (grid <= 0 || a.spins_per_cta % kMmaChunk != 0 || a.n_pad % 2 != 0) return cudaErrorInvalidValue;
-    readout_mma_kernel<<<static_cast<unsigned>(grid), kMmaThreads + 32, kMmaDynSmem,
-                         static_cast<cudaStream_t>(stream)>>>(a);
+    readout_mma_kernel<kZ, kDF><<<static_cast<unsigned>(grid), kMmaThreads + 32, kMmaDynSmem, st>>>(a);
     return cudaGetLastError();
+}
+
+int launch_readout_mma(const MmaArgs& a, int grid, void* stream) {
+    if (grid <= 0 || a.spins_per_cta % kMmaChunk != 0 || a.n_pad % 2 != 0) return cudaErrorInvalidValue;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool z = (a.used & 4) != 0, df = (a.used & 8) != 0;
+    if (z) return df ? launch_readout_mma_t<true, true>(a, grid, st) : launch_readout_mma_t<true, false>(a, grid, st);
+    return df ? launch_readout_mma_t<false, true>(a, grid, st) : launch_readout_mma_t<false, false>(a, grid, st);
 }
 
 int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream) {

@@ -970,7 +970,6 @@ void plan_mma(std::vector<koma::Rec32>& r32, int64_t n_adc, MmaPlan& P) {
                 }
                 run.th = R.a[6];
                 run.tl = R.a[7];
-                run.terms = (R.count >> koma::kTermShift) & 0xF;
                 G.max_len = std::max(G.max_len, run.len);
                 if (run.snap != snap[(*v)[g0]]) G.one_snap = 0;
                 P.n_samples += run.len;
