@@ -1946,13 +1946,15 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
     unsigned char* s_in = s_mma + 2 * kMmaStageBytes;  // kMmaStaging staging buffers
     // mbarriers: [0, 1] stage full (producer threads arrive), [2, 3] stage
     // empty (MMA commit), [4, 5] accumulator buffer read (producer threads),
-    // [6 .. 9] staging loaded (producer threads, on their copies' completion),
-    // [10 .. 13] staging read
-    // (producer threads); then the TMEM address, the abort flag, the commit count
+    // [6 .. 9] staging loaded (producer threads, on their copies' completion);
+    // then the TMEM address, the abort flag, the commit count. A staging
+    // buffer needs no "read" barrier: block i + 2 is staged into the buffer
+    // of block i - 2 only after the MMAs of block i - 2 completed, and those
+    // waited for every producer's fill of that block.
     uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_in + kMmaStaging * kMmaStageInPad);
-    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(s_bar + 14);
-    volatile int* s_abort = reinterpret_cast<volatile int*>(s_bar + 15);
-    volatile int* s_issued = reinterpret_cast<volatile int*>(s_bar + 16);
+    uint32_t* s_taddr = reinterpret_cast<uint32_t*>(s_bar + 10);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(s_bar + 11);
+    volatile int* s_issued = reinterpret_cast<volatile int*>(s_bar + 12);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t c_begin = static_cast<int64_t>(blockIdx.x) * A.spins_per_cta;
     const int64_t c_end = min(A.n, c_begin + A.spins_per_cta);
@@ -1963,7 +1965,6 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
     auto empty = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(2 + i); };
     auto acc_free = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(4 + i); };
     auto staged = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(6 + i); };
-    auto staging_free = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(10 + i); };
     constexpr int kProducerWarps = kMmaThreads / 32;
     constexpr int kMmaWarp = kProducerWarps;
 
@@ -1979,10 +1980,7 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
             mbar_init(empty(i), 1);
             mbar_init(acc_free(i), kMmaThreads);
         }
-        for (int i = 0; i < kMmaStaging; ++i) {
-            mbar_init(staged(i), kMmaThreads);
-            mbar_init(staging_free(i), kMmaThreads);
-        }
+        for (int i = 0; i < kMmaStaging; ++i) mbar_init(staged(i), kMmaThreads);
         *s_abort = 0;
         *s_issued = 0;
         fence_mbar_init();
@@ -2054,14 +2052,11 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
         for (int it = 0; it < n_it; ++it) {
             const int st = it & 1, buf = it % kMmaStaging;
             bool w = true;
-            if (it + 2 < n_it) {
-                // buffer (it + 2) % 4 last held block it - 2: every producer has read it
-                if (it + 2 >= kMmaStaging)
-                    w = mbar_wait_bounded(staging_free((it + 2) % kMmaStaging), ((it + 2 - kMmaStaging) / kMmaStaging) & 1);
-                if (w) stage_next(it + 2);
-            }
+            if (it >= 2) w = mbar_wait_bounded(empty(st), ((it - 2) >> 1) & 1);  // MMAs of block it - 2 done
+            // staging buffer (it + 2) % 4 last held block it - 2, read before
+            // those MMAs were issued
+            if (w && it + 2 < n_it) stage_next(it + 2);
             if (w) w = mbar_wait_bounded(staged(buf), (it / kMmaStaging) & 1);
-            if (w && it >= 2) w = mbar_wait_bounded(empty(st), ((it - 2) >> 1) & 1);  // MMAs of block it - 2 done
             if (!w || *s_abort) {
                 *s_abort = 1;
                 break;
@@ -2074,7 +2069,6 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
             mma_fill_z(stage, in, gpk, warp, lane);
             fence_proxy_async_smem();
             mbar_arrive(full(st));
-            mbar_arrive(staging_free(buf));
             if (++ch < n_chunks) continue;
             // epilogue of the group: its last commit covers all its MMAs
             if (!mbar_wait_bounded(empty(st), (it >> 1) & 1) || *s_abort) {
