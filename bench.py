@@ -15,6 +15,7 @@ spin-steps of all ranks divided by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -601,10 +602,14 @@ def run_ours(args, rank, world, local):
             e2e_step()
         n_e2e = max(1, min(args.steps, args.e2e_steps))
         barrier(world)
+        gc.collect()
+        gc.disable()  # no interpreter collection pause inside the timed calls
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             e2e_step()
-        t_e2e = reduce_max((time.perf_counter() - t0) / n_e2e, world)
+        t_e2e = time.perf_counter() - t0
+        gc.enable()
+        t_e2e = reduce_max(t_e2e / n_e2e, world)
         n_pad = max(32, (ph.n + 31) // 32 * 32)
         # raw FP64 phantom rows, velocity blocks (FP32 hi/lo + FP64), three record streams
         h2d = ph.n * 7 * 8 + n_pad * (6 * 4 + 3 * 8) + info["n_records"] * (64 + 128 + 128)
@@ -626,16 +631,24 @@ def run_ours(args, rank, world, local):
             koma.koma_simulate_host(ctx2, ph_host, seq_host, koma.KOMA_FP32_SPLITPHASE, out=host_sig)
         n_e2e = max(1, min(args.steps, args.e2e_steps))
         barrier(world)
+        gc.collect()
+        gc.disable()  # no interpreter collection pause inside the timed calls
+        calls = []
         t0 = time.perf_counter()
         for _ in range(n_e2e):
+            c0 = time.perf_counter()
             koma.koma_simulate_host(ctx2, ph_host, seq_host, koma.KOMA_FP32_SPLITPHASE, out=host_sig)
+            calls.append(time.perf_counter() - c0)
         t_e2e = (time.perf_counter() - t0) / n_e2e
+        gc.enable()
         t_e2e = reduce_max(t_e2e, world)
         sim2.close()
         # raw FP64 phantom rows (the FP32 block is built on the device), three record streams
         h2d = ph.n * 7 * 8 + info["n_records"] * (64 + 128 + 128)
         e2e = {"value": units * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(ph.n_groups * seq.n_adc * 16),
+               "ms_per_call": 1e3 * t_e2e, "ms_per_call_median": 1e3 * float(np.median(calls)),
+               "ms_per_call_max": 1e3 * max(calls), "calls": n_e2e,
                "path": "koma_simulate_host from pinned host arrays: validation + preprocessing + uploads + "
                        "simulate + signal copy-back into pinned memory"}
 
@@ -739,7 +752,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOAD_TEXT), default="epi512")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--cpu-target-s", type=float, default=15.0)

@@ -295,10 +295,12 @@ def ellipse_phantom(n: int = 512, fov: float = 0.256, n_ellipses: int = 10,
 
 def epi(n_read: int = 128, n_lines: int = 128, fov: float = 0.256, dwell: float = 4e-6,
         rf_dt: float = 4e-6, rf_steps: int = 500, flip_deg: float = 90.0,
-        blip_steps: int = 8) -> Sequence:
+        blip_steps: int = 8, kz: float = 0.0) -> Sequence:
     """Single-shot gradient-echo EPI: a Hann-sinc excitation, a prephaser to
     the k-space corner, then ``n_lines`` readouts of ``n_read`` samples with
-    alternating readout gradient and a triangular phase blip between lines."""
+    alternating readout gradient and a triangular phase blip between lines.
+    ``kz`` (1/m) adds a partition-encoding moment to the prephaser (one
+    partition of a 3-D EPI)."""
     dk = 1.0 / fov
     g_read = dk / (GAMMA_BAR * dwell)
     half = blip_steps // 2
@@ -306,7 +308,7 @@ def epi(n_read: int = 128, n_lines: int = 128, fov: float = 0.256, dwell: float 
     b.steps(rf_steps, rf_dt, b1=sinc_pulse(rf_steps, rf_dt, flip_deg))
     kx_pre = -(n_read // 2 + 1 + half / 2) * dk
     ky_pre = -(n_lines // 2) * dk
-    b.trapezoid([kx_pre, ky_pre, 0.0], 10, 30, dwell)
+    b.trapezoid([kx_pre, ky_pre, kz], 10, 30, dwell)
     b.steps(half, dwell, [g_read, 0, 0])
     g_blip = dk / (GAMMA_BAR * half * dwell)
     sign = 1.0

@@ -284,3 +284,24 @@ def test_random_readout_shapes(sim, seed):
     got, li = run(sim, ph, seq)
     assert (li["mma_grid"] > 0) == (info["n_mma_groups"] > 0)
     assert rel_err(got, ref) < TOL32, (n_read, n_lines, info)
+
+
+@pytest.mark.parametrize("dim,df_hz,kz", [
+    (2, 0.0, 0.0),      # x, y terms only
+    (2, 40.0, 0.0),     # + off-resonance
+    (3, 0.0, 37.0),     # + a z moment on every line (one partition of a 3-D EPI)
+    (3, 40.0, -23.0),   # all four terms
+])
+def test_phase_term_instances(sim, dim, df_hz, kz):
+    """The readout kernel is compiled per set of phase terms the phantom
+    needs (z, off-resonance); each instance against the oracle."""
+    seq = epi(n_read=64, n_lines=48, fov=0.2, rf_steps=40, kz=kz)
+    ph = random_spins(700, seed=61 + dim, extent=0.09, dim=dim, dw_std=2 * np.pi * df_hz)
+    if df_hz == 0.0:
+        ph.dw = np.zeros(ph.n)
+    ref = oracle.simulate(ph, seq)
+    got, li = run(sim, ph, seq)
+    assert li["mma_grid"] >= 1
+    assert rel_err(got, ref) < TOL32
+    off, _ = run(sim, ph, seq, mma=False)
+    assert rel_err(got, off) < 2e-5
