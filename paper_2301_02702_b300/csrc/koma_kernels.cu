@@ -262,6 +262,7 @@ struct Spins {
     int stride;
     float dt_cached;               // em1/em2 belong to this dt
     int rf_mode;                   // rotation path of the current RF run (uniform)
+    int rf_terms;                  // series length of the run on the series path (1, 2 or 4)
     bool rf_grad;                  // the run's gradient reaches some spin (else theta_z = pi dt df)
     float key0, key1, key2, key3;  // zr/zi belong to this (dK, dtau)
     float kb0, kb1, kb2, kb3;      // zr2/zi2 belong to this one (the previous run's)
@@ -314,6 +315,7 @@ struct Spins {
         }
         dt_cached = -1.f;
         rf_mode = 0;
+        rf_terms = 4;
         rf_grad = true;
         key0 = __int_as_float(0x7fc00000);  // NaN: no rotator yet
         key1 = key2 = key3 = 0.f;
@@ -384,11 +386,15 @@ struct Spins {
     }
 
     // Series path (|theta| <= 0.754 for every step and spin): cos t and
-    // sin(t)/t as even series in t^2 = theta.theta (terms to t^10 and t^8;
-    // remainders below 3e-9), so no square root, division or sine is needed;
-    // the same rotation and relaxation as rf_slots, on spin pairs in packed
-    // f32x2 arithmetic (half the issued instructions).
-    template <bool GRAD>
+    // sin(t)/t as even series in t^2 = theta.theta, so no square root,
+    // division or sine is needed; the same rotation and relaxation as
+    // rf_slots, on spin pairs in packed f32x2 arithmetic (half the issued
+    // instructions). NT = terms after the leading 1, chosen per run from its
+    // largest |theta| so the remainder stays below 3e-9 (under half an FP32
+    // ulp): NT = 4 (cos to t^10, sinc to t^8) up to 0.754, NT = 2 (t^4, t^4:
+    // remainders t^6/720 and t^6/5040) up to 0.1, NT = 1 (t^2, t^2: t^4/24
+    // and t^4/120) up to 0.015 — a short excitation pulse's steps.
+    template <bool GRAD, int NT>
     __device__ __forceinline__ void rf_pairs_small(float gx, float gy, float gz, float bx, float by, float b2,
                                                    float dt) {
         const float pdt = dt * 3.14159265358979323846f;
@@ -404,17 +410,29 @@ struct Spins {
                 az = fma2(GX, X, fma2(GY, Y, fma2(GZ, Z, az)));
             }
             const f32x2 t2 = fma2(az, az, B2);
-            f32x2 q = fma2(t2, pk(-2.75573192239858907e-6f, -2.75573192239858907e-6f),
-                           pk(1.98412698412698413e-4f, 1.98412698412698413e-4f));
-            q = fma2(q, t2, pk(-8.33333333333333333e-3f, -8.33333333333333333e-3f));
-            q = fma2(q, t2, pk(1.66666666666666667e-1f, 1.66666666666666667e-1f));
-            const f32x2 nsinc = fma2(q, t2, pk(-1.0f, -1.0f));
-            f32x2 c = fma2(t2, pk(-2.75573192239858907e-7f, -2.75573192239858907e-7f),
-                           pk(2.48015873015873016e-5f, 2.48015873015873016e-5f));
-            c = fma2(c, t2, pk(-1.38888888888888889e-3f, -1.38888888888888889e-3f));
-            c = fma2(c, t2, pk(4.16666666666666667e-2f, 4.16666666666666667e-2f));
-            c = fma2(c, t2, pk(-0.5f, -0.5f));
-            const f32x2 ch = fma2(c, t2, pk(1.0f, 1.0f));
+            f32x2 nsinc, ch;
+            if constexpr (NT == 1) {
+                nsinc = fma2(t2, pk(1.66666666666666667e-1f, 1.66666666666666667e-1f), pk(-1.0f, -1.0f));
+                ch = fma2(t2, pk(-0.5f, -0.5f), pk(1.0f, 1.0f));
+            } else if constexpr (NT == 2) {
+                const f32x2 q = fma2(t2, pk(-8.33333333333333333e-3f, -8.33333333333333333e-3f),
+                                     pk(1.66666666666666667e-1f, 1.66666666666666667e-1f));
+                nsinc = fma2(q, t2, pk(-1.0f, -1.0f));
+                const f32x2 c = fma2(t2, pk(4.16666666666666667e-2f, 4.16666666666666667e-2f), pk(-0.5f, -0.5f));
+                ch = fma2(c, t2, pk(1.0f, 1.0f));
+            } else {
+                f32x2 q = fma2(t2, pk(-2.75573192239858907e-6f, -2.75573192239858907e-6f),
+                               pk(1.98412698412698413e-4f, 1.98412698412698413e-4f));
+                q = fma2(q, t2, pk(-8.33333333333333333e-3f, -8.33333333333333333e-3f));
+                q = fma2(q, t2, pk(1.66666666666666667e-1f, 1.66666666666666667e-1f));
+                nsinc = fma2(q, t2, pk(-1.0f, -1.0f));
+                f32x2 c = fma2(t2, pk(-2.75573192239858907e-7f, -2.75573192239858907e-7f),
+                               pk(2.48015873015873016e-5f, 2.48015873015873016e-5f));
+                c = fma2(c, t2, pk(-1.38888888888888889e-3f, -1.38888888888888889e-3f));
+                c = fma2(c, t2, pk(4.16666666666666667e-2f, 4.16666666666666667e-2f));
+                c = fma2(c, t2, pk(-0.5f, -0.5f));
+                ch = fma2(c, t2, pk(1.0f, 1.0f));
+            }
             const f32x2 ux = mul2(BX, nsinc), uy = mul2(BY, nsinc), uz = mul2(az, nsinc);
             const f32x2 nux = neg2(ux), nuy = neg2(uy), nuz = neg2(uz);
             const f32x2 nq = fma2(ch, ch, fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))));
@@ -438,6 +456,18 @@ struct Spins {
         }
     }
 
+    __device__ __forceinline__ void rf_series(float gx, float gy, float gz, float bx, float by, float b2, float dt) {
+        if (rf_grad) {
+            if (rf_terms == 1) rf_pairs_small<true, 1>(gx, gy, gz, bx, by, b2, dt);
+            else if (rf_terms == 2) rf_pairs_small<true, 2>(gx, gy, gz, bx, by, b2, dt);
+            else rf_pairs_small<true, 4>(gx, gy, gz, bx, by, b2, dt);
+        } else {
+            if (rf_terms == 1) rf_pairs_small<false, 1>(gx, gy, gz, bx, by, b2, dt);
+            else if (rf_terms == 2) rf_pairs_small<false, 2>(gx, gy, gz, bx, by, b2, dt);
+            else rf_pairs_small<false, 4>(gx, gy, gz, bx, by, b2, dt);
+        }
+    }
+
     // Rotation path of an RF run from its header record (see rf()).
     __device__ __forceinline__ void set_mode(const Rec32& H, const float (&ext)[4]) {
         const float mb = H.a[7], mgx = H.a[8], mgy = H.a[9], mgz = H.a[10], mdt = H.a[11];
@@ -445,6 +475,7 @@ struct Spins {
                           (mgz == 0.f || ext[2] == 0.f) && ext[3] == 0.f;
         const float bound = mb + mgx * ext[0] + mgy * ext[1] + mgz * ext[2] + mdt * 3.14159265358979323846f * ext[3];
         rf_mode = same ? (mb <= 0.754f ? 3 : 2) : (bound <= 0.754f ? 1 : 0);
+        rf_terms = bound <= 0.015f ? 1 : bound <= 0.1f ? 2 : 4;
         rf_grad = (mgx != 0.f && ext[0] != 0.f) || (mgy != 0.f && ext[1] != 0.f) || (mgz != 0.f && ext[2] != 0.f);
     }
 
@@ -471,7 +502,7 @@ struct Spins {
         if (rf_mode >= 2)
             rf_uniform(bx, by, b2, rf_mode == 3);
         else if (rf_mode == 1)
-            rf_grad ? rf_pairs_small<true>(gx, gy, gz, bx, by, b2, dt) : rf_pairs_small<false>(gx, gy, gz, bx, by, b2, dt);
+            rf_series(gx, gy, gz, bx, by, b2, dt);
         else
             rf_slots(gx, gy, gz, bx, by, b2, dt);
     }
