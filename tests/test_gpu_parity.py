@@ -130,6 +130,26 @@ def test_edge_cases(sim):
     assert rel_err(gpu_signal(sim, ph3, seq5), ref) < TOL32
 
 
+
+@pytest.mark.parametrize("theta", [0.004, 0.0125, 0.0175, 0.06, 0.095, 0.12, 0.4, 0.74])
+@pytest.mark.parametrize("slice_grad", [False, True])
+def test_rf_series_lengths(sim, theta, slice_grad):
+    """The series path's length follows the RF run's largest half angle
+    (terms to t^2 up to 0.015, to t^4 up to 0.1, to t^10 up to 0.754): pulses
+    whose per-step half angle (plus the off-resonance and slice-gradient
+    share) falls in each band and next to its edges, spins off resonance so
+    the rotation axis is per spin."""
+    n, dt = 40, 10e-6
+    ph = random_spins(300, seed=77, extent=0.004, dim=3, dw_std=2 * np.pi * 40.0)
+    b = SequenceBuilder()
+    g_rf = [0.0, 0.0, 0.001] if slice_grad else None
+    b.steps(n, dt, g_rf, b1=hard_pulse_b1(2 * n * theta, n * dt, 0.4))
+    b.steps(4, dt, [0.0, 0.0, 0.0])
+    b.steps(64, dt, [0.02, 0.0, 0.0], adc=True)
+    seq = b.build()
+    ref = oracle.simulate(ph, seq)
+    assert rel_err(gpu_signal(sim, ph, seq), ref) < TOL32
+
 def test_grouped_phantom(sim):
     ph = random_spins(300, seed=21)
     offs = np.array([0, 7, 7, 100, 101, 240, 300])
