@@ -435,8 +435,14 @@ struct Spins {
             }
             const f32x2 ux = mul2(BX, nsinc), uy = mul2(BY, nsinc), uz = mul2(az, nsinc);
             const f32x2 nux = neg2(ux), nuy = neg2(uy), nuz = neg2(uz);
-            const f32x2 nq = fma2(ch, ch, fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))));
-            const f32x2 c2 = fma2(pk(-2.f, -2.f), nq, pk(4.f, 4.f));
+            // 2 / |q|^2 to first order; with the two-term series |q|^2 - 1 =
+            // -t^4/12 (below 5e-9 here) and the correction multiplies terms
+            // of order |theta|, so 2 itself is exact to FP32 rounding
+            f32x2 c2 = pk(2.f, 2.f);
+            if constexpr (NT > 1) {
+                const f32x2 nq = fma2(ch, ch, fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))));
+                c2 = fma2(pk(-2.f, -2.f), nq, pk(4.f, 4.f));
+            }
             const f32x2 MX = pk(mx[s0], mx[s1]), MY = pk(my[s0], my[s1]), MZ = pk(mz[s0], mz[s1]);
             const f32x2 px = fma2(uy, MZ, mul2(nuz, MY));
             const f32x2 py = fma2(uz, MX, mul2(nux, MZ));
