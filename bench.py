@@ -225,12 +225,19 @@ def cpu_sample_run(ph, seq, target_s: float, threads: int):
     """Time the oracle on a random spin sample sized for ~target_s seconds."""
     import oracle
     rng = np.random.default_rng(123)
-    n_cal = min(ph.n, max(4 * threads, 64))
-    idx = np.sort(rng.choice(ph.n, n_cal, replace=False))
-    t0 = time.perf_counter()
-    oracle.simulate(ph.subset(idx), seq, threads=threads)
-    t_cal = max(time.perf_counter() - t0, 1e-3)
-    n = int(min(ph.n, max(threads, n_cal * target_s / t_cal)))
+    # two calibration sizes: the slope is the per-spin cost, the rest the
+    # per-call cost (sequence conversion, threads), which a one-point
+    # estimate would spread over the spins
+    n_cal = min(ph.n, max(16 * threads, 64))
+    t = []
+    for n in (n_cal, 2 * n_cal):
+        idx = np.sort(rng.choice(ph.n, min(ph.n, n), replace=False))
+        t0 = time.perf_counter()
+        oracle.simulate(ph.subset(idx), seq, threads=threads)
+        t.append(time.perf_counter() - t0)
+    per_spin = max((t[1] - t[0]) / n_cal, t[1] / (2 * n_cal) * 0.25, 1e-9)
+    fixed = max(t[0] - per_spin * n_cal, 0.0)
+    n = int(min(ph.n, max(threads, (target_s - fixed) / per_spin)))
     idx = np.sort(rng.choice(ph.n, n, replace=False))
     return idx
 
