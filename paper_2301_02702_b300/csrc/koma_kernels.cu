@@ -1932,13 +1932,17 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // the block's group (thread t copies 16 bytes of rows t / 16 and t / 16 + 32:
 // the rows of the group's runs, or row 0 alone when they share one) and the
 // block's spin parameters (threads 0..71). Spins past the last one are copied
-// as they are (inside the padded rows) and read as zero. The group's row
-// offsets are cached per thread.
+// as they are (inside the padded rows) and read as zero. Each thread keeps its
+// source rows (at spin 0) and destinations, set once per group, so a block
+// costs it one 64-bit add and one cp.async per copy.
 struct MmaStager {
     int group = -1;
-    int64_t off[2] = {-1, -1};  // element offset of the thread's two snapshot rows (snap x n_pad), -1: none
+    const float2* row[2] = {nullptr, nullptr};  // this thread's snapshot rows at spin 0 (+ its 16 bytes)
+    bool has_row[2] = {false, false};
+    const float* prm = nullptr;                 // its parameter row at spin 0 (+ its 16 bytes), threads < 72
+    uint32_t dst_row = 0, dst_prm = 0;          // offsets in a staging buffer
 
-    __device__ __forceinline__ void stage(unsigned char* in, const MmaArgs& A, int g, int64_t s0, int tid);
+    __device__ __forceinline__ void stage(uint32_t buf, const MmaArgs& A, int g, int64_t s0, int tid);
 };
 
 // 16-byte global -> shared copy (cp.async, L2 only), and the arrival on
@@ -1950,31 +1954,30 @@ __device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void MmaStager::stage(unsigned char* in, const MmaArgs& A, int g, int64_t s0, int tid) {
+__device__ __forceinline__ void MmaStager::stage(uint32_t buf, const MmaArgs& A, int g, int64_t s0, int tid) {
     if (g != group) {
         const MmaGroup G = A.groups[g];
         const int rows = G.one_snap ? 1 : G.n_runs;
+        const int q = tid & 15;
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int r = (tid >> 4) + 32 * i;
-            off[i] = r < rows ? static_cast<int64_t>(A.runs[G.run0 + r].snap) * A.n_pad : -1;
+            has_row[i] = r < rows;
+            row[i] = has_row[i] ? A.snap + static_cast<int64_t>(A.runs[G.run0 + r].snap) * A.n_pad + 2 * q : nullptr;
+        }
+        dst_row = static_cast<uint32_t>((tid >> 4) * kMmaERowBytes + q * 16);
+        if (group < 0 && tid < kMmaParams * 8) {
+            const int a = tid >> 3, qq = tid & 7;
+            const int prow = a == 0 ? P32_XH : a == 1 ? P32_XL : a == 2 ? P32_YH : a == 3 ? P32_YL : a == 4 ? P32_ZH
+                           : a == 5 ? P32_ZL : a == 6 ? P32_FH : a == 7 ? P32_FL : P32_R2;
+            prm = A.p32 + static_cast<int64_t>(prow) * A.n_pad + 4 * qq;
+            dst_prm = static_cast<uint32_t>(kMmaStageE + a * kMmaChunk * 4 + qq * 16);
         }
         group = g;
     }
-    const uint32_t base = smem_u32(in);
-    const int q = tid & 15;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-        if (off[i] >= 0)
-            cp_async16(base + static_cast<uint32_t>(((tid >> 4) + 32 * i) * kMmaERowBytes + q * 16),
-                       A.snap + off[i] + s0 + 2 * q);
-    if (tid < kMmaParams * 8) {
-        const int a = tid >> 3, qq = tid & 7;
-        const int row = a == 0 ? P32_XH : a == 1 ? P32_XL : a == 2 ? P32_YH : a == 3 ? P32_YL : a == 4 ? P32_ZH
-                      : a == 5 ? P32_ZL : a == 6 ? P32_FH : a == 7 ? P32_FL : P32_R2;
-        cp_async16(base + static_cast<uint32_t>(kMmaStageE + a * kMmaChunk * 4 + qq * 16),
-                   A.p32 + static_cast<int64_t>(row) * A.n_pad + s0 + 4 * qq);
-    }
+    if (has_row[0]) cp_async16(buf + dst_row, row[0] + s0);
+    if (has_row[1]) cp_async16(buf + dst_row + 32 * kMmaERowBytes, row[1] + s0);
+    if (prm != nullptr) cp_async16(buf + dst_prm, prm + s0);
 }
 
 template <bool kZ, bool kDF>
@@ -2069,8 +2072,8 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
         MmaStager pf;
         int pg = 0, pc = 0;  // (group, block) of the next block to stage
         auto stage_next = [&](int k) {
-            pf.stage(s_in + (k % kMmaStaging) * kMmaStageInPad, A, pg, c_begin + static_cast<int64_t>(pc) * kMmaChunk,
-                     tid);
+            pf.stage(smem_u32(s_in + (k % kMmaStaging) * kMmaStageInPad), A, pg,
+                     c_begin + static_cast<int64_t>(pc) * kMmaChunk, tid);
             cp_async_arrive(staged(k % kMmaStaging));
             if (++pc == n_chunks) {
                 pc = 0;
