@@ -1674,7 +1674,9 @@ __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_cons
 // 256 B apart. z_s^l comes from z^(j + 32 g) and z^8 (direct, with an exact
 // phase reduction) and three complex products: l = 32 g + 8 q + j.
 // ---------------------------------------------------------------------------
-constexpr int kMmaThreads = 512;
+constexpr int kMmaThreads = 512;                    // E-slice producer threads (16 warps)
+constexpr int kMmaZThreads = 256;                   // B-slice producer threads (8 warps)
+constexpr int kMmaCtaThreads = kMmaThreads + kMmaZThreads + 32;  // + the MMA warp
 constexpr int kMmaChunk = 32;                       // spins per block
 constexpr int kMmaTileBytes = 128 * 16 * 2;         // one K = 16 slice of a 128-row FP16 operand
 constexpr int kMmaStageBytes = 16 * kMmaTileBytes;  // A hi, A lo, B hi, B lo x 4 slices (64 KB)
@@ -1871,14 +1873,16 @@ __device__ __forceinline__ void mma_fill_e(unsigned char* stage, const unsigned 
     *reinterpret_cast<uint4*>(stage + 4 * kMmaTileBytes + off + 16) = make_uint4(lo2[0], lo2[1], lo2[2], lo2[3]);
 }
 
-// B slices (rotator powers) of a stage: thread = (spin pair, j = l mod 8,
-// g = l div 32), warp w: K slice w & 3, g = w >> 2; lane: pair half, j, K
-// group. 2 spins (one per f32x2 half) x samples l = 32 g + 8 q + j, q < 4;
-// a warp's 8-byte stores of one q fill 256 contiguous bytes. Spins past the
-// last one have zero parameters (z = 1) and zero E.
+// B slices (rotator powers) of a stage, by the 8 B-slice warps: thread =
+// (spin pair, j = l mod 8, g = l div 64), warp v: K slice v & 3, g = v >> 2;
+// lane: pair half, j, K group. 2 spins (one per f32x2 half) x samples
+// l = 64 g + 8 q + j, q < 8; a warp's 8-byte stores of one q fill 256
+// contiguous bytes. Spins past the last one have zero parameters (z = 1) and
+// zero E.
 __device__ __forceinline__ void mma_fill_z(unsigned char* stage, const unsigned char* in, const MmaGroupPk& G,
-                                           int warp, int lane) {
-    const int kap = warp & 3, g = warp >> 2;
+                                           int v, int lane) {
+    constexpr int NQ = 8;
+    const int kap = v & 3, g = v >> 2;
     const int half = lane & 1, j = (lane >> 1) & 7, kg = lane >> 4;
     const int s2 = 8 * kap + 4 * kg + 2 * half;
     constexpr int R = kMmaChunk / 2;
@@ -1888,7 +1892,7 @@ __device__ __forceinline__ void mma_fill_z(unsigned char* stage, const unsigned 
     // give the same roundings as negating the sum)
     const f32x2 th1 = fma2(G.ndk[0], X, fma2(G.ndk[1], Y, fma2(G.ndk[2], Z, mul2(F, G.ndtau))));
     const f32x2 rate = mul2(G.dtau, R2);
-    const float m0 = static_cast<float>(j + 32 * g);
+    const float m0 = static_cast<float>(j + 8 * NQ * g);
     // one-shot phases (not accumulated beyond three products): the
     // fractional turn exactly reduced, then the hardware sine; 8 th1 is exact
     const f32x2 M0 = bcast2(m0);
@@ -1910,14 +1914,14 @@ __device__ __forceinline__ void mma_fill_z(unsigned char* stage, const unsigned 
     f32x2 zr = mul2(mag, pk(c0, c1)), zi = mul2(mag, pk(s0, s1));
     const f32x2 wr = mul2(mag8, pk(c8, c9)), wi = mul2(mag8, pk(s8, s9)), nwi = neg2(wi);
 #pragma unroll
-    for (int qq = 0; qq < 4; ++qq) {
-        const int l = 32 * g + 8 * qq + j;
+    for (int qq = 0; qq < NQ; ++qq) {
+        const int l = 8 * NQ * g + 8 * qq + j;
         uint32_t hi[2], lo[2];
         split_cplx2(zr, zi, hi, lo);
         const uint32_t off = static_cast<uint32_t>((8 + kap) * kMmaTileBytes) + mma_word_off(l, kg) + 8u * half;
         *reinterpret_cast<uint2*>(stage + off) = make_uint2(hi[0], hi[1]);
         *reinterpret_cast<uint2*>(stage + 4 * kMmaTileBytes + off) = make_uint2(lo[0], lo[1]);
-        if (qq < 3) {
+        if (qq < NQ - 1) {
             const f32x2 nr = fma2(zr, wr, mul2(zi, nwi));
             zi = fma2(zr, wi, mul2(zi, wr));
             zr = nr;
@@ -1981,7 +1985,7 @@ __device__ __forceinline__ void MmaStager::stage(uint32_t buf, const MmaArgs& A,
 }
 
 template <bool kZ, bool kDF>
-__global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const __grid_constant__ MmaArgs A) {
+__global__ void __launch_bounds__(kMmaCtaThreads, 1) readout_mma_kernel(const __grid_constant__ MmaArgs A) {
     extern __shared__ __align__(1024) unsigned char s_mma[];
     unsigned char* s_in = s_mma + 2 * kMmaStageBytes;  // kMmaStaging staging buffers
     // mbarriers: [0, 1] stage full (producer threads arrive), [2, 3] stage
@@ -2005,8 +2009,8 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
     auto empty = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(2 + i); };
     auto acc_free = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(4 + i); };
     auto staged = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(6 + i); };
-    constexpr int kProducerWarps = kMmaThreads / 32;
-    constexpr int kMmaWarp = kProducerWarps;
+    constexpr int kEWarps = kMmaThreads / 32;
+    constexpr int kMmaWarp = (kMmaThreads + kMmaZThreads) / 32;
 
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_taddr)),
@@ -2016,7 +2020,7 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
     }
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
-            mbar_init(full(i), kMmaThreads);
+            mbar_init(full(i), kMmaThreads + kMmaZThreads);
             mbar_init(empty(i), 1);
             mbar_init(acc_free(i), kMmaThreads);
         }
@@ -2065,9 +2069,33 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
                 ++gi;
             }
         }
+    } else if (warp >= kEWarps) {
+        // ---- B-slice producers: the rotator powers of each block once its
+        // stage is free and its staging has landed
+        const int v = warp - kEWarps;
+        int gi = 0, ch = 0;
+        MmaGroupPk gpk;
+        if (n_it > 0) gpk.set(A.groups[0]);
+        for (int it = 0; it < n_it; ++it) {
+            const int st = it & 1, buf = it % kMmaStaging;
+            bool w = true;
+            if (it >= 2) w = mbar_wait_bounded(empty(st), ((it - 2) >> 1) & 1);
+            if (w) w = mbar_wait_bounded(staged(buf), (it / kMmaStaging) & 1);
+            if (!w || *s_abort) {
+                *s_abort = 1;
+                break;
+            }
+            mma_fill_z(s_mma + st * kMmaStageBytes, s_in + buf * kMmaStageInPad, gpk, v, lane);
+            fence_proxy_async_smem();
+            mbar_arrive(full(st));
+            if (++ch == n_chunks) {
+                ch = 0;
+                if (++gi < A.n_groups) gpk.set(A.groups[gi]);
+            }
+        }
     } else {
-        // ---- producers: staging two blocks ahead, operand slices from the
-        // staging, each group's epilogue
+        // ---- E-slice producers: staging two blocks ahead, the A slices from
+        // the staging, each group's epilogue
         float* __restrict__ out = reinterpret_cast<float*>(A.partial + static_cast<int64_t>(blockIdx.x) * A.n_adc);
         MmaStager pf;
         int pg = 0, pc = 0;  // (group, block) of the next block to stage
@@ -2083,8 +2111,6 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
         for (int k = 0; k < 2 && k < n_it; ++k) stage_next(k);
         int gi = 0, ch = 0;
         MmaGroup G = n_it > 0 ? A.groups[0] : MmaGroup{};
-        MmaGroupPk gpk;
-        gpk.set(G);
         // this thread's run of the E slices (run 4 warp + lane % 4 of the group)
         const int my_r = 4 * warp + (lane & 3);
         MmaRunPk my_run;
@@ -2106,7 +2132,6 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
             unsigned char* stage = s_mma + st * kMmaStageBytes;
             const unsigned char* in = s_in + buf * kMmaStageInPad;
             mma_fill_e<kZ, kDF>(stage, in, my_run, my_r < G.n_runs, G.one_snap != 0, live, warp, lane);
-            mma_fill_z(stage, in, gpk, warp, lane);
             fence_proxy_async_smem();
             mbar_arrive(full(st));
             if (++ch < n_chunks) continue;
@@ -2136,7 +2161,6 @@ __global__ void __launch_bounds__(kMmaThreads + 32, 1) readout_mma_kernel(const 
             ch = 0;
             if (++gi < A.n_groups) {
                 G = A.groups[gi];
-                gpk.set(G);
                 if (my_r < G.n_runs) my_run.set(A.runs[G.run0 + my_r]);
             }
         }
@@ -2494,7 +2518,7 @@ static int launch_readout_mma_t(const MmaArgs& a, int grid, cudaStream_t st) {
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   static_cast<int>(kMmaDynSmem));
     if (attr != cudaSuccess) return attr;
-    readout_mma_kernel<kZ, kDF><<<static_cast<unsigned>(grid), kMmaThreads + 32, kMmaDynSmem, st>>>(a);
+    readout_mma_kernel<kZ, kDF><<<static_cast<unsigned>(grid), kMmaCtaThreads, kMmaDynSmem, st>>>(a);
     return cudaGetLastError();
 }
 
