@@ -5,7 +5,7 @@
 //                           spin range (SPLIT: several CTAs per range divide
 //                           its ADC runs).
 // K1d bloch_fp64_kernel     the same walk in FP64 (KOMA_FP64).
-// K2  reduce_partials<P>    fixed-order FP64 sum of the per-CTA partials.
+// K2  reduce_partials<P>    fixed-order sum of the per-CTA partials (FP32 rows by TwoSum).
 // K3  bloch_items_kernel<S> grouped phantoms: one warp per work item of one
 //                           group, persistent CTAs, per-item partial rows.
 // K4  bloch_batches_kernel  serving: batches of many simulations in one
@@ -2256,10 +2256,54 @@ __global__ void bounded_wait_check_kernel(int* status, unsigned long long limit_
 }
 
 // ---------------------------------------------------------------------------
-// K2: sig[g][k] = sum over the CTAs c of group g of partial[c][k], in FP64,
-// in a fixed order (deterministic; threadIdx.y strides the CTAs, the eight
-// strided sums are then added in y order).
+// K2: sig[g][k] = sum over the CTAs c of group g of partial[c][k] in a fixed
+// order (deterministic; threadIdx.y strides the CTAs, the eight strided sums
+// are then added in y order in FP64). FP32 rows are summed with an error-free
+// transformation per addition (Knuth's TwoSum: s + x = t + e exactly, t the
+// rounded sum), the errors e collected in a second FP32 accumulator and the
+// two joined in FP64: the result is the exact sum up to that accumulator's
+// own rounding, about n 2^-48 of the sum of magnitudes for n rows — as close
+// as FP64 additions — at FP32 speed: the part's FP64 unit runs at 1/64 of
+// the FP32 rate, and plain FP64 additions bounded this kernel (epi512 0.029
+// -> 0.010 ms). FP64 rows are added in FP64.
 // ---------------------------------------------------------------------------
+struct TwoSumAcc {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        const float z = t - s;
+        c += (s - (t - z)) + (x - z);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return static_cast<double>(s) + static_cast<double>(c); }
+};
+
+// rows c_lo, c_lo + c_step, ... < c_hi of column k, in that order
+__device__ __forceinline__ void strided_sum(const float2* __restrict__ part, int64_t n_adc, int64_t k, int c_lo,
+                                            int c_hi, int c_step, double& re, double& im) {
+    TwoSumAcc a, b;
+#pragma unroll 4
+    for (int c = c_lo; c < c_hi; c += c_step) {
+        const float2 p = part[static_cast<int64_t>(c) * n_adc + k];
+        a.add(p.x);
+        b.add(p.y);
+    }
+    re = a.value();
+    im = b.value();
+}
+__device__ __forceinline__ void strided_sum(const double2* __restrict__ part, int64_t n_adc, int64_t k, int c_lo,
+                                            int c_hi, int c_step, double& re, double& im) {
+    double x = 0.0, y = 0.0;
+#pragma unroll 4
+    for (int c = c_lo; c < c_hi; c += c_step) {
+        const double2 p = part[static_cast<int64_t>(c) * n_adc + k];
+        x += p.x;
+        y += p.y;
+    }
+    re = x;
+    im = y;
+}
+
 template <typename P>
 __global__ void __launch_bounds__(256) reduce_partials_kernel(const __grid_constant__ ReduceArgs R) {
     __shared__ double s_re[8][32];
@@ -2273,13 +2317,7 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const __grid_const
     const int c_hi = mm ? R.grid_mma : (R.group_cta ? R.group_cta[g + 1] : R.grid);
     const P* __restrict__ part = static_cast<const P*>(mm ? R.partial_mma : R.partial);
     double re = 0.0, im = 0.0;
-    if (k < R.n_adc) {
-        for (int c = c_lo + static_cast<int>(threadIdx.y); c < c_hi; c += 8) {
-            const P p = part[static_cast<int64_t>(c) * R.n_adc + k];
-            re += p.x;
-            im += p.y;
-        }
-    }
+    if (k < R.n_adc) strided_sum(part, R.n_adc, k, c_lo + static_cast<int>(threadIdx.y), c_hi, 8, re, im);
     s_re[threadIdx.y][threadIdx.x] = re;
     s_im[threadIdx.y][threadIdx.x] = im;
     __syncthreads();
@@ -2310,12 +2348,7 @@ __global__ void __launch_bounds__(256) reduce_rows_kernel(const __grid_constant_
     const int c_hi = R.group_cta ? R.group_cta[g + 1] : R.grid;
     const P* __restrict__ part = static_cast<const P*>(R.partial);
     double re = 0.0, im = 0.0;
-#pragma unroll 4
-    for (int c = c_lo; c < c_hi; ++c) {
-        const P p = part[static_cast<int64_t>(c) * R.n_adc + k];
-        re += p.x;
-        im += p.y;
-    }
+    strided_sum(part, R.n_adc, k, c_lo, c_hi, 1, re, im);
     R.sig[2 * (g * R.n_adc + k)] = re;
     R.sig[2 * (g * R.n_adc + k) + 1] = im;
 }
