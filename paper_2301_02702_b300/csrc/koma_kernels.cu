@@ -1656,23 +1656,25 @@ __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_cons
 //
 // Pipeline per CTA (one per SM), warp-specialised, block i of the flattened
 // (group, block) sequence:
-//   16 producer warps copy block i + 2's E rows (256 bytes per run) and
-//   spin parameters into staging buffer (i + 2) % 4 with cp.async once
-//   every producer has read the block that used it before ("staging
-//   read"); each thread arrives on "staged" when its copies have landed;
-//   they turn block i's staging into the FP16 operand slices
-//   of stage i & 1 once the MMAs of block i - 2 have released it ("empty",
-//   the tensor core's commit), then arrive on "full" and "staging read";
+//   16 E warps, once the MMAs of block i - 2 have released stage i & 1
+//   ("empty", the tensor core's commit), copy block i + 2's snapshot rows
+//   and spin parameters into staging buffer (i + 2) % 4 with cp.async (that
+//   buffer held block i - 2, whose fill preceded those MMAs); each thread
+//   arrives on "staged" when its copies have landed; they then turn block
+//   i's staging into the E operand slices of stage i & 1 and arrive on
+//   "full";
+//   8 B warps wait for the same "empty" and "staged", write the rotator
+//   slices of stage i & 1 and arrive on "full";
 //   one MMA warp waits for "full", issues block i's 12 MMAs into accumulator
 //   buffer (group & 1) and commits them to "empty";
-//   after a group's last block the producers read the accumulator from
-//   tensor memory into the CTA's partial row and release the buffer
-//   ("accumulator read").
+//   after a group's last block the E warps read the accumulator from tensor
+//   memory into the CTA's partial row and release the buffer ("accumulator
+//   read").
 // Every wait is bounded; a wait that gives up stops every role.
 // Operand slices: 128 rows x 16 FP16 (4 KB), K-major without swizzle: 8-row
 // x 16-byte core matrices, K-adjacent ones 128 B apart, row-adjacent ones
-// 256 B apart. z_s^l comes from z^(j + 32 g) and z^8 (direct, with an exact
-// phase reduction) and three complex products: l = 32 g + 8 q + j.
+// 256 B apart. z_s^l comes from z^(j + 64 g) and z^8 (direct, with an exact
+// phase reduction) and seven complex products: l = 64 g + 8 q + j.
 // ---------------------------------------------------------------------------
 constexpr int kMmaThreads = 512;                    // E-slice producer threads (16 warps)
 constexpr int kMmaZThreads = 256;                   // B-slice producer threads (8 warps)
