@@ -235,6 +235,11 @@ __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 
 // ---------------------------------------------------------------------------
 // Per-thread spin set: S spins held in registers for a whole walk of the
@@ -455,7 +460,7 @@ struct Spins {
             const f32x2 nz = fma2(c2, fma2(ch, pz, qz), MZ);
             const f32x2 E2 = pk(em2[s0], em2[s1]), E1 = pk(em1[s0], em1[s1]);
             const f32x2 rx = fma2(E2, nx, nx), ry = fma2(E2, ny, ny);
-            const f32x2 rz = fma2(E1, add2(nz, pk(-m0[s0], -m0[s1])), nz);
+            const f32x2 rz = fma2(E1, sub2(nz, pk(m0[s0], m0[s1])), nz);
             unpk(rx, mx[s0], mx[s1]);
             unpk(ry, my[s0], my[s1]);
             unpk(rz, mz[s0], mz[s1]);
@@ -556,7 +561,7 @@ struct Spins {
             const f32x2 nz = fma2(C2, fma2(CH, pz, qz), MZ);
             const f32x2 E2 = pk(em2[s0], em2[s1]), E1 = pk(em1[s0], em1[s1]);
             const f32x2 rx = fma2(E2, nx, nx), ry = fma2(E2, ny, ny);
-            const f32x2 rz = fma2(E1, add2(nz, pk(-m0[s0], -m0[s1])), nz);
+            const f32x2 rz = fma2(E1, sub2(nz, pk(m0[s0], m0[s1])), nz);
             unpk(rx, mx[s0], mx[s1]);
             unpk(ry, my[s0], my[s1]);
             unpk(rz, mz[s0], mz[s1]);
@@ -1741,11 +1746,6 @@ __device__ __forceinline__ void split_half2(float a, float b, uint32_t& hi, uint
 }
 
 // Packed helpers of the operand generation (two spins per f32x2)
-__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
-    f32x2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
 __device__ __forceinline__ f32x2 bcast2(float v) { return pk(v, v); }
 // v - rint(v) for both halves (exact)
 __device__ __forceinline__ f32x2 frac2(f32x2 v) {
