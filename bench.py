@@ -3,10 +3,17 @@
 
 One *step* is one complete simulation of the workload (every spin through
 every discretised sequence step, with the per-ADC-sample signal sum), i.e. one
-``koma_simulate`` call = the Bloch kernel + the fixed-order reduction.
+``koma_simulate`` call: the Bloch kernel, the tensor-core readout when the
+sequence has matrix-form readout groups, and the fixed-order reduction.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload epi512]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload se128]
+    python bench.py --workload serve ...     # the serving workload on its own
     python bench.py --impl reference ...     # the FP64 CPU oracle, host cores
+
+The default workload is the largest single-GPU configuration, the 128^3
+spin echo (se128). Its line also carries a ``serving`` object: a Poisson
+stream of mixed requests through the continuous-batching server, with
+p50/p99 latency and served spin-steps/s.
 
 Under torchrun (N > 1) every rank simulates its own replica of the workload
 (the path has no data exchange: spins are independent); ``value`` is the
@@ -34,10 +41,11 @@ METRIC = "Bloch spin-steps/s at <=1e-4 rel err vs FP64 oracle"
 UNIT = "spin-steps/s"
 TOL = 1e-4
 
-# Algorithmic FP32 work per unit (FMA = 2 flops; derivation in the design doc):
-# an excitation step rotates M about the step's constant field and relaxes it,
-# an ADC sample advances Mxy by one complex rotation-with-decay and adds it
-# to the signal. Steps without RF and without ADC cost nothing (merged).
+# Algorithmic FP32 work per unit (FMA = 2 flops): an excitation step rotates
+# M about the step's constant field and relaxes it (50 flops per spin), an ADC
+# sample advances Mxy by one complex rotation-with-decay and adds it to the
+# signal (8 flops per spin). Steps without RF and without ADC cost nothing
+# (the closed form of the merged precession is evaluated where it is observed).
 FLOPS_RF_STEP = 50
 FLOPS_ADC_SAMPLE = 8
 # moving spins: the RF step's field also moves the position (3 FMA), and an
@@ -48,22 +56,14 @@ FLOPS_ADC_SAMPLE_MOVING = 16
 # FP32 peak of the part: 148 SMs x 128 lanes x 2 flops x 2032 MHz (max SM clock)
 SM_COUNT = 148
 PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * 2032e6 / 1e12
-# The step-class cost model of the method evaluated per sample (every ADC
-# sample an exact phase evaluation, every RF step a spinor rotation): FP32
-# operations and MUFU operations per spin and step class, with the issue rates
-# measured on B300 by paper_2301_02702_b300/csrc/probe_rates.cu (FFMA 117,
-# MUFU ex2 21 per SM per clock). t_min = max(sum FP32 / R_FP32, sum MUFU /
-# R_MUFU); the kernels do less work than this model (merged precession,
-# per-sample rotator), so t_min / t_kernel can exceed 1.
-MODEL_RF = (50, 3)
-MODEL_ADC = (25, 3)
-PROBE_FFMA_PER_SM_CLK = 117
-PROBE_MUFU_PER_SM_CLK = 21
 # tensor-core readout: per 32-spin block and matrix-form group, 4 K slices x
 # 3 FP16 products (hi hi, hi lo, lo hi) of one M = N = 128, K = 16 MMA
 MMA_FLOPS_PER_BLOCK_GROUP = 12 * 2 * 128 * 128 * 16
-# dense FP16/BF16 tensor peak when MEASURED_PEAKS.json is absent (fallback)
+# dense FP16/BF16 tensor peak and HBM bandwidth when MEASURED_PEAKS.json is absent (fallback)
 PEAK_TENSOR_FALLBACK = 1800.0
+PEAK_HBM_FALLBACK = 6400.0
+# contiguous spins kept for the se128 parity check (the rest get PD = 0)
+SE128_PARITY_SLAB = 65536
 
 WORKLOAD_TEXT = {
     "gre32": "gre32: 32x32 grid phantom (1,024 spins), spoiled GRE 32 TRs x 10 ms on a 10 us grid "
@@ -215,6 +215,16 @@ def tensor_peak():
         return PEAK_TENSOR_FALLBACK, "fallback 1.8 PFLOP/s dense BF16 (no measured peaks file)"
 
 
+def hbm_peak():
+    """(GB/s, source) of the measured HBM copy bandwidth of this pool's parts."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured HBM copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError, TypeError):
+        return PEAK_HBM_FALLBACK, "fallback 6.4 TB/s (no measured peaks file)"
+
+
 def algorithmic_flops(info: dict, n_spins: int, moving: bool = False) -> float:
     if moving:
         return float(n_spins) * (info["n_rf"] * FLOPS_RF_STEP_MOVING + info["n_adc"] * FLOPS_ADC_SAMPLE_MOVING)
@@ -297,16 +307,20 @@ def run_reference(args, rank, world):
     return 0
 
 
+
+
 # --------------------------------------------------------------------------
 # serving workload
 # --------------------------------------------------------------------------
 def make_requests(n_req: int, seed: int = 1005):
-    """Request mix of the serving workload (phantom, sequence, spin-steps)."""
+    """Request mix of the serving workload (phantom, sequence, spin-steps):
+    spins log-uniform in [1e3, 1e6] (random subsets of the epi512 and se128
+    phantoms), steps log-uniform in [1e3, 1e5] (the gre32, epi512, se128 and
+    MRF sequences truncated or repeated)."""
     from paper_2301_02702_b300.workloads import Sequence, workload
     rng = np.random.default_rng(seed)
     phs = [workload("epi512", "full")[0], workload("se128", "full")[0]]
     seqs = [workload(w, "full")[1] for w in ("epi512", "se128", "gre32", "mrf")]
-    seqs[3] = seqs[3]  # the MRF train (ungrouped here: one phantom per request)
 
     def take(seq, steps):
         reps = -(-steps // seq.n_steps)
@@ -327,6 +341,150 @@ def make_requests(n_req: int, seed: int = 1005):
     return out
 
 
+def fifo_latencies(arrivals, service):
+    """Latencies of requests served one at a time in arrival order."""
+    free_at, lat = 0.0, []
+    for a, sv in zip(arrivals, service):
+        start = max(a, free_at)
+        free_at = start + sv
+        lat.append(free_at - a)
+    return lat
+
+
+def serve_measure(local: int, n_req: int, rate: float, plain_host: bool = False, n_clients: int = 4,
+                  floods: int = 3):
+    """Serve a Poisson stream of mixed requests (open loop) and measure
+    latency and throughput; then the same requests as floods (saturated
+    throughput) and, for comparison, one plain koma_simulate per request on
+    device-resident inputs (and optionally koma_simulate_host per request)."""
+    import torch
+    from paper_2301_02702_b300 import koma
+    reqs = make_requests(n_req)
+    rng = np.random.default_rng(77)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+    total_units = sum(r[2] for r in reqs)
+    srv = koma.Server(local, mem_budget_bytes=int(150e9))
+    for ph, seq, _ in reqs[:3]:  # warm-up
+        srv.wait(srv.submit(ph, seq))
+
+    # open loop: submit at the Poisson arrival times from several client
+    # threads (arrival i -> client i % n_clients), collect latencies
+    ids = [None] * len(reqs)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+
+    def client(c):
+        for i in range(c, len(reqs), n_clients):
+            d = t0 + arrivals[i] - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            ids[i] = srv.submit(reqs[i][0], reqs[i][1])
+
+    ths = [threading.Thread(target=client, args=(c,)) for c in range(n_clients)]
+    for th in ths:
+        th.start()
+    lat = []
+    for i in range(len(reqs)):
+        while ids[i] is None:
+            time.sleep(0.0005)
+        _, info = srv.wait(ids[i])
+        lat.append(info["latency_s"])
+    for th in ths:
+        th.join()
+    t_open = time.perf_counter() - t0
+    clk = clocks.stop()
+    stats = srv.stats()
+
+    # saturation: everything submitted at once by the same client threads;
+    # the median of the floods (host threads make single floods noisy)
+    sid = [None] * len(reqs)
+
+    def flood(c):
+        for i in range(c, len(reqs), n_clients):
+            sid[i] = srv.submit(reqs[i][0], reqs[i][1])
+
+    t_floods = []
+    for _ in range(floods):
+        t1 = time.perf_counter()
+        ths = [threading.Thread(target=flood, args=(c,)) for c in range(n_clients)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        for rid in sid:
+            srv.wait(rid)
+        t_floods.append(time.perf_counter() - t1)
+    t_sat = statistics.median(t_floods)
+    launches = int(srv.stats()["launches"])
+    srv.close()
+
+    # plain, device resident: every request's phantom and sequence uploaded
+    # beforehand, then one koma_simulate per request back to back on one
+    # stream (the readout on the tensor cores where the sequence has
+    # matrix-form groups), device time per call from CUDA events
+    sim = koma.Simulator(local)
+    stream = torch.cuda.Stream(local)
+    service_dev = []
+    chunk = 64
+    for c0 in range(0, len(reqs), chunk):
+        part = reqs[c0:c0 + chunk]
+        hs_ = [(sim.upload_phantom(ph), sim.upload_sequence(seq), seq.n_adc) for ph, seq, _ in part]
+        outs = [torch.empty((1, n_adc), dtype=torch.complex128, device=f"cuda:{local}") for _, _, n_adc in hs_]
+        for (hp, hq, _), o in zip(hs_, outs):  # warm: scratch grown, launch tables in place
+            sim.simulate(hp, hq, "fp32", out=o, stream=stream)
+        sim.sync(stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in hs_]
+        for (hp, hq, _), o, (e0, e1) in zip(hs_, outs, evs):
+            e0.record(stream)
+            sim.simulate(hp, hq, "fp32", out=o, stream=stream)
+            e1.record(stream)
+        sim.sync(stream)
+        service_dev += [e0.elapsed_time(e1) / 1e3 for e0, e1 in evs]
+        for hp, hq, _ in hs_:
+            koma.koma_sequence_free(hq)
+            koma.koma_phantom_free(hp)
+    sim.close()
+    t_plain_dev = sum(service_dev)
+    plain_lat = fifo_latencies(arrivals, service_dev)
+    out = {
+        "requests": len(reqs), "rate_per_s": rate,
+        "mean_spin_steps_per_request": total_units / len(reqs),
+        "offered_spin_steps_per_s": total_units / arrivals[-1],
+        "served": {"value": total_units / t_open, "unit": UNIT, "seconds": t_open},
+        "latency": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                    "mean_s": float(np.mean(lat)), "max_s": float(np.max(lat))},
+        "saturated": {"value": total_units / t_sat, "unit": UNIT, "seconds": t_sat,
+                      "floods_s": [round(t, 4) for t in t_floods], "statistic": f"median of {floods} floods"},
+        "plain_device": {"value": total_units / t_plain_dev, "unit": UNIT, "seconds": t_plain_dev,
+                         "p50_s": float(np.percentile(plain_lat, 50)),
+                         "p99_s": float(np.percentile(plain_lat, 99)),
+                         "plain": "one koma_simulate per request on device-resident inputs, back to back on one "
+                                  "stream (device time, CUDA events); latencies under the same arrivals"},
+        "ratio_saturated_vs_plain_device": t_plain_dev / t_sat,
+        "server": {k: stats[k] for k in ("batches", "mem_peak", "completed", "failed")},
+        "server_launches": launches,
+        "clocks": clk,
+    }
+    if plain_host:
+        # plain through the host API: one koma_simulate_host per request
+        # (upload, simulate, copy back), one at a time in arrival order
+        ctx = koma.koma_init(local)
+        service = []
+        for ph, seq, _ in reqs:
+            buf = np.empty((1, seq.n_adc), dtype=np.complex128)
+            ts = time.perf_counter()
+            koma.koma_simulate_host(ctx, ph, seq, koma.KOMA_FP32_SPLITPHASE, out=buf)
+            service.append(time.perf_counter() - ts)
+        koma.koma_destroy(ctx)
+        hl = fifo_latencies(arrivals, service)
+        out["plain_host"] = {"value": total_units / sum(service), "unit": UNIT, "seconds": sum(service),
+                             "p50_s": float(np.percentile(hl, 50)), "p99_s": float(np.percentile(hl, 99)),
+                             "plain": "koma_simulate_host per request (upload, simulate, copy back), one at a "
+                                      "time in arrival order; latencies under the same arrivals"}
+    return out
+
+
 def run_serve(args, rank, world, local):
     import torch
     from paper_2301_02702_b300 import build, koma
@@ -339,107 +497,21 @@ def run_serve(args, rank, world, local):
     if rank == 0 or not os.path.exists(koma.LIB_PATH):
         build.build()
     barrier(world)
-    reqs = make_requests(args.requests)
-    rng = np.random.default_rng(77)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, len(reqs)))
-    total_units = sum(r[2] for r in reqs)
-    srv = koma.Server(local, mem_budget_bytes=int(150e9))
-    for ph, seq, _ in reqs[:3]:  # warm-up
-        srv.wait(srv.submit(ph, seq))
-
-    # open loop: submit at the Poisson arrival times, collect latencies
-    ids = [None] * len(reqs)
-    clocks = ClockSampler(local)
-    barrier(world)
-    clocks.start()
-    t0 = time.perf_counter()
-
-    n_clients = 4  # requests come from several client threads (arrival i -> client i % 4)
-
-    def client(c):
-        for i in range(c, len(reqs), n_clients):
-            d = t0 + arrivals[i] - time.perf_counter()
-            if d > 0:
-                time.sleep(d)
-            ids[i] = srv.submit(reqs[i][0], reqs[i][1])
-
-    ths = [threading.Thread(target=client, args=(c,)) for c in range(n_clients)]
-    for th in ths:
-        th.start()
-    lat, done = [], []
-    for i in range(len(reqs)):
-        while ids[i] is None:
-            time.sleep(0.0005)
-        _, info = srv.wait(ids[i])
-        lat.append(info["latency_s"])
-        done.append(info["done_s"])
-    for th in ths:
-        th.join()
-    t_open = time.perf_counter() - t0
-    clk = clocks.stop()
-    stats = srv.stats()
-
-    # saturation: everything submitted at once (by the same client threads);
-    # the median of three floods (host threads make single floods noisy)
-    sid = [None] * len(reqs)
-
-    def flood(c):
-        for i in range(c, len(reqs), n_clients):
-            sid[i] = srv.submit(reqs[i][0], reqs[i][1])
-
-    t_floods = []
-    for _ in range(3):
-        t1 = time.perf_counter()
-        ths = [threading.Thread(target=flood, args=(c,)) for c in range(n_clients)]
-        for th in ths:
-            th.start()
-        for th in ths:
-            th.join()
-        for rid in sid:
-            srv.wait(rid)
-        t_floods.append(time.perf_counter() - t1)
-    t_sat = statistics.median(t_floods)
-    srv.close()
-
-    # plain: one koma_simulate_host per request, in arrival order, one at a time
-    ctx = koma.koma_init(local)
-    service = []
-    for ph, seq, _ in reqs:
-        buf = np.empty((1, seq.n_adc), dtype=np.complex128)
-        ts = time.perf_counter()
-        koma.koma_simulate_host(ctx, ph, seq, koma.KOMA_FP32_SPLITPHASE, out=buf)
-        service.append(time.perf_counter() - ts)
-    koma.koma_destroy(ctx)
-    t_plain = sum(service)
-    free_at, plain_lat = 0.0, []
-    for a, sv in zip(arrivals, service):
-        start = max(a, free_at)
-        free_at = start + sv
-        plain_lat.append(free_at - a)
-
-    value = total_units / t_open
-    value = value * world  # replicas
+    r = serve_measure(local, args.requests, args.rate, plain_host=True)
+    # replicas: every rank serves its own stream; the slowest rank's time counts
+    t_open = reduce_max(r["served"]["seconds"], world)
+    value = r["served"]["value"] * r["served"]["seconds"] / t_open * world
     if rank == 0:
         line = {
             "metric": "Bloch spin-steps/s served (open-loop Poisson load); p50/p99 latency", "value": value,
-            "unit": UNIT, "n_gpus": world, "steps": len(reqs), "warmup": 3, "ms_per_step": 1e3 * t_open / len(reqs),
+            "unit": UNIT, "n_gpus": world, "steps": r["requests"], "warmup": 3,
+            "ms_per_step": 1e3 * r["served"]["seconds"] / r["requests"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_TEXT["serve"], "requests": len(reqs), "rate_per_s": args.rate,
-                       "mean_spin_steps_per_request": total_units / len(reqs),
-                       "offered_spin_steps_per_s": total_units / arrivals[-1], "parallelism": f"replicas x{world}"},
-            "latency": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                        "mean_s": float(np.mean(lat)), "max_s": float(np.max(lat))},
-            "saturated": {"value": total_units / t_sat, "unit": UNIT, "seconds": t_sat,
-                          "floods_s": [round(t, 4) for t in t_floods], "statistic": "median of 3 floods"},
-            "vs_plain": {"plain_value": total_units / t_plain, "unit": UNIT,
-                         "ratio_saturated": (total_units / t_sat) / (total_units / t_plain),
-                         "plain_p50_s": float(np.percentile(plain_lat, 50)),
-                         "plain_p99_s": float(np.percentile(plain_lat, 99)),
-                         "plain": "koma_simulate_host per request (upload, simulate, copy back), one at a time in "
-                                  "arrival order; latencies under the same arrivals"},
-            "server": {k: stats[k] for k in ("launches", "batches", "mem_peak", "completed", "failed")},
-            "gpu_launches": int(stats["launches"]),
-            "clocks": clk,
+            "config": {"workload": WORKLOAD_TEXT["serve"], "requests": r["requests"], "rate_per_s": args.rate,
+                       "parallelism": f"replicas x{world}"},
+            "serving": r,
+            "gpu_launches": r["server_launches"],
+            "clocks": r["clocks"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -451,6 +523,40 @@ def run_serve(args, rank, world, local):
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+def parity_case(name, ph, seq):
+    """(phantom to launch, phantom the oracle runs, description, group rows)
+    of the parity check in the benchmark's launch configuration. Every spin
+    contributes except for se128 (a contiguous slab of 65,536 spins around
+    the excited slice, PD = 0 elsewhere: the signal is then the slab's) and
+    the MRF dictionary (200 random entries, each an independent output)."""
+    from paper_2301_02702_b300.workloads import Phantom
+    if ph.n_groups > 1:
+        rng = np.random.default_rng(11)
+        groups = np.sort(rng.choice(ph.n_groups, min(ph.n_groups, 200), replace=False))
+        idx = np.concatenate([np.arange(ph.group_offsets[g], ph.group_offsets[g + 1]) for g in groups])
+        offs = np.concatenate([[0], np.cumsum(np.diff(ph.group_offsets)[groups])])
+        sub = Phantom(ph.x[idx], ph.y[idx], ph.z[idx], ph.pd[idx], ph.t1[idx], ph.t2[idx], ph.dw[idx],
+                      group_offsets=offs)
+        return ph, sub, (f"{len(groups)} random dictionary entries of the full launch vs FP64 oracle "
+                         f"(per-entry max-abs error over the entry's maximum)"), groups
+    if name == "se128":
+        lo = ph.n // 2 - SE128_PARITY_SLAB // 2
+        keep = np.arange(lo, lo + SE128_PARITY_SLAB)
+        pd = np.zeros(ph.n)
+        pd[keep] = ph.pd[keep]
+        masked = Phantom(ph.x, ph.y, ph.z, pd, ph.t1, ph.t2, ph.dw, velocity=ph.velocity)
+        return masked, ph.subset(keep), (f"full {ph.n}-spin launch with a contiguous slab of {len(keep)} spins "
+                                         f"around the excited slice kept (PD = 0 elsewhere) vs FP64 oracle on the "
+                                         f"slab"), None
+    return ph, ph, f"every spin ({ph.n}) of the full launch vs FP64 oracle", None
+
+
+def rel_err_of(got, ref, groups):
+    if groups is not None:
+        return float(np.max(np.max(np.abs(got[groups] - ref), axis=1) / np.max(np.abs(ref), axis=1)))
+    return float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2301_02702_b300 import build, koma
@@ -475,43 +581,31 @@ def run_ours(args, rank, world, local):
     out = torch.empty((ph.n_groups, seq.n_adc), dtype=torch.complex128, device=f"cuda:{local}")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > 126 MB L2
     grouped = ph.n_groups > 1
+    moving = ph.velocity is not None
     tuned = sim.tune(hp, hs, stream) if (grouped or args.tune) else None
 
-    # parity in this launch configuration: PD-masked spin sample vs oracle
+    def run_once(handle, mma=True):
+        koma.koma_set_mma(sim.ctx, mma)
+        with torch.cuda.stream(stream):
+            sim.simulate(handle, hs, "fp32", out=out, stream=stream)
+        sim.sync(stream)
+        koma.koma_set_mma(sim.ctx, True)
+        return out.cpu().numpy()
+
+    # parity in this launch configuration against the FP64 oracle
     parity = None
-    if rank == 0 and not args.no_parity and grouped:
+    par_handle, par_ref, par_groups = None, None, None
+    if rank == 0 and not args.no_parity:
         import oracle
-        from paper_2301_02702_b300.workloads import Phantom as Ph
-        with torch.cuda.stream(stream):
-            sim.simulate(hp, hs, "fp32", out=out, stream=stream)
-        sim.sync(stream)
-        rng = np.random.default_rng(11)
-        groups = np.sort(rng.choice(ph.n_groups, min(ph.n_groups, 200), replace=False))
-        got = out[torch.as_tensor(groups, device=out.device)].cpu().numpy()
-        idx = np.concatenate([np.arange(ph.group_offsets[g], ph.group_offsets[g + 1]) for g in groups])
-        offs = np.concatenate([[0], np.cumsum(np.diff(ph.group_offsets)[groups])])
-        sub = Ph(ph.x[idx], ph.y[idx], ph.z[idx], ph.pd[idx], ph.t1[idx], ph.t2[idx], ph.dw[idx], group_offsets=offs)
-        ref = oracle.simulate(sub, seq)
-        err = float(np.max(np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref), axis=1)))
-        parity = {"rel_err": err, "tol": TOL, "pass": err <= TOL,
-                  "sample": f"{len(groups)} random dictionary entries of the full launch vs FP64 oracle "
-                            f"(per-entry max-abs error over the entry's maximum)"}
-    elif rank == 0 and not args.no_parity:
-        import oracle
-        rng = np.random.default_rng(5)
-        keep = np.sort(rng.choice(ph.n, min(ph.n, 1536), replace=False))
-        pd = np.zeros(ph.n)
-        pd[keep] = ph.pd[keep]
-        hm = sim.upload_phantom(Phantom(ph.x, ph.y, ph.z, pd, ph.t1, ph.t2, ph.dw, velocity=ph.velocity))
-        with torch.cuda.stream(stream):
-            sim.simulate(hm, hs, "fp32", out=out, stream=stream)
-        sim.sync(stream)
-        got = out.cpu().numpy()
-        koma.koma_phantom_free(hm)
-        ref = oracle.simulate(ph.subset(keep), seq)
-        err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
-        parity = {"rel_err": err, "tol": TOL, "pass": err <= TOL,
-                  "sample": f"{len(keep)} random spins (others PD=0) in the full-size launch, vs FP64 oracle"}
+        launch_ph, oracle_ph, desc, par_groups = parity_case(args.workload, ph, seq)
+        par_handle = hp if launch_ph is ph else sim.upload_phantom(launch_ph)
+        got = run_once(par_handle)
+        t0 = time.perf_counter()
+        par_ref = oracle.simulate(oracle_ph, seq)
+        t_or = time.perf_counter() - t0
+        err = rel_err_of(got, par_ref, par_groups)
+        parity = {"rel_err": err, "tol": TOL, "pass": err <= TOL, "sample": desc,
+                  "oracle_s": round(t_or, 1)}
 
     koma.koma_set_timing(sim.ctx, True)
     for _ in range(args.warmup):
@@ -520,7 +614,7 @@ def run_ours(args, rank, world, local):
     launch = sim.launch_info()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    k1_ms = []
+    stage_ms = []
     clocks = ClockSampler(local)
     barrier(world)
     torch.cuda.synchronize(local)
@@ -532,7 +626,7 @@ def run_ours(args, rank, world, local):
             sim.simulate(hp, hs, "fp32", out=out, stream=stream)
             ev[i][1].record(stream)
         if args.kernel_timing:
-            k1_ms.append(koma.koma_get_stage_timing(sim.ctx))
+            stage_ms.append(koma.koma_get_stage_timing(sim.ctx))
     torch.cuda.synchronize(local)
     barrier(world)
     clk = clocks.stop()
@@ -542,6 +636,34 @@ def run_ours(args, rank, world, local):
     ms_max = reduce_max(ms, world)
     units = ph.n * seq.n_steps
     value = units * world / (ms_max / 1e3)
+
+    # the same step with every ADC sample stepped by the Bloch kernel (no
+    # tensor cores), with its own parity against the same oracle result
+    no_mma = None
+    if rank == 0 and launch.get("mma_grid", 0) > 0:
+        koma.koma_set_mma(sim.ctx, False)
+        for _ in range(2):
+            sim.simulate(hp, hs, "fp32", out=out, stream=stream)
+        sim.sync(stream)
+        n_nm = max(1, min(args.steps, 5))
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_nm)]
+        for e0, e1 in evs:
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0.record(stream)
+                sim.simulate(hp, hs, "fp32", out=out, stream=stream)
+                e1.record(stream)
+        sim.sync(stream)
+        nm_ms = sum(a.elapsed_time(b) for a, b in evs) / n_nm
+        koma.koma_set_mma(sim.ctx, True)
+        no_mma = {"value": units / (nm_ms / 1e3), "unit": UNIT, "ms_per_step": nm_ms, "steps": n_nm,
+                  "path": "koma_set_mma(ctx, 0): every ADC sample stepped by the Bloch kernel (FP32 pipes only)"}
+        if par_handle is not None:
+            err = rel_err_of(run_once(par_handle, mma=False), par_ref, par_groups)
+            no_mma["rel_err"] = err
+            no_mma["pass"] = err <= TOL
+    if par_handle is not None and par_handle is not hp:
+        koma.koma_phantom_free(par_handle)
 
     # the plain path for a dictionary: one koma_simulate per entry (sample)
     vs_plain = None
@@ -575,7 +697,6 @@ def run_ours(args, rank, world, local):
     # inputs and the result live in pinned host memory (as a serving front end keeps
     # them); every step copies them to and from the device inside the timed region.
     e2e = None
-    moving = ph.velocity is not None
     pinned_keep = []
 
     def pinned(a):
@@ -672,75 +793,22 @@ def run_ours(args, rank, world, local):
                "sample": f"{len(idx)} of {ph.n} spins (random, seed 123) x all {seq.n_steps} steps, "
                          f"{dt:.1f} s"}
 
+    # serving: a Poisson stream of mixed requests through the server (rank 0)
+    serving = None
+    if rank == 0 and args.workload == "se128" and args.serving_requests > 0:
+        serving = serve_measure(local, args.serving_requests, args.rate)
+
+    line = None
     if rank == 0:
-        # stages of one simulate: Bloch kernel, tensor-core readout (0 when the
-        # call has none), reduction
-        k1 = k6 = None
-        if k1_ms:
-            k1 = sum(t[0] for t in k1_ms) / len(k1_ms)
-            k6 = sum(t[1] for t in k1_ms) / len(k1_ms)
-        mma = launch.get("mma_grid", 0) > 0
-        mma_samples = info.get("n_mma_samples", 0) if mma else 0
-        flops_all = algorithmic_flops(info, ph.n, moving)
-        # the Bloch kernel's share: every RF step and the samples it steps
-        flops = flops_all - float(ph.n) * mma_samples * FLOPS_ADC_SAMPLE
-        achieved = flops / (k1 / 1e3) / 1e12 if k1 else None
-        kname = "bloch_motion_kernel" if moving else ("bloch_items_kernel" if grouped else "bloch_fp32_kernel")
-        roof = {"bound": "alu", "kernel": f"{kname}<{launch['spins_per_thread']}>",
-                "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                "frac": (achieved / PEAK_FP32_TFLOPS) if achieved else None,
-                "traffic": measured_traffic(args.workload),
-                "kernel_ms": k1, "algorithmic_flops_per_launch": flops,
-                "peak_source": "FP32 peak 148 SMs x 128 lanes x 2 x 2032 MHz (max SM clock)"}
-        roof_mma = None
-        if mma and k6:
-            peak_t, peak_src = tensor_peak()
-            blocks = (ph.n + 31) // 32
-            tflops = float(blocks) * info["n_mma_groups"] * MMA_FLOPS_PER_BLOCK_GROUP
-            direct = float(ph.n) * mma_samples * FLOPS_ADC_SAMPLE
-            roof_mma = {"bound": "tensor", "kernel": "readout_mma_kernel", "achieved": tflops / (k6 / 1e3) / 1e12,
-                        "peak": peak_t, "unit": "TFLOP/s", "frac": tflops / (k6 / 1e3) / 1e12 / peak_t,
-                        "traffic": measured_traffic(args.workload + ":readout"), "kernel_ms": k6,
-                        "tensor_flops_per_launch": tflops, "peak_source": peak_src,
-                        "samples": mma_samples,
-                        "direct_sum_flops_per_launch": direct,
-                        "direct_sum_tflops": direct / (k6 / 1e3) / 1e12}
-            if k6 > k1:  # the readout dominates the step: it is the line's roofline
-                roof, roof_mma = roof_mma, roof
-        if k1:
-            k1_total = k1 + (k6 or 0.0)
-            mhz = (clk or {}).get("sm_mhz") or 2032.0
-            fp32_ops = ph.n * (info["n_rf"] * MODEL_RF[0] + info["n_adc"] * MODEL_ADC[0])
-            mufu_ops = ph.n * (info["n_rf"] * MODEL_RF[1] + info["n_adc"] * MODEL_ADC[1])
-            t_fp32 = fp32_ops / (SM_COUNT * PROBE_FFMA_PER_SM_CLK * mhz * 1e6) * 1e3
-            t_mufu = mufu_ops / (SM_COUNT * PROBE_MUFU_PER_SM_CLK * mhz * 1e6) * 1e3
-            roof["step_model"] = {"fp32_ops": fp32_ops, "mufu_ops": mufu_ops, "t_fp32_ms": t_fp32,
-                                  "t_mufu_ms": t_mufu, "t_min_ms": max(t_fp32, t_mufu),
-                                  "kernels_ms": k1_total,
-                                  "frac": max(t_fp32, t_mufu) / k1_total,
-                                  "model": "per spin: RF step 50 FP32 + 3 MUFU, ADC sample 25 FP32 + 3 MUFU, "
-                                           "at the probed FFMA/MUFU issue rates and the sampled SM clock"}
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_TEXT[args.workload], "spins": ph.n, "steps_per_sim": seq.n_steps,
-                       "n_adc": seq.n_adc, "n_rf": info["n_rf"], "records": info["n_records"],
-                       "precision": "KOMA_FP32_SPLITPHASE", "l2": "flushed (256 MB write) between timed steps",
-                       "parallelism": f"replicas x{world}",
-                       "launch": {k: launch[k] for k in ("grid", "block", "spins_per_thread", "spins_per_cta")}},
-            "roofline": roof,
-            "roofline_other": roof_mma,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": launch["kernels"] * args.steps,
-            "clocks": clk,
-            "parity": parity,
-        }
-        if tuned is not None:
-            line["config"]["tuned"] = {k: tuned[k] for k in ("grid", "block", "spins_per_thread")}
+        line = result_line(args, world, ph, seq, info, launch, stage_ms, clk, value, ms_max, tuned, moving,
+                           grouped)
+        line.update({"cpu_baseline": cpu, "e2e": e2e, "parity": parity})
+        if no_mma is not None:
+            line["no_tensor_cores"] = no_mma
         if vs_plain is not None:
             line["vs_plain"] = vs_plain
+        if serving is not None:
+            line["serving"] = serving
         print(json.dumps(line), flush=True)
     koma.koma_sequence_free(hs)
     koma.koma_phantom_free(hp)
@@ -751,30 +819,106 @@ def run_ours(args, rank, world, local):
     return 0
 
 
+def result_line(args, world, ph, seq, info, launch, stage_ms, clk, value, ms_max, tuned, moving, grouped):
+    """The JSON line of our arm: the metric, the launch, and the roofline of
+    each kernel of the step (with the step's time-weighted fraction)."""
+    k1 = k6 = k2 = None
+    if stage_ms:
+        k1 = sum(t[0] for t in stage_ms) / len(stage_ms)
+        k6 = sum(t[1] for t in stage_ms) / len(stage_ms)
+        k2 = sum(t[2] for t in stage_ms) / len(stage_ms)
+    mma = launch.get("mma_grid", 0) > 0
+    mma_samples = info.get("n_mma_samples", 0) if mma else 0
+    flops_all = algorithmic_flops(info, ph.n, moving)
+    # the Bloch kernel's share: every RF step and the samples it steps
+    flops = flops_all - float(ph.n) * mma_samples * FLOPS_ADC_SAMPLE
+    achieved = flops / (k1 / 1e3) / 1e12 if k1 else None
+    kname = "bloch_motion_kernel" if moving else ("bloch_items_kernel" if grouped else "bloch_fp32_kernel")
+    roofs = []
+    roof1 = {"bound": "alu", "kernel": f"{kname}<{launch['spins_per_thread']}>",
+             "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+             "frac": (achieved / PEAK_FP32_TFLOPS) if achieved else None,
+             "traffic": measured_traffic(args.workload),
+             "kernel_ms": k1, "algorithmic_flops_per_launch": flops,
+             "peak_source": "FP32 peak 148 SMs x 128 lanes x 2 x 2032 MHz (unit counts, max SM clock)"}
+    roofs.append(roof1)
+    if mma and k6:
+        peak_t, peak_src = tensor_peak()
+        blocks = (ph.n + 31) // 32
+        tflops = float(blocks) * info["n_mma_groups"] * MMA_FLOPS_PER_BLOCK_GROUP
+        direct = float(ph.n) * mma_samples * FLOPS_ADC_SAMPLE
+        roofs.append({"bound": "tensor", "kernel": "readout_mma_kernel", "achieved": tflops / (k6 / 1e3) / 1e12,
+                      "peak": peak_t, "unit": "TFLOP/s", "frac": tflops / (k6 / 1e3) / 1e12 / peak_t,
+                      "traffic": measured_traffic(args.workload + ":readout"), "kernel_ms": k6,
+                      "tensor_flops_per_launch": tflops, "peak_source": peak_src + " (of measured)",
+                      "samples": mma_samples, "direct_sum_flops_per_launch": direct,
+                      "direct_sum_tflops": direct / (k6 / 1e3) / 1e12})
+    if k2 and not grouped:
+        # the reduction reads each sample's partial rows once (8 B per row and
+        # sample) and writes the FP64 signal (16 B per sample)
+        peak_h, hsrc = hbm_peak()
+        rows1 = launch["grid"] // max(1, launch.get("split", 1))
+        n_adc = info["n_adc"]
+        rb = 8.0 * (rows1 * (n_adc - mma_samples) + launch.get("mma_grid", 0) * mma_samples) + 16.0 * n_adc
+        if mma:
+            rb += n_adc  # the per-sample source map
+        roofs.append({"bound": "hbm", "kernel": "reduce_partials_kernel", "achieved": rb / (k2 / 1e3) / 1e9,
+                      "peak": peak_h, "unit": "GB/s", "frac": rb / (k2 / 1e3) / 1e9 / peak_h,
+                      "traffic": None, "kernel_ms": k2, "algorithmic_bytes_per_launch": rb,
+                      "peak_source": hsrc + " (of measured)"})
+    roofs.sort(key=lambda r: -(r["kernel_ms"] or 0.0))
+    step = None
+    if k1:
+        tot = sum(r["kernel_ms"] for r in roofs)
+        step = {"kernels_ms": tot, "frac": sum(r["kernel_ms"] * r["frac"] for r in roofs) / tot,
+                "how": "kernel-time-weighted mean of the step's kernels' roofline fractions"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "spins": ph.n, "steps_per_sim": seq.n_steps,
+                   "n_adc": seq.n_adc, "n_rf": info["n_rf"], "records": info["n_records"],
+                   "precision": "KOMA_FP32_SPLITPHASE", "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"replicas x{world}",
+                   "launch": {k: launch[k] for k in ("grid", "block", "spins_per_thread", "spins_per_cta",
+                                                     "mma_grid")}},
+        "roofline": roofs[0],
+        "roofline_other": roofs[1:],
+        "roofline_step": step,
+        "gpu_launches": launch["kernels"] * args.steps,
+        "clocks": clk,
+    }
+    if tuned is not None:
+        line["config"]["tuned"] = {k: tuned[k] for k in ("grid", "block", "spins_per_thread")}
+    return line
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOAD_TEXT), default="epi512")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_TEXT), default="se128")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--cpu-target-s", type=float, default=15.0)
     ap.add_argument("--reference-budget-s", type=float, default=150.0)
     ap.add_argument("--no-kernel-timing", dest="kernel_timing", action="store_false")
     ap.add_argument("--tune", action="store_true", help="autotune the launch first (grouped workloads always do)")
-    ap.add_argument("--requests", type=int, default=200, help="serving workload: number of requests")
-    ap.add_argument("--rate", type=float, default=200.0, help="serving workload: Poisson arrival rate, 1/s")
+    ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
+    ap.add_argument("--serving-requests", type=int, default=400,
+                    help="requests of the serving stream in the se128 line (0: none)")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate, 1/s")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     rank, world, local = dist_env()
     if args.impl == "reference":
         if args.workload == "serve":
-            args.workload = "epi512"
+            args.workload = "se128"
         return run_reference(args, rank, world)
     if args.workload == "serve":
         return run_serve(args, rank, world, local)

@@ -341,7 +341,9 @@ koma_status koma_get_stage_timing(koma_ctx *ctx, float *bloch_ms, float *mma_ms,
  * KOMA_E_INVALID (NULL). */
 koma_status koma_set_mma(koma_ctx *ctx, int enable);
 
-/* Launch description of the last koma_simulate on ctx. */
+/* Launch description of the last koma_simulate or koma_simulate_static on
+ * ctx (after a static call, koma_get_timing reports no timed call: that entry
+ * point records no stage events). */
 koma_status koma_get_launch_info(const koma_ctx *ctx, koma_launch_info *info);
 
 /*

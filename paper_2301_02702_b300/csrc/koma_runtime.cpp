@@ -1534,6 +1534,11 @@ extern "C" koma_status koma_simulate_static(const koma_phantom* ph, const koma_s
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(ctx, KOMA_E_CUDA, "simulate_static: cannot select device %d", ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the launch description and stage timing describe this call from here on
+    // (the static path records no stage events)
+    ctx->last = koma_launch_info{};
+    ctx->last.bloch_stream = stream;
+    ctx->timing_recorded = false;
     if (ph->n == 0) {
         cudaError_t e = cudaMemsetAsync(sig_dev, 0, static_cast<size_t>(n_adc) * 2 * sizeof(double), st);
         return e == cudaSuccess ? KOMA_OK : cuda_fail(ctx, e, "simulate_static: memset");
@@ -1579,6 +1584,14 @@ extern "C" koma_status koma_simulate_static(const koma_phantom* ph, const koma_s
     if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate_static: Bloch kernel launch");
     e = koma::launch_reduce(R, false, stream);
     if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate_static: reduction launch");
+    ctx->last.kernels = 2;
+    ctx->last.grid = L.grid;
+    ctx->last.block = L.block;
+    ctx->last.spins_per_thread = L.spins_per_thread;
+    ctx->last.spins_per_cta = L.spins_per_cta;
+    ctx->last.n_records = seq->info.n_records;
+    ctx->last.partial_bytes = static_cast<int64_t>(L.grid) * n_adc * static_cast<int64_t>(sizeof(float2));
+    ctx->last.split = 1;
     return KOMA_OK;
 }
 

@@ -54,6 +54,8 @@ def test_static_entry_matches_simulate_on_two_calls(sim, name, scale):
             err = rel_err(got, ref)
             assert err < TOL32, f"call {call}: rel err {err:.3g} vs koma_simulate"
             assert koma.koma_mem_used(sim.ctx) == held
+            info = sim.launch_info()  # describes this call, not the koma_simulate before it
+            assert info["kernels"] == 2 and info["mma_grid"] == 0 and info["grid"] >= 1
             if call == 1:
                 assert free_after == free_before, "the call took device memory"
     finally:
