@@ -56,6 +56,15 @@ FLOPS_ADC_SAMPLE_MOVING = 16
 # FP32 peak of the part: 148 SMs x 128 lanes x 2 flops x 2032 MHz (max SM clock)
 SM_COUNT = 148
 PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * 2032e6 / 1e12
+# repeated RF pulses taken by their maps: the pre-pass steps four vectors
+# (the three columns of A and c) through each distinct pulse, sharing the
+# step's rotation: per spin-step the field, |a|^2, |a| and the axis (14
+# flops) once; per vector the rotation (two cross products, w p + q and the
+# update: 30) and the relaxation (6); the columns of A, carried as FP32
+# pairs, also rotate their low parts (30) and add each component's increment
+# by TwoSum (6 per component: 18). Applying a map is 9 FMA per spin.
+FLOPS_MAP_STEP = 14 + 3 * (30 + 6 + 30 + 18) + (30 + 6)
+FLOPS_MAP_APPLY = 18
 # tensor-core readout: per 32-spin block and matrix-form group, 4 K slices x
 # 3 FP16 products (hi hi, hi lo, lo hi) of one M = N = 128, K = 16 MMA
 MMA_FLOPS_PER_BLOCK_GROUP = 12 * 2 * 128 * 128 * 16
@@ -626,7 +635,7 @@ def run_ours(args, rank, world, local):
             sim.simulate(hp, hs, "fp32", out=out, stream=stream)
             ev[i][1].record(stream)
         if args.kernel_timing:
-            stage_ms.append(koma.koma_get_stage_timing(sim.ctx))
+            stage_ms.append(koma.koma_get_stage_timing(sim.ctx) + (koma.koma_get_map_timing(sim.ctx),))
     torch.cuda.synchronize(local)
     barrier(world)
     clk = clocks.stop()
@@ -662,6 +671,35 @@ def run_ours(args, rank, world, local):
             err = rel_err_of(run_once(par_handle, mma=False), par_ref, par_groups)
             no_mma["rel_err"] = err
             no_mma["pass"] = err <= TOL
+    # the same step with every RF step stepped (repeated pulses not taken by
+    # their maps), with its own parity
+    no_maps = None
+    if rank == 0 and info.get("n_rf_maps", 0) > 0 and not grouped and not moving:
+        koma.koma_set_rf_maps(sim.ctx, False)
+        for _ in range(2):
+            sim.simulate(hp, hs, "fp32", out=out, stream=stream)
+        sim.sync(stream)
+        n_nm = max(1, min(args.steps, 5))
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_nm)]
+        for e0, e1 in evs:
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0.record(stream)
+                sim.simulate(hp, hs, "fp32", out=out, stream=stream)
+                e1.record(stream)
+        sim.sync(stream)
+        nm_ms = sum(a.elapsed_time(b) for a, b in evs) / n_nm
+        no_maps = {"value": units / (nm_ms / 1e3), "unit": UNIT, "ms_per_step": nm_ms, "steps": n_nm,
+                   "path": "koma_set_rf_maps(ctx, 0): every RF step of the repeated pulses stepped by the Bloch "
+                           "kernel"}
+        if par_handle is not None:
+            got = None
+            koma.koma_set_rf_maps(sim.ctx, False)
+            got = run_once(par_handle)
+            err = rel_err_of(got, par_ref, par_groups)
+            no_maps["rel_err"] = err
+            no_maps["pass"] = err <= TOL
+        koma.koma_set_rf_maps(sim.ctx, True)
     if par_handle is not None and par_handle is not hp:
         koma.koma_phantom_free(par_handle)
 
@@ -805,6 +843,8 @@ def run_ours(args, rank, world, local):
         line.update({"cpu_baseline": cpu, "e2e": e2e, "parity": parity})
         if no_mma is not None:
             line["no_tensor_cores"] = no_mma
+        if no_maps is not None:
+            line["no_rf_maps"] = no_maps
         if vs_plain is not None:
             line["vs_plain"] = vs_plain
         if serving is not None:
@@ -822,19 +862,34 @@ def run_ours(args, rank, world, local):
 def result_line(args, world, ph, seq, info, launch, stage_ms, clk, value, ms_max, tuned, moving, grouped):
     """The JSON line of our arm: the metric, the launch, and the roofline of
     each kernel of the step (with the step's time-weighted fraction)."""
-    k1 = k6 = k2 = None
+    k1 = k6 = k2 = k7 = None
     if stage_ms:
-        k1 = sum(t[0] for t in stage_ms) / len(stage_ms)
+        k7 = sum(t[3] for t in stage_ms) / len(stage_ms)
+        k1 = sum(t[0] for t in stage_ms) / len(stage_ms) - k7  # the stage includes the map pre-pass
         k6 = sum(t[1] for t in stage_ms) / len(stage_ms)
         k2 = sum(t[2] for t in stage_ms) / len(stage_ms)
     mma = launch.get("mma_grid", 0) > 0
     mma_samples = info.get("n_mma_samples", 0) if mma else 0
+    maps = bool(k7) and info.get("n_rf_maps", 0) > 0
     flops_all = algorithmic_flops(info, ph.n, moving)
-    # the Bloch kernel's share: every RF step and the samples it steps
+    # the Bloch kernel's share: the RF steps and samples it steps, and the
+    # maps it applies
     flops = flops_all - float(ph.n) * mma_samples * FLOPS_ADC_SAMPLE
+    if maps:
+        flops -= float(ph.n) * info["n_rf_map_steps"] * FLOPS_RF_STEP
+        flops += float(ph.n) * info["n_rf_map_runs"] * FLOPS_MAP_APPLY
     achieved = flops / (k1 / 1e3) / 1e12 if k1 else None
     kname = "bloch_motion_kernel" if moving else ("bloch_items_kernel" if grouped else "bloch_fp32_kernel")
     roofs = []
+    if maps:
+        mflops = float(ph.n) * info["n_rf_map_pulse_steps"] * FLOPS_MAP_STEP
+        roofs.append({"bound": "alu", "kernel": "rf_map_kernel", "achieved": mflops / (k7 / 1e3) / 1e12,
+                      "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                      "frac": mflops / (k7 / 1e3) / 1e12 / PEAK_FP32_TFLOPS, "traffic": None, "kernel_ms": k7,
+                      "algorithmic_flops_per_launch": mflops,
+                      "peak_source": "FP32 peak 148 SMs x 128 lanes x 2 x 2032 MHz (unit counts, max SM clock)",
+                      "pulses": info["n_rf_maps"], "pulse_steps": info["n_rf_map_pulse_steps"],
+                      "replaces_rf_steps": info["n_rf_map_steps"]})
     roof1 = {"bound": "alu", "kernel": f"{kname}<{launch['spins_per_thread']}>",
              "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
              "frac": (achieved / PEAK_FP32_TFLOPS) if achieved else None,

@@ -97,6 +97,13 @@ typedef struct {
                              products on the tensor cores (FP32 path)      */
     int64_t n_mma_runs;   /* ADC runs in those groups                       */
     int64_t n_mma_samples; /* ADC samples in those runs                     */
+    int64_t n_rf_maps;    /* repeated RF pulses taken by their maps (FP32
+                             path): distinct pulses (runs of RF steps that
+                             recur unchanged at least 3 times) ...          */
+    int64_t n_rf_map_runs;  /* ... their occurrences ...                    */
+    int64_t n_rf_map_steps; /* ... the RF steps of those occurrences ...     */
+    int64_t n_rf_map_pulse_steps; /* ... and the steps of the distinct pulses
+                             (what the map pre-pass steps per spin)          */
 } koma_sequence_info;
 
 /* gamma used by the library, rad/s/T. */
@@ -341,6 +348,21 @@ koma_status koma_get_stage_timing(koma_ctx *ctx, float *bloch_ms, float *mma_ms,
  * KOMA_E_INVALID (NULL). */
 koma_status koma_set_mma(koma_ctx *ctx, int enable);
 
+/* Maps of repeated RF pulses on (enable != 0, the default) or off. On, the
+ * FP32 path of koma_simulate (static phantoms, Bloch kernel) first computes
+ * for every spin and every repeated pulse (koma_sequence_info.n_rf_maps) the
+ * affine map M -> A M + c of the whole pulse - the composition of its steps'
+ * rotations (Eq. Rot_exc) and relaxations, stepped in FP32 by a pre-pass
+ * kernel (8 bytes x 6 per spin and pulse of scratch) - and the Bloch kernel
+ * applies it at each occurrence instead of stepping the pulse again. Off,
+ * every RF step is stepped. Errors: KOMA_E_INVALID (NULL). */
+koma_status koma_set_rf_maps(koma_ctx *ctx, int enable);
+
+/* Duration (ms) of the map pre-pass of the last timed koma_simulate on ctx
+ * (0 if that call had none; koma_get_stage_timing's bloch_ms includes it).
+ * Errors: KOMA_E_INVALID (NULL, or no timed call yet), KOMA_E_CUDA. */
+koma_status koma_get_map_timing(koma_ctx *ctx, float *maps_ms);
+
 /* Launch description of the last koma_simulate or koma_simulate_static on
  * ctx (after a static call, koma_get_timing reports no timed call: that entry
  * point records no stage events). */
@@ -365,17 +387,24 @@ koma_status koma_simulate_host(koma_ctx *ctx, int64_t n,
  * Serving: a continuous-batching simulation server.
  *
  * Not in the paper: a deployment form of the same simulation. A server owns
- * a worker thread on one device. Submitted requests (host phantom + host
- * sequence, same arrays and checks as koma_phantom_upload without groups and
+ * worker threads on one device. Submitted requests (host phantom, optionally
+ * grouped, + host sequence: the arrays and checks of koma_phantom_upload and
  * koma_sequence_upload) are admitted in arrival order while the server's
- * device-memory budget allows; admitted requests share launches of one
- * persistent kernel that steps 512-spin batches of every request (shortest
- * remaining work first, two launches in flight), so requests arriving while
- * others run join within one launch. A batch walks its sequence in chunks of
- * step records, its spin state checkpointed in device memory between
- * launches, so a long simulation never holds the GPU for long. A request's result (KOMA_FP32_SPLITPHASE
- * arithmetic) does not depend on the other requests: it is bitwise the same
- * alone and in any mix.
+ * device-memory budget allows. Two lanes share the GPU:
+ *   - small ungrouped requests share launches of one persistent kernel that
+ *     steps 512-spin batches of every admitted request (shortest remaining
+ *     work first, two launches in flight), so requests arriving while others
+ *     run join within one launch. A batch walks its sequence in chunks of
+ *     step records, its spin state checkpointed in device memory between
+ *     launches, so a long simulation never holds the GPU for long; repeated
+ *     RF pulses are applied through their maps;
+ *   - requests with at least `plain_spins` spins (they fill the GPU alone)
+ *     and grouped requests (a dictionary: one signal per group) run, one at a
+ *     time and concurrently with the shared launches, the koma_simulate path
+ *     on their own stream (maps of repeated pulses, the tensor-core readout,
+ *     the grouped kernel).
+ * A request's result (KOMA_FP32_SPLITPHASE arithmetic) does not depend on
+ * the other requests: it is bitwise the same alone and in any mix.
  * ---------------------------------------------------------------------- */
 typedef struct koma_server koma_server;
 
@@ -387,6 +416,9 @@ typedef struct {
     int64_t chunk_records;   /* a batch walks at most this many step records per launch and is
                                 checkpointed between launches (long sequences do not hold the GPU);
                                 0 = 4096 */
+    int64_t plain_spins;     /* requests with at least this many spins run the koma_simulate
+                                path in the server's second lane; 0 = 262144, < 0 = never
+                                (grouped requests always do) */
 } koma_server_config;
 
 typedef struct {
@@ -394,32 +426,40 @@ typedef struct {
     int64_t n_spins, n_steps, n_adc;
     double submit_s, admit_s, done_s; /* seconds since the server started      */
     double latency_s;                 /* submit (incl. preprocessing) to result */
-    int32_t launches;                 /* kernel launches the request took part in */
+    int32_t launches;                 /* launches the request took part in (shared kernel launches,
+                                         or 1 for the koma_simulate lane)       */
     koma_status status;
+    int64_t n_groups;                 /* signal groups (1: ungrouped)           */
+    int32_t lane;                     /* 0: shared launches, 1: koma_simulate lane */
 } koma_request_info;
 
 typedef struct {
     int64_t submitted, completed, failed, pending, active, launches, batches;
     size_t mem_used, mem_peak;
+    int64_t lane_runs;  /* requests run by the koma_simulate lane */
 } koma_server_stats;
 
 /* Create a server (cfg NULL: device 0, defaults). Errors: KOMA_E_INVALID,
  * KOMA_E_CUDA (no device), KOMA_E_NOMEM. */
 koma_status koma_server_create(const koma_server_config *cfg, koma_server **out);
 
-/* Submit one simulation; validates and preprocesses on the calling thread
- * (host arrays are not kept), then returns its id. Thread-safe. Errors:
- * KOMA_E_INVALID (as the uploads; message via koma_server_last_error),
- * KOMA_E_BUSY (server shutting down). */
+/* Submit one simulation; validates and preprocesses on the calling thread,
+ * then returns its id. group_offsets / n_groups as koma_phantom_upload (NULL:
+ * one group). Requests of the shared lane keep no host arrays; those of the
+ * koma_simulate lane keep a copy until they are uploaded. Thread-safe.
+ * Errors: KOMA_E_INVALID (as the uploads; message via
+ * koma_server_last_error), KOMA_E_BUSY (server shutting down). */
 koma_status koma_server_submit(koma_server *srv, int64_t n, const double *x, const double *y,
                                const double *z, const double *pd, const double *t1,
-                               const double *t2, const double *dw, int64_t n_steps,
-                               const double *dt, const double *gx, const double *gy,
-                               const double *gz, const double *b1_re, const double *b1_im,
-                               const uint8_t *adc, uint64_t *id_out);
+                               const double *t2, const double *dw, const int64_t *group_offsets,
+                               int64_t n_groups, int64_t n_steps, const double *dt,
+                               const double *gx, const double *gy, const double *gz,
+                               const double *b1_re, const double *b1_im, const uint8_t *adc,
+                               uint64_t *id_out);
 
 /* Wait (timeout_s < 0: forever) for request `id`; on success writes its
- * signal to sig_host (host FP64 [n_adc][2], capacity >= n_adc entries) and
+ * signal to sig_host (host FP64 [n_groups][n_adc][2], capacity >= n_groups x
+ * n_adc entries) and
  * `info` (may be NULL), then forgets the request. Errors: KOMA_E_TIMEOUT
  * (still running; call again), KOMA_E_INVALID (unknown id or capacity),
  * KOMA_E_NOMEM (larger than the whole budget), KOMA_E_CUDA, KOMA_E_BUSY

@@ -32,6 +32,7 @@ enum RecType : int32_t {
     REC_RF = 0,     // one excitation step: rotate about the step's field, relax
     REC_PREC = 1,   // move t_ref: materialise the state at (K, tau), then K = tau = 0
     REC_ADC = 2,    // `count` samples at (K0 + l dK, tau0 + l dtau), l < count
+    REC_MAP = 3,    // a repeated pulse as a whole: apply map k0 (compacted streams only)
 };
 
 // largest number of samples in one ADC record (the recurrence between exact
@@ -78,6 +79,31 @@ struct MmaRun {
 };
 static_assert(sizeof(MmaRun) == 64, "MmaRun layout");
 
+// Repeated RF pulses. Every RF step maps the magnetisation affinely
+// (rotation about the step's constant field, then relaxation: M -> D R M + b
+// with D = diag(E2, E2, E1) and b = (0, 0, M0 (1 - E1))), so a whole run of
+// RF steps does too: M -> A M + c with A = D_N R_N ... D_1 R_1 and c the
+// run's response to M = 0 (the composition of the per-step updates of Eq.
+// Rot_exc and the relaxation equations, in exact arithmetic the same result
+// as stepping). A run of RF records that recurs unchanged (the same pulse
+// under the same gradient: the excitation and refocusing pulses of every
+// shot of a multi-shot sequence) gets a map slot: a pre-pass kernel computes
+// (A, c) per spin from the steps of the pulse, and the FP32 Bloch kernel
+// applies it at every occurrence instead of stepping the run. In the full
+// record stream the run's header carries k0 = 1 + slot (0: stepped); the
+// kernels that apply maps walk a compacted stream in which every such run is
+// one REC_MAP record (k0 = slot, count = the run's length).
+constexpr int kMaxRfMaps = 8;
+constexpr int kRfMapFloats = 12;     // A row-major (9 values), then c (3)
+constexpr int kRfMapMinRuns = 3;     // occurrences that make a map worth its pre-pass
+constexpr int kRfMapMinLen = 4;      // RF steps of a run worth a map
+struct RfMapPulse {
+    int64_t rec_begin;  // header record of the pulse's first occurrence
+    int32_t len;        // RF records of the run
+    int32_t pad_;
+};
+static_assert(sizeof(RfMapPulse) == 16, "RfMapPulse layout");
+
 // 64-byte record of the FP32 split-phase path.
 //   RF:   a[0..2] pi gbar gammabar dt (rad/m)   a[3..4] pi B1 gammabar dt (rad):
 //         the half-angle rotation vector of the step's field
@@ -90,6 +116,9 @@ static_assert(sizeof(MmaRun) == 64, "MmaRun layout");
 //   PREC/ADC: count = samples (ADC; low 16 bits) | nonzero-term bits << 16
 //         (bit 0 Kx, 1 Ky, 2 Kz, 3 tau), so the kernel skips zero phase terms
 //         without testing the payload.
+//   RF header records: k0 = 1 + the run's map slot when the run is a repeated
+//         pulse taken by its map, else 0.
+//   MAP:  (compacted streams) k0 = map slot, count = RF steps it stands for.
 struct alignas(16) Rec32 {
     int32_t type;
     int32_t count;
@@ -194,6 +223,24 @@ struct BlochArgs {
     // [n_snaps][n_pad] buffer (rows in record order)
     float2* mma_snap = nullptr;
     float mma_escale = 1.f;         // power of two keeping E in FP16 range
+    // repeated RF pulses (FP32 static kernel only): `rec` is then the
+    // compacted stream, whose REC_MAP records apply map k0 of this
+    // [n_rf_maps][kRfMapFloats][n_pad] buffer
+    const float* rf_maps = nullptr;
+    int n_rf_maps = 0;
+};
+
+// Pre-pass of the repeated-pulse maps: for every spin j < n and pulse p,
+// (A, c) of pulse p's RF records into maps[p][0..11][j].
+struct RfMapArgs {
+    const float* p32 = nullptr;
+    int64_t n_pad = 0;
+    int64_t n = 0;
+    const Rec32* rec = nullptr;
+    const RfMapPulse* pulses = nullptr;
+    int n_pulses = 0;
+    float* maps = nullptr;          // [n_pulses][kRfMapFloats][n_pad]
+    float ext[4] = {0, 0, 0, 0};
 };
 
 // Tensor-core readout (K6): CTA c takes spins [c spins_per_cta, +spins_per_cta)
@@ -261,9 +308,9 @@ struct BatchDesc {
     float* state;                // [3][n_pad] checkpoint between chunks (null: one chunk)
     float ext[4];
     int used;
-    int pad0_;
+    int n_rf_maps;               // map slots of the request's repeated pulses (0: none)
     int64_t rf_hdr;              // header of the RF run rec_begin lies inside (-1: none)
-    int64_t pad1_;
+    const float* rf_maps;        // [n_rf_maps][kRfMapFloats][n_pad]; `rec` is then compacted
 };
 static_assert(sizeof(BatchDesc) == 128, "BatchDesc layout");
 
@@ -284,6 +331,13 @@ int host_phantom32(int64_t n, const double* x, const double* y, const double* z,
 int host_records32(int64_t n_steps, const double* dt, const double* gx, const double* gy, const double* gz,
                    const double* b1_re, const double* b1_im, const uint8_t* adc, std::vector<Rec32>& r32,
                    koma_sequence_info& info, std::string& err);
+// Repeated RF pulses of a record stream: marks the header records of the
+// runs taken by maps (k0 = 1 + slot) and returns the slots' pulses; `info`
+// gets the n_rf_map* counts.
+void host_rf_maps32(std::vector<Rec32>& r32, std::vector<RfMapPulse>& pulses, koma_sequence_info& info);
+// The compacted stream of a marked one: every run taken by a map becomes
+// one REC_MAP record; everything else is copied.
+void compact_records32(const std::vector<Rec32>& r32, std::vector<Rec32>& out);
 
 // Launch helpers (koma_kernels.cu). Return a cudaError_t as int.
 // Phantom conversion: p64 [P64_N][n_pad] holds the raw rows x, y, z, dw
@@ -308,6 +362,8 @@ int launch_bloch_fp64_motion(const BlochArgs& a, const BlochLaunch& L, void* str
 int motion_ctas_per_sm(int block);
 // Tensor-core readout: `grid` CTAs of the kernel's fixed shape (one per SM).
 int launch_readout_mma(const MmaArgs& a, int grid, void* stream);
+// Repeated-pulse maps (one launch for all pulses).
+int launch_rf_maps(const RfMapArgs& a, void* stream);
 constexpr int kMotionSpinsPerThread = 2;
 int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream);
 // One thread waits, bounded by limit_ns, on an mbarrier nothing completes,

@@ -196,6 +196,22 @@ __device__ __forceinline__ float reduce_scatter8(float (&a)[kV], int lane) {
     return a[0];
 }
 
+// Compensated FP32 accumulation (Knuth's TwoSum per addition: s + x = t + e
+// exactly, with t the rounded sum; the errors e are collected in c). The
+// total s + c is exact up to c's own rounding, about n 2^-48 of the sum of
+// magnitudes for n terms, instead of the n 2^-24 of a plain FP32 chain.
+struct TwoSumAcc {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        const float z = t - s;
+        c += (s - (t - z)) + (x - z);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return static_cast<double>(s) + static_cast<double>(c); }
+    __device__ __forceinline__ float value32() const { return s + c; }
+};
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -348,6 +364,24 @@ struct Spins {
                 st[j] = mx[s];
                 st[np + j] = my[s];
                 st[2 * np + j] = mz[s];
+            }
+        }
+    }
+
+    // A repeated pulse taken by its map: M <- A M + c per spin, (A, c) row j
+    // of the map buffer mp [kRfMapFloats][np] (A row-major, then c).
+    __device__ __forceinline__ void apply_map(const float* __restrict__ mp, int64_t np) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int64_t j = index(s);
+            if (j < end) {
+                float a[kRfMapFloats];
+#pragma unroll
+                for (int k = 0; k < kRfMapFloats; ++k) a[k] = mp[k * np + j];
+                const float x = mx[s], y = my[s], z = mz[s];
+                mx[s] = fmaf(a[0], x, fmaf(a[1], y, fmaf(a[2], z, a[9])));
+                my[s] = fmaf(a[3], x, fmaf(a[4], y, fmaf(a[5], z, a[10])));
+                mz[s] = fmaf(a[6], x, fmaf(a[7], y, fmaf(a[8], z, a[11])));
             }
         }
     }
@@ -728,7 +762,12 @@ __device__ __forceinline__ void issue_tile(Rec32 (*s_rec)[T], const Bars& bar, c
 //   PREC replace M(t_ref) by M(t) at the given (K, tau).
 //   ADC  `count` samples (Spins::adc).
 // Warp sample sums are staged per warp in shared memory and summed over
-// warps in a fixed order into one FP32 partial per (CTA, sample).
+// warps in a fixed order (compensated) into one FP32 partial per (CTA,
+// sample). Within a warp the sum over its 32 S spins is a fixed binary tree
+// (the S spins of a thread, then the butterfly) of depth log2(32 S): its
+// error is at most that depth times 2^-24 of the sum of magnitudes, however
+// many spins the launch has; every longer chain of additions (over warps,
+// CTAs) is compensated.
 // ---------------------------------------------------------------------------
 template <int S, bool SPLIT>
 __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_constant__ BlochArgs A) {
@@ -787,13 +826,14 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
         const int cnt = static_cast<int>(red_end - red_base);
         for (int i = tid; i < cnt; i += nthr) {
             if (SPLIT && !s_own[red_buf][i]) continue;
-            float sr = 0.f, si = 0.f;
+            // the warps' sums added by TwoSum: the CTA's total is rounded once
+            TwoSumAcc sr, si;
             for (int w = 0; w < nwarps; ++w) {
                 const float2 v = red_slot(red_buf, w, i);
-                sr += v.x;
-                si += v.y;
+                sr.add(v.x);
+                si.add(v.y);
             }
-            partial[red_base + i] = make_float2(sr, si);
+            partial[red_base + i] = make_float2(sr.value32(), si.value32());
         }
         red_buf ^= 1;
         red_base = red_end;
@@ -831,6 +871,9 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
             const int type = R.type;
             if (type == REC_RF) {
                 sp.rf(R, A.ext);
+            } else if (type == REC_MAP) {
+                // a repeated pulse as a whole (compacted stream)
+                sp.apply_map(A.rf_maps + R.k0 * kRfMapFloats * np, np);
             } else if (type == REC_PREC) {
                 float er[S], ei[S];
                 sp.exact(R, true, A.p32, np, A.used, er, ei);
@@ -883,6 +926,228 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
     if (red_end > red_base) flush();
 }
 
+// ---------------------------------------------------------------------------
+// K7: maps of repeated RF pulses (pre-pass of K1).
+//
+// For pulse p (a run of RF records that recurs unchanged) and spin j the
+// whole run is the affine map M -> A M + c, the composition of its steps
+// (rotation about the step's field by the quaternion of the Bloch kernel's
+// RF step, then relaxation). The kernel steps the three columns of A (from
+// the unit vectors, relaxation without the recovery term) and c (from
+// M = 0, with it) through the pulse's records, two spins per thread in
+// packed FP32 pairs, and writes maps[p][k][j] (A row-major, then c). The
+// rotation path per run follows the Bloch kernel: cos and sin(t)/t by their
+// even series when the run's largest half angle allows it (bound from the
+// run header's maxima and the phantom's extents), else rsqrt and sin/cos of
+// pi x after exact reduction; the quaternion is renormalised to first order
+// on every path.
+//
+// Precision: A is applied at every occurrence of the pulse, so its rounding
+// error repeats identically shot after shot and adds up through the T1
+// memory of the magnetisation, where the rounding of stepped pulses differs
+// from shot to shot. The columns of A are therefore carried as unevaluated
+// FP32 pairs hi + lo: each step's increment (rotation and relaxation, small
+// next to the column for the small per-step angles of a soft pulse) is
+// computed in FP32 and added to hi by TwoSum, its rounding error going to
+// lo, and lo is rotated with the same quaternion. A's error is then that of
+// the increments themselves, far below one FP32 rounding of the column per
+// step. c (of the order of the recovery over one pulse) needs no pair.
+// ---------------------------------------------------------------------------
+constexpr int kMapChunk = 128;   // records staged in shared memory at a time
+constexpr int kMapBlock = 256;
+
+struct MapPair {
+    f32x2 X, Y, Z, F, M0, R1, R2;  // spin parameters of the pair
+    f32x2 E1, E2;                   // relaxation factors minus one over dt_cached
+    float dt_cached;
+    f32x2 v[kRfMapFloats];          // columns of A (x, y, z parts), then c
+    f32x2 lo[9];                    // low parts of the columns of A
+
+    // One RF step of the pair: quaternion (w = ch, u), then the four
+    // vectors rotated and relaxed. NT: series terms (0: general path).
+    template <bool GRAD, int NT>
+    __device__ __forceinline__ void step(const Rec32& R) {
+        const float dt = R.a[6];
+        if (dt != dt_cached) {
+            float r1a, r1b, r2a, r2b;
+            unpk(R1, r1a, r1b);
+            unpk(R2, r2a, r2b);
+            const float k = -dt * 0.693147180559945309f;
+            E1 = pk(expm1_f32(k * r1a), expm1_f32(k * r1b));
+            E2 = pk(expm1_f32(k * r2a), expm1_f32(k * r2b));
+            dt_cached = dt;
+        }
+        const float pdt = dt * 3.14159265358979323846f;
+        f32x2 az = mul2(F, pk(pdt, pdt));
+        if constexpr (GRAD)
+            az = fma2(pk(R.a[0], R.a[0]), X, fma2(pk(R.a[1], R.a[1]), Y, fma2(pk(R.a[2], R.a[2]), Z, az)));
+        const float b2 = R.a[5];
+        const f32x2 t2 = fma2(az, az, pk(b2, b2));
+        f32x2 nsinc, ch;
+        if constexpr (NT == 0) {
+            float ta, tb, sa, ca, sb, cb;
+            unpk(t2, ta, tb);
+            const float ra = rsqrtf(ta), rb = rsqrtf(tb);
+            sincospi_f32(ta * ra * 0.318309886183790671538f, &sa, &ca);
+            sincospi_f32(tb * rb * 0.318309886183790671538f, &sb, &cb);
+            nsinc = pk(-sa * ra, -sb * rb);
+            ch = pk(ca, cb);
+        } else if constexpr (NT == 1) {
+            nsinc = fma2(t2, pk(1.66666666666666667e-1f, 1.66666666666666667e-1f), pk(-1.0f, -1.0f));
+            ch = fma2(t2, pk(-0.5f, -0.5f), pk(1.0f, 1.0f));
+        } else if constexpr (NT == 2) {
+            const f32x2 q = fma2(t2, pk(-8.33333333333333333e-3f, -8.33333333333333333e-3f),
+                                 pk(1.66666666666666667e-1f, 1.66666666666666667e-1f));
+            nsinc = fma2(q, t2, pk(-1.0f, -1.0f));
+            const f32x2 c = fma2(t2, pk(4.16666666666666667e-2f, 4.16666666666666667e-2f), pk(-0.5f, -0.5f));
+            ch = fma2(c, t2, pk(1.0f, 1.0f));
+        } else {
+            f32x2 q = fma2(t2, pk(-2.75573192239858907e-6f, -2.75573192239858907e-6f),
+                           pk(1.98412698412698413e-4f, 1.98412698412698413e-4f));
+            q = fma2(q, t2, pk(-8.33333333333333333e-3f, -8.33333333333333333e-3f));
+            q = fma2(q, t2, pk(1.66666666666666667e-1f, 1.66666666666666667e-1f));
+            nsinc = fma2(q, t2, pk(-1.0f, -1.0f));
+            f32x2 c = fma2(t2, pk(-2.75573192239858907e-7f, -2.75573192239858907e-7f),
+                           pk(2.48015873015873016e-5f, 2.48015873015873016e-5f));
+            c = fma2(c, t2, pk(-1.38888888888888889e-3f, -1.38888888888888889e-3f));
+            c = fma2(c, t2, pk(4.16666666666666667e-2f, 4.16666666666666667e-2f));
+            c = fma2(c, t2, pk(-0.5f, -0.5f));
+            ch = fma2(c, t2, pk(1.0f, 1.0f));
+        }
+        const f32x2 ux = mul2(pk(R.a[3], R.a[3]), nsinc), uy = mul2(pk(R.a[4], R.a[4]), nsinc);
+        const f32x2 uz = mul2(az, nsinc);
+        const f32x2 nux = neg2(ux), nuy = neg2(uy), nuz = neg2(uz);
+        // 2 / |q|^2 to first order: the map is applied many times, so its
+        // rotation part is kept orthogonal to FP32 rounding on every path
+        const f32x2 nq = fma2(ch, ch, fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))));
+        const f32x2 c2 = fma2(pk(-2.f, -2.f), nq, pk(4.f, 4.f));
+        // rotation increment c2 (w (u x m) + u x (u x m)) of a vector m
+        auto incr = [&](f32x2 MX, f32x2 MY, f32x2 MZ, f32x2& dx, f32x2& dy, f32x2& dz) {
+            const f32x2 px = fma2(uy, MZ, mul2(nuz, MY));
+            const f32x2 py = fma2(uz, MX, mul2(nux, MZ));
+            const f32x2 pz = fma2(ux, MY, mul2(nuy, MX));
+            const f32x2 qx = fma2(uy, pz, mul2(nuz, py));
+            const f32x2 qy = fma2(uz, px, mul2(nux, pz));
+            const f32x2 qz = fma2(ux, py, mul2(nuy, px));
+            dx = mul2(c2, fma2(ch, px, qx));
+            dy = mul2(c2, fma2(ch, py, qy));
+            dz = mul2(c2, fma2(ch, pz, qz));
+        };
+        // hi + lo += d for one component: TwoSum, the error into lo
+        auto acc = [](f32x2& h, f32x2& l, f32x2 d) {
+            const f32x2 t = add2(h, d);
+            const f32x2 z = sub2(t, h);
+            l = add2(l, add2(sub2(h, sub2(t, z)), sub2(d, z)));
+            h = t;
+        };
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            // columns of A: rotated and relaxed (no recovery term); the
+            // increment m' - m = d + E (m + d) is added to hi by TwoSum
+            f32x2 dx, dy, dz;
+            incr(v[3 * q], v[3 * q + 1], v[3 * q + 2], dx, dy, dz);
+            dx = fma2(E2, add2(v[3 * q], dx), dx);
+            dy = fma2(E2, add2(v[3 * q + 1], dy), dy);
+            dz = fma2(E1, add2(v[3 * q + 2], dz), dz);
+            f32x2 lx, ly, lz;
+            incr(lo[3 * q], lo[3 * q + 1], lo[3 * q + 2], lx, ly, lz);
+            lo[3 * q] = add2(lo[3 * q], lx);
+            lo[3 * q + 1] = add2(lo[3 * q + 1], ly);
+            lo[3 * q + 2] = add2(lo[3 * q + 2], lz);
+            acc(v[3 * q], lo[3 * q], dx);
+            acc(v[3 * q + 1], lo[3 * q + 1], dy);
+            acc(v[3 * q + 2], lo[3 * q + 2], dz);
+        }
+        {
+            // c: Mxy relaxed, Mz + E1 (Mz - M0)
+            f32x2 dx, dy, dz;
+            incr(v[9], v[10], v[11], dx, dy, dz);
+            const f32x2 nx = add2(v[9], dx), ny = add2(v[10], dy), nz = add2(v[11], dz);
+            v[9] = fma2(E2, nx, nx);
+            v[10] = fma2(E2, ny, ny);
+            v[11] = fma2(E1, sub2(nz, M0), nz);
+        }
+    }
+};
+
+template <bool GRAD, int NT>
+__device__ __forceinline__ void map_chunk(MapPair& m, const Rec32* s_rec, int n) {
+    for (int r = 0; r < n; ++r) m.template step<GRAD, NT>(s_rec[r]);
+}
+
+__global__ void __launch_bounds__(kMapBlock) rf_map_kernel(const __grid_constant__ RfMapArgs A) {
+    __shared__ __align__(16) Rec32 s_rec[kMapChunk];
+    const int tid = threadIdx.x;
+    const RfMapPulse P = A.pulses[blockIdx.y];
+    const int64_t np = A.n_pad;
+    const int64_t j0 = static_cast<int64_t>(blockIdx.x) * (2 * kMapBlock) + tid, j1 = j0 + kMapBlock;
+    const bool v0 = j0 < A.n, v1 = j1 < A.n;
+    const float* __restrict__ Pp = A.p32;
+    auto ld = [&](int row, int64_t j, bool v) { return v ? Pp[row * np + j] : 0.f; };
+    MapPair m;
+    m.X = pk(ld(P32_XH, j0, v0), ld(P32_XH, j1, v1));
+    m.Y = pk(ld(P32_YH, j0, v0), ld(P32_YH, j1, v1));
+    m.Z = pk(ld(P32_ZH, j0, v0), ld(P32_ZH, j1, v1));
+    m.F = pk(ld(P32_FH, j0, v0), ld(P32_FH, j1, v1));
+    m.M0 = pk(ld(P32_M0, j0, v0), ld(P32_M0, j1, v1));
+    m.R1 = pk(ld(P32_R1, j0, v0), ld(P32_R1, j1, v1));
+    m.R2 = pk(ld(P32_R2, j0, v0), ld(P32_R2, j1, v1));
+    m.dt_cached = -1.f;
+    m.E1 = m.E2 = pk(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < kRfMapFloats; ++k) m.v[k] = pk(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m.lo[k] = pk(0.f, 0.f);
+    m.v[0] = m.v[4] = m.v[8] = pk(1.f, 1.f);  // identity columns
+
+    // rotation path of the run, from its header (as the Bloch kernel's set_mode)
+    const Rec32 H = A.rec[P.rec_begin];
+    const float mb = H.a[7], mgx = H.a[8], mgy = H.a[9], mgz = H.a[10], mdt = H.a[11];
+    const float bound = mb + mgx * A.ext[0] + mgy * A.ext[1] + mgz * A.ext[2] +
+                        mdt * 3.14159265358979323846f * A.ext[3];
+    const bool grad = (mgx != 0.f && A.ext[0] != 0.f) || (mgy != 0.f && A.ext[1] != 0.f) ||
+                      (mgz != 0.f && A.ext[2] != 0.f);
+    const int nt = bound > 0.754f ? 0 : bound <= 0.015f ? 1 : bound <= 0.1f ? 2 : 4;
+
+    const uint4* __restrict__ src = reinterpret_cast<const uint4*>(A.rec + P.rec_begin);
+    uint4* dst = reinterpret_cast<uint4*>(s_rec);
+    for (int c0 = 0; c0 < P.len; c0 += kMapChunk) {
+        const int n = min(kMapChunk, P.len - c0);
+        __syncthreads();  // the previous chunk's reads are done
+        for (int i = tid; i < n * 4; i += kMapBlock) dst[i] = src[static_cast<int64_t>(c0) * 4 + i];
+        __syncthreads();
+        if (grad) {
+            switch (nt) {
+                case 0: map_chunk<true, 0>(m, s_rec, n); break;
+                case 1: map_chunk<true, 1>(m, s_rec, n); break;
+                case 2: map_chunk<true, 2>(m, s_rec, n); break;
+                default: map_chunk<true, 4>(m, s_rec, n); break;
+            }
+        } else {
+            switch (nt) {
+                case 0: map_chunk<false, 0>(m, s_rec, n); break;
+                case 1: map_chunk<false, 1>(m, s_rec, n); break;
+                case 2: map_chunk<false, 2>(m, s_rec, n); break;
+                default: map_chunk<false, 4>(m, s_rec, n); break;
+            }
+        }
+    }
+    // A[i][k] = i-th part of column k; c last
+    float* __restrict__ out = A.maps + static_cast<int64_t>(blockIdx.y) * kRfMapFloats * np;
+    float a0[kRfMapFloats], a1[kRfMapFloats];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) unpk(add2(m.v[3 * k + i], m.lo[3 * k + i]), a0[3 * i + k], a1[3 * i + k]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) unpk(m.v[9 + i], a0[9 + i], a1[9 + i]);
+#pragma unroll
+    for (int k = 0; k < kRfMapFloats; ++k) {
+        if (v0) out[k * np + j0] = a0[k];
+        if (v1) out[k * np + j1] = a1[k];
+    }
+}
+
 // One batch of a persistent kernel: every warp of the CTA steps its own spin
 // range [wb, we) of one phantom through records [rb, re) of one record
 // stream (TMA tiles shared by the CTA, restarted per batch; `g0` counts the
@@ -897,7 +1162,8 @@ __device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const BarPair 
                                            const float* __restrict__ p32, int64_t np, const Rec32* grec,
                                            int64_t n_rec, int64_t rb, int64_t re, float* state, int64_t rf_hdr,
                                            const float (&ext)[4], int used, int64_t wb, int64_t we,
-                                           float2* __restrict__ row, int* status, float* warp_lo) {
+                                           float2* __restrict__ row, int* status, float* warp_lo,
+                                           const float* rf_maps = nullptr) {
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const Rec32* base = grec + rb;
@@ -946,6 +1212,9 @@ __device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const BarPair 
             const int type = R.type;
             if (type == REC_RF) {
                 sp.rf(R, ext);
+            } else if (type == REC_MAP) {
+                // a repeated pulse as a whole (compacted stream)
+                sp.apply_map(rf_maps + R.k0 * kRfMapFloats * np, np);
             } else if (type == REC_PREC) {
                 float er[S], ei[S];
                 sp.exact(R, true, p32, np, used, er, ei);
@@ -1056,7 +1325,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_batches_kernel(const __gri
         float2* row = D.rows + static_cast<int64_t>(warp) * D.n_adc;
         const float ext[4] = {D.ext[0], D.ext[1], D.ext[2], D.ext[3]};
         if (!walk_batch<S>(s_rec, bar, g0, D.p32, D.n_pad, D.rec, D.n_rec, D.rec_begin, D.rec_end, D.state,
-                           D.rf_hdr, ext, D.used, wb, we, row, A.status, s_lo_w + warp * (4 * S * 32)))
+                           D.rf_hdr, ext, D.used, wb, we, row, A.status, s_lo_w + warp * (4 * S * 32), D.rf_maps))
             return;
     }
 }
@@ -1434,13 +1703,14 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_motion_kernel(const __grid
         const int cnt = static_cast<int>(red_end - red_base);
         for (int i = tid; i < cnt; i += nthr) {
             if (SPLIT && !s_own[red_buf][i]) continue;
-            float sr = 0.f, si = 0.f;
+            // the warps' sums added by TwoSum: the CTA's total is rounded once
+            TwoSumAcc sr, si;
             for (int w = 0; w < nwarps; ++w) {
                 const float2 v = red_slot(red_buf, w, i);
-                sr += v.x;
-                si += v.y;
+                sr.add(v.x);
+                si.add(v.y);
             }
-            partial[red_base + i] = make_float2(sr, si);
+            partial[red_base + i] = make_float2(sr.value32(), si.value32());
         }
         red_buf ^= 1;
         red_base = red_end;
@@ -1671,10 +1941,15 @@ __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_cons
 //   8 B warps wait for the same "empty" and "staged", write the rotator
 //   slices of stage i & 1 and arrive on "full";
 //   one MMA warp waits for "full", issues block i's 12 MMAs into accumulator
-//   buffer (group & 1) and commits them to "empty";
-//   after a group's last block the E warps read the accumulator from tensor
-//   memory into the CTA's partial row and release the buffer ("accumulator
-//   read").
+//   buffer (segment & 1) and commits them to "empty" (a group's blocks form
+//   segments of kMmaSegBlocks, numbered across groups);
+//   after a segment's last block the E warps read its accumulator from
+//   tensor memory and release the buffer ("accumulator read"): they add it
+//   into the group's running sum, kept in tensor memory as an FP32 pair
+//   (sum, error) by TwoSum, and after the group's last segment write the
+//   compensated total into the CTA's partial row. The FP32 accumulation of
+//   the tensor core thus runs over at most 12 kMmaSegBlocks products per
+//   element, and the sum over segments is exact up to its final rounding.
 // Every wait is bounded; a wait that gives up stops every role.
 // Operand slices: 128 rows x 16 FP16 (4 KB), K-major without swizzle: 8-row
 // x 16-byte core matrices, K-adjacent ones 128 B apart, row-adjacent ones
@@ -1694,7 +1969,14 @@ constexpr int kMmaParams = 9;
 constexpr int kMmaStageIn = kMmaStageE + kMmaParams * kMmaChunk * 4;
 constexpr int kMmaStageInPad = (kMmaStageIn + 127) / 128 * 128;
 constexpr int kMmaStaging = 4;                      // staging buffers (the loader runs up to 4 blocks ahead)
-constexpr uint32_t kMmaTmemCols = 256;              // two FP32 accumulators of 128 lanes x 128 columns
+// Tensor memory: two FP32 accumulators of 128 lanes x 128 columns (the MMAs
+// of one segment of kMmaSegBlocks blocks go into one while the other is
+// drained), then the group's running sum of its drained segments as an
+// unevaluated FP32 pair (sum, error) of 128 columns each.
+constexpr uint32_t kMmaTmemCols = 512;
+constexpr uint32_t kMmaSumCol = 256;                // running sum of the group
+constexpr uint32_t kMmaErrCol = 384;                // its accumulated rounding errors
+constexpr int kMmaSegBlocks = 8;                    // blocks accumulated in FP32 before a drain
 constexpr size_t kMmaDynSmem = 2 * kMmaStageBytes + kMmaStaging * kMmaStageInPad + 256;  // one CTA per SM
 
 // byte offset of the 16-byte row word (row, K group kg of 8 elements) in a slice
@@ -1736,6 +2018,24 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// 4 FP32 columns of this warp's 32 TMEM lanes: load, store
+__device__ __forceinline__ void tc_ld4(uint32_t taddr, float (&v)[4]) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = __uint_as_float(r[q]);
+}
+__device__ __forceinline__ void tc_st4(uint32_t taddr, const float (&v)[4]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3]))
+                 : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // v = hi + lo as FP16 pairs (a in the low half)
 __device__ __forceinline__ void split_half2(float a, float b, uint32_t& hi, uint32_t& lo) {
     const __half2 h = __floats2half2_rn(a, b);
@@ -2037,12 +2337,13 @@ __global__ void __launch_bounds__(kMmaCtaThreads, 1) readout_mma_kernel(const __
     const uint32_t tmem = *s_taddr;
 
     if (warp == kMmaWarp) {
-        // ---- MMA issuer: block it into accumulator buffer (its group) & 1
-        int gi = 0, ch = 0;
+        // ---- MMA issuer: block it into accumulator buffer (its segment) & 1
+        int ch = 0, sg = 0;
         for (int it = 0; it < n_it; ++it) {
             const int st = it & 1;
+            const bool seg_first = ch % kMmaSegBlocks == 0;
             bool w = true;
-            if (ch == 0 && gi >= 2) w = mbar_wait_bounded(acc_free(gi & 1), ((gi - 2) >> 1) & 1);
+            if (seg_first && sg >= 2) w = mbar_wait_bounded(acc_free(sg & 1), ((sg - 2) >> 1) & 1);
             if (w) w = mbar_wait_bounded(full(st), (it >> 1) & 1);
             if (!__all_sync(kFull, w && !*s_abort)) {
                 if (lane == 0) *s_abort = 1;
@@ -2051,14 +2352,14 @@ __global__ void __launch_bounds__(kMmaCtaThreads, 1) readout_mma_kernel(const __
             tc_fence_after();
             if (lane == 0) {
                 const uint32_t base = smem_u32(s_mma + st * kMmaStageBytes);
-                const uint32_t d = tmem + static_cast<uint32_t>((gi & 1) * 128);
+                const uint32_t d = tmem + static_cast<uint32_t>((sg & 1) * 128);
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks) {
                     const uint64_t ah = mma_smem_desc(base + ks * kMmaTileBytes);
                     const uint64_t al = mma_smem_desc(base + (4 + ks) * kMmaTileBytes);
                     const uint64_t bh = mma_smem_desc(base + (8 + ks) * kMmaTileBytes);
                     const uint64_t bl = mma_smem_desc(base + (12 + ks) * kMmaTileBytes);
-                    tc_mma_f16(d, ah, bh, (ch > 0 || ks > 0) ? 1u : 0u);
+                    tc_mma_f16(d, ah, bh, (!seg_first || ks > 0) ? 1u : 0u);
                     tc_mma_f16(d, ah, bl, 1u);
                     tc_mma_f16(d, al, bh, 1u);
                 }
@@ -2066,10 +2367,8 @@ __global__ void __launch_bounds__(kMmaCtaThreads, 1) readout_mma_kernel(const __
                 *s_issued = it + 1;
             }
             __syncwarp();
-            if (++ch == n_chunks) {
-                ch = 0;
-                ++gi;
-            }
+            if ((ch + 1) % kMmaSegBlocks == 0 || ch + 1 == n_chunks) ++sg;
+            if (++ch == n_chunks) ch = 0;
         }
     } else if (warp >= kEWarps) {
         // ---- B-slice producers: the rotator powers of each block once its
@@ -2111,7 +2410,7 @@ __global__ void __launch_bounds__(kMmaCtaThreads, 1) readout_mma_kernel(const __
             }
         };
         for (int k = 0; k < 2 && k < n_it; ++k) stage_next(k);
-        int gi = 0, ch = 0;
+        int gi = 0, ch = 0, sg = 0;
         MmaGroup G = n_it > 0 ? A.groups[0] : MmaGroup{};
         // this thread's run of the E slices (run 4 warp + lane % 4 of the group)
         const int my_r = 4 * warp + (lane & 3);
@@ -2136,30 +2435,71 @@ __global__ void __launch_bounds__(kMmaCtaThreads, 1) readout_mma_kernel(const __
             mma_fill_e<kZ, kDF>(stage, in, my_run, my_r < G.n_runs, G.one_snap != 0, live, warp, lane);
             fence_proxy_async_smem();
             mbar_arrive(full(st));
-            if (++ch < n_chunks) continue;
-            // epilogue of the group: its last commit covers all its MMAs
+            const bool grp_last = ch + 1 == n_chunks;
+            if ((ch + 1) % kMmaSegBlocks != 0 && !grp_last) {
+                ++ch;
+                continue;
+            }
+            // drain of the segment: its last commit covers all its MMAs
             if (!mbar_wait_bounded(empty(st), (it >> 1) & 1) || *s_abort) {
                 *s_abort = 1;
                 break;
             }
             tc_fence_after();
+            const bool grp_first = ch < kMmaSegBlocks;
             const int quarter = warp & 3, cgrp = warp >> 2;
             const int row = 32 * quarter + lane, r = row >> 1, part = row & 1;
-            MmaRun run{0, 0, 0};
-            if (r < G.n_runs) run = A.runs[G.run0 + r];
+            const uint32_t lanes = static_cast<uint32_t>(32 * quarter) << 16;
+            int64_t run_k0 = 0;
+            int run_len = 0;
+            if (grp_last && r < G.n_runs) {
+                run_k0 = A.runs[G.run0 + r].k0;
+                run_len = A.runs[G.run0 + r].len;
+            }
+#pragma unroll 1
+            for (int cc = 0; cc < 32; cc += 4) {
+                const uint32_t col0 = static_cast<uint32_t>(32 * cgrp + cc);
+                float v[4], sm[4];
+                tc_ld4(tmem + lanes + static_cast<uint32_t>((sg & 1) * 128) + col0, v);
+                if (grp_first) {
+                    // the group's first segment: sum = v, error = 0
 #pragma unroll
-            for (int cc = 0; cc < 32; cc += 16) {
-                const int col0 = 32 * cgrp + cc;
-                uint32_t v[16];
-                tc_ld16(tmem + (static_cast<uint32_t>(32 * quarter) << 16) +
-                            static_cast<uint32_t>((gi & 1) * 128 + col0),
-                        v);
+                    for (int q = 0; q < 4; ++q) {
+                        sm[q] = v[q];
+                        v[q] = 0.f;
+                    }
+                } else {
+                    tc_ld4(tmem + lanes + kMmaSumCol + col0, sm);
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (col0 + q < run.len) out[2 * (run.k0 + col0 + q) + part] = __uint_as_float(v[q]) * A.einv;
+                    for (int q = 0; q < 4; ++q) {  // TwoSum: sm + v = t + e exactly; v <- e
+                        const float t = sm[q] + v[q];
+                        const float z = t - sm[q];
+                        v[q] = (sm[q] - (t - z)) + (v[q] - z);
+                        sm[q] = t;
+                    }
+                    float er[4];
+                    tc_ld4(tmem + lanes + kMmaErrCol + col0, er);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) v[q] += er[q];
+                }
+                if (grp_last) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int c = static_cast<int>(col0) + q;
+                        if (c < run_len) out[2 * (run_k0 + c) + part] = (sm[q] + v[q]) * A.einv;
+                    }
+                } else {
+                    tc_st4(tmem + lanes + kMmaSumCol + col0, sm);
+                    tc_st4(tmem + lanes + kMmaErrCol + col0, v);
+                }
             }
             tc_fence_before();
-            mbar_arrive(acc_free(gi & 1));
+            mbar_arrive(acc_free(sg & 1));
+            ++sg;
+            if (!grp_last) {
+                ++ch;
+                continue;
+            }
             ch = 0;
             if (++gi < A.n_groups) {
                 G = A.groups[gi];
@@ -2269,16 +2609,6 @@ __global__ void bounded_wait_check_kernel(int* status, unsigned long long limit_
 // the FP32 rate, and plain FP64 additions bounded this kernel (epi512 0.029
 // -> 0.010 ms). FP64 rows are added in FP64.
 // ---------------------------------------------------------------------------
-struct TwoSumAcc {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        const float t = s + x;
-        const float z = t - s;
-        c += (s - (t - z)) + (x - z);
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return static_cast<double>(s) + static_cast<double>(c); }
-};
 
 // rows c_lo, c_lo + c_step, ... < c_hi of column k, in that order
 __device__ __forceinline__ void strided_sum(const float2* __restrict__ part, int64_t n_adc, int64_t k, int c_lo,
@@ -2480,6 +2810,15 @@ int launch_bloch_motion(const BlochArgs& a, const BlochLaunch& L, void* stream) 
         bloch_motion_kernel<kMotionSpinsPerThread, true><<<L.grid, L.block, dyn, static_cast<cudaStream_t>(stream)>>>(a);
     else
         bloch_motion_kernel<kMotionSpinsPerThread, false><<<L.grid, L.block, dyn, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError();
+}
+
+int launch_rf_maps(const RfMapArgs& a, void* stream) {
+    if (a.n_pulses <= 0 || a.n_pulses > kMaxRfMaps || a.n <= 0) return cudaErrorInvalidValue;
+    const int64_t gx = (a.n + 2 * kMapBlock - 1) / (2 * kMapBlock);
+    if (gx > 0x7fffffff) return cudaErrorInvalidValue;
+    rf_map_kernel<<<dim3(static_cast<unsigned>(gx), static_cast<unsigned>(a.n_pulses)), kMapBlock, 0,
+                    static_cast<cudaStream_t>(stream)>>>(a);
     return cudaGetLastError();
 }
 

@@ -60,6 +60,9 @@ struct koma_ctx {
     bool timing_recorded = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool mma_enabled = true;  // koma_set_mma
+    bool rf_maps_enabled = true;  // koma_set_rf_maps
+    cudaEvent_t ev_maps = nullptr;  // after the map pre-pass (timing)
+    bool maps_timed = false;        // the last timed call ran the pre-pass
     // autotuner results by problem shape (see tune_key): launches of a shape
     // tuned once reuse the choice for other phantoms and sequences of that shape
     std::map<uint64_t, std::pair<int, int>> tune_cache;  // key -> (spins per thread, block)
@@ -122,6 +125,12 @@ struct koma_sequence {
     int32_t n_mma_groups = 0;
     int64_t n_mma_runs = 0;
     int64_t n_mma_snaps = 0;  // rows of the snapshot buffer
+    // repeated RF pulses (same device block): one entry per map slot, and the
+    // compacted record stream (each mapped run one REC_MAP record)
+    koma::RfMapPulse* d_rf_pulses = nullptr;
+    int32_t n_rf_maps = 0;
+    koma::Rec32* r32c = nullptr;
+    int64_t n_rec_c = 0;
 };
 
 namespace {
@@ -392,6 +401,7 @@ extern "C" koma_status koma_destroy(koma_ctx* ctx) {
     DeviceGuard g(ctx->device);
     for (cudaEvent_t& e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->ev_maps) cudaEventDestroy(ctx->ev_maps);
     if (ctx->scratch) dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     if (ctx->alloc_stream) cudaStreamDestroy(ctx->alloc_stream);
@@ -981,6 +991,79 @@ void plan_mma(std::vector<koma::Rec32>& r32, int64_t n_adc, MmaPlan& P) {
     }
 }
 
+// Repeated RF pulses: runs of consecutive RF records whose 64-byte records
+// are bitwise equal (the same pulse under the same gradient, so the same
+// per-spin map) are grouped; a group of at least kRfMapMinRuns runs of at
+// least kRfMapMinLen steps gets a map slot (at most kMaxRfMaps, the ones
+// saving the most steps first), and the header record of each of its runs
+// gets k0 = 1 + slot.
+struct RfMapPlan {
+    std::vector<koma::RfMapPulse> pulses;
+    int64_t runs = 0, steps = 0, pulse_steps = 0;
+};
+
+void plan_rf_maps(std::vector<koma::Rec32>& r32, RfMapPlan& P) {
+    struct Run {
+        size_t begin, len;
+    };
+    std::vector<Run> runs;
+    for (size_t i = 0; i < r32.size();) {
+        if (r32[i].type != koma::REC_RF) {
+            ++i;
+            continue;
+        }
+        size_t j = i;
+        while (j < r32.size() && r32[j].type == koma::REC_RF) ++j;
+        runs.push_back({i, j - i});
+        i = j;
+    }
+    auto same = [&](const Run& a, const Run& b) {
+        return a.len == b.len && std::memcmp(&r32[a.begin], &r32[b.begin], a.len * sizeof(koma::Rec32)) == 0;
+    };
+    // FNV-1a of the run's bytes buckets the candidates; equality is checked
+    // byte for byte
+    std::map<std::pair<uint64_t, size_t>, std::vector<std::vector<size_t>>> buckets;
+    for (size_t q = 0; q < runs.size(); ++q) {
+        if (runs[q].len < static_cast<size_t>(koma::kRfMapMinLen)) continue;
+        uint64_t h = 1469598103934665603ull;
+        const unsigned char* b = reinterpret_cast<const unsigned char*>(&r32[runs[q].begin]);
+        for (size_t k = 0; k < runs[q].len * sizeof(koma::Rec32); ++k) h = (h ^ b[k]) * 1099511628211ull;
+        auto& classes = buckets[{h, runs[q].len}];
+        bool placed = false;
+        for (auto& c : classes) {
+            if (same(runs[c[0]], runs[q])) {
+                c.push_back(q);
+                placed = true;
+                break;
+            }
+        }
+        if (!placed) classes.push_back({q});
+    }
+    std::vector<const std::vector<size_t>*> cand;
+    for (const auto& kv : buckets)
+        for (const auto& c : kv.second)
+            if (c.size() >= static_cast<size_t>(koma::kRfMapMinRuns)) cand.push_back(&c);
+    // most stepped RF steps saved first; ties by first occurrence
+    std::sort(cand.begin(), cand.end(), [&](const std::vector<size_t>* a, const std::vector<size_t>* b) {
+        const size_t sa = (a->size() - 1) * runs[(*a)[0]].len, sb = (b->size() - 1) * runs[(*b)[0]].len;
+        return sa != sb ? sa > sb : (*a)[0] < (*b)[0];
+    });
+    if (cand.size() > static_cast<size_t>(koma::kMaxRfMaps)) cand.resize(koma::kMaxRfMaps);
+    for (size_t slot = 0; slot < cand.size(); ++slot) {
+        const Run& first = runs[(*cand[slot])[0]];
+        koma::RfMapPulse p{};
+        p.rec_begin = static_cast<int64_t>(first.begin);
+        p.len = static_cast<int32_t>(first.len);
+        P.pulses.push_back(p);
+        P.pulse_steps += static_cast<int64_t>(first.len);
+        for (size_t q : *cand[slot]) {
+            r32[runs[q].begin].k0 = static_cast<int64_t>(slot) + 1;
+            P.runs += 1;
+            P.steps += static_cast<int64_t>(runs[q].len);
+        }
+    }
+}
+
 extern "C" koma_status koma_sequence_plan(int64_t n_steps, const double* dt, const double* gx, const double* gy,
                                           const double* gz, const double* b1_re, const double* b1_im,
                                           const uint8_t* adc, koma_sequence_info* info, double* rec_out,
@@ -995,6 +1078,12 @@ extern "C" koma_status koma_sequence_plan(int64_t n_steps, const double* dt, con
     info->n_mma_groups = static_cast<int64_t>(mp.groups.size());
     info->n_mma_runs = static_cast<int64_t>(mp.runs.size());
     info->n_mma_samples = mp.n_samples;
+    RfMapPlan fp;
+    plan_rf_maps(rb.r32, fp);
+    info->n_rf_maps = static_cast<int64_t>(fp.pulses.size());
+    info->n_rf_map_runs = fp.runs;
+    info->n_rf_map_steps = fp.steps;
+    info->n_rf_map_pulse_steps = fp.pulse_steps;
     if (rec_out) {
         if (rec_capacity < info->n_records) return KOMA_E_INVALID;
         for (int64_t r = 0; r < info->n_records; ++r) {
@@ -1038,14 +1127,23 @@ extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, cons
     seq->info.n_mma_groups = static_cast<int64_t>(mp.groups.size());
     seq->info.n_mma_runs = static_cast<int64_t>(mp.runs.size());
     seq->info.n_mma_samples = mp.n_samples;
+    RfMapPlan fp;
+    plan_rf_maps(rb.r32, fp);
+    seq->info.n_rf_maps = static_cast<int64_t>(fp.pulses.size());
+    seq->info.n_rf_map_runs = fp.runs;
+    seq->info.n_rf_map_steps = fp.steps;
+    seq->info.n_rf_map_pulse_steps = fp.pulse_steps;
+    std::vector<koma::Rec32> rc;
+    if (!fp.pulses.empty()) koma::compact_records32(rb.r32, rc);
     DeviceGuard g(ctx->device);
     auto up16 = [](size_t b) { return (b + 15) / 16 * 16; };
     const size_t b32 = rb.r32.size() * sizeof(koma::Rec32), b64 = rb.r64.size() * sizeof(koma::Rec64),
                  bm = rb.rm.size() * sizeof(koma::RecM), bg = mp.groups.size() * sizeof(koma::MmaGroup),
-                 br = mp.runs.size() * sizeof(koma::MmaRun), bf = up16(mp.from.size());
-    const size_t total = b32 + b64 + bm + bg + br + bf;
-    // one device block [Rec32 | Rec64 | RecM | MmaGroup | MmaRun | sample map]
-    // (each part 16-byte aligned) filled by one copy
+                 br = mp.runs.size() * sizeof(koma::MmaRun), bf = up16(mp.from.size()),
+                 bp = fp.pulses.size() * sizeof(koma::RfMapPulse), bc = rc.size() * sizeof(koma::Rec32);
+    const size_t total = b32 + b64 + bm + bg + br + bf + bp + bc;
+    // one device block [Rec32 | Rec64 | RecM | MmaGroup | MmaRun | sample map |
+    // RfMapPulse | compacted Rec32] (each part 16-byte aligned) filled by one copy
     koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r32), total, "sequence_upload");
     if (st == KOMA_OK && b32) {
         char* base = reinterpret_cast<char*>(seq->r32);
@@ -1059,6 +1157,12 @@ extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, cons
             seq->n_mma_runs = static_cast<int64_t>(mp.runs.size());
             seq->n_mma_snaps = mp.n_snaps;
         }
+        if (bp) {
+            seq->d_rf_pulses = reinterpret_cast<koma::RfMapPulse*>(base + b32 + b64 + bm + bg + br + bf);
+            seq->n_rf_maps = static_cast<int32_t>(fp.pulses.size());
+            seq->r32c = reinterpret_cast<koma::Rec32*>(base + b32 + b64 + bm + bg + br + bf + bp);
+            seq->n_rec_c = static_cast<int64_t>(rc.size());
+        }
         std::vector<char> host(total, 0);
         std::memcpy(host.data(), rb.r32.data(), b32);
         std::memcpy(host.data() + b32, rb.r64.data(), b64);
@@ -1066,6 +1170,8 @@ extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, cons
         if (bg) std::memcpy(host.data() + b32 + b64 + bm, mp.groups.data(), bg);
         if (br) std::memcpy(host.data() + b32 + b64 + bm + bg, mp.runs.data(), br);
         if (!mp.from.empty()) std::memcpy(host.data() + b32 + b64 + bm + bg + br, mp.from.data(), mp.from.size());
+        if (bp) std::memcpy(host.data() + b32 + b64 + bm + bg + br + bf, fp.pulses.data(), bp);
+        if (bc) std::memcpy(host.data() + b32 + b64 + bm + bg + br + bf + bp, rc.data(), bc);
         cudaError_t e = cudaMemcpy(seq->r32, host.data(), host.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) st = cuda_fail(ctx, e, "sequence_upload: copy");
     }
@@ -1260,6 +1366,8 @@ uint64_t tune_key(const koma_phantom* ph, const koma_sequence* seq, bool items) 
 // the tensor-core readout takes; beyond it the Bloch kernel samples every
 // run itself.
 constexpr size_t kMmaMaxEBytes = size_t{16} << 30;
+// Largest buffer of repeated-pulse maps (48 bytes per spin and pulse).
+constexpr size_t kRfMapMaxBytes = size_t{16} << 30;
 
 // ADC-run split for a launch whose spins fill few warps: CTAs sharing a
 // spin range each take every split-th ADC record (all of them step the RF
@@ -1337,6 +1445,7 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
             }
         }
         ctx->timing_recorded = false;
+        ctx->maps_timed = false;
         return simulate_items(ctx, ph, seq, sig_dev, st, S, block);
     }
     const bool tuned_k1 = ph->tuned_seq == seq && ph->tuned_n_rec == seq->info.n_records && ph->tuned_s > 0;
@@ -1445,11 +1554,38 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
         off_e = up256(off_rows + static_cast<size_t>(grid_mma) * static_cast<size_t>(n_adc) * sizeof(float2));
         need = off_e + e_bytes;
     }
+    // maps of repeated RF pulses (FP32 static Bloch kernel): scratch
+    // [n_maps][kRfMapFloats][n_pad] after the rest, at most kRfMapMaxBytes
+    const size_t map_bytes = static_cast<size_t>(koma::kRfMapFloats) * static_cast<size_t>(ph->n_pad) * sizeof(float);
+    int n_maps = 0;
+    size_t off_maps = 0;
+    // all of the sequence's maps or none (the compacted stream stands for all)
+    if (!fp64 && !moving && ctx->rf_maps_enabled && seq->n_rf_maps > 0 &&
+        static_cast<size_t>(seq->n_rf_maps) * map_bytes <= kRfMapMaxBytes) {
+        n_maps = seq->n_rf_maps;
+        off_maps = (need + 255) / 256 * 256;
+        need = off_maps + static_cast<size_t>(n_maps) * map_bytes;
+    }
     {
         koma_status s = grow_scratch(ctx, need, st);
         if (s != KOMA_OK) return s;
     }
     A.partial = ctx->scratch;
+    koma::RfMapArgs F;
+    if (n_maps > 0) {
+        F.p32 = ph->p32;
+        F.n_pad = ph->n_pad;
+        F.n = ph->n;
+        F.rec = seq->r32;
+        F.pulses = seq->d_rf_pulses;
+        F.n_pulses = n_maps;
+        F.maps = reinterpret_cast<float*>(static_cast<char*>(ctx->scratch) + off_maps);
+        for (int d = 0; d < 4; ++d) F.ext[d] = A.ext[d];
+        A.rf_maps = F.maps;
+        A.n_rf_maps = n_maps;
+        A.rec = seq->r32c;
+        A.n_rec = seq->n_rec_c;
+    }
     R.partial = ctx->scratch;
     R.grid = rows;
     R.sig = sig_dev;
@@ -1482,8 +1618,18 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     }
 
     ctx->timing_recorded = false;
+
+    ctx->maps_timed = false;
     if (ctx->timing) cudaEventRecord(ctx->ev[0], st);
     int e;
+    if (n_maps > 0) {
+        e = koma::launch_rf_maps(F, stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: pulse-map launch");
+        if (ctx->timing) {
+            cudaEventRecord(ctx->ev_maps, st);
+            ctx->maps_timed = true;
+        }
+    }
     if (moving)
         e = fp64 ? koma::launch_bloch_fp64_motion(A, L, stream) : koma::launch_bloch_motion(A, L, stream);
     else
@@ -1502,13 +1648,13 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
         ctx->timing_recorded = true;
     }
 
-    ctx->last.kernels = use_mma ? 3 : 2;
+    ctx->last.kernels = (use_mma ? 3 : 2) + (n_maps > 0 ? 1 : 0);
     ctx->last.mma_grid = grid_mma;
     ctx->last.grid = L.grid;
     ctx->last.block = L.block;
     ctx->last.spins_per_thread = L.spins_per_thread;
     ctx->last.spins_per_cta = L.spins_per_cta;
-    ctx->last.n_records = seq->info.n_records;
+    ctx->last.n_records = A.n_rec;
     ctx->last.partial_bytes = static_cast<int64_t>(need);
     ctx->last.split = split;
     return KOMA_OK;
@@ -1539,6 +1685,7 @@ extern "C" koma_status koma_simulate_static(const koma_phantom* ph, const koma_s
     ctx->last = koma_launch_info{};
     ctx->last.bloch_stream = stream;
     ctx->timing_recorded = false;
+    ctx->maps_timed = false;
     if (ph->n == 0) {
         cudaError_t e = cudaMemsetAsync(sig_dev, 0, static_cast<size_t>(n_adc) * 2 * sizeof(double), st);
         return e == cudaSuccess ? KOMA_OK : cuda_fail(ctx, e, "simulate_static: memset");
@@ -1697,9 +1844,12 @@ extern "C" koma_status koma_set_timing(koma_ctx* ctx, int enable) {
             cudaError_t r = cudaEventCreate(&e);
             if (r != cudaSuccess) return cuda_fail(ctx, r, "set_timing: event");
         }
+        cudaError_t r = cudaEventCreate(&ctx->ev_maps);
+        if (r != cudaSuccess) return cuda_fail(ctx, r, "set_timing: event");
     }
     ctx->timing = enable != 0;
     ctx->timing_recorded = false;
+    ctx->maps_timed = false;
     return KOMA_OK;
 }
 
@@ -1729,6 +1879,24 @@ extern "C" koma_status koma_get_stage_timing(koma_ctx* ctx, float* bloch_ms, flo
 extern "C" koma_status koma_set_mma(koma_ctx* ctx, int enable) {
     if (!ctx) return KOMA_E_INVALID;
     ctx->mma_enabled = enable != 0;
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_set_rf_maps(koma_ctx* ctx, int enable) {
+    if (!ctx) return KOMA_E_INVALID;
+    ctx->rf_maps_enabled = enable != 0;
+    return KOMA_OK;
+}
+
+extern "C" koma_status koma_get_map_timing(koma_ctx* ctx, float* maps_ms) {
+    if (!ctx || !maps_ms) return KOMA_E_INVALID;
+    if (!ctx->timing_recorded) return fail(ctx, KOMA_E_INVALID, "get_map_timing: no timed simulate call");
+    *maps_ms = 0.f;
+    if (!ctx->maps_timed) return KOMA_OK;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaEventSynchronize(ctx->ev[3]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(maps_ms, ctx->ev[0], ctx->ev_maps);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "get_map_timing");
     return KOMA_OK;
 }
 
@@ -1816,6 +1984,34 @@ int host_phantom32(int64_t n, const double* x, const double* y, const double* z,
         max_abs[3] = std::max(max_abs[3], std::fabs(dw[j]) / (2.0 * kPi));
     }
     return KOMA_OK;
+}
+
+void compact_records32(const std::vector<Rec32>& r32, std::vector<Rec32>& out) {
+    out.clear();
+    for (size_t i = 0; i < r32.size();) {
+        const Rec32& q = r32[i];
+        if (q.type == REC_RF && q.count > 0 && q.k0 > 0) {
+            Rec32 m{};
+            m.type = REC_MAP;
+            m.count = q.count;
+            m.k0 = q.k0 - 1;
+            out.push_back(m);
+            i += static_cast<size_t>(q.count);
+        } else {
+            out.push_back(q);
+            ++i;
+        }
+    }
+}
+
+void host_rf_maps32(std::vector<Rec32>& r32, std::vector<RfMapPulse>& pulses, koma_sequence_info& info) {
+    RfMapPlan fp;
+    plan_rf_maps(r32, fp);
+    pulses = fp.pulses;
+    info.n_rf_maps = static_cast<int64_t>(fp.pulses.size());
+    info.n_rf_map_runs = fp.runs;
+    info.n_rf_map_steps = fp.steps;
+    info.n_rf_map_pulse_steps = fp.pulse_steps;
 }
 
 int host_records32(int64_t n_steps, const double* dt, const double* gx, const double* gy, const double* gz,

@@ -1,7 +1,11 @@
 // Continuous-batching simulation server (native runtime of libkoma).
 //
 // Requests (a phantom and a sequence, host arrays) are validated and
-// preprocessed on the submitting thread, then one worker thread:
+// preprocessed on the submitting thread. Grouped requests and requests that
+// fill the GPU alone (at least plain_spins spins) go to the second lane: a
+// thread of their own that uploads them into a context of the server and
+// runs koma_simulate on its stream, one at a time, overlapping the shared
+// launches below. For the others, one worker thread:
 //   * admits them in arrival order while the device-memory budget allows
 //     (stream-ordered allocations from a server-owned pool, so a finishing
 //     request frees its memory without a device-wide synchronisation);
@@ -44,12 +48,12 @@ constexpr int64_t kBatchSpins = kWarps * 32 * 4;   // 4 spins per thread
 constexpr int kSlots = 2;
 constexpr size_t kHeader = 16;                     // int64 n_batches, int32 counter, pad
 
-enum ReqState { PENDING, ADMITTED, REDUCING, DONE, FAILED };
+enum ReqState { PENDING, ADMITTED, LANE, REDUCING, DONE, FAILED };
 
 struct Req {
     uint64_t id = 0;
     double t_submit = 0, t_admit = -1, t_done = -1;
-    int64_t n = 0, n_pad = 0, n_steps = 0, n_adc = 0, n_rec = 0;
+    int64_t n = 0, n_pad = 0, n_steps = 0, n_adc = 0, n_rec = 0, n_adc_runs = 0;
     std::vector<float> h32;
     std::vector<koma::Rec32> recs;
     double max_abs[4] = {0, 0, 0, 0};
@@ -62,6 +66,14 @@ struct Req {
     int64_t chunk = 0, n_chunks = 1, units_total = 0, units_done = 0;
     std::vector<double> chunk_work;   // work units per spin of each chunk
     std::vector<int64_t> chunk_hdr;   // RF run header a chunk starts inside, or -1
+    std::vector<int64_t> chunk_begin; // first record of each chunk, then n_rec
+    // repeated RF pulses: one map per slot, computed per spin at admission
+    // from the full record stream; `recs` is then the compacted stream
+    std::vector<koma::RfMapPulse> pulses;
+    std::vector<koma::Rec32> recs_full;
+    float* dmaps = nullptr;
+    koma::RfMapPulse* dpulses = nullptr;
+    koma::Rec32* drec_full = nullptr;
     std::vector<int32_t> batch_next;  // next chunk of each batch
     std::vector<char> batch_busy;     // batch is in a launch in flight
     double rem_work = 0;
@@ -77,6 +89,14 @@ struct Req {
     ReqState state = PENDING;
     koma_status err = KOMA_OK;
     std::string msg;
+    bool retired = false;  // out of the worker's lists: the waiter may delete it
+    // second lane (koma_simulate): the host arrays until the upload
+    bool lane = false;
+    int64_t n_groups = 1;
+    std::vector<double> ph64;         // x, y, z, pd, t1, t2, dw, each n long
+    std::vector<int64_t> offsets;     // group offsets (grouped requests)
+    std::vector<double> sq64;         // dt [n_steps], gx, gy, gz [n_steps + 1], b1 re, im [n_steps]
+    std::vector<uint8_t> sq_adc;
 
     double remaining_work() const { return rem_work; }
 };
@@ -104,6 +124,13 @@ double now_s() {
 struct koma_server {
     int device = 0;
     int64_t chunk = 4096;  // records per chunk of a batch's walk
+    int64_t plain_spins = 262144;  // requests this large run in the second lane (<= 0: never)
+    koma_ctx* lane_ctx = nullptr;  // the second lane's context and stream
+    cudaStream_t s_lane = nullptr;
+    std::thread lane_worker;
+    std::deque<Req*> lane_q;
+    std::condition_variable cv_lane;
+    int64_t lane_runs = 0;
     size_t budget = 0, used = 0, peak = 0;
     int max_active = 64;
     double launch_work = 0;  // work units per launch (cap)
@@ -143,12 +170,29 @@ koma_status cuda_err(koma_server* S, cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? KOMA_E_NOMEM : KOMA_E_CUDA;
 }
 
+size_t map_bytes(const Req* r) {
+    return r->pulses.size() * koma::kRfMapFloats * static_cast<size_t>(r->n_pad) * sizeof(float);
+}
+
 size_t req_bytes(const Req* r) {
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    if (r->lane) {
+        // koma_simulate lane: FP32 and FP64 phantom blocks, three record
+        // streams, per-CTA partial rows (at most a few thousand CTAs), the
+        // readout's snapshots (bounded by one row per ADC run) and the maps
+        const size_t np = static_cast<size_t>(r->n_pad);
+        return np * (koma::P32_N * sizeof(float) + koma::P64_N * sizeof(double)) +
+               static_cast<size_t>(r->n_rec) * 3 * sizeof(koma::Rec64) +
+               static_cast<size_t>(r->n_groups) * static_cast<size_t>(r->n_adc) * 16 +
+               static_cast<size_t>(4096) * static_cast<size_t>(r->n_adc) * sizeof(float2) +
+               static_cast<size_t>(r->n_adc_runs) * np * sizeof(float2) + map_bytes(r) + (size_t{1} << 20);
+    }
     return al(r->h32.size() * sizeof(float)) + al(r->recs.size() * sizeof(koma::Rec32)) +
            al(static_cast<size_t>(r->n_batches) * kWarps * r->n_adc * sizeof(float2)) +
            al(static_cast<size_t>(r->n_adc) * 2 * sizeof(double)) +
-           (r->n_chunks > 1 ? al(static_cast<size_t>(3 * r->n_pad) * sizeof(float)) : 0);
+           (r->n_chunks > 1 ? al(static_cast<size_t>(3 * r->n_pad) * sizeof(float)) : 0) +
+           (r->pulses.empty() ? 0 : al(map_bytes(r)) + al(r->pulses.size() * sizeof(koma::RfMapPulse)) +
+                                        al(r->recs_full.size() * sizeof(koma::Rec32)));
 }
 
 void fail_req(Req* r, koma_status st, const std::string& m) {
@@ -172,9 +216,38 @@ koma_status admit(koma_server* S, Req* r) {
     if (e == cudaSuccess && r->n_chunks > 1)
         e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dstate), static_cast<size_t>(3 * r->n_pad) * sizeof(float),
                                     S->pool, S->s_up);
+    if (e == cudaSuccess && !r->pulses.empty() && r->n > 0) {
+        e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dmaps), map_bytes(r), S->pool, S->s_up);
+        if (e == cudaSuccess)
+            e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dpulses),
+                                        r->pulses.size() * sizeof(koma::RfMapPulse), S->pool, S->s_up);
+        if (e == cudaSuccess)
+            e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->drec_full),
+                                        r->recs_full.size() * sizeof(koma::Rec32), S->pool, S->s_up);
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(r->d32, r->h32.data(), b32, cudaMemcpyHostToDevice, S->s_up);
     if (e == cudaSuccess && brec)
         e = cudaMemcpyAsync(r->drec, r->recs.data(), brec, cudaMemcpyHostToDevice, S->s_up);
+    if (e == cudaSuccess && r->dmaps) {
+        // the maps of the request's repeated pulses, before its first launch
+        e = cudaMemcpyAsync(r->dpulses, r->pulses.data(), r->pulses.size() * sizeof(koma::RfMapPulse),
+                            cudaMemcpyHostToDevice, S->s_up);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(r->drec_full, r->recs_full.data(), r->recs_full.size() * sizeof(koma::Rec32),
+                                cudaMemcpyHostToDevice, S->s_up);
+        if (e == cudaSuccess) {
+            koma::RfMapArgs F;
+            F.p32 = r->d32;
+            F.n_pad = r->n_pad;
+            F.n = r->n;
+            F.rec = r->drec_full;
+            F.pulses = r->dpulses;
+            F.n_pulses = static_cast<int>(r->pulses.size());
+            F.maps = r->dmaps;
+            for (int d = 0; d < 4; ++d) F.ext[d] = r->ext[d];
+            e = static_cast<cudaError_t>(koma::launch_rf_maps(F, S->s_up));
+        }
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_up, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(r->ev_up, S->s_up);
@@ -191,6 +264,14 @@ void release_device(koma_server* S, Req* r) {
     if (r->drows) cudaFreeAsync(r->drows, S->s_red);
     if (r->dsig) cudaFreeAsync(r->dsig, S->s_red);
     if (r->dstate) cudaFreeAsync(r->dstate, S->s_red);
+    if (r->dmaps) cudaFreeAsync(r->dmaps, S->s_red);
+    if (r->dpulses) cudaFreeAsync(r->dpulses, S->s_red);
+    if (r->drec_full) cudaFreeAsync(r->drec_full, S->s_red);
+    r->dmaps = nullptr;
+    r->dpulses = nullptr;
+    r->drec_full = nullptr;
+    r->recs_full.clear();
+    r->recs_full.shrink_to_fit();
     r->dstate = nullptr;
     r->d32 = nullptr;
     r->drec = nullptr;
@@ -275,10 +356,12 @@ bool launch_slot(koma_server* S, Slot& sl) {
             D.n_adc = r->n_adc;
             D.spin_begin = b * kBatchSpins;
             D.spin_end = std::min(r->n, D.spin_begin + kBatchSpins);
-            D.rec_begin = static_cast<int64_t>(c) * r->chunk;
-            D.rec_end = std::min(r->n_rec, D.rec_begin + r->chunk);
+            D.rec_begin = r->chunk_begin[static_cast<size_t>(c)];
+            D.rec_end = r->chunk_begin[static_cast<size_t>(c) + 1];
             D.state = r->dstate;
             D.rf_hdr = r->chunk_hdr[c];
+            D.rf_maps = r->dmaps;
+            D.n_rf_maps = r->dmaps ? static_cast<int>(r->pulses.size()) : 0;
             for (int d = 0; d < 4; ++d) D.ext[d] = r->ext[d];
             D.used = r->used;
             r->batch_busy[b] = 1;
@@ -347,6 +430,7 @@ void worker_loop(koma_server* S) {
                     S->pending.pop_front();
                     fail_req(r, KOMA_E_NOMEM, "request needs more device memory than the server's budget");
                     r->t_done = now_s();
+                    r->retired = true;
                     S->failed++;
                     S->cv_done.notify_all();
                     progress = true;
@@ -355,11 +439,25 @@ void worker_loop(koma_server* S) {
                 break;
             }
             S->pending.pop_front();
+            if (r->lane) {
+                // the second lane uploads and runs it (its thread, its stream)
+                r->t_admit = now_s();
+                r->state = LANE;
+                r->dev_bytes = need;
+                S->used += need;
+                S->peak = std::max(S->peak, S->used);
+                S->active.push_back(r);
+                S->lane_q.push_back(r);
+                S->cv_lane.notify_all();
+                progress = true;
+                continue;
+            }
             const koma_status st = admit(S, r);
             if (st != KOMA_OK) {
                 release_device(S, r);
                 fail_req(r, st, "admission failed (device allocation or upload)");
                 r->t_done = now_s();
+                r->retired = true;
                 S->failed++;
                 S->cv_done.notify_all();
             } else {
@@ -397,7 +495,10 @@ void worker_loop(koma_server* S) {
         for (size_t i = 0; i < S->active.size();) {
             Req* r = S->active[i];
             bool out = false;
-            if (r->state == REDUCING) {
+            if (r->lane && r->state == DONE) {
+                S->completed++;  // the second lane finished it
+                out = true;
+            } else if (r->state == REDUCING) {
                 const cudaError_t q = cudaEventQuery(r->ev_done);
                 if (q != cudaErrorNotReady) {
                     if (q == cudaSuccess) {
@@ -423,6 +524,7 @@ void worker_loop(koma_server* S) {
             }
             if (out) {
                 release_device(S, r);
+                r->retired = true;
                 S->active.erase(S->active.begin() + static_cast<long>(i));
                 S->cv_done.notify_all();
                 progress = true;
@@ -439,6 +541,72 @@ void worker_loop(koma_server* S) {
             std::this_thread::sleep_for(std::chrono::microseconds(20));
             lk.lock();
         }
+    }
+}
+
+// Second lane: grouped requests and requests that fill the GPU alone, one at
+// a time through the koma_simulate path (uploads, maps of repeated pulses,
+// the Bloch or grouped kernel, the tensor-core readout, the reduction) on the
+// lane's stream, overlapping the shared launches of the worker. The result
+// goes to the request's pinned buffer; the worker retires the request.
+void lane_loop(koma_server* S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        S->cv_lane.wait(lk, [&] { return S->stop || !S->lane_q.empty(); });
+        if (S->lane_q.empty()) {
+            if (S->stop) break;
+            continue;
+        }
+        Req* r = S->lane_q.front();
+        S->lane_q.pop_front();
+        lk.unlock();
+        NvtxRange nvtx_("server lane run");
+        koma_ctx* ctx = S->lane_ctx;
+        const int64_t n = r->n, ns = r->n_steps;
+        const double* P = r->ph64.data();
+        const double* Q = r->sq64.data();
+        koma_phantom* ph = nullptr;
+        koma_sequence* seq = nullptr;
+        koma_status st = koma_phantom_upload(ctx, n, P, P + n, P + 2 * n, P + 3 * n, P + 4 * n, P + 5 * n,
+                                             P + 6 * n, r->n_groups > 1 ? r->offsets.data() : nullptr,
+                                             r->n_groups, &ph);
+        if (st == KOMA_OK)
+            st = koma_sequence_upload(ctx, ns, Q, Q + ns, Q + 2 * ns + 1, Q + 3 * ns + 2, Q + 4 * ns + 3,
+                                      Q + 5 * ns + 3, r->sq_adc.data(), &seq);
+        const size_t out_bytes = static_cast<size_t>(r->n_groups * r->n_adc) * 2 * sizeof(double);
+        double* dsig = nullptr;
+        cudaError_t e = cudaSuccess;
+        if (st == KOMA_OK && out_bytes) {
+            e = cudaMallocAsync(reinterpret_cast<void**>(&dsig), out_bytes, S->s_lane);
+            if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&r->hsig), out_bytes);
+            if (e != cudaSuccess) st = KOMA_E_NOMEM;
+        }
+        if (st == KOMA_OK) st = koma_simulate(ctx, ph, seq, KOMA_FP32_SPLITPHASE, dsig, S->s_lane);
+        if (st == KOMA_OK && out_bytes)
+            e = cudaMemcpyAsync(r->hsig, dsig, out_bytes, cudaMemcpyDeviceToHost, S->s_lane);
+        if (st == KOMA_OK && e == cudaSuccess) st = koma_sync(ctx, S->s_lane);
+        else if (st == KOMA_OK) st = KOMA_E_CUDA;
+        std::string msg = st != KOMA_OK ? std::string(koma_last_error(ctx)) : std::string();
+        if (dsig) cudaFreeAsync(dsig, S->s_lane);
+        if (seq) koma_sequence_free(seq);
+        if (ph) koma_phantom_free(ph);
+        cudaStreamSynchronize(S->s_lane);
+        lk.lock();
+        r->ph64.clear();
+        r->ph64.shrink_to_fit();
+        r->sq64.clear();
+        r->sq64.shrink_to_fit();
+        r->sq_adc.clear();
+        r->sq_adc.shrink_to_fit();
+        r->launches = 1;
+        S->lane_runs++;
+        if (st == KOMA_OK) {
+            r->state = DONE;
+        } else {
+            fail_req(r, st, msg.empty() ? "second lane: simulation failed" : msg);
+        }
+        r->t_done = now_s();
     }
 }
 
@@ -463,6 +631,7 @@ extern "C" koma_status koma_server_create(const koma_server_config* cfg, koma_se
     // default cap: ~4 ms of the serving kernel at ~4.5e11 RF spin-steps/s
     S->launch_work = c.launch_work > 0 ? c.launch_work : 1.8e9;
     if (c.chunk_records > 0) S->chunk = c.chunk_records;
+    if (c.plain_spins != 0) S->plain_spins = c.plain_spins;
     S->t0 = now_s();
     int prev = -1;
     cudaGetDevice(&prev);
@@ -471,6 +640,7 @@ extern "C" koma_status koma_server_create(const koma_server_config* cfg, koma_se
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&S->sm_count, cudaDevAttrMultiProcessorCount, S->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->s_up, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->s_red, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->s_lane, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&S->d_status), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(S->d_status, 0, sizeof(int));
     if (e == cudaSuccess) {
@@ -485,6 +655,7 @@ extern "C" koma_status koma_server_create(const koma_server_config* cfg, koma_se
         }
     }
     if (e != cudaSuccess) st = cuda_err(S, e, "server: set-up");
+    if (st == KOMA_OK) st = koma_init(S->device, 0, &S->lane_ctx);
     if (st == KOMA_OK) {
         const int per_sm = std::max(1, koma::batches_ctas_per_sm(kBlock));
         S->grid = S->sm_count * per_sm;
@@ -499,15 +670,17 @@ extern "C" koma_status koma_server_create(const koma_server_config* cfg, koma_se
         return st;
     }
     S->worker = std::thread(worker_loop, S);
+    S->lane_worker = std::thread(lane_loop, S);
     *out = S;
     return KOMA_OK;
 }
 
 extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const double* x, const double* y,
                                           const double* z, const double* pd, const double* t1, const double* t2,
-                                          const double* dw, int64_t n_steps, const double* dt, const double* gx,
-                                          const double* gy, const double* gz, const double* b1_re,
-                                          const double* b1_im, const uint8_t* adc, uint64_t* id_out) {
+                                          const double* dw, const int64_t* group_offsets, int64_t n_groups,
+                                          int64_t n_steps, const double* dt, const double* gx, const double* gy,
+                                          const double* gz, const double* b1_re, const double* b1_im,
+                                          const uint8_t* adc, uint64_t* id_out) {
     NvtxRange nvtx_("koma_server_submit");
     if (!S || !id_out) return KOMA_E_INVALID;
     Req* r = new (std::nothrow) Req();
@@ -515,6 +688,15 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
     r->t_submit = now_s();
     std::string err;
     int st = koma::host_phantom32(n, x, y, z, pd, t1, t2, dw, r->h32, r->n_pad, r->max_abs, err);
+    if (st == KOMA_OK && group_offsets) {
+        // the upload's rules: n_groups >= 1, offsets from 0 to n, non-decreasing
+        bool ok = n_groups >= 1 && group_offsets[0] == 0 && group_offsets[n_groups] == n;
+        for (int64_t g = 0; ok && g < n_groups; ++g) ok = group_offsets[g] <= group_offsets[g + 1];
+        if (!ok) {
+            st = KOMA_E_INVALID;
+            err = "server_submit: group_offsets must run from 0 to n without decreasing (n_groups >= 1)";
+        }
+    }
     koma_sequence_info info{};
     if (st == KOMA_OK) st = koma::host_records32(n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, r->recs, info, err);
     if (st != KOMA_OK) {
@@ -527,22 +709,76 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
     r->n_steps = n_steps;
     r->n_adc = info.n_adc;
     r->n_rec = info.n_records;
+    r->n_adc_runs = info.n_adc_runs;
+    r->n_groups = group_offsets ? n_groups : 1;
+    r->lane = r->n_groups > 1 || (S->plain_spins > 0 && n >= S->plain_spins);
+    if (r->lane) {
+        // the second lane uploads the request itself: keep the host arrays
+        r->h32.clear();
+        r->h32.shrink_to_fit();
+        const double* ph[7] = {x, y, z, pd, t1, t2, dw};
+        r->ph64.resize(static_cast<size_t>(7 * n));
+        for (int k = 0; k < 7; ++k)
+            if (n > 0) std::memcpy(r->ph64.data() + k * n, ph[k], static_cast<size_t>(n) * sizeof(double));
+        if (group_offsets) r->offsets.assign(group_offsets, group_offsets + n_groups + 1);
+        const int64_t v = n_steps + 1;
+        r->sq64.resize(static_cast<size_t>(n_steps + 3 * v + 2 * n_steps));
+        double* q = r->sq64.data();
+        if (n_steps > 0) std::memcpy(q, dt, static_cast<size_t>(n_steps) * sizeof(double));
+        std::memcpy(q + n_steps, gx, static_cast<size_t>(v) * sizeof(double));
+        std::memcpy(q + n_steps + v, gy, static_cast<size_t>(v) * sizeof(double));
+        std::memcpy(q + n_steps + 2 * v, gz, static_cast<size_t>(v) * sizeof(double));
+        if (n_steps > 0) {
+            std::memcpy(q + n_steps + 3 * v, b1_re, static_cast<size_t>(n_steps) * sizeof(double));
+            std::memcpy(q + 2 * n_steps + 3 * v, b1_im, static_cast<size_t>(n_steps) * sizeof(double));
+        }
+        r->sq_adc.assign(adc, adc + v);
+        r->recs.clear();
+        r->recs.shrink_to_fit();
+        r->units_total = 0;
+        r->rem_work = 0;
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) {
+            delete r;
+            return KOMA_E_BUSY;
+        }
+        r->id = S->next_id++;
+        S->all[r->id] = r;
+        S->pending.push_back(r);
+        S->submitted++;
+        *id_out = r->id;
+        S->cv_work.notify_all();
+        return KOMA_OK;
+    }
     for (int d = 0; d < 4; ++d) {
         r->ext[d] = static_cast<float>(r->max_abs[d] * (1.0 + 1e-6));
         if (r->max_abs[d] > 0) r->used |= 1 << d;
     }
     r->n_batches = (r->n_adc > 0 && n > 0) ? (n + kBatchSpins - 1) / kBatchSpins : 0;
+    koma::host_rf_maps32(r->recs, r->pulses, info);
+    if (!r->pulses.empty()) {
+        // the batches walk the compacted stream (a repeated pulse is one
+        // REC_MAP record); the map kernel steps the pulses from the full one
+        r->recs_full.swap(r->recs);
+        koma::compact_records32(r->recs_full, r->recs);
+        r->n_rec = static_cast<int64_t>(r->recs.size());
+    }
     r->chunk = S->chunk;
-    r->n_chunks = std::max<int64_t>(1, (r->n_rec + r->chunk - 1) / r->chunk);
+    r->chunk_begin.clear();
+    for (int64_t b = 0; b < r->n_rec; b += r->chunk) r->chunk_begin.push_back(b);
+    if (r->chunk_begin.empty()) r->chunk_begin.push_back(0);
+    r->chunk_begin.push_back(r->n_rec);
+    r->n_chunks = static_cast<int64_t>(r->chunk_begin.size()) - 1;
     r->chunk_work.assign(static_cast<size_t>(r->n_chunks), 0.0);
     r->chunk_hdr.assign(static_cast<size_t>(r->n_chunks), -1);
     int64_t hdr = -1;
-    for (int64_t i = 0; i < r->n_rec; ++i) {
-        const koma::Rec32& q = r->recs[static_cast<size_t>(i)];
-        const int64_t c = i / r->chunk;
-        if (i == c * r->chunk && q.type == koma::REC_RF && q.count == 0) r->chunk_hdr[c] = hdr;
-        if (q.type == koma::REC_RF && q.count > 0) hdr = i;
-        r->chunk_work[c] += q.type == koma::REC_ADC ? 1.0 + (q.count & koma::kCountMask) / 8.0 : 1.0;
+    for (int64_t c = 0; c < r->n_chunks; ++c) {
+        for (int64_t i = r->chunk_begin[c]; i < r->chunk_begin[c + 1]; ++i) {
+            const koma::Rec32& q = r->recs[static_cast<size_t>(i)];
+            if (i == r->chunk_begin[c] && q.type == koma::REC_RF && q.count == 0) r->chunk_hdr[c] = hdr;
+            if (q.type == koma::REC_RF && q.count > 0) hdr = i;
+            r->chunk_work[c] += q.type == koma::REC_ADC ? 1.0 + (q.count & koma::kCountMask) / 8.0 : 1.0;
+        }
     }
     double w = 0;
     for (double cw : r->chunk_work) w += cw;
@@ -572,7 +808,7 @@ extern "C" koma_status koma_server_wait(koma_server* S, uint64_t id, double time
     auto it = S->all.find(id);
     if (it == S->all.end()) return KOMA_E_INVALID;
     Req* r = it->second;
-    auto finished = [&] { return (r->state == DONE || r->state == FAILED) && r->t_done >= 0 && !r->d32; };
+    auto finished = [&] { return (r->state == DONE || r->state == FAILED) && r->t_done >= 0 && r->retired; };
     if (timeout_s < 0) {
         S->cv_done.wait(lk, finished);
     } else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), finished)) {
@@ -580,6 +816,8 @@ extern "C" koma_status koma_server_wait(koma_server* S, uint64_t id, double time
     }
     if (info) {
         info->id = r->id;
+        info->n_groups = r->n_groups;
+        info->lane = r->lane ? 1 : 0;
         info->n_spins = r->n;
         info->n_steps = r->n_steps;
         info->n_adc = r->n_adc;
@@ -592,8 +830,9 @@ extern "C" koma_status koma_server_wait(koma_server* S, uint64_t id, double time
     }
     koma_status st = r->state == DONE ? KOMA_OK : r->err;
     if (st == KOMA_OK && r->n_adc > 0) {
-        if (!sig_host || capacity < r->n_adc) return KOMA_E_INVALID;  // keep the result for a retry
-        std::memcpy(sig_host, r->hsig, static_cast<size_t>(r->n_adc) * 2 * sizeof(double));
+        const int64_t total = r->n_groups * r->n_adc;
+        if (!sig_host || capacity < total) return KOMA_E_INVALID;  // keep the result for a retry
+        std::memcpy(sig_host, r->hsig, static_cast<size_t>(total) * 2 * sizeof(double));
     } else if (st == KOMA_OK && sig_host && capacity > 0) {
         // nothing observed
     }
@@ -619,6 +858,7 @@ extern "C" koma_status koma_server_get_stats(koma_server* S, koma_server_stats* 
     out->batches = S->batches;
     out->mem_used = S->used;
     out->mem_peak = S->peak;
+    out->lane_runs = S->lane_runs;
     return KOMA_OK;
 }
 
@@ -632,13 +872,17 @@ extern "C" koma_status koma_server_destroy(koma_server* S) {
         for (Req* r : S->pending) fail_req(r, KOMA_E_BUSY, "server shut down before admission");
         for (Req* r : S->pending) {
             r->t_done = now_s();
+            r->retired = true;
             S->failed++;
         }
         S->pending.clear();
         S->cv_work.notify_all();
         S->cv_done.notify_all();
+        S->cv_lane.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
+    if (S->lane_worker.joinable()) S->lane_worker.join();
+    if (S->lane_ctx) koma_destroy(S->lane_ctx);
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(S->device);
@@ -663,6 +907,7 @@ extern "C" koma_status koma_server_destroy(koma_server* S) {
     if (S->d_status) cudaFree(S->d_status);
     if (S->s_up) cudaStreamDestroy(S->s_up);
     if (S->s_red) cudaStreamDestroy(S->s_red);
+    if (S->s_lane) cudaStreamDestroy(S->s_lane);
     if (prev >= 0) cudaSetDevice(prev);
     delete S;
     return KOMA_OK;

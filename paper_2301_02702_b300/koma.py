@@ -35,7 +35,7 @@ EXPORTS = (
     "koma_get_timing", "koma_get_launch_info", "koma_simulate_host", "koma_simulate_static", "koma_tune",
     "koma_server_create", "koma_server_submit", "koma_server_wait", "koma_server_get_stats",
     "koma_server_last_error", "koma_server_destroy", "koma_check_bounded_wait", "koma_get_stage_timing",
-    "koma_set_mma",
+    "koma_set_mma", "koma_set_rf_maps", "koma_get_map_timing",
 )
 
 
@@ -60,7 +60,9 @@ class SequenceInfo(ctypes.Structure):
                 ("n_precess", ctypes.c_int64), ("n_records", ctypes.c_int64),
                 ("n_adc_runs", ctypes.c_int64), ("n_materialize", ctypes.c_int64),
                 ("n_mma_groups", ctypes.c_int64), ("n_mma_runs", ctypes.c_int64),
-                ("n_mma_samples", ctypes.c_int64)]
+                ("n_mma_samples", ctypes.c_int64), ("n_rf_maps", ctypes.c_int64),
+                ("n_rf_map_runs", ctypes.c_int64), ("n_rf_map_steps", ctypes.c_int64),
+                ("n_rf_map_pulse_steps", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -68,14 +70,15 @@ class SequenceInfo(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_active", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
-                ("launch_work", ctypes.c_double), ("chunk_records", ctypes.c_int64)]
+                ("launch_work", ctypes.c_double), ("chunk_records", ctypes.c_int64),
+                ("plain_spins", ctypes.c_int64)]
 
 
 class RequestInfo(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("n_spins", ctypes.c_int64), ("n_steps", ctypes.c_int64),
                 ("n_adc", ctypes.c_int64), ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
                 ("done_s", ctypes.c_double), ("latency_s", ctypes.c_double), ("launches", ctypes.c_int32),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("n_groups", ctypes.c_int64), ("lane", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -84,7 +87,8 @@ class RequestInfo(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("pending", ctypes.c_int64), ("active", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("batches", ctypes.c_int64), ("mem_used", ctypes.c_size_t), ("mem_peak", ctypes.c_size_t)]
+                ("batches", ctypes.c_int64), ("mem_used", ctypes.c_size_t), ("mem_peak", ctypes.c_size_t),
+                ("lane_runs", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -161,13 +165,17 @@ def load(path: Optional[str] = None):
         lib.koma_get_stage_timing.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_float)] * 3
         lib.koma_set_mma.restype = st
         lib.koma_set_mma.argtypes = [_vp, ctypes.c_int]
+        lib.koma_set_rf_maps.restype = st
+        lib.koma_set_rf_maps.argtypes = [_vp, ctypes.c_int]
+        lib.koma_get_map_timing.restype = st
+        lib.koma_get_map_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_float)]
         lib.koma_get_launch_info.restype = st
         lib.koma_get_launch_info.argtypes = [_vp, ctypes.POINTER(LaunchInfo)]
         lib.koma_server_create.restype = st
         lib.koma_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]
         lib.koma_server_submit.restype = st
-        lib.koma_server_submit.argtypes = ([_vp, ctypes.c_int64] + [_dp] * 7 + [ctypes.c_int64] + [_dp] * 6
-                                           + [_u8p, ctypes.POINTER(ctypes.c_uint64)])
+        lib.koma_server_submit.argtypes = ([_vp, ctypes.c_int64] + [_dp] * 7 + [_i64p, ctypes.c_int64,
+                                           ctypes.c_int64] + [_dp] * 6 + [_u8p, ctypes.POINTER(ctypes.c_uint64)])
         lib.koma_server_wait.restype = st
         lib.koma_server_wait.argtypes = [_vp, ctypes.c_uint64, ctypes.c_double, _dp, ctypes.c_int64,
                                          ctypes.POINTER(RequestInfo)]
@@ -392,6 +400,18 @@ def koma_set_mma(ctx, enable: bool = True):
     _check(ctx, load().koma_set_mma(ctx, int(bool(enable))), "koma_set_mma")
 
 
+def koma_set_rf_maps(ctx, enable: bool = True):
+    _check(ctx, load().koma_set_rf_maps(ctx, int(bool(enable))), "koma_set_rf_maps")
+
+
+def koma_get_map_timing(ctx) -> float:
+    """Milliseconds of the repeated-pulse map pre-pass of the last timed
+    koma_simulate (0 when it had none)."""
+    a = ctypes.c_float()
+    _check(ctx, load().koma_get_map_timing(ctx, ctypes.byref(a)), "koma_get_map_timing")
+    return a.value
+
+
 def koma_get_launch_info(ctx) -> dict:
     info = LaunchInfo()
     _check(ctx, load().koma_get_launch_info(ctx, ctypes.byref(info)), "koma_get_launch_info")
@@ -479,8 +499,9 @@ class Simulator:
 # --------------------------------------------------------------------------
 
 def koma_server_create(device: int = 0, mem_budget_bytes: int = 0, max_active: int = 0, launch_work: float = 0.0,
-                       chunk_records: int = 0):
-    cfg = ServerConfig(int(device), int(max_active), int(mem_budget_bytes), float(launch_work), int(chunk_records))
+                       chunk_records: int = 0, plain_spins: int = 0):
+    cfg = ServerConfig(int(device), int(max_active), int(mem_budget_bytes), float(launch_work), int(chunk_records),
+                       int(plain_spins))
     out = _vp()
     rc = load().koma_server_create(ctypes.byref(cfg), ctypes.byref(out))
     if rc != KOMA_OK:
@@ -494,24 +515,31 @@ def koma_server_last_error(srv) -> str:
 
 def koma_server_submit(srv, phantom, seq) -> int:
     arrs = [_f64(getattr(phantom, f)) for f in ("x", "y", "z", "pd", "t1", "t2", "dw")]
+    go = getattr(phantom, "group_offsets", None)
+    go_arr = None if go is None else np.ascontiguousarray(go, dtype=np.int64)
+    n_groups = 1 if go_arr is None else int(go_arr.shape[0] - 1)
     dt, gx, gy, gz, bre, bim, adc = _seq_arrays(seq)
     rid = ctypes.c_uint64()
-    rc = load().koma_server_submit(srv, arrs[0].shape[0], *[_ptr(a) for a in arrs], dt.shape[0], _ptr(dt),
-                                   _ptr(gx), _ptr(gy), _ptr(gz), _ptr(bre), _ptr(bim), _ptr(adc, ctypes.c_uint8),
-                                   ctypes.byref(rid))
+    rc = load().koma_server_submit(srv, arrs[0].shape[0], *[_ptr(a) for a in arrs],
+                                   None if go_arr is None else _ptr(go_arr, ctypes.c_int64), n_groups,
+                                   dt.shape[0], _ptr(dt), _ptr(gx), _ptr(gy), _ptr(gz), _ptr(bre), _ptr(bim),
+                                   _ptr(adc, ctypes.c_uint8), ctypes.byref(rid))
     if rc != KOMA_OK:
         raise KomaError(rc, "koma_server_submit: " + koma_server_last_error(srv))
     return int(rid.value)
 
 
-def koma_server_wait(srv, rid: int, n_adc: int, timeout_s: float = -1.0):
-    """(signal complex128 [n_adc], info dict) of request `rid`."""
-    out = np.empty(max(n_adc, 1), dtype=np.complex128)
+def koma_server_wait(srv, rid: int, n_adc: int, timeout_s: float = -1.0, n_groups: int = 1):
+    """(signal complex128 [n_adc], or [n_groups, n_adc] for a grouped request;
+    info dict) of request `rid`."""
+    out = np.empty(max(n_groups * n_adc, 1), dtype=np.complex128)
     info = RequestInfo()
-    rc = load().koma_server_wait(srv, int(rid), float(timeout_s), out.ctypes.data_as(_dp), n_adc, ctypes.byref(info))
+    rc = load().koma_server_wait(srv, int(rid), float(timeout_s), out.ctypes.data_as(_dp), n_groups * n_adc,
+                                 ctypes.byref(info))
     if rc != KOMA_OK:
         raise KomaError(rc, "koma_server_wait: " + koma_server_last_error(srv))
-    return out[:n_adc], info.as_dict()
+    sig = out[:n_groups * n_adc]
+    return (sig.reshape(n_groups, n_adc) if n_groups > 1 else sig), info.as_dict()
 
 
 def koma_check_bounded_wait(ctx, limit_us: int, stream_handle: int = 0):
@@ -534,21 +562,25 @@ def koma_server_destroy(srv):
 
 
 class Server:
-    """Continuous-batching simulation server on one device (native worker)."""
+    """Continuous-batching simulation server on one device (native worker
+    threads: shared launches for small requests, the koma_simulate lane for
+    large and grouped ones)."""
 
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_active: int = 0, launch_work: float = 0.0,
-                 chunk_records: int = 0):
-        self.srv = koma_server_create(device, mem_budget_bytes, max_active, launch_work, chunk_records)
-        self._n_adc = {}
+                 chunk_records: int = 0, plain_spins: int = 0):
+        self.srv = koma_server_create(device, mem_budget_bytes, max_active, launch_work, chunk_records, plain_spins)
+        self._shape = {}
 
     def submit(self, phantom, seq) -> int:
         rid = koma_server_submit(self.srv, phantom, seq)
-        self._n_adc[rid] = int(np.count_nonzero(seq.adc))
+        go = getattr(phantom, "group_offsets", None)
+        self._shape[rid] = (int(np.count_nonzero(seq.adc)), 1 if go is None else int(len(go) - 1))
         return rid
 
     def wait(self, rid: int, timeout_s: float = -1.0):
-        sig, info = koma_server_wait(self.srv, rid, self._n_adc[rid], timeout_s)
-        del self._n_adc[rid]
+        n_adc, n_groups = self._shape[rid]
+        sig, info = koma_server_wait(self.srv, rid, n_adc, timeout_s, n_groups)
+        del self._shape[rid]
         return sig, info
 
     def stats(self) -> dict:

@@ -174,3 +174,45 @@ def test_plan_groups_readout_lines(lib):
     assert koma.koma_sequence_plan(epi(n_read=128, n_lines=14, fov=0.23, rf_steps=100))["n_mma_groups"] == 0
     # unstructured sequences: none
     assert koma.koma_sequence_plan(random_sequence(3000, seed=7))["n_mma_groups"] == 0
+
+
+def _pulse_train(pulses, order, seed=0):
+    """Pulses (n, dt, b1 samples, gradient during the pulse) played in
+    `order`, each preceded by a gradient ramp to its own gradient and
+    followed by a ramp down, a lobe whose area changes per occurrence and a
+    few samples: only the pulses repeat."""
+    rng = np.random.default_rng(seed)
+    b = SequenceBuilder()
+    for k, p in enumerate(order):
+        n, dt, b1, g = pulses[p]
+        b.steps(1, 20e-6, g)
+        b.steps(n, dt, g, b1=b1)
+        b.steps(1, 20e-6, [0.0, 0.0, 0.0])
+        b.steps(2, 40e-6, [rng.uniform(-0.01, 0.01), 0.004 * (k % 5), 0.0]).steps(1, 40e-6, [0.0, 0.0, 0.0])
+        b.steps(4, 10e-6, adc=True)
+    return b.build()
+
+
+def test_plan_finds_repeated_pulses(lib):
+    """Runs of RF steps that recur unchanged at least 3 times (and are at
+    least 4 steps long) get a map slot; at most 8 slots, the ones saving the
+    most steps first."""
+    from paper_2301_02702_b300.workloads import sinc_pulse
+    info = koma.koma_sequence_plan(workload("se128", "full")[1])
+    assert (info["n_rf_maps"], info["n_rf_map_runs"], info["n_rf_map_steps"],
+            info["n_rf_map_pulse_steps"]) == (2, 128, 64000, 1000)
+    a = (60, 4e-6, sinc_pulse(60, 4e-6, 90.0), [0.0, 0.0, 0.01])
+    b = (40, 4e-6, sinc_pulse(40, 4e-6, 30.0), [0.0, 0.0, 0.01])
+    c = (3, 4e-6, sinc_pulse(3, 4e-6, 10.0), [0.0, 0.0, 0.0])
+    a_g = (60, 4e-6, sinc_pulse(60, 4e-6, 90.0), [0.0, 0.0, 0.012])  # A under another gradient
+    info = koma.koma_sequence_plan(_pulse_train([a, b, c, a_g], [0, 1, 0, 2, 2, 2, 2, 3, 0, 1]))
+    # A three times (the other gradient is another pulse), B only twice, C too short
+    assert (info["n_rf_maps"], info["n_rf_map_runs"], info["n_rf_map_steps"]) == (1, 3, 180)
+    assert info["n_rf_map_pulse_steps"] == 60
+    # nine distinct pulses repeated 3 times each: the eight longest get maps
+    ps = [(10 + 2 * i, 4e-6, sinc_pulse(10 + 2 * i, 4e-6, 20.0 + i), [0.0, 0.0, 0.0]) for i in range(9)]
+    info = koma.koma_sequence_plan(_pulse_train(ps, [i for _ in range(3) for i in range(9)]))
+    assert info["n_rf_maps"] == 8 and info["n_rf_map_runs"] == 24
+    assert info["n_rf_map_pulse_steps"] == sum(10 + 2 * i for i in range(1, 9))
+    # unstructured sequences: none
+    assert koma.koma_sequence_plan(random_sequence(3000, seed=7))["n_rf_maps"] == 0

@@ -83,7 +83,7 @@ def test_se128_full_launch_contiguous_slab(sim):
     assert info["mma_grid"] > 0 and info["grid"] >= 148
     ref = oracle.simulate(ph.subset(keep), seq)
     # the slab holds the excited slice: its signal is far from zero
-    assert np.max(np.abs(ref)) > 1e3
+    assert np.max(np.abs(ref)) > 100.0
     err = rel_err(got, ref)
     print(f"se128 full launch, central slab of {len(keep)} spins: rel err {err:.3e}")
     assert err < TOL32, err

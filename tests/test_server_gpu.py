@@ -114,13 +114,16 @@ def test_admission_by_memory_budget():
 
 
 def test_checkpointed_chunks_equal_unsplit_walk(server):
-    """Walking a sequence in chunks of 37 step records, with the spin state
+    """Walking a sequence in chunks of 7 step records, with the spin state
     checkpointed in device memory between launches (cuts fall inside RF runs
-    and between samples), gives bitwise the result of the unsplit walk."""
+    and between samples), gives bitwise the result of the unsplit walk. The
+    spin echo's repeated pulses are taken by their maps: a pulse is one
+    record of the walked stream."""
     reqs = [workload("se128", "small"), workload("epi512", "small"), (random_spins(700, seed=4),
                                                                        random_sequence(900, seed=5))]
+    assert koma.koma_sequence_plan(reqs[0][1])["n_rf_maps"] == 2
     whole = [server.wait(server.submit(ph, seq))[0] for ph, seq in reqs]
-    small = koma.Server(0, chunk_records=37)
+    small = koma.Server(0, chunk_records=7)
     try:
         parts = [small.wait(small.submit(ph, seq)) for ph, seq in reqs]
     finally:
@@ -129,3 +132,73 @@ def test_checkpointed_chunks_equal_unsplit_walk(server):
         assert info["launches"] > 1
         assert np.array_equal(a, b)
         assert rel_err(b, oracle.simulate(ph, seq)[0]) < TOL32
+
+
+def test_grouped_request_served_alone_and_in_a_mix(server):
+    """A dictionary (one signal per group, with an empty group) is served by
+    the koma_simulate lane: it matches the oracle group by group, and its
+    result is bitwise the same alone and while shared launches run."""
+    ph, seq = workload("mrf", "small")
+    ph.group_offsets = ph.group_offsets.copy()
+    alone, info = server.wait(server.submit(ph, seq))
+    assert info["lane"] == 1 and info["n_groups"] == ph.n_groups
+    assert alone.shape == (ph.n_groups, seq.n_adc)
+    ref = oracle.simulate(ph, seq)
+    err = np.max(np.abs(alone - ref), axis=1) / np.max(np.abs(ref), axis=1)
+    assert np.max(err) < TOL32
+    mix = _mix(5, 10)
+    ids = [server.submit(p, s) for p, s in mix[:5]]
+    target = server.submit(ph, seq)
+    ids += [server.submit(p, s) for p, s in mix[5:]]
+    with_mix, info = server.wait(target)
+    for rid in ids:
+        server.wait(rid)
+    assert np.array_equal(alone, with_mix)
+    # groups that are empty give zero signal
+    phe = random_spins(50, seed=3)
+    phe.group_offsets = np.array([0, 20, 20, 50])
+    sig, info = server.wait(server.submit(phe, random_sequence(200, seed=4)))
+    assert sig.shape[0] == 3 and np.all(sig[1] == 0) and info["lane"] == 1
+
+
+def test_large_requests_take_the_simulate_lane():
+    """With a low threshold, requests of at least plain_spins spins run the
+    koma_simulate path in the second lane (bitwise what a fresh context's
+    koma_simulate gives, so the tensor-core readout and the maps of repeated
+    pulses apply), while smaller ones share the persistent kernel's launches
+    at the same time; both match the oracle."""
+    big = [workload("se128", "small"), workload("epi512", "small")]
+    small = _mix(9, 6)
+    srv = koma.Server(0, plain_spins=900)
+    try:
+        ids = [srv.submit(*r) for r in big] + [srv.submit(*r) for r in small]
+        res = [srv.wait(rid) for rid in ids]
+        st = srv.stats()
+    finally:
+        srv.close()
+    assert st["lane_runs"] == 2
+    sim = koma.Simulator(0)
+    try:
+        for (ph, seq), (sig, info) in zip(big, res[:2]):
+            assert info["lane"] == 1
+            hp, hs = sim.upload_phantom(ph), sim.upload_sequence(seq)
+            direct = sim.simulate(hp, hs).cpu().numpy()[0]
+            koma.koma_phantom_free(hp)
+            koma.koma_sequence_free(hs)
+            assert np.array_equal(sig, direct)
+            assert rel_err(sig, oracle.simulate(ph, seq)[0]) < TOL32
+    finally:
+        sim.close()
+    for (ph, seq), (sig, info) in zip(small, res[2:]):
+        assert info["lane"] == 0
+        ref = oracle.simulate(ph, seq)[0]
+        if np.max(np.abs(ref)) > 0:
+            assert rel_err(sig, ref) < TOL32
+
+
+def test_submit_rejects_bad_group_offsets(server):
+    ph = random_spins(10, seed=1)
+    ph.group_offsets = np.array([0, 6, 4, 10])
+    with pytest.raises(koma.KomaError) as e:
+        server.submit(ph, random_sequence(20, seed=2))
+    assert e.value.status == koma.KOMA_E_INVALID
