@@ -393,12 +393,13 @@ def serve_measure(local: int, n_req: int, rate: float, plain_host: bool = False,
     ths = [threading.Thread(target=client, args=(c,)) for c in range(n_clients)]
     for th in ths:
         th.start()
-    lat = []
+    lat, infos = [], []
     for i in range(len(reqs)):
         while ids[i] is None:
             time.sleep(0.0005)
         _, info = srv.wait(ids[i])
         lat.append(info["latency_s"])
+        infos.append(info)
     for th in ths:
         th.join()
     t_open = time.perf_counter() - t0
@@ -471,7 +472,14 @@ def serve_measure(local: int, n_req: int, rate: float, plain_host: bool = False,
                          "plain": "one koma_simulate per request on device-resident inputs, back to back on one "
                                   "stream (device time, CUDA events); latencies under the same arrivals"},
         "ratio_saturated_vs_plain_device": t_plain_dev / t_sat,
-        "server": {k: stats[k] for k in ("batches", "mem_peak", "completed", "failed")},
+        "server": {k: stats[k] for k in ("batches", "mem_peak", "completed", "failed", "lane_runs")},
+        "lanes": {"requests": [sum(1 for f in infos if f["lane"] == k) for k in (0, 1)],
+                  "spin_steps": [sum(r[2] for r, f in zip(reqs, infos) if f["lane"] == k) for k in (0, 1)],
+                  "prep_s_total": sum(f["prep_s"] for f in infos),
+                  "upload_s_total": sum(f["upload_s"] for f in infos),
+                  "run_s_total": sum(f["run_s"] for f in infos),
+                  "how": "open-loop stream: requests and spin-steps per lane (0 shared launches, 1 koma_simulate "
+                         "lane); host seconds summed over requests"},
         "server_launches": launches,
         "clocks": clk,
     }
@@ -944,7 +952,7 @@ def result_line(args, world, ph, seq, info, launch, stage_ms, clk, value, ms_max
         "clocks": clk,
     }
     if tuned is not None:
-        line["config"]["tuned"] = {k: tuned[k] for k in ("grid", "block", "spins_per_thread")}
+        line["config"]["tuned"] = {k: tuned[k] for k in ("grid", "block", "spins_per_thread", "tile_records")}
     return line
 
 

@@ -50,7 +50,10 @@ typedef enum {
     KOMA_E_NOMEM = 2,   /* device allocation failed or the memory budget is exceeded */
     KOMA_E_CUDA = 3,    /* a CUDA runtime call failed; see koma_last_error */
     KOMA_E_TIMEOUT = 4, /* a bounded device-side wait gave up (see koma_sync) */
-    KOMA_E_BUSY = 5     /* the object is in use by another request */
+    KOMA_E_BUSY = 5,    /* the object is in use by another request */
+    KOMA_E_INTERNAL = 6 /* a kernel's own bounds check caught a record pointing outside its
+                           launch's buffers (an inconsistent record stream); the access was
+                           skipped and the result is not to be used (see koma_sync) */
 } koma_status;
 
 typedef enum {
@@ -81,6 +84,8 @@ typedef struct {
                                  warps and sampling dominates the work)     */
     int32_t mma_grid;         /* CTAs of the tensor-core readout (0: not
                                  used by this call)                        */
+    int32_t tile_records;     /* step records per shared-memory tile of the
+                                 walking kernel                            */
 } koma_launch_info;
 
 /* Counts of the uploaded sequence by step class (hot-path cost model). */
@@ -297,8 +302,9 @@ koma_status koma_simulate_static(const koma_phantom *ph, const koma_sequence *se
 /*
  * Autotune the FP32 launch for this (phantom, sequence) pair: times the
  * candidate configurations on the full problem (grouped phantoms: spins per
- * thread {2, 4} x block {128, 256} of the work-item kernel; otherwise spins
- * per thread {2, 4} of the Bloch kernel) and keeps the fastest on the
+ * thread {2, 4} x block {128, 256} x sequence-tile length {64, 128, 256}
+ * records of the work-item kernel; otherwise spins per thread {2, 4} of the
+ * Bloch kernel) and keeps the fastest on the
  * phantom; later koma_simulate calls with this sequence use it. The choice
  * is also cached on the context by problem shape (kernel family and the
  * powers of two of spins, groups, records, ADC samples and RF steps), and
@@ -324,8 +330,11 @@ koma_status koma_check_bounded_wait(koma_ctx *ctx, int64_t limit_us, void *strea
 /*
  * Wait for `stream` and report device-side status: KOMA_E_TIMEOUT if a
  * bounded wait inside a kernel of this context gave up since the last
- * koma_sync (the flag is then cleared), KOMA_E_CUDA on an asynchronous CUDA
- * error, else KOMA_OK.
+ * koma_sync, KOMA_E_INTERNAL if a kernel skipped a record that pointed
+ * outside its buffers (an ADC run past the signal's end or out of order, a
+ * map slot or readout snapshot row out of range: the kernels check every
+ * index they take from a record before using it); the flags are then
+ * cleared. KOMA_E_CUDA on an asynchronous CUDA error, else KOMA_OK.
  */
 koma_status koma_sync(koma_ctx *ctx, void *stream);
 
@@ -398,11 +407,12 @@ koma_status koma_simulate_host(koma_ctx *ctx, int64_t n,
  *     step records, its spin state checkpointed in device memory between
  *     launches, so a long simulation never holds the GPU for long; repeated
  *     RF pulses are applied through their maps;
- *   - requests with at least `plain_spins` spins (they fill the GPU alone)
- *     and grouped requests (a dictionary: one signal per group) run, one at a
- *     time and concurrently with the shared launches, the koma_simulate path
- *     on their own stream (maps of repeated pulses, the tensor-core readout,
- *     the grouped kernel).
+ *   - requests with at least `plain_spins` spins and grouped requests (a
+ *     dictionary: one signal per group) run the koma_simulate path (maps of
+ *     repeated pulses, the tensor-core readout, the grouped kernel) on four
+ *     lane threads with a context and a stream each: one request's upload
+ *     overlaps other requests' kernels, and requests that do not fill the
+ *     GPU run side by side, next to the shared launches.
  * A request's result (KOMA_FP32_SPLITPHASE arithmetic) does not depend on
  * the other requests: it is bitwise the same alone and in any mix.
  * ---------------------------------------------------------------------- */
@@ -417,7 +427,7 @@ typedef struct {
                                 checkpointed between launches (long sequences do not hold the GPU);
                                 0 = 4096 */
     int64_t plain_spins;     /* requests with at least this many spins run the koma_simulate
-                                path in the server's second lane; 0 = 262144, < 0 = never
+                                path in the server's second lane; 0 = 32768, < 0 = never
                                 (grouped requests always do) */
 } koma_server_config;
 
@@ -431,6 +441,10 @@ typedef struct {
     koma_status status;
     int64_t n_groups;                 /* signal groups (1: ungrouped)           */
     int32_t lane;                     /* 0: shared launches, 1: koma_simulate lane */
+    double prep_s;                    /* host time of the submit call (checks, preprocessing, copies) */
+    double upload_s;                  /* koma_simulate lane: uploads (0 in the shared lane) */
+    double run_s;                     /* koma_simulate lane: simulate, copy-back and wait (0 in the
+                                         shared lane) */
 } koma_request_info;
 
 typedef struct {

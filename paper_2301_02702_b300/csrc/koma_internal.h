@@ -39,6 +39,18 @@ enum RecType : int32_t {
 // evaluations never runs longer than this)
 constexpr int kMaxAdcRun = 128;
 constexpr int kCountMask = 0xffff;   // samples field of an ADC record's count
+// Device status word bits (koma_sync reads and clears them): 1 = a bounded
+// wait of a kernel gave up; 2 = the bounded-wait self-check gave up (as it
+// is meant to); the others: a record pointed outside its launch's buffers
+// and its access was skipped: 4 = an ADC run past n_adc or before the
+// samples already staged, 8 = a map slot, 16 = a readout snapshot row,
+// 32 = a tensor-core readout run.
+constexpr int kStatusTimeout = 1;
+constexpr int kStatusWaitCheck = 2;
+constexpr int kStatusBadAdc = 4;
+constexpr int kStatusBadMap = 8;
+constexpr int kStatusBadSnap = 16;
+constexpr int kStatusBadRun = 32;
 constexpr int kTermShift = 16;       // nonzero-term bits of PREC/ADC records
 
 // Matrix form of the readout. ADC runs whose samples share the per-sample
@@ -228,6 +240,7 @@ struct BlochArgs {
     // [n_rf_maps][kRfMapFloats][n_pad] buffer
     const float* rf_maps = nullptr;
     int n_rf_maps = 0;
+    int64_t n_mma_snaps = 0;        // rows of mma_snap
 };
 
 // Pre-pass of the repeated-pulse maps: for every spin j < n and pulse p,
@@ -277,6 +290,7 @@ struct ItemArgs {
     int* status = nullptr;
     float ext[4] = {0, 0, 0, 0};
     int used = 0;
+    int uni_relax = 0;                    // every group has one T1 and one T2 (relaxation once per thread)
 };
 
 struct ReduceArgs {
@@ -331,6 +345,17 @@ int host_phantom32(int64_t n, const double* x, const double* y, const double* z,
 int host_records32(int64_t n_steps, const double* dt, const double* gx, const double* gy, const double* gz,
                    const double* b1_re, const double* b1_im, const uint8_t* adc, std::vector<Rec32>& r32,
                    koma_sequence_info& info, std::string& err);
+// The upload's input rules alone, without building anything (requests the
+// server hands to koma_simulate, which converts on the device): spins
+// (finite, pd >= 0, T1/T2 > 0 or +inf) and sequence arrays (dt > 0 finite,
+// finite G and B1, adc 0/1). `info` receives n_steps, n_adc, n_rf and, in
+// n_materialize, the number of RF runs (the state changes only there, so the
+// readout keeps at most that many + 1 snapshots).
+int host_check_phantom(int64_t n, const double* x, const double* y, const double* z, const double* pd,
+                       const double* t1, const double* t2, const double* dw, std::string& err);
+int host_check_sequence(int64_t n_steps, const double* dt, const double* gx, const double* gy, const double* gz,
+                        const double* b1_re, const double* b1_im, const uint8_t* adc, koma_sequence_info& info,
+                        std::string& err);
 // Repeated RF pulses of a record stream: marks the header records of the
 // runs taken by maps (k0 = 1 + slot) and returns the slots' pulses; `info`
 // gets the n_rf_map* counts.
@@ -369,8 +394,9 @@ int launch_reduce(const ReduceArgs& r, bool fp64_partials, void* stream);
 // One thread waits, bounded by limit_ns, on an mbarrier nothing completes,
 // then sets bit 1 of *status (the timeout path of the record-tile waits).
 int launch_bounded_wait_check(int* status, unsigned long long limit_ns, void* stream);
-int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, void* stream);
-int items_ctas_per_sm(int spins_per_thread, int block);
+// `tile`: step records per shared-memory tile, 64, 128 or 256.
+int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, int tile, void* stream);
+int items_ctas_per_sm(int spins_per_thread, int block, int tile);
 // Serving kernel (4 spins per thread, `block` threads: a batch is 128 x
 // block/32 spins).
 int launch_batches(const BatchArgs& a, int grid, int block, void* stream);

@@ -265,7 +265,7 @@ __device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
 // values stay 0): no per-slot branch, so the S spins' dependency chains
 // interleave.
 // ---------------------------------------------------------------------------
-template <int S>
+template <int S, bool UNI = false>
 struct Spins {
     static_assert(S % 2 == 0, "spins are processed in packed pairs");
     static constexpr int NP = S / 2;
@@ -287,6 +287,9 @@ struct Spins {
     bool rf_grad;                  // the run's gradient reaches some spin (else theta_z = pi dt df)
     float key0, key1, key2, key3;  // zr/zi belong to this (dK, dtau)
     float kb0, kb1, kb2, kb3;      // zr2/zi2 belong to this one (the previous run's)
+    // every spin of the walk has the same T1 and T2 (a dictionary entry's
+    // isochromats): relaxation factors are evaluated once, for slot 0
+    static constexpr bool uni = UNI;
 
     __device__ __forceinline__ int64_t index(int s) const { return base + static_cast<int64_t>(s) * stride; }
 
@@ -537,10 +540,20 @@ struct Spins {
         if (dt != dt_cached) {
             // relaxation factors minus one over dt, relatively accurate for
             // short steps (r = log2(e)/T, so -dt/T = -dt r ln 2)
+            if (uni) {
+                const float a = expm1_f32(-dt * r1[0] * 0.693147180559945309f);
+                const float b = expm1_f32(-dt * r2[0] * 0.693147180559945309f);
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                em1[s] = expm1_f32(-dt * r1[s] * 0.693147180559945309f);
-                em2[s] = expm1_f32(-dt * r2[s] * 0.693147180559945309f);
+                for (int s = 0; s < S; ++s) {
+                    em1[s] = a;
+                    em2[s] = b;
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    em1[s] = expm1_f32(-dt * r1[s] * 0.693147180559945309f);
+                    em2[s] = expm1_f32(-dt * r2[s] * 0.693147180559945309f);
+                }
             }
             dt_cached = dt;
         }
@@ -614,6 +627,12 @@ struct Spins {
         const float kzh = R.a[4], kzl = R.a[5], th = R.a[6], tl = R.a[7];
         const int terms = (R.count >> kTermShift) & used;
         const bool ux = terms & 1, uy = terms & 2, uz = terms & 4, uf = terms & 8;
+        // the decays of every slot, or once when all spins share T1 and T2
+        float e2u = 0.f, e1u = 0.f;
+        if (uni) {
+            e2u = exp2f(-th * r2[0]);
+            if (prec) e1u = exp2f(-th * r1[0]);
+        }
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             er[s] = 0.f;
@@ -633,11 +652,11 @@ struct Spins {
                 const float r = F - rintf(F);
                 __sincosf(-6.28318530717958647692f * r, &sn, &cs);
             }
-            const float e2 = exp2f(-th * r2[s]);
+            const float e2 = uni ? e2u : exp2f(-th * r2[s]);
             er[s] = e2 * fmaf(mx[s], cs, -my[s] * sn);
             ei[s] = e2 * fmaf(mx[s], sn, my[s] * cs);
             if (prec) {
-                const float e1 = exp2f(-th * r1[s]);
+                const float e1 = uni ? e1u : exp2f(-th * r1[s]);
                 mx[s] = er[s];
                 my[s] = ei[s];
                 mz[s] = fmaf(mz[s] - m0[s], e1, m0[s]);
@@ -859,7 +878,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
             // a tile never arrived: report, wait (bounded) for the copies in
             // flight into this CTA's shared memory, and leave
             if (tid == 0) {
-                atomicOr(A.status, 1);
+                atomicOr(A.status, kStatusTimeout);
                 mbar_wait_bounded(bar[b], static_cast<uint32_t>((t >> 1) & 1));
                 if (t + 1 < n_tiles) mbar_wait_bounded(bar[b ^ 1], static_cast<uint32_t>(((t + 1) >> 1) & 1));
             }
@@ -873,7 +892,10 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
                 sp.rf(R, A.ext);
             } else if (type == REC_MAP) {
                 // a repeated pulse as a whole (compacted stream)
-                sp.apply_map(A.rf_maps + R.k0 * kRfMapFloats * np, np);
+                if (R.k0 >= 0 && R.k0 < A.n_rf_maps)
+                    sp.apply_map(A.rf_maps + R.k0 * kRfMapFloats * np, np);
+                else if (tid == 0)
+                    atomicOr(A.status, kStatusBadMap);
             } else if (type == REC_PREC) {
                 float er[S], ei[S];
                 sp.exact(R, true, A.p32, np, A.used, er, ei);
@@ -884,7 +906,9 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
                     // staged (its samples of this CTA's row are never read); the
                     // first of its block stores the block's Mxy(t_ref)
                     if (R.count & kMmaSnapFlag) {
-                        if (own) {
+                        if (mma_snap_row >= A.n_mma_snaps) {
+                            if (tid == 0) atomicOr(A.status, kStatusBadSnap);
+                        } else if (own) {
                             float2* __restrict__ row = A.mma_snap + static_cast<int64_t>(mma_snap_row) * np;
 #pragma unroll
                             for (int s = 0; s < S; ++s) {
@@ -899,6 +923,10 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
                 }
                 const int L = min(max(R.count & kCountMask, 1), kMaxAdcRun);
                 const int64_t k0 = R.k0;
+                if (k0 < red_base || k0 + L > A.n_adc) {  // inside the row, not before the staged window
+                    if (tid == 0) atomicOr(A.status, kStatusBadAdc);
+                    continue;
+                }
                 if (k0 + L > red_base + kRed32) {
                     flush();
                     // samples skipped since (matrix-form runs) are not this row's
@@ -1016,56 +1044,61 @@ struct MapPair {
         }
         const f32x2 ux = mul2(pk(R.a[3], R.a[3]), nsinc), uy = mul2(pk(R.a[4], R.a[4]), nsinc);
         const f32x2 uz = mul2(az, nsinc);
-        const f32x2 nux = neg2(ux), nuy = neg2(uy), nuz = neg2(uz);
-        // 2 / |q|^2 to first order: the map is applied many times, so its
-        // rotation part is kept orthogonal to FP32 rounding on every path
-        const f32x2 nq = fma2(ch, ch, fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))));
+        // 2 / |q|^2 to first order (|u|^2 = t^2 sinc^2): the map is applied
+        // many times, so its rotation part is kept orthogonal to FP32
+        // rounding on every path
+        const f32x2 nq = fma2(ch, ch, mul2(mul2(nsinc, nsinc), t2));
         const f32x2 c2 = fma2(pk(-2.f, -2.f), nq, pk(4.f, 4.f));
-        // rotation increment c2 (w (u x m) + u x (u x m)) of a vector m
-        auto incr = [&](f32x2 MX, f32x2 MY, f32x2 MZ, f32x2& dx, f32x2& dy, f32x2& dz) {
-            const f32x2 px = fma2(uy, MZ, mul2(nuz, MY));
-            const f32x2 py = fma2(uz, MX, mul2(nux, MZ));
-            const f32x2 pz = fma2(ux, MY, mul2(nuy, MX));
-            const f32x2 qx = fma2(uy, pz, mul2(nuz, py));
-            const f32x2 qy = fma2(uz, px, mul2(nux, pz));
-            const f32x2 qz = fma2(ux, py, mul2(nuy, px));
-            dx = mul2(c2, fma2(ch, px, qx));
-            dy = mul2(c2, fma2(ch, py, qy));
-            dz = mul2(c2, fma2(ch, pz, qz));
-        };
-        // hi + lo += d for one component: TwoSum, the error into lo
+        // the step's rotation minus the identity, R - I = c2 (w [u]x + u u^T -
+        // |u|^2 I) (the quaternion update v + c2 (w u x v + u x (u x v)) as a
+        // matrix), built once and applied to the seven vectors
+        const f32x2 cx = mul2(c2, ux), cy = mul2(c2, uy), cz = mul2(c2, uz);
+        const f32x2 wx = mul2(cx, ch), wy = mul2(cy, ch), wz = mul2(cz, ch);
+        const f32x2 sxy = mul2(cx, uy), sxz = mul2(cx, uz), syz = mul2(cy, uz);
+        const f32x2 qx = mul2(cx, ux), qy = mul2(cy, uy), qz = mul2(cz, uz);
+        const f32x2 Mxx = neg2(add2(qy, qz)), Myy = neg2(add2(qx, qz)), Mzz = neg2(add2(qx, qy));
+        const f32x2 Mxy = sub2(sxy, wz), Myx = add2(sxy, wz);
+        const f32x2 Mxz = add2(sxz, wy), Mzx = sub2(sxz, wy);
+        const f32x2 Myz = sub2(syz, wx), Mzy = add2(syz, wx);
+        // with the relaxation folded in: the whole step is m -> m + N m (+ the
+        // recovery on z for c), N = (I + E)(I + M) - I = M + E (I + M) with
+        // E = diag(E2, E2, E1) (the relaxation factors minus one)
+        const f32x2 Nxx = fma2(E2, Mxx, add2(Mxx, E2)), Nyy = fma2(E2, Myy, add2(Myy, E2));
+        const f32x2 Nzz = fma2(E1, Mzz, add2(Mzz, E1));
+        const f32x2 Nxy = fma2(E2, Mxy, Mxy), Nxz = fma2(E2, Mxz, Mxz);
+        const f32x2 Nyx = fma2(E2, Myx, Myx), Nyz = fma2(E2, Myz, Myz);
+        const f32x2 Nzx = fma2(E1, Mzx, Mzx), Nzy = fma2(E1, Mzy, Mzy);
+        // hi + lo += d for one component (Fast2Sum: exact while |hi| >= |d|,
+        // the case of the small per-step increments compensation is for;
+        // otherwise within one rounding of d itself)
         auto acc = [](f32x2& h, f32x2& l, f32x2 d) {
             const f32x2 t = add2(h, d);
-            const f32x2 z = sub2(t, h);
-            l = add2(l, add2(sub2(h, sub2(t, z)), sub2(d, z)));
+            l = add2(l, sub2(d, sub2(t, h)));
             h = t;
         };
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            // columns of A: rotated and relaxed (no recovery term); the
-            // increment m' - m = d + E (m + d) is added to hi by TwoSum
-            f32x2 dx, dy, dz;
-            incr(v[3 * q], v[3 * q + 1], v[3 * q + 2], dx, dy, dz);
-            dx = fma2(E2, add2(v[3 * q], dx), dx);
-            dy = fma2(E2, add2(v[3 * q + 1], dy), dy);
-            dz = fma2(E1, add2(v[3 * q + 2], dz), dz);
-            f32x2 lx, ly, lz;
-            incr(lo[3 * q], lo[3 * q + 1], lo[3 * q + 2], lx, ly, lz);
-            lo[3 * q] = add2(lo[3 * q], lx);
-            lo[3 * q + 1] = add2(lo[3 * q + 1], ly);
-            lo[3 * q + 2] = add2(lo[3 * q + 2], lz);
+            // columns of A (no recovery term): the increment N m is added to
+            // hi; lo follows the same step exactly (m + N m, no rounding to
+            // recover there: lo is far below hi's resolution)
+            const f32x2 X = v[3 * q], Y = v[3 * q + 1], Z = v[3 * q + 2];
+            const f32x2 dx = fma2(Nxx, X, fma2(Nxy, Y, mul2(Nxz, Z)));
+            const f32x2 dy = fma2(Nyx, X, fma2(Nyy, Y, mul2(Nyz, Z)));
+            const f32x2 dz = fma2(Nzx, X, fma2(Nzy, Y, mul2(Nzz, Z)));
+            const f32x2 LX = lo[3 * q], LY = lo[3 * q + 1], LZ = lo[3 * q + 2];
+            lo[3 * q] = fma2(Nxx, LX, fma2(Nxy, LY, fma2(Nxz, LZ, LX)));
+            lo[3 * q + 1] = fma2(Nyx, LX, fma2(Nyy, LY, fma2(Nyz, LZ, LY)));
+            lo[3 * q + 2] = fma2(Nzx, LX, fma2(Nzy, LY, fma2(Nzz, LZ, LZ)));
             acc(v[3 * q], lo[3 * q], dx);
             acc(v[3 * q + 1], lo[3 * q + 1], dy);
             acc(v[3 * q + 2], lo[3 * q + 2], dz);
         }
         {
-            // c: Mxy relaxed, Mz + E1 (Mz - M0)
-            f32x2 dx, dy, dz;
-            incr(v[9], v[10], v[11], dx, dy, dz);
-            const f32x2 nx = add2(v[9], dx), ny = add2(v[10], dy), nz = add2(v[11], dz);
-            v[9] = fma2(E2, nx, nx);
-            v[10] = fma2(E2, ny, ny);
-            v[11] = fma2(E1, sub2(nz, M0), nz);
+            // c: the same step plus the recovery M0 (1 - e^{-dt/T1}) = -E1 M0 on z
+            const f32x2 X = v[9], Y = v[10], Z = v[11];
+            v[9] = fma2(Nxx, X, fma2(Nxy, Y, fma2(Nxz, Z, X)));
+            v[10] = fma2(Nyx, X, fma2(Nyy, Y, fma2(Nyz, Z, Y)));
+            v[11] = fma2(Nzx, X, fma2(Nzy, Y, fma2(Nzz, Z, fma2(neg2(E1), M0, Z))));
         }
     }
 };
@@ -1157,21 +1190,21 @@ __global__ void __launch_bounds__(kMapBlock) rf_map_kernel(const __grid_constant
 // RF path exactly as an unsplit walk had it);
 // one that stops before the end saves it there. Returns false if a tile never
 // arrived (status set, copies waited for).
-template <int S>
-__device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const BarPair bar, uint64_t& g0,
+template <int S, int T = kTile, bool UNI = false>
+__device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[T], const BarPair bar, uint64_t& g0,
                                            const float* __restrict__ p32, int64_t np, const Rec32* grec,
                                            int64_t n_rec, int64_t rb, int64_t re, float* state, int64_t rf_hdr,
                                            const float (&ext)[4], int used, int64_t wb, int64_t we,
-                                           float2* __restrict__ row, int* status, float* warp_lo,
-                                           const float* rf_maps = nullptr) {
+                                           float2* __restrict__ row, int64_t n_adc, int* status,
+                                           float* warp_lo, const float* rf_maps = nullptr, int n_maps = 0) {
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const Rec32* base = grec + rb;
     const int64_t n_walk = re - rb;
-    const int64_t n_tiles = (n_walk + kTile - 1) / kTile;
-    Spins<S> sp;
+    const int64_t n_tiles = (n_walk + T - 1) / T;
+    Spins<S, UNI> sp;
     sp.load(p32, np, wb + lane, 32, we);
-    if constexpr (!Spins<S>::kLoRegs) {
+    if constexpr (!Spins<S, UNI>::kLoRegs) {
         // the lo halves of the warp's spins, read at every exact evaluation
         __syncwarp();  // the previous batch's reads of warp_lo are done
 #pragma unroll
@@ -1200,13 +1233,13 @@ __device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const BarPair 
         const bool ok = mbar_wait_bounded(bar[b], static_cast<uint32_t>((g >> 1) & 1));
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
-                atomicOr(status, 1);
+                atomicOr(status, kStatusTimeout);
                 mbar_wait_bounded(bar[b], static_cast<uint32_t>((g >> 1) & 1));
                 if (t + 1 < n_tiles) mbar_wait_bounded(bar[b ^ 1], static_cast<uint32_t>(((g + 1) >> 1) & 1));
             }
             return false;
         }
-        const int nr = static_cast<int>(min(static_cast<int64_t>(kTile), n_walk - t * kTile));
+        const int nr = static_cast<int>(min(static_cast<int64_t>(T), n_walk - t * T));
         for (int r = 0; r < nr; ++r) {
             const Rec32& R = s_rec[b][r];
             const int type = R.type;
@@ -1214,13 +1247,20 @@ __device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const BarPair 
                 sp.rf(R, ext);
             } else if (type == REC_MAP) {
                 // a repeated pulse as a whole (compacted stream)
-                sp.apply_map(rf_maps + R.k0 * kRfMapFloats * np, np);
+                if (R.k0 >= 0 && R.k0 < n_maps)
+                    sp.apply_map(rf_maps + R.k0 * kRfMapFloats * np, np);
+                else if (tid == 0)
+                    atomicOr(status, kStatusBadMap);
             } else if (type == REC_PREC) {
                 float er[S], ei[S];
                 sp.exact(R, true, p32, np, used, er, ei);
             } else if (type == REC_ADC) {
                 const int L = min(max(R.count & kCountMask, 1), kMaxAdcRun);
                 const int64_t k0 = R.k0;
+                if (k0 < 0 || k0 + L > n_adc) {
+                    if (tid == 0) atomicOr(status, kStatusBadAdc);
+                    continue;
+                }
                 float er[S], ei[S];
                 sp.exact(R, false, p32, np, used, er, ei);
                 sp.adc(R, L, er, ei, lane, [&](int i, float sr, float si) {
@@ -1250,9 +1290,9 @@ __device__ __forceinline__ bool walk_batch(Rec32 (*s_rec)[kTile], const BarPair 
 // batches are the shortest. All warps of a CTA walk the record stream
 // together (shared TMA tiles).
 // ---------------------------------------------------------------------------
-template <int S>
+template <int S, int T, bool UNI>
 __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_kernel(const __grid_constant__ ItemArgs A) {
-    __shared__ __align__(128) Rec32 s_rec[2][kTile];
+    __shared__ __align__(128) Rec32 s_rec[2][T];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ float s_lo_w[Spins<S>::kLoRegs ? 1 : kMaxWarps * 4 * S * 32];  // per-warp lo halves
     __shared__ int64_t s_batch;
@@ -1281,8 +1321,9 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_kernel(const __grid_
             ie = A.item_begin[item + 1];
             row = static_cast<float2*>(A.partial) + item * A.n_adc;
         }
-        if (!walk_batch<S>(s_rec, bar, g0, A.p32, A.n_pad, static_cast<const Rec32*>(A.rec), A.n_rec, 0, A.n_rec,
-                           nullptr, -1, A.ext, A.used, ib, ie, row, A.status, s_lo_w + warp * (4 * S * 32)))
+        if (!walk_batch<S, T, UNI>(s_rec, bar, g0, A.p32, A.n_pad, static_cast<const Rec32*>(A.rec), A.n_rec, 0,
+                                   A.n_rec, nullptr, -1, A.ext, A.used, ib, ie, row, A.n_adc, A.status,
+                                   s_lo_w + warp * (4 * S * 32)))
             return;
     }
 }
@@ -1325,7 +1366,8 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_batches_kernel(const __gri
         float2* row = D.rows + static_cast<int64_t>(warp) * D.n_adc;
         const float ext[4] = {D.ext[0], D.ext[1], D.ext[2], D.ext[3]};
         if (!walk_batch<S>(s_rec, bar, g0, D.p32, D.n_pad, D.rec, D.n_rec, D.rec_begin, D.rec_end, D.state,
-                           D.rf_hdr, ext, D.used, wb, we, row, A.status, s_lo_w + warp * (4 * S * 32), D.rf_maps))
+                           D.rf_hdr, ext, D.used, wb, we, row, D.n_adc, A.status, s_lo_w + warp * (4 * S * 32),
+                           D.rf_maps, D.n_rf_maps))
             return;
     }
 }
@@ -1739,7 +1781,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_motion_kernel(const __grid
         const bool ok = mbar_wait_bounded(bar[b], static_cast<uint32_t>((t >> 1) & 1));
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
-                atomicOr(A.status, 1);
+                atomicOr(A.status, kStatusTimeout);
                 mbar_wait_bounded(bar[b], static_cast<uint32_t>((t >> 1) & 1));
                 if (t + 1 < n_tiles) mbar_wait_bounded(bar[b ^ 1], static_cast<uint32_t>(((t + 1) >> 1) & 1));
             }
@@ -1757,6 +1799,10 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_motion_kernel(const __grid
             } else if (type == REC_ADC) {
                 const int L = min(max(R.count & kCountMask, 1), kMaxAdcRun);
                 const int64_t k0 = R.k0;
+                if (k0 < red_base || k0 + L > A.n_adc) {  // inside the row, not before the staged window
+                    if (tid == 0) atomicOr(A.status, kStatusBadAdc);
+                    continue;
+                }
                 if (k0 + L > red_base + kRed32) flush();
                 const int off = static_cast<int>(k0 - red_base);
                 const bool own = !SPLIT || (t * kTile + r) % split == part;
@@ -1888,6 +1934,10 @@ __global__ void __launch_bounds__(kMaxBlock) bloch_fp64_kernel(const __grid_cons
         } else if (type == REC_ADC) {
             const int L = min(max(R.count, 1), kMaxAdcRun);
             const int64_t k0 = R.k0;
+            if (k0 < red_base || k0 + L > A.n_adc) {  // inside the row, not before the staged window
+                if (threadIdx.x == 0) atomicOr(A.status, kStatusBadAdc);
+                continue;
+            }
             if (k0 + L > red_base + kRed) flush();
             for (int l = 0; l < L; ++l) {
                 const double kx = R.a[0] + l * R.a[4], ky = R.a[1] + l * R.a[5], kz = R.a[2] + l * R.a[6];
@@ -2018,23 +2068,22 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-// 4 FP32 columns of this warp's 32 TMEM lanes: load, store
-__device__ __forceinline__ void tc_ld4(uint32_t taddr, float (&v)[4]) {
-    uint32_t r[4];
+// 4 FP32 columns of this warp's 32 TMEM lanes: load and store, completed by
+// tc_wait_ld / tc_wait_st (several in flight behind one wait)
+__device__ __forceinline__ void tc_ld4(uint32_t taddr, uint32_t (&r)[4]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = __uint_as_float(r[q]);
+                 : "r"(taddr)
+                 : "memory");
 }
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_st4(uint32_t taddr, const float (&v)[4]) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
                  "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
                  "r"(__float_as_uint(v[3]))
                  : "memory");
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // v = hi + lo as FP16 pairs (a in the low half)
 __device__ __forceinline__ void split_half2(float a, float b, uint32_t& hi, uint32_t& lo) {
@@ -2455,32 +2504,41 @@ __global__ void __launch_bounds__(kMmaCtaThreads, 1) readout_mma_kernel(const __
             if (grp_last && r < G.n_runs) {
                 run_k0 = A.runs[G.run0 + r].k0;
                 run_len = A.runs[G.run0 + r].len;
+                if (run_k0 < 0 || run_k0 + run_len > A.n_adc || run_len > kMaxAdcRun) {  // 128 accumulator columns
+                    atomicOr(A.status, kStatusBadRun);
+                    run_len = 0;
+                }
             }
 #pragma unroll 1
             for (int cc = 0; cc < 32; cc += 4) {
                 const uint32_t col0 = static_cast<uint32_t>(32 * cgrp + cc);
+                uint32_t rv[4], rs[4];
+                tc_ld4(tmem + lanes + static_cast<uint32_t>((sg & 1) * 128) + col0, rv);
+                if (!grp_first) tc_ld4(tmem + lanes + kMmaSumCol + col0, rs);
+                tc_wait_ld();
                 float v[4], sm[4];
-                tc_ld4(tmem + lanes + static_cast<uint32_t>((sg & 1) * 128) + col0, v);
-                if (grp_first) {
-                    // the group's first segment: sum = v, error = 0
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        sm[q] = v[q];
+                for (int q = 0; q < 4; ++q) {
+                    const float x = __uint_as_float(rv[q]);
+                    if (grp_first) {
+                        // the group's first segment: sum = x, error = 0
+                        sm[q] = x;
                         v[q] = 0.f;
-                    }
-                } else {
-                    tc_ld4(tmem + lanes + kMmaSumCol + col0, sm);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {  // TwoSum: sm + v = t + e exactly; v <- e
-                        const float t = sm[q] + v[q];
-                        const float z = t - sm[q];
-                        v[q] = (sm[q] - (t - z)) + (v[q] - z);
+                    } else {
+                        // TwoSum: sum + x = t + e exactly; v <- e
+                        const float a = __uint_as_float(rs[q]);
+                        const float t = a + x;
+                        const float z = t - a;
+                        v[q] = (a - (t - z)) + (x - z);
                         sm[q] = t;
                     }
-                    float er[4];
-                    tc_ld4(tmem + lanes + kMmaErrCol + col0, er);
+                }
+                if (!grp_first) {
+                    // plus the errors of the earlier segments
+                    tc_ld4(tmem + lanes + kMmaErrCol + col0, rs);
+                    tc_wait_ld();
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) v[q] += er[q];
+                    for (int q = 0; q < 4; ++q) v[q] += __uint_as_float(rs[q]);
                 }
                 if (grp_last) {
 #pragma unroll
@@ -2493,6 +2551,7 @@ __global__ void __launch_bounds__(kMmaCtaThreads, 1) readout_mma_kernel(const __
                     tc_st4(tmem + lanes + kMmaErrCol + col0, v);
                 }
             }
+            if (!grp_last) tc_wait_st();
             tc_fence_before();
             mbar_arrive(acc_free(sg & 1));
             ++sg;
@@ -2510,7 +2569,7 @@ __global__ void __launch_bounds__(kMmaCtaThreads, 1) readout_mma_kernel(const __
     }
     __syncthreads();
     if (*s_abort && tid == 0) {
-        atomicOr(A.status, 1);
+        atomicOr(A.status, kStatusTimeout);
         // tensor memory is released only after every issued MMA completed
         // (commits complete in order: wait for the latest)
         const int n = *s_issued;
@@ -2594,7 +2653,7 @@ __global__ void bounded_wait_check_kernel(int* status, unsigned long long limit_
     const uint32_t bar = smem_u32(&s_bar);
     mbar_init(bar, 1);
     fence_mbar_init();
-    if (!mbar_wait_bounded(bar, 0, limit_ns)) atomicOr(status, 2);
+    if (!mbar_wait_bounded(bar, 0, limit_ns)) atomicOr(status, kStatusWaitCheck);
 }
 
 // ---------------------------------------------------------------------------
@@ -2698,7 +2757,7 @@ cudaError_t prepare_fp32(size_t dyn) {
 
 template <int S>
 cudaError_t occupancy_fp32(int* n, int block, size_t dyn) {
-    cudaError_t e = prepare_fp32<S>(dyn);
+    cudaError_t e = prepare_fp32<S>(fp32_dyn_smem(kMaxBlock));
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, bloch_fp32_kernel<S, false>, block, dyn);
 }
@@ -2706,7 +2765,10 @@ cudaError_t occupancy_fp32(int* n, int block, size_t dyn) {
 template <int S>
 cudaError_t launch_fp32(const BlochArgs& a, const BlochLaunch& L, cudaStream_t st) {
     const size_t dyn = fp32_dyn_smem(L.block);
-    cudaError_t e = prepare_fp32<S>(dyn);
+    // the kernel's dynamic shared-memory limit is process-wide: set it to what
+    // the largest block needs (never lower), so launches from other threads
+    // with larger blocks are not invalidated between their set-up and launch
+    cudaError_t e = prepare_fp32<S>(fp32_dyn_smem(kMaxBlock));
     if (e != cudaSuccess) return e;
     if (a.split > 1)
         bloch_fp32_kernel<S, true><<<L.grid, L.block, dyn, st>>>(a);
@@ -2723,18 +2785,24 @@ cudaError_t prepare_motion(size_t dyn) {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
 }
 
-template <int S>
+template <int S, int T>
 cudaError_t occupancy_items(int* n, int block) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, bloch_items_kernel<S>, block, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, bloch_items_kernel<S, T, false>, block, 0);
 }
 
 }  // namespace
 
 int bloch_max_block() { return kMaxBlock; }
 
-int items_ctas_per_sm(int spins_per_thread, int block) {
+int items_ctas_per_sm(int spins_per_thread, int block, int tile) {
     int n = 0;
-    cudaError_t e = spins_per_thread == 2 ? occupancy_items<2>(&n, block) : occupancy_items<4>(&n, block);
+    cudaError_t e = cudaErrorInvalidValue;
+    if (spins_per_thread == 2)
+        e = tile == 256 ? occupancy_items<2, 256>(&n, block)
+                        : tile == 128 ? occupancy_items<2, 128>(&n, block) : occupancy_items<2, 64>(&n, block);
+    else if (spins_per_thread == 4)
+        e = tile == 256 ? occupancy_items<4, 256>(&n, block)
+                        : tile == 128 ? occupancy_items<4, 128>(&n, block) : occupancy_items<4, 64>(&n, block);
     return e == cudaSuccess ? n : -1;
 }
 
@@ -2750,12 +2818,24 @@ int launch_batches(const BatchArgs& a, int grid, int block, void* stream) {
     return cudaGetLastError();
 }
 
-int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, void* stream) {
+int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, int tile, void* stream) {
     if (block <= 0 || block > kMaxBlock || block % 32 != 0 || grid <= 0) return cudaErrorInvalidValue;
+    if (tile != 64 && tile != 128 && tile != 256) return cudaErrorInvalidValue;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    switch (spins_per_thread) {
-        case 2: bloch_items_kernel<2><<<grid, block, 0, st>>>(a); break;
-        case 4: bloch_items_kernel<4><<<grid, block, 0, st>>>(a); break;
+    const int key = (a.uni_relax ? 10000 : 0) + spins_per_thread * 1000 + tile;
+    switch (key) {
+        case 2064: bloch_items_kernel<2, 64, false><<<grid, block, 0, st>>>(a); break;
+        case 2128: bloch_items_kernel<2, 128, false><<<grid, block, 0, st>>>(a); break;
+        case 2256: bloch_items_kernel<2, 256, false><<<grid, block, 0, st>>>(a); break;
+        case 4064: bloch_items_kernel<4, 64, false><<<grid, block, 0, st>>>(a); break;
+        case 4128: bloch_items_kernel<4, 128, false><<<grid, block, 0, st>>>(a); break;
+        case 4256: bloch_items_kernel<4, 256, false><<<grid, block, 0, st>>>(a); break;
+        case 12064: bloch_items_kernel<2, 64, true><<<grid, block, 0, st>>>(a); break;
+        case 12128: bloch_items_kernel<2, 128, true><<<grid, block, 0, st>>>(a); break;
+        case 12256: bloch_items_kernel<2, 256, true><<<grid, block, 0, st>>>(a); break;
+        case 14064: bloch_items_kernel<4, 64, true><<<grid, block, 0, st>>>(a); break;
+        case 14128: bloch_items_kernel<4, 128, true><<<grid, block, 0, st>>>(a); break;
+        case 14256: bloch_items_kernel<4, 256, true><<<grid, block, 0, st>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -2793,7 +2873,7 @@ size_t motion_dyn_smem(int block) {
 
 int motion_ctas_per_sm(int block) {
     const size_t dyn = motion_dyn_smem(block);
-    if (prepare_motion(dyn) != cudaSuccess) return -1;
+    if (prepare_motion(motion_dyn_smem(kMaxBlock)) != cudaSuccess) return -1;
     int n = 0;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_motion_kernel<kMotionSpinsPerThread, false>,
                                                          block, dyn) == cudaSuccess ? n : -1;
@@ -2804,7 +2884,7 @@ int launch_bloch_motion(const BlochArgs& a, const BlochLaunch& L, void* stream) 
         L.spins_per_thread != kMotionSpinsPerThread || !a.pv32)
         return cudaErrorInvalidValue;
     const size_t dyn = motion_dyn_smem(L.block);
-    cudaError_t e = prepare_motion(dyn);
+    cudaError_t e = prepare_motion(motion_dyn_smem(kMaxBlock));  // never lowered (see launch_fp32)
     if (e != cudaSuccess) return e;
     if (a.split > 1)
         bloch_motion_kernel<kMotionSpinsPerThread, true><<<L.grid, L.block, dyn, static_cast<cudaStream_t>(stream)>>>(a);

@@ -65,7 +65,10 @@ struct koma_ctx {
     bool maps_timed = false;        // the last timed call ran the pre-pass
     // autotuner results by problem shape (see tune_key): launches of a shape
     // tuned once reuse the choice for other phantoms and sequences of that shape
-    std::map<uint64_t, std::pair<int, int>> tune_cache;  // key -> (spins per thread, block)
+    struct TuneChoice {
+        int s, block, tile;  // spins per thread, threads per CTA, records per tile
+    };
+    std::map<uint64_t, TuneChoice> tune_cache;  // shape key -> choice
     koma::ConvertStatus* d_conv = nullptr;  // checks and extents of the last phantom upload
     koma::ConvertStatus* h_conv = nullptr;  // pinned host copy of *d_conv
 };
@@ -103,7 +106,10 @@ struct koma_phantom {
     // configuration chosen by koma_tune for one sequence
     const koma_sequence* tuned_seq = nullptr;
     int64_t tuned_n_rec = -1;
-    int tuned_s = 0, tuned_block = 0;
+    int tuned_s = 0, tuned_block = 0, tuned_tile = 0;
+    // every group has a single T1 and a single T2 (a dictionary's entries):
+    // the grouped kernel evaluates relaxation once per thread
+    bool uni_relax = false;
 };
 
 struct koma_sequence {
@@ -204,6 +210,24 @@ void dev_free(koma_ctx* ctx, void* p, size_t bytes) {
     cudaFreeAsync(p, ctx->alloc_stream);
     cudaStreamSynchronize(ctx->alloc_stream);
     ctx->used -= std::min(ctx->used, bytes);
+}
+
+// Host -> device copy that has landed when the call returns. A plain
+// cudaMemcpy from pageable memory may return once the data is staged, before
+// the DMA into device memory completes, and it runs on the legacy default
+// stream, which the library's non-blocking streams do not wait for: a kernel
+// launched next on such a stream could read the block before it arrived.
+// The copy is therefore ordered on the context's own stream and waited for.
+cudaError_t h2d_sync(koma_ctx* ctx, void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->own_stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(ctx->own_stream) : e;
+}
+
+// Device memset complete on return (same reason as h2d_sync).
+cudaError_t memset_sync(koma_ctx* ctx, void* dst, int value, size_t bytes) {
+    cudaError_t e = cudaMemsetAsync(dst, value, bytes, ctx->own_stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(ctx->own_stream) : e;
 }
 
 inline void split(double v, float* hi, float* lo) {
@@ -360,8 +384,8 @@ extern "C" koma_status koma_init(int device, size_t mem_budget_bytes, koma_ctx**
     DeviceGuard g(device);
     if (!g.ok || cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(reinterpret_cast<void**>(&ctx->d_status), 2 * sizeof(int)) != cudaSuccess ||
-        cudaMemset(ctx->d_status, 0, 2 * sizeof(int)) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        memset_sync(ctx, ctx->d_status, 0, 2 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         if (ctx->d_status) cudaFree(ctx->d_status);
         delete ctx;
@@ -457,7 +481,14 @@ koma_status phantom_upload_start(koma_ctx* ctx, int64_t n, const double* x, cons
     ph->n = n;
     ph->n_pad = std::max<int64_t>(32, (n + 31) / 32 * 32);
     ph->n_groups = group_offsets ? n_groups : 1;
-    if (group_offsets) ph->group_offsets.assign(group_offsets, group_offsets + n_groups + 1);
+    if (group_offsets) {
+        ph->group_offsets.assign(group_offsets, group_offsets + n_groups + 1);
+        bool uni = true;
+        for (int64_t gi = 0; gi < n_groups && uni; ++gi)
+            for (int64_t j = group_offsets[gi] + 1; j < group_offsets[gi + 1] && uni; ++j)
+                uni = t1[j] == t1[group_offsets[gi]] && t2[j] == t2[group_offsets[gi]];
+        ph->uni_relax = uni;
+    }
     const int64_t np = ph->n_pad;
 
     DeviceGuard g(ctx->device);
@@ -616,8 +647,8 @@ extern "C" koma_status koma_phantom_set_motion(koma_phantom* ph, const double* v
         }
         ph->bytes += bv32 + bv64;
     }
-    cudaError_t e = cudaMemcpy(ph->pv32, h32.data(), bv32, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(ph->pv64, h64.data(), bv64, cudaMemcpyHostToDevice);
+    cudaError_t e = h2d_sync(ctx, ph->pv32, h32.data(), bv32);
+    if (e == cudaSuccess) e = h2d_sync(ctx, ph->pv64, h64.data(), bv64);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "phantom_set_motion: copy");
     for (int d = 0; d < 3; ++d) ph->max_v[d] = mv[d];
     return KOMA_OK;
@@ -1172,7 +1203,7 @@ extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, cons
         if (!mp.from.empty()) std::memcpy(host.data() + b32 + b64 + bm + bg + br, mp.from.data(), mp.from.size());
         if (bp) std::memcpy(host.data() + b32 + b64 + bm + bg + br + bf, fp.pulses.data(), bp);
         if (bc) std::memcpy(host.data() + b32 + b64 + bm + bg + br + bf + bp, rc.data(), bc);
-        cudaError_t e = cudaMemcpy(seq->r32, host.data(), host.size(), cudaMemcpyHostToDevice);
+        cudaError_t e = h2d_sync(ctx, seq->r32, host.data(), host.size());
         if (e != cudaSuccess) st = cuda_fail(ctx, e, "sequence_upload: copy");
     }
     if (st != KOMA_OK) {
@@ -1264,9 +1295,9 @@ koma_status ensure_items(koma_ctx* ctx, koma_phantom* ph, int S) {
     ph->items_bytes = b_items + b_order + b_gi;
     ph->d_order = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ph->d_items) + b_items);
     ph->d_group_item = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ph->d_items) + b_items + b_order);
-    cudaError_t e = cudaMemcpy(ph->d_items, begin.data(), b_items, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && b_order) e = cudaMemcpy(ph->d_order, order.data(), b_order, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(ph->d_group_item, gi.data(), b_gi, cudaMemcpyHostToDevice);
+    cudaError_t e = h2d_sync(ctx, ph->d_items, begin.data(), b_items);
+    if (e == cudaSuccess) e = h2d_sync(ctx, ph->d_order, order.data(), b_order);
+    if (e == cudaSuccess) e = h2d_sync(ctx, ph->d_group_item, gi.data(), b_gi);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "simulate: work-item table copy");
     ph->n_items = n_items;
     ph->items_s = S;
@@ -1295,11 +1326,11 @@ koma_status grow_scratch(koma_ctx* ctx, size_t need, cudaStream_t st) {
 
 // Grouped kernel (K3) + per-group reduction (K2).
 koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence* seq, double* sig_dev,
-                           cudaStream_t st, int S, int block) {
+                           cudaStream_t st, int S, int block, int tile) {
     koma_status rc = ensure_items(ctx, ph, S);
     if (rc != KOMA_OK) return rc;
     const int64_t n_adc = seq->info.n_adc;
-    const int per_sm = std::max(1, koma::items_ctas_per_sm(S, block));
+    const int per_sm = std::max(1, koma::items_ctas_per_sm(S, block, tile));
     const int64_t batches = (ph->n_items + block / 32 - 1) / (block / 32);
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(batches,
                                                          static_cast<int64_t>(ctx->sm_count) * per_sm)));
@@ -1319,10 +1350,11 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     A.n_adc = n_adc;
     A.status = ctx->d_status;
     phantom_ext(ph, A.ext, &A.used);
+    A.uni_relax = ph->uni_relax ? 1 : 0;
     cudaError_t ce = cudaMemsetAsync(A.counter, 0, sizeof(int), st);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "simulate: counter reset");
     if (ctx->timing) cudaEventRecord(ctx->ev[0], st);
-    int e = koma::launch_items(A, grid, block, S, st);
+    int e = koma::launch_items(A, grid, block, S, tile, st);
     if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: grouped kernel launch");
     if (ctx->timing) {
         cudaEventRecord(ctx->ev[1], st);
@@ -1349,6 +1381,7 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     ctx->last.n_records = seq->info.n_records;
     ctx->last.partial_bytes = static_cast<int64_t>(ph->n_items * n_adc * 8);
     ctx->last.split = 1;
+    ctx->last.tile_records = tile;
     return KOMA_OK;
 }
 
@@ -1437,22 +1470,24 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
         const bool tuned = ph->tuned_seq == seq && ph->tuned_n_rec == seq->info.n_records;
         // untuned default: the tuner's usual pick for dictionaries of small groups
         int S = tuned ? ph->tuned_s : 2, block = tuned ? ph->tuned_block : 128;
+        int tile = tuned && ph->tuned_tile > 0 ? ph->tuned_tile : 64;
         if (!tuned) {
             auto it = ctx->tune_cache.find(tune_key(ph, seq, true));
             if (it != ctx->tune_cache.end()) {
-                S = it->second.first;
-                block = it->second.second;
+                S = it->second.s;
+                block = it->second.block;
+                tile = it->second.tile;
             }
         }
         ctx->timing_recorded = false;
         ctx->maps_timed = false;
-        return simulate_items(ctx, ph, seq, sig_dev, st, S, block);
+        return simulate_items(ctx, ph, seq, sig_dev, st, S, block, tile);
     }
     const bool tuned_k1 = ph->tuned_seq == seq && ph->tuned_n_rec == seq->info.n_records && ph->tuned_s > 0;
     int s_k1 = tuned_k1 ? ph->tuned_s : 4;
     if (!tuned_k1 && !fp64) {
         auto it = ctx->tune_cache.find(tune_key(ph, seq, false));
-        if (it != ctx->tune_cache.end()) s_k1 = it->second.first;
+        if (it != ctx->tune_cache.end()) s_k1 = it->second.s;
     }
     koma::BlochLaunch L = choose_launch(ctx, ph->n, fp64, s_k1, moving);
     if (ph->n_groups > 1) {
@@ -1518,9 +1553,8 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
             if (s != KOMA_OK) return s;
             ph->table_bytes = tbytes;
             ph->d_group_cta = reinterpret_cast<int32_t*>(ph->d_cta_begin + h.size());
-            cudaError_t e = cudaMemcpy(ph->d_cta_begin, h.data(), h.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
-            if (e == cudaSuccess)
-                e = cudaMemcpy(ph->d_group_cta, gc.data(), gc.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+            cudaError_t e = h2d_sync(ctx, ph->d_cta_begin, h.data(), h.size() * sizeof(int64_t));
+            if (e == cudaSuccess) e = h2d_sync(ctx, ph->d_group_cta, gc.data(), gc.size() * sizeof(int32_t));
             if (e != cudaSuccess) return cuda_fail(ctx, e, "simulate: CTA table copy");
             ph->grid = static_cast<int>(n_cta);
             ph->cfg_spc = L.spins_per_cta;
@@ -1593,6 +1627,7 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     if (use_mma) {
         char* base = static_cast<char*>(ctx->scratch);
         A.mma_snap = reinterpret_cast<float2*>(base + off_e);
+        A.n_mma_snaps = seq->n_mma_snaps;
         M.p32 = ph->p32;
         M.n_pad = ph->n_pad;
         M.n = ph->n;
@@ -1657,6 +1692,7 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     ctx->last.n_records = A.n_rec;
     ctx->last.partial_bytes = static_cast<int64_t>(need);
     ctx->last.split = split;
+    ctx->last.tile_records = moving ? 64 : (fp64 ? 0 : 256);
     return KOMA_OK;
 }
 
@@ -1739,6 +1775,7 @@ extern "C" koma_status koma_simulate_static(const koma_phantom* ph, const koma_s
     ctx->last.n_records = seq->info.n_records;
     ctx->last.partial_bytes = static_cast<int64_t>(L.grid) * n_adc * static_cast<int64_t>(sizeof(float2));
     ctx->last.split = 1;
+    ctx->last.tile_records = 256;
     return KOMA_OK;
 }
 
@@ -1753,16 +1790,20 @@ extern "C" koma_status koma_tune(koma_ctx* ctx, const koma_phantom* ph_c, const 
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     struct Cand {
-        int s, block;
+        int s, block, tile;
     };
     std::vector<Cand> cands;
     const bool items = !ph->moving() && use_items_kernel(ph);
-    if (ph->moving())
-        cands = {{koma::kMotionSpinsPerThread, 0}};  // one motion kernel shape
-    else if (items)
-        cands = {{2, 128}, {2, 256}, {4, 128}, {4, 256}};
-    else
-        cands = {{2, 0}, {4, 0}};
+    if (ph->moving()) {
+        cands = {{koma::kMotionSpinsPerThread, 0, 0}};  // one motion kernel shape
+    } else if (items) {
+        // spins per thread x CTA size x sequence-tile length
+        for (int s_ : {2, 4})
+            for (int b_ : {128, 256})
+                for (int t_ : {64, 128, 256}) cands.push_back({s_, b_, t_});
+    } else {
+        cands = {{2, 0, 0}, {4, 0, 0}};
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(ctx, KOMA_E_CUDA, "tune: event creation");
@@ -1774,6 +1815,7 @@ extern "C" koma_status koma_tune(koma_ctx* ctx, const koma_phantom* ph_c, const 
         ph->tuned_n_rec = seq->info.n_records;
         ph->tuned_s = cands[i].s;
         ph->tuned_block = cands[i].block;
+        ph->tuned_tile = cands[i].tile;
         // one untimed run (tables, scratch), one timed
         for (int rep = 0; rep < 2 && rc == KOMA_OK; ++rep) {
             if (rep == 1) cudaEventRecord(e0, st);
@@ -1802,7 +1844,8 @@ extern "C" koma_status koma_tune(koma_ctx* ctx, const koma_phantom* ph_c, const 
     ph->tuned_n_rec = seq->info.n_records;
     ph->tuned_s = pick.s;
     ph->tuned_block = pick.block;
-    ctx->tune_cache[tune_key(ph, seq, items)] = {pick.s, pick.block};
+    ph->tuned_tile = pick.tile;
+    ctx->tune_cache[tune_key(ph, seq, items)] = {pick.s, pick.block, pick.tile};
     if (chosen) {
         rc = koma_simulate(ctx, ph, seq, KOMA_FP32_SPLITPHASE, sig_dev, stream);
         *chosen = ctx->last;
@@ -1827,11 +1870,20 @@ extern "C" koma_status koma_sync(koma_ctx* ctx, void* stream) {
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sync");
     int flag = 0;
-    e = cudaMemcpy(&flag, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    // the status word, read and cleared on the context's stream (ordered
+    // with everything the caller's stream ran before: it was synchronised)
+    e = cudaMemcpyAsync(&flag, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->own_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->own_stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sync: status read");
     if (flag) {
-        cudaMemset(ctx->d_status, 0, sizeof(int));
-        return fail(ctx, KOMA_E_TIMEOUT, "a bounded device-side wait gave up (status 0x%x)", flag);
+        memset_sync(ctx, ctx->d_status, 0, sizeof(int));
+        if (flag & (koma::kStatusTimeout | koma::kStatusWaitCheck))
+            return fail(ctx, KOMA_E_TIMEOUT, "a bounded device-side wait gave up (status 0x%x)", flag);
+        return fail(ctx, KOMA_E_INTERNAL,
+                    "a kernel met a record outside its launch's buffers and skipped it (status 0x%x:%s%s%s%s)",
+                    flag, (flag & koma::kStatusBadAdc) ? " ADC run" : "", (flag & koma::kStatusBadMap) ? " map slot" : "",
+                    (flag & koma::kStatusBadSnap) ? " snapshot row" : "",
+                    (flag & koma::kStatusBadRun) ? " readout run" : "");
     }
     return KOMA_OK;
 }
@@ -2002,6 +2054,57 @@ void compact_records32(const std::vector<Rec32>& r32, std::vector<Rec32>& out) {
             ++i;
         }
     }
+}
+
+int host_check_phantom(int64_t n, const double* x, const double* y, const double* z, const double* pd,
+                       const double* t1, const double* t2, const double* dw, std::string& err) {
+    if (n < 0) {
+        err = "phantom: n < 0";
+        return KOMA_E_INVALID;
+    }
+    if (n > 0 && (!x || !y || !z || !pd || !t1 || !t2 || !dw)) {
+        err = "phantom: NULL array";
+        return KOMA_E_INVALID;
+    }
+    return check_spin_values(n, x, y, z, pd, t1, t2, dw, err) ? KOMA_OK : KOMA_E_INVALID;
+}
+
+int host_check_sequence(int64_t n_steps, const double* dt, const double* gx, const double* gy, const double* gz,
+                        const double* b1_re, const double* b1_im, const uint8_t* adc, koma_sequence_info& info,
+                        std::string& err) {
+    char buf[160];
+    if (n_steps < 0 || !gx || !gy || !gz || !adc || (n_steps > 0 && (!dt || !b1_re || !b1_im))) {
+        err = "sequence: n_steps < 0 or a NULL array";
+        return KOMA_E_INVALID;
+    }
+    int64_t count = 0;
+    for (int64_t i = 0; i <= n_steps; ++i) {
+        if (!std::isfinite(gx[i]) || !std::isfinite(gy[i]) || !std::isfinite(gz[i]) || adc[i] > 1) {
+            snprintf(buf, sizeof(buf), "sequence: bad gradient or adc value at time point %lld", static_cast<long long>(i));
+            err = buf;
+            return KOMA_E_INVALID;
+        }
+        count += adc[i];
+    }
+    int64_t n_rf = 0, rf_runs = 0;
+    bool prev_rf = false;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        if (!std::isfinite(dt[k]) || !(dt[k] > 0) || !std::isfinite(b1_re[k]) || !std::isfinite(b1_im[k])) {
+            snprintf(buf, sizeof(buf), "sequence: bad dt or B1 at step %lld", static_cast<long long>(k));
+            err = buf;
+            return KOMA_E_INVALID;
+        }
+        const bool rf = b1_re[k] != 0.0 || b1_im[k] != 0.0;
+        n_rf += rf;
+        rf_runs += rf && !prev_rf;
+        prev_rf = rf;
+    }
+    info = koma_sequence_info{};
+    info.n_steps = n_steps;
+    info.n_adc = count;
+    info.n_rf = n_rf;
+    info.n_materialize = rf_runs;
+    return KOMA_OK;
 }
 
 void host_rf_maps32(std::vector<Rec32>& r32, std::vector<RfMapPulse>& pulses, koma_sequence_info& info) {

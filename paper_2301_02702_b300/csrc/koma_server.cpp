@@ -30,6 +30,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -46,7 +47,10 @@ constexpr int kBlock = 128;                        // K4 CTA: 4 warps
 constexpr int kWarps = kBlock / 32;
 constexpr int64_t kBatchSpins = kWarps * 32 * 4;   // 4 spins per thread
 constexpr int kSlots = 2;
-constexpr size_t kHeader = 16;                     // int64 n_batches, int32 counter, pad
+constexpr int kLanes = 4;                          // threads (contexts, streams) of the second lane
+constexpr int64_t kDefaultPlainSpins = 32768;      // requests this large take the second lane
+constexpr size_t kHeader = 16;                     // int64 n_batches, int32 counter, int32 status
+constexpr size_t kStatusOff = 12;                  // the launch's device status word in the header
 
 enum ReqState { PENDING, ADMITTED, LANE, REDUCING, DONE, FAILED };
 
@@ -90,10 +94,11 @@ struct Req {
     koma_status err = KOMA_OK;
     std::string msg;
     bool retired = false;  // out of the worker's lists: the waiter may delete it
+    double prep_s = 0, upload_s = 0, run_s = 0;  // host time of submit, lane upload, lane run
     // second lane (koma_simulate): the host arrays until the upload
     bool lane = false;
     int64_t n_groups = 1;
-    std::vector<double> ph64;         // x, y, z, pd, t1, t2, dw, each n long
+    std::unique_ptr<double[]> ph64;   // x, y, z, pd, t1, t2, dw, each n long
     std::vector<int64_t> offsets;     // group offsets (grouped requests)
     std::vector<double> sq64;         // dt [n_steps], gx, gy, gz [n_steps + 1], b1 re, im [n_steps]
     std::vector<uint8_t> sq_adc;
@@ -124,10 +129,13 @@ double now_s() {
 struct koma_server {
     int device = 0;
     int64_t chunk = 4096;  // records per chunk of a batch's walk
-    int64_t plain_spins = 262144;  // requests this large run in the second lane (<= 0: never)
-    koma_ctx* lane_ctx = nullptr;  // the second lane's context and stream
-    cudaStream_t s_lane = nullptr;
-    std::thread lane_worker;
+    int64_t plain_spins = kDefaultPlainSpins;  // requests this large run in the second lane (<= 0: never)
+    // the second lane: kLanes threads, each with a context and a stream of
+    // its own, so one request's upload overlaps another's kernels and
+    // requests that do not fill the GPU run side by side
+    koma_ctx* lane_ctx[kLanes] = {};
+    cudaStream_t s_lane[kLanes] = {};
+    std::thread lane_worker[kLanes];
     std::deque<Req*> lane_q;
     std::condition_variable cv_lane;
     int64_t lane_runs = 0;
@@ -147,7 +155,6 @@ struct koma_server {
     cudaStream_t s_up = nullptr, s_red = nullptr;
     cudaMemPool_t pool = nullptr;
     Slot slots[kSlots];
-    int* d_status = nullptr;
     // statistics
     int64_t submitted = 0, completed = 0, failed = 0, launches = 0, batches = 0;
     std::string fatal;
@@ -299,11 +306,14 @@ koma_status make_slot(koma_server* S, Slot& sl, int64_t cap) {
     A.desc = reinterpret_cast<const koma::BatchDesc*>(sl.d_buf + kHeader);
     A.n_batches_dev = reinterpret_cast<const int64_t*>(sl.d_buf);
     A.counter = reinterpret_cast<int*>(sl.d_buf + 8);
-    A.status = S->d_status;
+    // each launch has its own status word: zeroed by the table copy, read
+    // back into the host header after the kernel
+    A.status = reinterpret_cast<int*>(sl.d_buf + kStatusOff);
     e = cudaStreamBeginCapture(sl.st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaMemcpyAsync(sl.d_buf, sl.h_buf, kHeader + sizeof(koma::BatchDesc), cudaMemcpyHostToDevice, sl.st);
         koma::launch_batches(A, S->grid, kBlock, sl.st);
+        cudaMemcpyAsync(sl.h_buf + kStatusOff, sl.d_buf + kStatusOff, sizeof(int), cudaMemcpyDeviceToHost, sl.st);
         e = cudaStreamEndCapture(sl.st, &sl.graph);
     }
     if (e != cudaSuccess) return cuda_err(S, e, "server: graph capture");
@@ -314,7 +324,10 @@ koma_status make_slot(koma_server* S, Slot& sl, int64_t cap) {
     for (cudaGraphNode_t nd : nodes) {
         cudaGraphNodeType t;
         cudaGraphNodeGetType(nd, &t);
-        if (t == cudaGraphNodeTypeMemcpy) sl.copy = nd;
+        if (t != cudaGraphNodeTypeMemcpy) continue;
+        cudaMemcpy3DParms mp{};
+        cudaGraphMemcpyNodeGetParams(nd, &mp);
+        if (mp.kind == cudaMemcpyHostToDevice) sl.copy = nd;  // the table copy (the other reads the status)
     }
     if (!sl.copy) return cuda_err(S, cudaErrorUnknown, "server: graph has no copy node");
     e = cudaGraphInstantiate(&sl.exec, sl.graph, 0);
@@ -379,6 +392,7 @@ bool launch_slot(koma_server* S, Slot& sl) {
     if (nb == 0) return false;
     *reinterpret_cast<int64_t*>(sl.h_buf) = nb;
     *reinterpret_cast<int32_t*>(sl.h_buf + 8) = 0;
+    *reinterpret_cast<int32_t*>(sl.h_buf + kStatusOff) = 0;
     cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(sl.exec, sl.copy, sl.d_buf, sl.h_buf,
                                                        kHeader + static_cast<size_t>(nb) * sizeof(koma::BatchDesc),
                                                        cudaMemcpyHostToDevice);
@@ -475,10 +489,21 @@ void worker_loop(koma_server* S) {
             if (q == cudaErrorNotReady) continue;
             sl.busy = false;
             progress = true;
+            // the launch's device status: a bounded wait that gave up, or a
+            // record the kernel's bounds checks skipped
+            const int dev_flag = q == cudaSuccess ? *reinterpret_cast<volatile int32_t*>(sl.h_buf + kStatusOff) : 0;
             for (auto& m : sl.members) {
                 Req* r = m.first;
                 if (q != cudaSuccess) {
                     fail_req(r, KOMA_E_CUDA, cudaGetErrorString(q));
+                    continue;
+                }
+                if (dev_flag) {
+                    if (r->state != FAILED)
+                        fail_req(r, (dev_flag & (koma::kStatusTimeout | koma::kStatusWaitCheck)) ? KOMA_E_TIMEOUT : KOMA_E_INTERNAL,
+                                 (dev_flag & (koma::kStatusTimeout | koma::kStatusWaitCheck))
+                                     ? "serving kernel: a bounded device-side wait gave up"
+                                     : "serving kernel: a record pointed outside the request's buffers");
                     continue;
                 }
                 r->batch_busy[m.second] = 0;
@@ -544,12 +569,13 @@ void worker_loop(koma_server* S) {
     }
 }
 
-// Second lane: grouped requests and requests that fill the GPU alone, one at
-// a time through the koma_simulate path (uploads, maps of repeated pulses,
-// the Bloch or grouped kernel, the tensor-core readout, the reduction) on the
-// lane's stream, overlapping the shared launches of the worker. The result
-// goes to the request's pinned buffer; the worker retires the request.
-void lane_loop(koma_server* S) {
+// Second lane, thread k: grouped requests and large requests through the
+// koma_simulate path (uploads, maps of repeated pulses, the Bloch or grouped
+// kernel, the tensor-core readout, the reduction) on the thread's own
+// context and stream, overlapping the other lane threads and the shared
+// launches of the worker. The result goes to the request's pinned buffer;
+// the worker retires the request.
+void lane_loop(koma_server* S, int k) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
@@ -562,39 +588,44 @@ void lane_loop(koma_server* S) {
         S->lane_q.pop_front();
         lk.unlock();
         NvtxRange nvtx_("server lane run");
-        koma_ctx* ctx = S->lane_ctx;
+        koma_ctx* ctx = S->lane_ctx[k];
+        cudaStream_t st_k = S->s_lane[k];
         const int64_t n = r->n, ns = r->n_steps;
-        const double* P = r->ph64.data();
+        const double* P = r->ph64.get();
         const double* Q = r->sq64.data();
         koma_phantom* ph = nullptr;
         koma_sequence* seq = nullptr;
+        const double t_up = now_s();
         koma_status st = koma_phantom_upload(ctx, n, P, P + n, P + 2 * n, P + 3 * n, P + 4 * n, P + 5 * n,
                                              P + 6 * n, r->n_groups > 1 ? r->offsets.data() : nullptr,
                                              r->n_groups, &ph);
         if (st == KOMA_OK)
             st = koma_sequence_upload(ctx, ns, Q, Q + ns, Q + 2 * ns + 1, Q + 3 * ns + 2, Q + 4 * ns + 3,
                                       Q + 5 * ns + 3, r->sq_adc.data(), &seq);
+        const double t_run = now_s();
         const size_t out_bytes = static_cast<size_t>(r->n_groups * r->n_adc) * 2 * sizeof(double);
         double* dsig = nullptr;
         cudaError_t e = cudaSuccess;
         if (st == KOMA_OK && out_bytes) {
-            e = cudaMallocAsync(reinterpret_cast<void**>(&dsig), out_bytes, S->s_lane);
+            e = cudaMallocAsync(reinterpret_cast<void**>(&dsig), out_bytes, st_k);
             if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&r->hsig), out_bytes);
             if (e != cudaSuccess) st = KOMA_E_NOMEM;
         }
-        if (st == KOMA_OK) st = koma_simulate(ctx, ph, seq, KOMA_FP32_SPLITPHASE, dsig, S->s_lane);
+        if (st == KOMA_OK) st = koma_simulate(ctx, ph, seq, KOMA_FP32_SPLITPHASE, dsig, st_k);
         if (st == KOMA_OK && out_bytes)
-            e = cudaMemcpyAsync(r->hsig, dsig, out_bytes, cudaMemcpyDeviceToHost, S->s_lane);
-        if (st == KOMA_OK && e == cudaSuccess) st = koma_sync(ctx, S->s_lane);
+            e = cudaMemcpyAsync(r->hsig, dsig, out_bytes, cudaMemcpyDeviceToHost, st_k);
+        if (st == KOMA_OK && e == cudaSuccess) st = koma_sync(ctx, st_k);
         else if (st == KOMA_OK) st = KOMA_E_CUDA;
         std::string msg = st != KOMA_OK ? std::string(koma_last_error(ctx)) : std::string();
-        if (dsig) cudaFreeAsync(dsig, S->s_lane);
+        if (dsig) cudaFreeAsync(dsig, st_k);
         if (seq) koma_sequence_free(seq);
+        const double t_end = now_s();
         if (ph) koma_phantom_free(ph);
-        cudaStreamSynchronize(S->s_lane);
+        cudaStreamSynchronize(st_k);
         lk.lock();
-        r->ph64.clear();
-        r->ph64.shrink_to_fit();
+        r->upload_s = t_run - t_up;
+        r->run_s = t_end - t_run;
+        r->ph64.reset();
         r->sq64.clear();
         r->sq64.shrink_to_fit();
         r->sq_adc.clear();
@@ -604,7 +635,11 @@ void lane_loop(koma_server* S) {
         if (st == KOMA_OK) {
             r->state = DONE;
         } else {
-            fail_req(r, st, msg.empty() ? "second lane: simulation failed" : msg);
+            char shape[128];
+            snprintf(shape, sizeof(shape), " (request of %lld spins, %lld steps, %lld samples)",
+                     static_cast<long long>(r->n), static_cast<long long>(r->n_steps),
+                     static_cast<long long>(r->n_adc));
+            fail_req(r, st, (msg.empty() ? std::string("second lane: simulation failed") : msg) + shape);
         }
         r->t_done = now_s();
     }
@@ -640,9 +675,7 @@ extern "C" koma_status koma_server_create(const koma_server_config* cfg, koma_se
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&S->sm_count, cudaDevAttrMultiProcessorCount, S->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->s_up, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->s_red, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->s_lane, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&S->d_status), sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(S->d_status, 0, sizeof(int));
+    for (int k = 0; k < kLanes && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&S->s_lane[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) {
         cudaMemPoolProps props{};
         props.allocType = cudaMemAllocationTypePinned;
@@ -655,7 +688,7 @@ extern "C" koma_status koma_server_create(const koma_server_config* cfg, koma_se
         }
     }
     if (e != cudaSuccess) st = cuda_err(S, e, "server: set-up");
-    if (st == KOMA_OK) st = koma_init(S->device, 0, &S->lane_ctx);
+    for (int k = 0; k < kLanes && st == KOMA_OK; ++k) st = koma_init(S->device, 0, &S->lane_ctx[k]);
     if (st == KOMA_OK) {
         const int per_sm = std::max(1, koma::batches_ctas_per_sm(kBlock));
         S->grid = S->sm_count * per_sm;
@@ -670,7 +703,7 @@ extern "C" koma_status koma_server_create(const koma_server_config* cfg, koma_se
         return st;
     }
     S->worker = std::thread(worker_loop, S);
-    S->lane_worker = std::thread(lane_loop, S);
+    for (int k = 0; k < kLanes; ++k) S->lane_worker[k] = std::thread(lane_loop, S, k);
     *out = S;
     return KOMA_OK;
 }
@@ -687,7 +720,12 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
     if (!r) return KOMA_E_NOMEM;
     r->t_submit = now_s();
     std::string err;
-    int st = koma::host_phantom32(n, x, y, z, pd, t1, t2, dw, r->h32, r->n_pad, r->max_abs, err);
+    // the second lane (grouped requests, large ones) converts on the device:
+    // only the input rules are checked here
+    const bool lane = (group_offsets && n_groups > 1) || (S->plain_spins > 0 && n >= S->plain_spins);
+    int st = lane ? koma::host_check_phantom(n, x, y, z, pd, t1, t2, dw, err)
+                  : koma::host_phantom32(n, x, y, z, pd, t1, t2, dw, r->h32, r->n_pad, r->max_abs, err);
+    if (lane) r->n_pad = std::max<int64_t>(32, (n + 31) / 32 * 32);
     if (st == KOMA_OK && group_offsets) {
         // the upload's rules: n_groups >= 1, offsets from 0 to n, non-decreasing
         bool ok = n_groups >= 1 && group_offsets[0] == 0 && group_offsets[n_groups] == n;
@@ -698,7 +736,15 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
         }
     }
     koma_sequence_info info{};
-    if (st == KOMA_OK) st = koma::host_records32(n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, r->recs, info, err);
+    if (st == KOMA_OK && lane) {
+        st = koma::host_check_sequence(n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, info, err);
+        // memory estimate without the records: at most one record per step
+        // and time point, one readout snapshot row per block between RF runs
+        info.n_records = n_steps + 1;
+        info.n_adc_runs = std::min<int64_t>(info.n_adc, info.n_materialize + 1);
+    } else if (st == KOMA_OK) {
+        st = koma::host_records32(n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, r->recs, info, err);
+    }
     if (st != KOMA_OK) {
         std::lock_guard<std::mutex> lk(S->mu);
         S->fatal = err;
@@ -711,15 +757,20 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
     r->n_rec = info.n_records;
     r->n_adc_runs = info.n_adc_runs;
     r->n_groups = group_offsets ? n_groups : 1;
-    r->lane = r->n_groups > 1 || (S->plain_spins > 0 && n >= S->plain_spins);
+    r->lane = lane;
     if (r->lane) {
         // the second lane uploads the request itself: keep the host arrays
-        r->h32.clear();
-        r->h32.shrink_to_fit();
         const double* ph[7] = {x, y, z, pd, t1, t2, dw};
-        r->ph64.resize(static_cast<size_t>(7 * n));
-        for (int k = 0; k < 7; ++k)
-            if (n > 0) std::memcpy(r->ph64.data() + k * n, ph[k], static_cast<size_t>(n) * sizeof(double));
+        if (n > 0) {
+            // not value-initialised: the copy is the only write
+            r->ph64.reset(new (std::nothrow) double[static_cast<size_t>(7 * n)]);
+            if (!r->ph64) {
+                delete r;
+                return KOMA_E_NOMEM;
+            }
+            for (int k = 0; k < 7; ++k)
+                std::memcpy(r->ph64.get() + k * n, ph[k], static_cast<size_t>(n) * sizeof(double));
+        }
         if (group_offsets) r->offsets.assign(group_offsets, group_offsets + n_groups + 1);
         const int64_t v = n_steps + 1;
         r->sq64.resize(static_cast<size_t>(n_steps + 3 * v + 2 * n_steps));
@@ -742,6 +793,7 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
             delete r;
             return KOMA_E_BUSY;
         }
+        r->prep_s = now_s() - r->t_submit;
         r->id = S->next_id++;
         S->all[r->id] = r;
         S->pending.push_back(r);
@@ -792,6 +844,7 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
         delete r;
         return KOMA_E_BUSY;
     }
+    r->prep_s = now_s() - r->t_submit;
     r->id = S->next_id++;
     S->all[r->id] = r;
     S->pending.push_back(r);
@@ -818,6 +871,9 @@ extern "C" koma_status koma_server_wait(koma_server* S, uint64_t id, double time
         info->id = r->id;
         info->n_groups = r->n_groups;
         info->lane = r->lane ? 1 : 0;
+        info->prep_s = r->prep_s;
+        info->upload_s = r->upload_s;
+        info->run_s = r->run_s;
         info->n_spins = r->n;
         info->n_steps = r->n_steps;
         info->n_adc = r->n_adc;
@@ -881,8 +937,10 @@ extern "C" koma_status koma_server_destroy(koma_server* S) {
         S->cv_lane.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
-    if (S->lane_worker.joinable()) S->lane_worker.join();
-    if (S->lane_ctx) koma_destroy(S->lane_ctx);
+    for (int k = 0; k < kLanes; ++k) {
+        if (S->lane_worker[k].joinable()) S->lane_worker[k].join();
+        if (S->lane_ctx[k]) koma_destroy(S->lane_ctx[k]);
+    }
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(S->device);
@@ -904,10 +962,10 @@ extern "C" koma_status koma_server_destroy(koma_server* S) {
         delete r;
     }
     if (S->pool) cudaMemPoolDestroy(S->pool);
-    if (S->d_status) cudaFree(S->d_status);
     if (S->s_up) cudaStreamDestroy(S->s_up);
     if (S->s_red) cudaStreamDestroy(S->s_red);
-    if (S->s_lane) cudaStreamDestroy(S->s_lane);
+    for (int k = 0; k < kLanes; ++k)
+        if (S->s_lane[k]) cudaStreamDestroy(S->s_lane[k]);
     if (prev >= 0) cudaSetDevice(prev);
     delete S;
     return KOMA_OK;

@@ -18,9 +18,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkoma.so")
 
-KOMA_OK, KOMA_E_INVALID, KOMA_E_NOMEM, KOMA_E_CUDA, KOMA_E_TIMEOUT, KOMA_E_BUSY = range(6)
+KOMA_OK, KOMA_E_INVALID, KOMA_E_NOMEM, KOMA_E_CUDA, KOMA_E_TIMEOUT, KOMA_E_BUSY, KOMA_E_INTERNAL = range(7)
 STATUS_NAMES = {0: "KOMA_OK", 1: "KOMA_E_INVALID", 2: "KOMA_E_NOMEM", 3: "KOMA_E_CUDA",
-                4: "KOMA_E_TIMEOUT", 5: "KOMA_E_BUSY"}
+                4: "KOMA_E_TIMEOUT", 5: "KOMA_E_BUSY", 6: "KOMA_E_INTERNAL"}
 KOMA_FP64 = 0
 KOMA_FP32_SPLITPHASE = 1
 PRECISIONS = {"fp64": KOMA_FP64, "fp32": KOMA_FP32_SPLITPHASE}
@@ -49,7 +49,8 @@ class LaunchInfo(ctypes.Structure):
     _fields_ = [("kernels", ctypes.c_int32), ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("spins_per_thread", ctypes.c_int32), ("spins_per_cta", ctypes.c_int64),
                 ("n_records", ctypes.c_int64), ("partial_bytes", ctypes.c_int64),
-                ("bloch_stream", ctypes.c_void_p), ("split", ctypes.c_int32), ("mma_grid", ctypes.c_int32)]
+                ("bloch_stream", ctypes.c_void_p), ("split", ctypes.c_int32), ("mma_grid", ctypes.c_int32),
+                ("tile_records", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -78,7 +79,8 @@ class RequestInfo(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("n_spins", ctypes.c_int64), ("n_steps", ctypes.c_int64),
                 ("n_adc", ctypes.c_int64), ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
                 ("done_s", ctypes.c_double), ("latency_s", ctypes.c_double), ("launches", ctypes.c_int32),
-                ("status", ctypes.c_int), ("n_groups", ctypes.c_int64), ("lane", ctypes.c_int32)]
+                ("status", ctypes.c_int), ("n_groups", ctypes.c_int64), ("lane", ctypes.c_int32),
+                ("prep_s", ctypes.c_double), ("upload_s", ctypes.c_double), ("run_s", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

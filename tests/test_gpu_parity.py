@@ -246,9 +246,12 @@ def test_grouped_kernel_deterministic_and_tuned(sim):
         assert np.array_equal(a, b)
         choice = sim.tune(hp, hs)
         assert choice["spins_per_thread"] in (2, 4) and choice["block"] in (128, 256)
+        assert choice["tile_records"] in (64, 128, 256)  # the sequence-tile length is tuned too
         c = sim.simulate(hp, hs).cpu().numpy()
         sim.sync()
-        assert sim.launch_info()["spins_per_thread"] == choice["spins_per_thread"]
+        info = sim.launch_info()
+        assert info["spins_per_thread"] == choice["spins_per_thread"]
+        assert info["tile_records"] == choice["tile_records"]
         assert rel_err(c, a) < TOL32
         ref = oracle.simulate(ph, seq)
         assert rel_err(c, ref) < TOL32
@@ -338,7 +341,8 @@ def test_tuned_shape_is_reused_by_other_phantoms(sim):
         try:
             got = sim.simulate(hp2, hs).cpu().numpy()
             info = sim.launch_info()
-            assert (info["spins_per_thread"], info["block"]) == (choice["spins_per_thread"], choice["block"])
+            assert (info["spins_per_thread"], info["block"], info["tile_records"]) == (
+                choice["spins_per_thread"], choice["block"], choice["tile_records"])
             ref = oracle.simulate(ph2, seq)
             assert rel_err(got, ref) < TOL32
         finally:

@@ -167,8 +167,9 @@ def test_large_requests_take_the_simulate_lane():
     koma_simulate gives, so the tensor-core readout and the maps of repeated
     pulses apply), while smaller ones share the persistent kernel's launches
     at the same time; both match the oracle."""
-    big = [workload("se128", "small"), workload("epi512", "small")]
-    small = _mix(9, 6)
+    big = [workload("se128", "small"), workload("epi512", "small")]  # 922 and 2,304 spins
+    small = [(random_spins(n, seed=40 + i), random_sequence(300 + 50 * i, seed=60 + i))
+             for i, n in enumerate((1, 17, 300, 640, 800, 899))]
     srv = koma.Server(0, plain_spins=900)
     try:
         ids = [srv.submit(*r) for r in big] + [srv.submit(*r) for r in small]
