@@ -893,8 +893,11 @@ def result_line(args, world, ph, seq, info, launch, stage_ms, clk, value, ms_max
         mflops = float(ph.n) * info["n_rf_map_pulse_steps"] * FLOPS_MAP_STEP
         roofs.append({"bound": "alu", "kernel": "rf_map_kernel", "achieved": mflops / (k7 / 1e3) / 1e12,
                       "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                      "frac": mflops / (k7 / 1e3) / 1e12 / PEAK_FP32_TFLOPS, "traffic": None, "kernel_ms": k7,
+                      "frac": mflops / (k7 / 1e3) / 1e12 / PEAK_FP32_TFLOPS,
+                      "traffic": measured_traffic(args.workload + ":rf_map"), "kernel_ms": k7,
                       "algorithmic_flops_per_launch": mflops,
+                      # 7 FP32 phantom rows read, 12 map floats per spin and pulse written
+                      "algorithmic_bytes_per_launch": 4.0 * ph.n * (7 + 12 * info["n_rf_maps"]),
                       "peak_source": "FP32 peak 148 SMs x 128 lanes x 2 x 2032 MHz (unit counts, max SM clock)",
                       "pulses": info["n_rf_maps"], "pulse_steps": info["n_rf_map_pulse_steps"],
                       "replaces_rf_steps": info["n_rf_map_steps"]})
@@ -972,7 +975,7 @@ def main(argv=None):
     ap.add_argument("--no-kernel-timing", dest="kernel_timing", action="store_false")
     ap.add_argument("--tune", action="store_true", help="autotune the launch first (grouped workloads always do)")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
-    ap.add_argument("--serving-requests", type=int, default=400,
+    ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests of the serving stream in the se128 line (0: none)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate, 1/s")
     args = ap.parse_args(argv)

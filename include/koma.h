@@ -459,10 +459,15 @@ koma_status koma_server_create(const koma_server_config *cfg, koma_server **out)
 
 /* Submit one simulation; validates and preprocesses on the calling thread,
  * then returns its id. group_offsets / n_groups as koma_phantom_upload (NULL:
- * one group). Requests of the shared lane keep no host arrays; those of the
- * koma_simulate lane keep a copy until they are uploaded. Thread-safe.
- * Errors: KOMA_E_INVALID (as the uploads; message via
- * koma_server_last_error), KOMA_E_BUSY (server shutting down). */
+ * one group). Requests of the shared lane keep no host arrays. For those of
+ * the koma_simulate lane the calling thread copies the phantom into device
+ * memory, where the conversion kernel checks every spin and builds the FP32
+ * block (counted against the memory budget from then on); if the budget has
+ * no room for it yet, the spins are checked on the host and a host copy is
+ * kept until the lane uploads it. The sequence arrays are copied and checked
+ * on the host. Thread-safe. Errors: KOMA_E_INVALID (as the uploads; message
+ * via koma_server_last_error), KOMA_E_NOMEM, KOMA_E_CUDA, KOMA_E_BUSY (server
+ * shutting down). */
 koma_status koma_server_submit(koma_server *srv, int64_t n, const double *x, const double *y,
                                const double *z, const double *pd, const double *t1,
                                const double *t2, const double *dw, const int64_t *group_offsets,

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libkoma.so")
 SOURCES = [os.path.join(CSRC, "koma_kernels.cu"), os.path.join(CSRC, "koma_runtime.cpp"),
            os.path.join(CSRC, "koma_server.cpp")]
-HEADERS = [os.path.join(CSRC, "koma_internal.h"), os.path.join(INCLUDE, "koma.h")]
+HEADERS = [os.path.join(CSRC, "koma_internal.h"), os.path.join(CSRC, "koma_host.h"), os.path.join(INCLUDE, "koma.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

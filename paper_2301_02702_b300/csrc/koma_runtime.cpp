@@ -29,6 +29,7 @@
 
 #include "koma.h"
 #include "koma_internal.h"
+#include "koma_host.h"
 
 namespace {
 
@@ -110,6 +111,8 @@ struct koma_phantom {
     // every group has a single T1 and a single T2 (a dictionary's entries):
     // the grouped kernel evaluates relaxation once per thread
     bool uni_relax = false;
+    // p32 / p64 belong to the caller (koma::phantom_from_device): not freed here
+    bool borrowed = false;
 };
 
 struct koma_sequence {
@@ -228,6 +231,14 @@ cudaError_t h2d_sync(koma_ctx* ctx, void* dst, const void* src, size_t bytes) {
 cudaError_t memset_sync(koma_ctx* ctx, void* dst, int value, size_t bytes) {
     cudaError_t e = cudaMemsetAsync(dst, value, bytes, ctx->own_stream);
     return e == cudaSuccess ? cudaStreamSynchronize(ctx->own_stream) : e;
+}
+
+// Free ordered after the work already enqueued on `st` (the caller knows
+// that no other stream uses the block); nothing waits.
+void dev_free_on(koma_ctx* ctx, void* p, size_t bytes, cudaStream_t st) {
+    if (!p) return;
+    cudaFreeAsync(p, st);
+    ctx->used -= std::min(ctx->used, bytes);
 }
 
 inline void split(double v, float* hi, float* lo) {
@@ -590,8 +601,10 @@ extern "C" koma_status koma_phantom_free(koma_phantom* ph) {
     if (!ph) return KOMA_OK;
     koma_ctx* ctx = ph->ctx;
     DeviceGuard g(ctx->device);
-    dev_free(ctx, ph->p32, static_cast<size_t>(koma::P32_N * ph->n_pad) * sizeof(float));
-    dev_free(ctx, ph->p64, static_cast<size_t>(koma::P64_N * ph->n_pad) * sizeof(double));
+    if (!ph->borrowed) {
+        dev_free(ctx, ph->p32, static_cast<size_t>(koma::P32_N * ph->n_pad) * sizeof(float));
+        dev_free(ctx, ph->p64, static_cast<size_t>(koma::P64_N * ph->n_pad) * sizeof(double));
+    }
     if (ph->d_cta_begin) dev_free(ctx, ph->d_cta_begin, ph->table_bytes);
     if (ph->d_items) dev_free(ctx, ph->d_items, ph->items_bytes);
     dev_free(ctx, ph->pv32, static_cast<size_t>(koma::PV32_N * ph->n_pad) * sizeof(float));
@@ -2115,6 +2128,55 @@ void host_rf_maps32(std::vector<Rec32>& r32, std::vector<RfMapPulse>& pulses, ko
     info.n_rf_map_runs = fp.runs;
     info.n_rf_map_steps = fp.steps;
     info.n_rf_map_pulse_steps = fp.pulse_steps;
+}
+
+int phantom_from_device(koma_ctx* ctx, int64_t n, double* p64, float* p32, const double (&max_abs)[4],
+                        double max_pd, const int64_t* group_offsets, int64_t n_groups, bool uni_relax,
+                        koma_phantom** out) {
+    *out = nullptr;
+    if (!ctx || n < 0 || (n > 0 && (!p64 || !p32))) return KOMA_E_INVALID;
+    koma_phantom* ph = new (std::nothrow) koma_phantom();
+    if (!ph) return KOMA_E_NOMEM;
+    ph->ctx = ctx;
+    ph->n = n;
+    ph->n_pad = std::max<int64_t>(32, (n + 31) / 32 * 32);
+    ph->n_groups = group_offsets ? n_groups : 1;
+    if (group_offsets) ph->group_offsets.assign(group_offsets, group_offsets + n_groups + 1);
+    ph->uni_relax = group_offsets && uni_relax;
+    ph->p64 = p64;
+    ph->p32 = p32;
+    ph->borrowed = true;
+    for (int d = 0; d < 4; ++d) ph->max_abs[d] = max_abs[d];
+    ph->max_pd = max_pd;
+    ctx->live_objects++;
+    *out = ph;
+    return KOMA_OK;
+}
+
+void phantom_free_on(koma_phantom* ph, void* stream) {
+    if (!ph) return;
+    koma_ctx* ctx = ph->ctx;
+    DeviceGuard g(ctx->device);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!ph->borrowed) {
+        dev_free_on(ctx, ph->p32, static_cast<size_t>(P32_N * ph->n_pad) * sizeof(float), st);
+        dev_free_on(ctx, ph->p64, static_cast<size_t>(P64_N * ph->n_pad) * sizeof(double), st);
+    }
+    dev_free_on(ctx, ph->d_cta_begin, ph->table_bytes, st);
+    dev_free_on(ctx, ph->d_items, ph->items_bytes, st);
+    dev_free_on(ctx, ph->pv32, static_cast<size_t>(PV32_N * ph->n_pad) * sizeof(float), st);
+    dev_free_on(ctx, ph->pv64, static_cast<size_t>(3 * ph->n_pad) * sizeof(double), st);
+    ctx->live_objects--;
+    delete ph;
+}
+
+void sequence_free_on(koma_sequence* seq, void* stream) {
+    if (!seq) return;
+    koma_ctx* ctx = seq->ctx;
+    DeviceGuard g(ctx->device);
+    dev_free_on(ctx, seq->r32, seq->bytes, static_cast<cudaStream_t>(stream));
+    ctx->live_objects--;
+    delete seq;
 }
 
 int host_records32(int64_t n_steps, const double* dt, const double* gx, const double* gy, const double* gz,

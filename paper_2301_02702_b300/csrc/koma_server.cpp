@@ -40,6 +40,7 @@
 
 #include "koma.h"
 #include "koma_internal.h"
+#include "koma_host.h"
 
 namespace {
 
@@ -98,7 +99,14 @@ struct Req {
     // second lane (koma_simulate): the host arrays until the upload
     bool lane = false;
     int64_t n_groups = 1;
-    std::unique_ptr<double[]> ph64;   // x, y, z, pd, t1, t2, dw, each n long
+    std::unique_ptr<double[]> ph64;   // x, y, z, pd, t1, t2, dw, each n long (host path only)
+    // device path: the phantom uploaded, checked and converted at submit
+    // (blocks from the server's pool, counted in `used` until retirement)
+    double* dp64 = nullptr;
+    float* dp32 = nullptr;
+    size_t ph_dev_bytes = 0;
+    double max_pd = 0;
+    bool uni_relax = false;
     std::vector<int64_t> offsets;     // group offsets (grouped requests)
     std::vector<double> sq64;         // dt [n_steps], gx, gy, gz [n_steps + 1], b1 re, im [n_steps]
     std::vector<uint8_t> sq_adc;
@@ -139,6 +147,15 @@ struct koma_server {
     std::deque<Req*> lane_q;
     std::condition_variable cv_lane;
     int64_t lane_runs = 0;
+    // streams (with a conversion status word each) for the uploads that
+    // submit calls do on their own threads
+    struct UpSlot {
+        cudaStream_t st = nullptr;
+        koma::ConvertStatus* d_cs = nullptr;
+        koma::ConvertStatus* h_cs = nullptr;  // pinned
+    };
+    std::mutex up_mu;
+    std::vector<UpSlot*> up_free, up_all;
     size_t budget = 0, used = 0, peak = 0;
     int max_active = 64;
     double launch_work = 0;  // work units per launch (cap)
@@ -177,6 +194,105 @@ koma_status cuda_err(koma_server* S, cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? KOMA_E_NOMEM : KOMA_E_CUDA;
 }
 
+// A large request's phantom on the device, done by the submitting thread:
+// the caller's rows are copied into blocks of the server's pool on one of
+// the upload streams, and the conversion kernel checks every spin, takes the
+// extents and builds the FP32 block (what koma_phantom_upload does); the
+// lane later simulates on these blocks without a host copy or a second
+// upload. KOMA_E_INVALID (err set) for invalid spins; KOMA_E_NOMEM when the
+// budget or the pool has no room (the caller then keeps a host copy).
+koma_status upload_lane_phantom(koma_server* S, Req* r, int64_t n, const double* x, const double* y,
+                                const double* z, const double* pd, const double* t1, const double* t2,
+                                const double* dw, std::string& err) {
+    const int64_t np = r->n_pad;
+    const size_t b64 = static_cast<size_t>(koma::P64_N * np) * sizeof(double),
+                 b32 = static_cast<size_t>(koma::P32_N * np) * sizeof(float);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->budget && S->used + b64 + b32 > S->budget) return KOMA_E_NOMEM;
+        S->used += b64 + b32;
+        S->peak = std::max(S->peak, S->used);
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != S->device) cudaSetDevice(S->device);
+    koma_server::UpSlot* U = nullptr;
+    cudaError_t e = cudaSuccess;
+    {
+        std::lock_guard<std::mutex> lk(S->up_mu);
+        if (!S->up_free.empty()) {
+            U = S->up_free.back();
+            S->up_free.pop_back();
+        }
+    }
+    if (!U) {
+        U = new (std::nothrow) koma_server::UpSlot();
+        if (!U) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&U->st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&U->d_cs), sizeof(koma::ConvertStatus));
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&U->h_cs), sizeof(koma::ConvertStatus));
+        if (e == cudaSuccess) {
+            std::lock_guard<std::mutex> lk(S->up_mu);
+            S->up_all.push_back(U);
+        } else if (U) {
+            if (U->h_cs) cudaFreeHost(U->h_cs);
+            if (U->d_cs) cudaFree(U->d_cs);
+            if (U->st) cudaStreamDestroy(U->st);
+            delete U;
+            U = nullptr;
+        }
+    }
+    double* p64 = nullptr;
+    float* p32 = nullptr;
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&p64), b64, S->pool, U->st);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&p32), b32, S->pool, U->st);
+    const double* rows[koma::P64_N] = {x, y, z, dw, t1, t2, pd};  // the order of enum P64
+    for (int k = 0; k < koma::P64_N && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(p64 + k * np, rows[k], static_cast<size_t>(n) * sizeof(double), cudaMemcpyHostToDevice,
+                            U->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(U->d_cs, 0, sizeof(koma::ConvertStatus), U->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&U->d_cs->first_bad, 0xff, sizeof(unsigned long long), U->st);
+    if (e == cudaSuccess) e = static_cast<cudaError_t>(koma::launch_phantom_convert(p64, p32, n, np, U->d_cs, U->st));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(U->h_cs, U->d_cs, sizeof(koma::ConvertStatus), cudaMemcpyDeviceToHost, U->st);
+    if (U) {
+        const cudaError_t es = cudaStreamSynchronize(U->st);
+        if (e == cudaSuccess) e = es;
+    }
+    koma_status st = KOMA_OK;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        st = e == cudaErrorMemoryAllocation ? KOMA_E_NOMEM : KOMA_E_CUDA;
+        err = std::string("server_submit: phantom upload: ") + cudaGetErrorString(e);
+    } else if (U->h_cs->first_bad != ~0ull) {
+        st = static_cast<koma_status>(koma::host_check_phantom(n, x, y, z, pd, t1, t2, dw, err));
+        if (st == KOMA_OK) {  // the device found what the host check did not: report the index
+            st = KOMA_E_INVALID;
+            err = "phantom: invalid spin " + std::to_string(U->h_cs->first_bad);
+        }
+    } else {
+        for (int d = 0; d < 4; ++d) std::memcpy(&r->max_abs[d], &U->h_cs->max_bits[d], sizeof(double));
+        std::memcpy(&r->max_pd, &U->h_cs->max_bits[4], sizeof(double));
+        r->dp64 = p64;
+        r->dp32 = p32;
+        r->ph_dev_bytes = b64 + b32;
+    }
+    if (st != KOMA_OK) {
+        if (U) {
+            if (p64) cudaFreeAsync(p64, U->st);
+            if (p32) cudaFreeAsync(p32, U->st);
+        }
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->used -= std::min(S->used, b64 + b32);
+    }
+    if (U) {
+        std::lock_guard<std::mutex> lk(S->up_mu);
+        S->up_free.push_back(U);
+    }
+    if (prev >= 0 && prev != S->device) cudaSetDevice(prev);
+    return st;
+}
+
 size_t map_bytes(const Req* r) {
     return r->pulses.size() * koma::kRfMapFloats * static_cast<size_t>(r->n_pad) * sizeof(float);
 }
@@ -188,7 +304,8 @@ size_t req_bytes(const Req* r) {
         // streams, per-CTA partial rows (at most a few thousand CTAs), the
         // readout's snapshots (bounded by one row per ADC run) and the maps
         const size_t np = static_cast<size_t>(r->n_pad);
-        return np * (koma::P32_N * sizeof(float) + koma::P64_N * sizeof(double)) +
+        // (the phantom blocks of a request uploaded at submit are counted there)
+        return (r->dp64 ? 0 : np * (koma::P32_N * sizeof(float) + koma::P64_N * sizeof(double))) +
                static_cast<size_t>(r->n_rec) * 3 * sizeof(koma::Rec64) +
                static_cast<size_t>(r->n_groups) * static_cast<size_t>(r->n_adc) * 16 +
                static_cast<size_t>(4096) * static_cast<size_t>(r->n_adc) * sizeof(float2) +
@@ -266,6 +383,12 @@ koma_status admit(koma_server* S, Req* r) {
 }
 
 void release_device(koma_server* S, Req* r) {
+    if (r->dp64) cudaFreeAsync(r->dp64, S->s_red);
+    if (r->dp32) cudaFreeAsync(r->dp32, S->s_red);
+    r->dp64 = nullptr;
+    r->dp32 = nullptr;
+    S->used -= std::min(S->used, r->ph_dev_bytes);
+    r->ph_dev_bytes = 0;
     if (r->d32) cudaFreeAsync(r->d32, S->s_red);
     if (r->drec) cudaFreeAsync(r->drec, S->s_red);
     if (r->drows) cudaFreeAsync(r->drows, S->s_red);
@@ -596,9 +719,12 @@ void lane_loop(koma_server* S, int k) {
         koma_phantom* ph = nullptr;
         koma_sequence* seq = nullptr;
         const double t_up = now_s();
-        koma_status st = koma_phantom_upload(ctx, n, P, P + n, P + 2 * n, P + 3 * n, P + 4 * n, P + 5 * n,
-                                             P + 6 * n, r->n_groups > 1 ? r->offsets.data() : nullptr,
-                                             r->n_groups, &ph);
+        const int64_t* offs = r->n_groups > 1 ? r->offsets.data() : nullptr;
+        koma_status st = r->dp64 ? static_cast<koma_status>(koma::phantom_from_device(
+                                       ctx, n, r->dp64, r->dp32, r->max_abs, r->max_pd, offs, r->n_groups,
+                                       r->uni_relax, &ph))
+                                 : koma_phantom_upload(ctx, n, P, P + n, P + 2 * n, P + 3 * n, P + 4 * n,
+                                                       P + 5 * n, P + 6 * n, offs, r->n_groups, &ph);
         if (st == KOMA_OK)
             st = koma_sequence_upload(ctx, ns, Q, Q + ns, Q + 2 * ns + 1, Q + 3 * ns + 2, Q + 4 * ns + 3,
                                       Q + 5 * ns + 3, r->sq_adc.data(), &seq);
@@ -617,11 +743,12 @@ void lane_loop(koma_server* S, int k) {
         if (st == KOMA_OK && e == cudaSuccess) st = koma_sync(ctx, st_k);
         else if (st == KOMA_OK) st = KOMA_E_CUDA;
         std::string msg = st != KOMA_OK ? std::string(koma_last_error(ctx)) : std::string();
+        // every use of these was on st_k: frees ordered there, no device-wide wait
         if (dsig) cudaFreeAsync(dsig, st_k);
-        if (seq) koma_sequence_free(seq);
+        koma::sequence_free_on(seq, st_k);
+        koma::phantom_free_on(ph, st_k);
+        cudaStreamSynchronize(st_k);  // also after a failed launch: nothing may still read the blocks
         const double t_end = now_s();
-        if (ph) koma_phantom_free(ph);
-        cudaStreamSynchronize(st_k);
         lk.lock();
         r->upload_s = t_run - t_up;
         r->run_s = t_end - t_run;
@@ -720,12 +847,20 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
     if (!r) return KOMA_E_NOMEM;
     r->t_submit = now_s();
     std::string err;
-    // the second lane (grouped requests, large ones) converts on the device:
-    // only the input rules are checked here
+    // the second lane (grouped requests, large ones): the spins are checked
+    // and converted on the device below (or on the host when the phantom
+    // cannot be placed on the device yet)
     const bool lane = (group_offsets && n_groups > 1) || (S->plain_spins > 0 && n >= S->plain_spins);
-    int st = lane ? koma::host_check_phantom(n, x, y, z, pd, t1, t2, dw, err)
-                  : koma::host_phantom32(n, x, y, z, pd, t1, t2, dw, r->h32, r->n_pad, r->max_abs, err);
-    if (lane) r->n_pad = std::max<int64_t>(32, (n + 31) / 32 * 32);
+    int st = KOMA_OK;
+    if (lane) {
+        if (n < 0 || (n > 0 && (!x || !y || !z || !pd || !t1 || !t2 || !dw))) {
+            st = KOMA_E_INVALID;
+            err = "phantom: n < 0 or a NULL array";
+        }
+        r->n_pad = std::max<int64_t>(32, (n + 31) / 32 * 32);
+    } else {
+        st = koma::host_phantom32(n, x, y, z, pd, t1, t2, dw, r->h32, r->n_pad, r->max_abs, err);
+    }
     if (st == KOMA_OK && group_offsets) {
         // the upload's rules: n_groups >= 1, offsets from 0 to n, non-decreasing
         bool ok = n_groups >= 1 && group_offsets[0] == 0 && group_offsets[n_groups] == n;
@@ -759,19 +894,35 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
     r->n_groups = group_offsets ? n_groups : 1;
     r->lane = lane;
     if (r->lane) {
-        // the second lane uploads the request itself: keep the host arrays
-        const double* ph[7] = {x, y, z, pd, t1, t2, dw};
-        if (n > 0) {
-            // not value-initialised: the copy is the only write
-            r->ph64.reset(new (std::nothrow) double[static_cast<size_t>(7 * n)]);
-            if (!r->ph64) {
-                delete r;
-                return KOMA_E_NOMEM;
+        // the phantom on the device now (checked and converted there), else
+        // a host copy that the lane uploads
+        if (n > 0) st = upload_lane_phantom(S, r, n, x, y, z, pd, t1, t2, dw, err);
+        if (st == KOMA_E_NOMEM) {
+            st = koma::host_check_phantom(n, x, y, z, pd, t1, t2, dw, err);
+            const double* ph[7] = {x, y, z, pd, t1, t2, dw};
+            if (st == KOMA_OK) {
+                // not value-initialised: the copy is the only write
+                r->ph64.reset(new (std::nothrow) double[static_cast<size_t>(7 * n)]);
+                if (!r->ph64) st = KOMA_E_NOMEM;
             }
-            for (int k = 0; k < 7; ++k)
+            for (int k = 0; k < 7 && st == KOMA_OK; ++k)
                 std::memcpy(r->ph64.get() + k * n, ph[k], static_cast<size_t>(n) * sizeof(double));
         }
-        if (group_offsets) r->offsets.assign(group_offsets, group_offsets + n_groups + 1);
+        if (st != KOMA_OK) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->fatal = err;
+            delete r;
+            return static_cast<koma_status>(st);
+        }
+        if (group_offsets) {
+            r->offsets.assign(group_offsets, group_offsets + n_groups + 1);
+            // every group has one T1 and one T2 (a dictionary): relaxation once per thread
+            bool uni = true;
+            for (int64_t gi = 0; gi < n_groups && uni; ++gi)
+                for (int64_t j = group_offsets[gi] + 1; j < group_offsets[gi + 1] && uni; ++j)
+                    uni = t1[j] == t1[group_offsets[gi]] && t2[j] == t2[group_offsets[gi]];
+            r->uni_relax = uni;
+        }
         const int64_t v = n_steps + 1;
         r->sq64.resize(static_cast<size_t>(n_steps + 3 * v + 2 * n_steps));
         double* q = r->sq64.data();
@@ -790,6 +941,9 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
         r->rem_work = 0;
         std::lock_guard<std::mutex> lk(S->mu);
         if (S->stop) {
+            if (r->dp64) cudaFreeAsync(r->dp64, S->s_red);
+            if (r->dp32) cudaFreeAsync(r->dp32, S->s_red);
+            S->used -= std::min(S->used, r->ph_dev_bytes);
             delete r;
             return KOMA_E_BUSY;
         }
@@ -961,6 +1115,15 @@ extern "C" koma_status koma_server_destroy(koma_server* S) {
         if (r->ev_done) cudaEventDestroy(r->ev_done);
         delete r;
     }
+    for (koma_server::UpSlot* U : S->up_all) {
+        cudaStreamSynchronize(U->st);
+        cudaStreamDestroy(U->st);
+        cudaFree(U->d_cs);
+        cudaFreeHost(U->h_cs);
+        delete U;
+    }
+    S->up_all.clear();
+    S->up_free.clear();
     if (S->pool) cudaMemPoolDestroy(S->pool);
     if (S->s_up) cudaStreamDestroy(S->s_up);
     if (S->s_red) cudaStreamDestroy(S->s_red);

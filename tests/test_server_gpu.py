@@ -203,3 +203,61 @@ def test_submit_rejects_bad_group_offsets(server):
     with pytest.raises(koma.KomaError) as e:
         server.submit(ph, random_sequence(20, seed=2))
     assert e.value.status == koma.KOMA_E_INVALID
+
+
+def test_large_request_checked_on_the_device_at_submit():
+    """A large request's phantom goes to device memory at submit, where the
+    conversion kernel checks every spin: invalid spins are refused by submit
+    itself, with the offending spin's index, and the server keeps serving."""
+    srv = koma.Server(0, plain_spins=900)
+    try:
+        seq = random_sequence(150, seed=9)
+        for field, j, value in (("t2", 1234, -1.0), ("x", 77, np.nan), ("pd", 1999, -0.5)):
+            ph = random_spins(2000, seed=8)
+            getattr(ph, field)[j] = value
+            with pytest.raises(koma.KomaError) as e:
+                srv.submit(ph, seq)
+            assert e.value.status == koma.KOMA_E_INVALID
+            assert str(j) in str(e.value), str(e.value)
+        ph, seq = workload("epi512", "small")
+        sig, info = srv.wait(srv.submit(ph, seq))
+        assert info["lane"] == 1
+        assert rel_err(sig, oracle.simulate(ph, seq)[0]) < TOL32
+        assert srv.stats()["mem_used"] == 0  # the device phantom is released with the request
+    finally:
+        srv.close()
+
+
+def test_large_request_over_budget_keeps_a_host_copy():
+    """When the memory budget has no room for a large request's phantom at
+    submit, its spins are checked on the host and the lane uploads a host
+    copy once the request is admitted; the result is bitwise the device
+    path's. The budget is just under two phantoms: while the first request
+    (a long pulse, ~50 ms on the GPU) holds its phantom, the second cannot
+    place its own and takes the host path."""
+    from paper_2301_02702_b300.workloads import SequenceBuilder, sinc_pulse
+    ph = random_spins(600_000, seed=12, extent=0.05)
+    b = SequenceBuilder()
+    b.steps(50_000, 2e-6, [0.0, 0.0, 0.002], b1=sinc_pulse(50_000, 2e-6, 30.0))
+    b.steps(1, 1e-4)
+    b.steps(128, 8e-6, [0.01, 0.0, 0.0], adc=True)
+    b.steps(1, 1e-5)
+    seq = b.build()
+    n_pad = (ph.n + 31) // 32 * 32
+    ph_bytes = n_pad * (7 * 8 + 11 * 4)  # FP64 and FP32 phantom blocks
+    roomy = koma.Server(0, plain_spins=900)
+    try:
+        a, info_a = roomy.wait(roomy.submit(ph, seq))
+    finally:
+        roomy.close()
+    tight = koma.Server(0, plain_spins=900, mem_budget_bytes=2 * ph_bytes - 1)
+    try:
+        ids = [tight.submit(ph, seq) for _ in range(2)]
+        res = [tight.wait(i) for i in ids]
+        st = tight.stats()
+    finally:
+        tight.close()
+    assert info_a["lane"] == 1 and st["failed"] == 0 and st["mem_peak"] <= 2 * ph_bytes - 1
+    for b_sig, info in res:
+        assert info["lane"] == 1
+        assert np.array_equal(a, b_sig)
