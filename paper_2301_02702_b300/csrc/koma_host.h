@@ -3,7 +3,10 @@
 // on one stream. No kernel depends on this header.
 #pragma once
 
+#include <vector>
+
 #include "koma.h"
+#include "koma_internal.h"
 
 namespace koma {
 
@@ -19,5 +22,13 @@ int phantom_from_device(koma_ctx* ctx, int64_t n, double* p64, float* p32, const
 // device-wide wait, unlike koma_phantom_free / koma_sequence_free.
 void phantom_free_on(koma_phantom* ph, void* stream);
 void sequence_free_on(koma_sequence* seq, void* stream);
+// compact_records32 writing into `out` (null: count only); returns the
+// compacted stream's length.
+size_t compact_records32_into(const std::vector<Rec32>& r32, Rec32* out);
+// koma_sequence_upload building the FP32 record stream only (for a
+// simulation known to be FP32 on a static phantom).
+koma_status sequence_upload_fp32(koma_ctx* ctx, int64_t n_steps, const double* dt, const double* gx,
+                                 const double* gy, const double* gz, const double* b1_re, const double* b1_im,
+                                 const uint8_t* adc, koma_sequence** out);
 
 }  // namespace koma

@@ -72,6 +72,10 @@ struct koma_ctx {
     std::map<uint64_t, TuneChoice> tune_cache;  // shape key -> choice
     koma::ConvertStatus* d_conv = nullptr;  // checks and extents of the last phantom upload
     koma::ConvertStatus* h_conv = nullptr;  // pinned host copy of *d_conv
+    // pinned staging of sequence uploads (grows, kept): the record block is
+    // assembled here and copied by DMA
+    char* h_stage = nullptr;
+    size_t h_stage_bytes = 0;
 };
 
 struct koma_phantom {
@@ -119,12 +123,9 @@ struct koma_sequence {
     koma_ctx* ctx = nullptr;
     koma_sequence_info info{};
     koma::Rec32* r32 = nullptr;  // one allocation: r32, then r64, then rm
-    koma::Rec64* r64 = nullptr;
-    koma::RecM* rm = nullptr;
+    koma::Rec64* r64 = nullptr;  // null when built without the FP64 stream
+    koma::RecM* rm = nullptr;    // null when built without the motion stream
     size_t bytes = 0;
-    // over RF steps: max |B1| gammabar dt (turns), max |Gbar_d| gammabar dt
-    // (turns/m) per axis, max dt (s); bound the per-step rotation |a|
-    double rf_b1 = 0, rf_g[3] = {0, 0, 0}, rf_dt = 0;
     // matrix-form readout tables, in the same device block after the
     // records: groups, runs (n_mma_runs = rows of the E buffer) and the
     // per-sample source map of the reduction
@@ -443,6 +444,7 @@ extern "C" koma_status koma_destroy(koma_ctx* ctx) {
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->d_conv) cudaFree(ctx->d_conv);
     if (ctx->h_conv) cudaFreeHost(ctx->h_conv);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->d_status) cudaFree(ctx->d_status);
     delete ctx;
     return KOMA_OK;
@@ -676,6 +678,7 @@ struct RecordBuilder {
     std::vector<koma::Rec32> r32;
     std::vector<koma::Rec64> r64;
     std::vector<koma::RecM> rm;  // motion records (Rec32 fields + first moments)
+    bool want64 = true, wantM = true;  // build the FP64 / motion streams too
     int64_t n_adc = 0;
     int64_t n_runs = 0;
     int64_t n_mat = 0;
@@ -686,6 +689,27 @@ struct RecordBuilder {
     double run_k[3] = {0, 0, 0}, run_k1[3] = {0, 0, 0}, run_tau = 0;  // first sample
     double run_dk[3] = {0, 0, 0}, run_dk1[3] = {0, 0, 0}, run_dtau = 0;  // first spacing (count >= 2)
     double last_k[3] = {0, 0, 0}, last_k1[3] = {0, 0, 0}, last_tau = 0;
+
+    // Empty, for a new sequence; the vectors keep their capacity (a builder
+    // reused by one thread writes warm memory).
+    void reset(bool w64, bool wM) {
+        r32.clear();
+        r64.clear();
+        rm.clear();
+        want64 = w64;
+        wantM = wM;
+        n_adc = n_runs = n_mat = 0;
+        run_open = false;
+        run_k0 = 0;
+        run_count = 0;
+        run_tau = run_dtau = last_tau = 0;
+        for (int d = 0; d < 3; ++d) run_k[d] = run_k1[d] = run_dk[d] = run_dk1[d] = last_k[d] = last_k1[d] = 0;
+    }
+    void push(const koma::Rec32& a, const koma::Rec64& b, const koma::RecM& m) {
+        r32.push_back(a);
+        if (want64) r64.push_back(b);
+        if (wantM) rm.push_back(m);
+    }
 
     // Motion record carrying `a`'s fields.
     static koma::RecM extend(const koma::Rec32& a) {
@@ -731,9 +755,7 @@ struct RecordBuilder {
             split(run_count > 1 ? run_dk1[d] : 0.0, &m.a[18 + 2 * d], &m.a[19 + 2 * d]);
         }
         m.count = a.count | (k1_bits(m, 12) << koma::kTermShift);
-        r32.push_back(a);
-        r64.push_back(b);
-        rm.push_back(m);
+        push(a, b, m);
         ++n_runs;
         run_open = false;
     }
@@ -766,7 +788,7 @@ struct RecordBuilder {
                 mb = std::max(mb, std::sqrt(q.a[3] * q.a[3] + q.a[4] * q.a[4]));
                 for (int d = 0; d < 3; ++d) mg[d] = std::max(mg[d], std::fabs(q.a[d]));
                 mdt = std::max(mdt, q.a[6]);
-                mt = std::max(mt, rm[j].a[13]);
+                if (wantM) mt = std::max(mt, rm[j].a[13]);
                 ++j;
             }
             koma::Rec32& h = r32[i];
@@ -774,10 +796,12 @@ struct RecordBuilder {
             h.a[7] = mb * (1.f + 1e-6f);
             for (int d = 0; d < 3; ++d) h.a[8 + d] = mg[d];
             h.a[11] = mdt;
-            koma::RecM& hm = rm[i];
-            hm.count = h.count;
-            for (int k = 7; k < 12; ++k) hm.a[k] = h.a[k];
-            hm.a[12] = mt * (1.f + 1e-6f);
+            if (wantM) {
+                koma::RecM& hm = rm[i];
+                hm.count = h.count;
+                for (int k = 7; k < 12; ++k) hm.a[k] = h.a[k];
+                hm.a[12] = mt * (1.f + 1e-6f);
+            }
             i = j;
         }
     }
@@ -886,9 +910,7 @@ koma_status build_records(int64_t n_steps, const double* dt, const double* gx, c
                 koma::RecM m = RecordBuilder::extend(a);
                 for (int d = 0; d < 3; ++d) split(K1[d], &m.a[8 + 2 * d], &m.a[9 + 2 * d]);
                 m.count = a.count | (RecordBuilder::k1_bits(m, 8) << koma::kTermShift);
-                rb.r32.push_back(a);
-                rb.r64.push_back(b);
-                rb.rm.push_back(m);
+                rb.push(a, b, m);
                 ++rb.n_mat;
             }
             koma::Rec32 a{};
@@ -914,9 +936,7 @@ koma_status build_records(int64_t n_steps, const double* dt, const double* gx, c
             b.a[6] = t_mid;
             koma::RecM m = RecordBuilder::extend(a);
             m.a[13] = static_cast<float>(t_mid);
-            rb.r32.push_back(a);
-            rb.r64.push_back(b);
-            rb.rm.push_back(m);
+            rb.push(a, b, m);
             for (int d = 0; d < 3; ++d) K[d] = K1[d] = 0.0;
             tau = 0.0;
         } else {
@@ -1064,14 +1084,19 @@ void plan_rf_maps(std::vector<koma::Rec32>& r32, RfMapPlan& P) {
     auto same = [&](const Run& a, const Run& b) {
         return a.len == b.len && std::memcmp(&r32[a.begin], &r32[b.begin], a.len * sizeof(koma::Rec32)) == 0;
     };
-    // FNV-1a of the run's bytes buckets the candidates; equality is checked
-    // byte for byte
+    // a multiplicative hash of the run's 8-byte words buckets the candidates;
+    // equality is checked byte for byte
     std::map<std::pair<uint64_t, size_t>, std::vector<std::vector<size_t>>> buckets;
     for (size_t q = 0; q < runs.size(); ++q) {
         if (runs[q].len < static_cast<size_t>(koma::kRfMapMinLen)) continue;
         uint64_t h = 1469598103934665603ull;
         const unsigned char* b = reinterpret_cast<const unsigned char*>(&r32[runs[q].begin]);
-        for (size_t k = 0; k < runs[q].len * sizeof(koma::Rec32); ++k) h = (h ^ b[k]) * 1099511628211ull;
+        for (size_t k = 0; k < runs[q].len * sizeof(koma::Rec32); k += 8) {  // 64-byte records: whole words
+            uint64_t w;
+            std::memcpy(&w, b + k, 8);
+            h = (h ^ w) * 1099511628211ull;
+            h ^= h >> 29;
+        }
         auto& classes = buckets[{h, runs[q].len}];
         bool placed = false;
         for (auto& c : classes) {
@@ -1142,14 +1167,24 @@ extern "C" koma_status koma_sequence_plan(int64_t n_steps, const double* dt, con
     return KOMA_OK;
 }
 
-extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, const double* dt, const double* gx,
-                                            const double* gy, const double* gz, const double* b1_re,
-                                            const double* b1_im, const uint8_t* adc, koma_sequence** out) {
-    NvtxRange nvtx_("koma_sequence_upload");
+namespace {
+
+// Sequence upload. The records are built by a builder the calling thread
+// keeps (its vectors stay warm from one upload to the next), the device
+// block [Rec32 | Rec64 | RecM | MmaGroup | MmaRun | sample map | RfMapPulse |
+// compacted Rec32] (each part 16-byte aligned) is assembled in the
+// context's pinned staging buffer and copied by DMA. need64 / needM: build
+// and upload the FP64 and the motion record streams (koma_sequence_upload
+// builds every stream; callers that know the precision, and that the
+// phantom is static, build the FP32 stream only).
+koma_status sequence_upload_impl(koma_ctx* ctx, int64_t n_steps, const double* dt, const double* gx,
+                                 const double* gy, const double* gz, const double* b1_re, const double* b1_im,
+                                 const uint8_t* adc, bool need64, bool needM, koma_sequence** out) {
     if (!ctx) return KOMA_E_INVALID;
     if (!out) return fail(ctx, KOMA_E_INVALID, "sequence_upload: out is NULL");
     *out = nullptr;
-    RecordBuilder rb;
+    static thread_local RecordBuilder rb;
+    rb.reset(need64, needM);
     koma_sequence_info info{};
     {
         std::string err;
@@ -1160,12 +1195,6 @@ extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, cons
     if (!seq) return fail(ctx, KOMA_E_NOMEM, "sequence_upload: host allocation");
     seq->ctx = ctx;
     seq->info = info;
-    for (const koma::Rec64& q : rb.r64) {
-        if (q.type != koma::REC_RF) continue;
-        seq->rf_b1 = std::max(seq->rf_b1, std::hypot(q.a[3], q.a[4]));
-        for (int d = 0; d < 3; ++d) seq->rf_g[d] = std::max(seq->rf_g[d], std::fabs(q.a[d]));
-        seq->rf_dt = std::max(seq->rf_dt, q.a[5]);
-    }
     MmaPlan mp;
     plan_mma(rb.r32, info.n_adc, mp);
     seq->info.n_mma_groups = static_cast<int64_t>(mp.groups.size());
@@ -1177,46 +1206,63 @@ extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, cons
     seq->info.n_rf_map_runs = fp.runs;
     seq->info.n_rf_map_steps = fp.steps;
     seq->info.n_rf_map_pulse_steps = fp.pulse_steps;
-    std::vector<koma::Rec32> rc;
-    if (!fp.pulses.empty()) koma::compact_records32(rb.r32, rc);
+    // the compacted stream's length (the stream itself is written into the block)
+    const size_t n_rc = fp.pulses.empty() ? 0 : koma::compact_records32_into(rb.r32, nullptr);
     DeviceGuard g(ctx->device);
     auto up16 = [](size_t b) { return (b + 15) / 16 * 16; };
     const size_t b32 = rb.r32.size() * sizeof(koma::Rec32), b64 = rb.r64.size() * sizeof(koma::Rec64),
                  bm = rb.rm.size() * sizeof(koma::RecM), bg = mp.groups.size() * sizeof(koma::MmaGroup),
                  br = mp.runs.size() * sizeof(koma::MmaRun), bf = up16(mp.from.size()),
-                 bp = fp.pulses.size() * sizeof(koma::RfMapPulse), bc = rc.size() * sizeof(koma::Rec32);
+                 bp = fp.pulses.size() * sizeof(koma::RfMapPulse), bc = n_rc * sizeof(koma::Rec32);
     const size_t total = b32 + b64 + bm + bg + br + bf + bp + bc;
-    // one device block [Rec32 | Rec64 | RecM | MmaGroup | MmaRun | sample map |
-    // RfMapPulse | compacted Rec32] (each part 16-byte aligned) filled by one copy
     koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r32), total, "sequence_upload");
+    if (st == KOMA_OK && total > ctx->h_stage_bytes) {
+        if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+        ctx->h_stage = nullptr;
+        ctx->h_stage_bytes = 0;
+        const size_t want = (total + total / 4 + (size_t{1} << 20) - 1) / (size_t{1} << 20) * (size_t{1} << 20);
+        cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&ctx->h_stage), want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->h_stage = nullptr;
+            st = cuda_fail(ctx, e, "sequence_upload: staging buffer");
+        } else {
+            ctx->h_stage_bytes = want;
+        }
+    }
     if (st == KOMA_OK && b32) {
         char* base = reinterpret_cast<char*>(seq->r32);
-        seq->r64 = reinterpret_cast<koma::Rec64*>(base + b32);
-        seq->rm = reinterpret_cast<koma::RecM*>(base + b32 + b64);
+        char* h = ctx->h_stage;
+        if (b64) seq->r64 = reinterpret_cast<koma::Rec64*>(base + b32);
+        if (bm) seq->rm = reinterpret_cast<koma::RecM*>(base + b32 + b64);
+        size_t off = b32 + b64 + bm;
         if (!mp.groups.empty()) {
-            seq->d_mma_groups = reinterpret_cast<koma::MmaGroup*>(base + b32 + b64 + bm);
-            seq->d_mma_runs = reinterpret_cast<koma::MmaRun*>(base + b32 + b64 + bm + bg);
-            seq->d_from_mma = reinterpret_cast<uint8_t*>(base + b32 + b64 + bm + bg + br);
+            seq->d_mma_groups = reinterpret_cast<koma::MmaGroup*>(base + off);
+            seq->d_mma_runs = reinterpret_cast<koma::MmaRun*>(base + off + bg);
+            seq->d_from_mma = reinterpret_cast<uint8_t*>(base + off + bg + br);
             seq->n_mma_groups = static_cast<int32_t>(mp.groups.size());
             seq->n_mma_runs = static_cast<int64_t>(mp.runs.size());
             seq->n_mma_snaps = mp.n_snaps;
         }
-        if (bp) {
-            seq->d_rf_pulses = reinterpret_cast<koma::RfMapPulse*>(base + b32 + b64 + bm + bg + br + bf);
-            seq->n_rf_maps = static_cast<int32_t>(fp.pulses.size());
-            seq->r32c = reinterpret_cast<koma::Rec32*>(base + b32 + b64 + bm + bg + br + bf + bp);
-            seq->n_rec_c = static_cast<int64_t>(rc.size());
+        std::memcpy(h, rb.r32.data(), b32);
+        if (b64) std::memcpy(h + b32, rb.r64.data(), b64);
+        if (bm) std::memcpy(h + b32 + b64, rb.rm.data(), bm);
+        if (bg) std::memcpy(h + off, mp.groups.data(), bg);
+        if (br) std::memcpy(h + off + bg, mp.runs.data(), br);
+        if (bf) {
+            std::memcpy(h + off + bg + br, mp.from.data(), mp.from.size());
+            std::memset(h + off + bg + br + mp.from.size(), 0, bf - mp.from.size());
         }
-        std::vector<char> host(total, 0);
-        std::memcpy(host.data(), rb.r32.data(), b32);
-        std::memcpy(host.data() + b32, rb.r64.data(), b64);
-        std::memcpy(host.data() + b32 + b64, rb.rm.data(), bm);
-        if (bg) std::memcpy(host.data() + b32 + b64 + bm, mp.groups.data(), bg);
-        if (br) std::memcpy(host.data() + b32 + b64 + bm + bg, mp.runs.data(), br);
-        if (!mp.from.empty()) std::memcpy(host.data() + b32 + b64 + bm + bg + br, mp.from.data(), mp.from.size());
-        if (bp) std::memcpy(host.data() + b32 + b64 + bm + bg + br + bf, fp.pulses.data(), bp);
-        if (bc) std::memcpy(host.data() + b32 + b64 + bm + bg + br + bf + bp, rc.data(), bc);
-        cudaError_t e = h2d_sync(ctx, seq->r32, host.data(), host.size());
+        off += bg + br + bf;
+        if (bp) {
+            seq->d_rf_pulses = reinterpret_cast<koma::RfMapPulse*>(base + off);
+            seq->n_rf_maps = static_cast<int32_t>(fp.pulses.size());
+            seq->r32c = reinterpret_cast<koma::Rec32*>(base + off + bp);
+            seq->n_rec_c = static_cast<int64_t>(n_rc);
+            std::memcpy(h + off, fp.pulses.data(), bp);
+            koma::compact_records32_into(rb.r32, reinterpret_cast<koma::Rec32*>(h + off + bp));
+        }
+        cudaError_t e = h2d_sync(ctx, seq->r32, h, total);
         if (e != cudaSuccess) st = cuda_fail(ctx, e, "sequence_upload: copy");
     }
     if (st != KOMA_OK) {
@@ -1228,6 +1274,15 @@ extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, cons
     ctx->live_objects++;
     *out = seq;
     return KOMA_OK;
+}
+
+}  // namespace
+
+extern "C" koma_status koma_sequence_upload(koma_ctx* ctx, int64_t n_steps, const double* dt, const double* gx,
+                                            const double* gy, const double* gz, const double* b1_re,
+                                            const double* b1_im, const uint8_t* adc, koma_sequence** out) {
+    NvtxRange nvtx_("koma_sequence_upload");
+    return sequence_upload_impl(ctx, n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, true, true, out);
 }
 
 extern "C" int64_t koma_sequence_n_adc(const koma_sequence* seq) { return seq ? seq->info.n_adc : -1; }
@@ -1528,6 +1583,9 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     A.p64 = ph->p64;
     A.n_pad = ph->n_pad;
     A.n = ph->n;
+    if ((fp64 && !seq->r64) || (moving && !fp64 && !seq->rm))
+        return fail(ctx, KOMA_E_INVALID, "simulate: the sequence was uploaded without its %s records",
+                    fp64 ? "FP64" : "motion");
     A.rec = fp64 ? static_cast<const void*>(seq->r64)
                  : (moving ? static_cast<const void*>(seq->rm) : static_cast<const void*>(seq->r32));
     A.n_rec = seq->info.n_records;
@@ -1985,7 +2043,10 @@ extern "C" koma_status koma_simulate_host(koma_ctx* ctx, int64_t n, const double
     // the phantom's copies and conversion run on the device while the host
     // preprocesses and uploads the sequence
     koma_status st = phantom_upload_start(ctx, n, x, y, z, pd, t1, t2, dw, group_offsets, n_groups, &ph);
-    if (st == KOMA_OK) st = koma_sequence_upload(ctx, n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, &seq);
+    // the phantom is static here: no motion records; FP64 records only for the FP64 path
+    if (st == KOMA_OK)
+        st = sequence_upload_impl(ctx, n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, precision == KOMA_FP64, false,
+                                  &seq);
     if (ph) {
         const koma_status sp = phantom_upload_finish(ctx, &ph, x, y, z, pd, t1, t2, dw);
         if (st == KOMA_OK) st = sp;
@@ -2003,9 +2064,10 @@ extern "C" koma_status koma_simulate_host(koma_ctx* ctx, int64_t n, const double
         if (e != cudaSuccess) st = cuda_fail(ctx, e, "simulate_host: copy back");
     }
     if (st == KOMA_OK) st = koma_sync(ctx, ctx->own_stream);
-    if (d_sig) dev_free(ctx, d_sig, out_bytes);
-    koma_sequence_free(seq);
-    koma_phantom_free(ph);
+    // every use of these blocks was on own_stream: frees ordered there
+    dev_free_on(ctx, d_sig, out_bytes, ctx->own_stream);
+    koma::sequence_free_on(seq, ctx->own_stream);
+    koma::phantom_free_on(ph, ctx->own_stream);
     return st;
 }
 
@@ -2051,22 +2113,28 @@ int host_phantom32(int64_t n, const double* x, const double* y, const double* z,
     return KOMA_OK;
 }
 
-void compact_records32(const std::vector<Rec32>& r32, std::vector<Rec32>& out) {
-    out.clear();
-    for (size_t i = 0; i < r32.size();) {
+size_t compact_records32_into(const std::vector<Rec32>& r32, Rec32* out) {
+    size_t n = 0;
+    for (size_t i = 0; i < r32.size(); ++n) {
         const Rec32& q = r32[i];
         if (q.type == REC_RF && q.count > 0 && q.k0 > 0) {
             Rec32 m{};
             m.type = REC_MAP;
             m.count = q.count;
             m.k0 = q.k0 - 1;
-            out.push_back(m);
+            if (out) out[n] = m;
             i += static_cast<size_t>(q.count);
         } else {
-            out.push_back(q);
+            if (out) out[n] = q;
             ++i;
         }
     }
+    return n;
+}
+
+void compact_records32(const std::vector<Rec32>& r32, std::vector<Rec32>& out) {
+    out.resize(compact_records32_into(r32, nullptr));
+    compact_records32_into(r32, out.data());
 }
 
 int host_check_phantom(int64_t n, const double* x, const double* y, const double* z, const double* pd,
@@ -2130,6 +2198,13 @@ void host_rf_maps32(std::vector<Rec32>& r32, std::vector<RfMapPulse>& pulses, ko
     info.n_rf_map_pulse_steps = fp.pulse_steps;
 }
 
+koma_status sequence_upload_fp32(koma_ctx* ctx, int64_t n_steps, const double* dt, const double* gx,
+                                 const double* gy, const double* gz, const double* b1_re, const double* b1_im,
+                                 const uint8_t* adc, koma_sequence** out) {
+    NvtxRange nvtx_("sequence_upload_fp32");
+    return sequence_upload_impl(ctx, n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, false, false, out);
+}
+
 int phantom_from_device(koma_ctx* ctx, int64_t n, double* p64, float* p32, const double (&max_abs)[4],
                         double max_pd, const int64_t* group_offsets, int64_t n_groups, bool uni_relax,
                         koma_phantom** out) {
@@ -2183,6 +2258,7 @@ int host_records32(int64_t n_steps, const double* dt, const double* gx, const do
                    const double* b1_re, const double* b1_im, const uint8_t* adc, std::vector<Rec32>& r32,
                    koma_sequence_info& info, std::string& err) {
     RecordBuilder rb;
+    rb.reset(false, false);  // the FP32 stream only
     koma_status st = build_records(n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, rb, info, err);
     if (st != KOMA_OK) return st;
     r32.swap(rb.r32);

@@ -726,8 +726,8 @@ void lane_loop(koma_server* S, int k) {
                                  : koma_phantom_upload(ctx, n, P, P + n, P + 2 * n, P + 3 * n, P + 4 * n,
                                                        P + 5 * n, P + 6 * n, offs, r->n_groups, &ph);
         if (st == KOMA_OK)
-            st = koma_sequence_upload(ctx, ns, Q, Q + ns, Q + 2 * ns + 1, Q + 3 * ns + 2, Q + 4 * ns + 3,
-                                      Q + 5 * ns + 3, r->sq_adc.data(), &seq);
+            st = koma::sequence_upload_fp32(ctx, ns, Q, Q + ns, Q + 2 * ns + 1, Q + 3 * ns + 2, Q + 4 * ns + 3,
+                                            Q + 5 * ns + 3, r->sq_adc.data(), &seq);
         const double t_run = now_s();
         const size_t out_bytes = static_cast<size_t>(r->n_groups * r->n_adc) * 2 * sizeof(double);
         double* dsig = nullptr;
