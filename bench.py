@@ -476,6 +476,7 @@ def serve_measure(local: int, n_req: int, rate: float, plain_host: bool = False,
         "lanes": {"requests": [sum(1 for f in infos if f["lane"] == k) for k in (0, 1)],
                   "spin_steps": [sum(r[2] for r, f in zip(reqs, infos) if f["lane"] == k) for k in (0, 1)],
                   "prep_s_total": sum(f["prep_s"] for f in infos),
+                  "prep_s_by_lane": [sum(f["prep_s"] for f in infos if f["lane"] == k) for k in (0, 1)],
                   "upload_s_total": sum(f["upload_s"] for f in infos),
                   "run_s_total": sum(f["run_s"] for f in infos),
                   "how": "open-loop stream: requests and spin-steps per lane (0 shared launches, 1 koma_simulate "

@@ -293,15 +293,15 @@ struct Spins {
 
     __device__ __forceinline__ int64_t index(int s) const { return base + static_cast<int64_t>(s) * stride; }
 
-    // lo half of a coordinate of slot s (spin j; v: j < end)
+    // lo half of a coordinate of slot s: in registers, or in the shared-memory
+    // copy every kernel using this path makes at start (slo; zero for slots
+    // past the end)
     template <int N>
-    __device__ __forceinline__ float lo(const float (&regs)[N], int row, int s, const float* __restrict__ P,
-                                        int64_t np, int64_t j, bool v) const {
+    __device__ __forceinline__ float lo(const float (&regs)[N], int row, int s) const {
         if constexpr (kLoRegs) {
             return regs[s];
         } else {
-            if (slo) return slo[((row - P32_XL) >> 1) * (S * stride) + sidx + s * stride];
-            return v ? P[row * np + j] : 0.f;
+            return slo[((row - P32_XL) >> 1) * (S * stride) + sidx + s * stride];
         }
     }
 
@@ -633,29 +633,35 @@ struct Spins {
             e2u = exp2f(-th * r2[0]);
             if (prec) e1u = exp2f(-th * r1[0]);
         }
+        if (ux || uy || uz || uf) {
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            er[s] = 0.f;
-            ei[s] = 0.f;
-            const int64_t j = index(s);
-            const bool v = j < end;
-            float F = 0.f;
-            if (ux) F += frac_product(xh[s], lo(xl, P32_XL, s, P, np, j, v), kxh, kxl);
-            if (uy) F += frac_product(yh[s], lo(yl, P32_YL, s, P, np, j, v), kyh, kyl);
-            if (uz) F += frac_product(zh[s], lo(zl, P32_ZL, s, P, np, j, v), kzh, kzl);
-            if (uf) F += frac_product(fh[s], lo(fl, P32_FL, s, P, np, j, v), th, tl);
-            // one-shot phase: reduce to [-1/2, 1/2] turn and use the hardware
-            // sine (absolute error ~4e-7, not accumulated: every run and every
-            // materialisation starts from an exact evaluation)
-            float sn = 0.f, cs = 1.f;
-            if (ux || uy || uz || uf) {
+            for (int s = 0; s < S; ++s) {
+                float F = 0.f;
+                if (ux) F += frac_product(xh[s], lo(xl, P32_XL, s), kxh, kxl);
+                if (uy) F += frac_product(yh[s], lo(yl, P32_YL, s), kyh, kyl);
+                if (uz) F += frac_product(zh[s], lo(zl, P32_ZL, s), kzh, kzl);
+                if (uf) F += frac_product(fh[s], lo(fl, P32_FL, s), th, tl);
+                // one-shot phase: reduce to [-1/2, 1/2] turn and use the
+                // hardware sine (absolute error ~4e-7, not accumulated: every
+                // run and every materialisation starts from an exact evaluation)
                 const float r = F - rintf(F);
+                float sn, cs;
                 __sincosf(-6.28318530717958647692f * r, &sn, &cs);
+                const float e2 = uni ? e2u : exp2f(-th * r2[s]);
+                er[s] = e2 * fmaf(mx[s], cs, -my[s] * sn);
+                ei[s] = e2 * fmaf(mx[s], sn, my[s] * cs);
             }
-            const float e2 = uni ? e2u : exp2f(-th * r2[s]);
-            er[s] = e2 * fmaf(mx[s], cs, -my[s] * sn);
-            ei[s] = e2 * fmaf(mx[s], sn, my[s] * cs);
-            if (prec) {
+        } else {  // no phase since t_ref (a sample or a pause with no moment and no off-resonance)
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const float e2 = uni ? e2u : exp2f(-th * r2[s]);
+                er[s] = e2 * mx[s];
+                ei[s] = e2 * my[s];
+            }
+        }
+        if (prec) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
                 const float e1 = uni ? e1u : exp2f(-th * r1[s]);
                 mx[s] = er[s];
                 my[s] = ei[s];
