@@ -634,17 +634,32 @@ struct Spins {
             if (prec) e1u = exp2f(-th * r1[0]);
         }
         if (ux || uy || uz || uf) {
+            // the phase's terms, each a uniform branch around all slots
+            float F[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) F[s] = 0.f;
+            if (ux) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) F[s] += frac_product(xh[s], lo(xl, P32_XL, s), kxh, kxl);
+            }
+            if (uy) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) F[s] += frac_product(yh[s], lo(yl, P32_YL, s), kyh, kyl);
+            }
+            if (uz) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) F[s] += frac_product(zh[s], lo(zl, P32_ZL, s), kzh, kzl);
+            }
+            if (uf) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) F[s] += frac_product(fh[s], lo(fl, P32_FL, s), th, tl);
+            }
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                float F = 0.f;
-                if (ux) F += frac_product(xh[s], lo(xl, P32_XL, s), kxh, kxl);
-                if (uy) F += frac_product(yh[s], lo(yl, P32_YL, s), kyh, kyl);
-                if (uz) F += frac_product(zh[s], lo(zl, P32_ZL, s), kzh, kzl);
-                if (uf) F += frac_product(fh[s], lo(fl, P32_FL, s), th, tl);
                 // one-shot phase: reduce to [-1/2, 1/2] turn and use the
                 // hardware sine (absolute error ~4e-7, not accumulated: every
                 // run and every materialisation starts from an exact evaluation)
-                const float r = F - rintf(F);
+                const float r = F[s] - rintf(F[s]);
                 float sn, cs;
                 __sincosf(-6.28318530717958647692f * r, &sn, &cs);
                 const float e2 = uni ? e2u : exp2f(-th * r2[s]);
@@ -1557,29 +1572,44 @@ struct MSpins {
                                           float (&ei)[S]) {
         const int terms = (R.count >> kTermShift) & used;
         const float th = R.a[6], tl = R.a[7];
+        if (terms) {
+            // the phase's terms, each a uniform branch around all slots
+            float F[S];
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            er[s] = 0.f;
-            ei[s] = 0.f;
-            const int64_t j = index(s);
-            const bool v = j < end;
-            float F = 0.f;
-            if (terms & 1) F += frac_product(xh[s], lo(0, s), R.a[0], R.a[1]);
-            if (terms & 2) F += frac_product(yh[s], lo(1, s), R.a[2], R.a[3]);
-            if (terms & 4) F += frac_product(zh[s], lo(2, s), R.a[4], R.a[5]);
-            if (terms & 8) F += frac_product(fh[s], lo(3, s), th, tl);
-            if (terms & 16) F += frac_product(vxh[s], lo(4, s), R.a[koff], R.a[koff + 1]);
-            if (terms & 32) F += frac_product(vyh[s], lo(5, s), R.a[koff + 2], R.a[koff + 3]);
-            if (terms & 64) F += frac_product(vzh[s], lo(6, s), R.a[koff + 4], R.a[koff + 5]);
-            float sn = 0.f, cs = 1.f;
-            if (terms) {
-                const float r = F - rintf(F);
+            for (int s = 0; s < S; ++s) F[s] = 0.f;
+            auto term = [&](int bit, const float (&ch)[S], int q, float kh, float kl) {
+                if (terms & bit) {
+#pragma unroll
+                    for (int s = 0; s < S; ++s) F[s] += frac_product(ch[s], lo(q, s), kh, kl);
+                }
+            };
+            term(1, xh, 0, R.a[0], R.a[1]);
+            term(2, yh, 1, R.a[2], R.a[3]);
+            term(4, zh, 2, R.a[4], R.a[5]);
+            term(8, fh, 3, th, tl);
+            term(16, vxh, 4, R.a[koff], R.a[koff + 1]);
+            term(32, vyh, 5, R.a[koff + 2], R.a[koff + 3]);
+            term(64, vzh, 6, R.a[koff + 4], R.a[koff + 5]);
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const float r = F[s] - rintf(F[s]);
+                float sn, cs;
                 __sincosf(-6.28318530717958647692f * r, &sn, &cs);
+                const float e2 = exp2f(-th * r2[s]);
+                er[s] = e2 * fmaf(mx[s], cs, -my[s] * sn);
+                ei[s] = e2 * fmaf(mx[s], sn, my[s] * cs);
             }
-            const float e2 = exp2f(-th * r2[s]);
-            er[s] = e2 * fmaf(mx[s], cs, -my[s] * sn);
-            ei[s] = e2 * fmaf(mx[s], sn, my[s] * cs);
-            if (prec) {
+        } else {
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const float e2 = exp2f(-th * r2[s]);
+                er[s] = e2 * mx[s];
+                ei[s] = e2 * my[s];
+            }
+        }
+        if (prec) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
                 const float e1 = exp2f(-th * r1[s]);
                 mx[s] = er[s];
                 my[s] = ei[s];
