@@ -111,6 +111,9 @@ struct Req {
     std::vector<double> sq64;         // dt [n_steps], gx, gy, gz [n_steps + 1], b1 re, im [n_steps]
     std::vector<uint8_t> sq_adc;
 
+    // uploaded by the submitting thread (its device memory already counted)
+    bool uploaded = false;
+
     double remaining_work() const { return rem_work; }
 };
 
@@ -194,6 +197,41 @@ koma_status cuda_err(koma_server* S, cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? KOMA_E_NOMEM : KOMA_E_CUDA;
 }
 
+// An upload stream (with its conversion status word) for a submitting
+// thread: a free one, else a new one; null if none can be made.
+koma_server::UpSlot* up_acquire(koma_server* S) {
+    {
+        std::lock_guard<std::mutex> lk(S->up_mu);
+        if (!S->up_free.empty()) {
+            koma_server::UpSlot* U = S->up_free.back();
+            S->up_free.pop_back();
+            return U;
+        }
+    }
+    koma_server::UpSlot* U = new (std::nothrow) koma_server::UpSlot();
+    if (!U) return nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&U->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&U->d_cs), sizeof(koma::ConvertStatus));
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&U->h_cs), sizeof(koma::ConvertStatus));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (U->h_cs) cudaFreeHost(U->h_cs);
+        if (U->d_cs) cudaFree(U->d_cs);
+        if (U->st) cudaStreamDestroy(U->st);
+        delete U;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(S->up_mu);
+    S->up_all.push_back(U);
+    return U;
+}
+
+void up_release(koma_server* S, koma_server::UpSlot* U) {
+    if (!U) return;
+    std::lock_guard<std::mutex> lk(S->up_mu);
+    S->up_free.push_back(U);
+}
+
 // A large request's phantom on the device, done by the submitting thread:
 // the caller's rows are copied into blocks of the server's pool on one of
 // the upload streams, and the conversion kernel checks every spin, takes the
@@ -216,32 +254,8 @@ koma_status upload_lane_phantom(koma_server* S, Req* r, int64_t n, const double*
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != S->device) cudaSetDevice(S->device);
-    koma_server::UpSlot* U = nullptr;
-    cudaError_t e = cudaSuccess;
-    {
-        std::lock_guard<std::mutex> lk(S->up_mu);
-        if (!S->up_free.empty()) {
-            U = S->up_free.back();
-            S->up_free.pop_back();
-        }
-    }
-    if (!U) {
-        U = new (std::nothrow) koma_server::UpSlot();
-        if (!U) e = cudaErrorMemoryAllocation;
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&U->st, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&U->d_cs), sizeof(koma::ConvertStatus));
-        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&U->h_cs), sizeof(koma::ConvertStatus));
-        if (e == cudaSuccess) {
-            std::lock_guard<std::mutex> lk(S->up_mu);
-            S->up_all.push_back(U);
-        } else if (U) {
-            if (U->h_cs) cudaFreeHost(U->h_cs);
-            if (U->d_cs) cudaFree(U->d_cs);
-            if (U->st) cudaStreamDestroy(U->st);
-            delete U;
-            U = nullptr;
-        }
-    }
+    koma_server::UpSlot* U = up_acquire(S);
+    cudaError_t e = U ? cudaSuccess : cudaErrorMemoryAllocation;
     double* p64 = nullptr;
     float* p32 = nullptr;
     if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&p64), b64, S->pool, U->st);
@@ -285,10 +299,7 @@ koma_status upload_lane_phantom(koma_server* S, Req* r, int64_t n, const double*
         std::lock_guard<std::mutex> lk(S->mu);
         S->used -= std::min(S->used, b64 + b32);
     }
-    if (U) {
-        std::lock_guard<std::mutex> lk(S->up_mu);
-        S->up_free.push_back(U);
-    }
+    up_release(S, U);
     if (prev >= 0 && prev != S->device) cudaSetDevice(prev);
     return st;
 }
@@ -325,40 +336,43 @@ void fail_req(Req* r, koma_status st, const std::string& m) {
     r->msg = m;
 }
 
-// Worker side: allocate and upload an admitted request (stream s_up).
-koma_status admit(koma_server* S, Req* r) {
+// Allocate and upload a request of the shared lane on stream `st` (the
+// submitting thread's upload stream, or the worker's s_up): device blocks
+// from the server's pool, the copies, the maps of its repeated pulses; ev_up
+// marks the end. Nothing here waits for the copies.
+koma_status admit(koma_server* S, Req* r, cudaStream_t st) {
     NvtxRange nvtx_("server admit");
     const size_t b32 = r->h32.size() * sizeof(float), brec = r->recs.size() * sizeof(koma::Rec32);
     const size_t brows = static_cast<size_t>(r->n_batches) * kWarps * r->n_adc * sizeof(float2);
     const size_t bsig = static_cast<size_t>(r->n_adc) * 2 * sizeof(double);
-    cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->d32), b32, S->pool, S->s_up);
-    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->drec), brec, S->pool, S->s_up);
+    cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->d32), b32, S->pool, st);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->drec), brec, S->pool, st);
     if (e == cudaSuccess && brows)
-        e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->drows), brows, S->pool, S->s_up);
-    if (e == cudaSuccess && bsig) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dsig), bsig, S->pool, S->s_up);
+        e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->drows), brows, S->pool, st);
+    if (e == cudaSuccess && bsig) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dsig), bsig, S->pool, st);
     if (e == cudaSuccess && bsig) e = cudaMallocHost(reinterpret_cast<void**>(&r->hsig), bsig);
     if (e == cudaSuccess && r->n_chunks > 1)
         e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dstate), static_cast<size_t>(3 * r->n_pad) * sizeof(float),
-                                    S->pool, S->s_up);
+                                    S->pool, st);
     if (e == cudaSuccess && !r->pulses.empty() && r->n > 0) {
-        e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dmaps), map_bytes(r), S->pool, S->s_up);
+        e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dmaps), map_bytes(r), S->pool, st);
         if (e == cudaSuccess)
             e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dpulses),
-                                        r->pulses.size() * sizeof(koma::RfMapPulse), S->pool, S->s_up);
+                                        r->pulses.size() * sizeof(koma::RfMapPulse), S->pool, st);
         if (e == cudaSuccess)
             e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->drec_full),
-                                        r->recs_full.size() * sizeof(koma::Rec32), S->pool, S->s_up);
+                                        r->recs_full.size() * sizeof(koma::Rec32), S->pool, st);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(r->d32, r->h32.data(), b32, cudaMemcpyHostToDevice, S->s_up);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r->d32, r->h32.data(), b32, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && brec)
-        e = cudaMemcpyAsync(r->drec, r->recs.data(), brec, cudaMemcpyHostToDevice, S->s_up);
+        e = cudaMemcpyAsync(r->drec, r->recs.data(), brec, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && r->dmaps) {
         // the maps of the request's repeated pulses, before its first launch
         e = cudaMemcpyAsync(r->dpulses, r->pulses.data(), r->pulses.size() * sizeof(koma::RfMapPulse),
-                            cudaMemcpyHostToDevice, S->s_up);
+                            cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(r->drec_full, r->recs_full.data(), r->recs_full.size() * sizeof(koma::Rec32),
-                                cudaMemcpyHostToDevice, S->s_up);
+                                cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) {
             koma::RfMapArgs F;
             F.p32 = r->d32;
@@ -369,17 +383,28 @@ koma_status admit(koma_server* S, Req* r) {
             F.n_pulses = static_cast<int>(r->pulses.size());
             F.maps = r->dmaps;
             for (int d = 0; d < 4; ++d) F.ext[d] = r->ext[d];
-            e = static_cast<cudaError_t>(koma::launch_rf_maps(F, S->s_up));
+            e = static_cast<cudaError_t>(koma::launch_rf_maps(F, st));
         }
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_up, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(r->ev_up, S->s_up);
+    if (e == cudaSuccess) e = cudaEventRecord(r->ev_up, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? KOMA_E_NOMEM : KOMA_E_CUDA;
     r->dev_bytes = req_bytes(r);
     r->t_admit = now_s();
     r->state = ADMITTED;
     return KOMA_OK;
+}
+
+// The request's device blocks of the shared lane, freed in order on `st`.
+void free_shared_blocks(Req* r, cudaStream_t st) {
+    for (void** p : {reinterpret_cast<void**>(&r->d32), reinterpret_cast<void**>(&r->drec),
+                     reinterpret_cast<void**>(&r->drows), reinterpret_cast<void**>(&r->dsig),
+                     reinterpret_cast<void**>(&r->dstate), reinterpret_cast<void**>(&r->dmaps),
+                     reinterpret_cast<void**>(&r->dpulses), reinterpret_cast<void**>(&r->drec_full)}) {
+        if (*p) cudaFreeAsync(*p, st);
+        *p = nullptr;
+    }
 }
 
 void release_device(koma_server* S, Req* r) {
@@ -389,30 +414,56 @@ void release_device(koma_server* S, Req* r) {
     r->dp32 = nullptr;
     S->used -= std::min(S->used, r->ph_dev_bytes);
     r->ph_dev_bytes = 0;
-    if (r->d32) cudaFreeAsync(r->d32, S->s_red);
-    if (r->drec) cudaFreeAsync(r->drec, S->s_red);
-    if (r->drows) cudaFreeAsync(r->drows, S->s_red);
-    if (r->dsig) cudaFreeAsync(r->dsig, S->s_red);
-    if (r->dstate) cudaFreeAsync(r->dstate, S->s_red);
-    if (r->dmaps) cudaFreeAsync(r->dmaps, S->s_red);
-    if (r->dpulses) cudaFreeAsync(r->dpulses, S->s_red);
-    if (r->drec_full) cudaFreeAsync(r->drec_full, S->s_red);
-    r->dmaps = nullptr;
-    r->dpulses = nullptr;
-    r->drec_full = nullptr;
+    free_shared_blocks(r, S->s_red);
     r->recs_full.clear();
     r->recs_full.shrink_to_fit();
-    r->dstate = nullptr;
-    r->d32 = nullptr;
-    r->drec = nullptr;
-    r->drows = nullptr;
-    r->dsig = nullptr;
     S->used -= std::min(S->used, r->dev_bytes);
     r->dev_bytes = 0;
     r->h32.clear();
     r->h32.shrink_to_fit();
     r->recs.clear();
     r->recs.shrink_to_fit();
+}
+
+// A request of the shared lane uploaded by the submitting thread when the
+// memory budget has room for it now: the allocations, copies and map
+// pre-pass go on an upload stream (ev_up orders its launches after them),
+// and the host arrays are released at once. Otherwise, or if an allocation
+// fails, the worker uploads it at admission.
+void upload_shared_request(koma_server* S, Req* r) {
+    const size_t need = req_bytes(r);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop || (S->budget && S->used + need > S->budget)) return;
+        S->used += need;
+        S->peak = std::max(S->peak, S->used);
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != S->device) cudaSetDevice(S->device);
+    koma_server::UpSlot* U = up_acquire(S);
+    const koma_status st = U ? admit(S, r, U->st) : KOMA_E_NOMEM;
+    if (st == KOMA_OK) {
+        r->uploaded = true;  // r->dev_bytes == need: admit counted the same arrays
+        std::vector<float>().swap(r->h32);
+        std::vector<koma::Rec32>().swap(r->recs);
+        std::vector<koma::Rec32>().swap(r->recs_full);
+    } else {
+        cudaGetLastError();
+        if (U) cudaStreamSynchronize(U->st);  // nothing may still copy into the blocks
+        free_shared_blocks(r, U ? U->st : S->s_red);
+        if (r->hsig) cudaFreeHost(r->hsig);
+        r->hsig = nullptr;
+        if (r->ev_up) cudaEventDestroy(r->ev_up);
+        if (r->ev_done) cudaEventDestroy(r->ev_done);
+        r->ev_up = r->ev_done = nullptr;
+        r->dev_bytes = 0;
+        r->state = PENDING;
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->used -= std::min(S->used, need);
+    }
+    up_release(S, U);
+    if (prev >= 0 && prev != S->device) cudaSetDevice(prev);
 }
 
 koma_status make_slot(koma_server* S, Slot& sl, int64_t cap) {
@@ -561,6 +612,14 @@ void worker_loop(koma_server* S) {
         // admission (arrival order, device-memory budget)
         while (!S->pending.empty() && static_cast<int>(S->active.size()) < S->max_active) {
             Req* r = S->pending.front();
+            if (r->uploaded) {  // its submitting thread uploaded it (memory counted there)
+                S->pending.pop_front();
+                r->t_admit = now_s();
+                S->active.push_back(r);
+                if (r->units_total == 0) finalize(S, r);  // nothing to step
+                progress = true;
+                continue;
+            }
             const size_t need = req_bytes(r);
             if (S->budget && S->used + need > S->budget) {
                 if (S->active.empty()) {
@@ -589,7 +648,7 @@ void worker_loop(koma_server* S) {
                 progress = true;
                 continue;
             }
-            const koma_status st = admit(S, r);
+            const koma_status st = admit(S, r, S->s_up);
             if (st != KOMA_OK) {
                 release_device(S, r);
                 fail_req(r, st, "admission failed (device allocation or upload)");
@@ -993,8 +1052,16 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
     r->batch_next.assign(static_cast<size_t>(r->n_batches), 0);
     r->batch_busy.assign(static_cast<size_t>(r->n_batches), 0);
     r->rem_work = static_cast<double>(r->n_batches) * kBatchSpins * w;
+    upload_shared_request(S, r);
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->stop) {
+        if (r->uploaded) {
+            cudaEventSynchronize(r->ev_up);  // its copies are done
+            release_device(S, r);
+            if (r->hsig) cudaFreeHost(r->hsig);
+            cudaEventDestroy(r->ev_up);
+            cudaEventDestroy(r->ev_done);
+        }
         delete r;
         return KOMA_E_BUSY;
     }
