@@ -89,7 +89,8 @@ struct Req {
     koma::Rec32* drec = nullptr;
     float2* drows = nullptr;
     double* dsig = nullptr;
-    double* hsig = nullptr;  // pinned
+    double* hsig = nullptr;  // pinned, from the server's pool (size class hsig_cls)
+    int hsig_cls = -1;
     cudaEvent_t ev_up = nullptr, ev_done = nullptr;
     ReqState state = PENDING;
     koma_status err = KOMA_OK;
@@ -159,6 +160,11 @@ struct koma_server {
     };
     std::mutex up_mu;
     std::vector<UpSlot*> up_free, up_all;
+    // pinned result buffers, reused: free lists by power-of-two size class
+    // (cudaMallocHost / cudaFreeHost per request cost driver time, and a
+    // free waits for the device)
+    std::mutex host_mu;
+    std::vector<void*> host_free[48];
     size_t budget = 0, used = 0, peak = 0;
     int max_active = 64;
     double launch_work = 0;  // work units per launch (cap)
@@ -195,6 +201,40 @@ koma_status cuda_err(koma_server* S, cudaError_t e, const char* what) {
     snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
     S->fatal = buf;
     return e == cudaErrorMemoryAllocation ? KOMA_E_NOMEM : KOMA_E_CUDA;
+}
+
+// A pinned host buffer of at least `bytes` (4 KiB and up, power-of-two
+// classes) from the server's pool; *cls receives its class. Null on failure.
+double* host_acquire(koma_server* S, size_t bytes, int* cls) {
+    int c = 12;
+    while ((size_t{1} << c) < bytes && c < 47) ++c;
+    *cls = c;
+    {
+        std::lock_guard<std::mutex> lk(S->host_mu);
+        if (!S->host_free[c].empty()) {
+            void* p = S->host_free[c].back();
+            S->host_free[c].pop_back();
+            return static_cast<double*>(p);
+        }
+    }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, size_t{1} << c) != cudaSuccess) {
+        cudaGetLastError();
+        *cls = -1;
+        return nullptr;
+    }
+    return static_cast<double*>(p);
+}
+
+// Back to the pool (only once nothing copies into it any more).
+void host_release(koma_server* S, Req* r) {
+    if (!r->hsig) return;
+    {
+        std::lock_guard<std::mutex> lk(S->host_mu);
+        S->host_free[r->hsig_cls].push_back(r->hsig);
+    }
+    r->hsig = nullptr;
+    r->hsig_cls = -1;
 }
 
 // An upload stream (with its conversion status word) for a submitting
@@ -350,7 +390,10 @@ koma_status admit(koma_server* S, Req* r, cudaStream_t st) {
     if (e == cudaSuccess && brows)
         e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->drows), brows, S->pool, st);
     if (e == cudaSuccess && bsig) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dsig), bsig, S->pool, st);
-    if (e == cudaSuccess && bsig) e = cudaMallocHost(reinterpret_cast<void**>(&r->hsig), bsig);
+    if (e == cudaSuccess && bsig) {
+        r->hsig = host_acquire(S, bsig, &r->hsig_cls);
+        if (!r->hsig) e = cudaErrorMemoryAllocation;
+    }
     if (e == cudaSuccess && r->n_chunks > 1)
         e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->dstate), static_cast<size_t>(3 * r->n_pad) * sizeof(float),
                                     S->pool, st);
@@ -452,8 +495,7 @@ void upload_shared_request(koma_server* S, Req* r) {
         cudaGetLastError();
         if (U) cudaStreamSynchronize(U->st);  // nothing may still copy into the blocks
         free_shared_blocks(r, U ? U->st : S->s_red);
-        if (r->hsig) cudaFreeHost(r->hsig);
-        r->hsig = nullptr;
+        host_release(S, r);
         if (r->ev_up) cudaEventDestroy(r->ev_up);
         if (r->ev_done) cudaEventDestroy(r->ev_done);
         r->ev_up = r->ev_done = nullptr;
@@ -793,7 +835,10 @@ void lane_loop(koma_server* S, int k) {
         cudaError_t e = cudaSuccess;
         if (st == KOMA_OK && out_bytes) {
             e = cudaMallocAsync(reinterpret_cast<void**>(&dsig), out_bytes, st_k);
-            if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&r->hsig), out_bytes);
+            if (e == cudaSuccess) {
+                r->hsig = host_acquire(S, out_bytes, &r->hsig_cls);
+                if (!r->hsig) e = cudaErrorMemoryAllocation;
+            }
             if (e != cudaSuccess) st = KOMA_E_NOMEM;
         }
         if (st == KOMA_OK) st = koma_simulate(ctx, ph, seq, KOMA_FP32_SPLITPHASE, dsig, st_k);
@@ -1058,7 +1103,7 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
         if (r->uploaded) {
             cudaEventSynchronize(r->ev_up);  // its copies are done
             release_device(S, r);
-            if (r->hsig) cudaFreeHost(r->hsig);
+            host_release(S, r);
             cudaEventDestroy(r->ev_up);
             cudaEventDestroy(r->ev_done);
         }
@@ -1116,7 +1161,7 @@ extern "C" koma_status koma_server_wait(koma_server* S, uint64_t id, double time
     if (st != KOMA_OK) S->fatal = r->msg;
     S->all.erase(it);
     lk.unlock();
-    if (r->hsig) cudaFreeHost(r->hsig);
+    host_release(S, r);  // the result's copy into it completed before the request was retired
     if (r->ev_up) cudaEventDestroy(r->ev_up);
     if (r->ev_done) cudaEventDestroy(r->ev_done);
     delete r;
@@ -1182,6 +1227,8 @@ extern "C" koma_status koma_server_destroy(koma_server* S) {
         if (r->ev_done) cudaEventDestroy(r->ev_done);
         delete r;
     }
+    for (auto& v : S->host_free)
+        for (void* p : v) cudaFreeHost(p);
     for (koma_server::UpSlot* U : S->up_all) {
         cudaStreamSynchronize(U->st);
         cudaStreamDestroy(U->st);
