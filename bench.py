@@ -818,8 +818,13 @@ def run_ours(args, rank, world, local):
         gc.enable()
         t_e2e = reduce_max(t_e2e, world)
         sim2.close()
-        # raw FP64 phantom rows (the FP32 block is built on the device), three record streams
-        h2d = ph.n * 7 * 8 + info["n_records"] * (64 + 128 + 128)
+        # raw FP64 phantom rows (the FP32 block is built on the device), the FP32 record
+        # stream (the host call builds no FP64 or motion stream for an FP32 static
+        # simulation), the compacted stream of the mapped pulses, the readout tables
+        n_rec_c = (info["n_records"] - info.get("n_rf_map_steps", 0) + info.get("n_rf_map_runs", 0)
+                   if info.get("n_rf_maps", 0) else 0)
+        h2d = (ph.n * 7 * 8 + 64 * (info["n_records"] + n_rec_c) + 64 * info.get("n_mma_runs", 0)
+               + info["n_adc"] + 16 * info.get("n_rf_maps", 0))
         e2e = {"value": units * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(ph.n_groups * seq.n_adc * 16),
                "ms_per_call": 1e3 * t_e2e, "ms_per_call_median": 1e3 * float(np.median(calls)),

@@ -22,6 +22,16 @@ int phantom_from_device(koma_ctx* ctx, int64_t n, double* p64, float* p32, const
 // device-wide wait, unlike koma_phantom_free / koma_sequence_free.
 void phantom_free_on(koma_phantom* ph, void* stream);
 void sequence_free_on(koma_sequence* seq, void* stream);
+// While one exists, the calling thread's host preprocessing runs serially
+// (no worker pool): for threads that already run side by side, like the
+// server's submitting and lane threads.
+struct SerialHostScope {
+    SerialHostScope();
+    ~SerialHostScope();
+    SerialHostScope(const SerialHostScope&) = delete;
+    SerialHostScope& operator=(const SerialHostScope&) = delete;
+    bool prev;
+};
 // compact_records32 writing into `out` (null: count only); returns the
 // compacted stream's length.
 size_t compact_records32_into(const std::vector<Rec32>& r32, Rec32* out);

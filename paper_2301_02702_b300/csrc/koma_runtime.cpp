@@ -252,7 +252,7 @@ bool finite_or_posinf(double v) { return std::isfinite(v) || (std::isinf(v) && v
 
 // Persistent host worker threads for parallel_for: spawning threads costs
 // tens of microseconds each, a noticeable share of an upload. One job runs
-// at a time; a caller that finds the pool busy spawns its own threads.
+// at a time; a caller that finds the pool busy runs its job serially.
 class HostPool {
   public:
     static HostPool& get() {
@@ -329,23 +329,25 @@ class HostPool {
     bool stop_ = false;
 };
 
+// Whether this thread's host work may use the worker pool (threads that
+// already run side by side, like the server's, keep theirs serial).
+thread_local bool t_host_parallel = true;
+
 // fn(lo, hi) over [0, n) split across host threads for large n.
 template <class Fn>
 void parallel_for(int64_t n, Fn&& fn) {
     const int64_t grain = 1 << 15;
     unsigned hw = std::thread::hardware_concurrency();
     int64_t k = std::min<int64_t>(std::max(1u, std::min(hw, 16u)), (n + grain - 1) / grain);
-    if (k <= 1) {
+    if (k <= 1 || !t_host_parallel) {
         fn(int64_t(0), n);
         return;
     }
     const std::function<void(int)> task = [&](int t) { fn(n * t / k, n * (t + 1) / k); };
     if (HostPool::get().try_run(static_cast<int>(k), task)) return;
-    std::vector<std::thread> th;
-    th.reserve(static_cast<size_t>(k - 1));
-    for (int64_t t = 1; t < k; ++t) th.emplace_back(fn, n * t / k, n * (t + 1) / k);
-    fn(int64_t(0), n / k);
-    for (auto& x : th) x.join();
+    // the pool is busy with another caller's job (several threads submitting
+    // at once): serial here, so the callers do not oversubscribe the cores
+    fn(int64_t(0), n);
 }
 
 // Per-spin value checks shared by phantom uploads and server requests.
@@ -857,58 +859,39 @@ struct RecordBuilder {
     }
 };
 
-// Validation + preprocessing shared by koma_sequence_upload and
-// koma_sequence_plan. `err` receives the message on failure.
-koma_status build_records(int64_t n_steps, const double* dt, const double* gx, const double* gy,
-                          const double* gz, const double* b1_re, const double* b1_im, const uint8_t* adc,
-                          RecordBuilder& rb, koma_sequence_info& info, std::string& err) {
-    char buf[256];
-    auto bad = [&](const char* fmt, long long i, double v) {
-        snprintf(buf, sizeof(buf), fmt, i, v);
-        err = buf;
-        return KOMA_E_INVALID;
-    };
-    if (n_steps < 0) return bad("sequence: n_steps = %lld < 0%.0g", n_steps, 0.0);
-    if (!gx || !gy || !gz || !adc || (n_steps > 0 && (!dt || !b1_re || !b1_im)))
-        return bad("sequence: NULL array (n_steps %lld)%.0g", n_steps, 0.0);
-    for (int64_t i = 0; i <= n_steps; ++i) {
-        if (!std::isfinite(gx[i]) || !std::isfinite(gy[i]) || !std::isfinite(gz[i]))
-            return bad("sequence: non-finite gradient at time point %lld%.0g", i, 0.0);
-        if (adc[i] > 1) return bad("sequence: adc[%lld] = %g (must be 0 or 1)", i, adc[i]);
-    }
-    for (int64_t n = 0; n < n_steps; ++n) {
-        if (!std::isfinite(dt[n]) || !(dt[n] > 0))
-            return bad("sequence: dt[%lld] = %g (must be finite and > 0)", n, dt[n]);
-        if (!std::isfinite(b1_re[n]) || !std::isfinite(b1_im[n]))
-            return bad("sequence: non-finite B1 at step %lld%.0g", n, 0.0);
-    }
-    info = koma_sequence_info{};
-    info.n_steps = n_steps;
-    // moments since t_ref (FP64): K = gammabar int G, K1 = gammabar int G s ds
-    // with s absolute time (t_0 = 0), tau = t - t_ref
-    double K[3] = {0, 0, 0}, K1[3] = {0, 0, 0}, tau = 0.0, t = 0.0;
-    if (adc[0]) rb.sample(K, K1, tau);
-    for (int64_t n = 0; n < n_steps; ++n) {
+// Moments since t_ref and step counts of a build (FP64).
+struct BuildCounts {
+    double K[3] = {0, 0, 0}, K1[3] = {0, 0, 0}, tau = 0.0;
+    int64_t n_rf = 0, n_precess = 0;
+};
+
+// Steps [a, b) into rb, from the state in c at absolute time t0. The sample
+// of time point a belongs to the caller (the previous chunk, or the start).
+void build_steps(int64_t n_begin, int64_t n_end, double t0, const double* dt, const double* gx, const double* gy,
+                 const double* gz, const double* b1_re, const double* b1_im, const uint8_t* adc,
+                 RecordBuilder& rb, BuildCounts& c) {
+    double t = t0;
+    for (int64_t n = n_begin; n < n_end; ++n) {
         const double gm[3] = {0.5 * (gx[n] + gx[n + 1]), 0.5 * (gy[n] + gy[n + 1]), 0.5 * (gz[n] + gz[n + 1])};
         const bool rf = b1_re[n] != 0.0 || b1_im[n] != 0.0;
         const double t_next = t + dt[n];
         if (rf) {
-            ++info.n_rf;
+            ++c.n_rf;
             rb.close_run();
-            if (tau > 0.0) {  // bring the state to the start of this RF step
+            if (c.tau > 0.0) {  // bring the state to the start of this RF step
                 koma::Rec32 a{};
                 koma::Rec64 b{};
                 a.type = b.type = koma::REC_PREC;
                 for (int d = 0; d < 3; ++d) {
-                    split(K[d], &a.a[2 * d], &a.a[2 * d + 1]);
-                    b.a[d] = K[d];
-                    b.a[4 + d] = K1[d];
+                    split(c.K[d], &a.a[2 * d], &a.a[2 * d + 1]);
+                    b.a[d] = c.K[d];
+                    b.a[4 + d] = c.K1[d];
                 }
-                split(tau, &a.a[6], &a.a[7]);
-                b.a[3] = tau;
+                split(c.tau, &a.a[6], &a.a[7]);
+                b.a[3] = c.tau;
                 a.count = RecordBuilder::term_bits(a) << koma::kTermShift;
                 koma::RecM m = RecordBuilder::extend(a);
-                for (int d = 0; d < 3; ++d) split(K1[d], &m.a[8 + 2 * d], &m.a[9 + 2 * d]);
+                for (int d = 0; d < 3; ++d) split(c.K1[d], &m.a[8 + 2 * d], &m.a[9 + 2 * d]);
                 m.count = a.count | (RecordBuilder::k1_bits(m, 8) << koma::kTermShift);
                 rb.push(a, b, m);
                 ++rb.n_mat;
@@ -937,23 +920,190 @@ koma_status build_records(int64_t n_steps, const double* dt, const double* gx, c
             koma::RecM m = RecordBuilder::extend(a);
             m.a[13] = static_cast<float>(t_mid);
             rb.push(a, b, m);
-            for (int d = 0; d < 3; ++d) K[d] = K1[d] = 0.0;
-            tau = 0.0;
+            for (int d = 0; d < 3; ++d) c.K[d] = c.K1[d] = 0.0;
+            c.tau = 0.0;
         } else {
-            ++info.n_precess;
+            ++c.n_precess;
             const double g0[3] = {gx[n], gy[n], gz[n]}, g1[3] = {gx[n + 1], gy[n + 1], gz[n + 1]};
             for (int d = 0; d < 3; ++d) {
-                K[d] += kGammaBar * dt[n] * gm[d];
+                c.K[d] += kGammaBar * dt[n] * gm[d];
                 // integral of a linear G times s over [t, t_next]
-                K1[d] += kGammaBar * dt[n] / 6.0 * (g0[d] * (2.0 * t + t_next) + g1[d] * (t + 2.0 * t_next));
+                c.K1[d] += kGammaBar * dt[n] / 6.0 * (g0[d] * (2.0 * t + t_next) + g1[d] * (t + 2.0 * t_next));
             }
-            tau += dt[n];
+            c.tau += dt[n];
         }
         t = t_next;
-        if (adc[n + 1]) rb.sample(K, K1, tau);
+        if (adc[n + 1]) rb.sample(c.K, c.K1, c.tau);
     }
-    rb.close_run();
-    rb.mark_rf_runs();
+}
+
+// Builders of the parallel chunks, kept between builds (their vectors stay
+// allocated: the next build writes warm memory).
+std::mutex g_builders_mu;
+std::vector<RecordBuilder*> g_builders;
+
+RecordBuilder* builder_acquire() {
+    {
+        std::lock_guard<std::mutex> lk(g_builders_mu);
+        if (!g_builders.empty()) {
+            RecordBuilder* b = g_builders.back();
+            g_builders.pop_back();
+            return b;
+        }
+    }
+    return new RecordBuilder();
+}
+
+void builder_release(RecordBuilder* b) {
+    std::lock_guard<std::mutex> lk(g_builders_mu);
+    g_builders.push_back(b);
+}
+
+// Workers for k chunks (the host pool's size, at most k).
+int n_workers_for(int k) {
+    const unsigned hw = std::max(1u, std::min(std::thread::hardware_concurrency(), 16u));
+    return std::max(1, std::min(k, static_cast<int>(hw)));
+}
+
+// run(w) for w in [0, k) on the host pool, or one after another on the
+// calling thread when the pool is busy.
+void run_tasks(int k, const std::function<void(int)>& run) {
+    if (k <= 1 || !t_host_parallel) {
+        for (int w = 0; w < k; ++w) run(w);
+        return;
+    }
+    if (k <= 1) {
+        run(0);
+        return;
+    }
+    if (HostPool::get().try_run(k, run)) return;
+    for (int w = 0; w < k; ++w) run(w);  // the pool is busy: serial (see parallel_for)
+}
+
+// Validation + preprocessing shared by koma_sequence_upload and
+// koma_sequence_plan. `err` receives the message on failure.
+koma_status build_records(int64_t n_steps, const double* dt, const double* gx, const double* gy,
+                          const double* gz, const double* b1_re, const double* b1_im, const uint8_t* adc,
+                          RecordBuilder& rb, koma_sequence_info& info, std::string& err) {
+    char buf[256];
+    auto bad = [&](const char* fmt, long long i, double v) {
+        snprintf(buf, sizeof(buf), fmt, i, v);
+        err = buf;
+        return KOMA_E_INVALID;
+    };
+    if (n_steps < 0) return bad("sequence: n_steps = %lld < 0%.0g", n_steps, 0.0);
+    if (!gx || !gy || !gz || !adc || (n_steps > 0 && (!dt || !b1_re || !b1_im)))
+        return bad("sequence: NULL array (n_steps %lld)%.0g", n_steps, 0.0);
+    for (int64_t i = 0; i <= n_steps; ++i) {
+        if (!std::isfinite(gx[i]) || !std::isfinite(gy[i]) || !std::isfinite(gz[i]))
+            return bad("sequence: non-finite gradient at time point %lld%.0g", i, 0.0);
+        if (adc[i] > 1) return bad("sequence: adc[%lld] = %g (must be 0 or 1)", i, adc[i]);
+    }
+    for (int64_t n = 0; n < n_steps; ++n) {
+        if (!std::isfinite(dt[n]) || !(dt[n] > 0))
+            return bad("sequence: dt[%lld] = %g (must be finite and > 0)", n, dt[n]);
+        if (!std::isfinite(b1_re[n]) || !std::isfinite(b1_im[n]))
+            return bad("sequence: non-finite B1 at step %lld%.0g", n, 0.0);
+    }
+    info = koma_sequence_info{};
+    info.n_steps = n_steps;
+    // Long sequences are built in parallel chunks. A chunk starts at a step
+    // a that is not RF, follows the last step of an RF run, and whose time
+    // point a carries no sample:
+    // there the moments since t_ref are zero and no ADC run is open, so the
+    // chunk needs only the absolute time and the number of samples before
+    // it, which one serial pass gives (t summed in the same order as the
+    // serial build: the records are bitwise the same).
+    std::vector<int64_t> cut{0};
+    std::vector<double> t_at{0.0};
+    std::vector<int64_t> adc_at{0};
+    const int64_t kChunkSteps = 2048;
+    if (n_steps >= 2 * kChunkSteps) {
+        double t = 0.0;
+        int64_t na = adc[0];
+        int64_t next = kChunkSteps;
+        for (int64_t n = 0; n < n_steps; ++n) {
+            // step n - 1 ends an RF run (step n is not RF), time point n has no sample
+            if (n >= next && n > 0 && (b1_re[n - 1] != 0.0 || b1_im[n - 1] != 0.0) && b1_re[n] == 0.0 &&
+                b1_im[n] == 0.0 && !adc[n]) {
+                cut.push_back(n);
+                t_at.push_back(t);
+                adc_at.push_back(na);
+                next = n + kChunkSteps;
+            }
+            t = t + dt[n];
+            na += adc[n + 1];
+        }
+    }
+    cut.push_back(n_steps);
+    const int n_chunks = static_cast<int>(cut.size()) - 1;
+    if (n_chunks == 1) {
+        BuildCounts c;
+        if (adc[0]) rb.sample(c.K, c.K1, c.tau);
+        build_steps(0, n_steps, 0.0, dt, gx, gy, gz, b1_re, b1_im, adc, rb, c);
+        rb.close_run();
+        rb.mark_rf_runs();
+        info.n_rf = c.n_rf;
+        info.n_precess = c.n_precess;
+    } else {
+        // worker w builds chunks w, w + k, ... into a builder it keeps (warm
+        // memory), one after another; the chunks are then concatenated in
+        // order. No RF run crosses a cut, and a chunk never starts with an RF
+        // record (its first step is not RF and has dt > 0).
+        const int k = n_workers_for(n_chunks);
+        struct Range {
+            size_t r32[2], r64[2], rm[2];
+            int64_t n_adc_end;
+        };
+        std::vector<Range> rng(static_cast<size_t>(n_chunks));
+        std::vector<BuildCounts> cnt(static_cast<size_t>(n_chunks));
+        std::vector<RecordBuilder*> wb(static_cast<size_t>(k), nullptr);
+        for (int w = 0; w < k; ++w) wb[w] = builder_acquire();
+        const std::function<void(int)> run = [&](int w) {
+            RecordBuilder& tl = *wb[w];
+            tl.reset(rb.want64, rb.wantM);
+            for (int i = w; i < n_chunks; i += k) {
+                Range& R = rng[i];
+                R.r32[0] = tl.r32.size();
+                R.r64[0] = tl.r64.size();
+                R.rm[0] = tl.rm.size();
+                tl.n_adc = adc_at[i];
+                BuildCounts c;  // local: the chunks' counters share cache lines
+                if (i == 0 && adc[0]) tl.sample(c.K, c.K1, c.tau);
+                build_steps(cut[i], cut[i + 1], t_at[i], dt, gx, gy, gz, b1_re, b1_im, adc, tl, c);
+                cnt[i] = c;
+                tl.close_run();
+                R.r32[1] = tl.r32.size();
+                R.r64[1] = tl.r64.size();
+                R.rm[1] = tl.rm.size();
+                R.n_adc_end = tl.n_adc;
+            }
+            tl.mark_rf_runs();
+        };
+        run_tasks(k, run);
+        size_t n32 = 0, n64 = 0, nm = 0;
+        for (int w = 0; w < k; ++w) {
+            n32 += wb[w]->r32.size();
+            n64 += wb[w]->r64.size();
+            nm += wb[w]->rm.size();
+            rb.n_runs += wb[w]->n_runs;
+            rb.n_mat += wb[w]->n_mat;
+        }
+        rb.r32.reserve(n32);
+        if (rb.want64) rb.r64.reserve(n64);
+        if (rb.wantM) rb.rm.reserve(nm);
+        for (int i = 0; i < n_chunks; ++i) {
+            const RecordBuilder& b = *wb[i % k];
+            const Range& R = rng[i];
+            rb.r32.insert(rb.r32.end(), b.r32.begin() + R.r32[0], b.r32.begin() + R.r32[1]);
+            if (rb.want64) rb.r64.insert(rb.r64.end(), b.r64.begin() + R.r64[0], b.r64.begin() + R.r64[1]);
+            if (rb.wantM) rb.rm.insert(rb.rm.end(), b.rm.begin() + R.rm[0], b.rm.begin() + R.rm[1]);
+            info.n_rf += cnt[i].n_rf;
+            info.n_precess += cnt[i].n_precess;
+        }
+        rb.n_adc = rng[n_chunks - 1].n_adc_end;
+        for (int w = 0; w < k; ++w) builder_release(wb[w]);
+    }
     info.n_adc = rb.n_adc;
     info.n_records = static_cast<int64_t>(rb.r32.size());
     info.n_adc_runs = rb.n_runs;
@@ -1086,17 +1236,32 @@ void plan_rf_maps(std::vector<koma::Rec32>& r32, RfMapPlan& P) {
     };
     // a multiplicative hash of the run's 8-byte words buckets the candidates;
     // equality is checked byte for byte
+    // the runs' hashes, in parallel for long sequences (runs are independent)
+    std::vector<uint64_t> hash(runs.size(), 0);
+    auto hash_runs = [&](size_t q0, size_t q1) {
+        for (size_t q = q0; q < q1; ++q) {
+            if (runs[q].len < static_cast<size_t>(koma::kRfMapMinLen)) continue;
+            uint64_t h = 1469598103934665603ull;
+            const unsigned char* b = reinterpret_cast<const unsigned char*>(&r32[runs[q].begin]);
+            for (size_t k = 0; k < runs[q].len * sizeof(koma::Rec32); k += 8) {  // 64-byte records: whole words
+                uint64_t w;
+                std::memcpy(&w, b + k, 8);
+                h = (h ^ w) * 1099511628211ull;
+                h ^= h >> 29;
+            }
+            hash[q] = h;
+        }
+    };
+    if (r32.size() >= 16384 && runs.size() >= 16) {
+        const int k = n_workers_for(static_cast<int>(std::min<size_t>(runs.size(), 64)));
+        run_tasks(k, [&](int w) { hash_runs(runs.size() * w / k, runs.size() * (w + 1) / k); });
+    } else {
+        hash_runs(0, runs.size());
+    }
     std::map<std::pair<uint64_t, size_t>, std::vector<std::vector<size_t>>> buckets;
     for (size_t q = 0; q < runs.size(); ++q) {
         if (runs[q].len < static_cast<size_t>(koma::kRfMapMinLen)) continue;
-        uint64_t h = 1469598103934665603ull;
-        const unsigned char* b = reinterpret_cast<const unsigned char*>(&r32[runs[q].begin]);
-        for (size_t k = 0; k < runs[q].len * sizeof(koma::Rec32); k += 8) {  // 64-byte records: whole words
-            uint64_t w;
-            std::memcpy(&w, b + k, 8);
-            h = (h ^ w) * 1099511628211ull;
-            h ^= h >> 29;
-        }
+        const uint64_t h = hash[q];
         auto& classes = buckets[{h, runs[q].len}];
         bool placed = false;
         for (auto& c : classes) {
@@ -2197,6 +2362,9 @@ void host_rf_maps32(std::vector<Rec32>& r32, std::vector<RfMapPulse>& pulses, ko
     info.n_rf_map_steps = fp.steps;
     info.n_rf_map_pulse_steps = fp.pulse_steps;
 }
+
+SerialHostScope::SerialHostScope() : prev(t_host_parallel) { t_host_parallel = false; }
+SerialHostScope::~SerialHostScope() { t_host_parallel = prev; }
 
 koma_status sequence_upload_fp32(koma_ctx* ctx, int64_t n_steps, const double* dt, const double* gx,
                                  const double* gy, const double* gz, const double* b1_re, const double* b1_im,

@@ -801,6 +801,7 @@ void worker_loop(koma_server* S) {
 // the worker retires the request.
 void lane_loop(koma_server* S, int k) {
     cudaSetDevice(S->device);
+    const koma::SerialHostScope serial_;  // the lanes run side by side: no worker pool
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
         S->cv_lane.wait(lk, [&] { return S->stop || !S->lane_q.empty(); });
@@ -947,6 +948,7 @@ extern "C" koma_status koma_server_submit(koma_server* S, int64_t n, const doubl
                                           const uint8_t* adc, uint64_t* id_out) {
     NvtxRange nvtx_("koma_server_submit");
     if (!S || !id_out) return KOMA_E_INVALID;
+    const koma::SerialHostScope serial_;  // submitters run side by side: no worker pool
     Req* r = new (std::nothrow) Req();
     if (!r) return KOMA_E_NOMEM;
     r->t_submit = now_s();

@@ -132,6 +132,33 @@ def test_plan_reproduces_sample_moments(lib, name):
     assert int(np.sum(rec[:, 0] == 0)) == seq.n_rf
 
 
+@pytest.mark.parametrize("name", ["se128", "epi512", "random_long"])
+def test_long_sequences_built_in_chunks_reproduce_sample_moments(lib, name):
+    """Sequences of 16,384 steps and more are built in parallel chunks cut
+    after RF steps; every sample's moments (K with absolute-time first
+    moments K1) and index must still match the reference walk, and the
+    record counts must add up."""
+    seq = random_sequence(60000, seed=11) if name == "random_long" else workload(name, "full")[1]
+    assert seq.n_steps >= 16384
+    info, rec = koma.koma_sequence_plan(seq, with_records=True)
+    assert info["n_adc"] == seq.n_adc and info["n_rf"] == seq.n_rf
+    assert info["n_rf"] + info["n_precess"] == seq.n_steps
+    assert info["n_records"] == info["n_rf"] + info["n_adc_runs"] + info["n_materialize"]
+    ref = _reference_samples(seq)
+    got = _decode_samples(rec)
+    assert len(got) == len(ref)
+    kr = np.array([r[0] for r in ref]); kg = np.array([g[0] for g in got])
+    tr = np.array([r[1] for r in ref]); tg = np.array([g[1] for g in got])
+    k1r = np.array([r[2] for r in ref]); k1g = np.array([g[2] for g in got])
+    assert np.all(np.abs(kr - kg) <= 1e-9 * (1 + np.max(np.abs(kr), axis=1, keepdims=True)))
+    assert np.all(np.abs(tr - tg) <= 1e-12 * (1 + tr))
+    assert np.all(np.abs(k1r - k1g) <= 1e-9 * (1 + np.max(np.abs(k1r), axis=1, keepdims=True)))
+    assert int(np.sum(rec[:, 0] == 0)) == seq.n_rf
+    # the same records on every call (the chunks' order does not depend on timing)
+    info2, rec2 = koma.koma_sequence_plan(seq, with_records=True)
+    assert np.array_equal(rec, rec2)
+
+
 def test_plan_merges_uniform_readouts(lib):
     """A Cartesian readout of n samples at constant gradient becomes
     ceil(n / 128) ADC records."""
