@@ -106,7 +106,7 @@ static_assert(sizeof(MmaRun) == 64, "MmaRun layout");
 // kernels that apply maps walk a compacted stream in which every such run is
 // one REC_MAP record (k0 = slot, count = the run's length).
 constexpr int kMaxRfMaps = 8;
-constexpr int kRfMapFloats = 12;     // A row-major (9 values), then c (3)
+constexpr int kRfMapFloats = 12;     // per spin and map: three float4 rows (A_i0, A_i1, A_i2, c_i)
 constexpr int kRfMapMinRuns = 3;     // occurrences that make a map worth its pre-pass
 constexpr int kRfMapMinLen = 4;      // RF steps of a run worth a map
 struct RfMapPulse {
@@ -237,14 +237,14 @@ struct BlochArgs {
     float mma_escale = 1.f;         // power of two keeping E in FP16 range
     // repeated RF pulses (FP32 static kernel only): `rec` is then the
     // compacted stream, whose REC_MAP records apply map k0 of this
-    // [n_rf_maps][kRfMapFloats][n_pad] buffer
+    // [n_rf_maps][3][n_pad] float4 buffer (row i of A and c_i per spin)
     const float* rf_maps = nullptr;
     int n_rf_maps = 0;
     int64_t n_mma_snaps = 0;        // rows of mma_snap
 };
 
 // Pre-pass of the repeated-pulse maps: for every spin j < n and pulse p,
-// (A, c) of pulse p's RF records into maps[p][0..11][j].
+// (A, c) of pulse p's RF records into maps[p], three float4 rows per spin (row i of A, c_i).
 struct RfMapArgs {
     const float* p32 = nullptr;
     int64_t n_pad = 0;
@@ -252,7 +252,7 @@ struct RfMapArgs {
     const Rec32* rec = nullptr;
     const RfMapPulse* pulses = nullptr;
     int n_pulses = 0;
-    float* maps = nullptr;          // [n_pulses][kRfMapFloats][n_pad]
+    float* maps = nullptr;          // [n_pulses][3][n_pad] float4: row i of A, then c_i
     float ext[4] = {0, 0, 0, 0};
 };
 
@@ -324,7 +324,7 @@ struct BatchDesc {
     int used;
     int n_rf_maps;               // map slots of the request's repeated pulses (0: none)
     int64_t rf_hdr;              // header of the RF run rec_begin lies inside (-1: none)
-    const float* rf_maps;        // [n_rf_maps][kRfMapFloats][n_pad]; `rec` is then compacted
+    const float* rf_maps;        // [n_rf_maps][3][n_pad] float4 (row of A, c); `rec` is then compacted
 };
 static_assert(sizeof(BatchDesc) == 128, "BatchDesc layout");
 

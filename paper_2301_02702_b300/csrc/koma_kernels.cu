@@ -371,20 +371,20 @@ struct Spins {
         }
     }
 
-    // A repeated pulse taken by its map: M <- A M + c per spin, (A, c) row j
-    // of the map buffer mp [kRfMapFloats][np] (A row-major, then c).
+    // A repeated pulse taken by its map: M <- A M + c per spin. The map buffer
+    // mp holds, per spin j, the three rows (A_i0, A_i1, A_i2, c_i) as float4
+    // at mp4[i * np + j]: three 16-byte loads per spin.
     __device__ __forceinline__ void apply_map(const float* __restrict__ mp, int64_t np) {
+        const float4* __restrict__ mp4 = reinterpret_cast<const float4*>(mp);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const int64_t j = index(s);
             if (j < end) {
-                float a[kRfMapFloats];
-#pragma unroll
-                for (int k = 0; k < kRfMapFloats; ++k) a[k] = mp[k * np + j];
+                const float4 r0 = mp4[j], r1 = mp4[np + j], r2 = mp4[2 * np + j];
                 const float x = mx[s], y = my[s], z = mz[s];
-                mx[s] = fmaf(a[0], x, fmaf(a[1], y, fmaf(a[2], z, a[9])));
-                my[s] = fmaf(a[3], x, fmaf(a[4], y, fmaf(a[5], z, a[10])));
-                mz[s] = fmaf(a[6], x, fmaf(a[7], y, fmaf(a[8], z, a[11])));
+                mx[s] = fmaf(r0.x, x, fmaf(r0.y, y, fmaf(r0.z, z, r0.w)));
+                my[s] = fmaf(r1.x, x, fmaf(r1.y, y, fmaf(r1.z, z, r1.w)));
+                mz[s] = fmaf(r2.x, x, fmaf(r2.y, y, fmaf(r2.z, z, r2.w)));
             }
         }
     }
@@ -984,7 +984,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_fp32_kernel(const __grid_c
 // RF step, then relaxation). The kernel steps the three columns of A (from
 // the unit vectors, relaxation without the recovery term) and c (from
 // M = 0, with it) through the pulse's records, two spins per thread in
-// packed FP32 pairs, and writes maps[p][k][j] (A row-major, then c). The
+// packed FP32 pairs, and writes maps[p] as float4 rows (row i of A, c_i) per spin. The
 // rotation path per run follows the Bloch kernel: cos and sin(t)/t by their
 // even series when the run's largest half angle allows it (bound from the
 // run header's maxima and the phantom's extents), else rsqrt and sin/cos of
@@ -1186,8 +1186,9 @@ __global__ void __launch_bounds__(kMapBlock) rf_map_kernel(const __grid_constant
             }
         }
     }
-    // A[i][k] = i-th part of column k; c last
-    float* __restrict__ out = A.maps + static_cast<int64_t>(blockIdx.y) * kRfMapFloats * np;
+    // row i of A (A[i][k] = i-th part of column k) and c_i as one float4 per
+    // spin: out4[i * np + j]
+    float4* __restrict__ out4 = reinterpret_cast<float4*>(A.maps + static_cast<int64_t>(blockIdx.y) * kRfMapFloats * np);
     float a0[kRfMapFloats], a1[kRfMapFloats];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -1196,9 +1197,9 @@ __global__ void __launch_bounds__(kMapBlock) rf_map_kernel(const __grid_constant
 #pragma unroll
     for (int i = 0; i < 3; ++i) unpk(m.v[9 + i], a0[9 + i], a1[9 + i]);
 #pragma unroll
-    for (int k = 0; k < kRfMapFloats; ++k) {
-        if (v0) out[k * np + j0] = a0[k];
-        if (v1) out[k * np + j1] = a1[k];
+    for (int i = 0; i < 3; ++i) {
+        if (v0) out4[i * np + j0] = make_float4(a0[3 * i], a0[3 * i + 1], a0[3 * i + 2], a0[9 + i]);
+        if (v1) out4[i * np + j1] = make_float4(a1[3 * i], a1[3 * i + 1], a1[3 * i + 2], a1[9 + i]);
     }
 }
 

@@ -1825,7 +1825,7 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
         need = off_e + e_bytes;
     }
     // maps of repeated RF pulses (FP32 static Bloch kernel): scratch
-    // [n_maps][kRfMapFloats][n_pad] after the rest, at most kRfMapMaxBytes
+    // [n_maps][3][n_pad] float4 after the rest, at most kRfMapMaxBytes
     const size_t map_bytes = static_cast<size_t>(koma::kRfMapFloats) * static_cast<size_t>(ph->n_pad) * sizeof(float);
     int n_maps = 0;
     size_t off_maps = 0;
