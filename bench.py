@@ -457,6 +457,22 @@ def serve_measure(local: int, n_req: int, rate: float, plain_host: bool = False,
     sim.close()
     t_plain_dev = sum(service_dev)
     plain_lat = fifo_latencies(arrivals, service_dev)
+    # served roofline: the FP32 flops the kernels execute for the stream (stepped RF
+    # steps, pulse steps of the maps and their applications, stepped samples; samples
+    # summed on the tensor cores, in the koma_simulate lane, are not FP32 work) over
+    # the saturated time, against the FP32 peak
+    fp32 = 0.0
+    for (ph, seq, _), f in zip(reqs, infos):
+        p = koma.koma_sequence_plan(seq)
+        per_spin = ((p["n_rf"] - p["n_rf_map_steps"]) * FLOPS_RF_STEP + p["n_rf_map_pulse_steps"] * FLOPS_MAP_STEP
+                    + p["n_rf_map_runs"] * FLOPS_MAP_APPLY
+                    + (p["n_adc"] - (p["n_mma_samples"] if f["lane"] == 1 else 0)) * FLOPS_ADC_SAMPLE)
+        fp32 += float(ph.n) * per_spin
+    served_roof = {"bound": "alu", "achieved": fp32 / t_sat / 1e12, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                   "frac": fp32 / t_sat / 1e12 / PEAK_FP32_TFLOPS,
+                   "how": "FP32 flops the kernels execute for the whole stream (50 per stepped RF spin-step, "
+                          "302 per pulse step of a repeated pulse's map, 18 per map application, 8 per stepped "
+                          "sample; samples summed on the tensor cores not counted) / the saturated time"}
     out = {
         "requests": len(reqs), "rate_per_s": rate,
         "mean_spin_steps_per_request": total_units / len(reqs),
@@ -472,6 +488,7 @@ def serve_measure(local: int, n_req: int, rate: float, plain_host: bool = False,
                          "plain": "one koma_simulate per request on device-resident inputs, back to back on one "
                                   "stream (device time, CUDA events); latencies under the same arrivals"},
         "ratio_saturated_vs_plain_device": t_plain_dev / t_sat,
+        "roofline": served_roof,
         "server": {k: stats[k] for k in ("batches", "mem_peak", "completed", "failed", "lane_runs")},
         "lanes": {"requests": [sum(1 for f in infos if f["lane"] == k) for k in (0, 1)],
                   "spin_steps": [sum(r[2] for r, f in zip(reqs, infos) if f["lane"] == k) for k in (0, 1)],
