@@ -206,8 +206,10 @@ koma_status cuda_err(koma_server* S, cudaError_t e, const char* what) {
 // A pinned host buffer of at least `bytes` (4 KiB and up, power-of-two
 // classes) from the server's pool; *cls receives its class. Null on failure.
 double* host_acquire(koma_server* S, size_t bytes, int* cls) {
+    *cls = -1;
+    if (bytes > (size_t{1} << 47)) return nullptr;
     int c = 12;
-    while ((size_t{1} << c) < bytes && c < 47) ++c;
+    while ((size_t{1} << c) < bytes) ++c;
     *cls = c;
     {
         std::lock_guard<std::mutex> lk(S->host_mu);
