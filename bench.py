@@ -911,6 +911,8 @@ def result_line(args, world, ph, seq, info, launch, stage_ms, clk, value, ms_max
         flops += float(ph.n) * info["n_rf_map_runs"] * FLOPS_MAP_APPLY
     achieved = flops / (k1 / 1e3) / 1e12 if k1 else None
     kname = "bloch_motion_kernel" if moving else ("bloch_items_kernel" if grouped else "bloch_fp32_kernel")
+    if grouped and launch["spins_per_thread"] == 8:
+        kname = "bloch_items_z_kernel"  # the dictionary kernel for isochromats along z, 8 spins per thread
     roofs = []
     if maps:
         mflops = float(ph.n) * info["n_rf_map_pulse_steps"] * FLOPS_MAP_STEP
@@ -924,7 +926,8 @@ def result_line(args, world, ph, seq, info, launch, stage_ms, clk, value, ms_max
                       "peak_source": "FP32 peak 148 SMs x 128 lanes x 2 x 2032 MHz (unit counts, max SM clock)",
                       "pulses": info["n_rf_maps"], "pulse_steps": info["n_rf_map_pulse_steps"],
                       "replaces_rf_steps": info["n_rf_map_steps"]})
-    roof1 = {"bound": "alu", "kernel": f"{kname}<{launch['spins_per_thread']}>",
+    kfull = kname if kname == "bloch_items_z_kernel" else f"{kname}<{launch['spins_per_thread']}>"
+    roof1 = {"bound": "alu", "kernel": kfull,
              "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
              "frac": (achieved / PEAK_FP32_TFLOPS) if achieved else None,
              "traffic": measured_traffic(args.workload),

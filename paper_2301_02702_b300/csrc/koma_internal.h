@@ -397,6 +397,12 @@ int launch_bounded_wait_check(int* status, unsigned long long limit_ns, void* st
 // `tile`: step records per shared-memory tile, 64, 128 or 256.
 int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, int tile, void* stream);
 int items_ctas_per_sm(int spins_per_thread, int block, int tile);
+// K3z, the grouped kernel for dictionaries of isochromats along z (spins
+// differ only in z, one T1/T2 per group, RF without gradient, one sample
+// per ADC record): items of 128 spins (as K3 with 4 spins per thread), two
+// per warp, 8 spins per thread; `tile` 128 or 256 records.
+int launch_items_z(const ItemArgs& a, int grid, int block, int tile, void* stream);
+int items_z_ctas_per_sm(int block, int tile);
 // Serving kernel (4 spins per thread, `block` threads: a batch is 128 x
 // block/32 spins).
 int launch_batches(const BatchArgs& a, int grid, int block, void* stream);

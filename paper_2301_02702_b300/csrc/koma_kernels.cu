@@ -256,6 +256,21 @@ __device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
+// both halves equal
+__device__ __forceinline__ f32x2 bcast2(float v) { return pk(v, v); }
+// v - rint(v) for both halves (exact)
+__device__ __forceinline__ f32x2 frac2(f32x2 v) {
+    float a, b;
+    unpk(v, a, b);
+    return sub2(v, pk(rintf(a), rintf(b)));
+}
+// frac_product for two spins (a) and one factor (b, both halves equal):
+// the same operations as the scalar form, lane by lane
+__device__ __forceinline__ f32x2 frac_product2(f32x2 ah, f32x2 al, f32x2 bh, f32x2 bl) {
+    const f32x2 p = mul2(ah, bh);
+    const f32x2 e = fma2(ah, bh, neg2(p));
+    return add2(frac2(p), fma2(ah, bl, fma2(al, bh, e)));
+}
 
 // ---------------------------------------------------------------------------
 // Per-thread spin set: S spins held in registers for a whole walk of the
@@ -1351,6 +1366,209 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_kernel(const __grid_
 }
 
 // ---------------------------------------------------------------------------
+// K3z: grouped kernel for dictionaries of isochromats along z.
+//
+// When the spins of a phantom differ only in z (x = y = 0 and no off-resonance
+// anywhere), every group has a single T1 and T2, the sequence's RF steps carry
+// no gradient (so every RF step rotates all spins alike) and every ADC record
+// holds one sample, a spin needs no more state than M, its z (hi/lo) and M0,
+// and the record work that is the same for all spins (the pulse's rotation,
+// the relaxation factors, the decode) is shared by 8 spins per thread. The
+// items are those of K3 with 128 spins (16 lanes x 8); a warp takes two of
+// them, one per half-warp, so an entry fills as many lanes as under K3 with 4
+// spins per thread, and a sample's sum is a 16-lane butterfly per half. The
+// per-step arithmetic is that of K1/K3: the uniform RF step of Spins::rf_uniform
+// (series for the small angles), the hi/lo phase and hardware sine of
+// Spins::exact, the same relaxation factors.
+// ---------------------------------------------------------------------------
+constexpr int kZS = 8;             // spins per thread
+constexpr int kZNP = kZS / 2;      // packed pairs
+
+template <int T>
+__global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_z_kernel(const __grid_constant__ ItemArgs A) {
+    __shared__ __align__(128) Rec32 s_rec[2][T];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ int64_t s_batch;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int half = lane >> 4, hl = lane & 15;
+    const BarPair bar{smem_u32(&s_bar[0])};
+    if (tid == 0) {
+        mbar_init(bar[0], 1);
+        mbar_init(bar[1], 1);
+        fence_mbar_init();
+    }
+    const int64_t np = A.n_pad;
+    const float* __restrict__ P = A.p32;
+    const Rec32* grec = static_cast<const Rec32*>(A.rec);
+    const int64_t n_tiles = (A.n_rec + T - 1) / T;
+    uint64_t g0 = 0;
+    for (;;) {
+        if (tid == 0) s_batch = atomicAdd(A.counter, 1);
+        __syncthreads();
+        const int64_t batch = s_batch;
+        __syncthreads();
+        if (batch * 2 * nwarps >= A.n_items) break;
+        const int64_t oi = (batch * nwarps + warp) * 2 + half;
+        int64_t ib = 0, ie = 0;
+        float2* row = nullptr;
+        if (oi < A.n_items) {
+            const int64_t item = A.order[oi];
+            ib = A.item_begin[item];
+            ie = A.item_begin[item + 1];
+            row = static_cast<float2*>(A.partial) + item * A.n_adc;
+        }
+        // the lane's 8 spins: ib + hl + 16 s (zero state past the item's end)
+        f32x2 MX[kZNP], MY[kZNP], MZ[kZNP], ZH[kZNP], ZL[kZNP], M0[kZNP];
+#pragma unroll
+        for (int p = 0; p < kZNP; ++p) {
+            const int64_t j0 = ib + hl + 16 * (2 * p), j1 = j0 + 16;
+            const bool v0 = j0 < ie, v1 = j1 < ie;
+            ZH[p] = pk(v0 ? P[P32_ZH * np + j0] : 0.f, v1 ? P[P32_ZH * np + j1] : 0.f);
+            ZL[p] = pk(v0 ? P[P32_ZL * np + j0] : 0.f, v1 ? P[P32_ZL * np + j1] : 0.f);
+            M0[p] = pk(v0 ? P[P32_M0 * np + j0] : 0.f, v1 ? P[P32_M0 * np + j1] : 0.f);
+            MX[p] = pk(0.f, 0.f);
+            MY[p] = pk(0.f, 0.f);
+            MZ[p] = M0[p];
+        }
+        // the item's group shares T1 and T2
+        const float r1 = ib < ie ? P[P32_R1 * np + ib] : 0.f, r2 = ib < ie ? P[P32_R2 * np + ib] : 0.f;
+        float em1 = 0.f, em2 = 0.f, dt_cached = -1.f;
+        bool small = true;
+        if (tid == 0) {
+            for (int64_t t = 0; t < 2 && t < n_tiles; ++t) issue_tile(s_rec, bar, grec, A.n_rec, t, g0 + t);
+        }
+        for (int64_t t = 0; t < n_tiles; ++t) {
+            const uint64_t g = g0 + t;
+            const int b = static_cast<int>(g & 1);
+            const bool ok = mbar_wait_bounded(bar[b], static_cast<uint32_t>((g >> 1) & 1));
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicOr(A.status, kStatusTimeout);
+                    mbar_wait_bounded(bar[b], static_cast<uint32_t>((g >> 1) & 1));
+                    if (t + 1 < n_tiles) mbar_wait_bounded(bar[b ^ 1], static_cast<uint32_t>(((g + 1) >> 1) & 1));
+                }
+                return;
+            }
+            const int nr = static_cast<int>(min(static_cast<int64_t>(T), A.n_rec - t * T));
+            for (int r = 0; r < nr; ++r) {
+                const Rec32& R = s_rec[b][r];
+                const int type = R.type;
+                if (type == REC_RF) {
+                    const float bx = R.a[3], by = R.a[4], b2 = R.a[5], dt = R.a[6];
+                    if (R.count > 0) small = R.a[7] <= 0.754f;  // the run's largest half angle
+                    if (dt != dt_cached) {
+                        em1 = expm1_f32(-dt * r1 * 0.693147180559945309f);
+                        em2 = expm1_f32(-dt * r2 * 0.693147180559945309f);
+                        dt_cached = dt;
+                    }
+                    float ch, f;
+                    if (small) {
+                        float q = fmaf(b2, -2.75573192239858907e-6f, 1.98412698412698413e-4f);
+                        q = fmaf(q, b2, -8.33333333333333333e-3f);
+                        q = fmaf(q, b2, 1.66666666666666667e-1f);
+                        f = fmaf(q, b2, -1.0f);
+                        float c = fmaf(b2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);
+                        c = fmaf(c, b2, -1.38888888888888889e-3f);
+                        c = fmaf(c, b2, 4.16666666666666667e-2f);
+                        c = fmaf(c, b2, -0.5f);
+                        ch = fmaf(c, b2, 1.0f);
+                    } else {
+                        const float rs = rsqrtf(b2);
+                        float sh;
+                        sincospi_f32(b2 * rs * 0.318309886183790671538f, &sh, &ch);
+                        f = -sh * rs;
+                    }
+                    const float ux = bx * f, uy = by * f;
+                    const float c2 = fmaf(-2.f, fmaf(ch, ch, fmaf(ux, ux, uy * uy)), 4.f);
+                    const f32x2 UX = bcast2(ux), UY = bcast2(uy), NUX = bcast2(-ux), NUY = bcast2(-uy);
+                    const f32x2 CH = bcast2(ch), C2 = bcast2(c2), E1 = bcast2(em1), E2 = bcast2(em2);
+#pragma unroll
+                    for (int p = 0; p < kZNP; ++p) {
+                        const f32x2 px = mul2(UY, MZ[p]);
+                        const f32x2 py = mul2(NUX, MZ[p]);
+                        const f32x2 pz = fma2(UX, MY[p], mul2(NUY, MX[p]));
+                        const f32x2 qx = mul2(UY, pz);
+                        const f32x2 qy = mul2(NUX, pz);
+                        const f32x2 qz = fma2(UX, py, mul2(NUY, px));
+                        const f32x2 nx = fma2(C2, fma2(CH, px, qx), MX[p]);
+                        const f32x2 ny = fma2(C2, fma2(CH, py, qy), MY[p]);
+                        const f32x2 nz = fma2(C2, fma2(CH, pz, qz), MZ[p]);
+                        MX[p] = fma2(E2, nx, nx);
+                        MY[p] = fma2(E2, ny, ny);
+                        MZ[p] = fma2(E1, sub2(nz, M0[p]), nz);
+                    }
+                } else if (type == REC_PREC || type == REC_ADC) {
+                    const bool prec = type == REC_PREC;
+                    const float th = R.a[6];
+                    const bool uz = ((R.count >> kTermShift) & A.used) & 4;
+                    const f32x2 E2 = bcast2(exp2f(-th * r2));
+                    f32x2 ER[kZNP], EI[kZNP];
+                    if (uz) {
+                        const f32x2 KH = bcast2(R.a[4]), KL = bcast2(R.a[5]);
+#pragma unroll
+                        for (int p = 0; p < kZNP; ++p) {
+                            const f32x2 F = frac_product2(ZH[p], ZL[p], KH, KL);
+                            float f0, f1;
+                            unpk(F, f0, f1);
+                            float s0, c0, s1, c1;
+                            __sincosf(-6.28318530717958647692f * (f0 - rintf(f0)), &s0, &c0);
+                            __sincosf(-6.28318530717958647692f * (f1 - rintf(f1)), &s1, &c1);
+                            const f32x2 SN = pk(s0, s1), CS = pk(c0, c1);
+                            ER[p] = mul2(E2, fma2(MX[p], CS, neg2(mul2(MY[p], SN))));
+                            EI[p] = mul2(E2, fma2(MX[p], SN, mul2(MY[p], CS)));
+                        }
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < kZNP; ++p) {
+                            ER[p] = mul2(E2, MX[p]);
+                            EI[p] = mul2(E2, MY[p]);
+                        }
+                    }
+                    if (prec) {
+                        const f32x2 E1 = bcast2(exp2f(-th * r1));
+#pragma unroll
+                        for (int p = 0; p < kZNP; ++p) {
+                            MX[p] = ER[p];
+                            MY[p] = EI[p];
+                            MZ[p] = fma2(sub2(MZ[p], M0[p]), E1, M0[p]);
+                        }
+                    } else {
+                        const int64_t k0 = R.k0;
+                        if (k0 < 0 || k0 >= A.n_adc) {
+                            if (tid == 0) atomicOr(A.status, kStatusBadAdc);
+                            continue;
+                        }
+                        f32x2 sr2 = ER[0], si2 = EI[0];
+#pragma unroll
+                        for (int p = 1; p < kZNP; ++p) {
+                            sr2 = add2(sr2, ER[p]);
+                            si2 = add2(si2, EI[p]);
+                        }
+                        float a0, a1, c0, c1;
+                        unpk(sr2, a0, a1);
+                        unpk(si2, c0, c1);
+                        float sr = a0 + a1, si = c0 + c1;
+#pragma unroll
+                        for (int o = 8; o > 0; o >>= 1) {  // within the half-warp
+                            sr += __shfl_xor_sync(kFull, sr, o);
+                            si += __shfl_xor_sync(kFull, si, o);
+                        }
+                        if (hl == 0 && row) row[k0] = make_float2(sr, si);
+                    }
+                }
+            }
+            __syncthreads();  // everyone is done with tile buffer b
+            if (tid == 0 && t + 2 < n_tiles) {
+                fence_proxy_async_smem();
+                issue_tile(s_rec, bar, grec, A.n_rec, t + 2, g + 2);
+            }
+        }
+        g0 += static_cast<uint64_t>(n_tiles);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // K4: serving kernel, persistent. Batches come from a table that mixes the
 // simulations admitted by the server: batch = a contiguous spin range of one
 // request's phantom, walked through a chunk of that request's records
@@ -2131,21 +2349,6 @@ __device__ __forceinline__ void split_half2(float a, float b, uint32_t& hi, uint
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// Packed helpers of the operand generation (two spins per f32x2)
-__device__ __forceinline__ f32x2 bcast2(float v) { return pk(v, v); }
-// v - rint(v) for both halves (exact)
-__device__ __forceinline__ f32x2 frac2(f32x2 v) {
-    float a, b;
-    unpk(v, a, b);
-    return sub2(v, pk(rintf(a), rintf(b)));
-}
-// frac_product for two spins (a) and one factor (b, both halves equal):
-// the same operations as the scalar form, lane by lane
-__device__ __forceinline__ f32x2 frac_product2(f32x2 ah, f32x2 al, f32x2 bh, f32x2 bl) {
-    const f32x2 p = mul2(ah, bh);
-    const f32x2 e = fma2(ah, bh, neg2(p));
-    return add2(frac2(p), fma2(ah, bl, fma2(al, bh, e)));
-}
 // 2^x (PTX ex2.approx, subnormal results flushed to zero: the decays here
 // are factors in (0, 1] next to unit-scale values)
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -2853,6 +3056,25 @@ int launch_batches(const BatchArgs& a, int grid, int block, void* stream) {
     if (block <= 0 || block > kMaxBlock || block % 32 != 0 || grid <= 0) return cudaErrorInvalidValue;
     bloch_batches_kernel<4><<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(a);
     return cudaGetLastError();
+}
+
+int launch_items_z(const ItemArgs& a, int grid, int block, int tile, void* stream) {
+    if (block <= 0 || block > kMaxBlock || block % 32 != 0 || grid <= 0) return cudaErrorInvalidValue;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (tile) {
+        case 128: bloch_items_z_kernel<128><<<grid, block, 0, st>>>(a); break;
+        case 256: bloch_items_z_kernel<256><<<grid, block, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int items_z_ctas_per_sm(int block, int tile) {
+    int n = 0;
+    const cudaError_t e =
+        tile == 256 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_items_z_kernel<256>, block, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_items_z_kernel<128>, block, 0);
+    return e == cudaSuccess ? n : -1;
 }
 
 int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, int tile, void* stream) {

@@ -141,6 +141,9 @@ struct koma_sequence {
     int32_t n_rf_maps = 0;
     koma::Rec32* r32c = nullptr;
     int64_t n_rec_c = 0;
+    // every RF step has Gz = 0 and every ADC record one sample: with a
+    // phantom of isochromats along z only, the dictionary kernel K3z applies
+    bool z_dict = false;
 };
 
 namespace {
@@ -1342,6 +1345,17 @@ namespace {
 // and upload the FP64 and the motion record streams (koma_sequence_upload
 // builds every stream; callers that know the precision, and that the
 // phantom is static, build the FP32 stream only).
+// The record stream's side of K3z's condition: no RF step has a z gradient
+// (its rotation is the same for spins that differ only in z) and no ADC
+// record holds more than one sample.
+bool z_dictionary_stream(const std::vector<koma::Rec32>& r32) {
+    for (const koma::Rec32& R : r32) {
+        if (R.type == koma::REC_RF && (R.a[2] != 0.f || (R.count > 0 && R.a[10] != 0.f))) return false;
+        if (R.type == koma::REC_ADC && (R.count & koma::kCountMask) > 1) return false;
+    }
+    return true;
+}
+
 koma_status sequence_upload_impl(koma_ctx* ctx, int64_t n_steps, const double* dt, const double* gx,
                                  const double* gy, const double* gz, const double* b1_re, const double* b1_im,
                                  const uint8_t* adc, bool need64, bool needM, koma_sequence** out) {
@@ -1360,6 +1374,7 @@ koma_status sequence_upload_impl(koma_ctx* ctx, int64_t n_steps, const double* d
     if (!seq) return fail(ctx, KOMA_E_NOMEM, "sequence_upload: host allocation");
     seq->ctx = ctx;
     seq->info = info;
+    seq->z_dict = z_dictionary_stream(rb.r32);
     MmaPlan mp;
     plan_mma(rb.r32, info.n_adc, mp);
     seq->info.n_mma_groups = static_cast<int64_t>(mp.groups.size());
@@ -1543,6 +1558,14 @@ bool use_items_kernel(const koma_phantom* ph) {
     return ph->n_groups > 1 && ph->n <= 512 * ph->n_groups;
 }
 
+// K3z's condition: spins that differ only in z (no x, y or off-resonance
+// anywhere), a single T1 and T2 per group, and a stream without z gradients
+// under RF or multi-sample ADC records.
+bool z_dict_ok(const koma_phantom* ph, const koma_sequence* seq) {
+    return ph->uni_relax && !ph->moving() && ph->max_abs[0] == 0 && ph->max_abs[1] == 0 && ph->max_abs[3] == 0 &&
+           seq->z_dict;
+}
+
 koma_status grow_scratch(koma_ctx* ctx, size_t need, cudaStream_t st) {
     if (need <= ctx->scratch_bytes) return KOMA_OK;
     // the stream may still use the old buffer
@@ -1560,11 +1583,15 @@ koma_status grow_scratch(koma_ctx* ctx, size_t need, cudaStream_t st) {
 // Grouped kernel (K3) + per-group reduction (K2).
 koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence* seq, double* sig_dev,
                            cudaStream_t st, int S, int block, int tile) {
-    koma_status rc = ensure_items(ctx, ph, S);
+    // S == 8: K3z (items of 128 spins as for S = 4, two per warp)
+    const bool zk = S == 8;
+    if (zk && !z_dict_ok(ph, seq)) return fail(ctx, KOMA_E_INTERNAL, "simulate: K3z on an ineligible pair");
+    koma_status rc = ensure_items(ctx, ph, zk ? 4 : S);
     if (rc != KOMA_OK) return rc;
     const int64_t n_adc = seq->info.n_adc;
-    const int per_sm = std::max(1, koma::items_ctas_per_sm(S, block, tile));
-    const int64_t batches = (ph->n_items + block / 32 - 1) / (block / 32);
+    const int per_sm = std::max(1, zk ? koma::items_z_ctas_per_sm(block, tile) : koma::items_ctas_per_sm(S, block, tile));
+    const int64_t items_per_batch = (zk ? 2 : 1) * (block / 32);
+    const int64_t batches = (ph->n_items + items_per_batch - 1) / items_per_batch;
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(batches,
                                                          static_cast<int64_t>(ctx->sm_count) * per_sm)));
     rc = grow_scratch(ctx, static_cast<size_t>(ph->n_items) * static_cast<size_t>(n_adc) * 2 * sizeof(float), st);
@@ -1587,7 +1614,7 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     cudaError_t ce = cudaMemsetAsync(A.counter, 0, sizeof(int), st);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "simulate: counter reset");
     if (ctx->timing) cudaEventRecord(ctx->ev[0], st);
-    int e = koma::launch_items(A, grid, block, S, tile, st);
+    int e = zk ? koma::launch_items_z(A, grid, block, tile, st) : koma::launch_items(A, grid, block, S, tile, st);
     if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: grouped kernel launch");
     if (ctx->timing) {
         cudaEventRecord(ctx->ev[1], st);
@@ -1610,7 +1637,7 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     ctx->last.grid = grid;
     ctx->last.block = block;
     ctx->last.spins_per_thread = S;
-    ctx->last.spins_per_cta = 32LL * S * (block / 32);
+    ctx->last.spins_per_cta = 32LL * S * (block / 32);  // K3z: 2 items of 128 per warp, as 32 x 8
     ctx->last.n_records = seq->info.n_records;
     ctx->last.partial_bytes = static_cast<int64_t>(ph->n_items * n_adc * 8);
     ctx->last.split = 1;
@@ -1623,7 +1650,7 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
 // groups, records and ADC samples.
 uint64_t tune_key(const koma_phantom* ph, const koma_sequence* seq, bool items) {
     auto lg = [](int64_t v) { return static_cast<uint64_t>(v > 0 ? 64 - __builtin_clzll(static_cast<uint64_t>(v)) : 0); };
-    const uint64_t family = items ? 1 : (ph->moving() ? 2 : 0);
+    const uint64_t family = items ? (z_dict_ok(ph, seq) ? 3 : 1) : (ph->moving() ? 2 : 0);
     return family | lg(ph->n) << 2 | lg(ph->n_groups) << 10 | lg(seq->info.n_records) << 18 |
            lg(seq->info.n_adc) << 26 | lg(seq->info.n_rf) << 34;
 }
@@ -1701,9 +1728,11 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
     const bool moving = ph->moving();
     if (!fp64 && !moving && use_items_kernel(ph)) {
         const bool tuned = ph->tuned_seq == seq && ph->tuned_n_rec == seq->info.n_records;
-        // untuned default: the tuner's usual pick for dictionaries of small groups
-        int S = tuned ? ph->tuned_s : 2, block = tuned ? ph->tuned_block : 128;
-        int tile = tuned && ph->tuned_tile > 0 ? ph->tuned_tile : 64;
+        // untuned default: the tuner's usual pick for dictionaries of small
+        // groups, K3z where it applies
+        const bool zk = z_dict_ok(ph, seq);
+        int S = tuned ? ph->tuned_s : (zk ? 8 : 2), block = tuned ? ph->tuned_block : (zk ? 256 : 128);
+        int tile = tuned && ph->tuned_tile > 0 ? ph->tuned_tile : (zk ? 128 : 64);
         if (!tuned) {
             auto it = ctx->tune_cache.find(tune_key(ph, seq, true));
             if (it != ctx->tune_cache.end()) {
@@ -2037,6 +2066,9 @@ extern "C" koma_status koma_tune(koma_ctx* ctx, const koma_phantom* ph_c, const 
         for (int s_ : {2, 4})
             for (int b_ : {128, 256})
                 for (int t_ : {64, 128, 256}) cands.push_back({s_, b_, t_});
+        if (z_dict_ok(ph, seq))
+            for (int b_ : {128, 256})
+                for (int t_ : {128, 256}) cands.push_back({8, b_, t_});
     } else {
         cands = {{2, 0, 0}, {4, 0, 0}};
     }
