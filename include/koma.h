@@ -86,6 +86,11 @@ typedef struct {
                                  used by this call)                        */
     int32_t tile_records;     /* step records per shared-memory tile of the
                                  walking kernel                            */
+    int32_t phase_mode;       /* how the walking kernel took the phase
+                                 2 pi K.x: 0 the hi/lo fractional product;
+                                 1 one FP32 product (the dictionary kernel
+                                 for isochromats along z, when |z Kz| <= 1
+                                 turn for every spin and record)            */
 } koma_launch_info;
 
 /* Counts of the uploaded sequence by step class (hot-path cost model). */

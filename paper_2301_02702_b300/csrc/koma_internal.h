@@ -398,11 +398,14 @@ int launch_bounded_wait_check(int* status, unsigned long long limit_ns, void* st
 int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, int tile, void* stream);
 int items_ctas_per_sm(int spins_per_thread, int block, int tile);
 // K3z, the grouped kernel for dictionaries of isochromats along z (spins
-// differ only in z, one T1/T2 per group, RF without gradient, one sample
+// differ only in z, one T1/T2 per group, RF without z gradient, one sample
 // per ADC record): items of 128 spins (as K3 with 4 spins per thread), two
-// per warp, 8 spins per thread; `tile` 128 or 256 records.
-int launch_items_z(const ItemArgs& a, int grid, int block, int tile, void* stream);
-int items_z_ctas_per_sm(int block, int tile);
+// per warp, 8 spins per thread; `tile` 128 or 256 records. `a.rec` is the
+// K3z copy of the stream (RF records with the rotation in a[0..3], PREC/ADC
+// records with -2 pi Kz in a[8]); `small_phase`: |z Kz| <= 1 turn for every
+// spin and record, the phase as one FP32 product (then block <= 128).
+int launch_items_z(const ItemArgs& a, int grid, int block, int tile, bool small_phase, void* stream);
+int items_z_ctas_per_sm(int block, int tile, bool small_phase);
 // Serving kernel (4 spins per thread, `block` threads: a batch is 128 x
 // block/32 spins).
 int launch_batches(const BatchArgs& a, int grid, int block, void* stream);

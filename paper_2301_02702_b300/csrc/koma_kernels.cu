@@ -1370,22 +1370,27 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_kernel(const __grid_
 //
 // When the spins of a phantom differ only in z (x = y = 0 and no off-resonance
 // anywhere), every group has a single T1 and T2, the sequence's RF steps carry
-// no gradient (so every RF step rotates all spins alike) and every ADC record
-// holds one sample, a spin needs no more state than M, its z (hi/lo) and M0,
-// and the record work that is the same for all spins (the pulse's rotation,
-// the relaxation factors, the decode) is shared by 8 spins per thread. The
-// items are those of K3 with 128 spins (16 lanes x 8); a warp takes two of
-// them, one per half-warp, so an entry fills as many lanes as under K3 with 4
-// spins per thread, and a sample's sum is a 16-lane butterfly per half. The
-// per-step arithmetic is that of K1/K3: the uniform RF step of Spins::rf_uniform
-// (series for the small angles), the hi/lo phase and hardware sine of
-// Spins::exact, the same relaxation factors.
+// no z gradient (so every RF step rotates all spins alike) and every ADC record
+// holds one sample, a spin needs no more state than M, its z and M0, and the
+// record work that is the same for all spins is shared by 8 spins per thread.
+// The kernel walks its own copy of the record stream, prepared on the host:
+// an RF record carries the step's rotation (ux, uy, ch, c2 in a[0..3], the
+// quaternion of the uniform RF path of K1/K3, evaluated once per record instead
+// of by every thread), a PREC/ADC record -2 pi Kz in a[8]. The items are those
+// of K3 with 128 spins (16 lanes x 8); a warp takes two of them, one per
+// half-warp, and a sample's sum is a 16-lane butterfly per half.
+// SMALLPH (the host checked |z Kz| <= 1 turn for every spin and record): the
+// phase angle is z (-2 pi Kz) in one FP32 product, relative error a few ulp of
+// an angle of at most 2 pi; otherwise the hi/lo fractional product of K1/K3.
+// The rotation, relaxation and sine are applied as in K1/K3.
 // ---------------------------------------------------------------------------
 constexpr int kZS = 8;             // spins per thread
 constexpr int kZNP = kZS / 2;      // packed pairs
 
-template <int T>
-__global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_z_kernel(const __grid_constant__ ItemArgs A) {
+constexpr int kZSmallBlock = 128;  // the SMALLPH instances: 5 CTAs of 128 threads per SM (<= 96 registers)
+
+template <int T, bool SMALLPH>
+__global__ void __launch_bounds__(SMALLPH ? kZSmallBlock : kMaxBlock, SMALLPH ? 5 : 2) bloch_items_z_kernel(const __grid_constant__ ItemArgs A) {
     __shared__ __align__(128) Rec32 s_rec[2][T];
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ int64_t s_batch;
@@ -1425,7 +1430,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_z_kernel(const __gri
             const int64_t j0 = ib + hl + 16 * (2 * p), j1 = j0 + 16;
             const bool v0 = j0 < ie, v1 = j1 < ie;
             ZH[p] = pk(v0 ? P[P32_ZH * np + j0] : 0.f, v1 ? P[P32_ZH * np + j1] : 0.f);
-            ZL[p] = pk(v0 ? P[P32_ZL * np + j0] : 0.f, v1 ? P[P32_ZL * np + j1] : 0.f);
+            if (!SMALLPH) ZL[p] = pk(v0 ? P[P32_ZL * np + j0] : 0.f, v1 ? P[P32_ZL * np + j1] : 0.f);
             M0[p] = pk(v0 ? P[P32_M0 * np + j0] : 0.f, v1 ? P[P32_M0 * np + j1] : 0.f);
             MX[p] = pk(0.f, 0.f);
             MY[p] = pk(0.f, 0.f);
@@ -1433,8 +1438,13 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_z_kernel(const __gri
         }
         // the item's group shares T1 and T2
         const float r1 = ib < ie ? P[P32_R1 * np + ib] : 0.f, r2 = ib < ie ? P[P32_R2 * np + ib] : 0.f;
-        float em1 = 0.f, em2 = 0.f, dt_cached = -1.f;
-        bool small = true;
+        // relaxation factors minus one (Q1, Q2) for the last RF dt; the spins' phase
+        // rotators for the last phase record's Kz (hi, lo): a train of
+        // identical lobes (FISP) evaluates them once
+        f32x2 Q1 = 0, Q2 = 0;
+        float dt_cached = -1.f, kh_cached = 0.f, kl_cached = 0.f;
+        bool rot_ok = false;
+        f32x2 CS[kZNP], SN[kZNP];
         if (tid == 0) {
             for (int64_t t = 0; t < 2 && t < n_tiles; ++t) issue_tile(s_rec, bar, grec, A.n_rec, t, g0 + t);
         }
@@ -1455,48 +1465,23 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_z_kernel(const __gri
                 const Rec32& R = s_rec[b][r];
                 const int type = R.type;
                 if (type == REC_RF) {
-                    const float bx = R.a[3], by = R.a[4], b2 = R.a[5], dt = R.a[6];
-                    if (R.count > 0) small = R.a[7] <= 0.754f;  // the run's largest half angle
+                    const float dt = R.a[9];
                     if (dt != dt_cached) {
-                        em1 = expm1_f32(-dt * r1 * 0.693147180559945309f);
-                        em2 = expm1_f32(-dt * r2 * 0.693147180559945309f);
+                        Q1 = bcast2(expm1_f32(-dt * r1 * 0.693147180559945309f));
+                        Q2 = bcast2(expm1_f32(-dt * r2 * 0.693147180559945309f));
                         dt_cached = dt;
                     }
-                    float ch, f;
-                    if (small) {
-                        float q = fmaf(b2, -2.75573192239858907e-6f, 1.98412698412698413e-4f);
-                        q = fmaf(q, b2, -8.33333333333333333e-3f);
-                        q = fmaf(q, b2, 1.66666666666666667e-1f);
-                        f = fmaf(q, b2, -1.0f);
-                        float c = fmaf(b2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);
-                        c = fmaf(c, b2, -1.38888888888888889e-3f);
-                        c = fmaf(c, b2, 4.16666666666666667e-2f);
-                        c = fmaf(c, b2, -0.5f);
-                        ch = fmaf(c, b2, 1.0f);
-                    } else {
-                        const float rs = rsqrtf(b2);
-                        float sh;
-                        sincospi_f32(b2 * rs * 0.318309886183790671538f, &sh, &ch);
-                        f = -sh * rs;
-                    }
-                    const float ux = bx * f, uy = by * f;
-                    const float c2 = fmaf(-2.f, fmaf(ch, ch, fmaf(ux, ux, uy * uy)), 4.f);
-                    const f32x2 UX = bcast2(ux), UY = bcast2(uy), NUX = bcast2(-ux), NUY = bcast2(-uy);
-                    const f32x2 CH = bcast2(ch), C2 = bcast2(c2), E1 = bcast2(em1), E2 = bcast2(em2);
+                    const f32x2 A00 = bcast2(R.a[0]), A01 = bcast2(R.a[1]), A02 = bcast2(R.a[2]);
+                    const f32x2 A10 = bcast2(R.a[3]), A11 = bcast2(R.a[4]), A12 = bcast2(R.a[5]);
+                    const f32x2 A20 = bcast2(R.a[6]), A21 = bcast2(R.a[7]), A22 = bcast2(R.a[8]);
 #pragma unroll
                     for (int p = 0; p < kZNP; ++p) {
-                        const f32x2 px = mul2(UY, MZ[p]);
-                        const f32x2 py = mul2(NUX, MZ[p]);
-                        const f32x2 pz = fma2(UX, MY[p], mul2(NUY, MX[p]));
-                        const f32x2 qx = mul2(UY, pz);
-                        const f32x2 qy = mul2(NUX, pz);
-                        const f32x2 qz = fma2(UX, py, mul2(NUY, px));
-                        const f32x2 nx = fma2(C2, fma2(CH, px, qx), MX[p]);
-                        const f32x2 ny = fma2(C2, fma2(CH, py, qy), MY[p]);
-                        const f32x2 nz = fma2(C2, fma2(CH, pz, qz), MZ[p]);
-                        MX[p] = fma2(E2, nx, nx);
-                        MY[p] = fma2(E2, ny, ny);
-                        MZ[p] = fma2(E1, sub2(nz, M0[p]), nz);
+                        const f32x2 nx = fma2(A02, MZ[p], fma2(A01, MY[p], mul2(A00, MX[p])));
+                        const f32x2 ny = fma2(A12, MZ[p], fma2(A11, MY[p], mul2(A10, MX[p])));
+                        const f32x2 nz = fma2(A22, MZ[p], fma2(A21, MY[p], mul2(A20, MX[p])));
+                        MX[p] = fma2(Q2, nx, nx);
+                        MY[p] = fma2(Q2, ny, ny);
+                        MZ[p] = fma2(Q1, sub2(nz, M0[p]), nz);
                     }
                 } else if (type == REC_PREC || type == REC_ADC) {
                     const bool prec = type == REC_PREC;
@@ -1505,18 +1490,35 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_z_kernel(const __gri
                     const f32x2 E2 = bcast2(exp2f(-th * r2));
                     f32x2 ER[kZNP], EI[kZNP];
                     if (uz) {
-                        const f32x2 KH = bcast2(R.a[4]), KL = bcast2(R.a[5]);
+                        const float kh = R.a[4], kl = R.a[5];
+                        if (!rot_ok || kh != kh_cached || kl != kl_cached) {
+                            const f32x2 KH = bcast2(kh), KL = bcast2(kl), W = bcast2(R.a[8]);
+#pragma unroll
+                            for (int p = 0; p < kZNP; ++p) {
+                                float s0, c0, s1, c1;
+                                if (SMALLPH) {
+                                    float t0, t1;
+                                    unpk(mul2(ZH[p], W), t0, t1);
+                                    __sincosf(t0, &s0, &c0);
+                                    __sincosf(t1, &s1, &c1);
+                                } else {
+                                    const f32x2 F = frac_product2(ZH[p], ZL[p], KH, KL);
+                                    float f0, f1;
+                                    unpk(F, f0, f1);
+                                    __sincosf(-6.28318530717958647692f * (f0 - rintf(f0)), &s0, &c0);
+                                    __sincosf(-6.28318530717958647692f * (f1 - rintf(f1)), &s1, &c1);
+                                }
+                                SN[p] = pk(s0, s1);
+                                CS[p] = pk(c0, c1);
+                            }
+                            kh_cached = kh;
+                            kl_cached = kl;
+                            rot_ok = true;
+                        }
 #pragma unroll
                         for (int p = 0; p < kZNP; ++p) {
-                            const f32x2 F = frac_product2(ZH[p], ZL[p], KH, KL);
-                            float f0, f1;
-                            unpk(F, f0, f1);
-                            float s0, c0, s1, c1;
-                            __sincosf(-6.28318530717958647692f * (f0 - rintf(f0)), &s0, &c0);
-                            __sincosf(-6.28318530717958647692f * (f1 - rintf(f1)), &s1, &c1);
-                            const f32x2 SN = pk(s0, s1), CS = pk(c0, c1);
-                            ER[p] = mul2(E2, fma2(MX[p], CS, neg2(mul2(MY[p], SN))));
-                            EI[p] = mul2(E2, fma2(MX[p], SN, mul2(MY[p], CS)));
+                            ER[p] = mul2(E2, fma2(MX[p], CS[p], neg2(mul2(MY[p], SN[p]))));
+                            EI[p] = mul2(E2, fma2(MX[p], SN[p], mul2(MY[p], CS[p])));
                         }
                     } else {
 #pragma unroll
@@ -1535,7 +1537,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_z_kernel(const __gri
                         }
                     } else {
                         const int64_t k0 = R.k0;
-                        if (k0 < 0 || k0 >= A.n_adc) {
+                        if (k0 < 0 || k0 >= A.n_adc || (R.count & kCountMask) > 1) {
                             if (tid == 0) atomicOr(A.status, kStatusBadAdc);
                             continue;
                         }
@@ -3058,22 +3060,27 @@ int launch_batches(const BatchArgs& a, int grid, int block, void* stream) {
     return cudaGetLastError();
 }
 
-int launch_items_z(const ItemArgs& a, int grid, int block, int tile, void* stream) {
-    if (block <= 0 || block > kMaxBlock || block % 32 != 0 || grid <= 0) return cudaErrorInvalidValue;
+int launch_items_z(const ItemArgs& a, int grid, int block, int tile, bool small_phase, void* stream) {
+    if (block <= 0 || block > (small_phase ? kZSmallBlock : kMaxBlock) || block % 32 != 0 || grid <= 0)
+        return cudaErrorInvalidValue;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    switch (tile) {
-        case 128: bloch_items_z_kernel<128><<<grid, block, 0, st>>>(a); break;
-        case 256: bloch_items_z_kernel<256><<<grid, block, 0, st>>>(a); break;
-        default: return cudaErrorInvalidValue;
-    }
+    if (tile == 128 && small_phase) bloch_items_z_kernel<128, true><<<grid, block, 0, st>>>(a);
+    else if (tile == 128) bloch_items_z_kernel<128, false><<<grid, block, 0, st>>>(a);
+    else if (tile == 256 && small_phase) bloch_items_z_kernel<256, true><<<grid, block, 0, st>>>(a);
+    else if (tile == 256) bloch_items_z_kernel<256, false><<<grid, block, 0, st>>>(a);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-int items_z_ctas_per_sm(int block, int tile) {
+int items_z_ctas_per_sm(int block, int tile, bool small_phase) {
     int n = 0;
-    const cudaError_t e =
-        tile == 256 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_items_z_kernel<256>, block, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_items_z_kernel<128>, block, 0);
+    cudaError_t e;
+    if (tile == 256)
+        e = small_phase ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_items_z_kernel<256, true>, block, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_items_z_kernel<256, false>, block, 0);
+    else
+        e = small_phase ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_items_z_kernel<128, true>, block, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bloch_items_z_kernel<128, false>, block, 0);
     return e == cudaSuccess ? n : -1;
 }
 

@@ -143,7 +143,12 @@ struct koma_sequence {
     int64_t n_rec_c = 0;
     // every RF step has Gz = 0 and every ADC record one sample: with a
     // phantom of isochromats along z only, the dictionary kernel K3z applies
+    // and walks its own copy of the stream (r32z, same device block), whose
+    // RF records carry the pulse's rotation and whose PREC/ADC records carry
+    // -2 pi Kz as one FP32 value; z_kmax = max |Kz| (turns/m) over them
     bool z_dict = false;
+    koma::Rec32* r32z = nullptr;
+    double z_kmax = 0.0;
 };
 
 namespace {
@@ -1356,6 +1361,45 @@ bool z_dictionary_stream(const std::vector<koma::Rec32>& r32) {
     return true;
 }
 
+// K3z's record stream: a copy of the FP32 stream in which
+// * an RF record's a[0..8] hold the step's rotation as a 3x3 matrix (row
+//   major) and a[9] its dt. The rotation is that of the uniform RF path:
+//   the quaternion (ch, ux, uy, 0) = (cos h, -sin h / h (bx, by), 0) of half
+//   angle h = sqrt(b2) applied as v + c2 (ch u x v + u x (u x v)) with the
+//   first-order renormalisation c2 = 4 - 2 |q|^2, i.e. the matrix
+//   I + c2 (ch [u]x + [u]x^2), evaluated in FP64 from the record's FP32
+//   fields and rounded once per entry;
+// * a PREC/ADC record's a[8] holds -2 pi Kz (Kz = hi + lo, FP64, rounded once),
+//   the phase per metre of z when the phantom's extent keeps |z Kz| small.
+// Everything else is copied. Returns max |Kz| over the records with a z term.
+double build_z_stream(const std::vector<koma::Rec32>& r32, std::vector<koma::Rec32>& out) {
+    out = r32;
+    double kmax = 0.0;
+    for (koma::Rec32& R : out) {
+        if (R.type == koma::REC_RF) {
+            const double bx = R.a[3], by = R.a[4], b2 = R.a[5], dt = R.a[6];
+            double ch = 1.0, f = -1.0;
+            if (b2 > 0.0) {
+                const double h = std::sqrt(b2);
+                ch = std::cos(h);
+                f = -std::sin(h) / h;
+            }
+            const double ux = bx * f, uy = by * f, s = ux * ux + uy * uy;
+            const double c2 = 4.0 - 2.0 * (ch * ch + s);
+            const double m[9] = {1.0 - c2 * uy * uy, c2 * ux * uy,       c2 * ch * uy,
+                                 c2 * ux * uy,       1.0 - c2 * ux * ux, -c2 * ch * ux,
+                                 -c2 * ch * uy,      c2 * ch * ux,       1.0 - c2 * s};
+            for (int k = 0; k < 9; ++k) R.a[k] = static_cast<float>(m[k]);
+            R.a[9] = static_cast<float>(dt);
+        } else if (R.type == koma::REC_PREC || R.type == koma::REC_ADC) {
+            const double kz = static_cast<double>(R.a[4]) + static_cast<double>(R.a[5]);
+            R.a[8] = static_cast<float>(-2.0 * kPi * kz);
+            if ((R.count >> koma::kTermShift) & 4) kmax = std::max(kmax, std::fabs(kz));
+        }
+    }
+    return kmax;
+}
+
 koma_status sequence_upload_impl(koma_ctx* ctx, int64_t n_steps, const double* dt, const double* gx,
                                  const double* gy, const double* gz, const double* b1_re, const double* b1_im,
                                  const uint8_t* adc, bool need64, bool needM, koma_sequence** out) {
@@ -1375,6 +1419,8 @@ koma_status sequence_upload_impl(koma_ctx* ctx, int64_t n_steps, const double* d
     seq->ctx = ctx;
     seq->info = info;
     seq->z_dict = z_dictionary_stream(rb.r32);
+    std::vector<koma::Rec32> rz;
+    if (seq->z_dict) seq->z_kmax = build_z_stream(rb.r32, rz);
     MmaPlan mp;
     plan_mma(rb.r32, info.n_adc, mp);
     seq->info.n_mma_groups = static_cast<int64_t>(mp.groups.size());
@@ -1393,8 +1439,9 @@ koma_status sequence_upload_impl(koma_ctx* ctx, int64_t n_steps, const double* d
     const size_t b32 = rb.r32.size() * sizeof(koma::Rec32), b64 = rb.r64.size() * sizeof(koma::Rec64),
                  bm = rb.rm.size() * sizeof(koma::RecM), bg = mp.groups.size() * sizeof(koma::MmaGroup),
                  br = mp.runs.size() * sizeof(koma::MmaRun), bf = up16(mp.from.size()),
-                 bp = fp.pulses.size() * sizeof(koma::RfMapPulse), bc = n_rc * sizeof(koma::Rec32);
-    const size_t total = b32 + b64 + bm + bg + br + bf + bp + bc;
+                 bp = fp.pulses.size() * sizeof(koma::RfMapPulse), bc = n_rc * sizeof(koma::Rec32),
+                 bz = rz.size() * sizeof(koma::Rec32);
+    const size_t total = b32 + b64 + bm + bg + br + bf + bp + bc + bz;
     koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r32), total, "sequence_upload");
     if (st == KOMA_OK && total > ctx->h_stage_bytes) {
         if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
@@ -1441,6 +1488,11 @@ koma_status sequence_upload_impl(koma_ctx* ctx, int64_t n_steps, const double* d
             seq->n_rec_c = static_cast<int64_t>(n_rc);
             std::memcpy(h + off, fp.pulses.data(), bp);
             koma::compact_records32_into(rb.r32, reinterpret_cast<koma::Rec32*>(h + off + bp));
+        }
+        off += bp + bc;
+        if (bz) {
+            seq->r32z = reinterpret_cast<koma::Rec32*>(base + off);
+            std::memcpy(h + off, rz.data(), bz);
         }
         cudaError_t e = h2d_sync(ctx, seq->r32, h, total);
         if (e != cudaSuccess) st = cuda_fail(ctx, e, "sequence_upload: copy");
@@ -1563,7 +1615,13 @@ bool use_items_kernel(const koma_phantom* ph) {
 // under RF or multi-sample ADC records.
 bool z_dict_ok(const koma_phantom* ph, const koma_sequence* seq) {
     return ph->uni_relax && !ph->moving() && ph->max_abs[0] == 0 && ph->max_abs[1] == 0 && ph->max_abs[3] == 0 &&
-           seq->z_dict;
+           seq->z_dict && seq->r32z;
+}
+
+// K3z takes the phase as one FP32 product when |z Kz| <= 1 turn for every
+// spin and record (its launches then use 128-thread CTAs).
+bool z_small_phase(const koma_phantom* ph, const koma_sequence* seq) {
+    return ph->max_abs[2] * seq->z_kmax <= 1.0;
 }
 
 koma_status grow_scratch(koma_ctx* ctx, size_t need, cudaStream_t st) {
@@ -1589,7 +1647,10 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     koma_status rc = ensure_items(ctx, ph, zk ? 4 : S);
     if (rc != KOMA_OK) return rc;
     const int64_t n_adc = seq->info.n_adc;
-    const int per_sm = std::max(1, zk ? koma::items_z_ctas_per_sm(block, tile) : koma::items_ctas_per_sm(S, block, tile));
+    const bool small_phase = zk && z_small_phase(ph, seq);
+    if (small_phase) block = std::min(block, 128);
+    const int per_sm = std::max(1, zk ? koma::items_z_ctas_per_sm(block, tile, small_phase)
+                                      : koma::items_ctas_per_sm(S, block, tile));
     const int64_t items_per_batch = (zk ? 2 : 1) * (block / 32);
     const int64_t batches = (ph->n_items + items_per_batch - 1) / items_per_batch;
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(batches,
@@ -1604,7 +1665,7 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     A.order = ph->d_order;
     A.n_items = ph->n_items;
     A.counter = ctx->d_status + 1;
-    A.rec = seq->r32;
+    A.rec = zk ? seq->r32z : seq->r32;
     A.n_rec = seq->info.n_records;
     A.partial = ctx->scratch;
     A.n_adc = n_adc;
@@ -1614,7 +1675,8 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     cudaError_t ce = cudaMemsetAsync(A.counter, 0, sizeof(int), st);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "simulate: counter reset");
     if (ctx->timing) cudaEventRecord(ctx->ev[0], st);
-    int e = zk ? koma::launch_items_z(A, grid, block, tile, st) : koma::launch_items(A, grid, block, S, tile, st);
+    int e = zk ? koma::launch_items_z(A, grid, block, tile, small_phase, st)
+               : koma::launch_items(A, grid, block, S, tile, st);
     if (e != cudaSuccess) return cuda_fail(ctx, static_cast<cudaError_t>(e), "simulate: grouped kernel launch");
     if (ctx->timing) {
         cudaEventRecord(ctx->ev[1], st);
@@ -1642,17 +1704,19 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     ctx->last.partial_bytes = static_cast<int64_t>(ph->n_items * n_adc * 8);
     ctx->last.split = 1;
     ctx->last.tile_records = tile;
+    ctx->last.phase_mode = small_phase ? 1 : 0;
     return KOMA_OK;
 }
 
 // Shape bucket of a launch for the autotuner cache: the kernel family
-// (grouped items, FP32 Bloch, motion), and the powers of two of the spins,
-// groups, records and ADC samples.
+// (grouped items, K3z with either phase, FP32 Bloch, motion), and the powers
+// of two of the spins, groups, records and ADC samples.
 uint64_t tune_key(const koma_phantom* ph, const koma_sequence* seq, bool items) {
     auto lg = [](int64_t v) { return static_cast<uint64_t>(v > 0 ? 64 - __builtin_clzll(static_cast<uint64_t>(v)) : 0); };
-    const uint64_t family = items ? (z_dict_ok(ph, seq) ? 3 : 1) : (ph->moving() ? 2 : 0);
-    return family | lg(ph->n) << 2 | lg(ph->n_groups) << 10 | lg(seq->info.n_records) << 18 |
-           lg(seq->info.n_adc) << 26 | lg(seq->info.n_rf) << 34;
+    const bool z = items && z_dict_ok(ph, seq);
+    const uint64_t family = items ? (z ? (z_small_phase(ph, seq) ? 4 : 3) : 1) : (ph->moving() ? 2 : 0);
+    return family | lg(ph->n) << 3 | lg(ph->n_groups) << 11 | lg(seq->info.n_records) << 19 |
+           lg(seq->info.n_adc) << 27 | lg(seq->info.n_rf) << 35;
 }
 
 // Largest snapshot buffer (8 bytes per spin and block of matrix-form runs)
@@ -1731,7 +1795,7 @@ extern "C" koma_status koma_simulate(koma_ctx* ctx, const koma_phantom* ph_c, co
         // untuned default: the tuner's usual pick for dictionaries of small
         // groups, K3z where it applies
         const bool zk = z_dict_ok(ph, seq);
-        int S = tuned ? ph->tuned_s : (zk ? 8 : 2), block = tuned ? ph->tuned_block : (zk ? 256 : 128);
+        int S = tuned ? ph->tuned_s : (zk ? 8 : 2), block = tuned ? ph->tuned_block : 128;
         int tile = tuned && ph->tuned_tile > 0 ? ph->tuned_tile : (zk ? 128 : 64);
         if (!tuned) {
             auto it = ctx->tune_cache.find(tune_key(ph, seq, true));
@@ -2068,7 +2132,8 @@ extern "C" koma_status koma_tune(koma_ctx* ctx, const koma_phantom* ph_c, const 
                 for (int t_ : {64, 128, 256}) cands.push_back({s_, b_, t_});
         if (z_dict_ok(ph, seq))
             for (int b_ : {128, 256})
-                for (int t_ : {128, 256}) cands.push_back({8, b_, t_});
+                for (int t_ : {128, 256})
+                    if (b_ == 128 || !z_small_phase(ph, seq)) cands.push_back({8, b_, t_});
     } else {
         cands = {{2, 0, 0}, {4, 0, 0}};
     }

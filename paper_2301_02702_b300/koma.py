@@ -50,7 +50,7 @@ class LaunchInfo(ctypes.Structure):
                 ("spins_per_thread", ctypes.c_int32), ("spins_per_cta", ctypes.c_int64),
                 ("n_records", ctypes.c_int64), ("partial_bytes", ctypes.c_int64),
                 ("bloch_stream", ctypes.c_void_p), ("split", ctypes.c_int32), ("mma_grid", ctypes.c_int32),
-                ("tile_records", ctypes.c_int32)]
+                ("tile_records", ctypes.c_int32), ("phase_mode", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

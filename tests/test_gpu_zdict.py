@@ -3,7 +3,8 @@
 K3z runs when a grouped phantom's spins differ only in z (x = y = 0, no
 off-resonance), every group has one T1 and one T2, no RF step has a z
 gradient and every ADC record holds one sample: a FISP fingerprinting
-dictionary (Section "MR Fingerprinting"-style workloads). These tests check:
+dictionary (the MRF showcase, Section "Magnetic Resonance Fingerprinting"). These
+tests check:
 
 * eligible dictionaries with ragged groups (empty, 1, 127/128/129 spins: a
   K3z item is 128 spins, so groups end inside, at and just past an item),
@@ -65,14 +66,16 @@ def z_dictionary(sizes, seed, voxel=1e-3):
     return Phantom(x=np.zeros(n), y=np.zeros(n), z=z, pd=pd, t1=t1, t2=t2, dw=np.zeros(n), group_offsets=offs)
 
 
-def fisp_train(n_tr, seed, voxel=1e-3, sinc_steps=0, adc_samples=1, rf_gz=0.0):
+def fisp_train(n_tr, seed, voxel=1e-3, sinc_steps=0, adc_samples=1, rf_gz=0.0, lobe_turns=1.0):
     """Inversion, then TRs of a pulse (hard, or a sinc of `sinc_steps` steps,
-    with a random B1 phase), one ADC step at TE, a z lobe that dephases one
-    turn across the voxel, free precession. `adc_samples` > 1 or `rf_gz` != 0
-    break K3z's condition on the stream."""
+    with a random B1 phase), one ADC step at TE, a z lobe that dephases
+    `lobe_turns` turns across the voxel, free precession. `adc_samples` > 1 or
+    `rf_gz` != 0 break K3z's condition on the stream; with the spins inside
+    the voxel |z Kz| <= lobe_turns / 2, so lobe_turns > 2 takes K3z's hi/lo
+    phase."""
     rng = np.random.default_rng(seed)
     rf_dur, te, tg = 100e-6, 3e-3, 200e-6
-    amp = (1.0 / voxel) / (GAMMA_BAR * 2 * tg)
+    amp = (lobe_turns / voxel) / (GAMMA_BAR * 2 * tg)
     b = SequenceBuilder()
     b.steps(1, rf_dur, b1=hard_pulse_b1(np.pi, rf_dur))  # half angle pi/2: the closed form
     b.steps(1, 20e-3)
@@ -106,13 +109,15 @@ def check_groups(got, ref, offs):
 SIZES = [1, 0, 127, 128, 129, 300, 5, 256, 64, 383, 2, 129]
 
 
-@pytest.mark.parametrize("sinc_steps", [0, 24])
-def test_z_dictionary_matches_oracle(sim, sinc_steps):
+@pytest.mark.parametrize("sinc_steps,lobe_turns", [(0, 1.0), (24, 1.0), (0, 6.0), (24, 2.5)])
+def test_z_dictionary_matches_oracle(sim, sinc_steps, lobe_turns):
     ph = z_dictionary(SIZES, seed=3)
-    seq = fisp_train(60 if sinc_steps else 150, seed=4, sinc_steps=sinc_steps)
+    seq = fisp_train(60 if sinc_steps else 150, seed=4, sinc_steps=sinc_steps, lobe_turns=lobe_turns)
     assert seq.n_steps > 512  # several record tiles of the walk
     got, info = run(sim, ph, seq)
     assert info["spins_per_thread"] == 8, info  # K3z
+    # one FP32 product for the phase while |z Kz| <= 1 turn, else hi/lo
+    assert info["phase_mode"] == (1 if lobe_turns <= 2.0 else 0), info
     check_groups(got, oracle.simulate(ph, seq), ph.group_offsets)
     again, _ = run(sim, ph, seq)
     assert np.array_equal(got, again)
@@ -150,7 +155,7 @@ def _broken(kind):
 def test_broken_condition_takes_the_general_grouped_kernel(sim, kind):
     ph, seq = _broken(kind)
     got, info = run(sim, ph, seq)
-    assert info["spins_per_thread"] in (2, 4), (kind, info)
+    assert info["spins_per_thread"] in (2, 4) and info["phase_mode"] == 0, (kind, info)
     check_groups(got, oracle.simulate(ph, seq), ph.group_offsets)
 
 
