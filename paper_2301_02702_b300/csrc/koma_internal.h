@@ -291,6 +291,12 @@ struct ItemArgs {
     float ext[4] = {0, 0, 0, 0};
     int used = 0;
     int uni_relax = 0;                    // every group has one T1 and one T2 (relaxation once per thread)
+    // K3z: units of up to 8 consecutive spins of one group, packed across
+    // groups (a warp takes 32 consecutive units); each (warp, group) segment
+    // is one item, i.e. one partial row
+    const int64_t* unit_begin = nullptr;  // [n_units + 1] first spin of each unit
+    const int32_t* unit_item = nullptr;   // [n_units] item of each unit
+    int64_t n_units = 0;
 };
 
 struct ReduceArgs {
@@ -399,8 +405,8 @@ int launch_items(const ItemArgs& a, int grid, int block, int spins_per_thread, i
 int items_ctas_per_sm(int spins_per_thread, int block, int tile);
 // K3z, the grouped kernel for dictionaries of isochromats along z (spins
 // differ only in z, one T1/T2 per group, RF without z gradient, one sample
-// per ADC record): items of 128 spins (as K3 with 4 spins per thread), two
-// per warp, 8 spins per thread; `tile` 128 or 256 records. `a.rec` is the
+// per ADC record): one unit of up to 8 spins per thread (a.unit_begin,
+// a.unit_item, a.n_units); `tile` 128 or 256 records. `a.rec` is the
 // K3z copy of the stream (RF records with the rotation in a[0..3], PREC/ADC
 // records with -2 pi Kz in a[8]); `small_phase`: |z Kz| <= 1 turn for every
 // spin and record, the phase as one FP32 product (then block <= 128).

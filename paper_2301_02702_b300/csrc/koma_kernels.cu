@@ -1374,15 +1374,22 @@ __global__ void __launch_bounds__(kMaxBlock, 2) bloch_items_kernel(const __grid_
 // holds one sample, a spin needs no more state than M, its z and M0, and the
 // record work that is the same for all spins is shared by 8 spins per thread.
 // The kernel walks its own copy of the record stream, prepared on the host:
-// an RF record carries the step's rotation (ux, uy, ch, c2 in a[0..3], the
-// quaternion of the uniform RF path of K1/K3, evaluated once per record instead
-// of by every thread), a PREC/ADC record -2 pi Kz in a[8]. The items are those
-// of K3 with 128 spins (16 lanes x 8); a warp takes two of them, one per
-// half-warp, and a sample's sum is a 16-lane butterfly per half.
+// an RF record carries the step's rotation matrix (a[0..8], the renormalised
+// quaternion rotation of the uniform RF path of K1/K3, evaluated once per
+// record instead of by every thread) and its dt (a[9]), a PREC/ADC record
+// -2 pi Kz in a[8].
+// A thread steps one unit of up to 8 consecutive spins of one group; units
+// are packed across groups (a warp's lanes may hold several groups, a group
+// may span warps), so slots are filled to within 8 spins per group. A
+// sample's sum is a segmented butterfly over the warp's lanes, one partial
+// row per (warp, group) segment; K2 sums a group's rows in order.
+// The spins' phase rotators are kept while the phase records' Kz repeats (a
+// FISP train's identical unbalanced lobes), as the relaxation factors are
+// kept per RF dt.
 // SMALLPH (the host checked |z Kz| <= 1 turn for every spin and record): the
 // phase angle is z (-2 pi Kz) in one FP32 product, relative error a few ulp of
 // an angle of at most 2 pi; otherwise the hi/lo fractional product of K1/K3.
-// The rotation, relaxation and sine are applied as in K1/K3.
+// Relaxation and the sine are applied as in K1/K3.
 // ---------------------------------------------------------------------------
 constexpr int kZS = 8;             // spins per thread
 constexpr int kZNP = kZS / 2;      // packed pairs
@@ -1395,8 +1402,7 @@ __global__ void __launch_bounds__(SMALLPH ? kZSmallBlock : kMaxBlock, SMALLPH ? 
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ int64_t s_batch;
     const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const int half = lane >> 4, hl = lane & 15;
+    const int lane = tid & 31;
     const BarPair bar{smem_u32(&s_bar[0])};
     if (tid == 0) {
         mbar_init(bar[0], 1);
@@ -1409,26 +1415,40 @@ __global__ void __launch_bounds__(SMALLPH ? kZSmallBlock : kMaxBlock, SMALLPH ? 
     const int64_t n_tiles = (A.n_rec + T - 1) / T;
     uint64_t g0 = 0;
     for (;;) {
+        // a batch: blockDim.x consecutive units, one per thread
         if (tid == 0) s_batch = atomicAdd(A.counter, 1);
         __syncthreads();
         const int64_t batch = s_batch;
         __syncthreads();
-        if (batch * 2 * nwarps >= A.n_items) break;
-        const int64_t oi = (batch * nwarps + warp) * 2 + half;
-        int64_t ib = 0, ie = 0;
-        float2* row = nullptr;
-        if (oi < A.n_items) {
-            const int64_t item = A.order[oi];
-            ib = A.item_begin[item];
-            ie = A.item_begin[item + 1];
-            row = static_cast<float2*>(A.partial) + item * A.n_adc;
+        if (batch * blockDim.x >= A.n_units) break;
+        // this lane's unit: spins [sb, sb + cnt) of one group, item `item`
+        const int64_t u = batch * blockDim.x + tid;
+        int64_t sb = 0;
+        int cnt = 0, item = -1;
+        if (u < A.n_units) {
+            sb = A.unit_begin[u];
+            cnt = static_cast<int>(A.unit_begin[u + 1] - sb);
+            item = A.unit_item[u];
         }
-        // the lane's 8 spins: ib + hl + 16 s (zero state past the item's end)
+        // the warp's segments (runs of lanes with one item): bit k of `same`
+        // when lane + 2^k has this lane's item; the segment's first lane
+        // writes the item's partial row
+        unsigned same = 0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int o = __shfl_down_sync(kFull, item, 1 << k);
+            if (lane + (1 << k) < 32 && item >= 0 && o == item) same |= 1u << k;
+        }
+        const int prev = __shfl_up_sync(kFull, item, 1);
+        float2* row = nullptr;
+        if (item >= 0 && (lane == 0 || prev != item))
+            row = static_cast<float2*>(A.partial) + static_cast<int64_t>(item) * A.n_adc;
+        // the unit's 8 slots: spin sb + s for s < cnt, zero state past it
         f32x2 MX[kZNP], MY[kZNP], MZ[kZNP], ZH[kZNP], ZL[kZNP], M0[kZNP];
 #pragma unroll
         for (int p = 0; p < kZNP; ++p) {
-            const int64_t j0 = ib + hl + 16 * (2 * p), j1 = j0 + 16;
-            const bool v0 = j0 < ie, v1 = j1 < ie;
+            const int64_t j0 = sb + 2 * p, j1 = j0 + 1;
+            const bool v0 = 2 * p < cnt, v1 = 2 * p + 1 < cnt;
             ZH[p] = pk(v0 ? P[P32_ZH * np + j0] : 0.f, v1 ? P[P32_ZH * np + j1] : 0.f);
             if (!SMALLPH) ZL[p] = pk(v0 ? P[P32_ZL * np + j0] : 0.f, v1 ? P[P32_ZL * np + j1] : 0.f);
             M0[p] = pk(v0 ? P[P32_M0 * np + j0] : 0.f, v1 ? P[P32_M0 * np + j1] : 0.f);
@@ -1436,8 +1456,8 @@ __global__ void __launch_bounds__(SMALLPH ? kZSmallBlock : kMaxBlock, SMALLPH ? 
             MY[p] = pk(0.f, 0.f);
             MZ[p] = M0[p];
         }
-        // the item's group shares T1 and T2
-        const float r1 = ib < ie ? P[P32_R1 * np + ib] : 0.f, r2 = ib < ie ? P[P32_R2 * np + ib] : 0.f;
+        // the unit's group shares T1 and T2
+        const float r1 = cnt > 0 ? P[P32_R1 * np + sb] : 0.f, r2 = cnt > 0 ? P[P32_R2 * np + sb] : 0.f;
         // relaxation factors minus one (Q1, Q2) for the last RF dt; the spins' phase
         // rotators for the last phase record's Kz (hi, lo): a train of
         // identical lobes (FISP) evaluates them once
@@ -1551,12 +1571,20 @@ __global__ void __launch_bounds__(SMALLPH ? kZSmallBlock : kMaxBlock, SMALLPH ? 
                         unpk(sr2, a0, a1);
                         unpk(si2, c0, c1);
                         float sr = a0 + a1, si = c0 + c1;
+                        // segmented sum over the warp's lanes (each lane adds
+                        // the partial 2^k lanes up while that lane is in its
+                        // segment): the segment's first lane ends with the
+                        // segment's total, in a fixed order
 #pragma unroll
-                        for (int o = 8; o > 0; o >>= 1) {  // within the half-warp
-                            sr += __shfl_xor_sync(kFull, sr, o);
-                            si += __shfl_xor_sync(kFull, si, o);
+                        for (int k = 0; k < 5; ++k) {
+                            const float ur = __shfl_down_sync(kFull, sr, 1 << k);
+                            const float ui = __shfl_down_sync(kFull, si, 1 << k);
+                            if ((same >> k) & 1) {
+                                sr += ur;
+                                si += ui;
+                            }
                         }
-                        if (hl == 0 && row) row[k0] = make_float2(sr, si);
+                        if (row) row[k0] = make_float2(sr, si);
                     }
                 }
             }

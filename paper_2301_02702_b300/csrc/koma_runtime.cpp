@@ -97,8 +97,11 @@ struct koma_phantom {
     // work items of the grouped kernel, built for items_s spins per thread:
     // d_items [n_items + 1] first spin of each item, then (same allocation)
     // d_order [n_items] longest first, d_group_item [n_groups + 1]
+    // (items_s = 8: the K3z table instead: d_items [n_units + 1] first spin
+    // of each unit of up to 8 spins, d_order [n_units] the unit's item (a
+    // warp's segment of a group), d_group_item [n_groups + 1])
     int items_s = 0;
-    int64_t n_items = 0;
+    int64_t n_items = 0, n_units = 0;
     int64_t* d_items = nullptr;
     int32_t* d_order = nullptr;
     int32_t* d_group_item = nullptr;
@@ -1604,6 +1607,55 @@ koma_status ensure_items(koma_ctx* ctx, koma_phantom* ph, int S) {
     return KOMA_OK;
 }
 
+// K3z's work table: every group cut into units of up to 8 consecutive spins,
+// units in group order, a warp taking 32 consecutive units; an item (one
+// partial row) is the run of a warp's units that belong to one group, so a
+// group's items are consecutive and K2 sums them in item order. Cached on the
+// phantom (items_s = 8).
+koma_status ensure_zunits(koma_ctx* ctx, koma_phantom* ph) {
+    if (ph->items_s == 8 && ph->d_items) return KOMA_OK;
+    constexpr int64_t kUnit = 8, kWarpUnits = 32;
+    std::vector<int64_t> ub;
+    std::vector<int32_t> uitem;
+    std::vector<int32_t> gi(static_cast<size_t>(ph->n_groups + 1), 0);
+    ub.reserve(static_cast<size_t>(ph->n / kUnit + ph->n_groups + 1));
+    uitem.reserve(ub.capacity());
+    int64_t item = -1, u = 0;
+    for (int64_t g = 0; g < ph->n_groups; ++g) {
+        gi[g] = static_cast<int32_t>(item + 1);
+        const int64_t lo = ph->group_offsets[g], hi = ph->group_offsets[g + 1];
+        for (int64_t s0 = lo; s0 < hi; s0 += kUnit, ++u) {
+            if (s0 == lo || u % kWarpUnits == 0) ++item;
+            ub.push_back(s0);
+            uitem.push_back(static_cast<int32_t>(item));
+        }
+        if (item + 2 > std::numeric_limits<int32_t>::max())
+            return fail(ctx, KOMA_E_INVALID, "simulate: grouped phantom needs too many work items");
+    }
+    gi[ph->n_groups] = static_cast<int32_t>(item + 1);
+    ub.push_back(ph->n);
+    if (ph->d_items) dev_free(ctx, ph->d_items, ph->items_bytes);
+    ph->d_items = nullptr;
+    ph->items_s = 0;
+    auto up16 = [](size_t b) { return (b + 15) / 16 * 16; };
+    const size_t b_ub = ub.size() * sizeof(int64_t), b_ui = up16(uitem.size() * sizeof(int32_t)),
+                 b_gi = gi.size() * sizeof(int32_t);
+    koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&ph->d_items), b_ub + b_ui + b_gi,
+                               "simulate: unit table");
+    if (st != KOMA_OK) return st;
+    ph->items_bytes = b_ub + b_ui + b_gi;
+    ph->d_order = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ph->d_items) + b_ub);
+    ph->d_group_item = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ph->d_items) + b_ub + b_ui);
+    cudaError_t e = h2d_sync(ctx, ph->d_items, ub.data(), b_ub);
+    if (e == cudaSuccess && !uitem.empty()) e = h2d_sync(ctx, ph->d_order, uitem.data(), uitem.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = h2d_sync(ctx, ph->d_group_item, gi.data(), b_gi);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "simulate: unit table copy");
+    ph->n_items = item + 1;
+    ph->n_units = u;
+    ph->items_s = 8;
+    return KOMA_OK;
+}
+
 // The grouped kernel suits many small groups (dictionaries); a few large
 // groups run faster through the CTA-split path.
 bool use_items_kernel(const koma_phantom* ph) {
@@ -1644,15 +1696,16 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     // S == 8: K3z (items of 128 spins as for S = 4, two per warp)
     const bool zk = S == 8;
     if (zk && !z_dict_ok(ph, seq)) return fail(ctx, KOMA_E_INTERNAL, "simulate: K3z on an ineligible pair");
-    koma_status rc = ensure_items(ctx, ph, zk ? 4 : S);
+    koma_status rc = zk ? ensure_zunits(ctx, ph) : ensure_items(ctx, ph, S);
     if (rc != KOMA_OK) return rc;
     const int64_t n_adc = seq->info.n_adc;
     const bool small_phase = zk && z_small_phase(ph, seq);
     if (small_phase) block = std::min(block, 128);
     const int per_sm = std::max(1, zk ? koma::items_z_ctas_per_sm(block, tile, small_phase)
                                       : koma::items_ctas_per_sm(S, block, tile));
-    const int64_t items_per_batch = (zk ? 2 : 1) * (block / 32);
-    const int64_t batches = (ph->n_items + items_per_batch - 1) / items_per_batch;
+    // a batch is one item per warp (K3), or 32 units per warp (K3z)
+    const int64_t per_batch = zk ? block : block / 32, work = zk ? ph->n_units : ph->n_items;
+    const int64_t batches = (work + per_batch - 1) / per_batch;
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(batches,
                                                          static_cast<int64_t>(ctx->sm_count) * per_sm)));
     rc = grow_scratch(ctx, static_cast<size_t>(ph->n_items) * static_cast<size_t>(n_adc) * 2 * sizeof(float), st);
@@ -1672,6 +1725,13 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     A.status = ctx->d_status;
     phantom_ext(ph, A.ext, &A.used);
     A.uni_relax = ph->uni_relax ? 1 : 0;
+    if (zk) {
+        A.unit_begin = ph->d_items;
+        A.unit_item = ph->d_order;
+        A.n_units = ph->n_units;
+        A.item_begin = nullptr;
+        A.order = nullptr;
+    }
     cudaError_t ce = cudaMemsetAsync(A.counter, 0, sizeof(int), st);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "simulate: counter reset");
     if (ctx->timing) cudaEventRecord(ctx->ev[0], st);
@@ -1699,7 +1759,7 @@ koma_status simulate_items(koma_ctx* ctx, koma_phantom* ph, const koma_sequence*
     ctx->last.grid = grid;
     ctx->last.block = block;
     ctx->last.spins_per_thread = S;
-    ctx->last.spins_per_cta = 32LL * S * (block / 32);  // K3z: 2 items of 128 per warp, as 32 x 8
+    ctx->last.spins_per_cta = 32LL * S * (block / 32);
     ctx->last.n_records = seq->info.n_records;
     ctx->last.partial_bytes = static_cast<int64_t>(ph->n_items * n_adc * 8);
     ctx->last.split = 1;
