@@ -7,7 +7,8 @@ dictionary (the MRF showcase, Section "Magnetic Resonance Fingerprinting"). Thes
 tests check:
 
 * eligible dictionaries with ragged groups (empty, 1, 127/128/129 spins: a
-  K3z item is 128 spins, so groups end inside, at and just past an item),
+  K3z thread takes a unit of up to 8 spins of one group and a warp 32 units,
+  so groups end inside and at a unit, and span warps),
   pulses on both sides of the series/closed-form switch, multi-step pulses,
   complex B1 and streams of several record tiles, group by group against the
   oracle, and bitwise repeatable;
@@ -124,8 +125,9 @@ def test_z_dictionary_matches_oracle(sim, sinc_steps, lobe_turns):
 
 
 def test_many_small_groups_fill_whole_batches(sim):
-    """Hundreds of items: batches of 2 items per warp over all CTAs, the last
-    batch partly empty."""
+    """700 groups packed as 8-spin units across warps and CTAs: segments of
+    several groups in one warp, groups split between warps, the last batch
+    partly empty."""
     rng = np.random.default_rng(8)
     sizes = list(rng.integers(1, 260, size=700))
     ph = z_dictionary(sizes, seed=9)
