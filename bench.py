@@ -933,6 +933,11 @@ def result_line(args, world, ph, seq, info, launch, stage_ms, clk, value, ms_max
              "traffic": measured_traffic(args.workload),
              "kernel_ms": k1, "algorithmic_flops_per_launch": flops,
              "peak_source": "FP32 peak 148 SMs x 128 lanes x 2 x 2032 MHz (unit counts, max SM clock)"}
+    if kname == "bloch_items_z_kernel":
+        # its partial rows, plus z, M0, 1/T1, 1/T2 (FP32) per spin and 12 B per
+        # unit of <= 8 spins of one group (the work table)
+        units = int(np.sum((np.diff(ph.group_offsets) + 7) // 8))
+        roof1["algorithmic_bytes_per_launch"] = float(launch["partial_bytes"]) + 16.0 * ph.n + 12.0 * units
     roofs.append(roof1)
     if mma and k6:
         peak_t, peak_src = tensor_peak()
