@@ -32,8 +32,22 @@ struct SerialHostScope {
     SerialHostScope& operator=(const SerialHostScope&) = delete;
     bool prev;
 };
+// A record stream seen as pointer and length: a builder's vector, or the
+// records gathered straight into a staging buffer.
+struct RecSpan {
+    Rec32* p = nullptr;
+    size_t n = 0;
+    RecSpan() = default;
+    RecSpan(Rec32* p_, size_t n_) : p(p_), n(n_) {}
+    RecSpan(std::vector<Rec32>& v) : p(v.data()), n(v.size()) {}  // NOLINT: a view of the vector
+    size_t size() const { return n; }
+    Rec32& operator[](size_t i) const { return p[i]; }
+    Rec32* begin() const { return p; }
+    Rec32* end() const { return p + n; }
+};
 // compact_records32 writing into `out` (null: count only); returns the
 // compacted stream's length.
+size_t compact_records32_into(const Rec32* r32, size_t n, Rec32* out);
 size_t compact_records32_into(const std::vector<Rec32>& r32, Rec32* out);
 // koma_sequence_upload building the FP32 record stream only (for a
 // simulation known to be FP32 on a static phantom).

@@ -718,12 +718,6 @@ struct RecordBuilder {
         run_tau = run_dtau = last_tau = 0;
         for (int d = 0; d < 3; ++d) run_k[d] = run_k1[d] = run_dk[d] = run_dk1[d] = last_k[d] = last_k1[d] = 0;
     }
-    void push(const koma::Rec32& a, const koma::Rec64& b, const koma::RecM& m) {
-        r32.push_back(a);
-        if (want64) r64.push_back(b);
-        if (wantM) rm.push_back(m);
-    }
-
     // Motion record carrying `a`'s fields.
     static koma::RecM extend(const koma::Rec32& a) {
         koma::RecM m{};
@@ -745,30 +739,40 @@ struct RecordBuilder {
     void close_run() {
         if (!run_open) return;
         koma::Rec32 a{};
-        koma::Rec64 b{};
-        a.type = b.type = koma::REC_ADC;
-        b.count = run_count;
-        a.k0 = b.k0 = run_k0;
+        a.type = koma::REC_ADC;
+        a.k0 = run_k0;
         for (int d = 0; d < 3; ++d) {
             split(run_k[d], &a.a[2 * d], &a.a[2 * d + 1]);
-            b.a[d] = run_k[d];
             a.a[8 + d] = static_cast<float>(run_count > 1 ? run_dk[d] : 0.0);
-            b.a[4 + d] = run_count > 1 ? run_dk[d] : 0.0;
-            b.a[8 + d] = run_k1[d];
-            b.a[11 + d] = run_count > 1 ? run_dk1[d] : 0.0;
         }
         split(run_tau, &a.a[6], &a.a[7]);
-        b.a[3] = run_tau;
         a.a[11] = static_cast<float>(run_count > 1 ? run_dtau : 0.0);
-        b.a[7] = run_count > 1 ? run_dtau : 0.0;
         a.count = run_count | (term_bits(a) << koma::kTermShift);
-        koma::RecM m = extend(a);
-        for (int d = 0; d < 3; ++d) {
-            split(run_k1[d], &m.a[12 + 2 * d], &m.a[13 + 2 * d]);
-            split(run_count > 1 ? run_dk1[d] : 0.0, &m.a[18 + 2 * d], &m.a[19 + 2 * d]);
+        r32.push_back(a);
+        if (want64) {
+            koma::Rec64 b{};
+            b.type = koma::REC_ADC;
+            b.count = run_count;
+            b.k0 = run_k0;
+            for (int d = 0; d < 3; ++d) {
+                b.a[d] = run_k[d];
+                b.a[4 + d] = run_count > 1 ? run_dk[d] : 0.0;
+                b.a[8 + d] = run_k1[d];
+                b.a[11 + d] = run_count > 1 ? run_dk1[d] : 0.0;
+            }
+            b.a[3] = run_tau;
+            b.a[7] = run_count > 1 ? run_dtau : 0.0;
+            r64.push_back(b);
         }
-        m.count = a.count | (k1_bits(m, 12) << koma::kTermShift);
-        push(a, b, m);
+        if (wantM) {
+            koma::RecM m = extend(a);
+            for (int d = 0; d < 3; ++d) {
+                split(run_k1[d], &m.a[12 + 2 * d], &m.a[13 + 2 * d]);
+                split(run_count > 1 ? run_dk1[d] : 0.0, &m.a[18 + 2 * d], &m.a[19 + 2 * d]);
+            }
+            m.count = a.count | (k1_bits(m, 12) << koma::kTermShift);
+            rm.push_back(m);
+        }
         ++n_runs;
         run_open = false;
     }
@@ -891,31 +895,34 @@ void build_steps(int64_t n_begin, int64_t n_end, double t0, const double* dt, co
             rb.close_run();
             if (c.tau > 0.0) {  // bring the state to the start of this RF step
                 koma::Rec32 a{};
-                koma::Rec64 b{};
-                a.type = b.type = koma::REC_PREC;
-                for (int d = 0; d < 3; ++d) {
-                    split(c.K[d], &a.a[2 * d], &a.a[2 * d + 1]);
-                    b.a[d] = c.K[d];
-                    b.a[4 + d] = c.K1[d];
-                }
+                a.type = koma::REC_PREC;
+                for (int d = 0; d < 3; ++d) split(c.K[d], &a.a[2 * d], &a.a[2 * d + 1]);
                 split(c.tau, &a.a[6], &a.a[7]);
-                b.a[3] = c.tau;
                 a.count = RecordBuilder::term_bits(a) << koma::kTermShift;
-                koma::RecM m = RecordBuilder::extend(a);
-                for (int d = 0; d < 3; ++d) split(c.K1[d], &m.a[8 + 2 * d], &m.a[9 + 2 * d]);
-                m.count = a.count | (RecordBuilder::k1_bits(m, 8) << koma::kTermShift);
-                rb.push(a, b, m);
+                rb.r32.push_back(a);
+                if (rb.want64) {
+                    koma::Rec64 b{};
+                    b.type = koma::REC_PREC;
+                    for (int d = 0; d < 3; ++d) {
+                        b.a[d] = c.K[d];
+                        b.a[4 + d] = c.K1[d];
+                    }
+                    b.a[3] = c.tau;
+                    rb.r64.push_back(b);
+                }
+                if (rb.wantM) {
+                    koma::RecM m = RecordBuilder::extend(a);
+                    for (int d = 0; d < 3; ++d) split(c.K1[d], &m.a[8 + 2 * d], &m.a[9 + 2 * d]);
+                    m.count = a.count | (RecordBuilder::k1_bits(m, 8) << koma::kTermShift);
+                    rb.rm.push_back(m);
+                }
                 ++rb.n_mat;
             }
             koma::Rec32 a{};
-            koma::Rec64 b{};
-            a.type = b.type = koma::REC_RF;
+            a.type = koma::REC_RF;
             const double s = kGammaBar * dt[n];  // turns per tesla
             // FP32 record: half-angle vector pi s B (radians); FP64: s B (turns)
-            for (int d = 0; d < 3; ++d) {
-                a.a[d] = static_cast<float>(kPi * s * gm[d]);
-                b.a[d] = s * gm[d];
-            }
+            for (int d = 0; d < 3; ++d) a.a[d] = static_cast<float>(kPi * s * gm[d]);
             const double bx = s * b1_re[n], by = s * b1_im[n];
             a.a[3] = static_cast<float>(kPi * bx);
             a.a[4] = static_cast<float>(kPi * by);
@@ -923,14 +930,23 @@ void build_steps(int64_t n_begin, int64_t n_end, double t0, const double* dt, co
             // path's rsqrt stays finite for a vanishing field
             a.a[5] = std::max(a.a[3] * a.a[3] + a.a[4] * a.a[4], std::numeric_limits<float>::min());
             a.a[6] = static_cast<float>(dt[n]);
-            b.a[3] = bx;
-            b.a[4] = by;
-            b.a[5] = dt[n];
+            rb.r32.push_back(a);
             const double t_mid = t + 0.5 * dt[n];
-            b.a[6] = t_mid;
-            koma::RecM m = RecordBuilder::extend(a);
-            m.a[13] = static_cast<float>(t_mid);
-            rb.push(a, b, m);
+            if (rb.want64) {
+                koma::Rec64 b{};
+                b.type = koma::REC_RF;
+                for (int d = 0; d < 3; ++d) b.a[d] = s * gm[d];
+                b.a[3] = bx;
+                b.a[4] = by;
+                b.a[5] = dt[n];
+                b.a[6] = t_mid;
+                rb.r64.push_back(b);
+            }
+            if (rb.wantM) {
+                koma::RecM m = RecordBuilder::extend(a);
+                m.a[13] = static_cast<float>(t_mid);
+                rb.rm.push_back(m);
+            }
             for (int d = 0; d < 3; ++d) c.K[d] = c.K1[d] = 0.0;
             c.tau = 0.0;
         } else {
@@ -991,11 +1007,45 @@ void run_tasks(int k, const std::function<void(int)>& run) {
     for (int w = 0; w < k; ++w) run(w);  // the pool is busy: serial (see parallel_for)
 }
 
+// The FP32 records of a parallel build left in the chunk builders: the
+// FP32-only upload copies them, in parallel, straight to their places in its
+// staging buffer instead of concatenating them into one vector first.
+struct PendingChunks {
+    struct Part {
+        int w;                    // builder
+        size_t r0, r1, dst;       // its records [r0, r1) go to dst
+    };
+    std::vector<RecordBuilder*> wb;
+    std::vector<Part> parts;
+    size_t n32 = 0;
+    bool active() const { return !wb.empty(); }
+    void gather(koma::Rec32* dst) const {
+        const int k = n_workers_for(static_cast<int>(parts.size()));
+        run_tasks(k, [&](int t) {
+            for (size_t i = static_cast<size_t>(t); i < parts.size(); i += static_cast<size_t>(k)) {
+                const Part& q = parts[i];
+                if (q.r1 > q.r0)
+                    std::memcpy(dst + q.dst, wb[q.w]->r32.data() + q.r0, (q.r1 - q.r0) * sizeof(koma::Rec32));
+            }
+        });
+    }
+    void release() {
+        for (RecordBuilder* b : wb) builder_release(b);
+        wb.clear();
+        parts.clear();
+    }
+    ~PendingChunks() { release(); }
+};
+
 // Validation + preprocessing shared by koma_sequence_upload and
-// koma_sequence_plan. `err` receives the message on failure.
+// koma_sequence_plan. `err` receives the message on failure. With `pend`
+// (FP32 stream only: neither FP64 nor motion records wanted), a build in
+// parallel chunks leaves its records in the chunk builders (rb.r32 stays
+// empty) for the caller to gather.
 koma_status build_records(int64_t n_steps, const double* dt, const double* gx, const double* gy,
                           const double* gz, const double* b1_re, const double* b1_im, const uint8_t* adc,
-                          RecordBuilder& rb, koma_sequence_info& info, std::string& err) {
+                          RecordBuilder& rb, koma_sequence_info& info, std::string& err,
+                          PendingChunks* pend = nullptr) {
     char buf[256];
     auto bad = [&](const char* fmt, long long i, double v) {
         snprintf(buf, sizeof(buf), fmt, i, v);
@@ -1005,16 +1055,36 @@ koma_status build_records(int64_t n_steps, const double* dt, const double* gx, c
     if (n_steps < 0) return bad("sequence: n_steps = %lld < 0%.0g", n_steps, 0.0);
     if (!gx || !gy || !gz || !adc || (n_steps > 0 && (!dt || !b1_re || !b1_im)))
         return bad("sequence: NULL array (n_steps %lld)%.0g", n_steps, 0.0);
-    for (int64_t i = 0; i <= n_steps; ++i) {
-        if (!std::isfinite(gx[i]) || !std::isfinite(gy[i]) || !std::isfinite(gz[i]))
-            return bad("sequence: non-finite gradient at time point %lld%.0g", i, 0.0);
-        if (adc[i] > 1) return bad("sequence: adc[%lld] = %g (must be 0 or 1)", i, adc[i]);
+    // long sequences: a parallel pass finds whether anything is invalid, and
+    // only then do the serial loops below look for the first offending index
+    bool check_serially = true;
+    if (n_steps >= 65536) {
+        const int k = n_workers_for(16);
+        std::vector<uint8_t> bad_in(static_cast<size_t>(k), 0);
+        run_tasks(k, [&](int w) {
+            const int64_t lo = n_steps * w / k, hi = w + 1 == k ? n_steps + 1 : n_steps * (w + 1) / k;
+            bool b = false;
+            for (int64_t i = lo; i < hi; ++i) {
+                b |= !std::isfinite(gx[i]) || !std::isfinite(gy[i]) || !std::isfinite(gz[i]) || adc[i] > 1;
+                if (i < n_steps)
+                    b |= !std::isfinite(dt[i]) || !(dt[i] > 0) || !std::isfinite(b1_re[i]) || !std::isfinite(b1_im[i]);
+            }
+            bad_in[w] = b;
+        });
+        check_serially = std::find(bad_in.begin(), bad_in.end(), 1) != bad_in.end();
     }
-    for (int64_t n = 0; n < n_steps; ++n) {
-        if (!std::isfinite(dt[n]) || !(dt[n] > 0))
-            return bad("sequence: dt[%lld] = %g (must be finite and > 0)", n, dt[n]);
-        if (!std::isfinite(b1_re[n]) || !std::isfinite(b1_im[n]))
-            return bad("sequence: non-finite B1 at step %lld%.0g", n, 0.0);
+    if (check_serially) {
+        for (int64_t i = 0; i <= n_steps; ++i) {
+            if (!std::isfinite(gx[i]) || !std::isfinite(gy[i]) || !std::isfinite(gz[i]))
+                return bad("sequence: non-finite gradient at time point %lld%.0g", i, 0.0);
+            if (adc[i] > 1) return bad("sequence: adc[%lld] = %g (must be 0 or 1)", i, adc[i]);
+        }
+        for (int64_t n = 0; n < n_steps; ++n) {
+            if (!std::isfinite(dt[n]) || !(dt[n] > 0))
+                return bad("sequence: dt[%lld] = %g (must be finite and > 0)", n, dt[n]);
+            if (!std::isfinite(b1_re[n]) || !std::isfinite(b1_im[n]))
+                return bad("sequence: non-finite B1 at step %lld%.0g", n, 0.0);
+        }
     }
     info = koma_sequence_info{};
     info.n_steps = n_steps;
@@ -1100,6 +1170,26 @@ koma_status build_records(int64_t n_steps, const double* dt, const double* gx, c
             rb.n_runs += wb[w]->n_runs;
             rb.n_mat += wb[w]->n_mat;
         }
+        if (pend && !rb.want64 && !rb.wantM) {
+            // the caller gathers: chunk i's records go after those of chunks < i
+            pend->release();
+            size_t at = 0;
+            for (int i = 0; i < n_chunks; ++i) {
+                const Range& R = rng[i];
+                pend->parts.push_back({i % k, R.r32[0], R.r32[1], at});
+                at += R.r32[1] - R.r32[0];
+                info.n_rf += cnt[i].n_rf;
+                info.n_precess += cnt[i].n_precess;
+            }
+            pend->wb = wb;
+            pend->n32 = at;
+            rb.n_adc = rng[n_chunks - 1].n_adc_end;
+            info.n_adc = rb.n_adc;
+            info.n_records = static_cast<int64_t>(at);
+            info.n_adc_runs = rb.n_runs;
+            info.n_materialize = rb.n_mat;
+            return KOMA_OK;
+        }
         rb.r32.reserve(n32);
         if (rb.want64) rb.r64.reserve(n64);
         if (rb.wantM) rb.rm.reserve(nm);
@@ -1140,10 +1230,26 @@ struct MmaPlan {
     int64_t n_snaps = 0;
 };
 
-void plan_mma(std::vector<koma::Rec32>& r32, int64_t n_adc, MmaPlan& P) {
+// Length of the run of RF records that starts at record i: the builder
+// stores it in the run's first record (RecordBuilder::mark_rf_runs), so the
+// plans step over a pulse's records instead of visiting each; a run without
+// it is counted.
+size_t rf_run_len(koma::RecSpan r32, size_t i) {
+    const int32_t c = r32[i].count;
+    if (c > 0 && i + static_cast<size_t>(c) <= r32.size()) return static_cast<size_t>(c);
+    size_t j = i;
+    while (j < r32.size() && r32[j].type == koma::REC_RF) ++j;
+    return j - i;
+}
+
+void plan_mma(koma::RecSpan r32, int64_t n_adc, MmaPlan& P) {
     std::map<std::array<uint32_t, 4>, std::vector<size_t>> buckets;
     for (size_t i = 0; i < r32.size(); ++i) {
         const koma::Rec32& R = r32[i];
+        if (R.type == koma::REC_RF) {
+            i += rf_run_len(r32, i) - 1;
+            continue;
+        }
         if (R.type != koma::REC_ADC || (R.count & koma::kCountMask) < 2) continue;
         std::array<uint32_t, 4> key;
         std::memcpy(key.data(), &R.a[8], sizeof(key));
@@ -1168,6 +1274,7 @@ void plan_mma(std::vector<koma::Rec32>& r32, int64_t n_adc, MmaPlan& P) {
         koma::Rec32& R = r32[i];
         if (R.type != koma::REC_ADC) {
             block_has = false;  // RF or PREC: the state changes, a new block begins
+            if (R.type == koma::REC_RF) i += rf_run_len(r32, i) - 1;
             continue;
         }
         if (!taken[i]) continue;
@@ -1227,21 +1334,23 @@ struct RfMapPlan {
     int64_t runs = 0, steps = 0, pulse_steps = 0;
 };
 
-void plan_rf_maps(std::vector<koma::Rec32>& r32, RfMapPlan& P) {
+void plan_rf_maps(koma::RecSpan r32, RfMapPlan& P) {
     struct Run {
         size_t begin, len;
     };
+    // the maximal runs of RF records, stepped over by their stored lengths
+    const size_t n_rec = r32.size();
     std::vector<Run> runs;
-    for (size_t i = 0; i < r32.size();) {
+    for (size_t i = 0; i < n_rec;) {
         if (r32[i].type != koma::REC_RF) {
             ++i;
             continue;
         }
-        size_t j = i;
-        while (j < r32.size() && r32[j].type == koma::REC_RF) ++j;
-        runs.push_back({i, j - i});
-        i = j;
+        const size_t len = rf_run_len(r32, i);
+        runs.push_back({i, len});
+        i += len;
     }
+    const bool par = n_rec >= 16384;
     auto same = [&](const Run& a, const Run& b) {
         return a.len == b.len && std::memcmp(&r32[a.begin], &r32[b.begin], a.len * sizeof(koma::Rec32)) == 0;
     };
@@ -1263,23 +1372,46 @@ void plan_rf_maps(std::vector<koma::Rec32>& r32, RfMapPlan& P) {
             hash[q] = h;
         }
     };
-    if (r32.size() >= 16384 && runs.size() >= 16) {
+    const bool par_runs = par && runs.size() >= 16;
+    if (par_runs) {
         const int k = n_workers_for(static_cast<int>(std::min<size_t>(runs.size(), 64)));
         run_tasks(k, [&](int w) { hash_runs(runs.size() * w / k, runs.size() * (w + 1) / k); });
     } else {
         hash_runs(0, runs.size());
     }
-    std::map<std::pair<uint64_t, size_t>, std::vector<std::vector<size_t>>> buckets;
+    // equality with the first run of the same hash and length, checked byte
+    // for byte (in parallel for long streams); a run that differs from it (a
+    // hash collision) is placed by comparing it with every class of its bucket
+    std::map<std::pair<uint64_t, size_t>, size_t> first;
+    std::vector<size_t> rep(runs.size(), SIZE_MAX);
     for (size_t q = 0; q < runs.size(); ++q) {
         if (runs[q].len < static_cast<size_t>(koma::kRfMapMinLen)) continue;
-        const uint64_t h = hash[q];
-        auto& classes = buckets[{h, runs[q].len}];
+        rep[q] = first.emplace(std::make_pair(hash[q], runs[q].len), q).first->second;
+    }
+    std::vector<uint8_t> eq(runs.size(), 0);
+    auto check = [&](size_t q0, size_t q1) {
+        for (size_t q = q0; q < q1; ++q)
+            if (rep[q] != SIZE_MAX) eq[q] = rep[q] == q || same(runs[rep[q]], runs[q]);
+    };
+    if (par_runs) {
+        const int k = n_workers_for(static_cast<int>(std::min<size_t>(runs.size(), 64)));
+        run_tasks(k, [&](int w) { check(runs.size() * w / k, runs.size() * (w + 1) / k); });
+    } else {
+        check(0, runs.size());
+    }
+    std::map<std::pair<uint64_t, size_t>, std::vector<std::vector<size_t>>> buckets;
+    for (size_t q = 0; q < runs.size(); ++q) {
+        if (rep[q] == SIZE_MAX) continue;
+        auto& classes = buckets[{hash[q], runs[q].len}];
+        if (eq[q] && !classes.empty() && classes[0][0] == rep[q]) {
+            classes[0].push_back(q);  // equal to the bucket's first run: its class
+            continue;
+        }
         bool placed = false;
-        for (auto& c : classes) {
-            if (same(runs[c[0]], runs[q])) {
-                c.push_back(q);
+        for (size_t ci = eq[q] ? 0 : 1; ci < classes.size() && !placed; ++ci) {
+            if (same(runs[classes[ci][0]], runs[q])) {
+                classes[ci].push_back(q);
                 placed = true;
-                break;
             }
         }
         if (!placed) classes.push_back({q});
@@ -1356,7 +1488,7 @@ namespace {
 // The record stream's side of K3z's condition: no RF step has a z gradient
 // (its rotation is the same for spins that differ only in z) and no ADC
 // record holds more than one sample.
-bool z_dictionary_stream(const std::vector<koma::Rec32>& r32) {
+bool z_dictionary_stream(koma::RecSpan r32) {
     for (const koma::Rec32& R : r32) {
         if (R.type == koma::REC_RF && (R.a[2] != 0.f || (R.count > 0 && R.a[10] != 0.f))) return false;
         if (R.type == koma::REC_ADC && (R.count & koma::kCountMask) > 1) return false;
@@ -1375,8 +1507,8 @@ bool z_dictionary_stream(const std::vector<koma::Rec32>& r32) {
 // * a PREC/ADC record's a[8] holds -2 pi Kz (Kz = hi + lo, FP64, rounded once),
 //   the phase per metre of z when the phantom's extent keeps |z Kz| small.
 // Everything else is copied. Returns max |Kz| over the records with a z term.
-double build_z_stream(const std::vector<koma::Rec32>& r32, std::vector<koma::Rec32>& out) {
-    out = r32;
+double build_z_stream(koma::RecSpan r32, std::vector<koma::Rec32>& out) {
+    out.assign(r32.begin(), r32.end());
     double kmax = 0.0;
     for (koma::Rec32& R : out) {
         if (R.type == koma::REC_RF) {
@@ -1403,6 +1535,25 @@ double build_z_stream(const std::vector<koma::Rec32>& r32, std::vector<koma::Rec
     return kmax;
 }
 
+// The context's pinned staging buffer holds at least `need` bytes; when it
+// grows, its first `keep` bytes move to the new buffer (no copy is in flight:
+// uploads from it are synchronous).
+koma_status stage_reserve(koma_ctx* ctx, size_t need, size_t keep) {
+    if (need <= ctx->h_stage_bytes) return KOMA_OK;
+    const size_t want = (need + need / 4 + (size_t{1} << 20) - 1) / (size_t{1} << 20) * (size_t{1} << 20);
+    char* h = nullptr;
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&h), want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "sequence_upload: staging buffer");
+    }
+    if (keep && ctx->h_stage) std::memcpy(h, ctx->h_stage, std::min(keep, ctx->h_stage_bytes));
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = h;
+    ctx->h_stage_bytes = want;
+    return KOMA_OK;
+}
+
 koma_status sequence_upload_impl(koma_ctx* ctx, int64_t n_steps, const double* dt, const double* gx,
                                  const double* gy, const double* gz, const double* b1_re, const double* b1_im,
                                  const uint8_t* adc, bool need64, bool needM, koma_sequence** out) {
@@ -1412,54 +1563,56 @@ koma_status sequence_upload_impl(koma_ctx* ctx, int64_t n_steps, const double* d
     static thread_local RecordBuilder rb;
     rb.reset(need64, needM);
     koma_sequence_info info{};
+    PendingChunks pend;
     {
         std::string err;
-        koma_status st = build_records(n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, rb, info, err);
+        koma_status st = build_records(n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, rb, info, err, &pend);
         if (st != KOMA_OK) return fail(ctx, st, "%s", err.c_str());
+    }
+    // the FP32 records: the builder's vector, or (a parallel build of the FP32
+    // stream alone) gathered straight into the staging buffer, where the plans
+    // below mark them in place
+    const bool gathered = pend.active();
+    koma::RecSpan recs(rb.r32);
+    if (gathered) {
+        const koma_status st = stage_reserve(ctx, pend.n32 * sizeof(koma::Rec32), 0);
+        if (st != KOMA_OK) return st;
+        pend.gather(reinterpret_cast<koma::Rec32*>(ctx->h_stage));
+        recs = koma::RecSpan(reinterpret_cast<koma::Rec32*>(ctx->h_stage), pend.n32);
+        pend.release();
     }
     koma_sequence* seq = new (std::nothrow) koma_sequence();
     if (!seq) return fail(ctx, KOMA_E_NOMEM, "sequence_upload: host allocation");
     seq->ctx = ctx;
     seq->info = info;
-    seq->z_dict = z_dictionary_stream(rb.r32);
+    seq->z_dict = z_dictionary_stream(recs);
     std::vector<koma::Rec32> rz;
-    if (seq->z_dict) seq->z_kmax = build_z_stream(rb.r32, rz);
+    if (seq->z_dict) seq->z_kmax = build_z_stream(recs, rz);
     MmaPlan mp;
-    plan_mma(rb.r32, info.n_adc, mp);
+    plan_mma(recs, info.n_adc, mp);
     seq->info.n_mma_groups = static_cast<int64_t>(mp.groups.size());
     seq->info.n_mma_runs = static_cast<int64_t>(mp.runs.size());
     seq->info.n_mma_samples = mp.n_samples;
     RfMapPlan fp;
-    plan_rf_maps(rb.r32, fp);
+    plan_rf_maps(recs, fp);
     seq->info.n_rf_maps = static_cast<int64_t>(fp.pulses.size());
     seq->info.n_rf_map_runs = fp.runs;
     seq->info.n_rf_map_steps = fp.steps;
     seq->info.n_rf_map_pulse_steps = fp.pulse_steps;
     // the compacted stream's length (the stream itself is written into the block)
-    const size_t n_rc = fp.pulses.empty() ? 0 : koma::compact_records32_into(rb.r32, nullptr);
+    const size_t n_rc = fp.pulses.empty() ? 0 : koma::compact_records32_into(recs.p, recs.n, nullptr);
     DeviceGuard g(ctx->device);
     auto up16 = [](size_t b) { return (b + 15) / 16 * 16; };
-    const size_t b32 = rb.r32.size() * sizeof(koma::Rec32), b64 = rb.r64.size() * sizeof(koma::Rec64),
+    const size_t b32 = recs.size() * sizeof(koma::Rec32), b64 = rb.r64.size() * sizeof(koma::Rec64),
                  bm = rb.rm.size() * sizeof(koma::RecM), bg = mp.groups.size() * sizeof(koma::MmaGroup),
                  br = mp.runs.size() * sizeof(koma::MmaRun), bf = up16(mp.from.size()),
                  bp = fp.pulses.size() * sizeof(koma::RfMapPulse), bc = n_rc * sizeof(koma::Rec32),
                  bz = rz.size() * sizeof(koma::Rec32);
     const size_t total = b32 + b64 + bm + bg + br + bf + bp + bc + bz;
     koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&seq->r32), total, "sequence_upload");
-    if (st == KOMA_OK && total > ctx->h_stage_bytes) {
-        if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-        ctx->h_stage = nullptr;
-        ctx->h_stage_bytes = 0;
-        const size_t want = (total + total / 4 + (size_t{1} << 20) - 1) / (size_t{1} << 20) * (size_t{1} << 20);
-        cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&ctx->h_stage), want);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            ctx->h_stage = nullptr;
-            st = cuda_fail(ctx, e, "sequence_upload: staging buffer");
-        } else {
-            ctx->h_stage_bytes = want;
-        }
-    }
+    // the whole block in the staging buffer (keeping gathered records)
+    if (st == KOMA_OK) st = stage_reserve(ctx, total, gathered ? b32 : 0);
+    if (gathered) recs.p = reinterpret_cast<koma::Rec32*>(ctx->h_stage);
     if (st == KOMA_OK && b32) {
         char* base = reinterpret_cast<char*>(seq->r32);
         char* h = ctx->h_stage;
@@ -1474,7 +1627,7 @@ koma_status sequence_upload_impl(koma_ctx* ctx, int64_t n_steps, const double* d
             seq->n_mma_runs = static_cast<int64_t>(mp.runs.size());
             seq->n_mma_snaps = mp.n_snaps;
         }
-        std::memcpy(h, rb.r32.data(), b32);
+        if (!gathered) std::memcpy(h, rb.r32.data(), b32);
         if (b64) std::memcpy(h + b32, rb.r64.data(), b64);
         if (bm) std::memcpy(h + b32 + b64, rb.rm.data(), bm);
         if (bg) std::memcpy(h + off, mp.groups.data(), bg);
@@ -1490,7 +1643,7 @@ koma_status sequence_upload_impl(koma_ctx* ctx, int64_t n_steps, const double* d
             seq->r32c = reinterpret_cast<koma::Rec32*>(base + off + bp);
             seq->n_rec_c = static_cast<int64_t>(n_rc);
             std::memcpy(h + off, fp.pulses.data(), bp);
-            koma::compact_records32_into(rb.r32, reinterpret_cast<koma::Rec32*>(h + off + bp));
+            koma::compact_records32_into(recs.p, recs.n, reinterpret_cast<koma::Rec32*>(h + off + bp));
         }
         off += bp + bc;
         if (bz) {
@@ -2436,8 +2589,12 @@ int host_phantom32(int64_t n, const double* x, const double* y, const double* z,
 }
 
 size_t compact_records32_into(const std::vector<Rec32>& r32, Rec32* out) {
+    return compact_records32_into(r32.data(), r32.size(), out);
+}
+
+size_t compact_records32_into(const Rec32* r32, size_t n_rec, Rec32* out) {
     size_t n = 0;
-    for (size_t i = 0; i < r32.size(); ++n) {
+    for (size_t i = 0; i < n_rec; ++n) {
         const Rec32& q = r32[i];
         if (q.type == REC_RF && q.count > 0 && q.k0 > 0) {
             Rec32 m{};

@@ -63,6 +63,23 @@ def test_plan_rejects_bad_sequences(lib):
         assert e.value.status == koma.KOMA_E_INVALID
 
 
+def test_plan_rejects_bad_long_sequences(lib):
+    """Sequences of >= 65,536 steps are checked by a parallel pass before the
+    serial one names the first offence: an invalid value anywhere, up to the
+    last step and the last time point, is still refused."""
+    n = 70_000
+    koma.koma_sequence_plan(random_sequence(n, seed=3))
+    for i in (0, 33_001, n - 1):
+        for mutate in (lambda s: s.dt.__setitem__(i, 0.0), lambda s: s.dt.__setitem__(i, np.nan),
+                       lambda s: s.b1.__setitem__(i, complex(0, np.inf)), lambda s: s.gz.__setitem__(i, np.nan),
+                       lambda s: s.gy.__setitem__(n, -np.inf), lambda s: s.adc.__setitem__(n, 3)):
+            s = random_sequence(n, seed=3)
+            mutate(s)
+            with pytest.raises(koma.KomaError) as e:
+                koma.koma_sequence_plan(s)
+            assert e.value.status == koma.KOMA_E_INVALID
+
+
 def _reference_samples(seq: Sequence):
     """(K [turns/m], tau [s], K1 [turns s/m]) of every ADC sample relative
     to the end of the last RF step before it, by a plain loop over steps:
@@ -218,6 +235,31 @@ def _pulse_train(pulses, order, seed=0):
         b.steps(2, 40e-6, [rng.uniform(-0.01, 0.01), 0.004 * (k % 5), 0.0]).steps(1, 40e-6, [0.0, 0.0, 0.0])
         b.steps(4, 10e-6, adc=True)
     return b.build()
+
+
+def test_plan_on_long_streams_follows_the_rule(lib):
+    """Streams of >= 16,384 records find their RF runs, hash them and check
+    their equality in parallel slices; the plan is still the rule's: pulses
+    of >= 4 steps that recur unchanged >= 3 times, at most 8, the ones saving
+    the most stepped RF steps first (ties: first occurrence)."""
+    from paper_2301_02702_b300.workloads import sinc_pulse
+    rng = np.random.default_rng(5)
+    lens = [3] + [4 * i for i in range(1, 12)]  # pulse 0 is too short for a map
+    pulses = [(m, 4e-6, sinc_pulse(m, 4e-6, 15.0 + 5 * i), [0.0, 0.0, 0.002 * (i % 3)]) for i, m in enumerate(lens)]
+    order = [int(p) for p in rng.choice(10, size=900)]
+    order += [10, 10, 11]  # pulse 10 three times more, pulse 11 once
+    seq = _pulse_train(pulses, order, seed=6)
+    info = koma.koma_sequence_plan(seq)
+    assert info["n_records"] >= 16384
+    counts = {p: order.count(p) for p in set(order)}
+    first = {p: order.index(p) for p in counts}
+    cls = [p for p, c in counts.items() if c >= 3 and pulses[p][0] >= 4]
+    cls.sort(key=lambda p: (-(counts[p] - 1) * pulses[p][0], first[p]))
+    cls = cls[:8]
+    assert info["n_rf_maps"] == len(cls)
+    assert info["n_rf_map_runs"] == sum(counts[p] for p in cls)
+    assert info["n_rf_map_steps"] == sum(counts[p] * pulses[p][0] for p in cls)
+    assert info["n_rf_map_pulse_steps"] == sum(pulses[p][0] for p in cls)
 
 
 def test_plan_finds_repeated_pulses(lib):

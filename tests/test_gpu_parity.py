@@ -186,6 +186,23 @@ def test_simulate_host_matches_device_path(sim):
     assert np.array_equal(dev, host)
 
 
+@pytest.mark.parametrize("case", ["se128", "epi512", "random"])
+def test_host_call_equals_device_path_on_long_sequences(sim, case):
+    """The host call builds the FP32 stream alone in parallel chunks, gathers
+    it straight into the staging buffer and lets the readout and pulse plans
+    mark it there; the device path's upload builds all three streams and
+    concatenates them. Same records, so bitwise the same signal (long
+    sequences: 40,000 to 81,920 steps, many chunks)."""
+    if case == "random":
+        ph, seq = random_spins(1500, seed=31), random_sequence(40_000, seed=32)
+    else:
+        ph, seq = workload(case, "small")[0], workload(case, "full")[1]
+    dev = gpu_signal(sim, ph, seq)
+    host = koma.koma_simulate_host(sim.ctx, ph, seq, koma.KOMA_FP32_SPLITPHASE)
+    assert np.max(np.abs(dev)) > 0
+    assert np.array_equal(dev, host)
+
+
 def test_abi_errors(sim):
     bad = random_spins(10, seed=1)
     bad.t2[3] = 0.0
