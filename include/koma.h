@@ -397,6 +397,37 @@ koma_status koma_simulate_host(koma_ctx *ctx, int64_t n,
                                const double *b1_im, const uint8_t *adc,
                                koma_precision precision, double *sig_host);
 
+/* One simulation of a batch of host-buffer calls: the arguments of
+ * koma_simulate_host after ctx (arrays borrowed for the duration of the batch
+ * call; the caller owns them and sig_host). */
+typedef struct {
+    int64_t n;                      /* spins                                      */
+    const double *x, *y, *z;        /* [n] positions (m)                          */
+    const double *pd, *t1, *t2;     /* [n] proton density, T1, T2 (s)             */
+    const double *dw;               /* [n] off-resonance (rad/s)                  */
+    const int64_t *group_offsets;   /* NULL or [n_groups + 1]                     */
+    int64_t n_groups;
+    int64_t n_steps;                /* sequence, as for koma_sequence_upload       */
+    const double *dt, *gx, *gy, *gz, *b1_re, *b1_im;
+    const uint8_t *adc;
+    double *sig_host;               /* out: host FP64 [n_groups][n_adc][2]        */
+} koma_host_job;
+
+/*
+ * koma_simulate_host for each of jobs[0 .. n_jobs), with one job's host
+ * work (checks, preprocessing of its sequence, uploads) overlapped with the
+ * previous job's simulation on the device: jobs alternate between ctx and a
+ * second context on the same device that the first batch call creates and
+ * ctx keeps (same memory budget; destroyed with ctx). Every job's inputs are
+ * copied to the device and its signal copied back, as in koma_simulate_host;
+ * results are identical to one koma_simulate_host per job. Synchronous: all
+ * signals are in place on return. Errors: as koma_simulate_host, the first
+ * failing job's (jobs after it are not run; the message is ctx's), and
+ * KOMA_E_INVALID for n_jobs < 0 or jobs NULL with n_jobs > 0.
+ */
+koma_status koma_simulate_host_batch(koma_ctx *ctx, int64_t n_jobs, const koma_host_job *jobs,
+                                     koma_precision precision);
+
 /* ------------------------------------------------------------------------
  * Serving: a continuous-batching simulation server.
  *

@@ -50,6 +50,12 @@ struct koma_ctx {
     size_t scratch_bytes = 0;
     int* d_status = nullptr;  // [0] device status flags, [1] batch counter of the grouped kernel
     cudaStream_t own_stream = nullptr;
+    // uploads (the phantom's copies and conversion, the synchronous copies
+    // and memsets): waited for by the host before anything that uses them is
+    // launched; high priority, so an upload's small kernels get SMs while
+    // another simulation's kernels run
+    cudaStream_t up_stream = nullptr;
+    cudaEvent_t ev_job = nullptr;  // end of the last batch job's work on own_stream
     cudaMemPool_t pool = nullptr;  // device memory of phantoms, sequences and scratch
     cudaStream_t alloc_stream = nullptr;  // orders the pool's allocations and frees only
     koma_launch_info last{};
@@ -76,6 +82,8 @@ struct koma_ctx {
     // assembled here and copied by DMA
     char* h_stage = nullptr;
     size_t h_stage_bytes = 0;
+    // second context of koma_simulate_host_batch (same device and budget)
+    koma_ctx* twin = nullptr;
 };
 
 struct koma_phantom {
@@ -235,14 +243,14 @@ void dev_free(koma_ctx* ctx, void* p, size_t bytes) {
 // The copy is therefore ordered on the context's own stream and waited for.
 cudaError_t h2d_sync(koma_ctx* ctx, void* dst, const void* src, size_t bytes) {
     if (bytes == 0) return cudaSuccess;
-    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->own_stream);
-    return e == cudaSuccess ? cudaStreamSynchronize(ctx->own_stream) : e;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->up_stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(ctx->up_stream) : e;
 }
 
 // Device memset complete on return (same reason as h2d_sync).
 cudaError_t memset_sync(koma_ctx* ctx, void* dst, int value, size_t bytes) {
-    cudaError_t e = cudaMemsetAsync(dst, value, bytes, ctx->own_stream);
-    return e == cudaSuccess ? cudaStreamSynchronize(ctx->own_stream) : e;
+    cudaError_t e = cudaMemsetAsync(dst, value, bytes, ctx->up_stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(ctx->up_stream) : e;
 }
 
 // Free ordered after the work already enqueued on `st` (the caller knows
@@ -406,13 +414,18 @@ extern "C" koma_status koma_init(int device, size_t mem_budget_bytes, koma_ctx**
     if (!ctx) return KOMA_E_NOMEM;
     ctx->device = device;
     ctx->budget = mem_budget_bytes;
+    int prio_least = 0, prio_greatest = 0;
     DeviceGuard g(device);
     if (!g.ok || cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(reinterpret_cast<void**>(&ctx->d_status), 2 * sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->up_stream, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
         memset_sync(ctx, ctx->d_status, 0, 2 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         if (ctx->d_status) cudaFree(ctx->d_status);
+        if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+        if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
         delete ctx;
         return KOMA_E_CUDA;
     }
@@ -433,6 +446,7 @@ extern "C" koma_status koma_init(int device, size_t mem_budget_bytes, koma_ctx**
             if (ctx->alloc_stream) cudaStreamDestroy(ctx->alloc_stream);
             if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
             cudaStreamDestroy(ctx->own_stream);
+            cudaStreamDestroy(ctx->up_stream);
             cudaFree(ctx->d_status);
             delete ctx;
             return KOMA_E_CUDA;
@@ -447,12 +461,19 @@ extern "C" koma_status koma_destroy(koma_ctx* ctx) {
     if (ctx->live_objects > 0)
         return fail(ctx, KOMA_E_BUSY, "koma_destroy: %lld phantoms/sequences still allocated",
                     static_cast<long long>(ctx->live_objects));
+    if (ctx->twin) {
+        const koma_status tw = koma_destroy(ctx->twin);
+        if (tw != KOMA_OK) return fail(ctx, tw, "koma_destroy: batch context: %s", ctx->twin->err.c_str());
+        ctx->twin = nullptr;
+    }
     DeviceGuard g(ctx->device);
     for (cudaEvent_t& e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->ev_maps) cudaEventDestroy(ctx->ev_maps);
     if (ctx->scratch) dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
+    if (ctx->ev_job) cudaEventDestroy(ctx->ev_job);
     if (ctx->alloc_stream) cudaStreamDestroy(ctx->alloc_stream);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->d_conv) cudaFree(ctx->d_conv);
@@ -473,7 +494,7 @@ extern "C" size_t koma_mem_used(const koma_ctx* ctx) { return ctx ? ctx->used : 
 namespace {
 
 // First half of a phantom upload: argument checks, device blocks, the copies
-// of the caller's rows and the conversion kernel, all enqueued on own_stream;
+// of the caller's rows and the conversion kernel, all enqueued on up_stream;
 // the conversion's status is copied back into ctx->h_conv (pinned). The
 // caller may do other host work before phantom_upload_finish. The FP64 block
 // receives the caller's rows [x, y, z, dw, T1, T2, pd] as they are (pinned
@@ -538,24 +559,24 @@ koma_status phantom_upload_start(koma_ctx* ctx, int64_t n, const double* x, cons
         const double* rows[koma::P64_N] = {x, y, z, dw, t1, t2, pd};  // the order of enum P64
         for (int r = 0; r < koma::P64_N && st == KOMA_OK && n > 0; ++r) {
             cudaError_t e = cudaMemcpyAsync(ph->p64 + r * np, rows[r], static_cast<size_t>(n) * sizeof(double),
-                                            cudaMemcpyHostToDevice, ctx->own_stream);
+                                            cudaMemcpyHostToDevice, ctx->up_stream);
             if (e != cudaSuccess) st = cuda_fail(ctx, e, "phantom_upload: copy");
         }
     }
     if (st == KOMA_OK) {
-        cudaError_t ce = cudaMemsetAsync(ctx->d_conv, 0, sizeof(koma::ConvertStatus), ctx->own_stream);
+        cudaError_t ce = cudaMemsetAsync(ctx->d_conv, 0, sizeof(koma::ConvertStatus), ctx->up_stream);
         if (ce == cudaSuccess)
-            ce = cudaMemsetAsync(&ctx->d_conv->first_bad, 0xff, sizeof(unsigned long long), ctx->own_stream);
+            ce = cudaMemsetAsync(&ctx->d_conv->first_bad, 0xff, sizeof(unsigned long long), ctx->up_stream);
         if (ce == cudaSuccess)
             ce = static_cast<cudaError_t>(koma::launch_phantom_convert(ph->p64, ph->p32, n, np, ctx->d_conv,
-                                                                       ctx->own_stream));
+                                                                       ctx->up_stream));
         if (ce == cudaSuccess)
             ce = cudaMemcpyAsync(ctx->h_conv, ctx->d_conv, sizeof(koma::ConvertStatus), cudaMemcpyDeviceToHost,
-                                 ctx->own_stream);
+                                 ctx->up_stream);
         if (ce != cudaSuccess) st = cuda_fail(ctx, ce, "phantom_upload: conversion");
     }
     if (st != KOMA_OK) {
-        cudaStreamSynchronize(ctx->own_stream);  // no copy may still read or write the blocks
+        cudaStreamSynchronize(ctx->up_stream);  // no copy may still read or write the blocks
         dev_free(ctx, ph->p32, b32);
         dev_free(ctx, ph->p64, b64);
         delete ph;
@@ -575,7 +596,7 @@ koma_status phantom_upload_finish(koma_ctx* ctx, koma_phantom** out, const doubl
                                   const double* dw) {
     koma_phantom* ph = *out;
     DeviceGuard g(ctx->device);
-    cudaError_t ce = cudaStreamSynchronize(ctx->own_stream);
+    cudaError_t ce = cudaStreamSynchronize(ctx->up_stream);
     koma_status st = ce == cudaSuccess ? KOMA_OK : cuda_fail(ctx, ce, "phantom_upload: conversion");
     if (st == KOMA_OK && ctx->h_conv->first_bad != ~0ull) {  // report the first offending spin
         std::string msg;
@@ -2504,6 +2525,76 @@ extern "C" koma_status koma_get_launch_info(const koma_ctx* ctx, koma_launch_inf
     return KOMA_OK;
 }
 
+namespace {
+
+// A host-buffer simulation in two halves, so that a batch can run one job's
+// host work while the device simulates the previous one: start = checks,
+// uploads (the phantom's copies and conversion on the device while the host
+// preprocesses the sequence), the simulation and the signal's copy-back
+// enqueued on the context's stream; finish = wait, then the stream-ordered
+// frees.
+struct HostJob {
+    koma_phantom* ph = nullptr;
+    koma_sequence* seq = nullptr;
+    double* d_sig = nullptr;
+    size_t out_bytes = 0;
+    bool active = false;
+};
+
+koma_status host_job_finish(koma_ctx* ctx, HostJob& J, koma_status st) {
+    if (!J.active) return st;
+    DeviceGuard g(ctx->device);
+    if (st == KOMA_OK) st = koma_sync(ctx, ctx->own_stream);
+    // every use of these blocks was on own_stream: frees ordered there
+    dev_free_on(ctx, J.d_sig, J.out_bytes, ctx->own_stream);
+    koma::sequence_free_on(J.seq, ctx->own_stream);
+    koma::phantom_free_on(J.ph, ctx->own_stream);
+    J = HostJob{};
+    return st;
+}
+
+// `after`: an event the simulation waits for (a batch runs its jobs' device
+// work one after another: two simulations sharing the GPU slow each other
+// down more than they gain); `done`: recorded after the signal's copy-back.
+koma_status host_job_start(koma_ctx* ctx, const koma_host_job& j, koma_precision precision, HostJob& J,
+                           cudaEvent_t after = nullptr, cudaEvent_t done = nullptr) {
+    J = HostJob{};
+    J.active = true;
+    koma_status st = phantom_upload_start(ctx, j.n, j.x, j.y, j.z, j.pd, j.t1, j.t2, j.dw, j.group_offsets,
+                                          j.n_groups, &J.ph);
+    // the phantom is static here: no motion records; FP64 records only for the FP64 path
+    if (st == KOMA_OK)
+        st = sequence_upload_impl(ctx, j.n_steps, j.dt, j.gx, j.gy, j.gz, j.b1_re, j.b1_im, j.adc,
+                                  precision == KOMA_FP64, false, &J.seq);
+    if (J.ph) {
+        const koma_status sp = phantom_upload_finish(ctx, &J.ph, j.x, j.y, j.z, j.pd, j.t1, j.t2, j.dw);
+        if (st == KOMA_OK) st = sp;
+    }
+    DeviceGuard g(ctx->device);
+    if (st == KOMA_OK) {
+        J.out_bytes = static_cast<size_t>(J.seq->info.n_adc * J.ph->n_groups) * 2 * sizeof(double);
+        if (J.out_bytes && !j.sig_host) st = fail(ctx, KOMA_E_INVALID, "simulate_host: sig_host is NULL");
+    }
+    if (st == KOMA_OK)
+        st = dev_alloc(ctx, reinterpret_cast<void**>(&J.d_sig), J.out_bytes, "simulate_host: signal");
+    if (st == KOMA_OK && after) {
+        const cudaError_t e = cudaStreamWaitEvent(ctx->own_stream, after, 0);
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "simulate_host: ordering after the previous job");
+    }
+    if (st == KOMA_OK) st = koma_simulate(ctx, J.ph, J.seq, precision, J.d_sig, ctx->own_stream);
+    if (st == KOMA_OK && J.out_bytes) {
+        cudaError_t e = cudaMemcpyAsync(j.sig_host, J.d_sig, J.out_bytes, cudaMemcpyDeviceToHost, ctx->own_stream);
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "simulate_host: copy back");
+    }
+    if (st == KOMA_OK && done) {
+        const cudaError_t e = cudaEventRecord(done, ctx->own_stream);
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "simulate_host: job event");
+    }
+    return st;
+}
+
+}  // namespace
+
 extern "C" koma_status koma_simulate_host(koma_ctx* ctx, int64_t n, const double* x, const double* y,
                                           const double* z, const double* pd, const double* t1, const double* t2,
                                           const double* dw, const int64_t* group_offsets, int64_t n_groups,
@@ -2512,37 +2603,56 @@ extern "C" koma_status koma_simulate_host(koma_ctx* ctx, int64_t n, const double
                                           const uint8_t* adc, koma_precision precision, double* sig_host) {
     NvtxRange nvtx_("koma_simulate_host");
     if (!ctx) return KOMA_E_INVALID;
-    koma_phantom* ph = nullptr;
-    koma_sequence* seq = nullptr;
-    double* d_sig = nullptr;
-    // the phantom's copies and conversion run on the device while the host
-    // preprocesses and uploads the sequence
-    koma_status st = phantom_upload_start(ctx, n, x, y, z, pd, t1, t2, dw, group_offsets, n_groups, &ph);
-    // the phantom is static here: no motion records; FP64 records only for the FP64 path
-    if (st == KOMA_OK)
-        st = sequence_upload_impl(ctx, n_steps, dt, gx, gy, gz, b1_re, b1_im, adc, precision == KOMA_FP64, false,
-                                  &seq);
-    if (ph) {
-        const koma_status sp = phantom_upload_finish(ctx, &ph, x, y, z, pd, t1, t2, dw);
-        if (st == KOMA_OK) st = sp;
+    const koma_host_job j{n, x, y, z, pd, t1, t2, dw, group_offsets, n_groups, n_steps,
+                          dt, gx, gy, gz, b1_re, b1_im, adc, sig_host};
+    HostJob J;
+    const koma_status st = host_job_start(ctx, j, precision, J);
+    return host_job_finish(ctx, J, st);
+}
+
+extern "C" koma_status koma_simulate_host_batch(koma_ctx* ctx, int64_t n_jobs, const koma_host_job* jobs,
+                                                koma_precision precision) {
+    NvtxRange nvtx_("koma_simulate_host_batch");
+    if (!ctx) return KOMA_E_INVALID;
+    if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(ctx, KOMA_E_INVALID, "simulate_host_batch: bad job list");
+    if (n_jobs > 1 && !ctx->twin) {
+        const koma_status ti = koma_init(ctx->device, ctx->budget, &ctx->twin);
+        if (ti != KOMA_OK) {
+            ctx->twin = nullptr;
+            return fail(ctx, ti, "simulate_host_batch: second context: cannot create it");
+        }
+        ctx->twin->mma_enabled = ctx->mma_enabled;
+        ctx->twin->rf_maps_enabled = ctx->rf_maps_enabled;
+        ctx->twin->tune_cache = ctx->tune_cache;
     }
-    size_t out_bytes = 0;
-    DeviceGuard g(ctx->device);
-    if (st == KOMA_OK) {
-        out_bytes = static_cast<size_t>(seq->info.n_adc * ph->n_groups) * 2 * sizeof(double);
-        if (out_bytes && !sig_host) st = fail(ctx, KOMA_E_INVALID, "simulate_host: sig_host is NULL");
+    koma_ctx* c[2] = {ctx, ctx->twin ? ctx->twin : ctx};
+    for (koma_ctx* x : c) {
+        DeviceGuard g(x->device);
+        if (!x->ev_job && cudaEventCreateWithFlags(&x->ev_job, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            x->ev_job = nullptr;
+            return fail(ctx, KOMA_E_CUDA, "simulate_host_batch: event creation");
+        }
     }
-    if (st == KOMA_OK) st = dev_alloc(ctx, reinterpret_cast<void**>(&d_sig), out_bytes, "simulate_host: signal");
-    if (st == KOMA_OK) st = koma_simulate(ctx, ph, seq, precision, d_sig, ctx->own_stream);
-    if (st == KOMA_OK && out_bytes) {
-        cudaError_t e = cudaMemcpyAsync(sig_host, d_sig, out_bytes, cudaMemcpyDeviceToHost, ctx->own_stream);
-        if (e != cudaSuccess) st = cuda_fail(ctx, e, "simulate_host: copy back");
+    HostJob J[2];
+    koma_status st = KOMA_OK;
+    int failed = 0;
+    for (int64_t i = 0; i < n_jobs && st == KOMA_OK; ++i) {
+        const int k = static_cast<int>(i & 1);
+        st = host_job_finish(c[k], J[k], KOMA_OK);  // the job this context ran two jobs ago
+        // this job's device work follows the previous job's
+        if (st == KOMA_OK)
+            st = host_job_start(c[k], jobs[i], precision, J[k], i > 0 ? c[k ^ 1]->ev_job : nullptr, c[k]->ev_job);
+        if (st != KOMA_OK) failed = k;
     }
-    if (st == KOMA_OK) st = koma_sync(ctx, ctx->own_stream);
-    // every use of these blocks was on own_stream: frees ordered there
-    dev_free_on(ctx, d_sig, out_bytes, ctx->own_stream);
-    koma::sequence_free_on(seq, ctx->own_stream);
-    koma::phantom_free_on(ph, ctx->own_stream);
+    for (int k = 0; k < 2; ++k) {
+        const koma_status sk = host_job_finish(c[k], J[k], KOMA_OK);
+        if (st == KOMA_OK && sk != KOMA_OK) {
+            st = sk;
+            failed = k;
+        }
+    }
+    if (st != KOMA_OK && c[failed] != ctx) return fail(ctx, st, "%s", c[failed]->err.c_str());
     return st;
 }
 

@@ -32,7 +32,8 @@ EXPORTS = (
     "koma_phantom_set_motion",
     "koma_sequence_upload", "koma_sequence_n_adc", "koma_sequence_n_steps", "koma_sequence_get_info",
     "koma_sequence_free", "koma_sequence_plan", "koma_simulate", "koma_sync", "koma_set_timing",
-    "koma_get_timing", "koma_get_launch_info", "koma_simulate_host", "koma_simulate_static", "koma_tune",
+    "koma_get_timing", "koma_get_launch_info", "koma_simulate_host", "koma_simulate_host_batch",
+    "koma_simulate_static", "koma_tune",
     "koma_server_create", "koma_server_submit", "koma_server_wait", "koma_server_get_stats",
     "koma_server_last_error", "koma_server_destroy", "koma_check_bounded_wait", "koma_get_stage_timing",
     "koma_set_mma", "koma_set_rf_maps", "koma_get_map_timing",
@@ -43,6 +44,16 @@ class KomaError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
         self.status = status
+
+
+class HostJob(ctypes.Structure):
+    """koma_host_job: one simulation of koma_simulate_host_batch."""
+    _fields_ = ([("n", ctypes.c_int64)] + [(f, ctypes.POINTER(ctypes.c_double)) for f in
+                                          ("x", "y", "z", "pd", "t1", "t2", "dw")] +
+                [("group_offsets", ctypes.POINTER(ctypes.c_int64)), ("n_groups", ctypes.c_int64),
+                 ("n_steps", ctypes.c_int64)] +
+                [(f, ctypes.POINTER(ctypes.c_double)) for f in ("dt", "gx", "gy", "gz", "b1_re", "b1_im")] +
+                [("adc", ctypes.POINTER(ctypes.c_uint8)), ("sig_host", ctypes.POINTER(ctypes.c_double))])
 
 
 class LaunchInfo(ctypes.Structure):
@@ -193,6 +204,8 @@ def load(path: Optional[str] = None):
         lib.koma_check_bounded_wait.argtypes = [_vp, ctypes.c_int64, _vp]
         lib.koma_simulate_static.restype = st
         lib.koma_simulate_static.argtypes = [_vp, _vp, _vp, _vp]
+        lib.koma_simulate_host_batch.restype = st
+        lib.koma_simulate_host_batch.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(HostJob), ctypes.c_int]
         lib.koma_simulate_host.restype = st
         lib.koma_simulate_host.argtypes = ([_vp, ctypes.c_int64] + [_dp] * 7 + [_i64p, ctypes.c_int64,
                                            ctypes.c_int64] + [_dp] * 6 + [_u8p, ctypes.c_int, _dp])
@@ -438,6 +451,40 @@ def koma_simulate_host(ctx, phantom, seq, precision: int = KOMA_FP32_SPLITPHASE,
                                    out.ctypes.data_as(_dp))
     _check(ctx, rc, "koma_simulate_host")
     return out
+
+
+def koma_simulate_host_batch(ctx, jobs, precision: int = KOMA_FP32_SPLITPHASE):
+    """koma_simulate_host for each (phantom, seq, out) of `jobs`, one job's
+    host work overlapped with the previous job's simulation; `out` as for
+    koma_simulate_host (allocated when None). Returns the outputs."""
+    keep, arr, outs = [], (HostJob * max(1, len(jobs)))(), []
+    for i, (phantom, seq, out) in enumerate(jobs):
+        ph = [_f64(getattr(phantom, f)) for f in ("x", "y", "z", "pd", "t1", "t2", "dw")]
+        go = getattr(phantom, "group_offsets", None)
+        go_arr = None if go is None else np.ascontiguousarray(go, dtype=np.int64)
+        n_groups = 1 if go_arr is None else go_arr.shape[0] - 1
+        sq = _seq_arrays(seq)
+        n_adc = int(np.count_nonzero(sq[6]))
+        if out is None:
+            out = np.empty((n_groups, n_adc), dtype=np.complex128)
+        assert out.dtype == np.complex128 and out.flags.c_contiguous and out.size == n_groups * n_adc
+        keep += ph + list(sq) + [go_arr, out]
+        j = arr[i]
+        j.n = ph[0].shape[0]
+        for f, a in zip(("x", "y", "z", "pd", "t1", "t2", "dw"), ph):
+            setattr(j, f, _ptr(a))
+        j.group_offsets = None if go_arr is None else _ptr(go_arr, ctypes.c_int64)
+        j.n_groups = n_groups
+        j.n_steps = sq[0].shape[0]
+        for f, a in zip(("dt", "gx", "gy", "gz", "b1_re", "b1_im"), sq[:6]):
+            setattr(j, f, _ptr(a))
+        j.adc = _ptr(sq[6], ctypes.c_uint8)
+        j.sig_host = out.ctypes.data_as(_dp)
+        outs.append(out)
+    rc = load().koma_simulate_host_batch(ctx, len(jobs), arr, int(precision))
+    _check(ctx, rc, "koma_simulate_host_batch")
+    del keep
+    return outs
 
 
 # --------------------------------------------------------------------------
