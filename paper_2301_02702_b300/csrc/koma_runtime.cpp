@@ -352,6 +352,10 @@ class HostPool {
 // already run side by side, like the server's, keep theirs serial).
 thread_local bool t_host_parallel = true;
 
+// (defined with the record builder below)
+int n_workers_for(int k);
+void run_tasks(int k, const std::function<void(int)>& run);
+
 // fn(lo, hi) over [0, n) split across host threads for large n.
 template <class Fn>
 void parallel_for(int64_t n, Fn&& fn) {
@@ -528,14 +532,7 @@ koma_status phantom_upload_start(koma_ctx* ctx, int64_t n, const double* x, cons
     ph->n = n;
     ph->n_pad = std::max<int64_t>(32, (n + 31) / 32 * 32);
     ph->n_groups = group_offsets ? n_groups : 1;
-    if (group_offsets) {
-        ph->group_offsets.assign(group_offsets, group_offsets + n_groups + 1);
-        bool uni = true;
-        for (int64_t gi = 0; gi < n_groups && uni; ++gi)
-            for (int64_t j = group_offsets[gi] + 1; j < group_offsets[gi + 1] && uni; ++j)
-                uni = t1[j] == t1[group_offsets[gi]] && t2[j] == t2[group_offsets[gi]];
-        ph->uni_relax = uni;
-    }
+    if (group_offsets) ph->group_offsets.assign(group_offsets, group_offsets + n_groups + 1);
     const int64_t np = ph->n_pad;
 
     DeviceGuard g(ctx->device);
@@ -581,6 +578,20 @@ koma_status phantom_upload_start(koma_ctx* ctx, int64_t n, const double* x, cons
         dev_free(ctx, ph->p64, b64);
         delete ph;
         return st;
+    }
+    // while the rows travel: does every group have a single T1 and T2 (in
+    // slices of groups for large phantoms)?
+    if (group_offsets) {
+        const int k = n >= (int64_t{1} << 20) ? n_workers_for(16) : 1;
+        std::vector<uint8_t> uni(static_cast<size_t>(k), 1);
+        run_tasks(k, [&](int w) {
+            bool u = true;
+            for (int64_t gi = n_groups * w / k; gi < n_groups * (w + 1) / k && u; ++gi)
+                for (int64_t j = group_offsets[gi] + 1; j < group_offsets[gi + 1] && u; ++j)
+                    u = t1[j] == t1[group_offsets[gi]] && t2[j] == t2[group_offsets[gi]];
+            uni[w] = u;
+        });
+        ph->uni_relax = std::find(uni.begin(), uni.end(), 0) == uni.end();
     }
     ph->bytes = b32 + b64;
     ctx->live_objects++;
@@ -1789,43 +1800,53 @@ koma_status ensure_items(koma_ctx* ctx, koma_phantom* ph, int S) {
 koma_status ensure_zunits(koma_ctx* ctx, koma_phantom* ph) {
     if (ph->items_s == 8 && ph->d_items) return KOMA_OK;
     constexpr int64_t kUnit = 8, kWarpUnits = 32;
-    std::vector<int64_t> ub;
-    std::vector<int32_t> uitem;
-    std::vector<int32_t> gi(static_cast<size_t>(ph->n_groups + 1), 0);
-    ub.reserve(static_cast<size_t>(ph->n / kUnit + ph->n_groups + 1));
-    uitem.reserve(ub.capacity());
-    int64_t item = -1, u = 0;
-    for (int64_t g = 0; g < ph->n_groups; ++g) {
-        gi[g] = static_cast<int32_t>(item + 1);
-        const int64_t lo = ph->group_offsets[g], hi = ph->group_offsets[g + 1];
-        for (int64_t s0 = lo; s0 < hi; s0 += kUnit, ++u) {
-            if (s0 == lo || u % kWarpUnits == 0) ++item;
-            ub.push_back(s0);
-            uitem.push_back(static_cast<int32_t>(item));
-        }
-        if (item + 2 > std::numeric_limits<int32_t>::max())
-            return fail(ctx, KOMA_E_INVALID, "simulate: grouped phantom needs too many work items");
+    const int64_t G = ph->n_groups;
+    // first unit and first item of every group: a group of m units has one
+    // item plus one per warp start (a multiple of 32) strictly inside its units
+    std::vector<int64_t> u0(static_cast<size_t>(G + 1), 0), i0(static_cast<size_t>(G + 1), 0);
+    for (int64_t g = 0; g < G; ++g) {
+        const int64_t m = (ph->group_offsets[g + 1] - ph->group_offsets[g] + kUnit - 1) / kUnit;
+        u0[g + 1] = u0[g] + m;
+        i0[g + 1] = i0[g] + (m > 0 ? 1 + (u0[g] + m - 1) / kWarpUnits - u0[g] / kWarpUnits : 0);
     }
-    gi[ph->n_groups] = static_cast<int32_t>(item + 1);
-    ub.push_back(ph->n);
+    const int64_t n_units = u0[G], n_items = i0[G];
+    if (n_items + 1 > std::numeric_limits<int32_t>::max())
+        return fail(ctx, KOMA_E_INVALID, "simulate: grouped phantom needs too many work items");
     if (ph->d_items) dev_free(ctx, ph->d_items, ph->items_bytes);
     ph->d_items = nullptr;
     ph->items_s = 0;
     auto up16 = [](size_t b) { return (b + 15) / 16 * 16; };
-    const size_t b_ub = ub.size() * sizeof(int64_t), b_ui = up16(uitem.size() * sizeof(int32_t)),
-                 b_gi = gi.size() * sizeof(int32_t);
+    const size_t b_ub = static_cast<size_t>(n_units + 1) * sizeof(int64_t),
+                 b_ui = up16(static_cast<size_t>(n_units) * sizeof(int32_t)),
+                 b_gi = static_cast<size_t>(G + 1) * sizeof(int32_t);
     koma_status st = dev_alloc(ctx, reinterpret_cast<void**>(&ph->d_items), b_ub + b_ui + b_gi,
                                "simulate: unit table");
+    if (st == KOMA_OK) st = stage_reserve(ctx, b_ub + b_ui + b_gi, 0);
     if (st != KOMA_OK) return st;
     ph->items_bytes = b_ub + b_ui + b_gi;
     ph->d_order = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ph->d_items) + b_ub);
     ph->d_group_item = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ph->d_items) + b_ub + b_ui);
-    cudaError_t e = h2d_sync(ctx, ph->d_items, ub.data(), b_ub);
-    if (e == cudaSuccess && !uitem.empty()) e = h2d_sync(ctx, ph->d_order, uitem.data(), uitem.size() * sizeof(int32_t));
-    if (e == cudaSuccess) e = h2d_sync(ctx, ph->d_group_item, gi.data(), b_gi);
+    // the table, assembled in the pinned staging buffer (groups in parallel slices)
+    int64_t* ub = reinterpret_cast<int64_t*>(ctx->h_stage);
+    int32_t* ui = reinterpret_cast<int32_t*>(ctx->h_stage + b_ub);
+    int32_t* gi = reinterpret_cast<int32_t*>(ctx->h_stage + b_ub + b_ui);
+    const int k = n_units >= (int64_t{1} << 16) ? n_workers_for(16) : 1;
+    run_tasks(k, [&](int w) {
+        for (int64_t g = G * w / k; g < G * (w + 1) / k; ++g) {
+            const int64_t lo = ph->group_offsets[g];
+            gi[g] = static_cast<int32_t>(i0[g]);
+            for (int64_t u = u0[g]; u < u0[g + 1]; ++u) {
+                ub[u] = lo + (u - u0[g]) * kUnit;
+                ui[u] = static_cast<int32_t>(i0[g] + u / kWarpUnits - u0[g] / kWarpUnits);
+            }
+        }
+    });
+    gi[G] = static_cast<int32_t>(n_items);
+    ub[n_units] = ph->n;
+    cudaError_t e = h2d_sync(ctx, ph->d_items, ctx->h_stage, b_ub + b_ui + b_gi);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "simulate: unit table copy");
-    ph->n_items = item + 1;
-    ph->n_units = u;
+    ph->n_items = n_items;
+    ph->n_units = n_units;
     ph->items_s = 8;
     return KOMA_OK;
 }
@@ -2555,7 +2576,8 @@ koma_status host_job_finish(koma_ctx* ctx, HostJob& J, koma_status st) {
 
 // `after`: an event the simulation waits for (a batch runs its jobs' device
 // work one after another: two simulations sharing the GPU slow each other
-// down more than they gain); `done`: recorded after the signal's copy-back.
+// down more than they gain); `done`: recorded after the simulation, before
+// the signal's copy-back.
 koma_status host_job_start(koma_ctx* ctx, const koma_host_job& j, koma_precision precision, HostJob& J,
                            cudaEvent_t after = nullptr, cudaEvent_t done = nullptr) {
     J = HostJob{};
@@ -2582,13 +2604,13 @@ koma_status host_job_start(koma_ctx* ctx, const koma_host_job& j, koma_precision
         if (e != cudaSuccess) st = cuda_fail(ctx, e, "simulate_host: ordering after the previous job");
     }
     if (st == KOMA_OK) st = koma_simulate(ctx, J.ph, J.seq, precision, J.d_sig, ctx->own_stream);
+    if (st == KOMA_OK && done) {  // before the copy-back, which overlaps the next job's simulation
+        const cudaError_t e = cudaEventRecord(done, ctx->own_stream);
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "simulate_host: job event");
+    }
     if (st == KOMA_OK && J.out_bytes) {
         cudaError_t e = cudaMemcpyAsync(j.sig_host, J.d_sig, J.out_bytes, cudaMemcpyDeviceToHost, ctx->own_stream);
         if (e != cudaSuccess) st = cuda_fail(ctx, e, "simulate_host: copy back");
-    }
-    if (st == KOMA_OK && done) {
-        const cudaError_t e = cudaEventRecord(done, ctx->own_stream);
-        if (e != cudaSuccess) st = cuda_fail(ctx, e, "simulate_host: job event");
     }
     return st;
 }
