@@ -2643,6 +2643,8 @@ extern "C" koma_status koma_simulate_host_batch(koma_ctx* ctx, int64_t n_jobs, c
             ctx->twin = nullptr;
             return fail(ctx, ti, "simulate_host_batch: second context: cannot create it");
         }
+    }
+    if (ctx->twin) {  // the second context simulates as ctx would: its switches and tuned shapes
         ctx->twin->mma_enabled = ctx->mma_enabled;
         ctx->twin->rf_maps_enabled = ctx->rf_maps_enabled;
         ctx->twin->tune_cache = ctx->tune_cache;

@@ -62,3 +62,27 @@ def test_failing_job_stops_the_batch(ctx, bad_at):
     ph, seq = workload("se128", "small")
     (out,) = koma.koma_simulate_host_batch(ctx, [(ph, seq, None)])
     assert np.array_equal(out, koma.koma_simulate_host(ctx, ph, seq, koma.KOMA_FP32_SPLITPHASE))
+
+
+def test_batch_follows_the_context_switches_and_fp64(ctx):
+    """Switches set on the context after its second context exists apply to
+    every job of the next batch (readout on the tensor cores off, repeated
+    pulses stepped), and an FP64 batch equals FP64 single calls."""
+    jobs = [workload("se128", "small"), workload("epi512", "small"), workload("se128", "small")]
+    koma.koma_simulate_host_batch(ctx, [(ph, seq, None) for ph, seq in jobs])  # the second context exists
+    lib = koma.load()
+    try:
+        lib.koma_set_mma(ctx, 0)
+        lib.koma_set_rf_maps(ctx, 0)
+        single = [koma.koma_simulate_host(ctx, ph, seq, koma.KOMA_FP32_SPLITPHASE) for ph, seq in jobs]
+        outs = koma.koma_simulate_host_batch(ctx, [(ph, seq, None) for ph, seq in jobs])
+        for a, b in zip(outs, single):
+            assert np.array_equal(a, b)
+    finally:
+        lib.koma_set_mma(ctx, 1)
+        lib.koma_set_rf_maps(ctx, 1)
+    ph, seq = workload("gre32", "small")
+    one = koma.koma_simulate_host(ctx, ph, seq, koma.KOMA_FP64)
+    outs = koma.koma_simulate_host_batch(ctx, [(ph, seq, None), (ph, seq, None)], koma.KOMA_FP64)
+    assert all(np.array_equal(o, one) for o in outs)
+    assert np.max(np.abs(one - oracle.simulate(ph, seq))) < 1e-9 * np.max(np.abs(one))
