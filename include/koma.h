@@ -463,7 +463,7 @@ typedef struct {
                                 checkpointed between launches (long sequences do not hold the GPU);
                                 0 = 4096 */
     int64_t plain_spins;     /* requests with at least this many spins run the koma_simulate
-                                path in the server's second lane; 0 = 32768, < 0 = never
+                                path in the server's second lane; 0 = 524288, < 0 = never
                                 (grouped requests always do) */
 } koma_server_config;
 
