@@ -308,8 +308,11 @@ koma_status koma_simulate_static(const koma_phantom *ph, const koma_sequence *se
  * Autotune the FP32 launch for this (phantom, sequence) pair: times the
  * candidate configurations on the full problem (grouped phantoms: spins per
  * thread {2, 4} x block {128, 256} x sequence-tile length {64, 128, 256}
- * records of the work-item kernel; otherwise spins per thread {2, 4} of the
- * Bloch kernel) and keeps the fastest on the
+ * records of the work-item kernel, plus, for a dictionary of isochromats
+ * along z, the dictionary kernel (spins_per_thread 8 in the launch info)
+ * with tiles {128, 256} and block 128 (also 256 when it takes the hi/lo
+ * phase); otherwise spins per thread {2, 4} of the Bloch kernel) and keeps
+ * the fastest on the
  * phantom; later koma_simulate calls with this sequence use it. The choice
  * is also cached on the context by problem shape (kernel family and the
  * powers of two of spins, groups, records, ADC samples and RF steps), and
