@@ -114,6 +114,14 @@ typedef struct {
     int64_t n_rf_map_steps; /* ... the RF steps of those occurrences ...     */
     int64_t n_rf_map_pulse_steps; /* ... and the steps of the distinct pulses
                              (what the map pre-pass steps per spin)          */
+    int64_t z_dict;       /* 1: no RF step has a z gradient and every ADC
+                             record holds one sample, so a grouped phantom of
+                             isochromats along z (x = y = 0, no off-resonance,
+                             one T1/T2 per group) takes the dictionary kernel */
+    double z_kmax;        /* with z_dict: max |Kz| (turns/m) over the phase
+                             records; max |z| x z_kmax <= 1 lets the
+                             dictionary kernel take the phase as one FP32
+                             product (0 without z_dict)                       */
 } koma_sequence_info;
 
 /* gamma used by the library, rad/s/T. */

@@ -1473,6 +1473,11 @@ void plan_rf_maps(koma::RecSpan r32, RfMapPlan& P) {
     }
 }
 
+namespace {
+bool z_dictionary_stream(koma::RecSpan r32);
+double build_z_stream(koma::RecSpan r32, std::vector<koma::Rec32>& out);
+}  // namespace
+
 extern "C" koma_status koma_sequence_plan(int64_t n_steps, const double* dt, const double* gx, const double* gy,
                                           const double* gz, const double* b1_re, const double* b1_im,
                                           const uint8_t* adc, koma_sequence_info* info, double* rec_out,
@@ -1493,6 +1498,11 @@ extern "C" koma_status koma_sequence_plan(int64_t n_steps, const double* dt, con
     info->n_rf_map_runs = fp.runs;
     info->n_rf_map_steps = fp.steps;
     info->n_rf_map_pulse_steps = fp.pulse_steps;
+    info->z_dict = z_dictionary_stream(rb.r32) ? 1 : 0;
+    if (info->z_dict) {
+        std::vector<koma::Rec32> rz;
+        info->z_kmax = build_z_stream(rb.r32, rz);
+    }
     if (rec_out) {
         if (rec_capacity < info->n_records) return KOMA_E_INVALID;
         for (int64_t r = 0; r < info->n_records; ++r) {
@@ -1620,6 +1630,8 @@ koma_status sequence_upload_impl(koma_ctx* ctx, int64_t n_steps, const double* d
     seq->z_dict = z_dictionary_stream(recs);
     std::vector<koma::Rec32> rz;
     if (seq->z_dict) seq->z_kmax = build_z_stream(recs, rz);
+    seq->info.z_dict = seq->z_dict ? 1 : 0;
+    seq->info.z_kmax = seq->z_kmax;
     MmaPlan mp;
     plan_mma(recs, info.n_adc, mp);
     seq->info.n_mma_groups = static_cast<int64_t>(mp.groups.size());

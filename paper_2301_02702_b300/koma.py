@@ -74,7 +74,8 @@ class SequenceInfo(ctypes.Structure):
                 ("n_mma_groups", ctypes.c_int64), ("n_mma_runs", ctypes.c_int64),
                 ("n_mma_samples", ctypes.c_int64), ("n_rf_maps", ctypes.c_int64),
                 ("n_rf_map_runs", ctypes.c_int64), ("n_rf_map_steps", ctypes.c_int64),
-                ("n_rf_map_pulse_steps", ctypes.c_int64)]
+                ("n_rf_map_pulse_steps", ctypes.c_int64), ("z_dict", ctypes.c_int64),
+                ("z_kmax", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -262,6 +262,28 @@ def test_plan_on_long_streams_follows_the_rule(lib):
     assert info["n_rf_map_pulse_steps"] == sum(pulses[p][0] for p in cls)
 
 
+def test_plan_reports_the_dictionary_kernels_stream_condition(lib):
+    """The record stream's half of the dictionary kernel's condition (no RF step
+    with a z gradient, one sample per ADC record) and the largest |Kz| of the
+    phase records, which picks its one-product phase: the FISP dictionary
+    train qualifies with max |Kz| = the unbalanced lobe's moment, one turn per
+    voxel length; slice-selective pulses (se128), multi-sample readouts
+    (epi512) and a FISP train sampling twice per TR do not."""
+    from paper_2301_02702_b300.workloads import mrf_fisp
+    info = koma.koma_sequence_plan(mrf_fisp(n_tr=40, voxel=1e-3))
+    assert info["z_dict"] == 1
+    assert info["z_kmax"] == pytest.approx(1.0 / 1e-3, rel=1e-6)
+    assert koma.koma_sequence_plan(mrf_fisp(n_tr=40, voxel=2e-3))["z_kmax"] == pytest.approx(500.0, rel=1e-6)
+    for name in ("se128", "epi512"):
+        info = koma.koma_sequence_plan(workload(name, "small")[1])
+        assert info["z_dict"] == 0 and info["z_kmax"] == 0.0, name
+    b = SequenceBuilder()
+    for _ in range(5):
+        b.steps(1, 1e-4, b1=2e-6).steps(1, 3e-3).steps(2, 1e-5, adc=True)
+        b.steps(1, 2e-4, [0, 0, 0.01]).steps(1, 2e-4, [0, 0, 0]).steps(1, 8e-3)
+    assert koma.koma_sequence_plan(b.build())["z_dict"] == 0
+
+
 def test_plan_finds_repeated_pulses(lib):
     """Runs of RF steps that recur unchanged at least 3 times (and are at
     least 4 steps long) get a map slot; at most 8 slots, the ones saving the
