@@ -697,6 +697,32 @@ def run_ours(args, rank, world, local):
             err = rel_err_of(run_once(par_handle, mma=False), par_ref, par_groups)
             no_mma["rel_err"] = err
             no_mma["pass"] = err <= TOL
+    # gre32 is specified in FP64: the same step through KOMA_FP64 (one spin per
+    # thread, every sample evaluated in FP64), with its own parity
+    fp64_leg = None
+    if rank == 0 and args.workload == "gre32":
+        for _ in range(2):
+            sim.simulate(hp, hs, "fp64", out=out, stream=stream)
+        sim.sync(stream)
+        n64 = max(1, min(args.steps, 5))
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n64)]
+        for e0, e1 in evs:
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0.record(stream)
+                sim.simulate(hp, hs, "fp64", out=out, stream=stream)
+                e1.record(stream)
+        sim.sync(stream)
+        ms64 = sum(a.elapsed_time(b) for a, b in evs) / n64
+        fp64_leg = {"value": units / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": n64, "dtype": "f64",
+                    "path": "KOMA_FP64: every operation in FP64, one spin per thread, every sample evaluated"}
+        if par_handle is hp and par_ref is not None:
+            with torch.cuda.stream(stream):
+                sim.simulate(hp, hs, "fp64", out=out, stream=stream)
+            sim.sync(stream)
+            err = rel_err_of(out.cpu().numpy(), par_ref, par_groups)
+            fp64_leg["rel_err"] = err
+            fp64_leg["pass"] = err <= 1e-9
     # the same step with every RF step stepped (repeated pulses not taken by
     # their maps), with its own parity
     no_maps = None
@@ -886,6 +912,8 @@ def run_ours(args, rank, world, local):
         line.update({"cpu_baseline": cpu, "e2e": e2e, "parity": parity})
         if no_mma is not None:
             line["no_tensor_cores"] = no_mma
+        if fp64_leg is not None:
+            line["fp64"] = fp64_leg
         if no_maps is not None:
             line["no_rf_maps"] = no_maps
         if vs_plain is not None:
